@@ -1,0 +1,47 @@
+"""Small seeded systems for the oracle pins and parity tests (inputs only)."""
+from __future__ import annotations
+
+import numpy as np
+
+import workloads
+from workloads import System, ncart, _plane_waves, _finish_shells, _log_uniform
+
+
+def resolved(seed: int = 5, L: float = 6.0, cutoff: float = 150.0, nlevels: int = 3,
+             tau: float = 1e-14, amin: float = 0.25, amax: float = 1.5,
+             shells=((0, 2), (1, 1), (2, 1), (3, 1)), natm: int = 2) -> System:
+    """Cubic cell whose pair exponents are all resolved by their level grid
+    (alpha_p h^2 < 0.1), so grid sums equal integrals to ~1e-15 and the closed
+    forms apply.  `shells` lists (l, nprim) per atom; contraction coefficients
+    are 1, 0.5, 0.25, ..."""
+    rng = np.random.default_rng(seed)
+    coords = rng.uniform(0.0, L, size=(natm, 3))
+    sa, sl, se, sc = [], [], [], []
+    for a in range(natm):
+        for l, npr in shells:
+            sa.append(a)
+            sl.append(l)
+            se.append(_log_uniform(rng, amin, amax, npr))
+    shell_atom, shell_l, nprim, off, ex, _ = _finish_shells(sa, sl, se)
+    co = np.concatenate([0.5 ** np.arange(len(e)) for e in se])
+    nao = sum(ncart(l) for l in sl)
+    C = rng.standard_normal((nao, 3))
+    D = C @ C.T
+    return System("resolved", np.eye(3) * L, coords, shell_atom, shell_l, nprim, off, ex, co,
+                  D, cutoff_ha=cutoff, nlevels=nlevels, level_ratio=3.0, meshes=None,
+                  rel_cutoff=40.0, tau=tau, nocc=3, potential=_plane_waves(rng, 6, 2))
+
+
+def single_gaussian(alpha: float, L: float, cutoff: float = 200.0, nlevels: int = 3,
+                    pos=(0.3, 0.1, 0.7)) -> System:
+    """One s primitive (unit coefficient) in a cubic box, D = [[1]]."""
+    coords = np.array([pos], dtype=float) * L
+    return System("gauss", np.eye(3) * L, coords, np.array([0], np.int32),
+                  np.array([0], np.int32), np.array([1], np.int32), np.array([0], np.int32),
+                  np.array([alpha]), np.array([1.0]), np.array([[1.0]]), cutoff_ha=cutoff,
+                  nlevels=nlevels, level_ratio=3.0, meshes=None, rel_cutoff=40.0, tau=1e-14)
+
+
+def tiny14() -> System:
+    """The tiny workload at tau = 1e-14."""
+    return workloads.tiny().with_tau(1e-14)

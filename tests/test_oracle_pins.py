@@ -1,0 +1,320 @@
+"""Pins of the CPU oracle against mathematics it does not itself contain.
+
+The paper prints no values of rho, V, energies or forces (only timings), so every
+pin here is a closed form, a brute-force evaluation, an identity or an invariance:
+
+* normalisation: unit self-overlap from Gaussian moments (Sec. II basis);
+* integral of rho over the cell = tr(D S), S the lattice-summed analytic overlap
+  (Eq. rho integrated; resolved exponents so the grid sum is exact);
+* eval_mat(constant) = c S and eval_mat(plane waves) = closed-form Gaussian x
+  plane-wave integrals (Eq. J);
+* each level density equals the untruncated double lattice sum of Eq. (rho),
+  built from periodised orbitals, on the pairs of that level;
+* adjoint identity <v, rho(D)> = tr(D V(v)) through the multigrid Fourier
+  interpolation and restriction;
+* Hartree energy of one Gaussian charge against the analytic G sum and the
+  Ewald-corrected isolated self-energy (Eqs. vH, vHG);
+* LDA exchange of a uniform density against Dirac's -(3/4 pi) k_F per electron;
+* gradient contraction (Algorithm 3) against central finite differences;
+* invariance under lattice translations and whole-grid shifts.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+import closed_forms as cf
+import systems
+
+
+@pytest.fixture(scope="module")
+def res():
+    s = systems.resolved()
+    return s, oracle.Plan(s)
+
+
+@pytest.fixture(scope="module")
+def overlap(res):
+    return cf.lattice_overlap(res[0], reach=20.0)
+
+
+def test_normalisation_unit_self_overlap():
+    for l in range(4):
+        for a in (0.1, 0.7, 3.0, 25.0):
+            assert oracle.prim_norm(l, a) == pytest.approx(cf.norm(l, a), rel=1e-14)
+
+
+def test_cartesian_order():
+    assert oracle.cart_components(2) == [(2, 0, 0), (1, 1, 0), (1, 0, 1), (0, 2, 0), (0, 1, 1), (0, 0, 2)]
+    assert len(oracle.cart_components(3)) == 10
+
+
+def test_meshes_from_cutoff():
+    # 32-water: 280 Ha, L = 18.64, ratio 3 -> 144/84/50/30 (smallest even 7-smooth)
+    m, E, G = oracle.level_grids(workloads.water_box(1, 18.64, 0))
+    assert m[:, 0].tolist() == [144, 84, 50, 30]
+    for k in range(4):
+        # the strict cutoff sphere never reaches the Nyquist planes
+        assert G[k] * 18.64 / (2 * math.pi) < (m[k, 0] - 1) / 2
+    m, E, G = oracle.level_grids(workloads.tiny())
+    assert E[0] == pytest.approx(0.5 * (2 * math.pi * 19 / 6) ** 2)
+
+
+def test_integrated_density_is_trace_DS(res, overlap):
+    s, p = res
+    S = overlap
+    rho = p.combine(p.rho_levels(s.D))
+    omega = float(np.prod(np.diag(s.lattice)))
+    tot = omega / rho.size * rho.sum()
+    ref = float(np.sum(s.D * S))
+    assert tot == pytest.approx(ref, rel=1e-11, abs=1e-12)
+    # each level separately integrates to its share (sum over levels)
+    parts = [omega / r.size * r.sum() for r in p.rho_levels(s.D)]
+    assert sum(parts) == pytest.approx(ref, rel=1e-11)
+
+
+def test_mat_of_constant_is_overlap(res, overlap):
+    s, p = res
+    S = overlap
+    c = 0.37
+    V = p.mat_levels([np.full(tuple(m), c) for m in p.meshes])
+    assert np.max(np.abs(V - c * S)) < 1e-11 * np.max(np.abs(S))
+    assert np.max(np.abs(V - V.T)) < 1e-14 * np.max(np.abs(V))
+
+
+def test_mat_of_plane_waves_closed_form(res):
+    s, p = res
+    pw = s.potential
+    vf = pw.sample(p.meshes[0])
+    vl = p.restrict(vf)
+    # band-limited inside every level sphere: restriction reproduces the waves
+    for k in range(p.nlev):
+        assert np.max(np.abs(vl[k] - pw.sample(p.meshes[k]))) < 1e-12
+    V = p.mat_levels(vl)
+    ref = cf.lattice_pw_matrix(s, pw, reach=20.0)
+    assert np.max(np.abs(V - ref)) < 1e-10 * max(1.0, np.max(np.abs(ref)))
+
+
+def _periodic_prims(sys, mesh, reach=30.0):
+    """Per (AO, primitive): periodised primitive values on `mesh`."""
+    L = np.diag(sys.lattice)
+    x = [np.arange(mesh[d]) * (L[d] / mesh[d]) for d in range(3)]
+    n = [int(math.ceil(reach / L[d])) + 1 for d in range(3)]
+    out = []
+    ao = 0
+    for sh in range(sys.nshell):
+        l = int(sys.shell_l[sh])
+        o = int(sys.shell_prim_off[sh])
+        for c in oracle.cart_components(l):
+            for k in range(int(sys.shell_nprim[sh])):
+                a = float(sys.exponents[o + k])
+                cn = float(sys.coeffs[o + k]) * cf.norm(l, a)
+                f = np.zeros(tuple(int(m) for m in mesh))
+                for i in range(-n[0], n[0] + 1):
+                    for j in range(-n[1], n[1] + 1):
+                        for kk in range(-n[2], n[2] + 1):
+                            A = sys.coords[int(sys.shell_atom[sh])] + np.array([i, j, kk]) * L
+                            u = [x[d] - A[d] for d in range(3)]
+                            g = [u[d] ** c[d] * np.exp(-a * u[d] ** 2) for d in range(3)]
+                            f += cn * g[0][:, None, None] * g[1][None, :, None] * g[2][None, None, :]
+                out.append((ao, a, f))
+            ao += 1
+    return out
+
+
+@pytest.mark.parametrize("name", ["tiny14", "resolved"])
+def test_levels_match_untruncated_double_lattice_sum(name):
+    s = systems.tiny14() if name == "tiny14" else systems.resolved()
+    p = oracle.Plan(s)
+    rl = p.rho_levels(s.D, mode="plain")
+    for k in range(p.nlev):
+        mesh = p.meshes[k]
+        prims = _periodic_prims(s, mesh)
+        ref = np.zeros(tuple(int(m) for m in mesh))
+        for (m, am, fm) in prims:
+            for (n, an, fn) in prims:
+                ap = am + an
+                lev = 0
+                for kk in range(p.nlev - 1, -1, -1):
+                    if p.E[kk] >= 40.0 * ap:
+                        lev = kk
+                        break
+                if lev == k:
+                    ref += s.D[m, n] * fm * fn
+        scale = max(1.0, np.max(np.abs(ref)))
+        assert np.max(np.abs(rl[k] - ref)) < 1e-11 * scale, (name, k)
+
+
+def test_plain_equals_separable():
+    s = systems.tiny14()
+    p = oracle.Plan(s)
+    a = p.rho_levels(s.D, mode="plain")
+    b = p.rho_levels(s.D, mode="separable")
+    for x, y in zip(a, b):
+        assert np.max(np.abs(x - y)) <= 1e-12 * max(1.0, np.max(np.abs(x)))
+
+
+def test_screening_error_is_tau_sized():
+    s = workloads.tiny()        # tau = 1e-6
+    p6 = oracle.Plan(s)
+    p14 = oracle.Plan(s.with_tau(1e-14))
+    assert p14.npairs > p6.npairs
+    a = p6.rho_levels(s.D)
+    b = p14.rho_levels(s.D)
+    nd = float(np.max(np.abs(s.D)))
+    for x, y in zip(a, b):
+        # every dropped or clipped piece is below tau per unit D element
+        assert np.max(np.abs(x - y)) < 200 * 1e-6 * nd
+
+
+def test_adjoint_identity(res):
+    s, p = res
+    rng = np.random.default_rng(7)
+    D = rng.standard_normal((s.nao, s.nao))
+    D = D + D.T
+    v = rng.standard_normal(tuple(p.meshes[0]))
+    rho = p.combine(p.rho_levels(D))
+    omega = float(np.prod(np.diag(s.lattice)))
+    lhs = omega / rho.size * float(np.sum(v * rho))
+    V = p.mat_levels(p.restrict(v))
+    rhs = float(np.sum(D * V))
+    assert lhs == pytest.approx(rhs, rel=1e-12, abs=1e-12)
+
+
+@pytest.mark.parametrize("alpha,L", [(0.8, 10.0), (2.5, 8.0)])
+def test_hartree_of_gaussian_charge(alpha, L):
+    s = systems.single_gaussian(alpha, L)
+    p = oracle.Plan(s)
+    rho = p.combine(p.rho_levels(s.D))
+    _, EH = p.poisson(rho)
+    k = int(p.lev[0])
+    ref = cf.gaussian_charge_hartree(2 * alpha, L, gcut=p.G[k])
+    assert EH == pytest.approx(ref, rel=1e-11)
+
+
+def test_hartree_isolated_limit_with_ewald():
+    # unit Gaussian charge exponent a' = 2 alpha in a large cube:
+    # E_per = E_self + E_Madelung(L) + pi/(a' Omega) up to erfc tails
+    alpha, L = 1.2, 16.0
+    s = systems.single_gaussian(alpha, L, cutoff=160.0)
+    p = oracle.Plan(s)
+    _, EH = p.poisson(p.combine(p.rho_levels(s.D)))
+    ap = 2 * alpha
+    e_self = math.sqrt(ap / (2 * math.pi))
+    ref = e_self + cf.madelung_cubic_background(L) + math.pi / (ap * L ** 3)
+    assert EH == pytest.approx(ref, rel=1e-10)
+
+
+def test_lda_uniform_gas():
+    s = systems.resolved()
+    p = oracle.Plan(s)
+    c = 0.0123
+    rho = np.full(tuple(p.meshes[0]), c)
+    vx, Ex = p.lda_x(rho)
+    omega = float(np.prod(np.diag(s.lattice)))
+    kF = (3 * math.pi ** 2 * c) ** (1.0 / 3.0)
+    assert Ex == pytest.approx(-(3.0 / (4 * math.pi)) * kF * c * omega, rel=1e-13)
+    # v_x is the functional derivative: dE_x / d rho(r) = (Omega/N) v_x(r)
+    h = 1e-7
+    ep = p.lda_x(rho + h)[1]
+    em = p.lda_x(rho - h)[1]
+    assert (ep - em) / (2 * h) == pytest.approx(omega / rho.size * float(np.sum(vx)), rel=1e-7)
+    # negative density is clipped (continuous at 0)
+    vx0, E0 = p.lda_x(np.full(tuple(p.meshes[0]), -1.0))
+    assert E0 == 0.0 and np.all(vx0 == 0.0)
+
+
+def test_gradient_matches_finite_differences_of_bilinear_form(res):
+    s, p = res
+    v = [s.potential.sample(m) for m in p.meshes]
+    g = p.grad_levels(s.D, v)
+    omega = float(np.prod(np.diag(s.lattice)))
+
+    def form(coords):
+        q = p.with_coords(coords)
+        rl = q.rho_levels(s.D)
+        return sum(omega / r.size * float(np.sum(r * vv)) for r, vv in zip(rl, v))
+
+    h = 1e-4
+    for atom, d in [(0, 0), (0, 2), (1, 1)]:
+        cp = s.coords.copy()
+        cm = s.coords.copy()
+        cp[atom, d] += h
+        cm[atom, d] -= h
+        fd = (form(cp) - form(cm)) / (2 * h)
+        assert g[atom, d] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+def test_energy_gradient_matches_finite_differences(res):
+    s, p = res
+    out = p.fock(s.D)
+    g = p.grad_levels(s.D, out["v_levels"])
+    h = 1e-4
+    for atom, d in [(0, 1), (1, 0), (1, 2)]:
+        cp = s.coords.copy()
+        cm = s.coords.copy()
+        cp[atom, d] += h
+        cm[atom, d] -= h
+        fd = (p.with_coords(cp).energy(s.D) - p.with_coords(cm).energy(s.D)) / (2 * h)
+        assert g[atom, d] == pytest.approx(fd, rel=1e-6, abs=1e-7)
+
+
+def test_energy_derivative_wrt_density_matrix_is_V(res):
+    # dE/dD_mu,nu = V_mu,nu (symmetric perturbation)
+    s, p = res
+    out = p.fock(s.D)
+    rng = np.random.default_rng(3)
+    X = rng.standard_normal(s.D.shape)
+    X = X + X.T
+    h = 1e-5
+    fd = (p.energy(s.D + h * X) - p.energy(s.D - h * X)) / (2 * h)
+    assert fd == pytest.approx(float(np.sum(X * out["V"])), rel=1e-7)
+
+
+def test_lattice_translation_invariance():
+    s = systems.tiny14()
+    p = oracle.Plan(s)
+    c2 = s.coords.copy()
+    c2[1] += np.array([6.0, -6.0, 12.0])
+    q = oracle.Plan(s.with_coords(c2))
+    assert q.npairs == p.npairs
+    for x, y in zip(p.rho_levels(s.D), q.rho_levels(s.D)):
+        assert np.max(np.abs(x - y)) < 1e-11 * max(1.0, np.max(np.abs(x)))
+
+
+def test_whole_grid_shift():
+    s = systems.tiny14()
+    p = oracle.Plan(s)
+    # 4 finest-grid spacings = 2 on the 20^3 level = 1 on the 10^3 level
+    shift = 4 * 6.0 / 40
+    q = oracle.Plan(s.with_coords(s.coords + np.array([shift, 0, 0])))
+    a = p.rho_levels(s.D)
+    b = q.rho_levels(s.D)
+    for k, (x, y) in enumerate(zip(a, b)):
+        n = 4 * int(p.meshes[k][0]) // 40
+        assert np.max(np.abs(np.roll(x, n, axis=0) - y)) < 1e-11 * max(1.0, np.max(np.abs(x)))
+
+
+def test_rho_points_match_full_grid():
+    s = workloads.tiny()
+    p = oracle.Plan(s)
+    rl = p.rho_levels(s.D)
+    rng = np.random.default_rng(1)
+    for k in range(2):
+        pts = rng.integers(0, p.meshes[k][0], size=(20, 3))
+        got = p.rho_points(s.D, k, pts)
+        ref = rl[k][pts[:, 0], pts[:, 1], pts[:, 2]]
+        assert np.max(np.abs(got - ref)) < 1e-12 * max(1.0, np.max(np.abs(rl[k])))
+
+
+def test_mat_block_matches_full(res):
+    s, p = res
+    vl = [s.potential.sample(m) for m in p.meshes]
+    V = p.mat_levels(vl)
+    off = s.ao_offsets()
+    for sa, sb in [(0, 3), (2, 2), (4, 1)]:
+        blk = p.mat_block(vl, sa, sb)
+        ref = V[off[sa]:off[sa + 1], off[sb]:off[sb + 1]]
+        assert np.max(np.abs(blk - ref)) < 1e-13 * max(1.0, np.max(np.abs(V)))
