@@ -1,0 +1,189 @@
+/*
+ * gpw.h — C ABI of libgpw: multigrid Gaussian-plane-wave (FFTDF) collocation,
+ * integration and nuclear-gradient contraction on one GB300 (sm_103a), FP64.
+ *
+ * The operations follow arXiv 2603.24881 ("Implementation of the multigrid
+ * Gaussian-Plane-Wave algorithm with GPU acceleration in PySCF"):
+ *   - eval_rho:     density of Eq. (rho), evaluated as Eq. (rho_wrap) (one orbital
+ *                   in the home cell, the other over lattice images, folded back),
+ *                   pair by pair on the coarsest multigrid level that resolves the
+ *                   pair exponent (Sec. II, multigrid), then combined on the finest
+ *                   grid by Fourier interpolation;
+ *   - eval_mat:     the two-electron Fock matrix of Eq. (J) / (J_wrap) for a given
+ *                   real-space potential, integrated on the same levels;
+ *   - eval_mat_ip1: the Hxc part of the nuclear gradient (Algorithm 3);
+ *   - fock:         rho -> Poisson (Eqs. vH, vHG) + LDA exchange -> V.
+ *
+ * Conventions
+ *   Units: Bohr and Hartree.  Only orthorhombic cells (diagonal lattice).
+ *   Shells are Cartesian with angular momentum 0..3; within a shell the AO order is
+ *   lexicographic with x^l first (d: xx, xy, xz, yy, yz, zz).  AOs follow the shell
+ *   order of the descriptor.
+ *   Grids are C order [N0][N1][N2] along a1, a2, a3; point (i0,i1,i2) sits at
+ *   (i0 L0/N0, i1 L1/N1, i2 L2/N2).  Level 0 is the finest grid.
+ *   Matrices are row-major nao x nao doubles.
+ *
+ * Ownership and memory
+ *   The caller owns every D, rho, v, V and gradient buffer: device memory, FP64,
+ *   contiguous, unless a parameter says "host".  The plan owns its pair tables,
+ *   level grids, spectra, cuFFT plans and scratch, all allocated by gpw_plan; the
+ *   evaluation calls allocate nothing.
+ *
+ * Streams
+ *   Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy default)
+ *   except where noted.  One plan may be used by one stream at a time; different
+ *   plans are independent.
+ *
+ * Errors
+ *   Every int-returning call returns GPW_OK (0) or a negative GPW_E* code and never
+ *   throws across the ABI.  gpw_last_error() gives a message for the calling thread.
+ */
+#ifndef GPW_H_
+#define GPW_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GPW_OK 0
+#define GPW_EINVAL -1     /* bad argument: l > 3, non-orthogonal lattice, bad mesh, NULL */
+#define GPW_ENOMEM -2     /* device or host allocation failed */
+#define GPW_ECUDA -3      /* CUDA runtime error */
+#define GPW_ECUFFT -4     /* cuFFT error */
+#define GPW_ETIMEDOUT -5  /* a bounded wait gave up */
+#define GPW_EDEVICE -6    /* a kernel's bounds check set the device error word */
+#define GPW_ERANGE -7     /* a size is beyond a fixed limit of the library */
+
+#define GPW_MAX_LEVELS 8
+
+/* Flags for gpw_desc.flags */
+#define GPW_STRICT 0            /* default: the truncation definition of the paper */
+
+typedef struct gpw_plan_s* gpw_plan_t;
+
+/* Problem statement (Sec. II and III A of the paper): cell, atoms, Gaussian shells,
+ * plane-wave cutoff and multigrid levels, screening threshold tau of Eq. (cut).
+ * All pointers are host memory, read during gpw_plan only. */
+typedef struct {
+  double lattice[9];          /* rows a1, a2, a3 (Bohr); must be diagonal */
+  int natm;
+  const double* coords;       /* natm x 3 atom positions (Bohr) */
+  int nshell;
+  const int* shell_atom;      /* nshell: atom of each shell */
+  const int* shell_l;         /* nshell: angular momentum 0..3 */
+  const int* shell_nprim;     /* nshell: primitives in the shell */
+  const int* shell_prim_off;  /* nshell: first primitive in exponents/coeffs */
+  const double* exponents;    /* primitive exponents alpha (Bohr^-2) */
+  const double* coeffs;       /* contraction coefficients (unnormalised; each primitive
+                                 is multiplied by N_l(alpha), unit x^l self-overlap) */
+  double cutoff_ha;           /* finest-level cutoff E_0 (Hartree); ignored if meshes */
+  int nlevels;                /* 1..GPW_MAX_LEVELS */
+  double level_ratio;         /* E_k = E_0 / ratio^k */
+  const int* meshes;          /* optional nlevels x 3 explicit meshes; NULL = derive */
+  double rel_cutoff;          /* a pair of exponent alpha_p goes to the coarsest level
+                                 with E_k >= rel_cutoff * alpha_p (40 if <= 0) */
+  double tau;                 /* screening threshold of Eq. (cut) */
+  int flags;                  /* GPW_STRICT */
+} gpw_desc;
+
+/* Sizes and work counts of a plan (gpw_plan_query). */
+typedef struct {
+  int nao, natm, nlevels, lmax;
+  int meshes[GPW_MAX_LEVELS][3];
+  double level_cutoff[GPW_MAX_LEVELS];  /* E_k (Hartree) */
+  long long npairs;
+  long long npairs_level[GPW_MAX_LEVELS];
+  long long pair_points;                 /* sum over pairs of box volumes */
+  long long pair_points_level[GPW_MAX_LEVELS];
+  long long pair_points_L[8];            /* by la + lb */
+  long long nentries;                    /* (pair, sub-box) tasks */
+  long long device_bytes;                /* device memory owned by the plan */
+  double flops_rho;    /* model FP64 flops of one eval_rho grid pass: 2 (L+1) per pair-point */
+  double flops_mat;    /* same for eval_mat */
+  double flops_ip1;    /* 2 (L+2) per pair-point for eval_mat_ip1 */
+  int tile[3];         /* sub-box edge owned by one thread block */
+} gpw_plan_info;
+
+/* Build a plan: normalise primitives, screen pairs (Eq. cut; pairs a <= b over images T
+ * with |A - B - T| < r_a + r_b, Sec. III A), assign levels, build the per-level
+ * sub-box task lists, allocate grids/spectra/cuFFT plans, and precompute the 1-D
+ * Gaussian factor tables of Eq. (gab_lp) on the device (enqueued on `stream`).
+ * Returns GPW_EINVAL for a non-diagonal lattice, l > 3, nlevels outside
+ * 1..GPW_MAX_LEVELS, non-positive exponents, or meshes too small for the
+ * cutoff sphere.  *out is set only on success. */
+int gpw_plan(const gpw_desc* desc, void* stream, gpw_plan_t* out);
+
+/* Fill *info (host). */
+int gpw_plan_query(gpw_plan_t plan, gpw_plan_info* info);
+
+/* Move the atoms to `coords` (host, natm x 3) keeping the pair set, images, levels
+ * and integer boxes of the plan frozen (the energy is then smooth in the coordinates,
+ * which is what finite differences of the gradient need).  Recomputes the tables. */
+int gpw_plan_update_coords(gpw_plan_t plan, const double* coords, void* stream);
+
+/* Copy the screened pair table to host arrays of plan.npairs rows (any may be NULL):
+ * ab (2 ints: primitive indices a <= b), img (3 ints: T = img . diag(L)), level,
+ * lo/hi (3 ints each: integer box on the level mesh, inclusive).  Synchronous. */
+int gpw_plan_pairs(gpw_plan_t plan, int* ab, int* img, int* level, int* lo, int* hi);
+
+/* Density on the finest grid (Eq. rho_wrap + multigrid Fourier interpolation).
+ * D: device, nao x nao symmetric.  rho_fine: device, N0*N1*N2 of level 0 (overwritten). */
+int gpw_eval_rho(gpw_plan_t plan, const double* D, double* rho_fine, void* stream);
+
+/* Raw per-level densities before interpolation: rho_levels[k] (device, N_k doubles,
+ * overwritten) for k < nlevels (an entry may be NULL to skip copying that level). */
+int gpw_eval_rho_levels(gpw_plan_t plan, const double* D, double* const* rho_levels,
+                        void* stream);
+
+/* V_mu,nu = sum_k sum_pairs (Omega/N_k) sum_r v_k(r) phi_mu phi_nu (Eq. J_wrap), where
+ * v_k is v_fine restricted to level k (keep |G| < G_k).  v_fine: device, finest grid.
+ * V: device nao x nao, overwritten (symmetric). */
+int gpw_eval_mat(gpw_plan_t plan, const double* v_fine, double* V, void* stream);
+
+/* As gpw_eval_mat with the level potentials given directly (device pointers,
+ * N_k doubles each); no restriction is applied. */
+int gpw_eval_mat_levels(gpw_plan_t plan, const double* const* v_levels, double* V,
+                        void* stream);
+
+/* Hxc nuclear gradient dE/dR = <v_Hxc, d rho / dR> (Algorithm 3) for the density
+ * matrix D (device) and the finest-grid potential v_fine (device), with the boxes of
+ * the plan held fixed.  grad: device natm x 3, overwritten. */
+int gpw_eval_mat_ip1(gpw_plan_t plan, const double* D, const double* v_fine, double* grad,
+                     void* stream);
+
+/* As gpw_eval_mat_ip1 with per-level potentials (device, N_k doubles each). */
+int gpw_eval_mat_ip1_levels(gpw_plan_t plan, const double* D, const double* const* v_levels,
+                            double* grad, void* stream);
+
+/* One Fock build: rho = eval_rho(D); v_H from Eqs. (vH)/(vHG) with G = 0 dropped;
+ * Slater exchange v_x = -(3/pi)^(1/3) max(rho,0)^(1/3); v = v_H + v_x restricted to
+ * every level; V = eval_mat.  energies (host, 2 doubles): E_H = (1/2)<rho, v_H> and
+ * E_x = (Omega/N) sum e_x; the call synchronises `stream` to return them.
+ * rho_out and v_fine_out (device, finest grid) are optional (NULL). */
+int gpw_fock(gpw_plan_t plan, const double* D, double* V, double* energies,
+             double* rho_out, double* v_fine_out, void* stream);
+
+/* As gpw_fock without the final synchronisation: the two energies are written to
+ * `energies_dev` (device, 2 doubles) on `stream`.  Usable inside CUDA-graph capture. */
+int gpw_fock_async(gpw_plan_t plan, const double* D, double* V, double* energies_dev,
+                   double* rho_out, double* v_fine_out, void* stream);
+
+/* Read and clear the device error word of the plan (synchronises `stream`).
+ * Returns GPW_OK, or GPW_EDEVICE with *code set to the first recorded check. */
+int gpw_check_device(gpw_plan_t plan, int* code, void* stream);
+
+/* Release the plan and everything it owns.  NULL is ignored. */
+void gpw_plan_destroy(gpw_plan_t plan);
+
+/* Static message for an error code. */
+const char* gpw_strerror(int code);
+
+/* Message of the last failing call on this thread ("" if none). */
+const char* gpw_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPW_H_ */

@@ -1,0 +1,317 @@
+"""Thin ctypes binding of libgpw (include/gpw.h): argument marshalling only.
+
+Every step of the computation runs in libgpw's CUDA kernels and cuFFT on the device.
+Tensors are torch tensors on the current CUDA device (float64, contiguous); the
+calls are enqueued on torch's current stream.  There is no CPU fallback: loading
+fails loudly when the library is missing or cannot be built.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+GPW_MAX_LEVELS = 8
+_LOCK = threading.Lock()
+_LIB = None
+
+ERRORS = {0: "GPW_OK", -1: "GPW_EINVAL", -2: "GPW_ENOMEM", -3: "GPW_ECUDA", -4: "GPW_ECUFFT",
+          -5: "GPW_ETIMEDOUT", -6: "GPW_EDEVICE", -7: "GPW_ERANGE"}
+
+EXPORTS = ["gpw_plan", "gpw_plan_query", "gpw_plan_update_coords", "gpw_plan_pairs",
+           "gpw_eval_rho", "gpw_eval_rho_levels", "gpw_eval_mat", "gpw_eval_mat_levels",
+           "gpw_eval_mat_ip1", "gpw_eval_mat_ip1_levels", "gpw_fock", "gpw_fock_async",
+           "gpw_check_device", "gpw_plan_destroy", "gpw_strerror", "gpw_last_error"]
+
+
+class GpwError(RuntimeError):
+    def __init__(self, code, where, msg):
+        super().__init__(f"{where}: {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Desc(ctypes.Structure):
+    _fields_ = [("lattice", ctypes.c_double * 9), ("natm", ctypes.c_int),
+                ("coords", ctypes.c_void_p), ("nshell", ctypes.c_int),
+                ("shell_atom", ctypes.c_void_p), ("shell_l", ctypes.c_void_p),
+                ("shell_nprim", ctypes.c_void_p), ("shell_prim_off", ctypes.c_void_p),
+                ("exponents", ctypes.c_void_p), ("coeffs", ctypes.c_void_p),
+                ("cutoff_ha", ctypes.c_double), ("nlevels", ctypes.c_int),
+                ("level_ratio", ctypes.c_double), ("meshes", ctypes.c_void_p),
+                ("rel_cutoff", ctypes.c_double), ("tau", ctypes.c_double),
+                ("flags", ctypes.c_int)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nao", ctypes.c_int), ("natm", ctypes.c_int), ("nlevels", ctypes.c_int),
+                ("lmax", ctypes.c_int), ("meshes", (ctypes.c_int * 3) * GPW_MAX_LEVELS),
+                ("level_cutoff", ctypes.c_double * GPW_MAX_LEVELS),
+                ("npairs", ctypes.c_longlong),
+                ("npairs_level", ctypes.c_longlong * GPW_MAX_LEVELS),
+                ("pair_points", ctypes.c_longlong),
+                ("pair_points_level", ctypes.c_longlong * GPW_MAX_LEVELS),
+                ("pair_points_L", ctypes.c_longlong * 8), ("nentries", ctypes.c_longlong),
+                ("device_bytes", ctypes.c_longlong), ("flops_rho", ctypes.c_double),
+                ("flops_mat", ctypes.c_double), ("flops_ip1", ctypes.c_double),
+                ("tile", ctypes.c_int * 3)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load libgpw.so (building it in-tree with nvcc if absent).  Raises if it cannot."""
+    global _LIB
+    with _LOCK:
+        if _LIB is not None:
+            return _LIB
+        path = _build.LIB
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"libgpw not built: {path}")
+            _build.build()
+        L = ctypes.CDLL(path)
+        vp, ci, cd = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.gpw_plan.argtypes = [ctypes.POINTER(Desc), vp, ctypes.POINTER(vp)]
+        L.gpw_plan_query.argtypes = [vp, ctypes.POINTER(Info)]
+        L.gpw_plan_update_coords.argtypes = [vp, vp, vp]
+        L.gpw_plan_pairs.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.gpw_eval_rho.argtypes = [vp, vp, vp, vp]
+        L.gpw_eval_rho_levels.argtypes = [vp, vp, vp, vp]
+        L.gpw_eval_mat.argtypes = [vp, vp, vp, vp]
+        L.gpw_eval_mat_levels.argtypes = [vp, vp, vp, vp]
+        L.gpw_eval_mat_ip1.argtypes = [vp, vp, vp, vp, vp]
+        L.gpw_eval_mat_ip1_levels.argtypes = [vp, vp, vp, vp, vp]
+        L.gpw_fock.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.gpw_fock_async.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.gpw_check_device.argtypes = [vp, ctypes.POINTER(ci), vp]
+        L.gpw_plan_destroy.argtypes = [vp]
+        L.gpw_plan_destroy.restype = None
+        L.gpw_strerror.argtypes = [ci]
+        L.gpw_strerror.restype = ctypes.c_char_p
+        L.gpw_last_error.argtypes = []
+        L.gpw_last_error.restype = ctypes.c_char_p
+        for name in EXPORTS:
+            if name not in ("gpw_plan_destroy", "gpw_strerror", "gpw_last_error"):
+                getattr(L, name).restype = ci
+        _LIB = L
+        return L
+
+
+def check(rc: int, where: str):
+    if rc != 0:
+        msg = load().gpw_last_error().decode(errors="replace")
+        raise GpwError(rc, where, msg)
+
+
+def _ptr(t) -> int:
+    return int(t.data_ptr()) if t is not None else 0
+
+
+def _stream(stream=None) -> int:
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+def _dev_f64(x, shape=None):
+    import torch
+    if not isinstance(x, torch.Tensor):
+        x = torch.as_tensor(np.asarray(x, dtype=np.float64))
+    if x.device.type != "cuda" or x.dtype != torch.float64 or not x.is_contiguous():
+        x = x.to(device="cuda", dtype=torch.float64).contiguous()
+    if shape is not None and tuple(x.shape) != tuple(shape):
+        x = x.reshape(shape)
+    return x
+
+
+class Plan:
+    """A libgpw plan for one cell (Sec. II / III A of the paper): screened pairs,
+    levels, task lists, grids and FFT plans live on the current CUDA device."""
+
+    def __init__(self, system, stream=None):
+        import torch
+        self._lib = load()
+        s = system
+        self.system = s
+        self._keep = []
+
+        def arr(a, dt):
+            a = np.ascontiguousarray(np.asarray(a, dtype=dt))
+            self._keep.append(a)
+            return a.ctypes.data_as(ctypes.c_void_p)
+
+        d = Desc()
+        lat = np.asarray(s.lattice, dtype=np.float64).ravel()
+        for i in range(9):
+            d.lattice[i] = float(lat[i])
+        d.natm = int(s.coords.shape[0])
+        d.coords = arr(s.coords, np.float64)
+        d.nshell = int(len(s.shell_l))
+        d.shell_atom = arr(s.shell_atom, np.int32)
+        d.shell_l = arr(s.shell_l, np.int32)
+        d.shell_nprim = arr(s.shell_nprim, np.int32)
+        d.shell_prim_off = arr(s.shell_prim_off, np.int32)
+        d.exponents = arr(s.exponents, np.float64)
+        d.coeffs = arr(s.coeffs, np.float64)
+        d.cutoff_ha = float(s.cutoff_ha)
+        d.nlevels = int(s.nlevels)
+        d.level_ratio = float(s.level_ratio)
+        d.meshes = arr(s.meshes, np.int32) if s.meshes is not None else None
+        d.rel_cutoff = float(s.rel_cutoff)
+        d.tau = float(s.tau)
+        d.flags = 0
+        torch.cuda.init()
+        h = ctypes.c_void_p()
+        check(self._lib.gpw_plan(ctypes.byref(d), ctypes.c_void_p(_stream(stream)),
+                                 ctypes.byref(h)), "gpw_plan")
+        self._h = h
+        self._keep = []
+        info = Info()
+        check(self._lib.gpw_plan_query(h, ctypes.byref(info)), "gpw_plan_query")
+        self.info = info
+        self.nao = info.nao
+        self.natm = info.natm
+        self.nlevels = info.nlevels
+        self.meshes = [tuple(info.meshes[k][i] for i in range(3)) for k in range(info.nlevels)]
+        self.fine_mesh = self.meshes[0]
+
+    # -- housekeeping -------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.gpw_plan_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def stats(self) -> dict:
+        i = self.info
+        return dict(nao=i.nao, natm=i.natm, nlevels=i.nlevels, lmax=i.lmax,
+                    meshes=self.meshes, npairs=i.npairs,
+                    npairs_level=[i.npairs_level[k] for k in range(i.nlevels)],
+                    pair_points=i.pair_points,
+                    pair_points_level=[i.pair_points_level[k] for k in range(i.nlevels)],
+                    pair_points_L=[i.pair_points_L[l] for l in range(8)],
+                    nentries=i.nentries, device_bytes=i.device_bytes,
+                    flops_rho=i.flops_rho, flops_mat=i.flops_mat, flops_ip1=i.flops_ip1,
+                    level_cutoff=[i.level_cutoff[k] for k in range(i.nlevels)],
+                    tile=tuple(i.tile))
+
+    def pair_table(self) -> np.ndarray:
+        """Screened pairs as int64 rows (a, b, n0, n1, n2, level, lo0..2, hi0..2),
+        sorted lexicographically."""
+        n = int(self.info.npairs)
+        ab = np.zeros((n, 2), np.int32)
+        img = np.zeros((n, 3), np.int32)
+        lev = np.zeros(n, np.int32)
+        lo = np.zeros((n, 3), np.int32)
+        hi = np.zeros((n, 3), np.int32)
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        check(self._lib.gpw_plan_pairs(self._h, P(ab), P(img), P(lev), P(lo), P(hi)), "gpw_plan_pairs")
+        t = np.concatenate([ab, img, lev[:, None], lo, hi], axis=1).astype(np.int64)
+        return t[np.lexsort(t[:, ::-1].T)]
+
+    def update_coords(self, coords, stream=None):
+        c = np.ascontiguousarray(np.asarray(coords, dtype=np.float64))
+        check(self._lib.gpw_plan_update_coords(self._h, c.ctypes.data_as(ctypes.c_void_p),
+                                               ctypes.c_void_p(_stream(stream))),
+              "gpw_plan_update_coords")
+
+    def check_device(self, stream=None) -> int:
+        code = ctypes.c_int(0)
+        rc = self._lib.gpw_check_device(self._h, ctypes.byref(code), ctypes.c_void_p(_stream(stream)))
+        if rc not in (0, -6):
+            check(rc, "gpw_check_device")
+        return int(code.value)
+
+    # -- evaluations (device tensors) ----------------------------------------
+    def _levels_out(self, dtype=None):
+        import torch
+        return [torch.empty(m, dtype=torch.float64, device="cuda") for m in self.meshes]
+
+    def eval_rho(self, D, out=None, stream=None):
+        import torch
+        D = _dev_f64(D, (self.nao, self.nao))
+        if out is None:
+            out = torch.empty(self.fine_mesh, dtype=torch.float64, device="cuda")
+        check(self._lib.gpw_eval_rho(self._h, _ptr(D), _ptr(out), _stream(stream)), "gpw_eval_rho")
+        return out
+
+    def eval_rho_levels(self, D, stream=None):
+        D = _dev_f64(D, (self.nao, self.nao))
+        outs = self._levels_out()
+        ptrs = (ctypes.c_void_p * len(outs))(*[_ptr(o) for o in outs])
+        check(self._lib.gpw_eval_rho_levels(self._h, _ptr(D), ptrs, _stream(stream)),
+              "gpw_eval_rho_levels")
+        return outs
+
+    def eval_mat(self, v_fine, out=None, stream=None):
+        import torch
+        v = _dev_f64(v_fine, self.fine_mesh)
+        if out is None:
+            out = torch.empty((self.nao, self.nao), dtype=torch.float64, device="cuda")
+        check(self._lib.gpw_eval_mat(self._h, _ptr(v), _ptr(out), _stream(stream)), "gpw_eval_mat")
+        return out
+
+    def eval_mat_levels(self, v_levels, out=None, stream=None):
+        import torch
+        vs = [_dev_f64(v, m) for v, m in zip(v_levels, self.meshes)]
+        if out is None:
+            out = torch.empty((self.nao, self.nao), dtype=torch.float64, device="cuda")
+        ptrs = (ctypes.c_void_p * len(vs))(*[_ptr(v) for v in vs])
+        check(self._lib.gpw_eval_mat_levels(self._h, ptrs, _ptr(out), _stream(stream)),
+              "gpw_eval_mat_levels")
+        return out
+
+    def eval_mat_ip1(self, D, v_fine, out=None, stream=None):
+        import torch
+        D = _dev_f64(D, (self.nao, self.nao))
+        v = _dev_f64(v_fine, self.fine_mesh)
+        if out is None:
+            out = torch.empty((self.natm, 3), dtype=torch.float64, device="cuda")
+        check(self._lib.gpw_eval_mat_ip1(self._h, _ptr(D), _ptr(v), _ptr(out), _stream(stream)),
+              "gpw_eval_mat_ip1")
+        return out
+
+    def eval_mat_ip1_levels(self, D, v_levels, out=None, stream=None):
+        import torch
+        D = _dev_f64(D, (self.nao, self.nao))
+        vs = [_dev_f64(v, m) for v, m in zip(v_levels, self.meshes)]
+        if out is None:
+            out = torch.empty((self.natm, 3), dtype=torch.float64, device="cuda")
+        ptrs = (ctypes.c_void_p * len(vs))(*[_ptr(v) for v in vs])
+        check(self._lib.gpw_eval_mat_ip1_levels(self._h, _ptr(D), ptrs, _ptr(out), _stream(stream)),
+              "gpw_eval_mat_ip1_levels")
+        return out
+
+    def fock(self, D, want_rho=False, want_v=False, stream=None):
+        """One Fock build.  Returns dict(V, EH, Ex[, rho, v]) (energies as floats)."""
+        import torch
+        D = _dev_f64(D, (self.nao, self.nao))
+        V = torch.empty((self.nao, self.nao), dtype=torch.float64, device="cuda")
+        rho = torch.empty(self.fine_mesh, dtype=torch.float64, device="cuda") if want_rho else None
+        v = torch.empty(self.fine_mesh, dtype=torch.float64, device="cuda") if want_v else None
+        e = (ctypes.c_double * 2)()
+        check(self._lib.gpw_fock(self._h, _ptr(D), _ptr(V), e, _ptr(rho), _ptr(v), _stream(stream)),
+              "gpw_fock")
+        out = dict(V=V, EH=float(e[0]), Ex=float(e[1]))
+        if want_rho:
+            out["rho"] = rho
+        if want_v:
+            out["v"] = v
+        return out
+
+    def fock_async(self, D, V, energies, rho=None, v=None, stream=None):
+        """Enqueue a Fock build writing V and energies (device, 2 doubles) only."""
+        check(self._lib.gpw_fock_async(self._h, _ptr(D), _ptr(V), _ptr(energies), _ptr(rho),
+                                       _ptr(v), _stream(stream)), "gpw_fock_async")

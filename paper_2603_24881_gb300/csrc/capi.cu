@@ -1,0 +1,488 @@
+// C ABI of libgpw (declared in include/gpw.h): plan construction and upload, and the
+// orchestration of one evaluation on a stream — collocation kernels, cuFFT for the
+// level <-> finest-grid Fourier interpolation and the Poisson solve, exchange, and the
+// integration / gradient kernels with their fixed-order reductions.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <algorithm>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "gpw.h"
+#include "gpw_internal.h"
+#include "kernels.h"
+#include "plan_host.h"
+
+struct gpw_plan_s {
+  gpw::Plan p;
+};
+
+namespace gpw {
+
+static thread_local std::string g_err;
+void set_error(const std::string& msg) { g_err = msg; }
+
+namespace {
+
+#define GPW_CK(x)                                                                   \
+  do {                                                                              \
+    cudaError_t e_ = (x);                                                           \
+    if (e_ != cudaSuccess) {                                                        \
+      set_error(std::string(#x) + ": " + cudaGetErrorString(e_));                   \
+      return e_ == cudaErrorMemoryAllocation ? GPW_ENOMEM : GPW_ECUDA;              \
+    }                                                                               \
+  } while (0)
+
+#define GPW_CF(x)                                                                   \
+  do {                                                                              \
+    cufftResult r_ = (x);                                                           \
+    if (r_ != CUFFT_SUCCESS) {                                                      \
+      set_error(std::string(#x) + ": cufft error " + std::to_string((int)r_));      \
+      return r_ == CUFFT_ALLOC_FAILED ? GPW_ENOMEM : GPW_ECUFFT;                    \
+    }                                                                               \
+  } while (0)
+
+template <class T>
+int dalloc(T** ptr, long long count, long long* bytes) {
+  size_t b = sizeof(T) * (size_t)std::max<long long>(count, 1);
+  GPW_CK(cudaMalloc((void**)ptr, b));
+  *bytes += (long long)b;
+  return GPW_OK;
+}
+
+template <class T>
+int upload(T** ptr, const std::vector<T>& v, long long* bytes) {
+  int rc = dalloc(ptr, (long long)v.size(), bytes);
+  if (rc) return rc;
+  if (!v.empty()) GPW_CK(cudaMemcpy(*ptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  return GPW_OK;
+}
+
+void free_plan(Plan* P) {
+  DeviceArrays& d = P->d;
+  void* ptrs[] = {d.hot_a, d.hot_b, d.ids, d.ids2, d.geo, d.cab, d.pref, d.tab_off,
+                  d.coef_off, d.part_off, d.ent, d.sub_off, d.work, d.groups, d.atom_off,
+                  d.atom_list, d.tab, d.coef, d.part, d.pgrad, d.grids, d.spec, d.fspec,
+                  d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs};
+  for (void* q : ptrs)
+    if (q) cudaFree(q);
+  for (int k = 0; k < GPW_MAX_LEVELS; ++k)
+    if (P->fft_made[k]) {
+      cufftDestroy(P->fft_d2z[k]);
+      cufftDestroy(P->fft_z2d[k]);
+    }
+  d = DeviceArrays();
+}
+
+int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
+  long long b = 0;
+  DeviceArrays& d = P->d;
+  int rc;
+#define GPW_TRY(x) \
+  if ((rc = (x)) != GPW_OK) return rc
+  GPW_TRY(upload(&d.hot_a, H.hot_a, &b));
+  GPW_TRY(upload(&d.hot_b, H.hot_b, &b));
+  GPW_TRY(upload(&d.ids, H.ids, &b));
+  GPW_TRY(upload(&d.ids2, H.ids2, &b));
+  GPW_TRY(upload(&d.geo, H.geo, &b));
+  GPW_TRY(upload(&d.cab, H.cab, &b));
+  GPW_TRY(dalloc(&d.pref, P->npairs, &b));
+  GPW_TRY(upload(&d.tab_off, H.tab_off, &b));
+  GPW_TRY(upload(&d.coef_off, H.coef_off, &b));
+  GPW_TRY(upload(&d.part_off, H.part_off, &b));
+  GPW_TRY(upload(&d.ent, H.ent, &b));
+  GPW_TRY(upload(&d.sub_off, H.sub_off, &b));
+  GPW_TRY(upload(&d.work, H.work, &b));
+  GPW_TRY(upload(&d.groups, H.groups, &b));
+  GPW_TRY(upload(&d.atom_off, H.atom_off, &b));
+  GPW_TRY(upload(&d.atom_list, H.atom_list, &b));
+  GPW_TRY(dalloc(&d.tab, P->tab_total, &b));
+  GPW_TRY(dalloc(&d.coef, P->coef_total, &b));
+  GPW_TRY(dalloc(&d.part, P->part_total, &b));
+  GPW_TRY(dalloc(&d.pgrad, 6 * P->npairs, &b));
+  GPW_TRY(dalloc(&d.grids, P->grid_total, &b));
+  GPW_TRY(dalloc(&d.spec, P->spec_total, &b));
+  GPW_TRY(dalloc(&d.fspec, P->fine_spec_n, &b));
+  GPW_TRY(dalloc(&d.fspec2, P->fine_spec_n, &b));
+  GPW_TRY(dalloc(&d.fine_a, P->fine_n, &b));
+  GPW_TRY(dalloc(&d.fine_b, P->fine_n, &b));
+  GPW_TRY(dalloc(&d.red, 2 * kRedBlocks, &b));
+  GPW_TRY(dalloc(&d.energies, 2, &b));
+  GPW_TRY(dalloc(&d.err, 1, &b));
+  GPW_CK(cudaMemset(d.err, 0, sizeof(int)));
+  {
+    CoefTables t;
+    build_coef_tables(&t);
+    std::vector<CoefTables> v(1, t);
+    GPW_TRY(upload(&d.tabs, v, &b));
+  }
+#undef GPW_TRY
+  for (int k = 0; k < P->nlev; ++k) {
+    const LevelInfo& lv = P->lev[k];
+    GPW_CF(cufftPlan3d(&P->fft_d2z[k], lv.N[0], lv.N[1], lv.N[2], CUFFT_D2Z));
+    if (cufftPlan3d(&P->fft_z2d[k], lv.N[0], lv.N[1], lv.N[2], CUFFT_Z2D) != CUFFT_SUCCESS) {
+      cufftDestroy(P->fft_d2z[k]);
+      set_error("cufftPlan3d Z2D failed");
+      return GPW_ECUFFT;
+    }
+    P->fft_made[k] = true;
+    size_t ws = 0;
+    cufftGetSize(P->fft_d2z[k], &ws);
+    b += (long long)ws;
+    cufftGetSize(P->fft_z2d[k], &ws);
+    b += (long long)ws;
+  }
+  P->device_bytes = b;
+  GPW_CK(configure_kernels(P));
+  GPW_CK(launch_tables(*P, s));
+  return GPW_OK;
+}
+
+int fft_d2z(Plan& P, int k, const double* in, cufftDoubleComplex* out, cudaStream_t s) {
+  GPW_CF(cufftSetStream(P.fft_d2z[k], s));
+  GPW_CF(cufftExecD2Z(P.fft_d2z[k], const_cast<double*>(in), out));
+  return GPW_OK;
+}
+
+int fft_z2d(Plan& P, int k, cufftDoubleComplex* in, double* out, cudaStream_t s) {
+  GPW_CF(cufftSetStream(P.fft_z2d[k], s));
+  GPW_CF(cufftExecZ2D(P.fft_z2d[k], in, out));
+  return GPW_OK;
+}
+
+// rho_k on every level (raw collocation, Algorithm 1 / Eq. rho_wrap).
+int rho_levels(Plan& P, const double* D, cudaStream_t s) {
+  GPW_CK(launch_pair_coef(P, D, s));
+  GPW_CK(cudaMemsetAsync(P.d.grids, 0, sizeof(double) * (size_t)P.grid_total, s));
+  GPW_CK(launch_collocate(P, s));
+  return GPW_OK;
+}
+
+// Level densities -> finest spectrum S (Fourier interpolation, Sec. II).
+int combine(Plan& P, cudaStream_t s) {
+  for (int k = 0; k < P.nlev; ++k) {
+    int rc = fft_d2z(P, k, P.d.grids + P.lev[k].grid_off, P.d.spec + P.lev[k].spec_off, s);
+    if (rc) return rc;
+  }
+  GPW_CK(launch_combine(P, s));
+  return GPW_OK;
+}
+
+// Finest-grid potential -> level potentials in P.d.grids (restriction, Sec. II).
+int restrict_levels(Plan& P, const double* v_fine, cudaStream_t s) {
+  int rc = fft_d2z(P, 0, v_fine, P.d.fspec, s);
+  if (rc) return rc;
+  for (int k = 0; k < P.nlev; ++k) {
+    GPW_CK(launch_restrict(P, k, s));
+    rc = fft_z2d(P, k, P.d.spec + P.lev[k].spec_off, P.d.grids + P.lev[k].grid_off, s);
+    if (rc) return rc;
+  }
+  return GPW_OK;
+}
+
+int copy_levels(Plan& P, const double* const* v_levels, cudaStream_t s) {
+  for (int k = 0; k < P.nlev; ++k) {
+    if (!v_levels[k]) {
+      set_error("NULL level potential");
+      return GPW_EINVAL;
+    }
+    const LevelInfo& lv = P.lev[k];
+    GPW_CK(cudaMemcpyAsync(P.d.grids + lv.grid_off, v_levels[k],
+                           sizeof(double) * (size_t)lv.N[0] * lv.N[1] * lv.N[2],
+                           cudaMemcpyDeviceToDevice, s));
+  }
+  return GPW_OK;
+}
+
+// Integration of the level potentials in P.d.grids into V (Algorithm 2, Eq. J_wrap).
+int mat_from_grids(Plan& P, double* V, cudaStream_t s) {
+  GPW_CK(launch_integrate(P, 0, s));
+  GPW_CK(launch_reduce_parts(P, 0, s));
+  GPW_CK(launch_assemble_V(P, V, s));
+  return GPW_OK;
+}
+
+int ip1_from_grids(Plan& P, const double* D, double* grad, cudaStream_t s) {
+  GPW_CK(launch_integrate(P, 1, s));
+  GPW_CK(launch_reduce_parts(P, 1, s));
+  GPW_CK(launch_grad(P, D, grad, s));
+  return GPW_OK;
+}
+
+int fock_async(Plan& P, const double* D, double* V, double* energies_dev, double* rho_out,
+               double* v_out, cudaStream_t s) {
+  int rc = rho_levels(P, D, s);
+  if (rc) return rc;
+  if ((rc = combine(P, s))) return rc;
+  double* rho = rho_out ? rho_out : P.d.fine_b;
+  GPW_CK(cudaMemcpyAsync(P.d.fspec2, P.d.fspec, sizeof(cufftDoubleComplex) * (size_t)P.fine_spec_n,
+                         cudaMemcpyDeviceToDevice, s));
+  if ((rc = fft_z2d(P, 0, P.d.fspec2, rho, s))) return rc;
+  GPW_CK(launch_poisson(P, s));
+  if ((rc = fft_z2d(P, 0, P.d.fspec, P.d.fine_a, s))) return rc;
+  double* v = v_out ? v_out : P.d.fine_a;
+  GPW_CK(launch_lda(P, rho, P.d.fine_a, v, s));
+  GPW_CK(launch_energy_final(P, 0, kRedBlocks, s));
+  GPW_CK(launch_energy_final(P, 1, kRedBlocks, s));
+  if (energies_dev != P.d.energies)
+    GPW_CK(cudaMemcpyAsync(energies_dev, P.d.energies, 2 * sizeof(double),
+                           cudaMemcpyDeviceToDevice, s));
+  if ((rc = restrict_levels(P, v, s))) return rc;
+  return mat_from_grids(P, V, s);
+}
+
+bool bad(gpw_plan_t plan) {
+  if (!plan) {
+    set_error("NULL plan");
+    return true;
+  }
+  return false;
+}
+
+}  // namespace
+}  // namespace gpw
+
+using gpw::set_error;
+
+extern "C" {
+
+int gpw_plan(const gpw_desc* desc, void* stream, gpw_plan_t* out) {
+  if (!out) {
+    set_error("gpw_plan: NULL out");
+    return GPW_EINVAL;
+  }
+  try {
+    std::unique_ptr<gpw_plan_s> h(new gpw_plan_s());
+    gpw::HostArrays H;
+    int rc = gpw::build_host_plan(desc, &h->p, &H);
+    if (rc) return rc;
+    cudaGetDevice(&h->p.device);
+    rc = gpw::create_device(&h->p, H, (cudaStream_t)stream);
+    if (rc) {
+      gpw::free_plan(&h->p);
+      return rc;
+    }
+    *out = h.release();
+    return GPW_OK;
+  } catch (const std::bad_alloc&) {
+    set_error("gpw_plan: host allocation failed");
+    return GPW_ENOMEM;
+  } catch (...) {
+    set_error("gpw_plan: unexpected exception");
+    return GPW_EINVAL;
+  }
+}
+
+int gpw_plan_query(gpw_plan_t plan, gpw_plan_info* info) {
+  if (gpw::bad(plan) || !info) return GPW_EINVAL;
+  const gpw::Plan& P = plan->p;
+  std::memset(info, 0, sizeof(*info));
+  info->nao = P.nao;
+  info->natm = P.natm;
+  info->nlevels = P.nlev;
+  info->lmax = P.lmax;
+  for (int k = 0; k < P.nlev; ++k) {
+    for (int d = 0; d < 3; ++d) info->meshes[k][d] = P.lev[k].N[d];
+    info->level_cutoff[k] = P.E[k];
+    info->npairs_level[k] = P.npairs_level[k];
+    info->pair_points_level[k] = P.pair_points_level[k];
+  }
+  for (int l = 0; l < 8; ++l) info->pair_points_L[l] = P.pair_points_L[l];
+  info->npairs = P.npairs;
+  info->pair_points = P.pair_points;
+  info->nentries = P.nent;
+  info->device_bytes = P.device_bytes;
+  info->flops_rho = P.flops_rho;
+  info->flops_mat = P.flops_mat;
+  info->flops_ip1 = P.flops_ip1;
+  info->tile[0] = gpw::kT0;
+  info->tile[1] = gpw::kT1;
+  info->tile[2] = gpw::kT2;
+  return GPW_OK;
+}
+
+int gpw_plan_update_coords(gpw_plan_t plan, const double* coords, void* stream) {
+  if (gpw::bad(plan) || !coords) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  const long long np = P.npairs;
+  std::vector<double> geo(8 * np);
+  for (long long p = 0; p < np; ++p) {
+    const int a = P.pair_a[p], b = P.pair_b[p];
+    const int ia = P.prim_atom[a], ib = P.prim_atom[b];
+    for (int d = 0; d < 3; ++d) {
+      geo[8 * p + d] = coords[3 * ia + d];
+      geo[8 * p + 3 + d] = coords[3 * ib + d] + (double)P.h_img[3 * p + d] * P.L[d];
+    }
+    geo[8 * p + 6] = P.prim_alpha[a];
+    geo[8 * p + 7] = P.prim_alpha[b];
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (np) {
+    cudaError_t e = cudaMemcpyAsync(P.d.geo, geo.data(), sizeof(double) * geo.size(),
+                                    cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      set_error(std::string("update_coords: ") + cudaGetErrorString(e));
+      return GPW_ECUDA;
+    }
+  }
+  P.coords.assign(coords, coords + 3 * P.natm);
+  cudaError_t e = gpw::launch_tables(P, s);
+  if (e != cudaSuccess) {
+    set_error(std::string("update_coords: ") + cudaGetErrorString(e));
+    return GPW_ECUDA;
+  }
+  return GPW_OK;
+}
+
+int gpw_plan_pairs(gpw_plan_t plan, int* ab, int* img, int* level, int* lo, int* hi) {
+  if (gpw::bad(plan)) return GPW_EINVAL;
+  const gpw::Plan& P = plan->p;
+  if (ab) std::copy(P.h_ab.begin(), P.h_ab.end(), ab);
+  if (img) std::copy(P.h_img.begin(), P.h_img.end(), img);
+  if (level) std::copy(P.h_lev.begin(), P.h_lev.end(), level);
+  if (lo) std::copy(P.h_lo.begin(), P.h_lo.end(), lo);
+  if (hi) std::copy(P.h_hi.begin(), P.h_hi.end(), hi);
+  return GPW_OK;
+}
+
+int gpw_eval_rho_levels(gpw_plan_t plan, const double* D, double* const* rho_levels,
+                        void* stream) {
+  if (gpw::bad(plan) || !D || !rho_levels) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::rho_levels(P, D, s);
+  if (rc) return rc;
+  for (int k = 0; k < P.nlev; ++k) {
+    if (!rho_levels[k]) continue;
+    const gpw::LevelInfo& lv = P.lev[k];
+    cudaError_t e = cudaMemcpyAsync(rho_levels[k], P.d.grids + lv.grid_off,
+                                    sizeof(double) * (size_t)lv.N[0] * lv.N[1] * lv.N[2],
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+      set_error(std::string("eval_rho_levels: ") + cudaGetErrorString(e));
+      return GPW_ECUDA;
+    }
+  }
+  return GPW_OK;
+}
+
+int gpw_eval_rho(gpw_plan_t plan, const double* D, double* rho_fine, void* stream) {
+  if (gpw::bad(plan) || !D || !rho_fine) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::rho_levels(P, D, s);
+  if (rc) return rc;
+  if ((rc = gpw::combine(P, s))) return rc;
+  return gpw::fft_z2d(P, 0, P.d.fspec, rho_fine, s);
+}
+
+int gpw_eval_mat(gpw_plan_t plan, const double* v_fine, double* V, void* stream) {
+  if (gpw::bad(plan) || !v_fine || !V) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::restrict_levels(P, v_fine, s);
+  if (rc) return rc;
+  return gpw::mat_from_grids(P, V, s);
+}
+
+int gpw_eval_mat_levels(gpw_plan_t plan, const double* const* v_levels, double* V,
+                        void* stream) {
+  if (gpw::bad(plan) || !v_levels || !V) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::copy_levels(P, v_levels, s);
+  if (rc) return rc;
+  return gpw::mat_from_grids(P, V, s);
+}
+
+int gpw_eval_mat_ip1(gpw_plan_t plan, const double* D, const double* v_fine, double* grad,
+                     void* stream) {
+  if (gpw::bad(plan) || !D || !v_fine || !grad) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::restrict_levels(P, v_fine, s);
+  if (rc) return rc;
+  return gpw::ip1_from_grids(P, D, grad, s);
+}
+
+int gpw_eval_mat_ip1_levels(gpw_plan_t plan, const double* D, const double* const* v_levels,
+                            double* grad, void* stream) {
+  if (gpw::bad(plan) || !D || !v_levels || !grad) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::copy_levels(P, v_levels, s);
+  if (rc) return rc;
+  return gpw::ip1_from_grids(P, D, grad, s);
+}
+
+int gpw_fock_async(gpw_plan_t plan, const double* D, double* V, double* energies_dev,
+                   double* rho_out, double* v_fine_out, void* stream) {
+  if (gpw::bad(plan) || !D || !V || !energies_dev) return GPW_EINVAL;
+  return gpw::fock_async(plan->p, D, V, energies_dev, rho_out, v_fine_out, (cudaStream_t)stream);
+}
+
+int gpw_fock(gpw_plan_t plan, const double* D, double* V, double* energies, double* rho_out,
+             double* v_fine_out, void* stream) {
+  if (gpw::bad(plan) || !D || !V || !energies) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::fock_async(P, D, V, P.d.energies, rho_out, v_fine_out, s);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(energies, P.d.energies, 2 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_error(std::string("gpw_fock: ") + cudaGetErrorString(e));
+    return GPW_ECUDA;
+  }
+  return GPW_OK;
+}
+
+int gpw_check_device(gpw_plan_t plan, int* code, void* stream) {
+  if (gpw::bad(plan)) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int h = 0;
+  cudaError_t e = cudaMemcpyAsync(&h, P.d.err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.d.err, 0, sizeof(int), s);
+  if (e != cudaSuccess) {
+    set_error(std::string("gpw_check_device: ") + cudaGetErrorString(e));
+    return GPW_ECUDA;
+  }
+  if (code) *code = h;
+  if (h) {
+    set_error("device bounds check failed, code " + std::to_string(h));
+    return GPW_EDEVICE;
+  }
+  return GPW_OK;
+}
+
+void gpw_plan_destroy(gpw_plan_t plan) {
+  if (!plan) return;
+  gpw::free_plan(&plan->p);
+  delete plan;
+}
+
+const char* gpw_strerror(int code) {
+  switch (code) {
+    case GPW_OK: return "ok";
+    case GPW_EINVAL: return "invalid argument";
+    case GPW_ENOMEM: return "out of memory";
+    case GPW_ECUDA: return "CUDA error";
+    case GPW_ECUFFT: return "cuFFT error";
+    case GPW_ETIMEDOUT: return "timed out";
+    case GPW_EDEVICE: return "device bounds check failed";
+    case GPW_ERANGE: return "size beyond a fixed limit";
+    default: return "unknown error";
+  }
+}
+
+const char* gpw_last_error(void) { return gpw::g_err.c_str(); }
+
+}  // extern "C"

@@ -1,0 +1,130 @@
+// Internal layout of a libgpw plan: host-side screening results and the device arrays
+// the kernels read.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <string>
+#include <vector>
+
+#include "gpw.h"
+
+namespace gpw {
+
+constexpr int kShellLmax = 3;                   // Cartesian shells up to f
+constexpr int kLmax = 2 * kShellLmax;           // la + lb
+constexpr int kLextMax = kLmax + 1;             // one more for the centre derivatives
+constexpr int kNc3Max = (kLextMax + 1) * (kLextMax + 2) * (kLextMax + 3) / 6;  // 120
+constexpr int kNc2Max = (kLextMax + 1) * (kLextMax + 2) / 2;                   // 36
+
+// Sub-box (tile) owned by one thread block: kT0 x kT1 x kT2 grid points, the last
+// along the fastest grid index, so a tile row is 16 contiguous doubles (128 B).
+constexpr int kT0 = 8, kT1 = 8, kT2 = 16;
+constexpr int kTile = kT0 * kT1 * kT2;
+
+// Number of monomials x^l0 y^l1 z^l2 with l0 + l1 + l2 <= L, and of (l1, l2) pairs.
+__host__ __device__ constexpr int nc3(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
+__host__ __device__ constexpr int nc2(int L) { return (L + 1) * (L + 2) / 2; }
+
+// Flat order of the pair coefficient tensors D[l0,l1,l2] / V[l0,l1,l2] of total degree
+// <= L (Eqs. rho1 and the V tensor of Sec. III A):
+//   for l2 in 0..L, for l1 in 0..L-l2 (the (l2,l1) index c21), for l0 in 0..L-l2-l1.
+// Decode tables for every L <= kLextMax live in one small device array:
+//   dec21[L][c21] = l2 | l1 << 8 | base3 << 16   (base3 = flat index of (0,l1,l2))
+//   dec3[L][c]    = c21 | l0 << 8
+struct CoefTables {
+  int dec21[kLextMax + 1][kNc2Max];
+  int dec3[kLextMax + 1][kNc3Max];
+  int c21base[kLextMax + 1][kLextMax + 1];  // c21 of (l2, 0)
+};
+void build_coef_tables(CoefTables* t);
+
+struct LevelInfo {
+  int N[3];
+  int nsb[3];            // sub-boxes per dimension (ceil(N / tile))
+  long long grid_off;    // offset of the level grid in the level-grid buffer
+  long long spec_off;    // offset of the level half spectrum (complex elements)
+  long long sub_base;    // first sub-box of this level in the task CSR
+  double Gk2;            // cutoff sphere: |G|^2 < Gk2
+  double weight;         // Omega / (N0 N1 N2)
+  double h[3];           // grid spacing L_d / N_d
+};
+
+struct DeviceArrays {
+  // per pair (SoA)
+  int4* hot_a = nullptr;      // lo0, lo1, lo2, L = la + lb
+  int4* hot_b = nullptr;      // n0, n1, n2, level      (n = box extent)
+  int4* ids = nullptr;        // la, lb, ao_a, ao_b
+  int4* ids2 = nullptr;       // atom_a, atom_b, w (2 if a < b else 1), nentries
+  double* geo = nullptr;      // 8 per pair: A[3], B[3] (image of b), alpha_a, alpha_b
+  double* cab = nullptr;      // c_a N_a c_b N_b
+  double* pref = nullptr;     // c_a N_a c_b N_b K_ab (K_ab = exp(-a b |A-B|^2/(a+b)))
+  long long* tab_off = nullptr;   // 1-D factor tables
+  long long* coef_off = nullptr;  // D tensor (rho) / reduced V tensor (stride nc3(L+1))
+  long long* part_off = nullptr;  // per-task V tensors (stride nc3(L+1) per task)
+  // tasks
+  int4* ent = nullptr;        // pair, packed image shifts, rank within pair, 0
+  long long* sub_off = nullptr;   // CSR offsets over all sub-boxes of all levels
+  int2* work = nullptr;       // (level, sub-box) with tasks, heaviest first
+  // V assembly: groups of pairs sharing a contracted shell pair
+  int4* groups = nullptr;     // shell a, shell b, first pair, end pair
+  // gradient assembly
+  long long* atom_off = nullptr;  // CSR over atoms
+  int* atom_list = nullptr;       // 2 * pair + side
+  // tables and buffers
+  double* tab = nullptr;
+  double* coef = nullptr;     // per call: D tensors / reduced V tensors
+  double* part = nullptr;     // per call: task V tensors
+  double* pgrad = nullptr;    // 6 per pair
+  double* grids = nullptr;    // level real grids
+  cufftDoubleComplex* spec = nullptr;   // level half spectra
+  cufftDoubleComplex* fspec = nullptr;  // finest half spectrum (work)
+  cufftDoubleComplex* fspec2 = nullptr; // copy (C2R overwrites its input)
+  double* fine_a = nullptr;   // finest real scratch
+  double* fine_b = nullptr;
+  double* red = nullptr;      // reduction partials
+  double* energies = nullptr; // E_H, E_x (device)
+  int* err = nullptr;         // device error word
+  CoefTables* tabs = nullptr;
+};
+
+struct Plan {
+  int device = 0;
+  int nao = 0, natm = 0, nlev = 0, lmax = 0;
+  int nprim = 0, nshell = 0;
+  double L[3] = {0, 0, 0};
+  double omega = 0;
+  double E[GPW_MAX_LEVELS] = {0};
+  LevelInfo lev[GPW_MAX_LEVELS];
+  long long npairs = 0, nent = 0, nwork = 0, nsub_total = 0, ngroups = 0;
+  long long tab_total = 0, coef_total = 0, part_total = 0;
+  long long grid_total = 0, spec_total = 0, fine_n = 0, fine_spec_n = 0;
+  long long pair_points = 0;
+  long long pair_points_level[GPW_MAX_LEVELS] = {0};
+  long long pair_points_L[8] = {0};
+  long long npairs_level[GPW_MAX_LEVELS] = {0};
+  double flops_rho = 0, flops_mat = 0, flops_ip1 = 0;
+  long long device_bytes = 0;
+  // host copies needed after construction
+  std::vector<int> h_ab, h_img, h_lev, h_lo, h_hi;   // screened pair table (pair order)
+  std::vector<int> prim_atom;                          // per primitive
+  std::vector<double> prim_alpha;
+  std::vector<int> pair_a, pair_b;                     // primitive indices per pair
+  std::vector<double> coords;                          // natm * 3
+  DeviceArrays d;
+  cufftHandle fft_d2z[GPW_MAX_LEVELS];
+  cufftHandle fft_z2d[GPW_MAX_LEVELS];
+  bool fft_made[GPW_MAX_LEVELS] = {false};
+  int red_blocks = 0;
+  size_t smem_colloc = 0, smem_integ = 0, smem_integ1 = 0;
+  int nw_colloc = 8, nw_integ = 8;     // warps per thread block
+  int stg_colloc = 0, stg_integ = 0, stg_integ1 = 0;  // per-warp staging doubles
+};
+
+// plan.cpp (host): screening and task lists; fills everything except device arrays.
+int build_host_plan(const gpw_desc* desc, Plan* plan, struct HostArrays* host);
+
+void set_error(const std::string& msg);
+
+}  // namespace gpw

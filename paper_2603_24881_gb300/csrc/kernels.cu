@@ -1,0 +1,981 @@
+// libgpw CUDA kernels for sm_103a, all arithmetic in FP64.
+//
+// GB300 issues one warp-wide FP64 FMA per 64 cycles per SM sub-partition, while
+// integer, FP32 and shared-memory instructions issue every cycle.  The kernels are
+// therefore organised to spend as few FP64 instructions as possible per pair-point and
+// to keep every lane of each FP64 instruction busy; index arithmetic uses INT32/FP32.
+//
+// Collocation (Algorithm 1) and integration (Algorithm 2) both use the separable,
+// binomially expanded form of the pair product (Eqs. gx, gab, binomial, gab_lp, rho1
+// and the V tensor): a pair contributes
+//     sum_{l0+l1+l2 <= L} D[l0,l1,l2] g0[l0](x0) g1[l1](x1) g2[l2](x2)
+// with g_d[l](x) = (x - A_d)^l exp(-alpha_p (x - P_d)^2).  The 1-D factors are tabulated
+// once per plan; a thread block owns one kT0 x kT1 x kT2 sub-box of a level grid and
+// contracts the three dimensions one after another for every (pair, sub-box) task.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "gpw_internal.h"
+#include "kernels.h"
+
+namespace gpw {
+
+namespace {
+
+constexpr int kTabInts = (kLextMax + 1) * (kNc2Max + kNc3Max + kLextMax + 1);
+static_assert(kTabInts % 4 == 0, "table block must keep 16-byte alignment");
+static_assert(sizeof(CoefTables) == kTabInts * sizeof(int), "CoefTables layout");
+
+__device__ __forceinline__ int fdiv(int x, float inv) {
+  // exact floor(x / m) for 0 <= x < 4096, m <= 512, inv = 1/m rounded to fp32
+  return __float2int_rz(((float)x + 0.5f) * inv);
+}
+
+__device__ __forceinline__ void cart_comp(int l, int idx, int* c) {
+  int n = 0;
+  for (int ix = l; ix >= 0; --ix)
+    for (int iy = l - ix; iy >= 0; --iy) {
+      if (n == idx) {
+        c[0] = ix;
+        c[1] = iy;
+        c[2] = l - ix - iy;
+        return;
+      }
+      ++n;
+    }
+  c[0] = c[1] = c[2] = 0;
+}
+
+__device__ __forceinline__ double binom(int n, int k) {
+  // n <= 4
+  const double t[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0},
+                          {1, 4, 6, 4, 1}};
+  return t[n][k];
+}
+
+__device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
+
+__device__ __forceinline__ void load_tables(int* dst, const CoefTables* src, int tid, int nthr) {
+  const int4* s4 = reinterpret_cast<const int4*>(src);
+  int4* d4 = reinterpret_cast<int4*>(dst);
+  for (int i = tid; i < kTabInts / 4; i += nthr) d4[i] = s4[i];
+}
+
+// Intersection of a task's pair box with its sub-box copy.
+struct Task {
+  int p, L;
+  int m[3];   // extent of the intersection
+  int t[3];   // offset of the intersection in the pair box (table column)
+  int u[3];   // offset of the intersection in the sub-box
+  int n[3];   // pair box extent (table row length)
+  int rank;
+};
+
+__device__ __forceinline__ bool make_task(const int4 e, const int4* hot_a, const int4* hot_b,
+                                          const LevelInfo& lv, const int* s, const int* ext,
+                                          Task* tk) {
+  const int p = e.x;
+  const int4 ha = __ldg(hot_a + p);
+  const int4 hb = __ldg(hot_b + p);
+  const int k[3] = {(e.y & 1023) - 512, ((e.y >> 10) & 1023) - 512, ((e.y >> 20) & 1023) - 512};
+  const int lo[3] = {ha.x, ha.y, ha.z};
+  tk->p = p;
+  tk->L = ha.w;
+  tk->n[0] = hb.x;
+  tk->n[1] = hb.y;
+  tk->n[2] = hb.z;
+  tk->rank = e.z;
+  bool ok = true;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    int o = k[d] * lv.N[d] + s[d];
+    int a = max(lo[d], o);
+    int b = min(lo[d] + tk->n[d] - 1, o + ext[d] - 1);
+    tk->m[d] = b - a + 1;
+    tk->t[d] = a - lo[d];
+    tk->u[d] = a - o;
+    ok = ok && (tk->m[d] > 0);
+  }
+  return ok;
+}
+
+// ----------------------------------------------------------------------------------
+// 1-D factor tables (Eq. gab_lp with the exponential of Eq. gab):
+//   g_d[l](i) = (x - A_d)^l exp(-alpha_p (x - P_d)^2),  x = (lo_d + i) h_d,  l <= L + 1,
+// laid out per pair as [d][l][n_d].  Also pref = c_a N_a c_b N_b K_ab.  One warp per pair.
+__global__ void tables_kernel(long long np, const KLevels K, const int4* __restrict__ hot_a,
+                              const int4* __restrict__ hot_b, const double* __restrict__ geo,
+                              const double* __restrict__ cab,
+                              const long long* __restrict__ tab_off, double* __restrict__ tab,
+                              double* __restrict__ pref) {
+  const int lane = threadIdx.x & 31;
+  long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long sw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long p = gw; p < np; p += sw) {
+    const int4 ha = hot_a[p];
+    const int4 hb = hot_b[p];
+    const int L = ha.w;
+    const LevelInfo& lv = K.lv[hb.w];
+    const double* g = geo + 8 * p;
+    const double aa = g[6], ab = g[7], ap = aa + ab;
+    double P[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) P[d] = (aa * g[d] + ab * g[3 + d]) / ap;
+    if (lane == 0) {
+      double ab2 = 0.0;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) ab2 += (g[d] - g[3 + d]) * (g[d] - g[3 + d]);
+      pref[p] = cab[p] * exp(-aa * ab * ab2 / ap);
+    }
+    const int n[3] = {hb.x, hb.y, hb.z};
+    const int lo[3] = {ha.x, ha.y, ha.z};
+    const int ntot = n[0] + n[1] + n[2];
+    const long long base = tab_off[p];
+    for (int it = lane; it < ntot; it += 32) {
+      int d = it < n[0] ? 0 : (it < n[0] + n[1] ? 1 : 2);
+      int off = d == 0 ? 0 : (d == 1 ? n[0] : n[0] + n[1]);
+      int i = it - off;
+      double x = (double)(lo[d] + i) * lv.h[d];
+      double u = x - g[d];
+      double t = x - P[d];
+      double v = exp(-ap * t * t);
+      double* dst = tab + base + (long long)(L + 2) * off + i;
+      for (int l = 0; l <= L + 1; ++l) {
+        dst[(long long)l * n[d]] = v;
+        v *= u;
+      }
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------------
+// Pair coefficient tensor for collocation (Eq. rho1): contract the density-matrix block
+// of the pair with the binomial expansion of Eq. (binomial) in every dimension,
+//   D[k0,k1,k2] = w pref sum_{mu in a, nu in b} D_mu,nu prod_d C(b_d, k_d - a_d) (A_d - B_d)^(a_d + b_d - k_d)
+// w = 2 for a < b (the pair also stands for (b, a, -T)).  One thread per pair.
+__global__ void pair_coef_kernel(long long np, const int4* __restrict__ hot_a,
+                                 const int4* __restrict__ ids, const int4* __restrict__ ids2,
+                                 const double* __restrict__ geo, const double* __restrict__ pref,
+                                 const long long* __restrict__ coef_off,
+                                 const CoefTables* __restrict__ tabs, const double* __restrict__ D,
+                                 int nao, double* __restrict__ coef) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const int4 id = ids[p];
+  const int la = id.x, lb = id.y, L = la + lb;
+  const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
+  const double* g = geo + 8 * p;
+  double pw[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double ab = g[d] - g[3 + d];
+    pw[d][0] = 1.0;
+    pw[d][1] = ab;
+    pw[d][2] = ab * ab;
+    pw[d][3] = ab * ab * ab;
+  }
+  double acc[nc3(kLmax)];
+  const int nc = nc3(L);
+  for (int c = 0; c < nc; ++c) acc[c] = 0.0;
+  const double scale = (double)ids2[p].z * pref[p];
+  for (int mu = 0; mu < na; ++mu) {
+    int ca[3];
+    cart_comp(la, mu, ca);
+    const double* Drow = D + (long long)(id.z + mu) * nao + id.w;
+    for (int nu = 0; nu < nb; ++nu) {
+      int cb[3];
+      cart_comp(lb, nu, cb);
+      const double dmn = scale * Drow[nu];
+      for (int t2 = 0; t2 <= cb[2]; ++t2) {
+        const double c2 = dmn * binom(cb[2], t2) * pw[2][cb[2] - t2];
+        const int k2 = ca[2] + t2;
+        for (int t1 = 0; t1 <= cb[1]; ++t1) {
+          const double c21 = c2 * binom(cb[1], t1) * pw[1][cb[1] - t1];
+          const int k1 = ca[1] + t1;
+          const int base = tabs->dec21[L][tabs->c21base[L][k2] + k1] >> 16;
+          for (int t0 = 0; t0 <= cb[0]; ++t0)
+            acc[base + ca[0] + t0] += c21 * binom(cb[0], t0) * pw[0][cb[0] - t0];
+        }
+      }
+    }
+  }
+  double* out = coef + coef_off[p];
+  for (int c = 0; c < nc; ++c) out[c] = acc[c];
+}
+
+// ----------------------------------------------------------------------------------
+// Collocation (Algorithm 1, two-stage: accumulate on chip, write each point once).
+// One thread block per sub-box with tasks; warp w takes tasks w, w + NW, ... of the
+// sub-box's list and accumulates into its own copy of the sub-box in shared memory;
+// the NW copies are summed in a fixed order and written once (coalesced, no atomics).
+// Per task, with m the intersection extents:
+//   T1[l2,l1](i0) = sum_l0 D[l0,l1,l2] g0[l0](i0)            nc2(L) m0 FMAs
+//   T2[l2](i0,i1) = sum_l1 T1[l2,l1](i0) g1[l1](i1)          nc2(L) m0 m1
+//   rho(i0,i1,i2) += sum_l2 T2[l2](i0,i1) g2[l2](i2)         (L+1) m0 m1 m2
+template <int NW>
+__global__ void __launch_bounds__(NW * 32)
+    collocate_kernel(const KLevels K, const int2* __restrict__ work,
+                     const long long* __restrict__ sub_off, const int4* __restrict__ ent,
+                     const int4* __restrict__ hot_a, const int4* __restrict__ hot_b,
+                     const long long* __restrict__ tab_off, const long long* __restrict__ coef_off,
+                     const double* __restrict__ tab, const double* __restrict__ coef,
+                     const CoefTables* __restrict__ tabs, double* __restrict__ grids, int lp,
+                     int stg, int* __restrict__ err) {
+  extern __shared__ __align__(16) double sm[];
+  int* s_tab = reinterpret_cast<int*>(sm);
+  const int(*s_dec21)[kNc2Max] = reinterpret_cast<const int(*)[kNc2Max]>(s_tab);
+  const int(*s_c21b)[kLextMax + 1] = reinterpret_cast<const int(*)[kLextMax + 1]>(
+      s_tab + (kLextMax + 1) * (kNc2Max + kNc3Max));
+  double* acc_all = sm + kTabInts / 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  load_tables(s_tab, tabs, tid, NW * 32);
+  for (int i = tid; i < NW * kTile; i += NW * 32) acc_all[i] = 0.0;
+
+  const int2 item = work[blockIdx.x];
+  const LevelInfo& lv = K.lv[item.x];
+  const int sub = item.y;
+  const int j2 = sub % lv.nsb[2];
+  const int j1 = (sub / lv.nsb[2]) % lv.nsb[1];
+  const int j0 = sub / (lv.nsb[2] * lv.nsb[1]);
+  const int s[3] = {j0 * kT0, j1 * kT1, j2 * kT2};
+  const int ext[3] = {min(kT0, lv.N[0] - s[0]), min(kT1, lv.N[1] - s[1]),
+                      min(kT2, lv.N[2] - s[2])};
+  const long long eb = sub_off[lv.sub_base + sub], ee = sub_off[lv.sub_base + sub + 1];
+
+  double* acc = acc_all + warp * kTile;
+  double* sg0 = acc_all + NW * kTile + warp * stg;
+  double* sg1 = sg0 + lp * kT0;
+  double* sg2 = sg1 + lp * kT1;
+  double* sD = sg2 + lp * kT2;
+  double* sT1 = sD + nc3(lp - 1);
+  double* sT2 = sT1 + nc2(lp - 1) * kT0;
+  __syncthreads();
+
+  for (long long e = eb + warp; e < ee; e += NW) {
+    Task tk;
+    if (!make_task(__ldg(ent + e), hot_a, hot_b, lv, s, ext, &tk)) {
+      if (lane == 0) set_err(err, 1);
+      continue;
+    }
+    const int L = tk.L;
+    if (L + 1 > lp) {
+      if (lane == 0) set_err(err, 2);
+      continue;
+    }
+    const double* tb = tab + __ldg(tab_off + tk.p);
+    const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
+    // stage the three 1-D factor windows and the coefficient tensor
+    {
+      const int rows = L + 1;
+      const double* t0 = tb + tk.t[0];
+      const double* t1 = tb + (L + 2) * tk.n[0] + tk.t[1];
+      const double* t2 = tb + (L + 2) * (tk.n[0] + tk.n[1]) + tk.t[2];
+      const float i0f = __frcp_rn((float)m0), i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
+      for (int it = lane; it < rows * m0; it += 32) {
+        int l = fdiv(it, i0f), i = it - l * m0;
+        sg0[l * kT0 + i] = __ldg(t0 + l * tk.n[0] + i);
+      }
+      for (int it = lane; it < rows * m1; it += 32) {
+        int l = fdiv(it, i1f), i = it - l * m1;
+        sg1[l * kT1 + i] = __ldg(t1 + l * tk.n[1] + i);
+      }
+      for (int it = lane; it < rows * m2; it += 32) {
+        int l = fdiv(it, i2f), i = it - l * m2;
+        sg2[l * kT2 + i] = __ldg(t2 + l * tk.n[2] + i);
+      }
+      const double* cp = coef + __ldg(coef_off + tk.p);
+      for (int c = lane; c < nc3(L); c += 32) sD[c] = __ldg(cp + c);
+    }
+    __syncwarp();
+    // T1[c21](i0)
+    {
+      const float inv = __frcp_rn((float)m0);
+      const int items = nc2(L) * m0;
+      for (int it = lane; it < items; it += 32) {
+        const int c21 = fdiv(it, inv), i0 = it - c21 * m0;
+        const int dc = s_dec21[L][c21];
+        const int l2 = dc & 255, l1 = (dc >> 8) & 255, b3 = dc >> 16;
+        double acc1 = 0.0;
+        for (int l0 = 0; l0 <= L - l2 - l1; ++l0) acc1 = fma(sD[b3 + l0], sg0[l0 * kT0 + i0], acc1);
+        sT1[c21 * kT0 + i0] = acc1;
+      }
+    }
+    __syncwarp();
+    // T2[l2](q = i0 m1 + i1)
+    const int m01 = m0 * m1;
+    {
+      const float inv01 = __frcp_rn((float)m01), inv1 = __frcp_rn((float)m1);
+      const int items = (L + 1) * m01;
+      for (int it = lane; it < items; it += 32) {
+        const int l2 = fdiv(it, inv01), q = it - l2 * m01;
+        const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
+        const int cb = s_c21b[L][l2];
+        double acc2 = 0.0;
+        for (int l1 = 0; l1 <= L - l2; ++l1)
+          acc2 = fma(sT1[(cb + l1) * kT0 + i0], sg1[l1 * kT1 + i1], acc2);
+        sT2[l2 * (kT0 * kT1) + q] = acc2;
+      }
+    }
+    __syncwarp();
+    // rho(i0,i1,i2) += sum_l2 T2[l2](q) g2[l2](i2)
+    {
+      const float inv2 = __frcp_rn((float)m2), inv1 = __frcp_rn((float)m1);
+      const int items = m01 * m2;
+      const int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
+      for (int it = lane; it < items; it += 32) {
+        const int q = fdiv(it, inv2), i2 = it - q * m2;
+        const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
+        double* a = acc + ((u0 + i0) * kT1 + (u1 + i1)) * kT2 + (u2 + i2);
+        double r = *a;
+        for (int l2 = 0; l2 <= L; ++l2) r = fma(sT2[l2 * (kT0 * kT1) + q], sg2[l2 * kT2 + i2], r);
+        *a = r;
+      }
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+  // sum the warp copies in warp order and write the sub-box once
+  double* out = grids + lv.grid_off;
+  const int e12 = ext[1] * ext[2];
+  const int npts = ext[0] * e12;
+  for (int pt = tid; pt < npts; pt += NW * 32) {
+    const int i0 = pt / e12, r = pt - i0 * e12, i1 = r / ext[2], i2 = r - i1 * ext[2];
+    const int ti = (i0 * kT1 + i1) * kT2 + i2;
+    double v = acc_all[ti];
+#pragma unroll
+    for (int w = 1; w < NW; ++w) v += acc_all[w * kTile + ti];
+    out[((long long)(s[0] + i0) * lv.N[1] + (s[1] + i1)) * lv.N[2] + (s[2] + i2)] = v;
+  }
+}
+
+// ----------------------------------------------------------------------------------
+// Integration (Algorithm 2 and, with lext = 1, the gradient of Algorithm 3): the
+// thread block stages its sub-box of the level potential in shared memory once; every
+// task contracts it with the pair's 1-D factors (the V tensor of Sec. III A):
+//   U[l2](i0,i1) = sum_i2 v(i0,i1,i2) g2[l2](i2)        (Lx+1) m0 m1 m2 FMAs
+//   W[l2,l1](i0) = sum_i1 U[l2](i0,i1) g1[l1](i1)        nc2(Lx) m0 m1
+//   V[l0,l1,l2]  = sum_i0 W[l2,l1](i0) g0[l0](i0)        nc3(Lx) m0
+// and stores V for the task; the per-pair sum over tasks happens in reduce_parts_kernel
+// in a fixed order.  Lx = L + lext.
+template <int NW>
+__global__ void __launch_bounds__(NW * 32)
+    integrate_kernel(const KLevels K, const int2* __restrict__ work,
+                     const long long* __restrict__ sub_off, const int4* __restrict__ ent,
+                     const int4* __restrict__ hot_a, const int4* __restrict__ hot_b,
+                     const long long* __restrict__ tab_off, const long long* __restrict__ part_off,
+                     const double* __restrict__ tab, const CoefTables* __restrict__ tabs,
+                     const double* __restrict__ grids, double* __restrict__ part, int lext,
+                     int lpx, int stg, int* __restrict__ err) {
+  extern __shared__ __align__(16) double sm[];
+  int* s_tab = reinterpret_cast<int*>(sm);
+  const int(*s_dec21)[kNc2Max] = reinterpret_cast<const int(*)[kNc2Max]>(s_tab);
+  const int(*s_dec3)[kNc3Max] =
+      reinterpret_cast<const int(*)[kNc3Max]>(s_tab + (kLextMax + 1) * kNc2Max);
+  double* sv = sm + kTabInts / 2;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  load_tables(s_tab, tabs, tid, NW * 32);
+
+  const int2 item = work[blockIdx.x];
+  const LevelInfo& lv = K.lv[item.x];
+  const int sub = item.y;
+  const int j2 = sub % lv.nsb[2];
+  const int j1 = (sub / lv.nsb[2]) % lv.nsb[1];
+  const int j0 = sub / (lv.nsb[2] * lv.nsb[1]);
+  const int s[3] = {j0 * kT0, j1 * kT1, j2 * kT2};
+  const int ext[3] = {min(kT0, lv.N[0] - s[0]), min(kT1, lv.N[1] - s[1]),
+                      min(kT2, lv.N[2] - s[2])};
+  const long long eb = sub_off[lv.sub_base + sub], ee = sub_off[lv.sub_base + sub + 1];
+  {
+    const double* vin = grids + lv.grid_off;
+    const int e12 = ext[1] * ext[2];
+    const int npts = ext[0] * e12;
+    for (int pt = tid; pt < npts; pt += NW * 32) {
+      const int i0 = pt / e12, r = pt - i0 * e12, i1 = r / ext[2], i2 = r - i1 * ext[2];
+      sv[(i0 * kT1 + i1) * kT2 + i2] =
+          __ldg(vin + ((long long)(s[0] + i0) * lv.N[1] + (s[1] + i1)) * lv.N[2] + (s[2] + i2));
+    }
+  }
+  double* sg0 = sv + kTile + warp * stg;
+  double* sg1 = sg0 + lpx * kT0;
+  double* sg2 = sg1 + lpx * kT1;
+  double* sU = sg2 + lpx * kT2;
+  double* sW = sU + lpx * (kT0 * kT1);
+  __syncthreads();
+
+  for (long long e = eb + warp; e < ee; e += NW) {
+    Task tk;
+    if (!make_task(__ldg(ent + e), hot_a, hot_b, lv, s, ext, &tk)) {
+      if (lane == 0) set_err(err, 3);
+      continue;
+    }
+    const int L = tk.L, Lx = L + lext;
+    if (Lx + 1 > lpx) {
+      if (lane == 0) set_err(err, 4);
+      continue;
+    }
+    const double* tb = tab + __ldg(tab_off + tk.p);
+    const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
+    {
+      const int rows = Lx + 1;
+      const double* t0 = tb + tk.t[0];
+      const double* t1 = tb + (L + 2) * tk.n[0] + tk.t[1];
+      const double* t2 = tb + (L + 2) * (tk.n[0] + tk.n[1]) + tk.t[2];
+      const float i0f = __frcp_rn((float)m0), i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
+      for (int it = lane; it < rows * m0; it += 32) {
+        int l = fdiv(it, i0f), i = it - l * m0;
+        sg0[l * kT0 + i] = __ldg(t0 + l * tk.n[0] + i);
+      }
+      for (int it = lane; it < rows * m1; it += 32) {
+        int l = fdiv(it, i1f), i = it - l * m1;
+        sg1[l * kT1 + i] = __ldg(t1 + l * tk.n[1] + i);
+      }
+      for (int it = lane; it < rows * m2; it += 32) {
+        int l = fdiv(it, i2f), i = it - l * m2;
+        sg2[l * kT2 + i] = __ldg(t2 + l * tk.n[2] + i);
+      }
+    }
+    __syncwarp();
+    const int m01 = m0 * m1;
+    // U[l2](q)
+    {
+      const float inv01 = __frcp_rn((float)m01), inv1 = __frcp_rn((float)m1);
+      const int items = (Lx + 1) * m01;
+      const int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
+      for (int it = lane; it < items; it += 32) {
+        const int l2 = fdiv(it, inv01), q = it - l2 * m01;
+        const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
+        const double* vr = sv + ((u0 + i0) * kT1 + (u1 + i1)) * kT2 + u2;
+        const double* gr = sg2 + l2 * kT2;
+        double a = 0.0;
+        for (int i2 = 0; i2 < m2; ++i2) a = fma(vr[i2], gr[i2], a);
+        sU[l2 * (kT0 * kT1) + q] = a;
+      }
+    }
+    __syncwarp();
+    // W[c21](i0)
+    {
+      const float inv0 = __frcp_rn((float)m0);
+      const int items = nc2(Lx) * m0;
+      for (int it = lane; it < items; it += 32) {
+        const int c21 = fdiv(it, inv0), i0 = it - c21 * m0;
+        const int dc = s_dec21[Lx][c21];
+        const int l2 = dc & 255, l1 = (dc >> 8) & 255;
+        const double* ur = sU + l2 * (kT0 * kT1) + i0 * m1;
+        const double* gr = sg1 + l1 * kT1;
+        double a = 0.0;
+        for (int i1 = 0; i1 < m1; ++i1) a = fma(ur[i1], gr[i1], a);
+        sW[c21 * kT0 + i0] = a;
+      }
+    }
+    __syncwarp();
+    // V[c] -> task slot
+    {
+      const int nc = nc3(Lx);
+      double* dst = part + __ldg(part_off + tk.p) + (long long)tk.rank * nc;
+      for (int c = lane; c < nc; c += 32) {
+        const int dc = s_dec3[Lx][c];
+        const int c21 = dc & 255, l0 = dc >> 8;
+        const double* wr = sW + c21 * kT0;
+        const double* gr = sg0 + l0 * kT0;
+        double a = 0.0;
+        for (int i0 = 0; i0 < m0; ++i0) a = fma(wr[i0], gr[i0], a);
+        dst[c] = a;
+      }
+    }
+    __syncwarp();
+  }
+}
+
+// Per-pair sum of the task V tensors (fixed task order), times the level weight
+// Omega / N_k (Sec. III A).  One warp per pair.
+__global__ void reduce_parts_kernel(long long np, const KLevels K, const int4* __restrict__ hot_a,
+                                    const int4* __restrict__ hot_b, const int4* __restrict__ ids2,
+                                    const long long* __restrict__ part_off,
+                                    const long long* __restrict__ coef_off,
+                                    const double* __restrict__ part, double* __restrict__ coef,
+                                    int lext) {
+  const int lane = threadIdx.x & 31;
+  long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long sw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long p = gw; p < np; p += sw) {
+    const int Lx = hot_a[p].w + lext;
+    const int nc = nc3(Lx);
+    const int nt = ids2[p].w;
+    const double wgt = K.lv[hot_b[p].w].weight;
+    const double* src = part + part_off[p];
+    double* dst = coef + coef_off[p];
+    for (int c = lane; c < nc; c += 32) {
+      double a = 0.0;
+      for (int r = 0; r < nt; ++r) a += src[(long long)r * nc + c];
+      dst[c] = wgt * a;
+    }
+  }
+}
+
+// V assembly: one warp per contracted shell pair (sa, sb), lanes over its (mu, nu)
+// elements; each element sums over the group's pairs
+//   X_mu,nu = pref sum_k V[k] prod_d C(b_d, k_d - a_d) (A_d - B_d)^(a_d + b_d - k_d)
+// (Eq. binomial contracted with the V tensor).  A pair a < b in a diagonal shell
+// block also contributes X^T (its mirror (b, a, -T)); off-diagonal blocks are written
+// together with their transpose.
+__device__ double contract_elem(const int* ca, const int* cb, const double pw[3][4],
+                                const double* V, int L, const int (*dec21)[kNc2Max],
+                                const int (*c21b)[kLextMax + 1]) {
+  double s = 0.0;
+  for (int t2 = 0; t2 <= cb[2]; ++t2) {
+    const double c2 = binom(cb[2], t2) * pw[2][cb[2] - t2];
+    const int k2 = ca[2] + t2;
+    for (int t1 = 0; t1 <= cb[1]; ++t1) {
+      const double c21 = c2 * binom(cb[1], t1) * pw[1][cb[1] - t1];
+      const int k1 = ca[1] + t1;
+      const int base = dec21[L][c21b[L][k2] + k1] >> 16;
+      double s0 = 0.0;
+      for (int t0 = 0; t0 <= cb[0]; ++t0) s0 += binom(cb[0], t0) * pw[0][cb[0] - t0] * V[base + ca[0] + t0];
+      s += c21 * s0;
+    }
+  }
+  return s;
+}
+
+__global__ void assemble_V_kernel(long long ngroups, const int4* __restrict__ groups,
+                                  const int4* __restrict__ ids, const int4* __restrict__ ids2,
+                                  const double* __restrict__ geo, const double* __restrict__ pref,
+                                  const long long* __restrict__ coef_off,
+                                  const double* __restrict__ coef,
+                                  const CoefTables* __restrict__ tabs, int nao,
+                                  double* __restrict__ V) {
+  const int lane = threadIdx.x & 31;
+  long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= ngroups) return;
+  const int4 gr = groups[gw];
+  const int4 id0 = ids[gr.z];
+  const int la = id0.x, lb = id0.y, L = la + lb;
+  const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
+  const bool diag = gr.x == gr.y;
+  for (int el = lane; el < na * nb; el += 32) {
+    const int mu = el / nb, nu = el - mu * nb;
+    int ca[3], cb[3];
+    cart_comp(la, mu, ca);
+    cart_comp(lb, nu, cb);
+    double tot = 0.0;
+    for (int p = gr.z; p < gr.w; ++p) {
+      const double* g = geo + 8LL * p;
+      double pw[3][4];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        double ab = g[d] - g[3 + d];
+        pw[d][0] = 1.0;
+        pw[d][1] = ab;
+        pw[d][2] = ab * ab;
+        pw[d][3] = ab * ab * ab;
+      }
+      const double* Vp = coef + coef_off[p];
+      double x = contract_elem(ca, cb, pw, Vp, L, tabs->dec21, tabs->c21base);
+      if (diag && ids2[p].z == 2) {
+        int ca2[3], cb2[3];
+        cart_comp(la, nu, ca2);
+        cart_comp(lb, mu, cb2);
+        x += contract_elem(ca2, cb2, pw, Vp, L, tabs->dec21, tabs->c21base);
+      }
+      tot += pref[p] * x;
+    }
+    V[(long long)(id0.z + mu) * nao + id0.w + nu] = tot;
+    if (!diag) V[(long long)(id0.w + nu) * nao + id0.z + mu] = tot;
+  }
+}
+
+// Gradient contraction per pair (Algorithm 3): with the extended V tensor (degree
+// L + 1) of the pair,
+//   dE/dA_x += w pref sum_{mu,nu} D_mu,nu sum_k V[k] c^A_x[k0] e_y[k1] e_z[k2]
+// where c^A_x is the expansion of d/dA_x[(x-A)^a (x-B)^b exp(-a_a (x-A)^2 - ...)] /
+// exp(...) = -a (x-A)^(a-1)(x-B)^b + 2 alpha_a (x-A)^(a+1) (x-B)^b in powers of (x-A);
+// likewise for B.  Six values per pair.
+__device__ __forceinline__ void expand_1d(int i, int j, const double* pw, double* out, int kmax) {
+  // coefficients of (x-A)^k in (x-A)^i (x-B)^j, pw[t] = (A-B)^t
+  for (int k = 0; k <= kmax; ++k) out[k] = 0.0;
+  if (i < 0 || j < 0) return;
+  for (int t = 0; t <= j; ++t) out[i + t] += binom(j, t) * pw[j - t];
+}
+
+__global__ void grad_pair_kernel(long long np, const int4* __restrict__ ids,
+                                 const int4* __restrict__ ids2, const double* __restrict__ geo,
+                                 const double* __restrict__ pref,
+                                 const long long* __restrict__ coef_off,
+                                 const double* __restrict__ coef,
+                                 const CoefTables* __restrict__ tabs, const double* __restrict__ D,
+                                 int nao, double* __restrict__ pgrad) {
+  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const int4 id = ids[p];
+  const int la = id.x, lb = id.y, Lx = la + lb + 1;
+  const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
+  const double* g = geo + 8 * p;
+  const double aa = g[6], ab = g[7];
+  double pw[3][5];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double t = g[d] - g[3 + d];
+    pw[d][0] = 1.0;
+    for (int k = 1; k < 5; ++k) pw[d][k] = pw[d][k - 1] * t;
+  }
+  const double* Vp = coef + coef_off[p];
+  const double scale = (double)ids2[p].z * pref[p];
+  double out[6] = {0, 0, 0, 0, 0, 0};
+  for (int mu = 0; mu < na; ++mu) {
+    int ca[3];
+    cart_comp(la, mu, ca);
+    const double* Drow = D + (long long)(id.z + mu) * nao + id.w;
+    for (int nu = 0; nu < nb; ++nu) {
+      int cb[3];
+      cart_comp(lb, nu, cb);
+      const double dmn = scale * Drow[nu];
+      if (dmn == 0.0) continue;
+      double e[3][8];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) expand_1d(ca[d], cb[d], pw[d], e[d], 7);
+      for (int side = 0; side < 2; ++side)
+        for (int dir = 0; dir < 3; ++dir) {
+          double c[8], t1[8], t2[8];
+          if (side == 0) {
+            expand_1d(ca[dir] - 1, cb[dir], pw[dir], t1, 7);
+            expand_1d(ca[dir] + 1, cb[dir], pw[dir], t2, 7);
+            for (int k = 0; k < 8; ++k) c[k] = -(double)ca[dir] * t1[k] + 2.0 * aa * t2[k];
+          } else {
+            expand_1d(ca[dir], cb[dir] - 1, pw[dir], t1, 7);
+            expand_1d(ca[dir], cb[dir] + 1, pw[dir], t2, 7);
+            for (int k = 0; k < 8; ++k) c[k] = -(double)cb[dir] * t1[k] + 2.0 * ab * t2[k];
+          }
+          const double* c0 = dir == 0 ? c : e[0];
+          const double* c1 = dir == 1 ? c : e[1];
+          const double* c2 = dir == 2 ? c : e[2];
+          double s = 0.0;
+          for (int k2 = 0; k2 <= Lx; ++k2) {
+            if (c2[k2] == 0.0) continue;
+            for (int k1 = 0; k1 <= Lx - k2; ++k1) {
+              if (c1[k1] == 0.0) continue;
+              const int base = tabs->dec21[Lx][tabs->c21base[Lx][k2] + k1] >> 16;
+              double s0 = 0.0;
+              for (int k0 = 0; k0 <= Lx - k2 - k1; ++k0) s0 += c0[k0] * Vp[base + k0];
+              s += c2[k2] * c1[k1] * s0;
+            }
+          }
+          out[3 * side + dir] += dmn * s;
+        }
+    }
+  }
+  for (int i = 0; i < 6; ++i) pgrad[6 * p + i] = out[i];
+}
+
+__global__ void grad_atom_kernel(int natm, const long long* __restrict__ atom_off,
+                                 const int* __restrict__ atom_list,
+                                 const double* __restrict__ pgrad, double* __restrict__ grad) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * natm) return;
+  const int atom = t / 3, d = t - 3 * atom;
+  double s = 0.0;
+  for (long long i = atom_off[atom]; i < atom_off[atom + 1]; ++i) {
+    const int code = atom_list[i];
+    s += pgrad[6LL * (code >> 1) + 3 * (code & 1) + d];
+  }
+  grad[t] = s;
+}
+
+// ----------------------------------------------------------------------------------
+// Spectral steps.  |G|^2 is formed exactly as ((2 pi s)/L)^2 summed in index order,
+// without FMA contraction, so the strict sphere test |G| < G_k is the same decision as
+// the reference (Sec. II multigrid, Eq. vHG).
+__device__ __forceinline__ int signed_freq(int m, int N) { return m < (N + 1) / 2 ? m : m - N; }
+
+__device__ __forceinline__ double gsq(int s0, int s1, int s2, const double* Ld) {
+  const double tp = 6.283185307179586;  // 2 pi in double
+  double g0 = __ddiv_rn(__dmul_rn(tp, (double)s0), Ld[0]);
+  double g1 = __ddiv_rn(__dmul_rn(tp, (double)s1), Ld[1]);
+  double g2 = __ddiv_rn(__dmul_rn(tp, (double)s2), Ld[2]);
+  return __dadd_rn(__dadd_rn(__dmul_rn(g0, g0), __dmul_rn(g1, g1)), __dmul_rn(g2, g2));
+}
+
+struct Cell {
+  double L[3];
+};
+
+// Fine spectrum S(G) = sum_k [|G| < G_k] rho^_k(G) / N_k (unnormalised level DFTs):
+// Fourier interpolation of every level onto the finest grid; one C2R then gives rho.
+__global__ void combine_kernel(const KLevels K, const Cell cell,
+                               const cufftDoubleComplex* __restrict__ spec,
+                               cufftDoubleComplex* __restrict__ fspec) {
+  const LevelInfo& f = K.lv[0];
+  const int h2 = f.N[2] / 2 + 1;
+  const long long total = (long long)f.N[0] * f.N[1] * h2;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int m2 = (int)(idx % h2);
+    const long long r = idx / h2;
+    const int m1 = (int)(r % f.N[1]);
+    const int m0 = (int)(r / f.N[1]);
+    const int s0 = signed_freq(m0, f.N[0]), s1 = signed_freq(m1, f.N[1]), s2 = m2;
+    const double G2 = gsq(s0, s1, s2, cell.L);
+    double re = 0.0, im = 0.0;
+    for (int k = 0; k < K.nlev; ++k) {
+      const LevelInfo& lv = K.lv[k];
+      if (!(G2 < lv.Gk2)) continue;
+      if (2 * abs(s0) > lv.N[0] - 1 || 2 * abs(s1) > lv.N[1] - 1 || 2 * s2 > lv.N[2] - 1) continue;
+      const int i0 = s0 < 0 ? s0 + lv.N[0] : s0;
+      const int i1 = s1 < 0 ? s1 + lv.N[1] : s1;
+      const double inv = 1.0 / ((double)lv.N[0] * lv.N[1] * lv.N[2]);
+      const cufftDoubleComplex z =
+          spec[lv.spec_off + ((long long)i0 * lv.N[1] + i1) * (lv.N[2] / 2 + 1) + s2];
+      re += z.x * inv;
+      im += z.y * inv;
+    }
+    fspec[idx].x = re;
+    fspec[idx].y = im;
+  }
+}
+
+// Level spectrum from the fine spectrum: T_k(G) = [|G| < G_k] v^_fine(G) / N_fine.
+__global__ void restrict_kernel(const KLevels K, const Cell cell, int level,
+                                const cufftDoubleComplex* __restrict__ fspec,
+                                cufftDoubleComplex* __restrict__ spec) {
+  const LevelInfo& f = K.lv[0];
+  const LevelInfo& lv = K.lv[level];
+  const int h2 = lv.N[2] / 2 + 1, fh2 = f.N[2] / 2 + 1;
+  const long long total = (long long)lv.N[0] * lv.N[1] * h2;
+  const double inv = 1.0 / ((double)f.N[0] * f.N[1] * f.N[2]);
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int m2 = (int)(idx % h2);
+    const long long r = idx / h2;
+    const int m1 = (int)(r % lv.N[1]);
+    const int m0 = (int)(r / lv.N[1]);
+    const int s0 = signed_freq(m0, lv.N[0]), s1 = signed_freq(m1, lv.N[1]), s2 = m2;
+    cufftDoubleComplex out;
+    out.x = 0.0;
+    out.y = 0.0;
+    const double G2 = gsq(s0, s1, s2, cell.L);
+    if (G2 < lv.Gk2 && 2 * abs(s0) <= lv.N[0] - 1 && 2 * abs(s1) <= lv.N[1] - 1 &&
+        2 * s2 <= lv.N[2] - 1) {
+      const int i0 = s0 < 0 ? s0 + f.N[0] : s0;
+      const int i1 = s1 < 0 ? s1 + f.N[1] : s1;
+      const cufftDoubleComplex z = fspec[((long long)i0 * f.N[1] + i1) * fh2 + s2];
+      out.x = z.x * inv;
+      out.y = z.y * inv;
+    }
+    spec[lv.spec_off + idx] = out;
+  }
+}
+
+__device__ __forceinline__ double block_sum(double v, double* sh) {
+  const int tid = threadIdx.x;
+  sh[tid] = v;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (tid < s) sh[tid] += sh[tid + s];
+    __syncthreads();
+  }
+  return sh[0];
+}
+
+// Poisson in place on the fine spectrum (Eqs. vH, vHG): S <- 4 pi S / |G|^2, G = 0
+// dropped; E_H = (Omega/2) sum_G |S|^2 4 pi / |G|^2 over the full spectrum (half
+// spectrum weighted by Hermitian symmetry), block partials to red.
+__global__ void poisson_kernel(const KLevels K, const Cell cell, double omega,
+                               cufftDoubleComplex* __restrict__ fspec, double* __restrict__ red) {
+  __shared__ double sh[kRedThreads];
+  const LevelInfo& f = K.lv[0];
+  const int h2 = f.N[2] / 2 + 1;
+  const long long total = (long long)f.N[0] * f.N[1] * h2;
+  double part = 0.0;
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int m2 = (int)(idx % h2);
+    const long long r = idx / h2;
+    const int m1 = (int)(r % f.N[1]);
+    const int m0 = (int)(r / f.N[1]);
+    const int s0 = signed_freq(m0, f.N[0]), s1 = signed_freq(m1, f.N[1]);
+    const int s2 = (f.N[2] % 2 == 0 && m2 == f.N[2] / 2) ? -m2 : m2;
+    const double G2 = gsq(s0, s1, s2, cell.L);
+    cufftDoubleComplex z = fspec[idx];
+    double kern = G2 > 0.0 ? (4.0 * 3.141592653589793) / G2 : 0.0;
+    const double mult = (m2 == 0 || (f.N[2] % 2 == 0 && m2 == f.N[2] / 2)) ? 1.0 : 2.0;
+    part += mult * kern * (z.x * z.x + z.y * z.y);
+    z.x *= kern;
+    z.y *= kern;
+    fspec[idx] = z;
+  }
+  const double s = block_sum(part, sh);
+  if (threadIdx.x == 0) red[blockIdx.x] = 0.5 * omega * s;
+}
+
+// Slater exchange on the fine grid (Sec. II, LDA), summed with v_H:
+// v_out = v_H - (3/pi)^(1/3) rho+^(1/3); E_x partials (Omega/N) sum -(3/4)(3/pi)^(1/3) rho+^(4/3).
+__global__ void lda_kernel(long long n, double wgt, const double* __restrict__ rho,
+                           const double* __restrict__ vH, double* __restrict__ vout,
+                           double* __restrict__ red) {
+  __shared__ double sh[kRedThreads];
+  const double cx = 0.98474502184269641;  // (3/pi)^(1/3)
+  double part = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double r = fmax(rho[i], 0.0);
+    const double c = cbrt(r);
+    vout[i] = vH[i] - cx * c;
+    part += -0.75 * cx * r * c;
+  }
+  const double s = block_sum(part, sh);
+  if (threadIdx.x == 0) red[blockIdx.x] = wgt * s;
+}
+
+__global__ void energy_final_kernel(const double* __restrict__ red, int nparts,
+                                    double* __restrict__ out) {
+  __shared__ double sh[kRedThreads];
+  double v = 0.0;
+  for (int i = threadIdx.x; i < nparts; i += blockDim.x) v += red[i];
+  const double s = block_sum(v, sh);
+  if (threadIdx.x == 0) *out = s;
+}
+
+template <int NW>
+size_t colloc_smem(int stg) {
+  return sizeof(int) * kTabInts + sizeof(double) * (size_t)NW * (kTile + stg);
+}
+template <int NW>
+size_t integ_smem(int stg) {
+  return sizeof(int) * kTabInts + sizeof(double) * ((size_t)kTile + (size_t)NW * stg);
+}
+
+int even(int x) { return (x + 1) & ~1; }
+
+}  // namespace
+
+KLevels make_klevels(const Plan& p) {
+  KLevels k;
+  for (int i = 0; i < GPW_MAX_LEVELS; ++i) k.lv[i] = p.lev[i];
+  k.nlev = p.nlev;
+  return k;
+}
+
+cudaError_t configure_kernels(Plan* p) {
+  const int lp = p->lmax + 1;
+  p->stg_colloc = even(lp * (kT0 + kT1 + kT2) + nc3(p->lmax) + nc2(p->lmax) * kT0 + lp * kT0 * kT1);
+  for (int lext = 0; lext <= 1; ++lext) {
+    const int lpx = p->lmax + lext + 1;
+    int stg = even(lpx * (kT0 + kT1 + kT2) + lpx * kT0 * kT1 + nc2(p->lmax + lext) * kT0);
+    if (lext == 0) p->stg_integ = stg; else p->stg_integ1 = stg;
+  }
+  p->nw_colloc = 8;
+  p->nw_integ = 8;
+  p->smem_colloc = colloc_smem<8>(p->stg_colloc);
+  p->smem_integ = integ_smem<8>(p->stg_integ);
+  p->smem_integ1 = integ_smem<8>(p->stg_integ1);
+  // the attribute is per function and shared by all plans: raise it to the device
+  // maximum once, the launch itself asks for what this plan needs
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  if ((size_t)optin < std::max(p->smem_colloc, std::max(p->smem_integ, p->smem_integ1)))
+    return cudaErrorInvalidValue;
+  e = cudaFuncSetAttribute(collocate_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  if (e != cudaSuccess) return e;
+  e = cudaFuncSetAttribute(integrate_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+  return e;
+}
+
+cudaError_t launch_tables(const Plan& p, cudaStream_t s) {
+  if (p.npairs == 0) return cudaSuccess;
+  long long blocks = std::min<long long>((p.npairs + 7) / 8, 152LL * 64);
+  tables_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, make_klevels(p), p.d.hot_a, p.d.hot_b,
+                                             p.d.geo, p.d.cab, p.d.tab_off, p.d.tab, p.d.pref);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s) {
+  if (p.npairs == 0) return cudaSuccess;
+  pair_coef_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
+      p.npairs, p.d.hot_a, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, p.d.tabs, D,
+      p.nao, p.d.coef);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_collocate(const Plan& p, cudaStream_t s) {
+  if (p.nwork == 0) return cudaSuccess;
+  collocate_kernel<8><<<(int)p.nwork, 8 * 32, p.smem_colloc, s>>>(
+      make_klevels(p), p.d.work, p.d.sub_off, p.d.ent, p.d.hot_a, p.d.hot_b, p.d.tab_off,
+      p.d.coef_off, p.d.tab, p.d.coef, p.d.tabs, p.d.grids, p.lmax + 1, p.stg_colloc, p.d.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s) {
+  if (p.nwork == 0) return cudaSuccess;
+  integrate_kernel<8><<<(int)p.nwork, 8 * 32, lext ? p.smem_integ1 : p.smem_integ, s>>>(
+      make_klevels(p), p.d.work, p.d.sub_off, p.d.ent, p.d.hot_a, p.d.hot_b, p.d.tab_off,
+      p.d.part_off, p.d.tab, p.d.tabs, p.d.grids, p.d.part, lext, p.lmax + lext + 1,
+      lext ? p.stg_integ1 : p.stg_integ, p.d.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s) {
+  if (p.npairs == 0) return cudaSuccess;
+  long long blocks = std::min<long long>((p.npairs + 7) / 8, 152LL * 64);
+  reduce_parts_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, make_klevels(p), p.d.hot_a, p.d.hot_b,
+                                                  p.d.ids2, p.d.part_off, p.d.coef_off, p.d.part,
+                                                  p.d.coef, lext);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_V(const Plan& p, double* V, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(V, 0, sizeof(double) * (size_t)p.nao * p.nao, s);
+  if (e != cudaSuccess || p.ngroups == 0) return e;
+  assemble_V_kernel<<<(int)((p.ngroups + 7) / 8), 256, 0, s>>>(
+      p.ngroups, p.d.groups, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, p.d.coef,
+      p.d.tabs, p.nao, V);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad(const Plan& p, const double* D, double* grad, cudaStream_t s) {
+  if (p.npairs > 0) {
+    grad_pair_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
+        p.npairs, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, p.d.coef, p.d.tabs, D,
+        p.nao, p.d.pgrad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  grad_atom_kernel<<<(3 * p.natm + 127) / 128, 128, 0, s>>>(p.natm, p.d.atom_off, p.d.atom_list,
+                                                            p.d.pgrad, grad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_combine(const Plan& p, cudaStream_t s) {
+  Cell c{{p.L[0], p.L[1], p.L[2]}};
+  combine_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p), c, p.d.spec, p.d.fspec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_restrict(const Plan& p, int level, cudaStream_t s) {
+  Cell c{{p.L[0], p.L[1], p.L[2]}};
+  restrict_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p), c, level, p.d.fspec, p.d.spec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_poisson(const Plan& p, cudaStream_t s) {
+  Cell c{{p.L[0], p.L[1], p.L[2]}};
+  poisson_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(make_klevels(p), c, p.omega, p.d.fspec, p.d.red);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lda(const Plan& p, const double* rho, const double* vH, double* v_out,
+                       cudaStream_t s) {
+  lda_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(p.fine_n, p.omega / (double)p.fine_n, rho, vH, v_out,
+                                                p.d.red + kRedBlocks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_energy_final(const Plan& p, int slot, int nparts, cudaStream_t s) {
+  energy_final_kernel<<<1, kRedThreads, 0, s>>>(p.d.red + slot * kRedBlocks, nparts,
+                                                p.d.energies + slot);
+  return cudaGetLastError();
+}
+
+}  // namespace gpw

@@ -1,0 +1,33 @@
+// Launch wrappers of the libgpw CUDA kernels (sm_103a).  Not part of the C ABI.
+#pragma once
+
+#include "gpw_internal.h"
+
+namespace gpw {
+
+struct KLevels {
+  LevelInfo lv[GPW_MAX_LEVELS];
+  int nlev;
+};
+
+KLevels make_klevels(const Plan& p);
+
+cudaError_t launch_tables(const Plan& p, cudaStream_t s);
+cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s);
+cudaError_t launch_collocate(const Plan& p, cudaStream_t s);
+cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s);
+cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s);
+cudaError_t launch_assemble_V(const Plan& p, double* V, cudaStream_t s);
+cudaError_t launch_grad(const Plan& p, const double* D, double* grad, cudaStream_t s);
+cudaError_t launch_combine(const Plan& p, cudaStream_t s);
+cudaError_t launch_restrict(const Plan& p, int level, cudaStream_t s);
+cudaError_t launch_poisson(const Plan& p, cudaStream_t s);
+cudaError_t launch_lda(const Plan& p, const double* rho, const double* vH, double* v_out,
+                       cudaStream_t s);
+cudaError_t launch_energy_final(const Plan& p, int slot, int nparts, cudaStream_t s);
+cudaError_t configure_kernels(Plan* p);
+
+constexpr int kRedBlocks = 304;
+constexpr int kRedThreads = 256;
+
+}  // namespace gpw

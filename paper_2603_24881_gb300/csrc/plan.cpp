@@ -1,0 +1,549 @@
+// Host part of gpw_plan: primitive normalisation, shell cutoff radii (Eq. cut), pair
+// screening over lattice images (Sec. III A), multigrid level assignment (Sec. II),
+// integer pair boxes and the per-level sub-box task lists that the collocation and
+// integration kernels walk.  Compiled with -ffp-contract=off: every screening decision
+// is an exact function of the inputs.
+#include <algorithm>
+#include <cmath>
+#include <cstdint>
+#include <cstring>
+#include <numeric>
+#include <string>
+#include <vector>
+
+#include "gpw_internal.h"
+#include "plan_host.h"
+
+namespace gpw {
+
+namespace {
+
+double ipow(double x, int n) {
+  double p = 1.0;
+  for (int k = 0; k < n; ++k) p *= x;
+  return p;
+}
+
+double dfact(int n) {
+  double r = 1.0;
+  while (n > 1) {
+    r *= n;
+    n -= 2;
+  }
+  return r;
+}
+
+// N_l(alpha): unit self-overlap of the x^l component of a primitive Cartesian Gaussian.
+double prim_norm(int l, double alpha) {
+  double ip = 1.0;
+  for (int k = 0; k < l; ++k) ip *= 4.0 * alpha;
+  return std::sqrt(std::pow(2.0 * alpha / M_PI, 1.5) * ip / dfact(2 * l - 1));
+}
+
+// Eq. (cut) for one primitive: f(r) = |c N| r^(l+2) exp(-alpha r^2); r_cut is the largest
+// root of f = tau on the decreasing branch (64 bisection steps); -1 drops the primitive.
+double prim_f(double cn, int l, double alpha, double r) {
+  return cn * ipow(r, l + 2) * std::exp(-alpha * r * r);
+}
+
+double prim_rcut(double cn, int l, double alpha, double tau) {
+  double r0 = std::sqrt((double)(l + 2) / (2.0 * alpha));
+  if (prim_f(cn, l, alpha, r0) < tau) return -1.0;
+  double hi = r0;
+  for (int it = 0; it < 200 && prim_f(cn, l, alpha, hi) >= tau; ++it) hi *= 2.0;
+  double lo = r0;
+  for (int it = 0; it < 64; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (prim_f(cn, l, alpha, mid) >= tau) lo = mid; else hi = mid;
+  }
+  return hi;
+}
+
+// Eq. (cut) for the product Gaussian of Eq. (gab): magnitude bound at distance r from P,
+// h(r) = |c_a N_a c_b N_b| K_ab (r + |P-A|)^la (r + |P-B|)^lb r^2 exp(-alpha_p r^2).
+double pair_h(double cab, double kab, int la, int lb, double dA, double dB, double ap,
+              double r) {
+  return cab * kab * ipow(r + dA, la) * ipow(r + dB, lb) * r * r * std::exp(-ap * r * r);
+}
+
+double pair_extent(double cab, double kab, int la, int lb, double dA, double dB, double ap,
+                   double tau) {
+  double r0 = std::sqrt((double)(la + lb + 2) / (2.0 * ap));
+  if (pair_h(cab, kab, la, lb, dA, dB, ap, r0) < tau) return -1.0;
+  double hi = r0;
+  for (int it = 0; it < 200 && pair_h(cab, kab, la, lb, dA, dB, ap, hi) >= tau; ++it) hi *= 2.0;
+  double lo = r0;
+  for (int it = 0; it < 64; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (pair_h(cab, kab, la, lb, dA, dB, ap, mid) >= tau) lo = mid; else hi = mid;
+  }
+  return hi;
+}
+
+bool smooth7(int m) {
+  for (int f : {2, 3, 5, 7})
+    while (m % f == 0) m /= f;
+  return m == 1;
+}
+
+int smooth7_even_at_least(int n) {
+  int m = std::max(2, n);
+  while (!(m % 2 == 0 && smooth7(m))) ++m;
+  return m;
+}
+
+long long floordiv(long long a, long long b) {
+  long long q = a / b;
+  if ((a % b != 0) && ((a < 0) != (b < 0))) --q;
+  return q;
+}
+
+struct Prim {
+  int atom, l, shell;
+  long long ao;
+  double alpha, cn, rcut;
+};
+
+struct PairTmp {
+  int a, b, sa, sb;
+  int img[3];
+  int level;
+  int lo[3], hi[3];
+};
+
+struct Seg {
+  int k, j;
+};
+
+void segments(int lo, int hi, int N, int T, std::vector<Seg>* out) {
+  out->clear();
+  long long i = lo;
+  while (i <= hi) {
+    long long k = floordiv(i, N);
+    long long ip = i - k * N;
+    long long j = ip / T;
+    long long end = k * N + std::min<long long>((j + 1) * T, N) - 1;
+    out->push_back({(int)k, (int)j});
+    i = std::min<long long>(hi, end) + 1;
+  }
+}
+
+}  // namespace
+
+int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
+  if (!desc || !plan || !H) {
+    set_error("gpw_plan: NULL argument");
+    return GPW_EINVAL;
+  }
+  const double* lat = desc->lattice;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      if (i != j && lat[3 * i + j] != 0.0) {
+        set_error("gpw_plan: only orthorhombic (diagonal) lattices are supported");
+        return GPW_EINVAL;
+      }
+  for (int d = 0; d < 3; ++d) {
+    plan->L[d] = lat[4 * d];
+    if (!(plan->L[d] > 0)) {
+      set_error("gpw_plan: lattice lengths must be positive");
+      return GPW_EINVAL;
+    }
+  }
+  plan->omega = plan->L[0] * plan->L[1] * plan->L[2];
+  if (desc->nlevels < 1 || desc->nlevels > GPW_MAX_LEVELS) {
+    set_error("gpw_plan: nlevels must be in 1..GPW_MAX_LEVELS");
+    return GPW_EINVAL;
+  }
+  if (desc->natm < 1 || desc->nshell < 1 || !desc->coords || !desc->shell_atom ||
+      !desc->shell_l || !desc->shell_nprim || !desc->shell_prim_off || !desc->exponents ||
+      !desc->coeffs) {
+    set_error("gpw_plan: empty or missing basis/atoms");
+    return GPW_EINVAL;
+  }
+  if (!(desc->tau > 0)) {
+    set_error("gpw_plan: tau must be positive");
+    return GPW_EINVAL;
+  }
+  const int K = desc->nlevels;
+  plan->nlev = K;
+  plan->natm = desc->natm;
+  plan->nshell = desc->nshell;
+  plan->coords.assign(desc->coords, desc->coords + 3 * desc->natm);
+  const double rel = desc->rel_cutoff > 0 ? desc->rel_cutoff : 40.0;
+
+  // ---- multigrid levels (Sec. II): cutoffs E_k and meshes
+  int mesh[GPW_MAX_LEVELS][3];
+  for (int k = 0; k < K; ++k) {
+    if (desc->meshes) {
+      double G = 1e300;
+      for (int d = 0; d < 3; ++d) {
+        mesh[k][d] = desc->meshes[3 * k + d];
+        if (mesh[k][d] < 2) {
+          set_error("gpw_plan: explicit meshes must be >= 2");
+          return GPW_EINVAL;
+        }
+        G = std::min(G, 2.0 * M_PI * (double)((mesh[k][d] - 1) / 2) / plan->L[d]);
+      }
+      plan->E[k] = 0.5 * G * G;
+    } else {
+      if (!(desc->cutoff_ha > 0) || !(desc->level_ratio > 1.0)) {
+        set_error("gpw_plan: cutoff_ha > 0 and level_ratio > 1 required without meshes");
+        return GPW_EINVAL;
+      }
+      double div = 1.0;
+      for (int i = 0; i < k; ++i) div *= desc->level_ratio;
+      plan->E[k] = desc->cutoff_ha / div;
+      double G = std::sqrt(2.0 * plan->E[k]);
+      for (int d = 0; d < 3; ++d)
+        mesh[k][d] = smooth7_even_at_least(2 * (int)std::ceil(G * plan->L[d] / (2.0 * M_PI)) + 1);
+    }
+  }
+  for (int k = 0; k < K; ++k) {
+    LevelInfo& lv = plan->lev[k];
+    double G = std::sqrt(2.0 * plan->E[k]);
+    lv.Gk2 = G * G;
+    for (int d = 0; d < 3; ++d) {
+      lv.N[d] = mesh[k][d];
+      lv.h[d] = plan->L[d] / lv.N[d];
+      // the strict sphere |G| < G_k must stay inside |m_d| <= (N_d - 1)/2 on its level
+      // and on the finest level, so the field stays real and no Nyquist plane is used
+      if (!(G * plan->L[d] / (2.0 * M_PI) <= (double)((lv.N[d] - 1) / 2)) ||
+          mesh[k][d] > mesh[0][d]) {
+        set_error("gpw_plan: level mesh too small for its cutoff sphere");
+        return GPW_EINVAL;
+      }
+    }
+    const int T[3] = {kT0, kT1, kT2};
+    for (int d = 0; d < 3; ++d) lv.nsb[d] = (lv.N[d] + T[d] - 1) / T[d];
+    lv.weight = plan->omega / ((double)lv.N[0] * lv.N[1] * lv.N[2]);
+  }
+  for (int k = 1; k < K; ++k)
+    if (plan->E[k] > plan->E[k - 1]) {
+      set_error("gpw_plan: level cutoffs must decrease from level 0");
+      return GPW_EINVAL;
+    }
+
+  // ---- primitives
+  std::vector<Prim> prims;
+  std::vector<long long> ao_off(desc->nshell + 1, 0);
+  for (int s = 0; s < desc->nshell; ++s) {
+    int l = desc->shell_l[s];
+    if (l < 0 || l > kShellLmax) {
+      set_error("gpw_plan: shell angular momentum must be 0..3");
+      return GPW_EINVAL;
+    }
+    int a = desc->shell_atom[s];
+    if (a < 0 || a >= desc->natm) {
+      set_error("gpw_plan: shell_atom out of range");
+      return GPW_EINVAL;
+    }
+    ao_off[s + 1] = ao_off[s] + (l + 1) * (l + 2) / 2;
+    for (int k = 0; k < desc->shell_nprim[s]; ++k) {
+      double alpha = desc->exponents[desc->shell_prim_off[s] + k];
+      double c = desc->coeffs[desc->shell_prim_off[s] + k];
+      if (!(alpha > 0)) {
+        set_error("gpw_plan: exponents must be positive");
+        return GPW_EINVAL;
+      }
+      Prim p;
+      p.atom = a;
+      p.l = l;
+      p.shell = s;
+      p.ao = ao_off[s];
+      p.alpha = alpha;
+      p.cn = c * prim_norm(l, alpha);
+      p.rcut = prim_rcut(std::fabs(p.cn), l, alpha, desc->tau);
+      prims.push_back(p);
+    }
+  }
+  plan->nao = (int)ao_off[desc->nshell];
+  plan->nprim = (int)prims.size();
+  plan->prim_atom.resize(prims.size());
+  plan->prim_alpha.resize(prims.size());
+  for (size_t i = 0; i < prims.size(); ++i) {
+    plan->prim_atom[i] = prims[i].atom;
+    plan->prim_alpha[i] = prims[i].alpha;
+  }
+
+  // ---- pair screening over images (Sec. III A, Eq. cut)
+  const int natm = desc->natm;
+  std::vector<std::vector<int>> atom_prims(natm);
+  std::vector<double> atom_rmax(natm, -1.0);
+  for (int i = 0; i < (int)prims.size(); ++i) {
+    if (prims[i].rcut < 0) continue;
+    atom_prims[prims[i].atom].push_back(i);
+    atom_rmax[prims[i].atom] = std::max(atom_rmax[prims[i].atom], prims[i].rcut);
+  }
+  const double* X = desc->coords;
+  std::vector<PairTmp> pairs;
+  for (int ia = 0; ia < natm; ++ia) {
+    if (atom_rmax[ia] < 0) continue;
+    for (int ib = 0; ib < natm; ++ib) {
+      if (atom_rmax[ib] < 0) continue;
+      double rsum_max = atom_rmax[ia] + atom_rmax[ib];
+      int nlo[3], nhi[3];
+      for (int d = 0; d < 3; ++d) {
+        double dd = X[3 * ia + d] - X[3 * ib + d];
+        // one more image on each side than the atom-level bound: the exact
+        // per-primitive distance test below decides
+        nlo[d] = (int)std::floor((dd - rsum_max) / plan->L[d]) - 1;
+        nhi[d] = (int)std::ceil((dd + rsum_max) / plan->L[d]) + 1;
+      }
+      for (int n0 = nlo[0]; n0 <= nhi[0]; ++n0)
+        for (int n1 = nlo[1]; n1 <= nhi[1]; ++n1)
+          for (int n2 = nlo[2]; n2 <= nhi[2]; ++n2) {
+            const int nn[3] = {n0, n1, n2};
+            double Bt[3], AB2 = 0.0;
+            for (int d = 0; d < 3; ++d) {
+              Bt[d] = X[3 * ib + d] + (double)nn[d] * plan->L[d];
+              double t = X[3 * ia + d] - Bt[d];
+              AB2 += t * t;
+            }
+            if (std::sqrt(AB2) >= rsum_max + 1e-9 * (1.0 + rsum_max)) continue;
+            for (int a : atom_prims[ia])
+              for (int b : atom_prims[ib]) {
+                if (a > b) continue;
+                const Prim& pa = prims[a];
+                const Prim& pb = prims[b];
+                double rsum = pa.rcut + pb.rcut;
+                if (!(std::sqrt(AB2) < rsum)) continue;
+                double aa = pa.alpha, ab = pb.alpha, ap = aa + ab;
+                double P[3], dA2 = 0.0, dB2 = 0.0;
+                for (int d = 0; d < 3; ++d) {
+                  P[d] = (aa * X[3 * ia + d] + ab * Bt[d]) / ap;
+                  double ta = P[d] - X[3 * ia + d], tb = P[d] - Bt[d];
+                  dA2 += ta * ta;
+                  dB2 += tb * tb;
+                }
+                double kab = std::exp(-aa * ab * AB2 / ap);
+                double cab = std::fabs(pa.cn * pb.cn);
+                double R = pair_extent(cab, kab, pa.l, pb.l, std::sqrt(dA2), std::sqrt(dB2), ap,
+                                       desc->tau);
+                if (R < 0) continue;
+                int level = 0;
+                for (int k = K - 1; k >= 0; --k)
+                  if (plan->E[k] >= rel * ap) {
+                    level = k;
+                    break;
+                  }
+                PairTmp t;
+                t.a = a;
+                t.b = b;
+                t.sa = pa.shell;
+                t.sb = pb.shell;
+                t.level = level;
+                for (int d = 0; d < 3; ++d) {
+                  t.img[d] = nn[d];
+                  double Nd = (double)mesh[level][d];
+                  t.lo[d] = (int)std::ceil((P[d] - R) * Nd / plan->L[d]);
+                  t.hi[d] = (int)std::floor((P[d] + R) * Nd / plan->L[d]);
+                }
+                if (t.hi[0] < t.lo[0] || t.hi[1] < t.lo[1] || t.hi[2] < t.lo[2]) continue;
+                pairs.push_back(t);
+              }
+          }
+    }
+  }
+  // deterministic order: contracted shell pair, then primitives, then image
+  std::sort(pairs.begin(), pairs.end(), [](const PairTmp& x, const PairTmp& y) {
+    if (x.sa != y.sa) return x.sa < y.sa;
+    if (x.sb != y.sb) return x.sb < y.sb;
+    if (x.a != y.a) return x.a < y.a;
+    if (x.b != y.b) return x.b < y.b;
+    for (int d = 0; d < 3; ++d)
+      if (x.img[d] != y.img[d]) return x.img[d] < y.img[d];
+    return false;
+  });
+  const long long np = (long long)pairs.size();
+  plan->npairs = np;
+  if (np > (1LL << 31) - 1) {
+    set_error("gpw_plan: too many pairs");
+    return GPW_ERANGE;
+  }
+
+  // ---- per-pair arrays
+  H->hot_a.resize(np);
+  H->hot_b.resize(np);
+  H->ids.resize(np);
+  H->ids2.resize(np);
+  H->geo.resize(8 * np);
+  H->cab.resize(np);
+  H->tab_off.resize(np);
+  H->coef_off.resize(np);
+  H->part_off.resize(np);
+  plan->h_ab.resize(2 * np);
+  plan->h_img.resize(3 * np);
+  plan->h_lev.resize(np);
+  plan->h_lo.resize(3 * np);
+  plan->h_hi.resize(3 * np);
+  plan->pair_a.resize(np);
+  plan->pair_b.resize(np);
+  long long tab_total = 0, coef_total = 0;
+  int lmax = 0;
+  for (long long p = 0; p < np; ++p) {
+    const PairTmp& t = pairs[p];
+    const Prim& pa = prims[t.a];
+    const Prim& pb = prims[t.b];
+    int L = pa.l + pb.l;
+    lmax = std::max(lmax, L);
+    int n[3];
+    for (int d = 0; d < 3; ++d) n[d] = t.hi[d] - t.lo[d] + 1;
+    H->hot_a[p] = make_int4(t.lo[0], t.lo[1], t.lo[2], L);
+    H->hot_b[p] = make_int4(n[0], n[1], n[2], t.level);
+    H->ids[p] = make_int4(pa.l, pb.l, (int)pa.ao, (int)pb.ao);
+    H->ids2[p] = make_int4(pa.atom, pb.atom, t.a < t.b ? 2 : 1, 0);
+    for (int d = 0; d < 3; ++d) {
+      H->geo[8 * p + d] = X[3 * pa.atom + d];
+      H->geo[8 * p + 3 + d] = X[3 * pb.atom + d] + (double)t.img[d] * plan->L[d];
+    }
+    H->geo[8 * p + 6] = pa.alpha;
+    H->geo[8 * p + 7] = pb.alpha;
+    H->cab[p] = pa.cn * pb.cn;
+    H->tab_off[p] = tab_total;
+    tab_total += (long long)(L + 2) * (n[0] + n[1] + n[2]);
+    H->coef_off[p] = coef_total;
+    coef_total += nc3(L + 1);
+    long long pts = (long long)n[0] * n[1] * n[2];
+    plan->pair_points += pts;
+    plan->pair_points_level[t.level] += pts;
+    plan->pair_points_L[L] += pts;
+    plan->npairs_level[t.level] += 1;
+    plan->flops_rho += 2.0 * (L + 1) * (double)pts;
+    plan->flops_mat += 2.0 * (L + 1) * (double)pts;
+    plan->flops_ip1 += 2.0 * (L + 2) * (double)pts;
+    plan->h_ab[2 * p] = t.a;
+    plan->h_ab[2 * p + 1] = t.b;
+    plan->pair_a[p] = t.a;
+    plan->pair_b[p] = t.b;
+    for (int d = 0; d < 3; ++d) {
+      plan->h_img[3 * p + d] = t.img[d];
+      plan->h_lo[3 * p + d] = t.lo[d];
+      plan->h_hi[3 * p + d] = t.hi[d];
+    }
+    plan->h_lev[p] = t.level;
+  }
+  plan->lmax = lmax;
+  plan->tab_total = tab_total;
+  plan->coef_total = coef_total;
+
+  // ---- per-level sub-box task lists (CSR), one task per (pair, sub-box, image shift)
+  long long nsub = 0;
+  for (int k = 0; k < K; ++k) {
+    plan->lev[k].sub_base = nsub;
+    nsub += (long long)plan->lev[k].nsb[0] * plan->lev[k].nsb[1] * plan->lev[k].nsb[2];
+  }
+  plan->nsub_total = nsub;
+  std::vector<long long> count(nsub + 1, 0);
+  const int T[3] = {kT0, kT1, kT2};
+  std::vector<Seg> sg[3];
+  for (long long p = 0; p < np; ++p) {
+    const PairTmp& t = pairs[p];
+    const LevelInfo& lv = plan->lev[t.level];
+    for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
+    for (auto& s0 : sg[0])
+      for (auto& s1 : sg[1])
+        for (auto& s2 : sg[2])
+          count[lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j + 1]++;
+  }
+  for (long long i = 0; i < nsub; ++i) count[i + 1] += count[i];
+  const long long nent = count[nsub];
+  plan->nent = nent;
+  H->sub_off = count;
+  H->ent.resize(nent);
+  std::vector<long long> fill(count.begin(), count.end() - 1);
+  long long part_total = 0;
+  for (long long p = 0; p < np; ++p) {
+    const PairTmp& t = pairs[p];
+    const LevelInfo& lv = plan->lev[t.level];
+    for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
+    int rank = 0;
+    for (auto& s0 : sg[0])
+      for (auto& s1 : sg[1])
+        for (auto& s2 : sg[2]) {
+          if (s0.k < -512 || s0.k > 511 || s1.k < -512 || s1.k > 511 || s2.k < -512 || s2.k > 511) {
+            set_error("gpw_plan: pair box wraps the cell more than 511 times");
+            return GPW_ERANGE;
+          }
+          int kpack = (s0.k + 512) | ((s1.k + 512) << 10) | ((s2.k + 512) << 20);
+          long long sub = lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j;
+          H->ent[fill[sub]++] = make_int4((int)p, kpack, rank, 0);
+          ++rank;
+        }
+    H->ids2[p].w = rank;
+    int L = H->hot_a[p].w;
+    H->part_off[p] = part_total;
+    part_total += (long long)rank * nc3(L + 1);
+  }
+  plan->part_total = part_total;
+
+  // ---- work list: sub-boxes with tasks, heaviest first (then level, then index)
+  std::vector<std::pair<long long, long long>> w;  // (-count, global sub)
+  for (long long s = 0; s < nsub; ++s) {
+    long long c = H->sub_off[s + 1] - H->sub_off[s];
+    if (c > 0) w.push_back({-c, s});
+  }
+  std::sort(w.begin(), w.end());
+  H->work.resize(w.size());
+  for (size_t i = 0; i < w.size(); ++i) {
+    long long s = w[i].second;
+    int k = 0;
+    while (k + 1 < K && plan->lev[k + 1].sub_base <= s) ++k;
+    H->work[i] = make_int2(k, (int)(s - plan->lev[k].sub_base));
+  }
+  plan->nwork = (long long)w.size();
+
+  // ---- V assembly groups: runs of pairs with the same contracted shell pair
+  for (long long p = 0; p < np;) {
+    long long q = p;
+    while (q < np && pairs[q].sa == pairs[p].sa && pairs[q].sb == pairs[p].sb) ++q;
+    H->groups.push_back(make_int4(pairs[p].sa, pairs[p].sb, (int)p, (int)q));
+    p = q;
+  }
+  plan->ngroups = (long long)H->groups.size();
+
+  // ---- gradient assembly: per atom, the (pair, side) contributions in pair order
+  std::vector<long long> acount(natm + 1, 0);
+  for (long long p = 0; p < np; ++p) {
+    acount[prims[pairs[p].a].atom + 1]++;
+    acount[prims[pairs[p].b].atom + 1]++;
+  }
+  for (int i = 0; i < natm; ++i) acount[i + 1] += acount[i];
+  H->atom_off = acount;
+  H->atom_list.resize(2 * np);
+  std::vector<long long> afill(acount.begin(), acount.end() - 1);
+  for (long long p = 0; p < np; ++p) {
+    H->atom_list[afill[prims[pairs[p].a].atom]++] = (int)(2 * p);
+    H->atom_list[afill[prims[pairs[p].b].atom]++] = (int)(2 * p + 1);
+  }
+
+  // ---- spectral sizes
+  plan->grid_total = 0;
+  plan->spec_total = 0;
+  for (int k = 0; k < K; ++k) {
+    LevelInfo& lv = plan->lev[k];
+    lv.grid_off = plan->grid_total;
+    lv.spec_off = plan->spec_total;
+    plan->grid_total += (long long)lv.N[0] * lv.N[1] * lv.N[2];
+    plan->spec_total += (long long)lv.N[0] * lv.N[1] * (lv.N[2] / 2 + 1);
+  }
+  plan->fine_n = (long long)plan->lev[0].N[0] * plan->lev[0].N[1] * plan->lev[0].N[2];
+  plan->fine_spec_n = (long long)plan->lev[0].N[0] * plan->lev[0].N[1] * (plan->lev[0].N[2] / 2 + 1);
+  return GPW_OK;
+}
+
+void build_coef_tables(CoefTables* t) {
+  std::memset(t, 0, sizeof(*t));
+  for (int L = 0; L <= kLextMax; ++L) {
+    int c21 = 0, flat = 0;
+    for (int l2 = 0; l2 <= L; ++l2) {
+      t->c21base[L][l2] = c21;
+      for (int l1 = 0; l1 <= L - l2; ++l1) {
+        t->dec21[L][c21] = l2 | (l1 << 8) | (flat << 16);
+        for (int l0 = 0; l0 <= L - l2 - l1; ++l0) t->dec3[L][flat++] = c21 | (l0 << 8);
+        ++c21;
+      }
+    }
+  }
+}
+
+}  // namespace gpw

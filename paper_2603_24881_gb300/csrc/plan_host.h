@@ -1,0 +1,22 @@
+// Host staging arrays produced by build_host_plan and uploaded by gpw_plan.
+#pragma once
+
+#include <vector>
+
+#include "gpw_internal.h"
+
+namespace gpw {
+
+struct HostArrays {
+  std::vector<int4> hot_a, hot_b, ids, ids2;
+  std::vector<double> geo, cab;
+  std::vector<long long> tab_off, coef_off, part_off;
+  std::vector<int4> ent;
+  std::vector<long long> sub_off;
+  std::vector<int2> work;
+  std::vector<int4> groups;
+  std::vector<long long> atom_off;
+  std::vector<int> atom_list;
+};
+
+}  // namespace gpw

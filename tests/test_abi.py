@@ -1,0 +1,40 @@
+"""The C-ABI library loads and exports every entry point that include/gpw.h
+declares (no compute calls: this runs without a GPU)."""
+import ctypes
+import os
+import re
+
+import paper_2603_24881_gb300 as gpw
+from paper_2603_24881_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"^\s*(?:int|void|const char\*)\s+(gpw_\w+)\s*\(", src, flags=re.M)
+    return names
+
+
+def test_header_declares_the_path():
+    names = _declared()
+    for n in ["gpw_plan", "gpw_eval_rho", "gpw_eval_mat", "gpw_eval_mat_ip1", "gpw_fock"]:
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = ctypes.CDLL(gpw.lib_path())
+    for n in _declared():
+        assert hasattr(lib, n), n
+    assert set(binding.EXPORTS) <= set(_declared())
+
+
+def test_strerror_without_gpu():
+    lib = gpw.load()
+    assert lib.gpw_strerror(0) == b"ok"
+    assert lib.gpw_strerror(-1) == b"invalid argument"
+    assert lib.gpw_strerror(-7) == b"size beyond a fixed limit"

@@ -1,0 +1,205 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Tolerances (stated in the north-star of this path): 1e-10 relative (max-norm over
+the array) for rho and V, 1e-8 Ha for energies, 1e-7 Ha/Bohr for gradients.
+Integer plan data (pair sets, images, levels, boxes) must match exactly.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+import systems
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+def _rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+@pytest.fixture(scope="module")
+def gpw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2603_24881_gb300 as g
+    g.load()
+    return g
+
+
+def _cases():
+    return {
+        "tiny": workloads.tiny(),
+        "tiny14": systems.tiny14(),
+        "resolved": systems.resolved(),
+        "water4": workloads.config("water4"),
+    }
+
+
+@pytest.fixture(scope="module")
+def cases():
+    out = {}
+    for k, s in _cases().items():
+        out[k] = (s, oracle.Plan(s))
+    return out
+
+
+@pytest.mark.parametrize("name", ["tiny", "tiny14", "resolved", "water4"])
+def test_plan_pairs_identical(gpw, cases, name):
+    s, op = cases[name]
+    gp = gpw.Plan(s)
+    a = gp.pair_table()
+    b = op.pair_table()
+    assert a.shape == b.shape
+    assert np.array_equal(a, b)
+    st = gp.stats()
+    assert st["pair_points"] == op.pair_points()
+    assert [tuple(m) for m in op.meshes.tolist()] == [tuple(m) for m in st["meshes"]]
+
+
+@pytest.mark.parametrize("name", ["tiny", "tiny14", "resolved", "water4"])
+def test_rho_levels(gpw, cases, name):
+    s, op = cases[name]
+    gp = gpw.Plan(s)
+    got = [x.cpu().numpy() for x in gp.eval_rho_levels(s.D)]
+    ref = op.rho_levels(s.D)
+    scale = max(np.max(np.abs(r)) for r in ref)
+    for k, (x, y) in enumerate(zip(got, ref)):
+        assert np.max(np.abs(x - y)) <= RTOL * scale, (name, k)
+    assert gp.check_device() == 0
+
+
+@pytest.mark.parametrize("name", ["tiny", "resolved", "water4"])
+def test_rho_fine(gpw, cases, name):
+    s, op = cases[name]
+    gp = gpw.Plan(s)
+    got = gp.eval_rho(s.D).cpu().numpy()
+    ref = op.combine(op.rho_levels(s.D))
+    assert _rel(got, ref) <= RTOL
+
+
+@pytest.mark.parametrize("name", ["tiny", "resolved", "water4"])
+def test_mat_plane_waves(gpw, cases, name):
+    s, op = cases[name]
+    gp = gpw.Plan(s)
+    vf = s.potential.sample(op.meshes[0])
+    got = gp.eval_mat(vf).cpu().numpy()
+    ref = op.mat_levels(op.restrict(vf))
+    assert _rel(got, ref) <= RTOL
+    assert np.max(np.abs(got - got.T)) <= 1e-12 * np.max(np.abs(got))
+
+
+@pytest.mark.parametrize("name", ["tiny", "resolved"])
+def test_mat_levels_random(gpw, cases, name):
+    s, op = cases[name]
+    gp = gpw.Plan(s)
+    rng = np.random.default_rng(5)
+    vl = [rng.standard_normal(tuple(m)) for m in op.meshes]
+    got = gp.eval_mat_levels(vl).cpu().numpy()
+    ref = op.mat_levels(vl)
+    assert _rel(got, ref) <= RTOL
+
+
+@pytest.mark.parametrize("name", ["tiny", "resolved", "water4"])
+def test_fock(gpw, cases, name):
+    s, op = cases[name]
+    gp = gpw.Plan(s)
+    out = gp.fock(s.D, want_rho=True, want_v=True)
+    ref = op.fock(s.D)
+    assert abs(out["EH"] - ref["EH"]) <= 1e-8
+    assert abs(out["Ex"] - ref["Ex"]) <= 1e-8
+    assert _rel(out["rho"].cpu().numpy(), ref["rho_fine"]) <= RTOL
+    assert _rel(out["v"].cpu().numpy(), ref["v_fine"]) <= RTOL
+    assert _rel(out["V"].cpu().numpy(), ref["V"]) <= RTOL
+
+
+@pytest.mark.parametrize("name", ["tiny", "resolved", "water4"])
+def test_ip1(gpw, cases, name):
+    s, op = cases[name]
+    gp = gpw.Plan(s)
+    vf = s.potential.sample(op.meshes[0])
+    got = gp.eval_mat_ip1(s.D, vf).cpu().numpy()
+    ref = op.grad_levels(s.D, op.restrict(vf))
+    assert np.max(np.abs(got - ref)) <= 1e-7
+    assert _rel(got, ref) <= 1e-9
+
+
+def test_fock_gradient_matches_oracle_and_fd(gpw, cases):
+    s, op = cases["resolved"]
+    gp = gpw.Plan(s)
+    out = gp.fock(s.D, want_v=True)
+    g = gp.eval_mat_ip1(s.D, out["v"]).cpu().numpy()
+    ref = op.fock(s.D)
+    gref = op.grad_levels(s.D, ref["v_levels"])
+    assert np.max(np.abs(g - gref)) <= 1e-7
+    # central differences of the GPU energy with frozen plan boxes
+    h = 1e-4
+    for atom, d in [(0, 0), (1, 2)]:
+        e = []
+        for sgn in (1, -1):
+            c = s.coords.copy()
+            c[atom, d] += sgn * h
+            gp.update_coords(c)
+            o = gp.fock(s.D)
+            e.append(o["EH"] + o["Ex"])
+        gp.update_coords(s.coords)
+        fd = (e[0] - e[1]) / (2 * h)
+        assert abs(fd - g[atom, d]) <= 1e-6 * max(1.0, abs(g[atom, d]))
+
+
+def test_adjoint_identity_gpu(gpw, cases):
+    s, op = cases["water4"]
+    gp = gpw.Plan(s)
+    rng = np.random.default_rng(9)
+    D = rng.standard_normal((s.nao, s.nao))
+    D = D + D.T
+    v = rng.standard_normal(tuple(op.meshes[0]))
+    rho = gp.eval_rho(D).cpu().numpy()
+    V = gp.eval_mat(v).cpu().numpy()
+    omega = float(np.prod(np.diag(s.lattice)))
+    lhs = omega / rho.size * float(np.sum(v * rho))
+    rhs = float(np.sum(D * V))
+    assert abs(lhs - rhs) <= 1e-10 * max(abs(lhs), 1.0)
+
+
+def test_repeatable_and_independent_plans(gpw, cases):
+    s, _ = cases["water4"]
+    a = gpw.Plan(s)
+    b = gpw.Plan(s)
+    r1 = a.fock(s.D)
+    r2 = b.fock(s.D)
+    r3 = a.fock(s.D)
+    assert r1["EH"] == r2["EH"] == r3["EH"]
+    assert torch.equal(r1["V"], r3["V"])
+    assert torch.equal(r1["V"], r2["V"])
+
+
+def test_empty_screening(gpw):
+    # tau so large that every primitive is dropped: zero density, zero V, zero energy
+    s = workloads.tiny().with_tau(1e6)
+    gp = gpw.Plan(s)
+    assert gp.stats()["npairs"] == 0
+    out = gp.fock(s.D, want_rho=True)
+    assert float(out["rho"].abs().max()) == 0.0
+    assert float(out["V"].abs().max()) == 0.0
+    assert out["EH"] == 0.0 and out["Ex"] == 0.0
+
+
+def test_invalid_inputs(gpw):
+    s = workloads.tiny()
+    bad = s.with_coords(s.coords)
+    bad.lattice = s.lattice.copy()
+    bad.lattice[0, 1] = 0.5
+    with pytest.raises(gpw.GpwError) as e:
+        gpw.Plan(bad)
+    assert e.value.code == -1
+    bad2 = s.with_coords(s.coords)
+    bad2.shell_l = s.shell_l.copy()
+    bad2.shell_l[0] = 4
+    with pytest.raises(gpw.GpwError):
+        gpw.Plan(bad2)
