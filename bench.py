@@ -1,0 +1,319 @@
+#!/usr/bin/env python
+"""Throughput of the multigrid GPW hot path on GB300 (one JSON line on rank 0).
+
+One step = one full pass of the path over the 256-water workload: gpw_fock_grad (pair
+D tensors, collocation on every level, Fourier interpolation, Poisson, Slater exchange,
+restriction, one integration pass at degree L+1 per pair, V assembly and the Hxc
+gradient contraction).
+The plan (screening, task lists, 1-D tables) is built once per geometry before the
+timed region, as the method prescribes; its time is reported as plan_ms.
+
+value = model FP64 FLOPs of the two grid passes (2(L+1) per pair-point for eval_rho,
+2(L+2) for the integration that serves eval_mat and eval_mat_ip1) per second, summed
+over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs an independent replica of the workload on its own GPU
+(weak scaling, no collective on the data path).  --impl reference times the CPU
+oracle on a bounded sample of the same workload, on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "eval_rho+eval_mat FP64 TFLOP/s (% of peak); served builds/s, p50/p99 latency"
+# FP64 peak of one GB300: 152 SMs x 4 FLOP/clk/SM (the nominal 1.25 TFLOP/s at the
+# 2070 MHz maximum SM clock is 3.97 FLOP/clk/SM) x 2.070 GHz.
+FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
+WORKLOAD = "water256"
+WORKLOAD_DESC = ("256 H2O, cubic L=37.3 Bohr, 7168 Cartesian AOs, 280 Ha, 4 levels "
+                 "(288/168/96/60), tau=1e-6; step = gpw_fock_grad (V, energies, Hxc gradient)")
+# DRAM bytes per launch of the dominant kernel from one ncu capture, valid while the
+# kernel source is unchanged (sha256 of csrc/kernels.cu at capture time).
+TRAFFIC = {}
+
+
+def _kernels_sha() -> str:
+    p = os.path.join(ROOT, "paper_2603_24881_gb300", "csrc", "kernels.cu")
+    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpw", choices=["gpw", "reference"])
+    ap.add_argument("--workload", default=WORKLOAD)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-stride", type=int, default=8)
+    ap.add_argument("--tile", default=None, help="sub-box shape t0,t1,t2 (default: tuned)")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ clocks -----
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.proc = None
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", gpu_id], stdout=self.file, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        rows = [l.strip().split(",") for l in open(self.file.name) if l.strip()]
+        os.unlink(self.file.name)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _gpu_id(torch) -> str:
+    try:
+        u = torch.cuda.get_device_properties(torch.cuda.current_device()).uuid
+        return "GPU-" + str(u)
+    except Exception:
+        return str(torch.cuda.current_device())
+
+
+# ------------------------------------------------------------------ oracle -----
+def oracle_sample(sys_, stride: int, offset: int = 0, threads: int = 0):
+    """Time the CPU oracle (as it stands) on every stride-th pair of the workload:
+    separable collocation, integration and the gradient contraction.  Returns
+    (model flops, seconds, pairs, pair-points, threads)."""
+    import numpy as np
+    import oracle
+    p = oracle.Plan(sys_)
+    idx = np.arange(offset % stride, p.npairs, stride)
+    sub = p.subset(idx)
+    L = (p.prims["l"][sub.ab[:, 0]] + p.prims["l"][sub.ab[:, 1]]).astype(np.float64)
+    pts = np.prod(sub.hi - sub.lo + 1, axis=1).astype(np.float64)
+    flops = float(np.sum(2 * (L + 1) * pts) * 2 + np.sum(2 * (L + 2) * pts))
+    rng = np.random.default_rng(0)
+    vl = [rng.standard_normal(tuple(m)) for m in p.meshes]
+    nthr = threads or os.cpu_count() or 1
+    t0 = time.perf_counter()
+    sub.rho_levels(sys_.D, mode="separable", nthreads=nthr)
+    sub._pair_blocks(vl, nthreads=nthr)
+    sub._pair_blocks(vl, grad_D=sys_.D, nthreads=nthr)
+    dt = time.perf_counter() - t0
+    return flops, dt, len(idx), float(pts.sum()), nthr
+
+
+def cpu_baseline(sys_, stride: int) -> dict:
+    f, dt, n, pts, nthr = oracle_sample(sys_, stride)
+    return {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": nthr, "kind": "oracle",
+            "sample": f"every {stride}th screened pair of {WORKLOAD} ({n} pairs, {pts:.3e} "
+                      f"pair-points): separable collocation + integration + gradient "
+                      f"contraction, {dt:.1f} s on {nthr} threads"}
+
+
+def run_reference(a, rank, world):
+    """Reference arm: the CPU oracle, timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import workloads
+    s = workloads.config(a.workload)
+    stride = max(a.cpu_stride * 4, 64)
+    for i in range(a.warmup):
+        oracle_sample(s, stride * 4, offset=i)
+    tot_f, tot_t, nthr = 0.0, 0.0, 0
+    for i in range(a.steps):
+        f, dt, n, pts, nthr = oracle_sample(s, stride, offset=i)
+        tot_f += f
+        tot_t += dt
+    val = tot_f / tot_t / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "TFLOP/s",
+            "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1e3 * tot_t / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD_DESC, "sample": f"every {stride}th pair per step"},
+            "cpu_baseline": {"value": val, "unit": "TFLOP/s", "cores": nthr, "kind": "oracle",
+                             "sample": f"every {stride}th screened pair of {a.workload} per step"},
+            "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ main -------
+def main():
+    a = _args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if a.impl == "reference":
+        run_reference(a, rank, world)
+        return
+    import numpy as np
+    import torch
+    import workloads
+    import paper_2603_24881_gb300 as gpw
+
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    gpw.load()
+    s = workloads.config(a.workload)
+    t0 = time.perf_counter()
+    tile = tuple(int(x) for x in a.tile.split(",")) if a.tile else None
+    plan = gpw.Plan(s, tile=tile)
+    torch.cuda.synchronize()
+    plan_ms = 1e3 * (time.perf_counter() - t0)
+    st = plan.stats()
+    flops_step = st["flops_rho"] + st["flops_ip1"]
+
+    D = torch.as_tensor(s.D, device="cuda")
+    V = torch.empty((plan.nao, plan.nao), dtype=torch.float64, device="cuda")
+    E = torch.empty(2, dtype=torch.float64, device="cuda")
+    v = torch.empty(plan.fine_mesh, dtype=torch.float64, device="cuda")
+    g = torch.empty((plan.natm, 3), dtype=torch.float64, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def step():
+        plan.fock_grad_async(D, V, g, E, stream=stream)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    plan.check_device()
+    plan.profile(True)
+    l0 = plan.launches()
+    clk = Clocks(_gpu_id(torch)) if rank == 0 else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = clk.stop() if clk else None
+    launches = plan.launches() - l0
+    prof = plan.profile_read()
+    plan.profile(False)
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    err = plan.check_device()
+    if err:
+        raise RuntimeError(f"device bounds check fired: code {err}")
+    value = flops_step * a.steps * world / (ms * 1e-3) / 1e12
+
+    # dominant kernel: the grid pass with the largest share of device time
+    ph_flops = {"collocate": st["flops_rho"], "integrate_ip1": st["flops_ip1"]}
+    dom = max(ph_flops, key=lambda k: prof["ms"][k])
+    per_launch_ms = prof["ms"][dom] / max(prof["count"][dom], 1)
+    achieved = ph_flops[dom] / (per_launch_ms * 1e-3) / 1e12
+    tr = TRAFFIC.get(dom)
+    traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == _kernels_sha() else None
+    roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
+                "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
+                "peak_source": "FP64 pipe: 152 SMs x 4 FLOP/clk x 2.07 GHz (no FP64 figure in "
+                               "MEASURED_PEAKS.json)"}
+
+    e2e = None
+    if not a.no_e2e:
+        Dh = torch.as_tensor(s.D).pin_memory()
+        out = dict(V=torch.empty((plan.nao, plan.nao), dtype=torch.float64, pin_memory=True),
+                   grad=torch.empty((plan.natm, 3), dtype=torch.float64, pin_memory=True),
+                   E=torch.empty(2, dtype=torch.float64, pin_memory=True))
+        for _ in range(2):
+            plan.fock_grad_host(Dh, out=out)
+        if dist:
+            dist.barrier()
+        t1 = time.perf_counter()
+        for _ in range(a.steps):
+            plan.fock_grad_host(Dh, out=out)
+        e2e_s = time.perf_counter() - t1
+        if dist:
+            t = torch.tensor([e2e_s], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_s = float(t.item())
+        e2e = {"value": flops_step * a.steps * world / e2e_s / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(Dh.numel() * 8),
+               "d2h_bytes_per_step": int((out["V"].numel() + out["grad"].numel() + 2) * 8),
+               "api": "Plan.fock_grad_host (pinned host D in; V, gradient, energies out)"}
+
+    if rank == 0:
+        cpu = None
+        if not a.no_cpu:
+            try:
+                cpu = cpu_baseline(s, a.cpu_stride)
+            except Exception as ex:  # the CPU oracle is a reported baseline only
+                cpu = {"value": None, "unit": "TFLOP/s", "cores": os.cpu_count(),
+                       "kind": "oracle", "sample": f"failed: {ex}"}
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
+                "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic",
+                "config": {"workload": WORKLOAD_DESC, "pairs": st["npairs"],
+                           "pair_points": st["pair_points"], "tasks": st["nentries"],
+                           "l2": "no flush: plan tables, tasks and grids (>2 GB) exceed L2",
+                           "tile": list(st["tile"]),
+                           "parallelism": f"replicas x{world}"},
+                "pct_of_fp64_peak": 100.0 * value / world / FP64_PEAK_TFLOPS,
+                "pair_points_per_s": st["pair_points"] * a.steps * world / (ms * 1e-3),
+                "plan_ms": plan_ms, "phase_ms_per_step": {k: v / a.steps for k, v in prof["ms"].items()},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": launches, "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -86,6 +86,9 @@ typedef struct {
                                  with E_k >= rel_cutoff * alpha_p (40 if <= 0) */
   double tau;                 /* screening threshold of Eq. (cut) */
   int flags;                  /* GPW_STRICT */
+  int tile[3];                /* sub-box owned by one thread block (grid points along
+                                 a1, a2, a3); {0,0,0} = default {8,8,16}.  Supported:
+                                 see gpw_tile_supported. */
 } gpw_desc;
 
 /* Sizes and work counts of a plan (gpw_plan_query). */
@@ -114,6 +117,9 @@ typedef struct {
  * 1..GPW_MAX_LEVELS, non-positive exponents, or meshes too small for the
  * cutoff sphere.  *out is set only on success. */
 int gpw_plan(const gpw_desc* desc, void* stream, gpw_plan_t* out);
+
+/* 1 if the sub-box shape (t0, t1, t2) has compiled kernels, else 0. */
+int gpw_tile_supported(int t0, int t1, int t2);
 
 /* Fill *info (host). */
 int gpw_plan_query(gpw_plan_t plan, gpw_plan_info* info);
@@ -170,9 +176,42 @@ int gpw_fock(gpw_plan_t plan, const double* D, double* V, double* energies,
 int gpw_fock_async(gpw_plan_t plan, const double* D, double* V, double* energies_dev,
                    double* rho_out, double* v_fine_out, void* stream);
 
+/* Fock build plus Hxc gradient in one pass: the level potentials of the build are
+ * integrated once at degree L + 1 per pair, which yields both V (Algorithm 2) and the
+ * gradient contraction (Algorithm 3) with the density matrix D.  V (device nao x nao),
+ * grad (device natm x 3), energies (host, 2 doubles; the call synchronises `stream`). */
+int gpw_fock_grad(gpw_plan_t plan, const double* D, double* V, double* grad, double* energies,
+                  void* stream);
+
+/* As gpw_fock_grad with the energies written to device memory (2 doubles), no sync. */
+int gpw_fock_grad_async(gpw_plan_t plan, const double* D, double* V, double* grad,
+                        double* energies_dev, void* stream);
+
 /* Read and clear the device error word of the plan (synchronises `stream`).
  * Returns GPW_OK, or GPW_EDEVICE with *code set to the first recorded check. */
 int gpw_check_device(gpw_plan_t plan, int* code, void* stream);
+
+/* Phases timed by the profiler (gpw_profile). */
+#define GPW_PHASE_COEF 0            /* pair D tensors (Eq. rho1 coefficients) */
+#define GPW_PHASE_COLLOCATE 1       /* collocation kernel (Algorithm 1) */
+#define GPW_PHASE_SPECTRAL 2        /* FFTs, interpolation, Poisson, exchange, restriction */
+#define GPW_PHASE_INTEGRATE 3       /* integration kernel (Algorithm 2) */
+#define GPW_PHASE_ASSEMBLE 4        /* per-pair reductions and V assembly */
+#define GPW_PHASE_INTEGRATE_IP1 5   /* integration kernel at degree L+1 (Algorithm 3) */
+#define GPW_PHASE_GRAD 6            /* gradient contraction and per-atom sums */
+#define GPW_NPHASES 7
+
+/* Device timing of later calls on this plan, per phase, with CUDA events recorded on
+ * each call's stream.  enable != 0 clears the totals and starts recording; 0 stops.
+ * Not for use inside CUDA-graph capture. */
+int gpw_profile(gpw_plan_t plan, int enable);
+
+/* Synchronise the recorded events and return, per phase (up to nphases entries),
+ * the summed milliseconds (ms) and the number of timed intervals (count); either
+ * pointer may be NULL.  *launches (optional) receives the number of libgpw kernels
+ * launched on this plan since the plan was built (cuFFT's own kernels excluded). */
+int gpw_profile_read(gpw_plan_t plan, double* ms, long long* count, int nphases,
+                     long long* launches);
 
 /* Release the plan and everything it owns.  NULL is ignored. */
 void gpw_plan_destroy(gpw_plan_t plan);

@@ -25,7 +25,10 @@ ERRORS = {0: "GPW_OK", -1: "GPW_EINVAL", -2: "GPW_ENOMEM", -3: "GPW_ECUDA", -4: 
 EXPORTS = ["gpw_plan", "gpw_plan_query", "gpw_plan_update_coords", "gpw_plan_pairs",
            "gpw_eval_rho", "gpw_eval_rho_levels", "gpw_eval_mat", "gpw_eval_mat_levels",
            "gpw_eval_mat_ip1", "gpw_eval_mat_ip1_levels", "gpw_fock", "gpw_fock_async",
-           "gpw_check_device", "gpw_plan_destroy", "gpw_strerror", "gpw_last_error"]
+           "gpw_fock_grad", "gpw_fock_grad_async", "gpw_tile_supported",
+           "gpw_check_device", "gpw_profile", "gpw_profile_read", "gpw_plan_destroy",
+           "gpw_strerror", "gpw_last_error"]
+PHASES = ["coef", "collocate", "spectral", "integrate", "assemble", "integrate_ip1", "grad"]
 
 
 class GpwError(RuntimeError):
@@ -43,7 +46,9 @@ class Desc(ctypes.Structure):
                 ("cutoff_ha", ctypes.c_double), ("nlevels", ctypes.c_int),
                 ("level_ratio", ctypes.c_double), ("meshes", ctypes.c_void_p),
                 ("rel_cutoff", ctypes.c_double), ("tau", ctypes.c_double),
-                ("flags", ctypes.c_int)]
+                ("flags", ctypes.c_int), ("tile", ctypes.c_int * 3)]
+
+TILES = [(8, 8, 16), (4, 8, 32), (8, 8, 32), (4, 8, 64)]
 
 
 class Info(ctypes.Structure):
@@ -89,7 +94,12 @@ def load(build_if_missing: bool = True):
         L.gpw_eval_mat_ip1_levels.argtypes = [vp, vp, vp, vp, vp]
         L.gpw_fock.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.gpw_fock_async.argtypes = [vp, vp, vp, vp, vp, vp, vp]
+        L.gpw_fock_grad.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.gpw_fock_grad_async.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.gpw_tile_supported.argtypes = [ci, ci, ci]
         L.gpw_check_device.argtypes = [vp, ctypes.POINTER(ci), vp]
+        L.gpw_profile.argtypes = [vp, ci]
+        L.gpw_profile_read.argtypes = [vp, vp, vp, ci, vp]
         L.gpw_plan_destroy.argtypes = [vp]
         L.gpw_plan_destroy.restype = None
         L.gpw_strerror.argtypes = [ci]
@@ -135,7 +145,7 @@ class Plan:
     """A libgpw plan for one cell (Sec. II / III A of the paper): screened pairs,
     levels, task lists, grids and FFT plans live on the current CUDA device."""
 
-    def __init__(self, system, stream=None):
+    def __init__(self, system, stream=None, tile=None):
         import torch
         self._lib = load()
         s = system
@@ -167,6 +177,9 @@ class Plan:
         d.rel_cutoff = float(s.rel_cutoff)
         d.tau = float(s.tau)
         d.flags = 0
+        if tile is not None:
+            for i in range(3):
+                d.tile[i] = int(tile[i])
         torch.cuda.init()
         h = ctypes.c_void_p()
         check(self._lib.gpw_plan(ctypes.byref(d), ctypes.c_void_p(_stream(stream)),
@@ -233,6 +246,28 @@ class Plan:
         if rc not in (0, -6):
             check(rc, "gpw_check_device")
         return int(code.value)
+
+    def profile(self, enable: bool = True):
+        """Start (clearing totals) or stop per-phase CUDA-event timing of later calls."""
+        check(self._lib.gpw_profile(self._h, 1 if enable else 0), "gpw_profile")
+
+    def profile_read(self) -> dict:
+        """Per-phase summed device milliseconds and interval counts, plus the number of
+        libgpw kernels launched on this plan so far."""
+        n = len(PHASES)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_longlong * n)()
+        launches = ctypes.c_longlong(0)
+        check(self._lib.gpw_profile_read(self._h, ms, cnt, n, ctypes.byref(launches)),
+              "gpw_profile_read")
+        return dict(ms={PHASES[i]: ms[i] for i in range(n)},
+                    count={PHASES[i]: cnt[i] for i in range(n)}, launches=int(launches.value))
+
+    def launches(self) -> int:
+        launches = ctypes.c_longlong(0)
+        check(self._lib.gpw_profile_read(self._h, None, None, 0, ctypes.byref(launches)),
+              "gpw_profile_read")
+        return int(launches.value)
 
     # -- evaluations (device tensors) ----------------------------------------
     def _levels_out(self, dtype=None):
@@ -310,6 +345,55 @@ class Plan:
         if want_v:
             out["v"] = v
         return out
+
+    def fock_grad_host(self, D_host, out=None, stream=None):
+        """End-to-end Fock build plus Hxc gradient from HOST memory: copies D in
+        (pinned host -> device), runs gpw_fock_grad_async on the stream, copies V,
+        the gradient and the two energies back, synchronises.
+        Returns dict(V, grad, EH, Ex) of host tensors."""
+        import torch
+        st = torch.cuda.current_stream() if stream is None else stream
+        ws = self._host_ws()
+        ws["D"].copy_(D_host, non_blocking=True)
+        self.fock_grad_async(ws["D"], ws["V"], ws["g"], ws["E"], stream=st)
+        if out is None:
+            out = dict(V=torch.empty((self.nao, self.nao), dtype=torch.float64, pin_memory=True),
+                       grad=torch.empty((self.natm, 3), dtype=torch.float64, pin_memory=True),
+                       E=torch.empty(2, dtype=torch.float64, pin_memory=True))
+        out["V"].copy_(ws["V"], non_blocking=True)
+        out["grad"].copy_(ws["g"], non_blocking=True)
+        out["E"].copy_(ws["E"], non_blocking=True)
+        st.synchronize()
+        return out
+
+    def _host_ws(self):
+        import torch
+        ws = getattr(self, "_ws", None)
+        if ws is None:
+            dev = dict(dtype=torch.float64, device="cuda")
+            ws = dict(D=torch.empty((self.nao, self.nao), **dev),
+                      V=torch.empty((self.nao, self.nao), **dev),
+                      E=torch.empty(2, **dev), v=torch.empty(self.fine_mesh, **dev),
+                      g=torch.empty((self.natm, 3), **dev))
+            self._ws = ws
+        return ws
+
+    def fock_grad(self, D, stream=None):
+        """Fock build and Hxc gradient in one pass (gpw_fock_grad).
+        Returns dict(V, grad, EH, Ex)."""
+        import torch
+        D = _dev_f64(D, (self.nao, self.nao))
+        V = torch.empty((self.nao, self.nao), dtype=torch.float64, device="cuda")
+        g = torch.empty((self.natm, 3), dtype=torch.float64, device="cuda")
+        e = (ctypes.c_double * 2)()
+        check(self._lib.gpw_fock_grad(self._h, _ptr(D), _ptr(V), _ptr(g), e, _stream(stream)),
+              "gpw_fock_grad")
+        return dict(V=V, grad=g, EH=float(e[0]), Ex=float(e[1]))
+
+    def fock_grad_async(self, D, V, grad, energies, stream=None):
+        """Enqueue gpw_fock_grad_async: V, grad and energies (device, 2 doubles)."""
+        check(self._lib.gpw_fock_grad_async(self._h, _ptr(D), _ptr(V), _ptr(grad), _ptr(energies),
+                                            _stream(stream)), "gpw_fock_grad_async")
 
     def fock_async(self, D, V, energies, rho=None, v=None, stream=None):
         """Enqueue a Fock build writing V and energies (device, 2 doubles) only."""

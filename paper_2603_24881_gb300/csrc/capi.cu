@@ -65,11 +65,13 @@ int upload(T** ptr, const std::vector<T>& v, long long* bytes) {
 void free_plan(Plan* P) {
   DeviceArrays& d = P->d;
   void* ptrs[] = {d.hot_a, d.hot_b, d.ids, d.ids2, d.geo, d.cab, d.pref, d.tab_off,
-                  d.coef_off, d.part_off, d.ent, d.sub_off, d.work, d.groups, d.atom_off,
+                  d.coef_off, d.part_off, d.task, d.sub_off, d.work, d.groups, d.atom_off,
                   d.atom_list, d.tab, d.coef, d.part, d.pgrad, d.grids, d.spec, d.fspec,
                   d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs};
   for (void* q : ptrs)
     if (q) cudaFree(q);
+  for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
+  P->ev_pool.clear();
   for (int k = 0; k < GPW_MAX_LEVELS; ++k)
     if (P->fft_made[k]) {
       cufftDestroy(P->fft_d2z[k]);
@@ -94,7 +96,7 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
   GPW_TRY(upload(&d.tab_off, H.tab_off, &b));
   GPW_TRY(upload(&d.coef_off, H.coef_off, &b));
   GPW_TRY(upload(&d.part_off, H.part_off, &b));
-  GPW_TRY(upload(&d.ent, H.ent, &b));
+  GPW_TRY(upload(&d.task, H.task, &b));
   GPW_TRY(upload(&d.sub_off, H.sub_off, &b));
   GPW_TRY(upload(&d.work, H.work, &b));
   GPW_TRY(upload(&d.groups, H.groups, &b));
@@ -154,16 +156,49 @@ int fft_z2d(Plan& P, int k, cufftDoubleComplex* in, double* out, cudaStream_t s)
   return GPW_OK;
 }
 
+// Records a CUDA event pair around one phase on the call's stream when profiling.
+class Phase {
+ public:
+  Phase(Plan& P, int ph, cudaStream_t s) : P_(P), s_(s), on_(P.prof) {
+    if (!on_) return;
+    while (P_.ev_pool.size() < P_.ev_used + 2) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        on_ = false;
+        return;
+      }
+      P_.ev_pool.push_back(e);
+    }
+    cudaEventRecord(P_.ev_pool[P_.ev_used], s_);
+    P_.ev_phase.push_back(ph);
+  }
+  ~Phase() {
+    if (!on_) return;
+    cudaEventRecord(P_.ev_pool[P_.ev_used + 1], s_);
+    P_.ev_used += 2;
+  }
+
+ private:
+  Plan& P_;
+  cudaStream_t s_;
+  bool on_;
+};
+
 // rho_k on every level (raw collocation, Algorithm 1 / Eq. rho_wrap).
 int rho_levels(Plan& P, const double* D, cudaStream_t s) {
-  GPW_CK(launch_pair_coef(P, D, s));
+  {
+    Phase ph(P, GPW_PHASE_COEF, s);
+    GPW_CK(launch_pair_coef(P, D, s));
+  }
   GPW_CK(cudaMemsetAsync(P.d.grids, 0, sizeof(double) * (size_t)P.grid_total, s));
+  Phase ph(P, GPW_PHASE_COLLOCATE, s);
   GPW_CK(launch_collocate(P, s));
   return GPW_OK;
 }
 
 // Level densities -> finest spectrum S (Fourier interpolation, Sec. II).
 int combine(Plan& P, cudaStream_t s) {
+  Phase ph(P, GPW_PHASE_SPECTRAL, s);
   for (int k = 0; k < P.nlev; ++k) {
     int rc = fft_d2z(P, k, P.d.grids + P.lev[k].grid_off, P.d.spec + P.lev[k].spec_off, s);
     if (rc) return rc;
@@ -174,6 +209,7 @@ int combine(Plan& P, cudaStream_t s) {
 
 // Finest-grid potential -> level potentials in P.d.grids (restriction, Sec. II).
 int restrict_levels(Plan& P, const double* v_fine, cudaStream_t s) {
+  Phase ph(P, GPW_PHASE_SPECTRAL, s);
   int rc = fft_d2z(P, 0, v_fine, P.d.fspec, s);
   if (rc) return rc;
   for (int k = 0; k < P.nlev; ++k) {
@@ -200,39 +236,83 @@ int copy_levels(Plan& P, const double* const* v_levels, cudaStream_t s) {
 
 // Integration of the level potentials in P.d.grids into V (Algorithm 2, Eq. J_wrap).
 int mat_from_grids(Plan& P, double* V, cudaStream_t s) {
-  GPW_CK(launch_integrate(P, 0, s));
+  {
+    Phase ph(P, GPW_PHASE_INTEGRATE, s);
+    GPW_CK(launch_integrate(P, 0, s));
+  }
+  Phase ph(P, GPW_PHASE_ASSEMBLE, s);
   GPW_CK(launch_reduce_parts(P, 0, s));
-  GPW_CK(launch_assemble_V(P, V, s));
+  GPW_CK(launch_assemble_V(P, 0, V, s));
+  return GPW_OK;
+}
+
+// One integration pass at degree L + 1 serves both V (its monomials of degree <= L) and
+// the gradient contraction: Algorithms 2 and 3 share the task sweep.
+int mat_ip1_from_grids(Plan& P, const double* D, double* V, double* grad, cudaStream_t s) {
+  {
+    Phase ph(P, GPW_PHASE_INTEGRATE_IP1, s);
+    GPW_CK(launch_integrate(P, 1, s));
+  }
+  {
+    Phase ph(P, GPW_PHASE_ASSEMBLE, s);
+    GPW_CK(launch_reduce_parts(P, 1, s));
+    GPW_CK(launch_assemble_V(P, 1, V, s));
+  }
+  Phase ph(P, GPW_PHASE_GRAD, s);
+  GPW_CK(launch_grad(P, D, grad, s));
   return GPW_OK;
 }
 
 int ip1_from_grids(Plan& P, const double* D, double* grad, cudaStream_t s) {
-  GPW_CK(launch_integrate(P, 1, s));
+  {
+    Phase ph(P, GPW_PHASE_INTEGRATE_IP1, s);
+    GPW_CK(launch_integrate(P, 1, s));
+  }
+  Phase ph(P, GPW_PHASE_GRAD, s);
   GPW_CK(launch_reduce_parts(P, 1, s));
   GPW_CK(launch_grad(P, D, grad, s));
   return GPW_OK;
 }
 
-int fock_async(Plan& P, const double* D, double* V, double* energies_dev, double* rho_out,
-               double* v_out, cudaStream_t s) {
+// rho -> interpolation -> Poisson + exchange -> restricted level potentials in P.d.grids;
+// energies to energies_dev.
+int fock_potential(Plan& P, const double* D, double* energies_dev, double* rho_out,
+                   double* v_out, cudaStream_t s) {
   int rc = rho_levels(P, D, s);
   if (rc) return rc;
   if ((rc = combine(P, s))) return rc;
   double* rho = rho_out ? rho_out : P.d.fine_b;
-  GPW_CK(cudaMemcpyAsync(P.d.fspec2, P.d.fspec, sizeof(cufftDoubleComplex) * (size_t)P.fine_spec_n,
-                         cudaMemcpyDeviceToDevice, s));
-  if ((rc = fft_z2d(P, 0, P.d.fspec2, rho, s))) return rc;
-  GPW_CK(launch_poisson(P, s));
-  if ((rc = fft_z2d(P, 0, P.d.fspec, P.d.fine_a, s))) return rc;
   double* v = v_out ? v_out : P.d.fine_a;
-  GPW_CK(launch_lda(P, rho, P.d.fine_a, v, s));
-  GPW_CK(launch_energy_final(P, 0, kRedBlocks, s));
-  GPW_CK(launch_energy_final(P, 1, kRedBlocks, s));
-  if (energies_dev != P.d.energies)
-    GPW_CK(cudaMemcpyAsync(energies_dev, P.d.energies, 2 * sizeof(double),
+  {
+    Phase ph(P, GPW_PHASE_SPECTRAL, s);
+    GPW_CK(cudaMemcpyAsync(P.d.fspec2, P.d.fspec,
+                           sizeof(cufftDoubleComplex) * (size_t)P.fine_spec_n,
                            cudaMemcpyDeviceToDevice, s));
-  if ((rc = restrict_levels(P, v, s))) return rc;
+    if ((rc = fft_z2d(P, 0, P.d.fspec2, rho, s))) return rc;
+    GPW_CK(launch_poisson(P, s));
+    if ((rc = fft_z2d(P, 0, P.d.fspec, P.d.fine_a, s))) return rc;
+    GPW_CK(launch_lda(P, rho, P.d.fine_a, v, s));
+    GPW_CK(launch_energy_final(P, 0, kRedBlocks, s));
+    GPW_CK(launch_energy_final(P, 1, kRedBlocks, s));
+    if (energies_dev != P.d.energies)
+      GPW_CK(cudaMemcpyAsync(energies_dev, P.d.energies, 2 * sizeof(double),
+                             cudaMemcpyDeviceToDevice, s));
+  }
+  return restrict_levels(P, v, s);
+}
+
+int fock_async(Plan& P, const double* D, double* V, double* energies_dev, double* rho_out,
+               double* v_out, cudaStream_t s) {
+  int rc = fock_potential(P, D, energies_dev, rho_out, v_out, s);
+  if (rc) return rc;
   return mat_from_grids(P, V, s);
+}
+
+int fock_grad_async(Plan& P, const double* D, double* V, double* grad, double* energies_dev,
+                    cudaStream_t s) {
+  int rc = fock_potential(P, D, energies_dev, nullptr, nullptr, s);
+  if (rc) return rc;
+  return mat_ip1_from_grids(P, D, V, grad, s);
 }
 
 bool bad(gpw_plan_t plan) {
@@ -299,9 +379,9 @@ int gpw_plan_query(gpw_plan_t plan, gpw_plan_info* info) {
   info->flops_rho = P.flops_rho;
   info->flops_mat = P.flops_mat;
   info->flops_ip1 = P.flops_ip1;
-  info->tile[0] = gpw::kT0;
-  info->tile[1] = gpw::kT1;
-  info->tile[2] = gpw::kT2;
+  info->tile[0] = P.tile[0];
+  info->tile[1] = P.tile[1];
+  info->tile[2] = P.tile[2];
   return GPW_OK;
 }
 
@@ -443,6 +523,29 @@ int gpw_fock(gpw_plan_t plan, const double* D, double* V, double* energies, doub
   return GPW_OK;
 }
 
+int gpw_fock_grad_async(gpw_plan_t plan, const double* D, double* V, double* grad,
+                        double* energies_dev, void* stream) {
+  if (gpw::bad(plan) || !D || !V || !grad || !energies_dev) return GPW_EINVAL;
+  return gpw::fock_grad_async(plan->p, D, V, grad, energies_dev, (cudaStream_t)stream);
+}
+
+int gpw_fock_grad(gpw_plan_t plan, const double* D, double* V, double* grad, double* energies,
+                  void* stream) {
+  if (gpw::bad(plan) || !D || !V || !grad || !energies) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::fock_grad_async(P, D, V, grad, P.d.energies, s);
+  if (rc) return rc;
+  cudaError_t e = cudaMemcpyAsync(energies, P.d.energies, 2 * sizeof(double),
+                                  cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_error(std::string("gpw_fock_grad: ") + cudaGetErrorString(e));
+    return GPW_ECUDA;
+  }
+  return GPW_OK;
+}
+
 int gpw_check_device(gpw_plan_t plan, int* code, void* stream) {
   if (gpw::bad(plan)) return GPW_EINVAL;
   gpw::Plan& P = plan->p;
@@ -460,6 +563,47 @@ int gpw_check_device(gpw_plan_t plan, int* code, void* stream) {
     set_error("device bounds check failed, code " + std::to_string(h));
     return GPW_EDEVICE;
   }
+  return GPW_OK;
+}
+
+int gpw_profile(gpw_plan_t plan, int enable) {
+  if (gpw::bad(plan)) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  if (enable) {
+    for (int i = 0; i < GPW_NPHASES; ++i) {
+      P.prof_ms[i] = 0.0;
+      P.prof_n[i] = 0;
+    }
+    P.ev_used = 0;
+    P.ev_phase.clear();
+  }
+  P.prof = enable != 0;
+  return GPW_OK;
+}
+
+int gpw_profile_read(gpw_plan_t plan, double* ms, long long* count, int nphases,
+                     long long* launches) {
+  if (gpw::bad(plan)) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  for (size_t i = 0; i < P.ev_phase.size(); ++i) {
+    cudaEvent_t a = P.ev_pool[2 * i], b = P.ev_pool[2 * i + 1];
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, a, b);
+    if (e != cudaSuccess) {
+      set_error(std::string("gpw_profile_read: ") + cudaGetErrorString(e));
+      return GPW_ECUDA;
+    }
+    P.prof_ms[P.ev_phase[i]] += t;
+    P.prof_n[P.ev_phase[i]] += 1;
+  }
+  P.ev_used = 0;
+  P.ev_phase.clear();
+  for (int i = 0; i < nphases && i < GPW_NPHASES; ++i) {
+    if (ms) ms[i] = P.prof_ms[i];
+    if (count) count[i] = P.prof_n[i];
+  }
+  if (launches) *launches = P.launches;
   return GPW_OK;
 }
 

@@ -10,6 +10,8 @@
 
 #include "gpw.h"
 
+extern "C" int gpw_tile_supported(int t0, int t1, int t2);
+
 namespace gpw {
 
 constexpr int kShellLmax = 3;                   // Cartesian shells up to f
@@ -18,10 +20,9 @@ constexpr int kLextMax = kLmax + 1;             // one more for the centre deriv
 constexpr int kNc3Max = (kLextMax + 1) * (kLextMax + 2) * (kLextMax + 3) / 6;  // 120
 constexpr int kNc2Max = (kLextMax + 1) * (kLextMax + 2) / 2;                   // 36
 
-// Sub-box (tile) owned by one thread block: kT0 x kT1 x kT2 grid points, the last
-// along the fastest grid index, so a tile row is 16 contiguous doubles (128 B).
+// Default sub-box (tile) owned by one thread block: T0 x T1 x T2 grid points, the last
+// along the fastest grid index.  The shape is a plan parameter (see kTileShapes).
 constexpr int kT0 = 8, kT1 = 8, kT2 = 16;
-constexpr int kTile = kT0 * kT1 * kT2;
 
 // Number of monomials x^l0 y^l1 z^l2 with l0 + l1 + l2 <= L, and of (l1, l2) pairs.
 __host__ __device__ constexpr int nc3(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
@@ -64,7 +65,7 @@ struct DeviceArrays {
   long long* coef_off = nullptr;  // D tensor (rho) / reduced V tensor (stride nc3(L+1))
   long long* part_off = nullptr;  // per-task V tensors (stride nc3(L+1) per task)
   // tasks
-  int4* ent = nullptr;        // pair, packed image shifts, rank within pair, 0
+  int4* task = nullptr;       // 2 per task: {pair, m|L, u, rank}, {t|n per dimension}
   long long* sub_off = nullptr;   // CSR offsets over all sub-boxes of all levels
   int2* work = nullptr;       // (level, sub-box) with tasks, heaviest first
   // V assembly: groups of pairs sharing a contracted shell pair
@@ -93,6 +94,7 @@ struct Plan {
   int device = 0;
   int nao = 0, natm = 0, nlev = 0, lmax = 0;
   int nprim = 0, nshell = 0;
+  int tile[3] = {kT0, kT1, kT2};
   double L[3] = {0, 0, 0};
   double omega = 0;
   double E[GPW_MAX_LEVELS] = {0};
@@ -120,6 +122,14 @@ struct Plan {
   size_t smem_colloc = 0, smem_integ = 0, smem_integ1 = 0;
   int nw_colloc = 8, nw_integ = 8;     // warps per thread block
   int stg_colloc = 0, stg_integ = 0, stg_integ1 = 0;  // per-warp staging doubles
+  // profiler: event pairs per phase, recorded on the calling stream when enabled
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_phase;   // phase of each recorded pair (pool index / 2)
+  size_t ev_used = 0;
+  double prof_ms[GPW_NPHASES] = {0};
+  long long prof_n[GPW_NPHASES] = {0};
+  mutable long long launches = 0;
 };
 
 // plan.cpp (host): screening and task lists; fills everything except device arrays.

@@ -63,44 +63,6 @@ __device__ __forceinline__ void load_tables(int* dst, const CoefTables* src, int
   for (int i = tid; i < kTabInts / 4; i += nthr) d4[i] = s4[i];
 }
 
-// Intersection of a task's pair box with its sub-box copy.
-struct Task {
-  int p, L;
-  int m[3];   // extent of the intersection
-  int t[3];   // offset of the intersection in the pair box (table column)
-  int u[3];   // offset of the intersection in the sub-box
-  int n[3];   // pair box extent (table row length)
-  int rank;
-};
-
-__device__ __forceinline__ bool make_task(const int4 e, const int4* hot_a, const int4* hot_b,
-                                          const LevelInfo& lv, const int* s, const int* ext,
-                                          Task* tk) {
-  const int p = e.x;
-  const int4 ha = __ldg(hot_a + p);
-  const int4 hb = __ldg(hot_b + p);
-  const int k[3] = {(e.y & 1023) - 512, ((e.y >> 10) & 1023) - 512, ((e.y >> 20) & 1023) - 512};
-  const int lo[3] = {ha.x, ha.y, ha.z};
-  tk->p = p;
-  tk->L = ha.w;
-  tk->n[0] = hb.x;
-  tk->n[1] = hb.y;
-  tk->n[2] = hb.z;
-  tk->rank = e.z;
-  bool ok = true;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    int o = k[d] * lv.N[d] + s[d];
-    int a = max(lo[d], o);
-    int b = min(lo[d] + tk->n[d] - 1, o + ext[d] - 1);
-    tk->m[d] = b - a + 1;
-    tk->t[d] = a - lo[d];
-    tk->u[d] = a - o;
-    ok = ok && (tk->m[d] > 0);
-  }
-  return ok;
-}
-
 // ----------------------------------------------------------------------------------
 // 1-D factor tables (Eq. gab_lp with the exponential of Eq. gab):
 //   g_d[l](i) = (x - A_d)^l exp(-alpha_p (x - P_d)^2),  x = (lo_d + i) h_d,  l <= L + 1,
@@ -205,6 +167,93 @@ __global__ void pair_coef_kernel(long long np, const int4* __restrict__ hot_a,
   for (int c = 0; c < nc; ++c) out[c] = acc[c];
 }
 
+// A task is one (pair, sub-box copy) intersection, precomputed by the plan as two int4:
+//   r0 = {pair, m0 | m1 << 8 | m2 << 16 | L << 24, u0 | u1 << 8 | u2 << 16, rank}
+//   r1 = {t0 | n0 << 16, t1 | n1 << 16, t2 | n2 << 16, 0}
+// m = intersection extent, u = its offset in the sub-box, t = its offset in the pair box
+// (column of the 1-D tables), n = pair box extent (table row length), rank = index of
+// the task among the pair's tasks.
+struct Task {
+  int p, L, rank;
+  int m[3], u[3], t[3], n[3];
+};
+
+__device__ __forceinline__ Task decode_task(const int4 r0, const int4 r1) {
+  Task t;
+  t.p = r0.x;
+  t.m[0] = r0.y & 255;
+  t.m[1] = (r0.y >> 8) & 255;
+  t.m[2] = (r0.y >> 16) & 255;
+  t.L = (r0.y >> 24) & 255;
+  t.u[0] = r0.z & 255;
+  t.u[1] = (r0.z >> 8) & 255;
+  t.u[2] = (r0.z >> 16) & 255;
+  t.rank = r0.w;
+  t.t[0] = r1.x & 0xffff;
+  t.n[0] = (r1.x >> 16) & 0xffff;
+  t.t[1] = r1.y & 0xffff;
+  t.n[1] = (r1.y >> 16) & 0xffff;
+  t.t[2] = r1.z & 0xffff;
+  t.n[2] = (r1.z >> 16) & 0xffff;
+  return t;
+}
+
+struct SubBox {
+  int s[3], ext[3];
+  long long eb, ee;
+};
+
+template <int T0, int T1, int T2>
+__device__ __forceinline__ SubBox sub_box(const LevelInfo& lv, int sub, const long long* sub_off) {
+  SubBox b;
+  const int j2 = sub % lv.nsb[2];
+  const int j1 = (sub / lv.nsb[2]) % lv.nsb[1];
+  const int j0 = sub / (lv.nsb[2] * lv.nsb[1]);
+  b.s[0] = j0 * T0;
+  b.s[1] = j1 * T1;
+  b.s[2] = j2 * T2;
+  b.ext[0] = min(T0, lv.N[0] - b.s[0]);
+  b.ext[1] = min(T1, lv.N[1] - b.s[1]);
+  b.ext[2] = min(T2, lv.N[2] - b.s[2]);
+  b.eb = sub_off[lv.sub_base + sub];
+  b.ee = sub_off[lv.sub_base + sub + 1];
+  return b;
+}
+
+// Stage rows l < rows of the three 1-D factor windows of a task into shared memory
+// (row strides P0, P1, P2).
+template <int P0, int P1, int P2>
+__device__ __forceinline__ void stage_tables(const double* tb, const Task& tk, int rows,
+                                             double* sg0, double* sg1, double* sg2, int lane) {
+  const int L = tk.L;
+  const double* t0 = tb + tk.t[0];
+  const double* t1 = tb + (L + 2) * tk.n[0] + tk.t[1];
+  const double* t2 = tb + (L + 2) * (tk.n[0] + tk.n[1]) + tk.t[2];
+  const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
+  const float i0f = __frcp_rn((float)m0), i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
+  for (int it = lane; it < rows * m0; it += 32) {
+    int l = fdiv(it, i0f), i = it - l * m0;
+    sg0[l * P0 + i] = __ldg(t0 + l * tk.n[0] + i);
+  }
+  for (int it = lane; it < rows * m1; it += 32) {
+    int l = fdiv(it, i1f), i = it - l * m1;
+    sg1[l * P1 + i] = __ldg(t1 + l * tk.n[1] + i);
+  }
+  for (int it = lane; it < rows * m2; it += 32) {
+    int l = fdiv(it, i2f), i = it - l * m2;
+    sg2[l * P2 + i] = __ldg(t2 + l * tk.n[2] + i);
+  }
+}
+
+template <int T0, int T1, int T2>
+struct CollocLayout {
+  static constexpr int kTileN = T0 * T1 * T2;
+  // per-warp staging, for lp = lmax + 1 factor rows
+  __host__ __device__ static int stage(int lp) {
+    return lp * (T0 + T1 + T2) + nc3(lp - 1) + nc2(lp - 1) * T0 + lp * T0 * T1;
+  }
+};
+
 // ----------------------------------------------------------------------------------
 // Collocation (Algorithm 1, two-stage: accumulate on chip, write each point once).
 // One thread block per sub-box with tasks; warp w takes tasks w, w + NW, ... of the
@@ -214,15 +263,16 @@ __global__ void pair_coef_kernel(long long np, const int4* __restrict__ hot_a,
 //   T1[l2,l1](i0) = sum_l0 D[l0,l1,l2] g0[l0](i0)            nc2(L) m0 FMAs
 //   T2[l2](i0,i1) = sum_l1 T1[l2,l1](i0) g1[l1](i1)          nc2(L) m0 m1
 //   rho(i0,i1,i2) += sum_l2 T2[l2](i0,i1) g2[l2](i2)         (L+1) m0 m1 m2
-template <int NW>
+// The next task's record and pair offsets are fetched while the current one computes.
+template <int T0, int T1, int T2, int NW>
 __global__ void __launch_bounds__(NW * 32)
     collocate_kernel(const KLevels K, const int2* __restrict__ work,
-                     const long long* __restrict__ sub_off, const int4* __restrict__ ent,
-                     const int4* __restrict__ hot_a, const int4* __restrict__ hot_b,
+                     const long long* __restrict__ sub_off, const int4* __restrict__ task,
                      const long long* __restrict__ tab_off, const long long* __restrict__ coef_off,
                      const double* __restrict__ tab, const double* __restrict__ coef,
                      const CoefTables* __restrict__ tabs, double* __restrict__ grids, int lp,
                      int stg, int* __restrict__ err) {
+  constexpr int kTileN = T0 * T1 * T2;
   extern __shared__ __align__(16) double sm[];
   int* s_tab = reinterpret_cast<int*>(sm);
   const int(*s_dec21)[kNc2Max] = reinterpret_cast<const int(*)[kNc2Max]>(s_tab);
@@ -231,122 +281,118 @@ __global__ void __launch_bounds__(NW * 32)
   double* acc_all = sm + kTabInts / 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   load_tables(s_tab, tabs, tid, NW * 32);
-  for (int i = tid; i < NW * kTile; i += NW * 32) acc_all[i] = 0.0;
+  for (int i = tid; i < NW * kTileN; i += NW * 32) acc_all[i] = 0.0;
 
   const int2 item = work[blockIdx.x];
   const LevelInfo& lv = K.lv[item.x];
-  const int sub = item.y;
-  const int j2 = sub % lv.nsb[2];
-  const int j1 = (sub / lv.nsb[2]) % lv.nsb[1];
-  const int j0 = sub / (lv.nsb[2] * lv.nsb[1]);
-  const int s[3] = {j0 * kT0, j1 * kT1, j2 * kT2};
-  const int ext[3] = {min(kT0, lv.N[0] - s[0]), min(kT1, lv.N[1] - s[1]),
-                      min(kT2, lv.N[2] - s[2])};
-  const long long eb = sub_off[lv.sub_base + sub], ee = sub_off[lv.sub_base + sub + 1];
+  const SubBox sb = sub_box<T0, T1, T2>(lv, item.y, sub_off);
 
-  double* acc = acc_all + warp * kTile;
-  double* sg0 = acc_all + NW * kTile + warp * stg;
-  double* sg1 = sg0 + lp * kT0;
-  double* sg2 = sg1 + lp * kT1;
-  double* sD = sg2 + lp * kT2;
+  double* acc = acc_all + warp * kTileN;
+  double* sg0 = acc_all + NW * kTileN + warp * stg;
+  double* sg1 = sg0 + lp * T0;
+  double* sg2 = sg1 + lp * T1;
+  double* sD = sg2 + lp * T2;
   double* sT1 = sD + nc3(lp - 1);
-  double* sT2 = sT1 + nc2(lp - 1) * kT0;
+  double* sT2 = sT1 + nc2(lp - 1) * T0;
   __syncthreads();
 
-  for (long long e = eb + warp; e < ee; e += NW) {
-    Task tk;
-    if (!make_task(__ldg(ent + e), hot_a, hot_b, lv, s, ext, &tk)) {
-      if (lane == 0) set_err(err, 1);
-      continue;
+  long long e = sb.eb + warp;
+  int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
+  long long toff = 0, coff = 0;
+  if (e < sb.ee) {
+    r0 = __ldg(task + 2 * e);
+    r1 = __ldg(task + 2 * e + 1);
+    toff = __ldg(tab_off + r0.x);
+    coff = __ldg(coef_off + r0.x);
+  }
+  for (; e < sb.ee; e += NW) {
+    int4 n0 = r0, n1 = r1;
+    if (e + NW < sb.ee) {
+      n0 = __ldg(task + 2 * (e + NW));
+      n1 = __ldg(task + 2 * (e + NW) + 1);
     }
+    const Task tk = decode_task(r0, r1);
     const int L = tk.L;
-    if (L + 1 > lp) {
-      if (lane == 0) set_err(err, 2);
-      continue;
-    }
-    const double* tb = tab + __ldg(tab_off + tk.p);
     const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
-    // stage the three 1-D factor windows and the coefficient tensor
-    {
-      const int rows = L + 1;
-      const double* t0 = tb + tk.t[0];
-      const double* t1 = tb + (L + 2) * tk.n[0] + tk.t[1];
-      const double* t2 = tb + (L + 2) * (tk.n[0] + tk.n[1]) + tk.t[2];
-      const float i0f = __frcp_rn((float)m0), i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
-      for (int it = lane; it < rows * m0; it += 32) {
-        int l = fdiv(it, i0f), i = it - l * m0;
-        sg0[l * kT0 + i] = __ldg(t0 + l * tk.n[0] + i);
-      }
-      for (int it = lane; it < rows * m1; it += 32) {
-        int l = fdiv(it, i1f), i = it - l * m1;
-        sg1[l * kT1 + i] = __ldg(t1 + l * tk.n[1] + i);
-      }
-      for (int it = lane; it < rows * m2; it += 32) {
-        int l = fdiv(it, i2f), i = it - l * m2;
-        sg2[l * kT2 + i] = __ldg(t2 + l * tk.n[2] + i);
-      }
-      const double* cp = coef + __ldg(coef_off + tk.p);
+    if (L + 1 > lp || m0 < 1 || m1 < 1 || m2 < 1 || tk.u[0] + m0 > sb.ext[0] ||
+        tk.u[1] + m1 > sb.ext[1] || tk.u[2] + m2 > sb.ext[2]) {
+      if (lane == 0) set_err(err, 1);
+    } else {
+      stage_tables<T0, T1, T2>(tab + toff, tk, L + 1, sg0, sg1, sg2, lane);
+      const double* cp = coef + coff;
       for (int c = lane; c < nc3(L); c += 32) sD[c] = __ldg(cp + c);
     }
+    // pair offsets of the next task (its record has arrived during the staging)
+    long long ntoff = toff, ncoff = coff;
+    if (e + NW < sb.ee) {
+      ntoff = __ldg(tab_off + n0.x);
+      ncoff = __ldg(coef_off + n0.x);
+    }
     __syncwarp();
-    // T1[c21](i0)
-    {
-      const float inv = __frcp_rn((float)m0);
-      const int items = nc2(L) * m0;
-      for (int it = lane; it < items; it += 32) {
-        const int c21 = fdiv(it, inv), i0 = it - c21 * m0;
-        const int dc = s_dec21[L][c21];
-        const int l2 = dc & 255, l1 = (dc >> 8) & 255, b3 = dc >> 16;
-        double acc1 = 0.0;
-        for (int l0 = 0; l0 <= L - l2 - l1; ++l0) acc1 = fma(sD[b3 + l0], sg0[l0 * kT0 + i0], acc1);
-        sT1[c21 * kT0 + i0] = acc1;
+    if (L + 1 <= lp && m0 >= 1 && m1 >= 1 && m2 >= 1 && tk.u[0] + m0 <= sb.ext[0] &&
+        tk.u[1] + m1 <= sb.ext[1] && tk.u[2] + m2 <= sb.ext[2]) {
+      // T1[c21](i0)
+      {
+        const float inv = __frcp_rn((float)m0);
+        const int items = nc2(L) * m0;
+        for (int it = lane; it < items; it += 32) {
+          const int c21 = fdiv(it, inv), i0 = it - c21 * m0;
+          const int dc = s_dec21[L][c21];
+          const int l2 = dc & 255, l1 = (dc >> 8) & 255, b3 = dc >> 16;
+          double a = 0.0;
+          for (int l0 = 0; l0 <= L - l2 - l1; ++l0) a = fma(sD[b3 + l0], sg0[l0 * T0 + i0], a);
+          sT1[c21 * T0 + i0] = a;
+        }
+      }
+      __syncwarp();
+      // T2[l2](q = i0 m1 + i1)
+      const int m01 = m0 * m1;
+      {
+        const float inv01 = __frcp_rn((float)m01), inv1 = __frcp_rn((float)m1);
+        const int items = (L + 1) * m01;
+        for (int it = lane; it < items; it += 32) {
+          const int l2 = fdiv(it, inv01), q = it - l2 * m01;
+          const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
+          const int cb = s_c21b[L][l2];
+          double a = 0.0;
+          for (int l1 = 0; l1 <= L - l2; ++l1) a = fma(sT1[(cb + l1) * T0 + i0], sg1[l1 * T1 + i1], a);
+          sT2[l2 * (T0 * T1) + q] = a;
+        }
+      }
+      __syncwarp();
+      // rho(i0,i1,i2) += sum_l2 T2[l2](q) g2[l2](i2)
+      {
+        const float inv2 = __frcp_rn((float)m2), inv1 = __frcp_rn((float)m1);
+        const int items = m01 * m2;
+        const int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
+        for (int it = lane; it < items; it += 32) {
+          const int q = fdiv(it, inv2), i2 = it - q * m2;
+          const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
+          double* a = acc + ((u0 + i0) * T1 + (u1 + i1)) * T2 + (u2 + i2);
+          double r = *a;
+          for (int l2 = 0; l2 <= L; ++l2) r = fma(sT2[l2 * (T0 * T1) + q], sg2[l2 * T2 + i2], r);
+          *a = r;
+        }
       }
     }
     __syncwarp();
-    // T2[l2](q = i0 m1 + i1)
-    const int m01 = m0 * m1;
-    {
-      const float inv01 = __frcp_rn((float)m01), inv1 = __frcp_rn((float)m1);
-      const int items = (L + 1) * m01;
-      for (int it = lane; it < items; it += 32) {
-        const int l2 = fdiv(it, inv01), q = it - l2 * m01;
-        const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
-        const int cb = s_c21b[L][l2];
-        double acc2 = 0.0;
-        for (int l1 = 0; l1 <= L - l2; ++l1)
-          acc2 = fma(sT1[(cb + l1) * kT0 + i0], sg1[l1 * kT1 + i1], acc2);
-        sT2[l2 * (kT0 * kT1) + q] = acc2;
-      }
-    }
-    __syncwarp();
-    // rho(i0,i1,i2) += sum_l2 T2[l2](q) g2[l2](i2)
-    {
-      const float inv2 = __frcp_rn((float)m2), inv1 = __frcp_rn((float)m1);
-      const int items = m01 * m2;
-      const int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
-      for (int it = lane; it < items; it += 32) {
-        const int q = fdiv(it, inv2), i2 = it - q * m2;
-        const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
-        double* a = acc + ((u0 + i0) * kT1 + (u1 + i1)) * kT2 + (u2 + i2);
-        double r = *a;
-        for (int l2 = 0; l2 <= L; ++l2) r = fma(sT2[l2 * (kT0 * kT1) + q], sg2[l2 * kT2 + i2], r);
-        *a = r;
-      }
-    }
-    __syncwarp();
+    r0 = n0;
+    r1 = n1;
+    toff = ntoff;
+    coff = ncoff;
   }
   __syncthreads();
   // sum the warp copies in warp order and write the sub-box once
   double* out = grids + lv.grid_off;
-  const int e12 = ext[1] * ext[2];
-  const int npts = ext[0] * e12;
+  const int e12 = sb.ext[1] * sb.ext[2];
+  const int npts = sb.ext[0] * e12;
   for (int pt = tid; pt < npts; pt += NW * 32) {
-    const int i0 = pt / e12, r = pt - i0 * e12, i1 = r / ext[2], i2 = r - i1 * ext[2];
-    const int ti = (i0 * kT1 + i1) * kT2 + i2;
+    const int i0 = pt / e12, r = pt - i0 * e12, i1 = r / sb.ext[2], i2 = r - i1 * sb.ext[2];
+    const int ti = (i0 * T1 + i1) * T2 + i2;
     double v = acc_all[ti];
 #pragma unroll
-    for (int w = 1; w < NW; ++w) v += acc_all[w * kTile + ti];
-    out[((long long)(s[0] + i0) * lv.N[1] + (s[1] + i1)) * lv.N[2] + (s[2] + i2)] = v;
+    for (int w = 1; w < NW; ++w) v += acc_all[w * kTileN + ti];
+    out[((long long)(sb.s[0] + i0) * lv.N[1] + (sb.s[1] + i1)) * lv.N[2] + (sb.s[2] + i2)] = v;
   }
 }
 
@@ -358,16 +404,28 @@ __global__ void __launch_bounds__(NW * 32)
 //   W[l2,l1](i0) = sum_i1 U[l2](i0,i1) g1[l1](i1)        nc2(Lx) m0 m1
 //   V[l0,l1,l2]  = sum_i0 W[l2,l1](i0) g0[l0](i0)        nc3(Lx) m0
 // and stores V for the task; the per-pair sum over tasks happens in reduce_parts_kernel
-// in a fixed order.  Lx = L + lext.
-template <int NW>
+// in a fixed order.  Lx = L + lext.  Shared rows are padded to an odd number of doubles
+// (P = T + 1) so that lanes walking different rows hit different banks.
+template <int T0, int T1, int T2>
+struct IntegLayout {
+  static constexpr int P0 = T0 + 1, P1 = T1 + 1, P2 = T2 + 1;
+  static constexpr int kSV = T0 * T1 * P2;  // padded potential tile
+  static constexpr int kUS = T1 * P0;       // one l2 slab of U: [i1][i0]
+  __host__ __device__ static int stage(int lpx) {
+    return lpx * (P0 + P1 + P2) + lpx * kUS + nc2(lpx - 1) * P0;
+  }
+};
+
+template <int T0, int T1, int T2, int NW>
 __global__ void __launch_bounds__(NW * 32)
     integrate_kernel(const KLevels K, const int2* __restrict__ work,
-                     const long long* __restrict__ sub_off, const int4* __restrict__ ent,
-                     const int4* __restrict__ hot_a, const int4* __restrict__ hot_b,
+                     const long long* __restrict__ sub_off, const int4* __restrict__ task,
                      const long long* __restrict__ tab_off, const long long* __restrict__ part_off,
                      const double* __restrict__ tab, const CoefTables* __restrict__ tabs,
                      const double* __restrict__ grids, double* __restrict__ part, int lext,
                      int lpx, int stg, int* __restrict__ err) {
+  using Lay = IntegLayout<T0, T1, T2>;
+  constexpr int P0 = Lay::P0, P1 = Lay::P1, P2 = Lay::P2, kUS = Lay::kUS;
   extern __shared__ __align__(16) double sm[];
   int* s_tab = reinterpret_cast<int*>(sm);
   const int(*s_dec21)[kNc2Max] = reinterpret_cast<const int(*)[kNc2Max]>(s_tab);
@@ -379,112 +437,106 @@ __global__ void __launch_bounds__(NW * 32)
 
   const int2 item = work[blockIdx.x];
   const LevelInfo& lv = K.lv[item.x];
-  const int sub = item.y;
-  const int j2 = sub % lv.nsb[2];
-  const int j1 = (sub / lv.nsb[2]) % lv.nsb[1];
-  const int j0 = sub / (lv.nsb[2] * lv.nsb[1]);
-  const int s[3] = {j0 * kT0, j1 * kT1, j2 * kT2};
-  const int ext[3] = {min(kT0, lv.N[0] - s[0]), min(kT1, lv.N[1] - s[1]),
-                      min(kT2, lv.N[2] - s[2])};
-  const long long eb = sub_off[lv.sub_base + sub], ee = sub_off[lv.sub_base + sub + 1];
+  const SubBox sb = sub_box<T0, T1, T2>(lv, item.y, sub_off);
   {
     const double* vin = grids + lv.grid_off;
-    const int e12 = ext[1] * ext[2];
-    const int npts = ext[0] * e12;
+    const int e12 = sb.ext[1] * sb.ext[2];
+    const int npts = sb.ext[0] * e12;
     for (int pt = tid; pt < npts; pt += NW * 32) {
-      const int i0 = pt / e12, r = pt - i0 * e12, i1 = r / ext[2], i2 = r - i1 * ext[2];
-      sv[(i0 * kT1 + i1) * kT2 + i2] =
-          __ldg(vin + ((long long)(s[0] + i0) * lv.N[1] + (s[1] + i1)) * lv.N[2] + (s[2] + i2));
+      const int i0 = pt / e12, r = pt - i0 * e12, i1 = r / sb.ext[2], i2 = r - i1 * sb.ext[2];
+      sv[(i0 * T1 + i1) * P2 + i2] = __ldg(
+          vin + ((long long)(sb.s[0] + i0) * lv.N[1] + (sb.s[1] + i1)) * lv.N[2] + (sb.s[2] + i2));
     }
   }
-  double* sg0 = sv + kTile + warp * stg;
-  double* sg1 = sg0 + lpx * kT0;
-  double* sg2 = sg1 + lpx * kT1;
-  double* sU = sg2 + lpx * kT2;
-  double* sW = sU + lpx * (kT0 * kT1);
+  double* sg0 = sv + Lay::kSV + warp * stg;
+  double* sg1 = sg0 + lpx * P0;
+  double* sg2 = sg1 + lpx * P1;
+  double* sU = sg2 + lpx * P2;
+  double* sW = sU + lpx * kUS;
   __syncthreads();
 
-  for (long long e = eb + warp; e < ee; e += NW) {
-    Task tk;
-    if (!make_task(__ldg(ent + e), hot_a, hot_b, lv, s, ext, &tk)) {
-      if (lane == 0) set_err(err, 3);
-      continue;
+  long long e = sb.eb + warp;
+  int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
+  long long toff = 0, poff = 0;
+  if (e < sb.ee) {
+    r0 = __ldg(task + 2 * e);
+    r1 = __ldg(task + 2 * e + 1);
+    toff = __ldg(tab_off + r0.x);
+    poff = __ldg(part_off + r0.x);
+  }
+  for (; e < sb.ee; e += NW) {
+    int4 n0 = r0, n1 = r1;
+    if (e + NW < sb.ee) {
+      n0 = __ldg(task + 2 * (e + NW));
+      n1 = __ldg(task + 2 * (e + NW) + 1);
     }
+    const Task tk = decode_task(r0, r1);
     const int L = tk.L, Lx = L + lext;
-    if (Lx + 1 > lpx) {
-      if (lane == 0) set_err(err, 4);
-      continue;
-    }
-    const double* tb = tab + __ldg(tab_off + tk.p);
     const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
-    {
-      const int rows = Lx + 1;
-      const double* t0 = tb + tk.t[0];
-      const double* t1 = tb + (L + 2) * tk.n[0] + tk.t[1];
-      const double* t2 = tb + (L + 2) * (tk.n[0] + tk.n[1]) + tk.t[2];
-      const float i0f = __frcp_rn((float)m0), i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
-      for (int it = lane; it < rows * m0; it += 32) {
-        int l = fdiv(it, i0f), i = it - l * m0;
-        sg0[l * kT0 + i] = __ldg(t0 + l * tk.n[0] + i);
+    const bool ok = Lx + 1 <= lpx && m0 >= 1 && m1 >= 1 && m2 >= 1 && tk.u[0] + m0 <= sb.ext[0] &&
+                    tk.u[1] + m1 <= sb.ext[1] && tk.u[2] + m2 <= sb.ext[2];
+    if (ok) stage_tables<P0, P1, P2>(tab + toff, tk, Lx + 1, sg0, sg1, sg2, lane);
+    else if (lane == 0) set_err(err, 3);
+    long long ntoff = toff, npoff = poff;
+    if (e + NW < sb.ee) {
+      ntoff = __ldg(tab_off + n0.x);
+      npoff = __ldg(part_off + n0.x);
+    }
+    __syncwarp();
+    if (ok) {
+      const int m01 = m0 * m1;
+      // U[l2](i1, i0): lanes walk consecutive i1 (rows P2 apart: conflict free)
+      {
+        const float inv01 = __frcp_rn((float)m01), inv1 = __frcp_rn((float)m1);
+        const int items = (Lx + 1) * m01;
+        const int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
+        for (int it = lane; it < items; it += 32) {
+          const int l2 = fdiv(it, inv01), q = it - l2 * m01;
+          const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
+          const double* vr = sv + ((u0 + i0) * T1 + (u1 + i1)) * P2 + u2;
+          const double* gr = sg2 + l2 * P2;
+          double a = 0.0;
+          for (int i2 = 0; i2 < m2; ++i2) a = fma(vr[i2], gr[i2], a);
+          sU[l2 * kUS + i1 * P0 + i0] = a;
+        }
       }
-      for (int it = lane; it < rows * m1; it += 32) {
-        int l = fdiv(it, i1f), i = it - l * m1;
-        sg1[l * kT1 + i] = __ldg(t1 + l * tk.n[1] + i);
+      __syncwarp();
+      // W[c21](i0): lanes walk consecutive i0
+      {
+        const float inv0 = __frcp_rn((float)m0);
+        const int items = nc2(Lx) * m0;
+        for (int it = lane; it < items; it += 32) {
+          const int c21 = fdiv(it, inv0), i0 = it - c21 * m0;
+          const int dc = s_dec21[Lx][c21];
+          const int l2 = dc & 255, l1 = (dc >> 8) & 255;
+          const double* ur = sU + l2 * kUS + i0;
+          const double* gr = sg1 + l1 * P1;
+          double a = 0.0;
+          for (int i1 = 0; i1 < m1; ++i1) a = fma(ur[i1 * P0], gr[i1], a);
+          sW[c21 * P0 + i0] = a;
+        }
       }
-      for (int it = lane; it < rows * m2; it += 32) {
-        int l = fdiv(it, i2f), i = it - l * m2;
-        sg2[l * kT2 + i] = __ldg(t2 + l * tk.n[2] + i);
+      __syncwarp();
+      // V[c] -> task slot
+      {
+        const int nc = nc3(Lx);
+        double* dst = part + poff + (long long)tk.rank * nc;
+        for (int c = lane; c < nc; c += 32) {
+          const int dc = s_dec3[Lx][c];
+          const int c21 = dc & 255, l0 = dc >> 8;
+          const double* wr = sW + c21 * P0;
+          const double* gr = sg0 + l0 * P0;
+          double a = 0.0;
+          for (int i0 = 0; i0 < m0; ++i0) a = fma(wr[i0], gr[i0], a);
+          dst[c] = a;
+        }
       }
     }
     __syncwarp();
-    const int m01 = m0 * m1;
-    // U[l2](q)
-    {
-      const float inv01 = __frcp_rn((float)m01), inv1 = __frcp_rn((float)m1);
-      const int items = (Lx + 1) * m01;
-      const int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
-      for (int it = lane; it < items; it += 32) {
-        const int l2 = fdiv(it, inv01), q = it - l2 * m01;
-        const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
-        const double* vr = sv + ((u0 + i0) * kT1 + (u1 + i1)) * kT2 + u2;
-        const double* gr = sg2 + l2 * kT2;
-        double a = 0.0;
-        for (int i2 = 0; i2 < m2; ++i2) a = fma(vr[i2], gr[i2], a);
-        sU[l2 * (kT0 * kT1) + q] = a;
-      }
-    }
-    __syncwarp();
-    // W[c21](i0)
-    {
-      const float inv0 = __frcp_rn((float)m0);
-      const int items = nc2(Lx) * m0;
-      for (int it = lane; it < items; it += 32) {
-        const int c21 = fdiv(it, inv0), i0 = it - c21 * m0;
-        const int dc = s_dec21[Lx][c21];
-        const int l2 = dc & 255, l1 = (dc >> 8) & 255;
-        const double* ur = sU + l2 * (kT0 * kT1) + i0 * m1;
-        const double* gr = sg1 + l1 * kT1;
-        double a = 0.0;
-        for (int i1 = 0; i1 < m1; ++i1) a = fma(ur[i1], gr[i1], a);
-        sW[c21 * kT0 + i0] = a;
-      }
-    }
-    __syncwarp();
-    // V[c] -> task slot
-    {
-      const int nc = nc3(Lx);
-      double* dst = part + __ldg(part_off + tk.p) + (long long)tk.rank * nc;
-      for (int c = lane; c < nc; c += 32) {
-        const int dc = s_dec3[Lx][c];
-        const int c21 = dc & 255, l0 = dc >> 8;
-        const double* wr = sW + c21 * kT0;
-        const double* gr = sg0 + l0 * kT0;
-        double a = 0.0;
-        for (int i0 = 0; i0 < m0; ++i0) a = fma(wr[i0], gr[i0], a);
-        dst[c] = a;
-      }
-    }
-    __syncwarp();
+    r0 = n0;
+    r1 = n1;
+    toff = ntoff;
+    poff = npoff;
   }
 }
 
@@ -544,14 +596,14 @@ __global__ void assemble_V_kernel(long long ngroups, const int4* __restrict__ gr
                                   const double* __restrict__ geo, const double* __restrict__ pref,
                                   const long long* __restrict__ coef_off,
                                   const double* __restrict__ coef,
-                                  const CoefTables* __restrict__ tabs, int nao,
+                                  const CoefTables* __restrict__ tabs, int nao, int lext,
                                   double* __restrict__ V) {
   const int lane = threadIdx.x & 31;
   long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (gw >= ngroups) return;
   const int4 gr = groups[gw];
   const int4 id0 = ids[gr.z];
-  const int la = id0.x, lb = id0.y, L = la + lb;
+  const int la = id0.x, lb = id0.y, Lx = la + lb + lext;
   const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
   const bool diag = gr.x == gr.y;
   for (int el = lane; el < na * nb; el += 32) {
@@ -572,12 +624,12 @@ __global__ void assemble_V_kernel(long long ngroups, const int4* __restrict__ gr
         pw[d][3] = ab * ab * ab;
       }
       const double* Vp = coef + coef_off[p];
-      double x = contract_elem(ca, cb, pw, Vp, L, tabs->dec21, tabs->c21base);
+      double x = contract_elem(ca, cb, pw, Vp, Lx, tabs->dec21, tabs->c21base);
       if (diag && ids2[p].z == 2) {
         int ca2[3], cb2[3];
         cart_comp(la, nu, ca2);
         cart_comp(lb, mu, cb2);
-        x += contract_elem(ca2, cb2, pw, Vp, L, tabs->dec21, tabs->c21base);
+        x += contract_elem(ca2, cb2, pw, Vp, Lx, tabs->dec21, tabs->c21base);
       }
       tot += pref[p] * x;
     }
@@ -606,7 +658,9 @@ __global__ void grad_pair_kernel(long long np, const int4* __restrict__ ids,
                                  const double* __restrict__ coef,
                                  const CoefTables* __restrict__ tabs, const double* __restrict__ D,
                                  int nao, double* __restrict__ pgrad) {
-  long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  // one warp per pair, lanes over the (mu, nu) elements of its D block
+  const int lane = threadIdx.x & 31;
+  const long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   if (p >= np) return;
   const int4 id = ids[p];
   const int la = id.x, lb = id.y, Lx = la + lb + 1;
@@ -623,49 +677,50 @@ __global__ void grad_pair_kernel(long long np, const int4* __restrict__ ids,
   const double* Vp = coef + coef_off[p];
   const double scale = (double)ids2[p].z * pref[p];
   double out[6] = {0, 0, 0, 0, 0, 0};
-  for (int mu = 0; mu < na; ++mu) {
-    int ca[3];
+  for (int el = lane; el < na * nb; el += 32) {
+    const int mu = el / nb, nu = el - mu * nb;
+    int ca[3], cb[3];
     cart_comp(la, mu, ca);
-    const double* Drow = D + (long long)(id.z + mu) * nao + id.w;
-    for (int nu = 0; nu < nb; ++nu) {
-      int cb[3];
-      cart_comp(lb, nu, cb);
-      const double dmn = scale * Drow[nu];
-      if (dmn == 0.0) continue;
-      double e[3][8];
+    cart_comp(lb, nu, cb);
+    const double dmn = scale * D[(long long)(id.z + mu) * nao + id.w + nu];
+    double e[3][8];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) expand_1d(ca[d], cb[d], pw[d], e[d], 7);
-      for (int side = 0; side < 2; ++side)
-        for (int dir = 0; dir < 3; ++dir) {
-          double c[8], t1[8], t2[8];
-          if (side == 0) {
-            expand_1d(ca[dir] - 1, cb[dir], pw[dir], t1, 7);
-            expand_1d(ca[dir] + 1, cb[dir], pw[dir], t2, 7);
-            for (int k = 0; k < 8; ++k) c[k] = -(double)ca[dir] * t1[k] + 2.0 * aa * t2[k];
-          } else {
-            expand_1d(ca[dir], cb[dir] - 1, pw[dir], t1, 7);
-            expand_1d(ca[dir], cb[dir] + 1, pw[dir], t2, 7);
-            for (int k = 0; k < 8; ++k) c[k] = -(double)cb[dir] * t1[k] + 2.0 * ab * t2[k];
-          }
-          const double* c0 = dir == 0 ? c : e[0];
-          const double* c1 = dir == 1 ? c : e[1];
-          const double* c2 = dir == 2 ? c : e[2];
-          double s = 0.0;
-          for (int k2 = 0; k2 <= Lx; ++k2) {
-            if (c2[k2] == 0.0) continue;
-            for (int k1 = 0; k1 <= Lx - k2; ++k1) {
-              if (c1[k1] == 0.0) continue;
-              const int base = tabs->dec21[Lx][tabs->c21base[Lx][k2] + k1] >> 16;
-              double s0 = 0.0;
-              for (int k0 = 0; k0 <= Lx - k2 - k1; ++k0) s0 += c0[k0] * Vp[base + k0];
-              s += c2[k2] * c1[k1] * s0;
-            }
-          }
-          out[3 * side + dir] += dmn * s;
+    for (int d = 0; d < 3; ++d) expand_1d(ca[d], cb[d], pw[d], e[d], 7);
+    for (int side = 0; side < 2; ++side)
+      for (int dir = 0; dir < 3; ++dir) {
+        double c[8], t1[8], t2[8];
+        if (side == 0) {
+          expand_1d(ca[dir] - 1, cb[dir], pw[dir], t1, 7);
+          expand_1d(ca[dir] + 1, cb[dir], pw[dir], t2, 7);
+          for (int k = 0; k < 8; ++k) c[k] = -(double)ca[dir] * t1[k] + 2.0 * aa * t2[k];
+        } else {
+          expand_1d(ca[dir], cb[dir] - 1, pw[dir], t1, 7);
+          expand_1d(ca[dir], cb[dir] + 1, pw[dir], t2, 7);
+          for (int k = 0; k < 8; ++k) c[k] = -(double)cb[dir] * t1[k] + 2.0 * ab * t2[k];
         }
-    }
+        const double* c0 = dir == 0 ? c : e[0];
+        const double* c1 = dir == 1 ? c : e[1];
+        const double* c2 = dir == 2 ? c : e[2];
+        double sacc = 0.0;
+        for (int k2 = 0; k2 <= Lx; ++k2) {
+          if (c2[k2] == 0.0) continue;
+          for (int k1 = 0; k1 <= Lx - k2; ++k1) {
+            if (c1[k1] == 0.0) continue;
+            const int base = tabs->dec21[Lx][tabs->c21base[Lx][k2] + k1] >> 16;
+            double s0 = 0.0;
+            for (int k0 = 0; k0 <= Lx - k2 - k1; ++k0) s0 += c0[k0] * Vp[base + k0];
+            sacc += c2[k2] * c1[k1] * s0;
+          }
+        }
+        out[3 * side + dir] += dmn * sacc;
+      }
   }
-  for (int i = 0; i < 6; ++i) pgrad[6 * p + i] = out[i];
+#pragma unroll
+  for (int i = 0; i < 6; ++i) {
+    double v = out[i];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (lane == 0) pgrad[6 * p + i] = v;
+  }
 }
 
 __global__ void grad_atom_kernel(int natm, const long long* __restrict__ atom_off,
@@ -836,18 +891,30 @@ __global__ void energy_final_kernel(const double* __restrict__ red, int nparts,
   if (threadIdx.x == 0) *out = s;
 }
 
-template <int NW>
-size_t colloc_smem(int stg) {
-  return sizeof(int) * kTabInts + sizeof(double) * (size_t)NW * (kTile + stg);
-}
-template <int NW>
-size_t integ_smem(int stg) {
-  return sizeof(int) * kTabInts + sizeof(double) * ((size_t)kTile + (size_t)NW * stg);
-}
-
 int even(int x) { return (x + 1) & ~1; }
 
+constexpr int kNW = 8;
+
+#define GPW_TILE_SHAPES(X) X(8, 8, 16) X(4, 8, 32) X(8, 8, 32) X(4, 8, 64)
+
+template <int T0, int T1, int T2>
+size_t colloc_smem(int stg) {
+  return sizeof(int) * kTabInts + sizeof(double) * (size_t)kNW * (T0 * T1 * T2 + stg);
+}
+template <int T0, int T1, int T2>
+size_t integ_smem(int stg) {
+  return sizeof(int) * kTabInts + sizeof(double) * ((size_t)IntegLayout<T0, T1, T2>::kSV + (size_t)kNW * stg);
+}
+
 }  // namespace
+
+extern "C" int gpw_tile_supported(int t0, int t1, int t2) {
+#define GPW_TILE_CHECK(a, b, c) \
+  if (t0 == a && t1 == b && t2 == c) return 1;
+  GPW_TILE_SHAPES(GPW_TILE_CHECK)
+#undef GPW_TILE_CHECK
+  return 0;
+}
 
 KLevels make_klevels(const Plan& p) {
   KLevels k;
@@ -858,34 +925,47 @@ KLevels make_klevels(const Plan& p) {
 
 cudaError_t configure_kernels(Plan* p) {
   const int lp = p->lmax + 1;
-  p->stg_colloc = even(lp * (kT0 + kT1 + kT2) + nc3(p->lmax) + nc2(p->lmax) * kT0 + lp * kT0 * kT1);
-  for (int lext = 0; lext <= 1; ++lext) {
-    const int lpx = p->lmax + lext + 1;
-    int stg = even(lpx * (kT0 + kT1 + kT2) + lpx * kT0 * kT1 + nc2(p->lmax + lext) * kT0);
-    if (lext == 0) p->stg_integ = stg; else p->stg_integ1 = stg;
+  const int t0 = p->tile[0], t1 = p->tile[1], t2 = p->tile[2];
+  bool found = false;
+#define GPW_TILE_CONF(a, b, c)                                                      \
+  if (t0 == a && t1 == b && t2 == c) {                                              \
+    found = true;                                                                   \
+    p->stg_colloc = even(CollocLayout<a, b, c>::stage(lp));                         \
+    p->stg_integ = even(IntegLayout<a, b, c>::stage(p->lmax + 1));                  \
+    p->stg_integ1 = even(IntegLayout<a, b, c>::stage(p->lmax + 2));                 \
+    p->smem_colloc = colloc_smem<a, b, c>(p->stg_colloc);                           \
+    p->smem_integ = integ_smem<a, b, c>(p->stg_integ);                              \
+    p->smem_integ1 = integ_smem<a, b, c>(p->stg_integ1);                            \
   }
-  p->nw_colloc = 8;
-  p->nw_integ = 8;
-  p->smem_colloc = colloc_smem<8>(p->stg_colloc);
-  p->smem_integ = integ_smem<8>(p->stg_integ);
-  p->smem_integ1 = integ_smem<8>(p->stg_integ1);
+  GPW_TILE_SHAPES(GPW_TILE_CONF)
+#undef GPW_TILE_CONF
+  if (!found) return cudaErrorInvalidValue;
+  p->nw_colloc = kNW;
+  p->nw_integ = kNW;
   // the attribute is per function and shared by all plans: raise it to the device
-  // maximum once, the launch itself asks for what this plan needs
+  // maximum, each launch asks for what its plan needs
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   if ((size_t)optin < std::max(p->smem_colloc, std::max(p->smem_integ, p->smem_integ1)))
     return cudaErrorInvalidValue;
-  e = cudaFuncSetAttribute(collocate_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+#define GPW_TILE_ATTR(a, b, c)                                                                    \
+  e = cudaFuncSetAttribute(collocate_kernel<a, b, c, kNW>,                                        \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, optin);                   \
+  if (e != cudaSuccess) return e;                                                                 \
+  e = cudaFuncSetAttribute(integrate_kernel<a, b, c, kNW>,                                        \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, optin);                   \
   if (e != cudaSuccess) return e;
-  e = cudaFuncSetAttribute(integrate_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
-  return e;
+  GPW_TILE_SHAPES(GPW_TILE_ATTR)
+#undef GPW_TILE_ATTR
+  return cudaSuccess;
 }
 
 cudaError_t launch_tables(const Plan& p, cudaStream_t s) {
   if (p.npairs == 0) return cudaSuccess;
   long long blocks = std::min<long long>((p.npairs + 7) / 8, 152LL * 64);
+  ++p.launches;
   tables_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, make_klevels(p), p.d.hot_a, p.d.hot_b,
                                              p.d.geo, p.d.cab, p.d.tab_off, p.d.tab, p.d.pref);
   return cudaGetLastError();
@@ -893,6 +973,7 @@ cudaError_t launch_tables(const Plan& p, cudaStream_t s) {
 
 cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s) {
   if (p.npairs == 0) return cudaSuccess;
+  ++p.launches;
   pair_coef_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
       p.npairs, p.d.hot_a, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, p.d.tabs, D,
       p.nao, p.d.coef);
@@ -901,47 +982,68 @@ cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s) {
 
 cudaError_t launch_collocate(const Plan& p, cudaStream_t s) {
   if (p.nwork == 0) return cudaSuccess;
-  collocate_kernel<8><<<(int)p.nwork, 8 * 32, p.smem_colloc, s>>>(
-      make_klevels(p), p.d.work, p.d.sub_off, p.d.ent, p.d.hot_a, p.d.hot_b, p.d.tab_off,
-      p.d.coef_off, p.d.tab, p.d.coef, p.d.tabs, p.d.grids, p.lmax + 1, p.stg_colloc, p.d.err);
-  return cudaGetLastError();
+  const int t0 = p.tile[0], t1 = p.tile[1], t2 = p.tile[2];
+  ++p.launches;
+#define GPW_TILE_COLLOC(a, b, c)                                                           \
+  if (t0 == a && t1 == b && t2 == c) {                                                     \
+    collocate_kernel<a, b, c, kNW><<<(int)p.nwork, kNW * 32, p.smem_colloc, s>>>(          \
+        make_klevels(p), p.d.work, p.d.sub_off, p.d.task, p.d.tab_off, p.d.coef_off,        \
+        p.d.tab, p.d.coef, p.d.tabs, p.d.grids, p.lmax + 1, p.stg_colloc, p.d.err);         \
+    return cudaGetLastError();                                                             \
+  }
+  GPW_TILE_SHAPES(GPW_TILE_COLLOC)
+#undef GPW_TILE_COLLOC
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s) {
   if (p.nwork == 0) return cudaSuccess;
-  integrate_kernel<8><<<(int)p.nwork, 8 * 32, lext ? p.smem_integ1 : p.smem_integ, s>>>(
-      make_klevels(p), p.d.work, p.d.sub_off, p.d.ent, p.d.hot_a, p.d.hot_b, p.d.tab_off,
-      p.d.part_off, p.d.tab, p.d.tabs, p.d.grids, p.d.part, lext, p.lmax + lext + 1,
-      lext ? p.stg_integ1 : p.stg_integ, p.d.err);
-  return cudaGetLastError();
+  const int t0 = p.tile[0], t1 = p.tile[1], t2 = p.tile[2];
+  ++p.launches;
+#define GPW_TILE_INTEG(a, b, c)                                                            \
+  if (t0 == a && t1 == b && t2 == c) {                                                     \
+    integrate_kernel<a, b, c, kNW><<<(int)p.nwork, kNW * 32,                               \
+                                     lext ? p.smem_integ1 : p.smem_integ, s>>>(            \
+        make_klevels(p), p.d.work, p.d.sub_off, p.d.task, p.d.tab_off, p.d.part_off,        \
+        p.d.tab, p.d.tabs, p.d.grids, p.d.part, lext, p.lmax + lext + 1,                    \
+        lext ? p.stg_integ1 : p.stg_integ, p.d.err);                                       \
+    return cudaGetLastError();                                                             \
+  }
+  GPW_TILE_SHAPES(GPW_TILE_INTEG)
+#undef GPW_TILE_INTEG
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s) {
   if (p.npairs == 0) return cudaSuccess;
   long long blocks = std::min<long long>((p.npairs + 7) / 8, 152LL * 64);
+  ++p.launches;
   reduce_parts_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, make_klevels(p), p.d.hot_a, p.d.hot_b,
                                                   p.d.ids2, p.d.part_off, p.d.coef_off, p.d.part,
                                                   p.d.coef, lext);
   return cudaGetLastError();
 }
 
-cudaError_t launch_assemble_V(const Plan& p, double* V, cudaStream_t s) {
+cudaError_t launch_assemble_V(const Plan& p, int lext, double* V, cudaStream_t s) {
   cudaError_t e = cudaMemsetAsync(V, 0, sizeof(double) * (size_t)p.nao * p.nao, s);
   if (e != cudaSuccess || p.ngroups == 0) return e;
+  ++p.launches;
   assemble_V_kernel<<<(int)((p.ngroups + 7) / 8), 256, 0, s>>>(
       p.ngroups, p.d.groups, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, p.d.coef,
-      p.d.tabs, p.nao, V);
+      p.d.tabs, p.nao, lext, V);
   return cudaGetLastError();
 }
 
 cudaError_t launch_grad(const Plan& p, const double* D, double* grad, cudaStream_t s) {
   if (p.npairs > 0) {
-    grad_pair_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
+    ++p.launches;
+    grad_pair_kernel<<<(int)((p.npairs + 7) / 8), 256, 0, s>>>(
         p.npairs, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, p.d.coef, p.d.tabs, D,
         p.nao, p.d.pgrad);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
+  ++p.launches;
   grad_atom_kernel<<<(3 * p.natm + 127) / 128, 128, 0, s>>>(p.natm, p.d.atom_off, p.d.atom_list,
                                                             p.d.pgrad, grad);
   return cudaGetLastError();
@@ -949,30 +1051,35 @@ cudaError_t launch_grad(const Plan& p, const double* D, double* grad, cudaStream
 
 cudaError_t launch_combine(const Plan& p, cudaStream_t s) {
   Cell c{{p.L[0], p.L[1], p.L[2]}};
+  ++p.launches;
   combine_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p), c, p.d.spec, p.d.fspec);
   return cudaGetLastError();
 }
 
 cudaError_t launch_restrict(const Plan& p, int level, cudaStream_t s) {
   Cell c{{p.L[0], p.L[1], p.L[2]}};
+  ++p.launches;
   restrict_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p), c, level, p.d.fspec, p.d.spec);
   return cudaGetLastError();
 }
 
 cudaError_t launch_poisson(const Plan& p, cudaStream_t s) {
   Cell c{{p.L[0], p.L[1], p.L[2]}};
+  ++p.launches;
   poisson_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(make_klevels(p), c, p.omega, p.d.fspec, p.d.red);
   return cudaGetLastError();
 }
 
 cudaError_t launch_lda(const Plan& p, const double* rho, const double* vH, double* v_out,
                        cudaStream_t s) {
+  ++p.launches;
   lda_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(p.fine_n, p.omega / (double)p.fine_n, rho, vH, v_out,
                                                 p.d.red + kRedBlocks);
   return cudaGetLastError();
 }
 
 cudaError_t launch_energy_final(const Plan& p, int slot, int nparts, cudaStream_t s) {
+  ++p.launches;
   energy_final_kernel<<<1, kRedThreads, 0, s>>>(p.d.red + slot * kRedBlocks, nparts,
                                                 p.d.energies + slot);
   return cudaGetLastError();

@@ -17,7 +17,7 @@ cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s);
 cudaError_t launch_collocate(const Plan& p, cudaStream_t s);
 cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s);
 cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s);
-cudaError_t launch_assemble_V(const Plan& p, double* V, cudaStream_t s);
+cudaError_t launch_assemble_V(const Plan& p, int lext, double* V, cudaStream_t s);
 cudaError_t launch_grad(const Plan& p, const double* D, double* grad, cudaStream_t s);
 cudaError_t launch_combine(const Plan& p, cudaStream_t s);
 cudaError_t launch_restrict(const Plan& p, int level, cudaStream_t s);

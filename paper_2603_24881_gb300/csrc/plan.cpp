@@ -166,6 +166,13 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   }
   const int K = desc->nlevels;
   plan->nlev = K;
+  if (desc->tile[0] || desc->tile[1] || desc->tile[2]) {
+    if (!gpw_tile_supported(desc->tile[0], desc->tile[1], desc->tile[2])) {
+      set_error("gpw_plan: unsupported tile shape");
+      return GPW_EINVAL;
+    }
+    for (int d = 0; d < 3; ++d) plan->tile[d] = desc->tile[d];
+  }
   plan->natm = desc->natm;
   plan->nshell = desc->nshell;
   plan->coords.assign(desc->coords, desc->coords + 3 * desc->natm);
@@ -213,8 +220,7 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
         return GPW_EINVAL;
       }
     }
-    const int T[3] = {kT0, kT1, kT2};
-    for (int d = 0; d < 3; ++d) lv.nsb[d] = (lv.N[d] + T[d] - 1) / T[d];
+    for (int d = 0; d < 3; ++d) lv.nsb[d] = (lv.N[d] + plan->tile[d] - 1) / plan->tile[d];
     lv.weight = plan->omega / ((double)lv.N[0] * lv.N[1] * lv.N[2]);
   }
   for (int k = 1; k < K; ++k)
@@ -434,7 +440,7 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   }
   plan->nsub_total = nsub;
   std::vector<long long> count(nsub + 1, 0);
-  const int T[3] = {kT0, kT1, kT2};
+  const int T[3] = {plan->tile[0], plan->tile[1], plan->tile[2]};
   std::vector<Seg> sg[3];
   for (long long p = 0; p < np; ++p) {
     const PairTmp& t = pairs[p];
@@ -449,28 +455,50 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   const long long nent = count[nsub];
   plan->nent = nent;
   H->sub_off = count;
-  H->ent.resize(nent);
+  H->task.resize(2 * nent);
   std::vector<long long> fill(count.begin(), count.end() - 1);
   long long part_total = 0;
   for (long long p = 0; p < np; ++p) {
     const PairTmp& t = pairs[p];
     const LevelInfo& lv = plan->lev[t.level];
     for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
+    const int L = H->hot_a[p].w;
+    int n[3];
+    for (int d = 0; d < 3; ++d) {
+      n[d] = t.hi[d] - t.lo[d] + 1;
+      if (n[d] > 65535) {
+        set_error("gpw_plan: pair box longer than 65535 grid points");
+        return GPW_ERANGE;
+      }
+    }
     int rank = 0;
+    // intersection of the pair box with the copy k of sub-box j along one dimension
+    auto isect = [&](int d, const Seg& sgm, int* m, int* u, int* tt) {
+      long long s0 = (long long)sgm.j * T[d];
+      long long ext = std::min<long long>(T[d], lv.N[d] - s0);
+      long long o = (long long)sgm.k * lv.N[d] + s0;
+      long long a = std::max<long long>(t.lo[d], o);
+      long long b = std::min<long long>(t.hi[d], o + ext - 1);
+      *m = (int)(b - a + 1);
+      *u = (int)(a - o);
+      *tt = (int)(a - t.lo[d]);
+    };
     for (auto& s0 : sg[0])
       for (auto& s1 : sg[1])
         for (auto& s2 : sg[2]) {
-          if (s0.k < -512 || s0.k > 511 || s1.k < -512 || s1.k > 511 || s2.k < -512 || s2.k > 511) {
-            set_error("gpw_plan: pair box wraps the cell more than 511 times");
-            return GPW_ERANGE;
-          }
-          int kpack = (s0.k + 512) | ((s1.k + 512) << 10) | ((s2.k + 512) << 20);
+          int m[3], u[3], tt[3];
+          isect(0, s0, &m[0], &u[0], &tt[0]);
+          isect(1, s1, &m[1], &u[1], &tt[1]);
+          isect(2, s2, &m[2], &u[2], &tt[2]);
           long long sub = lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j;
-          H->ent[fill[sub]++] = make_int4((int)p, kpack, rank, 0);
+          long long slot = fill[sub]++;
+          H->task[2 * slot] = make_int4((int)p, m[0] | (m[1] << 8) | (m[2] << 16) | (L << 24),
+                                        u[0] | (u[1] << 8) | (u[2] << 16), rank);
+          H->task[2 * slot + 1] = make_int4(tt[0] | (n[0] << 16), tt[1] | (n[1] << 16),
+                                            tt[2] | (n[2] << 16), 0);
           ++rank;
         }
     H->ids2[p].w = rank;
-    int L = H->hot_a[p].w;
     H->part_off[p] = part_total;
     part_total += (long long)rank * nc3(L + 1);
   }

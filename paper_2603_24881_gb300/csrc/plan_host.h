@@ -11,7 +11,7 @@ struct HostArrays {
   std::vector<int4> hot_a, hot_b, ids, ids2;
   std::vector<double> geo, cab;
   std::vector<long long> tab_off, coef_off, part_off;
-  std::vector<int4> ent;
+  std::vector<int4> task;   // 2 per task
   std::vector<long long> sub_off;
   std::vector<int2> work;
   std::vector<int4> groups;

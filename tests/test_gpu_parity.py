@@ -203,3 +203,39 @@ def test_invalid_inputs(gpw):
     bad2.shell_l[0] = 4
     with pytest.raises(gpw.GpwError):
         gpw.Plan(bad2)
+
+
+@pytest.mark.parametrize("name", ["tiny", "resolved", "water4"])
+def test_fock_grad_fused(gpw, cases, name):
+    # one integration pass at degree L+1 gives V and the gradient
+    s, op = cases[name]
+    gp = gpw.Plan(s)
+    out = gp.fock_grad(s.D)
+    ref = op.fock(s.D)
+    gref = op.grad_levels(s.D, ref["v_levels"])
+    assert abs(out["EH"] - ref["EH"]) <= 1e-8
+    assert abs(out["Ex"] - ref["Ex"]) <= 1e-8
+    assert _rel(out["V"].cpu().numpy(), ref["V"]) <= RTOL
+    assert np.max(np.abs(out["grad"].cpu().numpy() - gref)) <= 1e-7
+
+
+@pytest.mark.parametrize("tile", [(4, 8, 32), (8, 8, 32), (4, 8, 64)])
+def test_tile_shapes(gpw, cases, tile):
+    s, op = cases["water4"]
+    gp = gpw.Plan(s, tile=tile)
+    assert gp.stats()["tile"] == tile
+    rl = [x.cpu().numpy() for x in gp.eval_rho_levels(s.D)]
+    ref = op.rho_levels(s.D)
+    scale = max(np.max(np.abs(r)) for r in ref)
+    for x, y in zip(rl, ref):
+        assert np.max(np.abs(x - y)) <= RTOL * scale
+    out = gp.fock_grad(s.D)
+    r = op.fock(s.D)
+    assert _rel(out["V"].cpu().numpy(), r["V"]) <= RTOL
+    assert np.max(np.abs(out["grad"].cpu().numpy() - op.grad_levels(s.D, r["v_levels"]))) <= 1e-7
+    assert gp.check_device() == 0
+
+
+def test_unsupported_tile(gpw):
+    with pytest.raises(gpw.GpwError):
+        gpw.Plan(workloads.tiny(), tile=(3, 8, 16))
