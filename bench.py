@@ -62,7 +62,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-stride", type=int, default=8)
-    ap.add_argument("--tile", default=None, help="sub-box shape t0,t1,t2 (default: tuned)")
+    ap.add_argument("--tile", default=None, help="collocation sub-box t0,t1,t2")
+    ap.add_argument("--tile-integ", default=None, help="integration sub-box t0,t1,t2")
     return ap.parse_args()
 
 
@@ -204,7 +205,8 @@ def main():
     s = workloads.config(a.workload)
     t0 = time.perf_counter()
     tile = tuple(int(x) for x in a.tile.split(",")) if a.tile else None
-    plan = gpw.Plan(s, tile=tile)
+    tile_i = tuple(int(x) for x in a.tile_integ.split(",")) if a.tile_integ else None
+    plan = gpw.Plan(s, tile=tile, tile_integ=tile_i)
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0)
     st = plan.stats()
@@ -303,7 +305,7 @@ def main():
                 "config": {"workload": WORKLOAD_DESC, "pairs": st["npairs"],
                            "pair_points": st["pair_points"], "tasks": st["nentries"],
                            "l2": "no flush: plan tables, tasks and grids (>2 GB) exceed L2",
-                           "tile": list(st["tile"]),
+                           "tile": list(st["tile"]), "tile_integ": list(st["tile_integ"]),
                            "parallelism": f"replicas x{world}"},
                 "pct_of_fp64_peak": 100.0 * value / world / FP64_PEAK_TFLOPS,
                 "pair_points_per_s": st["pair_points"] * a.steps * world / (ms * 1e-3),

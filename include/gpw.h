@@ -86,9 +86,11 @@ typedef struct {
                                  with E_k >= rel_cutoff * alpha_p (40 if <= 0) */
   double tau;                 /* screening threshold of Eq. (cut) */
   int flags;                  /* GPW_STRICT */
-  int tile[3];                /* sub-box owned by one thread block (grid points along
-                                 a1, a2, a3); {0,0,0} = default {8,8,16}.  Supported:
-                                 see gpw_tile_supported. */
+  int tile[3];                /* sub-box owned by one collocation thread block (grid
+                                 points along a1, a2, a3); {0,0,0} = default {8,8,16} */
+  int tile_integ[3];          /* sub-box of one integration thread block;
+                                 {0,0,0} = default {4,8,64}.  Supported shapes:
+                                 gpw_tile_supported. */
 } gpw_desc;
 
 /* Sizes and work counts of a plan (gpw_plan_query). */
@@ -106,7 +108,9 @@ typedef struct {
   double flops_rho;    /* model FP64 flops of one eval_rho grid pass: 2 (L+1) per pair-point */
   double flops_mat;    /* same for eval_mat */
   double flops_ip1;    /* 2 (L+2) per pair-point for eval_mat_ip1 */
-  int tile[3];         /* sub-box edge owned by one thread block */
+  int tile[3];         /* collocation sub-box */
+  int tile_integ[3];   /* integration sub-box */
+  long long nentries_integ;  /* tasks of the integration sub-box lists */
 } gpw_plan_info;
 
 /* Build a plan: normalise primitives, screen pairs (Eq. cut; pairs a <= b over images T

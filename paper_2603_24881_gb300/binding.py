@@ -46,7 +46,8 @@ class Desc(ctypes.Structure):
                 ("cutoff_ha", ctypes.c_double), ("nlevels", ctypes.c_int),
                 ("level_ratio", ctypes.c_double), ("meshes", ctypes.c_void_p),
                 ("rel_cutoff", ctypes.c_double), ("tau", ctypes.c_double),
-                ("flags", ctypes.c_int), ("tile", ctypes.c_int * 3)]
+                ("flags", ctypes.c_int), ("tile", ctypes.c_int * 3),
+                ("tile_integ", ctypes.c_int * 3)]
 
 TILES = [(8, 8, 16), (4, 8, 32), (8, 8, 32), (4, 8, 64)]
 
@@ -62,7 +63,8 @@ class Info(ctypes.Structure):
                 ("pair_points_L", ctypes.c_longlong * 8), ("nentries", ctypes.c_longlong),
                 ("device_bytes", ctypes.c_longlong), ("flops_rho", ctypes.c_double),
                 ("flops_mat", ctypes.c_double), ("flops_ip1", ctypes.c_double),
-                ("tile", ctypes.c_int * 3)]
+                ("tile", ctypes.c_int * 3), ("tile_integ", ctypes.c_int * 3),
+                ("nentries_integ", ctypes.c_longlong)]
 
 
 def lib_path() -> str:
@@ -145,7 +147,7 @@ class Plan:
     """A libgpw plan for one cell (Sec. II / III A of the paper): screened pairs,
     levels, task lists, grids and FFT plans live on the current CUDA device."""
 
-    def __init__(self, system, stream=None, tile=None):
+    def __init__(self, system, stream=None, tile=None, tile_integ=None):
         import torch
         self._lib = load()
         s = system
@@ -180,6 +182,9 @@ class Plan:
         if tile is not None:
             for i in range(3):
                 d.tile[i] = int(tile[i])
+        if tile_integ is not None:
+            for i in range(3):
+                d.tile_integ[i] = int(tile_integ[i])
         torch.cuda.init()
         h = ctypes.c_void_p()
         check(self._lib.gpw_plan(ctypes.byref(d), ctypes.c_void_p(_stream(stream)),
@@ -218,7 +223,8 @@ class Plan:
                     nentries=i.nentries, device_bytes=i.device_bytes,
                     flops_rho=i.flops_rho, flops_mat=i.flops_mat, flops_ip1=i.flops_ip1,
                     level_cutoff=[i.level_cutoff[k] for k in range(i.nlevels)],
-                    tile=tuple(i.tile))
+                    tile=tuple(i.tile), tile_integ=tuple(i.tile_integ),
+                    nentries_integ=i.nentries_integ)
 
     def pair_table(self) -> np.ndarray:
         """Screened pairs as int64 rows (a, b, n0, n1, n2, level, lo0..2, hi0..2),

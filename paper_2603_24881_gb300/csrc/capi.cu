@@ -65,7 +65,7 @@ int upload(T** ptr, const std::vector<T>& v, long long* bytes) {
 void free_plan(Plan* P) {
   DeviceArrays& d = P->d;
   void* ptrs[] = {d.hot_a, d.hot_b, d.ids, d.ids2, d.geo, d.cab, d.pref, d.tab_off,
-                  d.coef_off, d.part_off, d.task, d.sub_off, d.work, d.groups, d.atom_off,
+                  d.coef_off, d.part_off, d.task_c, d.sub_off_c, d.work_c, d.task_i, d.sub_off_i, d.work_i, d.groups, d.atom_off,
                   d.atom_list, d.tab, d.coef, d.part, d.pgrad, d.grids, d.spec, d.fspec,
                   d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs};
   for (void* q : ptrs)
@@ -96,9 +96,12 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
   GPW_TRY(upload(&d.tab_off, H.tab_off, &b));
   GPW_TRY(upload(&d.coef_off, H.coef_off, &b));
   GPW_TRY(upload(&d.part_off, H.part_off, &b));
-  GPW_TRY(upload(&d.task, H.task, &b));
-  GPW_TRY(upload(&d.sub_off, H.sub_off, &b));
-  GPW_TRY(upload(&d.work, H.work, &b));
+  GPW_TRY(upload(&d.task_c, H.task_c, &b));
+  GPW_TRY(upload(&d.sub_off_c, H.sub_off_c, &b));
+  GPW_TRY(upload(&d.work_c, H.work_c, &b));
+  GPW_TRY(upload(&d.task_i, H.task_i, &b));
+  GPW_TRY(upload(&d.sub_off_i, H.sub_off_i, &b));
+  GPW_TRY(upload(&d.work_i, H.work_i, &b));
   GPW_TRY(upload(&d.groups, H.groups, &b));
   GPW_TRY(upload(&d.atom_off, H.atom_off, &b));
   GPW_TRY(upload(&d.atom_list, H.atom_list, &b));
@@ -208,12 +211,22 @@ int combine(Plan& P, cudaStream_t s) {
 }
 
 // Finest-grid potential -> level potentials in P.d.grids (restriction, Sec. II).
+int restrict_spectra(Plan& P, const cufftDoubleComplex* fa, const cufftDoubleComplex* fb,
+                     cudaStream_t s) {
+  for (int k = 0; k < P.nlev; ++k) {
+    GPW_CK(launch_restrict(P, k, fa, fb, s));
+    int rc = fft_z2d(P, k, P.d.spec + P.lev[k].spec_off, P.d.grids + P.lev[k].grid_off, s);
+    if (rc) return rc;
+  }
+  return GPW_OK;
+}
+
 int restrict_levels(Plan& P, const double* v_fine, cudaStream_t s) {
   Phase ph(P, GPW_PHASE_SPECTRAL, s);
   int rc = fft_d2z(P, 0, v_fine, P.d.fspec, s);
   if (rc) return rc;
   for (int k = 0; k < P.nlev; ++k) {
-    GPW_CK(launch_restrict(P, k, s));
+    GPW_CK(launch_restrict(P, k, P.d.fspec, nullptr, s));
     rc = fft_z2d(P, k, P.d.spec + P.lev[k].spec_off, P.d.grids + P.lev[k].grid_off, s);
     if (rc) return rc;
   }
@@ -275,30 +288,39 @@ int ip1_from_grids(Plan& P, const double* D, double* grad, cudaStream_t s) {
 }
 
 // rho -> interpolation -> Poisson + exchange -> restricted level potentials in P.d.grids;
-// energies to energies_dev.
+// energies to energies_dev.  Without v_out the Hartree part stays in G space: each level
+// spectrum is mask_k (FFT(v_x)/N + 4 pi S/G^2), one finest-grid C2R fewer.
 int fock_potential(Plan& P, const double* D, double* energies_dev, double* rho_out,
                    double* v_out, cudaStream_t s) {
   int rc = rho_levels(P, D, s);
   if (rc) return rc;
   if ((rc = combine(P, s))) return rc;
   double* rho = rho_out ? rho_out : P.d.fine_b;
-  double* v = v_out ? v_out : P.d.fine_a;
-  {
-    Phase ph(P, GPW_PHASE_SPECTRAL, s);
+  Phase ph(P, GPW_PHASE_SPECTRAL, s);
+  GPW_CK(cudaMemcpyAsync(P.d.fspec2, P.d.fspec, sizeof(cufftDoubleComplex) * (size_t)P.fine_spec_n,
+                         cudaMemcpyDeviceToDevice, s));
+  if ((rc = fft_z2d(P, 0, P.d.fspec2, rho, s))) return rc;
+  GPW_CK(launch_poisson(P, s));  // fspec <- 4 pi S / G^2, E_H
+  if (v_out) {
     GPW_CK(cudaMemcpyAsync(P.d.fspec2, P.d.fspec,
                            sizeof(cufftDoubleComplex) * (size_t)P.fine_spec_n,
                            cudaMemcpyDeviceToDevice, s));
-    if ((rc = fft_z2d(P, 0, P.d.fspec2, rho, s))) return rc;
-    GPW_CK(launch_poisson(P, s));
-    if ((rc = fft_z2d(P, 0, P.d.fspec, P.d.fine_a, s))) return rc;
-    GPW_CK(launch_lda(P, rho, P.d.fine_a, v, s));
-    GPW_CK(launch_energy_final(P, 0, kRedBlocks, s));
-    GPW_CK(launch_energy_final(P, 1, kRedBlocks, s));
-    if (energies_dev != P.d.energies)
-      GPW_CK(cudaMemcpyAsync(energies_dev, P.d.energies, 2 * sizeof(double),
-                             cudaMemcpyDeviceToDevice, s));
+    if ((rc = fft_z2d(P, 0, P.d.fspec2, P.d.fine_a, s))) return rc;  // v_H(r)
+    GPW_CK(launch_lda(P, rho, P.d.fine_a, v_out, s));               // v_out = v_H + v_x
+  } else {
+    GPW_CK(launch_lda(P, rho, nullptr, P.d.fine_a, s));              // v_x only
   }
-  return restrict_levels(P, v, s);
+  GPW_CK(launch_energy_final(P, 0, kRedBlocks, s));
+  GPW_CK(launch_energy_final(P, 1, kRedBlocks, s));
+  if (energies_dev != P.d.energies)
+    GPW_CK(cudaMemcpyAsync(energies_dev, P.d.energies, 2 * sizeof(double),
+                           cudaMemcpyDeviceToDevice, s));
+  if (v_out) {
+    if ((rc = fft_d2z(P, 0, v_out, P.d.fspec, s))) return rc;
+    return restrict_spectra(P, P.d.fspec, nullptr, s);
+  }
+  if ((rc = fft_d2z(P, 0, P.d.fine_a, P.d.fspec2, s))) return rc;   // FFT(v_x)
+  return restrict_spectra(P, P.d.fspec2, P.d.fspec, s);
 }
 
 int fock_async(Plan& P, const double* D, double* V, double* energies_dev, double* rho_out,
@@ -382,6 +404,8 @@ int gpw_plan_query(gpw_plan_t plan, gpw_plan_info* info) {
   info->tile[0] = P.tile[0];
   info->tile[1] = P.tile[1];
   info->tile[2] = P.tile[2];
+  for (int d = 0; d < 3; ++d) info->tile_integ[d] = P.tile_i[d];
+  info->nentries_integ = P.nent_i;
   return GPW_OK;
 }
 

@@ -46,7 +46,7 @@ struct LevelInfo {
   int nsb[3];            // sub-boxes per dimension (ceil(N / tile))
   long long grid_off;    // offset of the level grid in the level-grid buffer
   long long spec_off;    // offset of the level half spectrum (complex elements)
-  long long sub_base;    // first sub-box of this level in the task CSR
+  long long sub_base;    // first sub-box of this level in the task CSR (collocation)
   double Gk2;            // cutoff sphere: |G|^2 < Gk2
   double weight;         // Omega / (N0 N1 N2)
   double h[3];           // grid spacing L_d / N_d
@@ -64,10 +64,13 @@ struct DeviceArrays {
   long long* tab_off = nullptr;   // 1-D factor tables
   long long* coef_off = nullptr;  // D tensor (rho) / reduced V tensor (stride nc3(L+1))
   long long* part_off = nullptr;  // per-task V tensors (stride nc3(L+1) per task)
-  // tasks
-  int4* task = nullptr;       // 2 per task: {pair, m|L, u, rank}, {t|n per dimension}
-  long long* sub_off = nullptr;   // CSR offsets over all sub-boxes of all levels
-  int2* work = nullptr;       // (level, sub-box) with tasks, heaviest first
+  // tasks of the collocation (c) and integration (i) sub-box shapes
+  int4* task_c = nullptr;     // 2 per task: {pair, m|L, u, rank}, {t|n per dimension}
+  long long* sub_off_c = nullptr;  // CSR offsets over all sub-boxes of all levels
+  int2* work_c = nullptr;     // (level, sub-box) with tasks, heaviest first
+  int4* task_i = nullptr;
+  long long* sub_off_i = nullptr;
+  int2* work_i = nullptr;
   // V assembly: groups of pairs sharing a contracted shell pair
   int4* groups = nullptr;     // shell a, shell b, first pair, end pair
   // gradient assembly
@@ -94,12 +97,15 @@ struct Plan {
   int device = 0;
   int nao = 0, natm = 0, nlev = 0, lmax = 0;
   int nprim = 0, nshell = 0;
-  int tile[3] = {kT0, kT1, kT2};
+  int tile[3] = {kT0, kT1, kT2};      // collocation sub-box
+  int tile_i[3] = {4, 8, 64};         // integration sub-box
   double L[3] = {0, 0, 0};
   double omega = 0;
   double E[GPW_MAX_LEVELS] = {0};
-  LevelInfo lev[GPW_MAX_LEVELS];
+  LevelInfo lev[GPW_MAX_LEVELS];     // sub-box fields for the collocation tile
+  LevelInfo lev_i[GPW_MAX_LEVELS];   // same levels, sub-box fields for the integration tile
   long long npairs = 0, nent = 0, nwork = 0, nsub_total = 0, ngroups = 0;
+  long long nent_i = 0, nwork_i = 0;
   long long tab_total = 0, coef_total = 0, part_total = 0;
   long long grid_total = 0, spec_total = 0, fine_n = 0, fine_spec_n = 0;
   long long pair_points = 0;

@@ -48,14 +48,21 @@ __device__ __forceinline__ void cart_comp(int l, int idx, int* c) {
   c[0] = c[1] = c[2] = 0;
 }
 
-__device__ __forceinline__ double binom(int n, int k) {
-  // n <= 4
-  const double t[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0}, {1, 3, 3, 1, 0},
-                          {1, 4, 6, 4, 1}};
-  return t[n][k];
-}
+__constant__ double c_binom[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0},
+                                     {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+
+__device__ __forceinline__ double binom(int n, int k) { return c_binom[n][k]; }  // n <= 4
 
 __device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
+
+// Asynchronous global -> shared copies (LDGSTS): the next task's factor windows are
+// fetched while the current task computes.
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ void load_tables(int* dst, const CoefTables* src, int tid, int nthr) {
   const int4* s4 = reinterpret_cast<const int4*>(src);
@@ -220,11 +227,22 @@ __device__ __forceinline__ SubBox sub_box(const LevelInfo& lv, int sub, const lo
   return b;
 }
 
-// Stage rows l < rows of the three 1-D factor windows of a task into shared memory
-// (row strides P0, P1, P2).
+// Valid task for a sub-box: non-empty intersection inside the sub-box and inside the
+// pair's tables, and a degree the staging buffers were sized for.
+__device__ __forceinline__ bool task_ok(const Task& tk, int lx, int lrows, const SubBox& sb) {
+  bool ok = lx + 1 <= lrows;
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    ok = ok && tk.m[d] >= 1 && tk.u[d] + tk.m[d] <= sb.ext[d] && tk.t[d] + tk.m[d] <= tk.n[d];
+  return ok;
+}
+
+// Issue asynchronous copies of rows l < rows of the three 1-D factor windows of a task
+// into shared memory (row strides P0, P1, P2).
 template <int P0, int P1, int P2>
-__device__ __forceinline__ void stage_tables(const double* tb, const Task& tk, int rows,
-                                             double* sg0, double* sg1, double* sg2, int lane) {
+__device__ __forceinline__ void stage_tables_async(const double* tb, const Task& tk, int rows,
+                                                   double* sg0, double* sg1, double* sg2,
+                                                   int lane) {
   const int L = tk.L;
   const double* t0 = tb + tk.t[0];
   const double* t1 = tb + (L + 2) * tk.n[0] + tk.t[1];
@@ -233,24 +251,29 @@ __device__ __forceinline__ void stage_tables(const double* tb, const Task& tk, i
   const float i0f = __frcp_rn((float)m0), i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
   for (int it = lane; it < rows * m0; it += 32) {
     int l = fdiv(it, i0f), i = it - l * m0;
-    sg0[l * P0 + i] = __ldg(t0 + l * tk.n[0] + i);
+    cp_async8(sg0 + l * P0 + i, t0 + l * tk.n[0] + i);
   }
   for (int it = lane; it < rows * m1; it += 32) {
     int l = fdiv(it, i1f), i = it - l * m1;
-    sg1[l * P1 + i] = __ldg(t1 + l * tk.n[1] + i);
+    cp_async8(sg1 + l * P1 + i, t1 + l * tk.n[1] + i);
   }
   for (int it = lane; it < rows * m2; it += 32) {
     int l = fdiv(it, i2f), i = it - l * m2;
-    sg2[l * P2 + i] = __ldg(t2 + l * tk.n[2] + i);
+    cp_async8(sg2 + l * P2 + i, t2 + l * tk.n[2] + i);
   }
 }
 
 template <int T0, int T1, int T2>
 struct CollocLayout {
   static constexpr int kTileN = T0 * T1 * T2;
-  // per-warp staging, for lp = lmax + 1 factor rows
+  // one staging buffer: factor windows + D tensor, for lp = lmax + 1 factor rows (even
+  // length keeps 16-byte alignment)
+  __host__ __device__ static int buf(int lp) {
+    return (lp * (T0 + T1 + T2) + nc3(lp - 1) + 1) & ~1;
+  }
+  // per-warp staging: two buffers plus the T1 and T2 intermediates
   __host__ __device__ static int stage(int lp) {
-    return lp * (T0 + T1 + T2) + nc3(lp - 1) + nc2(lp - 1) * T0 + lp * T0 * T1;
+    return 2 * buf(lp) + nc2(lp - 1) * T0 + lp * T0 * T1;
   }
 };
 
@@ -272,6 +295,7 @@ __global__ void __launch_bounds__(NW * 32)
                      const double* __restrict__ tab, const double* __restrict__ coef,
                      const CoefTables* __restrict__ tabs, double* __restrict__ grids, int lp,
                      int stg, int* __restrict__ err) {
+  using Lay = CollocLayout<T0, T1, T2>;
   constexpr int kTileN = T0 * T1 * T2;
   extern __shared__ __align__(16) double sm[];
   int* s_tab = reinterpret_cast<int*>(sm);
@@ -288,49 +312,66 @@ __global__ void __launch_bounds__(NW * 32)
   const SubBox sb = sub_box<T0, T1, T2>(lv, item.y, sub_off);
 
   double* acc = acc_all + warp * kTileN;
-  double* sg0 = acc_all + NW * kTileN + warp * stg;
-  double* sg1 = sg0 + lp * T0;
-  double* sg2 = sg1 + lp * T1;
-  double* sD = sg2 + lp * T2;
-  double* sT1 = sD + nc3(lp - 1);
+  double* stage_base = acc_all + NW * kTileN + warp * stg;
+  const int bufn = Lay::buf(lp);
+  double* sT1 = stage_base + 2 * bufn;
   double* sT2 = sT1 + nc2(lp - 1) * T0;
   __syncthreads();
 
+  // staging buffer b: [sg0 lp*T0][sg1 lp*T1][sg2 lp*T2][D nc3]
+  auto issue = [&](const Task& tk, long long toff, long long coff, int b) {
+    double* sg0 = stage_base + b * bufn;
+    double* sg1 = sg0 + lp * T0;
+    double* sg2 = sg1 + lp * T1;
+    double* sD = sg2 + lp * T2;
+    stage_tables_async<T0, T1, T2>(tab + toff, tk, tk.L + 1, sg0, sg1, sg2, lane);
+    const double* cp = coef + coff;
+    for (int c = lane; c < nc3(tk.L); c += 32) cp_async8(sD + c, cp + c);
+  };
+
   long long e = sb.eb + warp;
-  int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
-  long long toff = 0, coff = 0;
+  int4 a0 = make_int4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
+  long long atoff = 0, acoff = 0, btoff = 0, bcoff = 0;
   if (e < sb.ee) {
-    r0 = __ldg(task + 2 * e);
-    r1 = __ldg(task + 2 * e + 1);
-    toff = __ldg(tab_off + r0.x);
-    coff = __ldg(coef_off + r0.x);
+    a0 = __ldg(task + 2 * e);
+    a1 = __ldg(task + 2 * e + 1);
+    atoff = __ldg(tab_off + a0.x);
+    acoff = __ldg(coef_off + a0.x);
+    const Task tk = decode_task(a0, a1);
+    if (task_ok(tk, tk.L, lp, sb)) issue(tk, atoff, acoff, 0);
+    cp_async_commit();
   }
-  for (; e < sb.ee; e += NW) {
-    int4 n0 = r0, n1 = r1;
+  if (e + NW < sb.ee) {
+    b0 = __ldg(task + 2 * (e + NW));
+    b1 = __ldg(task + 2 * (e + NW) + 1);
+    btoff = __ldg(tab_off + b0.x);
+    bcoff = __ldg(coef_off + b0.x);
+  }
+  int buf = 0;
+  for (; e < sb.ee; e += NW, buf ^= 1) {
+    cp_async_wait_all();
+    __syncwarp();
+    // fetch the next task's windows into the other buffer
     if (e + NW < sb.ee) {
-      n0 = __ldg(task + 2 * (e + NW));
-      n1 = __ldg(task + 2 * (e + NW) + 1);
+      const Task tn = decode_task(b0, b1);
+      if (task_ok(tn, tn.L, lp, sb)) issue(tn, btoff, bcoff, buf ^ 1);
+      cp_async_commit();
     }
-    const Task tk = decode_task(r0, r1);
+    int4 c0 = b0, c1 = b1;
+    if (e + 2 * NW < sb.ee) {
+      c0 = __ldg(task + 2 * (e + 2 * NW));
+      c1 = __ldg(task + 2 * (e + 2 * NW) + 1);
+    }
+    const Task tk = decode_task(a0, a1);
     const int L = tk.L;
     const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
-    if (L + 1 > lp || m0 < 1 || m1 < 1 || m2 < 1 || tk.u[0] + m0 > sb.ext[0] ||
-        tk.u[1] + m1 > sb.ext[1] || tk.u[2] + m2 > sb.ext[2]) {
+    if (!task_ok(tk, L, lp, sb)) {
       if (lane == 0) set_err(err, 1);
     } else {
-      stage_tables<T0, T1, T2>(tab + toff, tk, L + 1, sg0, sg1, sg2, lane);
-      const double* cp = coef + coff;
-      for (int c = lane; c < nc3(L); c += 32) sD[c] = __ldg(cp + c);
-    }
-    // pair offsets of the next task (its record has arrived during the staging)
-    long long ntoff = toff, ncoff = coff;
-    if (e + NW < sb.ee) {
-      ntoff = __ldg(tab_off + n0.x);
-      ncoff = __ldg(coef_off + n0.x);
-    }
-    __syncwarp();
-    if (L + 1 <= lp && m0 >= 1 && m1 >= 1 && m2 >= 1 && tk.u[0] + m0 <= sb.ext[0] &&
-        tk.u[1] + m1 <= sb.ext[1] && tk.u[2] + m2 <= sb.ext[2]) {
+      const double* sg0 = stage_base + buf * bufn;
+      const double* sg1 = sg0 + lp * T0;
+      const double* sg2 = sg1 + lp * T1;
+      const double* sD = sg2 + lp * T2;
       // T1[c21](i0)
       {
         const float inv = __frcp_rn((float)m0);
@@ -345,42 +386,77 @@ __global__ void __launch_bounds__(NW * 32)
         }
       }
       __syncwarp();
-      // T2[l2](q = i0 m1 + i1)
+      // T2[l2](q = i0 m1 + i1); two items per lane in flight (independent FMA chains)
       const int m01 = m0 * m1;
       {
         const float inv01 = __frcp_rn((float)m01), inv1 = __frcp_rn((float)m1);
         const int items = (L + 1) * m01;
-        for (int it = lane; it < items; it += 32) {
-          const int l2 = fdiv(it, inv01), q = it - l2 * m01;
-          const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
-          const int cb = s_c21b[L][l2];
-          double a = 0.0;
-          for (int l1 = 0; l1 <= L - l2; ++l1) a = fma(sT1[(cb + l1) * T0 + i0], sg1[l1 * T1 + i1], a);
-          sT2[l2 * (T0 * T1) + q] = a;
+        for (int base = 0; base < items; base += 64) {
+          const int itA = min(base + lane, items - 1);
+          const int itB = min(base + 32 + lane, items - 1);
+          const int l2A = fdiv(itA, inv01), qA = itA - l2A * m01;
+          const int i0A = fdiv(qA, inv1), i1A = qA - i0A * m1;
+          const int l2B = fdiv(itB, inv01), qB = itB - l2B * m01;
+          const int i0B = fdiv(qB, inv1), i1B = qB - i0B * m1;
+          const int cbA = s_c21b[L][l2A], cbB = s_c21b[L][l2B];
+          const int nA = L - l2A, nB = base + 32 < items ? L - l2B : -1;
+          double a = 0.0, b = 0.0;
+          for (int l1 = 0; l1 <= max(nA, nB); ++l1) {
+            if (l1 <= nA) a = fma(sT1[(cbA + l1) * T0 + i0A], sg1[l1 * T1 + i1A], a);
+            if (l1 <= nB) b = fma(sT1[(cbB + l1) * T0 + i0B], sg1[l1 * T1 + i1B], b);
+          }
+          if (base + lane < items) sT2[l2A * (T0 * T1) + qA] = a;
+          if (base + 32 + lane < items) sT2[l2B * (T0 * T1) + qB] = b;
         }
       }
       __syncwarp();
-      // rho(i0,i1,i2) += sum_l2 T2[l2](q) g2[l2](i2)
+      // rho(i0,i1,i2) += sum_l2 T2[l2](q) g2[l2](i2); two points per lane in flight
       {
         const float inv2 = __frcp_rn((float)m2), inv1 = __frcp_rn((float)m1);
         const int items = m01 * m2;
         const int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
-        for (int it = lane; it < items; it += 32) {
-          const int q = fdiv(it, inv2), i2 = it - q * m2;
-          const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
-          double* a = acc + ((u0 + i0) * T1 + (u1 + i1)) * T2 + (u2 + i2);
-          double r = *a;
-          for (int l2 = 0; l2 <= L; ++l2) r = fma(sT2[l2 * (T0 * T1) + q], sg2[l2 * T2 + i2], r);
-          *a = r;
+        for (int base = 0; base < items; base += 64) {
+          const bool two = base + 32 < items;  // warp-uniform
+          const bool okA = base + lane < items, okB = base + 32 + lane < items;
+          const int itA = min(base + lane, items - 1), itB = min(base + 32 + lane, items - 1);
+          const int qA = fdiv(itA, inv2), i2A = itA - qA * m2;
+          const int i0A = fdiv(qA, inv1), i1A = qA - i0A * m1;
+          const int qB = fdiv(itB, inv2), i2B = itB - qB * m2;
+          const int i0B = fdiv(qB, inv1), i1B = qB - i0B * m1;
+          double* pa = acc + ((u0 + i0A) * T1 + (u1 + i1A)) * T2 + (u2 + i2A);
+          double* pb = acc + ((u0 + i0B) * T1 + (u1 + i1B)) * T2 + (u2 + i2B);
+          if (two) {
+            double ra = okA ? *pa : 0.0, rb = okB ? *pb : 0.0;
+            for (int l2 = 0; l2 <= L; ++l2) {
+              ra = fma(sT2[l2 * (T0 * T1) + qA], sg2[l2 * T2 + i2A], ra);
+              rb = fma(sT2[l2 * (T0 * T1) + qB], sg2[l2 * T2 + i2B], rb);
+            }
+            if (okA) *pa = ra;
+            if (okB) *pb = rb;
+          } else if (okA) {
+            double ra = *pa;
+            for (int l2 = 0; l2 <= L; ++l2) ra = fma(sT2[l2 * (T0 * T1) + qA], sg2[l2 * T2 + i2A], ra);
+            *pa = ra;
+          }
         }
       }
     }
+    long long ctoff = btoff, ccoff = bcoff;
+    if (e + 2 * NW < sb.ee) {
+      ctoff = __ldg(tab_off + c0.x);
+      ccoff = __ldg(coef_off + c0.x);
+    }
     __syncwarp();
-    r0 = n0;
-    r1 = n1;
-    toff = ntoff;
-    coff = ncoff;
+    a0 = b0;
+    a1 = b1;
+    atoff = btoff;
+    acoff = bcoff;
+    b0 = c0;
+    b1 = c1;
+    btoff = ctoff;
+    bcoff = ccoff;
   }
+  cp_async_wait_all();
   __syncthreads();
   // sum the warp copies in warp order and write the sub-box once
   double* out = grids + lv.grid_off;
@@ -411,8 +487,10 @@ struct IntegLayout {
   static constexpr int P0 = T0 + 1, P1 = T1 + 1, P2 = T2 + 1;
   static constexpr int kSV = T0 * T1 * P2;  // padded potential tile
   static constexpr int kUS = T1 * P0;       // one l2 slab of U: [i1][i0]
+  __host__ __device__ static int buf(int lpx) { return (lpx * (P0 + P1 + P2) + 1) & ~1; }
+  // per-warp staging: two factor-window buffers plus the U and W intermediates
   __host__ __device__ static int stage(int lpx) {
-    return lpx * (P0 + P1 + P2) + lpx * kUS + nc2(lpx - 1) * P0;
+    return 2 * buf(lpx) + lpx * kUS + nc2(lpx - 1) * P0;
   }
 };
 
@@ -448,42 +526,59 @@ __global__ void __launch_bounds__(NW * 32)
           vin + ((long long)(sb.s[0] + i0) * lv.N[1] + (sb.s[1] + i1)) * lv.N[2] + (sb.s[2] + i2));
     }
   }
-  double* sg0 = sv + Lay::kSV + warp * stg;
-  double* sg1 = sg0 + lpx * P0;
-  double* sg2 = sg1 + lpx * P1;
-  double* sU = sg2 + lpx * P2;
+  double* stage_base = sv + Lay::kSV + warp * stg;
+  const int bufn = Lay::buf(lpx);
+  double* sU = stage_base + 2 * bufn;
   double* sW = sU + lpx * kUS;
   __syncthreads();
 
+  auto issue = [&](const Task& tk, long long toff, int b) {
+    double* sg0 = stage_base + b * bufn;
+    stage_tables_async<P0, P1, P2>(tab + toff, tk, tk.L + lext + 1, sg0, sg0 + lpx * P0,
+                                   sg0 + lpx * (P0 + P1), lane);
+  };
+
   long long e = sb.eb + warp;
-  int4 r0 = make_int4(0, 0, 0, 0), r1 = r0;
-  long long toff = 0, poff = 0;
+  int4 a0 = make_int4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
+  long long apoff = 0, btoff = 0, bpoff = 0;
   if (e < sb.ee) {
-    r0 = __ldg(task + 2 * e);
-    r1 = __ldg(task + 2 * e + 1);
-    toff = __ldg(tab_off + r0.x);
-    poff = __ldg(part_off + r0.x);
+    a0 = __ldg(task + 2 * e);
+    a1 = __ldg(task + 2 * e + 1);
+    const long long atoff = __ldg(tab_off + a0.x);
+    apoff = __ldg(part_off + a0.x);
+    const Task tk = decode_task(a0, a1);
+    if (task_ok(tk, tk.L + lext, lpx, sb)) issue(tk, atoff, 0);
+    cp_async_commit();
   }
-  for (; e < sb.ee; e += NW) {
-    int4 n0 = r0, n1 = r1;
+  if (e + NW < sb.ee) {
+    b0 = __ldg(task + 2 * (e + NW));
+    b1 = __ldg(task + 2 * (e + NW) + 1);
+    btoff = __ldg(tab_off + b0.x);
+    bpoff = __ldg(part_off + b0.x);
+  }
+  int buf = 0;
+  for (; e < sb.ee; e += NW, buf ^= 1) {
+    cp_async_wait_all();
+    __syncwarp();
     if (e + NW < sb.ee) {
-      n0 = __ldg(task + 2 * (e + NW));
-      n1 = __ldg(task + 2 * (e + NW) + 1);
+      const Task tn = decode_task(b0, b1);
+      if (task_ok(tn, tn.L + lext, lpx, sb)) issue(tn, btoff, buf ^ 1);
+      cp_async_commit();
     }
-    const Task tk = decode_task(r0, r1);
+    int4 c0 = b0, c1 = b1;
+    if (e + 2 * NW < sb.ee) {
+      c0 = __ldg(task + 2 * (e + 2 * NW));
+      c1 = __ldg(task + 2 * (e + 2 * NW) + 1);
+    }
+    const Task tk = decode_task(a0, a1);
     const int L = tk.L, Lx = L + lext;
     const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
-    const bool ok = Lx + 1 <= lpx && m0 >= 1 && m1 >= 1 && m2 >= 1 && tk.u[0] + m0 <= sb.ext[0] &&
-                    tk.u[1] + m1 <= sb.ext[1] && tk.u[2] + m2 <= sb.ext[2];
-    if (ok) stage_tables<P0, P1, P2>(tab + toff, tk, Lx + 1, sg0, sg1, sg2, lane);
-    else if (lane == 0) set_err(err, 3);
-    long long ntoff = toff, npoff = poff;
-    if (e + NW < sb.ee) {
-      ntoff = __ldg(tab_off + n0.x);
-      npoff = __ldg(part_off + n0.x);
-    }
-    __syncwarp();
-    if (ok) {
+    if (!task_ok(tk, Lx, lpx, sb)) {
+      if (lane == 0) set_err(err, 3);
+    } else {
+      const double* sg0 = stage_base + buf * bufn;
+      const double* sg1 = sg0 + lpx * P0;
+      const double* sg2 = sg1 + lpx * P1;
       const int m01 = m0 * m1;
       // U[l2](i1, i0): lanes walk consecutive i1 (rows P2 apart: conflict free)
       {
@@ -520,7 +615,7 @@ __global__ void __launch_bounds__(NW * 32)
       // V[c] -> task slot
       {
         const int nc = nc3(Lx);
-        double* dst = part + poff + (long long)tk.rank * nc;
+        double* dst = part + apoff + (long long)tk.rank * nc;
         for (int c = lane; c < nc; c += 32) {
           const int dc = s_dec3[Lx][c];
           const int c21 = dc & 255, l0 = dc >> 8;
@@ -532,12 +627,21 @@ __global__ void __launch_bounds__(NW * 32)
         }
       }
     }
+    long long ctoff = btoff, cpoff = bpoff;
+    if (e + 2 * NW < sb.ee) {
+      ctoff = __ldg(tab_off + c0.x);
+      cpoff = __ldg(part_off + c0.x);
+    }
     __syncwarp();
-    r0 = n0;
-    r1 = n1;
-    toff = ntoff;
-    poff = npoff;
+    a0 = b0;
+    a1 = b1;
+    apoff = bpoff;
+    b0 = c0;
+    b1 = c1;
+    btoff = ctoff;
+    bpoff = cpoff;
   }
+  cp_async_wait_all();
 }
 
 // Per-pair sum of the task V tensors (fixed task order), times the level weight
@@ -638,17 +742,29 @@ __global__ void assemble_V_kernel(long long ngroups, const int4* __restrict__ gr
   }
 }
 
-// Gradient contraction per pair (Algorithm 3): with the extended V tensor (degree
-// L + 1) of the pair,
-//   dE/dA_x += w pref sum_{mu,nu} D_mu,nu sum_k V[k] c^A_x[k0] e_y[k1] e_z[k2]
-// where c^A_x is the expansion of d/dA_x[(x-A)^a (x-B)^b exp(-a_a (x-A)^2 - ...)] /
-// exp(...) = -a (x-A)^(a-1)(x-B)^b + 2 alpha_a (x-A)^(a+1) (x-B)^b in powers of (x-A);
-// likewise for B.  Six values per pair.
-__device__ __forceinline__ void expand_1d(int i, int j, const double* pw, double* out, int kmax) {
-  // coefficients of (x-A)^k in (x-A)^i (x-B)^j, pw[t] = (A-B)^t
-  for (int k = 0; k <= kmax; ++k) out[k] = 0.0;
-  if (i < 0 || j < 0) return;
-  for (int t = 0; t <= j; ++t) out[i + t] += binom(j, t) * pw[j - t];
+// Gradient contraction per pair (Algorithm 3).  With X(a, b) the integral of v against
+// the product of the Cartesian components a (on A) and b (on B_T) of the two primitives,
+// contracted from the pair's degree-(L+1) V tensor through Eq. (binomial),
+//   dE/dA_d = w pref sum_{mu,nu} D_mu,nu [ -a_d X(a - e_d, b) + 2 alpha_a X(a + e_d, b) ]
+//   dE/dB_d = w pref sum_{mu,nu} D_mu,nu [ -b_d X(a, b - e_d) + 2 alpha_b X(a, b + e_d) ]
+// (the centre derivative of (x - A)^a exp(-alpha (x - A)^2)).  One thread per pair.
+__device__ __forceinline__ double xelem(int a0, int a1, int a2, int b0, int b1, int b2,
+                                        const double (*pw)[5], const double* V, int Lx,
+                                        const CoefTables* tabs) {
+  if (a0 < 0 || a1 < 0 || a2 < 0 || b0 < 0 || b1 < 0 || b2 < 0) return 0.0;
+  double s = 0.0;
+  for (int t2 = 0; t2 <= b2; ++t2) {
+    const double c2 = binom(b2, t2) * pw[2][b2 - t2];
+    const int k2 = a2 + t2;
+    for (int t1 = 0; t1 <= b1; ++t1) {
+      const double c21 = c2 * binom(b1, t1) * pw[1][b1 - t1];
+      const int base = tabs->dec21[Lx][tabs->c21base[Lx][k2] + a1 + t1] >> 16;
+      double s0 = 0.0;
+      for (int t0 = 0; t0 <= b0; ++t0) s0 += binom(b0, t0) * pw[0][b0 - t0] * V[base + a0 + t0];
+      s += c21 * s0;
+    }
+  }
+  return s;
 }
 
 __global__ void grad_pair_kernel(long long np, const int4* __restrict__ ids,
@@ -658,69 +774,53 @@ __global__ void grad_pair_kernel(long long np, const int4* __restrict__ ids,
                                  const double* __restrict__ coef,
                                  const CoefTables* __restrict__ tabs, const double* __restrict__ D,
                                  int nao, double* __restrict__ pgrad) {
-  // one warp per pair, lanes over the (mu, nu) elements of its D block
-  const int lane = threadIdx.x & 31;
-  const long long p = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   const int4 id = ids[p];
   const int la = id.x, lb = id.y, Lx = la + lb + 1;
   const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
   const double* g = geo + 8 * p;
-  const double aa = g[6], ab = g[7];
+  const double aa2 = 2.0 * g[6], ab2 = 2.0 * g[7];
   double pw[3][5];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
-    double t = g[d] - g[3 + d];
+    const double t = g[d] - g[3 + d];
     pw[d][0] = 1.0;
+#pragma unroll
     for (int k = 1; k < 5; ++k) pw[d][k] = pw[d][k - 1] * t;
   }
   const double* Vp = coef + coef_off[p];
   const double scale = (double)ids2[p].z * pref[p];
-  double out[6] = {0, 0, 0, 0, 0, 0};
-  for (int el = lane; el < na * nb; el += 32) {
-    const int mu = el / nb, nu = el - mu * nb;
-    int ca[3], cb[3];
-    cart_comp(la, mu, ca);
-    cart_comp(lb, nu, cb);
-    const double dmn = scale * D[(long long)(id.z + mu) * nao + id.w + nu];
-    double e[3][8];
-#pragma unroll
-    for (int d = 0; d < 3; ++d) expand_1d(ca[d], cb[d], pw[d], e[d], 7);
-    for (int side = 0; side < 2; ++side)
-      for (int dir = 0; dir < 3; ++dir) {
-        double c[8], t1[8], t2[8];
-        if (side == 0) {
-          expand_1d(ca[dir] - 1, cb[dir], pw[dir], t1, 7);
-          expand_1d(ca[dir] + 1, cb[dir], pw[dir], t2, 7);
-          for (int k = 0; k < 8; ++k) c[k] = -(double)ca[dir] * t1[k] + 2.0 * aa * t2[k];
-        } else {
-          expand_1d(ca[dir], cb[dir] - 1, pw[dir], t1, 7);
-          expand_1d(ca[dir], cb[dir] + 1, pw[dir], t2, 7);
-          for (int k = 0; k < 8; ++k) c[k] = -(double)cb[dir] * t1[k] + 2.0 * ab * t2[k];
-        }
-        const double* c0 = dir == 0 ? c : e[0];
-        const double* c1 = dir == 1 ? c : e[1];
-        const double* c2 = dir == 2 ? c : e[2];
-        double sacc = 0.0;
-        for (int k2 = 0; k2 <= Lx; ++k2) {
-          if (c2[k2] == 0.0) continue;
-          for (int k1 = 0; k1 <= Lx - k2; ++k1) {
-            if (c1[k1] == 0.0) continue;
-            const int base = tabs->dec21[Lx][tabs->c21base[Lx][k2] + k1] >> 16;
-            double s0 = 0.0;
-            for (int k0 = 0; k0 <= Lx - k2 - k1; ++k0) s0 += c0[k0] * Vp[base + k0];
-            sacc += c2[k2] * c1[k1] * s0;
-          }
-        }
-        out[3 * side + dir] += dmn * sacc;
-      }
+  double gA0 = 0, gA1 = 0, gA2 = 0, gB0 = 0, gB1 = 0, gB2 = 0;
+  for (int mu = 0; mu < na; ++mu) {
+    int a[3];
+    cart_comp(la, mu, a);
+    const double* Drow = D + (long long)(id.z + mu) * nao + id.w;
+    for (int nu = 0; nu < nb; ++nu) {
+      int b[3];
+      cart_comp(lb, nu, b);
+      const double dmn = scale * Drow[nu];
+      gA0 += dmn * (aa2 * xelem(a[0] + 1, a[1], a[2], b[0], b[1], b[2], pw, Vp, Lx, tabs) -
+                    a[0] * xelem(a[0] - 1, a[1], a[2], b[0], b[1], b[2], pw, Vp, Lx, tabs));
+      gA1 += dmn * (aa2 * xelem(a[0], a[1] + 1, a[2], b[0], b[1], b[2], pw, Vp, Lx, tabs) -
+                    a[1] * xelem(a[0], a[1] - 1, a[2], b[0], b[1], b[2], pw, Vp, Lx, tabs));
+      gA2 += dmn * (aa2 * xelem(a[0], a[1], a[2] + 1, b[0], b[1], b[2], pw, Vp, Lx, tabs) -
+                    a[2] * xelem(a[0], a[1], a[2] - 1, b[0], b[1], b[2], pw, Vp, Lx, tabs));
+      gB0 += dmn * (ab2 * xelem(a[0], a[1], a[2], b[0] + 1, b[1], b[2], pw, Vp, Lx, tabs) -
+                    b[0] * xelem(a[0], a[1], a[2], b[0] - 1, b[1], b[2], pw, Vp, Lx, tabs));
+      gB1 += dmn * (ab2 * xelem(a[0], a[1], a[2], b[0], b[1] + 1, b[2], pw, Vp, Lx, tabs) -
+                    b[1] * xelem(a[0], a[1], a[2], b[0], b[1] - 1, b[2], pw, Vp, Lx, tabs));
+      gB2 += dmn * (ab2 * xelem(a[0], a[1], a[2], b[0], b[1], b[2] + 1, pw, Vp, Lx, tabs) -
+                    b[2] * xelem(a[0], a[1], a[2], b[0], b[1], b[2] - 1, pw, Vp, Lx, tabs));
+    }
   }
-#pragma unroll
-  for (int i = 0; i < 6; ++i) {
-    double v = out[i];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (lane == 0) pgrad[6 * p + i] = v;
-  }
+  double* out = pgrad + 6 * p;
+  out[0] = gA0;
+  out[1] = gA1;
+  out[2] = gA2;
+  out[3] = gB0;
+  out[4] = gB1;
+  out[5] = gB2;
 }
 
 __global__ void grad_atom_kernel(int natm, const long long* __restrict__ atom_off,
@@ -789,9 +889,11 @@ __global__ void combine_kernel(const KLevels K, const Cell cell,
   }
 }
 
-// Level spectrum from the fine spectrum: T_k(G) = [|G| < G_k] v^_fine(G) / N_fine.
+// Level spectrum from fine spectra: T_k(G) = [|G| < G_k] (fa(G) sa + fb(G)), where fa is
+// an unnormalised DFT (sa = 1/N_fine) and fb, if given, is already a normalised spectrum.
 __global__ void restrict_kernel(const KLevels K, const Cell cell, int level,
-                                const cufftDoubleComplex* __restrict__ fspec,
+                                const cufftDoubleComplex* __restrict__ fa,
+                                const cufftDoubleComplex* __restrict__ fb,
                                 cufftDoubleComplex* __restrict__ spec) {
   const LevelInfo& f = K.lv[0];
   const LevelInfo& lv = K.lv[level];
@@ -813,9 +915,15 @@ __global__ void restrict_kernel(const KLevels K, const Cell cell, int level,
         2 * s2 <= lv.N[2] - 1) {
       const int i0 = s0 < 0 ? s0 + f.N[0] : s0;
       const int i1 = s1 < 0 ? s1 + f.N[1] : s1;
-      const cufftDoubleComplex z = fspec[((long long)i0 * f.N[1] + i1) * fh2 + s2];
+      const long long fi = ((long long)i0 * f.N[1] + i1) * fh2 + s2;
+      const cufftDoubleComplex z = fa[fi];
       out.x = z.x * inv;
       out.y = z.y * inv;
+      if (fb) {
+        const cufftDoubleComplex w = fb[fi];
+        out.x += w.x;
+        out.y += w.y;
+      }
     }
     spec[lv.spec_off + idx] = out;
   }
@@ -875,7 +983,7 @@ __global__ void lda_kernel(long long n, double wgt, const double* __restrict__ r
        i += (long long)gridDim.x * blockDim.x) {
     const double r = fmax(rho[i], 0.0);
     const double c = cbrt(r);
-    vout[i] = vH[i] - cx * c;
+    vout[i] = (vH ? vH[i] : 0.0) - cx * c;
     part += -0.75 * cx * r * c;
   }
   const double s = block_sum(part, sh);
@@ -898,8 +1006,26 @@ constexpr int kNW = 8;
 #define GPW_TILE_SHAPES(X) X(8, 8, 16) X(4, 8, 32) X(8, 8, 32) X(4, 8, 64)
 
 template <int T0, int T1, int T2>
-size_t colloc_smem(int stg) {
-  return sizeof(int) * kTabInts + sizeof(double) * (size_t)kNW * (T0 * T1 * T2 + stg);
+size_t colloc_smem(int stg, int nw) {
+  return sizeof(int) * kTabInts + sizeof(double) * (size_t)nw * (T0 * T1 * T2 + stg);
+}
+
+// Warps per collocation block: the candidate with the most resident warps per SM
+// (shared memory bounds the blocks per SM; each block reserves 1 KB).
+int pick_colloc_warps(size_t smem_per_sm, size_t (*smem_of)(int, int), int stg, int* nw_out,
+                      size_t* smem_out) {
+  int best = 0;
+  for (int nw : {8, 6, 4}) {
+    size_t need = smem_of(stg, nw);
+    int blocks = (int)(smem_per_sm / (need + 1024));
+    blocks = std::min(blocks, 32 / nw);
+    if (blocks * nw > best) {
+      best = blocks * nw;
+      *nw_out = nw;
+      *smem_out = need;
+    }
+  }
+  return best;
 }
 template <int T0, int T1, int T2>
 size_t integ_smem(int stg) {
@@ -916,42 +1042,53 @@ extern "C" int gpw_tile_supported(int t0, int t1, int t2) {
   return 0;
 }
 
-KLevels make_klevels(const Plan& p) {
+KLevels make_klevels(const Plan& p, bool integ) {
   KLevels k;
-  for (int i = 0; i < GPW_MAX_LEVELS; ++i) k.lv[i] = p.lev[i];
+  for (int i = 0; i < GPW_MAX_LEVELS; ++i) k.lv[i] = integ ? p.lev_i[i] : p.lev[i];
   k.nlev = p.nlev;
   return k;
 }
 
 cudaError_t configure_kernels(Plan* p) {
   const int lp = p->lmax + 1;
-  const int t0 = p->tile[0], t1 = p->tile[1], t2 = p->tile[2];
-  bool found = false;
+  int found = 0;
+  int dev = 0, optin = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e != cudaSuccess) return e;
 #define GPW_TILE_CONF(a, b, c)                                                      \
-  if (t0 == a && t1 == b && t2 == c) {                                              \
-    found = true;                                                                   \
+  if (p->tile[0] == a && p->tile[1] == b && p->tile[2] == c) {                      \
+    found |= 1;                                                                     \
     p->stg_colloc = even(CollocLayout<a, b, c>::stage(lp));                         \
+    if (pick_colloc_warps((size_t)per_sm, colloc_smem<a, b, c>, p->stg_colloc,       \
+                          &p->nw_colloc, &p->smem_colloc) == 0)                     \
+      return cudaErrorInvalidValue;                                                 \
+  }                                                                                 \
+  if (p->tile_i[0] == a && p->tile_i[1] == b && p->tile_i[2] == c) {                \
+    found |= 2;                                                                     \
     p->stg_integ = even(IntegLayout<a, b, c>::stage(p->lmax + 1));                  \
     p->stg_integ1 = even(IntegLayout<a, b, c>::stage(p->lmax + 2));                 \
-    p->smem_colloc = colloc_smem<a, b, c>(p->stg_colloc);                           \
     p->smem_integ = integ_smem<a, b, c>(p->stg_integ);                              \
     p->smem_integ1 = integ_smem<a, b, c>(p->stg_integ1);                            \
   }
   GPW_TILE_SHAPES(GPW_TILE_CONF)
 #undef GPW_TILE_CONF
-  if (!found) return cudaErrorInvalidValue;
-  p->nw_colloc = kNW;
+  if (found != 3) return cudaErrorInvalidValue;
   p->nw_integ = kNW;
   // the attribute is per function and shared by all plans: raise it to the device
   // maximum, each launch asks for what its plan needs
-  int dev = 0, optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return e;
   if ((size_t)optin < std::max(p->smem_colloc, std::max(p->smem_integ, p->smem_integ1)))
     return cudaErrorInvalidValue;
 #define GPW_TILE_ATTR(a, b, c)                                                                    \
-  e = cudaFuncSetAttribute(collocate_kernel<a, b, c, kNW>,                                        \
+  e = cudaFuncSetAttribute(collocate_kernel<a, b, c, 8>,                                          \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, optin);                   \
+  if (e != cudaSuccess) return e;                                                                 \
+  e = cudaFuncSetAttribute(collocate_kernel<a, b, c, 6>,                                          \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, optin);                   \
+  if (e != cudaSuccess) return e;                                                                 \
+  e = cudaFuncSetAttribute(collocate_kernel<a, b, c, 4>,                                          \
                            cudaFuncAttributeMaxDynamicSharedMemorySize, optin);                   \
   if (e != cudaSuccess) return e;                                                                 \
   e = cudaFuncSetAttribute(integrate_kernel<a, b, c, kNW>,                                        \
@@ -966,7 +1103,7 @@ cudaError_t launch_tables(const Plan& p, cudaStream_t s) {
   if (p.npairs == 0) return cudaSuccess;
   long long blocks = std::min<long long>((p.npairs + 7) / 8, 152LL * 64);
   ++p.launches;
-  tables_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, make_klevels(p), p.d.hot_a, p.d.hot_b,
+  tables_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, make_klevels(p, false), p.d.hot_a, p.d.hot_b,
                                              p.d.geo, p.d.cab, p.d.tab_off, p.d.tab, p.d.pref);
   return cudaGetLastError();
 }
@@ -984,27 +1121,31 @@ cudaError_t launch_collocate(const Plan& p, cudaStream_t s) {
   if (p.nwork == 0) return cudaSuccess;
   const int t0 = p.tile[0], t1 = p.tile[1], t2 = p.tile[2];
   ++p.launches;
-#define GPW_TILE_COLLOC(a, b, c)                                                           \
-  if (t0 == a && t1 == b && t2 == c) {                                                     \
-    collocate_kernel<a, b, c, kNW><<<(int)p.nwork, kNW * 32, p.smem_colloc, s>>>(          \
-        make_klevels(p), p.d.work, p.d.sub_off, p.d.task, p.d.tab_off, p.d.coef_off,        \
-        p.d.tab, p.d.coef, p.d.tabs, p.d.grids, p.lmax + 1, p.stg_colloc, p.d.err);         \
+#define GPW_COLLOC_NW(a, b, c, nw)                                                         \
+  if (t0 == a && t1 == b && t2 == c && p.nw_colloc == nw) {                                \
+    collocate_kernel<a, b, c, nw><<<(int)p.nwork, nw * 32, p.smem_colloc, s>>>(            \
+        make_klevels(p, false), p.d.work_c, p.d.sub_off_c, p.d.task_c, p.d.tab_off,         \
+        p.d.coef_off, p.d.tab, p.d.coef, p.d.tabs, p.d.grids, p.lmax + 1, p.stg_colloc,     \
+        p.d.err);                                                                          \
     return cudaGetLastError();                                                             \
   }
+#define GPW_TILE_COLLOC(a, b, c) GPW_COLLOC_NW(a, b, c, 8) GPW_COLLOC_NW(a, b, c, 6) GPW_COLLOC_NW(a, b, c, 4)
   GPW_TILE_SHAPES(GPW_TILE_COLLOC)
 #undef GPW_TILE_COLLOC
+#undef GPW_COLLOC_NW
   return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s) {
-  if (p.nwork == 0) return cudaSuccess;
-  const int t0 = p.tile[0], t1 = p.tile[1], t2 = p.tile[2];
+  if (p.nwork_i == 0) return cudaSuccess;
+  const int t0 = p.tile_i[0], t1 = p.tile_i[1], t2 = p.tile_i[2];
   ++p.launches;
 #define GPW_TILE_INTEG(a, b, c)                                                            \
   if (t0 == a && t1 == b && t2 == c) {                                                     \
-    integrate_kernel<a, b, c, kNW><<<(int)p.nwork, kNW * 32,                               \
+    integrate_kernel<a, b, c, kNW><<<(int)p.nwork_i, kNW * 32,                             \
                                      lext ? p.smem_integ1 : p.smem_integ, s>>>(            \
-        make_klevels(p), p.d.work, p.d.sub_off, p.d.task, p.d.tab_off, p.d.part_off,        \
+        make_klevels(p, true), p.d.work_i, p.d.sub_off_i, p.d.task_i, p.d.tab_off,          \
+        p.d.part_off,                                                                      \
         p.d.tab, p.d.tabs, p.d.grids, p.d.part, lext, p.lmax + lext + 1,                    \
         lext ? p.stg_integ1 : p.stg_integ, p.d.err);                                       \
     return cudaGetLastError();                                                             \
@@ -1018,7 +1159,7 @@ cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s) {
   if (p.npairs == 0) return cudaSuccess;
   long long blocks = std::min<long long>((p.npairs + 7) / 8, 152LL * 64);
   ++p.launches;
-  reduce_parts_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, make_klevels(p), p.d.hot_a, p.d.hot_b,
+  reduce_parts_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, make_klevels(p, false), p.d.hot_a, p.d.hot_b,
                                                   p.d.ids2, p.d.part_off, p.d.coef_off, p.d.part,
                                                   p.d.coef, lext);
   return cudaGetLastError();
@@ -1037,7 +1178,7 @@ cudaError_t launch_assemble_V(const Plan& p, int lext, double* V, cudaStream_t s
 cudaError_t launch_grad(const Plan& p, const double* D, double* grad, cudaStream_t s) {
   if (p.npairs > 0) {
     ++p.launches;
-    grad_pair_kernel<<<(int)((p.npairs + 7) / 8), 256, 0, s>>>(
+    grad_pair_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
         p.npairs, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, p.d.coef, p.d.tabs, D,
         p.nao, p.d.pgrad);
     cudaError_t e = cudaGetLastError();
@@ -1052,21 +1193,22 @@ cudaError_t launch_grad(const Plan& p, const double* D, double* grad, cudaStream
 cudaError_t launch_combine(const Plan& p, cudaStream_t s) {
   Cell c{{p.L[0], p.L[1], p.L[2]}};
   ++p.launches;
-  combine_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p), c, p.d.spec, p.d.fspec);
+  combine_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p, false), c, p.d.spec, p.d.fspec);
   return cudaGetLastError();
 }
 
-cudaError_t launch_restrict(const Plan& p, int level, cudaStream_t s) {
+cudaError_t launch_restrict(const Plan& p, int level, const cufftDoubleComplex* fa,
+                            const cufftDoubleComplex* fb, cudaStream_t s) {
   Cell c{{p.L[0], p.L[1], p.L[2]}};
   ++p.launches;
-  restrict_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p), c, level, p.d.fspec, p.d.spec);
+  restrict_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p, false), c, level, fa, fb, p.d.spec);
   return cudaGetLastError();
 }
 
 cudaError_t launch_poisson(const Plan& p, cudaStream_t s) {
   Cell c{{p.L[0], p.L[1], p.L[2]}};
   ++p.launches;
-  poisson_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(make_klevels(p), c, p.omega, p.d.fspec, p.d.red);
+  poisson_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(make_klevels(p, false), c, p.omega, p.d.fspec, p.d.red);
   return cudaGetLastError();
 }
 

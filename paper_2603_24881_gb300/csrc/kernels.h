@@ -10,7 +10,7 @@ struct KLevels {
   int nlev;
 };
 
-KLevels make_klevels(const Plan& p);
+KLevels make_klevels(const Plan& p, bool integ);
 
 cudaError_t launch_tables(const Plan& p, cudaStream_t s);
 cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s);
@@ -20,7 +20,8 @@ cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s);
 cudaError_t launch_assemble_V(const Plan& p, int lext, double* V, cudaStream_t s);
 cudaError_t launch_grad(const Plan& p, const double* D, double* grad, cudaStream_t s);
 cudaError_t launch_combine(const Plan& p, cudaStream_t s);
-cudaError_t launch_restrict(const Plan& p, int level, cudaStream_t s);
+cudaError_t launch_restrict(const Plan& p, int level, const cufftDoubleComplex* fa,
+                            const cufftDoubleComplex* fb, cudaStream_t s);
 cudaError_t launch_poisson(const Plan& p, cudaStream_t s);
 cudaError_t launch_lda(const Plan& p, const double* rho, const double* vH, double* v_out,
                        cudaStream_t s);

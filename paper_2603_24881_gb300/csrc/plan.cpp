@@ -128,6 +128,115 @@ void segments(int lo, int hi, int N, int T, std::vector<Seg>* out) {
   }
 }
 
+struct PairBox {
+  int level, lo[3], hi[3];
+};
+
+std::vector<PairBox> pairs_view(const std::vector<PairTmp>& pairs) {
+  std::vector<PairBox> v(pairs.size());
+  for (size_t i = 0; i < pairs.size(); ++i) {
+    v[i].level = pairs[i].level;
+    for (int d = 0; d < 3; ++d) {
+      v[i].lo[d] = pairs[i].lo[d];
+      v[i].hi[d] = pairs[i].hi[d];
+    }
+  }
+  return v;
+}
+
+// Task lists for one sub-box shape T: per level, sub-boxes of T (the last ones clipped
+// at the mesh edge), and for every pair each (sub-box, periodic copy) its box meets.
+// Fills lev[k].sub_base, the CSR offsets, the 2-int4 task records (sorted by pair
+// inside every sub-box), the work list (heaviest sub-box first) and, if ranks is
+// non-NULL, the number of tasks of every pair.
+int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector<int4>& hot_a,
+                const int* T, LevelInfo* lev, std::vector<long long>* sub_off,
+                std::vector<int4>* task, std::vector<int2>* work, long long* nent_out,
+                long long* nwork_out, long long* nsub_out, std::vector<int>* ranks) {
+  const int K = plan->nlev;
+  const long long np = (long long)pairs.size();
+  long long nsub = 0;
+  for (int k = 0; k < K; ++k) {
+    lev[k].sub_base = nsub;
+    nsub += (long long)lev[k].nsb[0] * lev[k].nsb[1] * lev[k].nsb[2];
+  }
+  *nsub_out = nsub;
+  std::vector<long long> count(nsub + 1, 0);
+  std::vector<Seg> sg[3];
+  for (long long p = 0; p < np; ++p) {
+    const PairBox& t = pairs[p];
+    const LevelInfo& lv = lev[t.level];
+    for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
+    for (auto& s0 : sg[0])
+      for (auto& s1 : sg[1])
+        for (auto& s2 : sg[2])
+          count[lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j + 1]++;
+  }
+  for (long long i = 0; i < nsub; ++i) count[i + 1] += count[i];
+  const long long nent = count[nsub];
+  *nent_out = nent;
+  task->assign(2 * nent, make_int4(0, 0, 0, 0));
+  if (ranks) ranks->assign(np, 0);
+  std::vector<long long> fill(count.begin(), count.end() - 1);
+  for (long long p = 0; p < np; ++p) {
+    const PairBox& t = pairs[p];
+    const LevelInfo& lv = lev[t.level];
+    for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
+    const int L = hot_a[p].w;
+    int n[3];
+    for (int d = 0; d < 3; ++d) {
+      n[d] = t.hi[d] - t.lo[d] + 1;
+      if (n[d] > 65535) {
+        set_error("gpw_plan: pair box longer than 65535 grid points");
+        return GPW_ERANGE;
+      }
+    }
+    int rank = 0;
+    auto isect = [&](int d, const Seg& sgm, int* m, int* u, int* tt) {
+      long long s0 = (long long)sgm.j * T[d];
+      long long ext = std::min<long long>(T[d], lv.N[d] - s0);
+      long long o = (long long)sgm.k * lv.N[d] + s0;
+      long long a = std::max<long long>(t.lo[d], o);
+      long long b = std::min<long long>(t.hi[d], o + ext - 1);
+      *m = (int)(b - a + 1);
+      *u = (int)(a - o);
+      *tt = (int)(a - t.lo[d]);
+    };
+    for (auto& s0 : sg[0])
+      for (auto& s1 : sg[1])
+        for (auto& s2 : sg[2]) {
+          int m[3], u[3], tt[3];
+          isect(0, s0, &m[0], &u[0], &tt[0]);
+          isect(1, s1, &m[1], &u[1], &tt[1]);
+          isect(2, s2, &m[2], &u[2], &tt[2]);
+          long long sub = lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j;
+          long long slot = fill[sub]++;
+          (*task)[2 * slot] = make_int4((int)p, m[0] | (m[1] << 8) | (m[2] << 16) | (L << 24),
+                                        u[0] | (u[1] << 8) | (u[2] << 16), rank);
+          (*task)[2 * slot + 1] = make_int4(tt[0] | (n[0] << 16), tt[1] | (n[1] << 16),
+                                            tt[2] | (n[2] << 16), 0);
+          ++rank;
+        }
+    if (ranks) (*ranks)[p] = rank;
+  }
+  *sub_off = count;
+  std::vector<std::pair<long long, long long>> w;  // (-count, global sub)
+  for (long long sidx = 0; sidx < nsub; ++sidx) {
+    long long c = count[sidx + 1] - count[sidx];
+    if (c > 0) w.push_back({-c, sidx});
+  }
+  std::sort(w.begin(), w.end());
+  work->resize(w.size());
+  for (size_t i = 0; i < w.size(); ++i) {
+    long long sidx = w[i].second;
+    int k = 0;
+    while (k + 1 < K && lev[k + 1].sub_base <= sidx) ++k;
+    (*work)[i] = make_int2(k, (int)(sidx - lev[k].sub_base));
+  }
+  *nwork_out = (long long)w.size();
+  return GPW_OK;
+}
+
 }  // namespace
 
 int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
@@ -172,6 +281,13 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
       return GPW_EINVAL;
     }
     for (int d = 0; d < 3; ++d) plan->tile[d] = desc->tile[d];
+  }
+  if (desc->tile_integ[0] || desc->tile_integ[1] || desc->tile_integ[2]) {
+    if (!gpw_tile_supported(desc->tile_integ[0], desc->tile_integ[1], desc->tile_integ[2])) {
+      set_error("gpw_plan: unsupported integration tile shape");
+      return GPW_EINVAL;
+    }
+    for (int d = 0; d < 3; ++d) plan->tile_i[d] = desc->tile_integ[d];
   }
   plan->natm = desc->natm;
   plan->nshell = desc->nshell;
@@ -432,93 +548,28 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   plan->tab_total = tab_total;
   plan->coef_total = coef_total;
 
-  // ---- per-level sub-box task lists (CSR), one task per (pair, sub-box, image shift)
-  long long nsub = 0;
-  for (int k = 0; k < K; ++k) {
-    plan->lev[k].sub_base = nsub;
-    nsub += (long long)plan->lev[k].nsb[0] * plan->lev[k].nsb[1] * plan->lev[k].nsb[2];
-  }
-  plan->nsub_total = nsub;
-  std::vector<long long> count(nsub + 1, 0);
-  const int T[3] = {plan->tile[0], plan->tile[1], plan->tile[2]};
-  std::vector<Seg> sg[3];
-  for (long long p = 0; p < np; ++p) {
-    const PairTmp& t = pairs[p];
-    const LevelInfo& lv = plan->lev[t.level];
-    for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
-    for (auto& s0 : sg[0])
-      for (auto& s1 : sg[1])
-        for (auto& s2 : sg[2])
-          count[lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j + 1]++;
-  }
-  for (long long i = 0; i < nsub; ++i) count[i + 1] += count[i];
-  const long long nent = count[nsub];
-  plan->nent = nent;
-  H->sub_off = count;
-  H->task.resize(2 * nent);
-  std::vector<long long> fill(count.begin(), count.end() - 1);
+  // ---- per-level sub-box task lists (CSR), one task per (pair, sub-box, image shift),
+  // for the collocation tile and for the integration tile
+  std::vector<int> ranks;
+  int rc = build_tasks(plan, pairs_view(pairs), H->hot_a, plan->tile, plan->lev, &H->sub_off_c,
+                       &H->task_c, &H->work_c, &plan->nent, &plan->nwork, &plan->nsub_total,
+                       nullptr);
+  if (rc) return rc;
+  for (int k = 0; k < K; ++k) plan->lev_i[k] = plan->lev[k];
+  for (int k = 0; k < K; ++k)
+    for (int d = 0; d < 3; ++d)
+      plan->lev_i[k].nsb[d] = (plan->lev[k].N[d] + plan->tile_i[d] - 1) / plan->tile_i[d];
+  long long nsub_i = 0;
+  rc = build_tasks(plan, pairs_view(pairs), H->hot_a, plan->tile_i, plan->lev_i, &H->sub_off_i,
+                   &H->task_i, &H->work_i, &plan->nent_i, &plan->nwork_i, &nsub_i, &ranks);
+  if (rc) return rc;
   long long part_total = 0;
   for (long long p = 0; p < np; ++p) {
-    const PairTmp& t = pairs[p];
-    const LevelInfo& lv = plan->lev[t.level];
-    for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
-    const int L = H->hot_a[p].w;
-    int n[3];
-    for (int d = 0; d < 3; ++d) {
-      n[d] = t.hi[d] - t.lo[d] + 1;
-      if (n[d] > 65535) {
-        set_error("gpw_plan: pair box longer than 65535 grid points");
-        return GPW_ERANGE;
-      }
-    }
-    int rank = 0;
-    // intersection of the pair box with the copy k of sub-box j along one dimension
-    auto isect = [&](int d, const Seg& sgm, int* m, int* u, int* tt) {
-      long long s0 = (long long)sgm.j * T[d];
-      long long ext = std::min<long long>(T[d], lv.N[d] - s0);
-      long long o = (long long)sgm.k * lv.N[d] + s0;
-      long long a = std::max<long long>(t.lo[d], o);
-      long long b = std::min<long long>(t.hi[d], o + ext - 1);
-      *m = (int)(b - a + 1);
-      *u = (int)(a - o);
-      *tt = (int)(a - t.lo[d]);
-    };
-    for (auto& s0 : sg[0])
-      for (auto& s1 : sg[1])
-        for (auto& s2 : sg[2]) {
-          int m[3], u[3], tt[3];
-          isect(0, s0, &m[0], &u[0], &tt[0]);
-          isect(1, s1, &m[1], &u[1], &tt[1]);
-          isect(2, s2, &m[2], &u[2], &tt[2]);
-          long long sub = lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j;
-          long long slot = fill[sub]++;
-          H->task[2 * slot] = make_int4((int)p, m[0] | (m[1] << 8) | (m[2] << 16) | (L << 24),
-                                        u[0] | (u[1] << 8) | (u[2] << 16), rank);
-          H->task[2 * slot + 1] = make_int4(tt[0] | (n[0] << 16), tt[1] | (n[1] << 16),
-                                            tt[2] | (n[2] << 16), 0);
-          ++rank;
-        }
-    H->ids2[p].w = rank;
+    H->ids2[p].w = ranks[p];
     H->part_off[p] = part_total;
-    part_total += (long long)rank * nc3(L + 1);
+    part_total += (long long)ranks[p] * nc3(H->hot_a[p].w + 1);
   }
   plan->part_total = part_total;
-
-  // ---- work list: sub-boxes with tasks, heaviest first (then level, then index)
-  std::vector<std::pair<long long, long long>> w;  // (-count, global sub)
-  for (long long s = 0; s < nsub; ++s) {
-    long long c = H->sub_off[s + 1] - H->sub_off[s];
-    if (c > 0) w.push_back({-c, s});
-  }
-  std::sort(w.begin(), w.end());
-  H->work.resize(w.size());
-  for (size_t i = 0; i < w.size(); ++i) {
-    long long s = w[i].second;
-    int k = 0;
-    while (k + 1 < K && plan->lev[k + 1].sub_base <= s) ++k;
-    H->work[i] = make_int2(k, (int)(s - plan->lev[k].sub_base));
-  }
-  plan->nwork = (long long)w.size();
 
   // ---- V assembly groups: runs of pairs with the same contracted shell pair
   for (long long p = 0; p < np;) {
@@ -553,6 +604,11 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     lv.spec_off = plan->spec_total;
     plan->grid_total += (long long)lv.N[0] * lv.N[1] * lv.N[2];
     plan->spec_total += (long long)lv.N[0] * lv.N[1] * (lv.N[2] / 2 + 1);
+  }
+  // the integration-tile level table shares everything but its sub-box fields
+  for (int k = 0; k < K; ++k) {
+    plan->lev_i[k].grid_off = plan->lev[k].grid_off;
+    plan->lev_i[k].spec_off = plan->lev[k].spec_off;
   }
   plan->fine_n = (long long)plan->lev[0].N[0] * plan->lev[0].N[1] * plan->lev[0].N[2];
   plan->fine_spec_n = (long long)plan->lev[0].N[0] * plan->lev[0].N[1] * (plan->lev[0].N[2] / 2 + 1);

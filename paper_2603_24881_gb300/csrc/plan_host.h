@@ -11,9 +11,9 @@ struct HostArrays {
   std::vector<int4> hot_a, hot_b, ids, ids2;
   std::vector<double> geo, cab;
   std::vector<long long> tab_off, coef_off, part_off;
-  std::vector<int4> task;   // 2 per task
-  std::vector<long long> sub_off;
-  std::vector<int2> work;
+  std::vector<int4> task_c, task_i;   // 2 int4 per task
+  std::vector<long long> sub_off_c, sub_off_i;
+  std::vector<int2> work_c, work_i;
   std::vector<int4> groups;
   std::vector<long long> atom_off;
   std::vector<int> atom_list;

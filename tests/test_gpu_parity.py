@@ -219,11 +219,11 @@ def test_fock_grad_fused(gpw, cases, name):
     assert np.max(np.abs(out["grad"].cpu().numpy() - gref)) <= 1e-7
 
 
-@pytest.mark.parametrize("tile", [(4, 8, 32), (8, 8, 32), (4, 8, 64)])
+@pytest.mark.parametrize("tile", [(8, 8, 16), (4, 8, 32), (8, 8, 32), (4, 8, 64)])
 def test_tile_shapes(gpw, cases, tile):
     s, op = cases["water4"]
-    gp = gpw.Plan(s, tile=tile)
-    assert gp.stats()["tile"] == tile
+    gp = gpw.Plan(s, tile=tile, tile_integ=tile)
+    assert gp.stats()["tile"] == tile and gp.stats()["tile_integ"] == tile
     rl = [x.cpu().numpy() for x in gp.eval_rho_levels(s.D)]
     ref = op.rho_levels(s.D)
     scale = max(np.max(np.abs(r)) for r in ref)
@@ -239,3 +239,15 @@ def test_tile_shapes(gpw, cases, tile):
 def test_unsupported_tile(gpw):
     with pytest.raises(gpw.GpwError):
         gpw.Plan(workloads.tiny(), tile=(3, 8, 16))
+
+
+def test_mixed_tiles_carbon_like_f_shells(gpw):
+    # f shells (L up to 6 per pair) with different collocation and integration tiles
+    s = systems.resolved(seed=8, shells=((0, 1), (1, 1), (2, 1), (3, 1)), natm=3)
+    op = oracle.Plan(s)
+    gp = gpw.Plan(s, tile=(4, 8, 32), tile_integ=(8, 8, 32))
+    out = gp.fock_grad(s.D)
+    r = op.fock(s.D)
+    assert _rel(out["V"].cpu().numpy(), r["V"]) <= RTOL
+    assert abs(out["EH"] - r["EH"]) <= 1e-8 and abs(out["Ex"] - r["Ex"]) <= 1e-8
+    assert np.max(np.abs(out["grad"].cpu().numpy() - op.grad_levels(s.D, r["v_levels"]))) <= 1e-7
