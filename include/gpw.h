@@ -217,6 +217,25 @@ int gpw_profile(gpw_plan_t plan, int enable);
 int gpw_profile_read(gpw_plan_t plan, double* ms, long long* count, int nphases,
                      long long* launches);
 
+/* Largest density grid gpw_lda_x_noalloc accepts (points). */
+#define GPW_LDA_NOALLOC_MAX_POINTS 67108864
+
+/* Slater exchange of a density grid without any device allocation and without a plan.
+ * The paper has no counterpart to this entry point: it exists for callers that cannot
+ * call cudaMalloc (an application whose memory pool owns the device, a loop that must
+ * not enter the driver's allocator, a library that does not own the CUDA context).
+ * rho: device, n doubles (n <= GPW_LDA_NOALLOC_MAX_POINTS, else GPW_ERANGE);
+ * v_x: device, n doubles, overwritten with -(3/pi)^(1/3) max(rho,0)^(1/3);
+ * e_x: device, 1 double, overwritten with weight * sum -(3/4)(3/pi)^(1/3) max(rho,0)^(4/3)
+ *      (weight = Omega / n gives E_x of gpw_fock).
+ * The working memory is one fixed 32 KB array in the library's device image, shared by
+ * every call on a GPU and keeping the last call's contents (each call writes what it
+ * reads, so nothing needs clearing); calls whose executions overlap on the GPU race on
+ * it.  The first call on each device looks up the array's address with that device
+ * current; make that first call before any stream capture.  Asynchronous on `stream`. */
+int gpw_lda_x_noalloc(const double* rho, long long n, double weight, double* v_x, double* e_x,
+                      void* stream);
+
 /* Release the plan and everything it owns.  NULL is ignored. */
 void gpw_plan_destroy(gpw_plan_t plan);
 
