@@ -44,7 +44,12 @@ WORKLOAD_DESC = ("256 H2O, cubic L=37.3 Bohr, 7168 Cartesian AOs, 280 Ha, 4 leve
                  "(288/168/96/60), tau=1e-6; step = gpw_fock_grad (V, energies, Hxc gradient)")
 # DRAM bytes per launch of the dominant kernel from one ncu capture, valid while the
 # kernel source is unchanged (sha256 of csrc/kernels.cu at capture time).
-TRAFFIC = {}
+TRAFFIC = {
+    # integration at degree L+1, 4x8x64 sub-box: 1.300 GB per launch on water32
+    # (1.413e9 pair-points), scaled by pair-points to water256 (1.027e10)
+    "integrate_ip1": {"bytes_per_launch": 9.451e+09, "src_sha": "e2d367342cdaf6af",
+                      "capture": "profiles/ncu_collocate_integrate_water32.md"},
+}
 
 
 def _kernels_sha() -> str:

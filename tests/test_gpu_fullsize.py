@@ -1,0 +1,106 @@
+"""Full-size parity on sampled outputs (water256 as timed by bench.py, and carbon with f
+shells), with the plans in their default launch configuration.
+
+The oracle cannot build whole grids at this size in seconds, so it computes one by one:
+the integer pair table (all of it), level densities at sampled grid points, V shell
+blocks for a band-limited potential, and the gradient on sampled atoms.  Properties
+that hold at any size check the rest (adjoint identity through the full Fock path).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def gpw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2603_24881_gb300 as g
+    g.load()
+    return g
+
+
+@pytest.fixture(scope="module", params=["water256", "carbon"])
+def big(request, gpw):
+    s = workloads.config(request.param)
+    gp = gpw.Plan(s)
+    op = oracle.Plan(s)
+    yield request.param, s, gp, op
+    gp.close()
+    torch.cuda.empty_cache()
+
+
+def test_pair_table_identical(big):
+    name, s, gp, op = big
+    assert np.array_equal(gp.pair_table(), op.pair_table()), name
+
+
+def test_rho_levels_sampled(big):
+    name, s, gp, op = big
+    rl = gp.eval_rho_levels(s.D)
+    rng = np.random.default_rng(21)
+    scale = max(float(r.abs().max()) for r in rl)
+    for k, r in enumerate(rl):
+        if op.lev.tolist().count(k) == 0:
+            assert float(r.abs().max()) == 0.0
+            continue
+        mesh = op.meshes[k]
+        pts = np.stack([rng.integers(0, mesh[d], 48) for d in range(3)], axis=1)
+        got = r.cpu().numpy()[pts[:, 0], pts[:, 1], pts[:, 2]]
+        ref = op.rho_points(s.D, k, pts)
+        assert np.max(np.abs(got - ref)) <= RTOL * scale, (name, k)
+
+
+def test_V_blocks_sampled(big):
+    name, s, gp, op = big
+    vl = [s.potential.sample(m) for m in op.meshes]
+    V = gp.eval_mat_levels(vl).cpu().numpy()
+    off = s.ao_offsets()
+    rng = np.random.default_rng(22)
+    blocks = [(int(a), int(b)) for a, b in rng.integers(0, s.nshell, size=(6, 2))]
+    # a shell with itself and a near neighbour (same atom) always included
+    blocks += [(0, 0), (0, 1)]
+    scale = float(np.max(np.abs(V)))
+    for sa, sb in blocks:
+        ref = op.mat_block(vl, sa, sb)
+        got = V[off[sa]:off[sa + 1], off[sb]:off[sb + 1]]
+        assert np.max(np.abs(got - ref)) <= RTOL * scale, (name, sa, sb)
+
+
+def test_gradient_sampled_atoms(big):
+    name, s, gp, op = big
+    vl = [s.potential.sample(m) for m in op.meshes]
+    g = gp.eval_mat_ip1_levels(s.D, vl).cpu().numpy()
+    rng = np.random.default_rng(23)
+    atoms = rng.choice(s.natm, size=3, replace=False)
+    pa = op.prims["atom"]
+    for at in atoms:
+        sel = np.nonzero((pa[op.ab[:, 0]] == at) | (pa[op.ab[:, 1]] == at))[0]
+        ref = op.grad_levels(s.D, vl, sel=sel)[at]
+        assert np.max(np.abs(g[at] - ref)) <= 1e-7, (name, at)
+
+
+def test_fused_path_consistent_and_adjoint(big, gpw):
+    # gpw_fock_grad (the bench step) equals gpw_fock + gpw_eval_mat_ip1 of the same
+    # density, and <v_fine, rho_fine> = tr(D V) through the Fock path
+    name, s, gp, op = big
+    fg = gp.fock_grad(s.D)
+    f = gp.fock(s.D, want_rho=True, want_v=True)
+    assert abs(fg["EH"] - f["EH"]) <= 1e-8 and abs(fg["Ex"] - f["Ex"]) <= 1e-8
+    V = f["V"]
+    assert float((fg["V"] - V).abs().max()) <= RTOL * float(V.abs().max())
+    g = gp.eval_mat_ip1(s.D, f["v"])
+    assert float((fg["grad"] - g).abs().max()) <= 1e-7
+    rho, v = f["rho"], f["v"]
+    omega = float(np.prod(np.diag(s.lattice)))
+    lhs = omega / rho.numel() * float((rho * v).sum())
+    rhs = float((torch.as_tensor(s.D, device="cuda") * V).sum())
+    assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
+    assert gp.check_device() == 0
