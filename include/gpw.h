@@ -62,6 +62,7 @@ extern "C" {
 #define GPW_STRICT 0            /* default: the truncation definition of the paper */
 
 typedef struct gpw_plan_s* gpw_plan_t;
+typedef struct gpw_batch_s* gpw_batch_t;
 
 /* Problem statement (Sec. II and III A of the paper): cell, atoms, Gaussian shells,
  * plane-wave cutoff and multigrid levels, screening threshold tau of Eq. (cut).
@@ -121,6 +122,16 @@ typedef struct {
  * 1..GPW_MAX_LEVELS, non-positive exponents, or meshes too small for the
  * cutoff sphere.  *out is set only on success. */
 int gpw_plan(const gpw_desc* desc, void* stream, gpw_plan_t* out);
+
+/* Host phase of gpw_plan only: screening, levels and task lists on the CPU, no device
+ * work and no device allocation.  gpw_plan_query then reports the exact device_bytes
+ * the commit will allocate (cuFFT work areas estimated), which lets a scheduler admit
+ * the plan by device memory before committing it.  Evaluations need a committed plan. */
+int gpw_plan_prepare(const gpw_desc* desc, gpw_plan_t* out);
+
+/* Device phase: allocate and upload the plan, create cuFFT plans and the 1-D tables
+ * (enqueued on `stream`).  On failure the plan stays prepared and can be retried. */
+int gpw_plan_commit(gpw_plan_t plan, void* stream);
 
 /* 1 if the sub-box shape (t0, t1, t2) has compiled kernels, else 0. */
 int gpw_tile_supported(int t0, int t1, int t2);
@@ -190,6 +201,26 @@ int gpw_fock_grad(gpw_plan_t plan, const double* D, double* V, double* grad, dou
 /* As gpw_fock_grad with the energies written to device memory (2 doubles), no sync. */
 int gpw_fock_grad_async(gpw_plan_t plan, const double* D, double* V, double* grad,
                         double* energies_dev, void* stream);
+
+/* Batches: the collocation and integration tasks of several plans (cells) run in one
+ * launch each, heaviest sub-boxes first across all plans, instead of one launch per
+ * plan; the other steps run per plan on the same stream.  Plans of a batch share their
+ * sub-box shapes and device.  Results per plan are identical to the plan run alone (the
+ * same tasks, in the same order per sub-box, with the same reductions). */
+int gpw_batch_create(int max_plans, gpw_batch_t* out);
+
+/* Attach nplans committed plans (<= max_plans): builds the merged work lists and the
+ * device views (synchronises `stream`).  Call again whenever the plan set changes. */
+int gpw_batch_set(gpw_batch_t batch, int nplans, const gpw_plan_t* plans, void* stream);
+
+/* gpw_fock_grad_async for every attached plan i: D[i], V[i] device nao_i x nao_i,
+ * grad[i] device natm_i x 3 (grad or grad[i] may be NULL to skip the gradient),
+ * energies_dev device 2*nplans doubles (E_H, E_x of plan i at 2i, 2i+1).  Allocates
+ * nothing and does not synchronise, so the sequence can be captured in a CUDA graph. */
+int gpw_batch_fock_grad_async(gpw_batch_t batch, const double* const* D, double* const* V,
+                              double* const* grad, double* energies_dev, void* stream);
+
+void gpw_batch_destroy(gpw_batch_t batch);
 
 /* Read and clear the device error word of the plan (synchronises `stream`).
  * Returns GPW_OK, or GPW_EDEVICE with *code set to the first recorded check. */

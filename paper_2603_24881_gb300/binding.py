@@ -26,6 +26,8 @@ EXPORTS = ["gpw_plan", "gpw_plan_query", "gpw_plan_update_coords", "gpw_plan_pai
            "gpw_eval_rho", "gpw_eval_rho_levels", "gpw_eval_mat", "gpw_eval_mat_levels",
            "gpw_eval_mat_ip1", "gpw_eval_mat_ip1_levels", "gpw_fock", "gpw_fock_async",
            "gpw_fock_grad", "gpw_fock_grad_async", "gpw_tile_supported",
+           "gpw_plan_prepare", "gpw_plan_commit", "gpw_batch_create", "gpw_batch_set",
+           "gpw_batch_fock_grad_async", "gpw_batch_destroy",
            "gpw_check_device", "gpw_profile", "gpw_profile_read", "gpw_plan_destroy",
            "gpw_strerror", "gpw_last_error"]
 PHASES = ["coef", "collocate", "spectral", "integrate", "assemble", "integrate_ip1", "grad"]
@@ -99,6 +101,13 @@ def load(build_if_missing: bool = True):
         L.gpw_fock_grad.argtypes = [vp, vp, vp, vp, vp, vp]
         L.gpw_fock_grad_async.argtypes = [vp, vp, vp, vp, vp, vp]
         L.gpw_tile_supported.argtypes = [ci, ci, ci]
+        L.gpw_plan_prepare.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(vp)]
+        L.gpw_plan_commit.argtypes = [vp, vp]
+        L.gpw_batch_create.argtypes = [ci, ctypes.POINTER(vp)]
+        L.gpw_batch_set.argtypes = [vp, ci, vp, vp]
+        L.gpw_batch_fock_grad_async.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.gpw_batch_destroy.argtypes = [vp]
+        L.gpw_batch_destroy.restype = None
         L.gpw_check_device.argtypes = [vp, ctypes.POINTER(ci), vp]
         L.gpw_profile.argtypes = [vp, ci]
         L.gpw_profile_read.argtypes = [vp, vp, vp, ci, vp]
@@ -109,7 +118,8 @@ def load(build_if_missing: bool = True):
         L.gpw_last_error.argtypes = []
         L.gpw_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("gpw_plan_destroy", "gpw_strerror", "gpw_last_error"):
+            if name not in ("gpw_plan_destroy", "gpw_strerror", "gpw_last_error",
+                            "gpw_batch_destroy"):
                 getattr(L, name).restype = ci
         _LIB = L
         return L
@@ -147,8 +157,10 @@ class Plan:
     """A libgpw plan for one cell (Sec. II / III A of the paper): screened pairs,
     levels, task lists, grids and FFT plans live on the current CUDA device."""
 
-    def __init__(self, system, stream=None, tile=None, tile_integ=None):
-        import torch
+    def __init__(self, system, stream=None, tile=None, tile_integ=None, commit=True):
+        """Prepare the plan on the host (screening, levels, task lists) and, unless
+        commit=False, commit it to the current device.  An uncommitted plan reports its
+        exact device footprint in stats()["device_bytes"]."""
         self._lib = load()
         s = system
         self.system = s
@@ -185,20 +197,35 @@ class Plan:
         if tile_integ is not None:
             for i in range(3):
                 d.tile_integ[i] = int(tile_integ[i])
-        torch.cuda.init()
         h = ctypes.c_void_p()
-        check(self._lib.gpw_plan(ctypes.byref(d), ctypes.c_void_p(_stream(stream)),
-                                 ctypes.byref(h)), "gpw_plan")
+        check(self._lib.gpw_plan_prepare(ctypes.byref(d), ctypes.byref(h)), "gpw_plan_prepare")
         self._h = h
         self._keep = []
+        self.committed = False
+        self._query()
+        if commit:
+            self.commit(stream)
+
+    def _query(self):
         info = Info()
-        check(self._lib.gpw_plan_query(h, ctypes.byref(info)), "gpw_plan_query")
+        check(self._lib.gpw_plan_query(self._h, ctypes.byref(info)), "gpw_plan_query")
         self.info = info
         self.nao = info.nao
         self.natm = info.natm
         self.nlevels = info.nlevels
         self.meshes = [tuple(info.meshes[k][i] for i in range(3)) for k in range(info.nlevels)]
         self.fine_mesh = self.meshes[0]
+
+    def commit(self, stream=None):
+        """Allocate and upload the plan on the current device (gpw_plan_commit)."""
+        import torch
+        if self.committed:
+            return self
+        torch.cuda.init()
+        check(self._lib.gpw_plan_commit(self._h, ctypes.c_void_p(_stream(stream))), "gpw_plan_commit")
+        self.committed = True
+        self._query()
+        return self
 
     # -- housekeeping -------------------------------------------------------
     def close(self):
@@ -405,3 +432,43 @@ class Plan:
         """Enqueue a Fock build writing V and energies (device, 2 doubles) only."""
         check(self._lib.gpw_fock_async(self._h, _ptr(D), _ptr(V), _ptr(energies), _ptr(rho),
                                        _ptr(v), _stream(stream)), "gpw_fock_async")
+
+
+class Batch:
+    """Several committed plans whose collocation and integration tasks run in one launch
+    each (gpw_batch_*).  set() attaches plans; fock_grad_async() enqueues one Fock build
+    plus gradient for every plan without allocating or synchronising."""
+
+    def __init__(self, max_plans: int):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        check(self._lib.gpw_batch_create(int(max_plans), ctypes.byref(h)), "gpw_batch_create")
+        self._h = h
+        self.max_plans = int(max_plans)
+        self.plans = []
+
+    def set(self, plans, stream=None):
+        arr = (ctypes.c_void_p * len(plans))(*[p._h.value for p in plans])
+        check(self._lib.gpw_batch_set(self._h, len(plans), arr, ctypes.c_void_p(_stream(stream))),
+              "gpw_batch_set")
+        self.plans = list(plans)
+        return self
+
+    def fock_grad_async(self, Ds, Vs, grads, energies, stream=None):
+        n = len(self.plans)
+        P = lambda ts: (ctypes.c_void_p * n)(*[_ptr(t) for t in ts])
+        g = P(grads) if grads is not None else None
+        check(self._lib.gpw_batch_fock_grad_async(self._h, P(Ds), P(Vs), g, _ptr(energies),
+                                                  ctypes.c_void_p(_stream(stream))),
+              "gpw_batch_fock_grad_async")
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.gpw_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

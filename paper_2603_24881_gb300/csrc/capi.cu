@@ -21,6 +21,17 @@ struct gpw_plan_s {
   gpw::Plan p;
 };
 
+// A set of plans whose collocation and integration tasks run in single launches.
+struct gpw_batch_s {
+  int cap = 0, n = 0;
+  gpw::PlanView* views = nullptr;       // device, cap entries
+  int4* work_c = nullptr;               // merged work lists (device)
+  int4* work_i = nullptr;
+  long long cap_c = 0, cap_i = 0, nwc = 0, nwi = 0;
+  gpw::GridLaunch colloc, integ1;
+  std::vector<gpw_plan_t> plans;
+};
+
 namespace gpw {
 
 static thread_local std::string g_err;
@@ -67,7 +78,7 @@ void free_plan(Plan* P) {
   void* ptrs[] = {d.hot_a, d.hot_b, d.ids, d.ids2, d.geo, d.cab, d.pref, d.tab_off,
                   d.coef_off, d.part_off, d.task_c, d.sub_off_c, d.work_c, d.task_i, d.sub_off_i, d.work_i, d.groups, d.atom_off,
                   d.atom_list, d.tab, d.coef, d.part, d.pgrad, d.grids, d.spec, d.fspec,
-                  d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs};
+                  d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs, d.view};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
@@ -78,6 +89,34 @@ void free_plan(Plan* P) {
       cufftDestroy(P->fft_z2d[k]);
     }
   d = DeviceArrays();
+  delete P->host;
+  P->host = nullptr;
+  P->committed = false;
+}
+
+// Device bytes create_device will allocate for this plan (cuFFT work areas estimated).
+long long estimate_bytes(const Plan& P, const HostArrays& H) {
+  auto sz = [](long long n, size_t e) { return (long long)e * std::max<long long>(n, 1); };
+  long long b = 0;
+  b += sz((long long)H.hot_a.size(), sizeof(int4)) * 4;                 // hot_a, hot_b, ids, ids2
+  b += sz((long long)H.geo.size(), sizeof(double)) + sz(P.npairs, sizeof(double)) * 2;
+  b += sz(P.npairs, sizeof(long long)) * 3;
+  b += sz((long long)H.task_c.size(), sizeof(int4)) + sz((long long)H.task_i.size(), sizeof(int4));
+  b += sz((long long)H.sub_off_c.size(), sizeof(long long)) + sz((long long)H.sub_off_i.size(), sizeof(long long));
+  b += sz((long long)H.work_c.size(), sizeof(int4)) + sz((long long)H.work_i.size(), sizeof(int4));
+  b += sz((long long)H.groups.size(), sizeof(int4)) + sz((long long)H.atom_off.size(), sizeof(long long));
+  b += sz((long long)H.atom_list.size(), sizeof(int));
+  b += sz(P.tab_total + P.coef_total + P.part_total + 6 * P.npairs + P.grid_total, sizeof(double));
+  b += sz(P.spec_total + 2 * P.fine_spec_n, sizeof(cufftDoubleComplex));
+  b += sz(2 * P.fine_n + 2 * 304 + 2, sizeof(double)) + sizeof(int) + sizeof(CoefTables) + sizeof(PlanView);
+  for (int k = 0; k < P.nlev; ++k) {
+    size_t ws = 0;
+    if (cufftEstimate3d(P.lev[k].N[0], P.lev[k].N[1], P.lev[k].N[2], CUFFT_D2Z, &ws) == CUFFT_SUCCESS)
+      b += (long long)ws;
+    if (cufftEstimate3d(P.lev[k].N[0], P.lev[k].N[1], P.lev[k].N[2], CUFFT_Z2D, &ws) == CUFFT_SUCCESS)
+      b += (long long)ws;
+  }
+  return b;
 }
 
 int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
@@ -126,6 +165,8 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
     GPW_TRY(upload(&d.tabs, v, &b));
   }
 #undef GPW_TRY
+#define GPW_TRY2(x) \
+  if ((rc = (x)) != GPW_OK) return rc
   for (int k = 0; k < P->nlev; ++k) {
     const LevelInfo& lv = P->lev[k];
     GPW_CF(cufftPlan3d(&P->fft_d2z[k], lv.N[0], lv.N[1], lv.N[2], CUFFT_D2Z));
@@ -141,11 +182,21 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
     cufftGetSize(P->fft_z2d[k], &ws);
     b += (long long)ws;
   }
+  {
+    std::vector<PlanView> v(1, PlanView());
+    P->device_bytes = b;
+    GPW_CK(configure_kernels(P));
+    v[0] = make_view(*P);
+    GPW_TRY2(upload(&d.view, v, &b));
+  }
+  P->work_c_host = H.work_c;
+  P->work_i_host = H.work_i;
   P->device_bytes = b;
-  GPW_CK(configure_kernels(P));
   GPW_CK(launch_tables(*P, s));
+  P->committed = true;
   return GPW_OK;
 }
+#undef GPW_TRY2
 
 int fft_d2z(Plan& P, int k, const double* in, cufftDoubleComplex* out, cudaStream_t s) {
   GPW_CF(cufftSetStream(P.fft_d2z[k], s));
@@ -187,13 +238,20 @@ class Phase {
   bool on_;
 };
 
-// rho_k on every level (raw collocation, Algorithm 1 / Eq. rho_wrap).
-int rho_levels(Plan& P, const double* D, cudaStream_t s) {
+// Pair D tensors and cleared level grids: everything collocation needs.
+int prep_rho(Plan& P, const double* D, cudaStream_t s) {
   {
     Phase ph(P, GPW_PHASE_COEF, s);
     GPW_CK(launch_pair_coef(P, D, s));
   }
   GPW_CK(cudaMemsetAsync(P.d.grids, 0, sizeof(double) * (size_t)P.grid_total, s));
+  return GPW_OK;
+}
+
+// rho_k on every level (raw collocation, Algorithm 1 / Eq. rho_wrap).
+int rho_levels(Plan& P, const double* D, cudaStream_t s) {
+  int rc = prep_rho(P, D, s);
+  if (rc) return rc;
   Phase ph(P, GPW_PHASE_COLLOCATE, s);
   GPW_CK(launch_collocate(P, s));
   return GPW_OK;
@@ -261,16 +319,24 @@ int mat_from_grids(Plan& P, double* V, cudaStream_t s) {
 
 // One integration pass at degree L + 1 serves both V (its monomials of degree <= L) and
 // the gradient contraction: Algorithms 2 and 3 share the task sweep.
+int finish_mat_ip1(Plan& P, const double* D, double* V, double* grad, cudaStream_t s);
+
 int mat_ip1_from_grids(Plan& P, const double* D, double* V, double* grad, cudaStream_t s) {
   {
     Phase ph(P, GPW_PHASE_INTEGRATE_IP1, s);
     GPW_CK(launch_integrate(P, 1, s));
   }
+  return finish_mat_ip1(P, D, V, grad, s);
+}
+
+// Per-pair V tensors (degree L+1) -> V and, if grad is non-NULL, the gradient.
+int finish_mat_ip1(Plan& P, const double* D, double* V, double* grad, cudaStream_t s) {
   {
     Phase ph(P, GPW_PHASE_ASSEMBLE, s);
     GPW_CK(launch_reduce_parts(P, 1, s));
     GPW_CK(launch_assemble_V(P, 1, V, s));
   }
+  if (!grad) return GPW_OK;
   Phase ph(P, GPW_PHASE_GRAD, s);
   GPW_CK(launch_grad(P, D, grad, s));
   return GPW_OK;
@@ -290,11 +356,10 @@ int ip1_from_grids(Plan& P, const double* D, double* grad, cudaStream_t s) {
 // rho -> interpolation -> Poisson + exchange -> restricted level potentials in P.d.grids;
 // energies to energies_dev.  Without v_out the Hartree part stays in G space: each level
 // spectrum is mask_k (FFT(v_x)/N + 4 pi S/G^2), one finest-grid C2R fewer.
-int fock_potential(Plan& P, const double* D, double* energies_dev, double* rho_out,
-                   double* v_out, cudaStream_t s) {
-  int rc = rho_levels(P, D, s);
+int potential_from_levels(Plan& P, double* energies_dev, double* rho_out, double* v_out,
+                          cudaStream_t s) {
+  int rc = combine(P, s);
   if (rc) return rc;
-  if ((rc = combine(P, s))) return rc;
   double* rho = rho_out ? rho_out : P.d.fine_b;
   Phase ph(P, GPW_PHASE_SPECTRAL, s);
   GPW_CK(cudaMemcpyAsync(P.d.fspec2, P.d.fspec, sizeof(cufftDoubleComplex) * (size_t)P.fine_spec_n,
@@ -323,6 +388,13 @@ int fock_potential(Plan& P, const double* D, double* energies_dev, double* rho_o
   return restrict_spectra(P, P.d.fspec2, P.d.fspec, s);
 }
 
+int fock_potential(Plan& P, const double* D, double* energies_dev, double* rho_out,
+                   double* v_out, cudaStream_t s) {
+  int rc = rho_levels(P, D, s);
+  if (rc) return rc;
+  return potential_from_levels(P, energies_dev, rho_out, v_out, s);
+}
+
 int fock_async(Plan& P, const double* D, double* V, double* energies_dev, double* rho_out,
                double* v_out, cudaStream_t s) {
   int rc = fock_potential(P, D, energies_dev, rho_out, v_out, s);
@@ -342,6 +414,18 @@ bool bad(gpw_plan_t plan) {
     set_error("NULL plan");
     return true;
   }
+  if (!plan->p.committed) {
+    set_error("plan not committed (gpw_plan_commit)");
+    return true;
+  }
+  return false;
+}
+
+bool null_plan(gpw_plan_t plan) {
+  if (!plan) {
+    set_error("NULL plan");
+    return true;
+  }
   return false;
 }
 
@@ -352,35 +436,76 @@ using gpw::set_error;
 
 extern "C" {
 
+int gpw_plan_prepare(const gpw_desc* desc, gpw_plan_t* out) {
+  if (!out) {
+    set_error("gpw_plan_prepare: NULL out");
+    return GPW_EINVAL;
+  }
+  try {
+    std::unique_ptr<gpw_plan_s> h(new gpw_plan_s());
+    std::unique_ptr<gpw::HostArrays> H(new gpw::HostArrays());
+    int rc = gpw::build_host_plan(desc, &h->p, H.get());
+    if (rc) return rc;
+    h->p.device_bytes = gpw::estimate_bytes(h->p, *H);
+    h->p.host = H.release();
+    *out = h.release();
+    return GPW_OK;
+  } catch (const std::bad_alloc&) {
+    set_error("gpw_plan_prepare: host allocation failed");
+    return GPW_ENOMEM;
+  } catch (...) {
+    set_error("gpw_plan_prepare: unexpected exception");
+    return GPW_EINVAL;
+  }
+}
+
+int gpw_plan_commit(gpw_plan_t plan, void* stream) {
+  if (gpw::null_plan(plan)) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  if (P.committed) return GPW_OK;
+  if (!P.host) {
+    set_error("gpw_plan_commit: plan has no host data");
+    return GPW_EINVAL;
+  }
+  try {
+    cudaGetDevice(&P.device);
+    int rc = gpw::create_device(&P, *P.host, (cudaStream_t)stream);
+    if (rc) {
+      // release what was allocated; the host data stays so the commit can be retried
+      gpw::HostArrays* keep = P.host;
+      P.host = nullptr;
+      gpw::free_plan(&P);
+      P.host = keep;
+      return rc;
+    }
+    delete P.host;
+    P.host = nullptr;
+    return GPW_OK;
+  } catch (const std::bad_alloc&) {
+    set_error("gpw_plan_commit: host allocation failed");
+    return GPW_ENOMEM;
+  }
+}
+
 int gpw_plan(const gpw_desc* desc, void* stream, gpw_plan_t* out) {
   if (!out) {
     set_error("gpw_plan: NULL out");
     return GPW_EINVAL;
   }
-  try {
-    std::unique_ptr<gpw_plan_s> h(new gpw_plan_s());
-    gpw::HostArrays H;
-    int rc = gpw::build_host_plan(desc, &h->p, &H);
-    if (rc) return rc;
-    cudaGetDevice(&h->p.device);
-    rc = gpw::create_device(&h->p, H, (cudaStream_t)stream);
-    if (rc) {
-      gpw::free_plan(&h->p);
-      return rc;
-    }
-    *out = h.release();
-    return GPW_OK;
-  } catch (const std::bad_alloc&) {
-    set_error("gpw_plan: host allocation failed");
-    return GPW_ENOMEM;
-  } catch (...) {
-    set_error("gpw_plan: unexpected exception");
-    return GPW_EINVAL;
+  gpw_plan_t h = nullptr;
+  int rc = gpw_plan_prepare(desc, &h);
+  if (rc) return rc;
+  rc = gpw_plan_commit(h, stream);
+  if (rc) {
+    gpw_plan_destroy(h);
+    return rc;
   }
+  *out = h;
+  return GPW_OK;
 }
 
 int gpw_plan_query(gpw_plan_t plan, gpw_plan_info* info) {
-  if (gpw::bad(plan) || !info) return GPW_EINVAL;
+  if (gpw::null_plan(plan) || !info) return GPW_EINVAL;
   const gpw::Plan& P = plan->p;
   std::memset(info, 0, sizeof(*info));
   info->nao = P.nao;
@@ -444,7 +569,7 @@ int gpw_plan_update_coords(gpw_plan_t plan, const double* coords, void* stream) 
 }
 
 int gpw_plan_pairs(gpw_plan_t plan, int* ab, int* img, int* level, int* lo, int* hi) {
-  if (gpw::bad(plan)) return GPW_EINVAL;
+  if (gpw::null_plan(plan)) return GPW_EINVAL;
   const gpw::Plan& P = plan->p;
   if (ab) std::copy(P.h_ab.begin(), P.h_ab.end(), ab);
   if (img) std::copy(P.h_img.begin(), P.h_img.end(), img);
@@ -568,6 +693,149 @@ int gpw_fock_grad(gpw_plan_t plan, const double* D, double* V, double* grad, dou
     return GPW_ECUDA;
   }
   return GPW_OK;
+}
+
+int gpw_batch_create(int max_plans, gpw_batch_t* out) {
+  if (!out || max_plans < 1) {
+    set_error("gpw_batch_create: bad arguments");
+    return GPW_EINVAL;
+  }
+  try {
+    gpw_batch_s* b = new gpw_batch_s();
+    b->cap = max_plans;
+    cudaError_t e = cudaMalloc((void**)&b->views, sizeof(gpw::PlanView) * (size_t)max_plans);
+    if (e != cudaSuccess) {
+      delete b;
+      set_error(std::string("gpw_batch_create: ") + cudaGetErrorString(e));
+      return GPW_ENOMEM;
+    }
+    *out = b;
+    return GPW_OK;
+  } catch (const std::bad_alloc&) {
+    set_error("gpw_batch_create: host allocation failed");
+    return GPW_ENOMEM;
+  }
+}
+
+int gpw_batch_set(gpw_batch_t b, int nplans, const gpw_plan_t* plans, void* stream) {
+  if (!b || nplans < 1 || nplans > b->cap || !plans) {
+    set_error("gpw_batch_set: bad arguments or more plans than the batch capacity");
+    return GPW_EINVAL;
+  }
+  int lmax = 0;
+  for (int i = 0; i < nplans; ++i) {
+    if (gpw::bad(plans[i])) return GPW_EINVAL;
+    const gpw::Plan& P = plans[i]->p;
+    const gpw::Plan& P0 = plans[0]->p;
+    for (int d = 0; d < 3; ++d)
+      if (P.tile[d] != P0.tile[d] || P.tile_i[d] != P0.tile_i[d]) {
+        set_error("gpw_batch_set: plans of a batch must share their sub-box shapes");
+        return GPW_EINVAL;
+      }
+    if (P.device != P0.device) {
+      set_error("gpw_batch_set: plans of a batch must live on one device");
+      return GPW_EINVAL;
+    }
+    lmax = std::max(lmax, P.lmax);
+  }
+  cudaError_t e = gpw::configure_batch(plans[0]->p.tile, plans[0]->p.tile_i, lmax, &b->colloc,
+                                       &b->integ1);
+  if (e != cudaSuccess) {
+    set_error(std::string("gpw_batch_set: ") + cudaGetErrorString(e));
+    return GPW_ECUDA;
+  }
+  // views and work lists of all plans, each list merged heaviest first
+  std::vector<gpw::PlanView> views(nplans);
+  std::vector<int4> wc, wi;
+  for (int i = 0; i < nplans; ++i) {
+    views[i] = gpw::make_view(plans[i]->p);
+    for (int4 w : plans[i]->p.work_c_host) wc.push_back(make_int4(i, w.y, w.z, w.w));
+    for (int4 w : plans[i]->p.work_i_host) wi.push_back(make_int4(i, w.y, w.z, w.w));
+  }
+  auto heavy = [](const int4& x, const int4& y) {
+    if (x.w != y.w) return x.w > y.w;
+    if (x.x != y.x) return x.x < y.x;
+    if (x.y != y.y) return x.y < y.y;
+    return x.z < y.z;
+  };
+  std::stable_sort(wc.begin(), wc.end(), heavy);
+  std::stable_sort(wi.begin(), wi.end(), heavy);
+  auto ensure = [&](int4** ptr, long long* cap, size_t n) -> cudaError_t {
+    if ((long long)n <= *cap) return cudaSuccess;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    *cap = 0;
+    cudaError_t r = cudaMalloc((void**)ptr, sizeof(int4) * std::max<size_t>(n, 1));
+    if (r == cudaSuccess) *cap = (long long)n;
+    return r;
+  };
+  e = ensure(&b->work_c, &b->cap_c, wc.size());
+  if (e == cudaSuccess) e = ensure(&b->work_i, &b->cap_i, wi.size());
+  cudaStream_t s = (cudaStream_t)stream;
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->views, views.data(), sizeof(gpw::PlanView) * views.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !wc.empty())
+    e = cudaMemcpyAsync(b->work_c, wc.data(), sizeof(int4) * wc.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !wi.empty())
+    e = cudaMemcpyAsync(b->work_i, wi.data(), sizeof(int4) * wi.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_error(std::string("gpw_batch_set: ") + cudaGetErrorString(e));
+    return GPW_ECUDA;
+  }
+  b->n = nplans;
+  b->nwc = (long long)wc.size();
+  b->nwi = (long long)wi.size();
+  b->plans.assign(plans, plans + nplans);
+  return GPW_OK;
+}
+
+int gpw_batch_fock_grad_async(gpw_batch_t b, const double* const* D, double* const* V,
+                              double* const* grad, double* energies_dev, void* stream) {
+  if (!b || b->n < 1 || !D || !V || !energies_dev) {
+    set_error("gpw_batch_fock_grad_async: batch not set or NULL argument");
+    return GPW_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = b->n;
+  for (int i = 0; i < n; ++i) {
+    if (!D[i] || !V[i]) {
+      set_error("gpw_batch_fock_grad_async: NULL D or V");
+      return GPW_EINVAL;
+    }
+    int rc = gpw::prep_rho(b->plans[i]->p, D[i], s);
+    if (rc) return rc;
+  }
+  gpw::Plan& P0 = b->plans[0]->p;
+  cudaError_t e = gpw::launch_collocate_views(b->colloc, b->views, b->work_c, b->nwc, P0.d.tabs, s);
+  if (e != cudaSuccess) {
+    set_error(std::string("batch collocation: ") + cudaGetErrorString(e));
+    return GPW_ECUDA;
+  }
+  for (int i = 0; i < n; ++i) {
+    int rc = gpw::potential_from_levels(b->plans[i]->p, energies_dev + 2 * i, nullptr, nullptr, s);
+    if (rc) return rc;
+  }
+  e = gpw::launch_integrate_views(b->integ1, 1, b->views, b->work_i, b->nwi, P0.d.tabs, s);
+  if (e != cudaSuccess) {
+    set_error(std::string("batch integration: ") + cudaGetErrorString(e));
+    return GPW_ECUDA;
+  }
+  for (int i = 0; i < n; ++i) {
+    int rc = gpw::finish_mat_ip1(b->plans[i]->p, D[i], V[i], grad ? grad[i] : nullptr, s);
+    if (rc) return rc;
+  }
+  b->plans[0]->p.launches += 2;
+  return GPW_OK;
+}
+
+void gpw_batch_destroy(gpw_batch_t b) {
+  if (!b) return;
+  if (b->views) cudaFree(b->views);
+  if (b->work_c) cudaFree(b->work_c);
+  if (b->work_i) cudaFree(b->work_i);
+  delete b;
 }
 
 int gpw_check_device(gpw_plan_t plan, int* code, void* stream) {

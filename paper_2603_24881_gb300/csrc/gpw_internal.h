@@ -52,6 +52,25 @@ struct LevelInfo {
   double h[3];           // grid spacing L_d / N_d
 };
 
+// Everything a grid kernel needs from one plan, in device memory, so that one launch can
+// serve the tasks of many plans (work items carry the index of their plan's view).
+struct PlanView {
+  LevelInfo lc[GPW_MAX_LEVELS];  // levels with the collocation sub-box fields
+  LevelInfo li[GPW_MAX_LEVELS];  // levels with the integration sub-box fields
+  const int4* task_c;
+  const long long* sub_off_c;
+  const int4* task_i;
+  const long long* sub_off_i;
+  const long long* tab_off;
+  const long long* coef_off;
+  const long long* part_off;
+  const double* tab;
+  const double* coef;
+  double* part;
+  double* grids;
+  int* err;
+};
+
 struct DeviceArrays {
   // per pair (SoA)
   int4* hot_a = nullptr;      // lo0, lo1, lo2, L = la + lb
@@ -67,10 +86,10 @@ struct DeviceArrays {
   // tasks of the collocation (c) and integration (i) sub-box shapes
   int4* task_c = nullptr;     // 2 per task: {pair, m|L, u, rank}, {t|n per dimension}
   long long* sub_off_c = nullptr;  // CSR offsets over all sub-boxes of all levels
-  int2* work_c = nullptr;     // (level, sub-box) with tasks, heaviest first
+  int4* work_c = nullptr;     // {plan slot (0), level, sub-box, tasks}, heaviest first
   int4* task_i = nullptr;
   long long* sub_off_i = nullptr;
-  int2* work_i = nullptr;
+  int4* work_i = nullptr;
   // V assembly: groups of pairs sharing a contracted shell pair
   int4* groups = nullptr;     // shell a, shell b, first pair, end pair
   // gradient assembly
@@ -91,6 +110,7 @@ struct DeviceArrays {
   double* energies = nullptr; // E_H, E_x (device)
   int* err = nullptr;         // device error word
   CoefTables* tabs = nullptr;
+  PlanView* view = nullptr;   // this plan's view (device)
 };
 
 struct Plan {
@@ -121,6 +141,9 @@ struct Plan {
   std::vector<int> pair_a, pair_b;                     // primitive indices per pair
   std::vector<double> coords;                          // natm * 3
   DeviceArrays d;
+  bool committed = false;
+  struct HostArrays* host = nullptr;       // host staging between prepare and commit
+  std::vector<int4> work_c_host, work_i_host;   // copies kept for batch merging
   cufftHandle fft_d2z[GPW_MAX_LEVELS];
   cufftHandle fft_z2d[GPW_MAX_LEVELS];
   bool fft_made[GPW_MAX_LEVELS] = {false};
@@ -140,6 +163,7 @@ struct Plan {
 
 // plan.cpp (host): screening and task lists; fills everything except device arrays.
 int build_host_plan(const gpw_desc* desc, Plan* plan, struct HostArrays* host);
+PlanView make_view(const Plan& p);
 
 void set_error(const std::string& msg);
 

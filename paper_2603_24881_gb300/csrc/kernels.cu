@@ -289,12 +289,8 @@ struct CollocLayout {
 // The next task's record and pair offsets are fetched while the current one computes.
 template <int T0, int T1, int T2, int NW>
 __global__ void __launch_bounds__(NW * 32)
-    collocate_kernel(const KLevels K, const int2* __restrict__ work,
-                     const long long* __restrict__ sub_off, const int4* __restrict__ task,
-                     const long long* __restrict__ tab_off, const long long* __restrict__ coef_off,
-                     const double* __restrict__ tab, const double* __restrict__ coef,
-                     const CoefTables* __restrict__ tabs, double* __restrict__ grids, int lp,
-                     int stg, int* __restrict__ err) {
+    collocate_kernel(const PlanView* __restrict__ views, const int4* __restrict__ work,
+                     const CoefTables* __restrict__ tabs, int lp, int stg) {
   using Lay = CollocLayout<T0, T1, T2>;
   constexpr int kTileN = T0 * T1 * T2;
   extern __shared__ __align__(16) double sm[];
@@ -307,9 +303,17 @@ __global__ void __launch_bounds__(NW * 32)
   load_tables(s_tab, tabs, tid, NW * 32);
   for (int i = tid; i < NW * kTileN; i += NW * 32) acc_all[i] = 0.0;
 
-  const int2 item = work[blockIdx.x];
-  const LevelInfo& lv = K.lv[item.x];
-  const SubBox sb = sub_box<T0, T1, T2>(lv, item.y, sub_off);
+  const int4 item = work[blockIdx.x];
+  const PlanView& pv = views[item.x];
+  const LevelInfo& lv = pv.lc[item.y];
+  const int4* __restrict__ task = pv.task_c;
+  const long long* __restrict__ tab_off = pv.tab_off;
+  const long long* __restrict__ coef_off = pv.coef_off;
+  const double* __restrict__ tab = pv.tab;
+  const double* __restrict__ coef = pv.coef;
+  double* __restrict__ grids = pv.grids;
+  int* __restrict__ err = pv.err;
+  const SubBox sb = sub_box<T0, T1, T2>(lv, item.z, pv.sub_off_c);
 
   double* acc = acc_all + warp * kTileN;
   double* stage_base = acc_all + NW * kTileN + warp * stg;
@@ -496,12 +500,8 @@ struct IntegLayout {
 
 template <int T0, int T1, int T2, int NW>
 __global__ void __launch_bounds__(NW * 32)
-    integrate_kernel(const KLevels K, const int2* __restrict__ work,
-                     const long long* __restrict__ sub_off, const int4* __restrict__ task,
-                     const long long* __restrict__ tab_off, const long long* __restrict__ part_off,
-                     const double* __restrict__ tab, const CoefTables* __restrict__ tabs,
-                     const double* __restrict__ grids, double* __restrict__ part, int lext,
-                     int lpx, int stg, int* __restrict__ err) {
+    integrate_kernel(const PlanView* __restrict__ views, const int4* __restrict__ work,
+                     const CoefTables* __restrict__ tabs, int lext, int lpx, int stg) {
   using Lay = IntegLayout<T0, T1, T2>;
   constexpr int P0 = Lay::P0, P1 = Lay::P1, P2 = Lay::P2, kUS = Lay::kUS;
   extern __shared__ __align__(16) double sm[];
@@ -513,9 +513,17 @@ __global__ void __launch_bounds__(NW * 32)
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   load_tables(s_tab, tabs, tid, NW * 32);
 
-  const int2 item = work[blockIdx.x];
-  const LevelInfo& lv = K.lv[item.x];
-  const SubBox sb = sub_box<T0, T1, T2>(lv, item.y, sub_off);
+  const int4 item = work[blockIdx.x];
+  const PlanView& pv = views[item.x];
+  const LevelInfo& lv = pv.li[item.y];
+  const int4* __restrict__ task = pv.task_i;
+  const long long* __restrict__ tab_off = pv.tab_off;
+  const long long* __restrict__ part_off = pv.part_off;
+  const double* __restrict__ tab = pv.tab;
+  const double* __restrict__ grids = pv.grids;
+  double* __restrict__ part = pv.part;
+  int* __restrict__ err = pv.err;
+  const SubBox sb = sub_box<T0, T1, T2>(lv, item.z, pv.sub_off_i);
   {
     const double* vin = grids + lv.grid_off;
     const int e12 = sb.ext[1] * sb.ext[2];
@@ -1117,16 +1125,16 @@ cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_collocate(const Plan& p, cudaStream_t s) {
-  if (p.nwork == 0) return cudaSuccess;
-  const int t0 = p.tile[0], t1 = p.tile[1], t2 = p.tile[2];
-  ++p.launches;
-#define GPW_COLLOC_NW(a, b, c, nw)                                                         \
-  if (t0 == a && t1 == b && t2 == c && p.nw_colloc == nw) {                                \
-    collocate_kernel<a, b, c, nw><<<(int)p.nwork, nw * 32, p.smem_colloc, s>>>(            \
-        make_klevels(p, false), p.d.work_c, p.d.sub_off_c, p.d.task_c, p.d.tab_off,         \
-        p.d.coef_off, p.d.tab, p.d.coef, p.d.tabs, p.d.grids, p.lmax + 1, p.stg_colloc,     \
-        p.d.err);                                                                          \
+// Collocation over `nwork` work items of the views in `views` (one plan, or a batch of
+// plans sharing the sub-box shapes); cfg gives the launch shape.
+cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views, const int4* work,
+                                   long long nwork, const CoefTables* tabs, cudaStream_t s) {
+  if (nwork == 0) return cudaSuccess;
+  const int t0 = cfg.tile[0], t1 = cfg.tile[1], t2 = cfg.tile[2];
+#define GPW_COLLOC_NW(a, b, c, NWV)                                                        \
+  if (t0 == a && t1 == b && t2 == c && cfg.nw == NWV) {                                    \
+    collocate_kernel<a, b, c, NWV><<<(int)nwork, NWV * 32, cfg.smem, s>>>(                 \
+        views, work, tabs, cfg.lp, cfg.stg);                                               \
     return cudaGetLastError();                                                             \
   }
 #define GPW_TILE_COLLOC(a, b, c) GPW_COLLOC_NW(a, b, c, 8) GPW_COLLOC_NW(a, b, c, 6) GPW_COLLOC_NW(a, b, c, 4)
@@ -1136,23 +1144,99 @@ cudaError_t launch_collocate(const Plan& p, cudaStream_t s) {
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s) {
-  if (p.nwork_i == 0) return cudaSuccess;
-  const int t0 = p.tile_i[0], t1 = p.tile_i[1], t2 = p.tile_i[2];
-  ++p.launches;
+cudaError_t launch_integrate_views(const GridLaunch& cfg, int lext, const PlanView* views,
+                                   const int4* work, long long nwork, const CoefTables* tabs,
+                                   cudaStream_t s) {
+  if (nwork == 0) return cudaSuccess;
+  const int t0 = cfg.tile[0], t1 = cfg.tile[1], t2 = cfg.tile[2];
 #define GPW_TILE_INTEG(a, b, c)                                                            \
   if (t0 == a && t1 == b && t2 == c) {                                                     \
-    integrate_kernel<a, b, c, kNW><<<(int)p.nwork_i, kNW * 32,                             \
-                                     lext ? p.smem_integ1 : p.smem_integ, s>>>(            \
-        make_klevels(p, true), p.d.work_i, p.d.sub_off_i, p.d.task_i, p.d.tab_off,          \
-        p.d.part_off,                                                                      \
-        p.d.tab, p.d.tabs, p.d.grids, p.d.part, lext, p.lmax + lext + 1,                    \
-        lext ? p.stg_integ1 : p.stg_integ, p.d.err);                                       \
+    integrate_kernel<a, b, c, kNW><<<(int)nwork, kNW * 32, cfg.smem, s>>>(                 \
+        views, work, tabs, lext, cfg.lp, cfg.stg);                                         \
     return cudaGetLastError();                                                             \
   }
   GPW_TILE_SHAPES(GPW_TILE_INTEG)
 #undef GPW_TILE_INTEG
   return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_collocate(const Plan& p, cudaStream_t s) {
+  if (p.nwork == 0) return cudaSuccess;
+  ++p.launches;
+  GridLaunch cfg;
+  for (int d = 0; d < 3; ++d) cfg.tile[d] = p.tile[d];
+  cfg.nw = p.nw_colloc;
+  cfg.lp = p.lmax + 1;
+  cfg.stg = p.stg_colloc;
+  cfg.smem = p.smem_colloc;
+  return launch_collocate_views(cfg, p.d.view, p.d.work_c, p.nwork, p.d.tabs, s);
+}
+
+cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s) {
+  if (p.nwork_i == 0) return cudaSuccess;
+  ++p.launches;
+  GridLaunch cfg;
+  for (int d = 0; d < 3; ++d) cfg.tile[d] = p.tile_i[d];
+  cfg.nw = kNW;
+  cfg.lp = p.lmax + lext + 1;
+  cfg.stg = lext ? p.stg_integ1 : p.stg_integ;
+  cfg.smem = lext ? p.smem_integ1 : p.smem_integ;
+  return launch_integrate_views(cfg, lext, p.d.view, p.d.work_i, p.nwork_i, p.d.tabs, s);
+}
+
+// Launch shapes for a batch of plans with the same sub-boxes and largest degree lmax.
+cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, GridLaunch* colloc,
+                            GridLaunch* integ1) {
+  int dev = 0, per_sm = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  if (e != cudaSuccess) return e;
+  int found = 0;
+  for (int d = 0; d < 3; ++d) {
+    colloc->tile[d] = tile_c[d];
+    integ1->tile[d] = tile_i[d];
+  }
+  colloc->lp = lmax + 1;
+  integ1->lp = lmax + 2;
+  integ1->nw = kNW;
+#define GPW_TILE_BCONF(a, b, c)                                                             \
+  if (tile_c[0] == a && tile_c[1] == b && tile_c[2] == c) {                                 \
+    found |= 1;                                                                             \
+    colloc->stg = even(CollocLayout<a, b, c>::stage(lmax + 1));                             \
+    if (pick_colloc_warps((size_t)per_sm, colloc_smem<a, b, c>, colloc->stg, &colloc->nw,    \
+                          &colloc->smem) == 0)                                              \
+      return cudaErrorInvalidValue;                                                         \
+  }                                                                                         \
+  if (tile_i[0] == a && tile_i[1] == b && tile_i[2] == c) {                                 \
+    found |= 2;                                                                             \
+    integ1->stg = even(IntegLayout<a, b, c>::stage(lmax + 2));                              \
+    integ1->smem = integ_smem<a, b, c>(integ1->stg);                                        \
+  }
+  GPW_TILE_SHAPES(GPW_TILE_BCONF)
+#undef GPW_TILE_BCONF
+  return found == 3 ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+PlanView make_view(const Plan& p) {
+  PlanView v;
+  for (int k = 0; k < GPW_MAX_LEVELS; ++k) {
+    v.lc[k] = p.lev[k];
+    v.li[k] = p.lev_i[k];
+  }
+  v.task_c = p.d.task_c;
+  v.sub_off_c = p.d.sub_off_c;
+  v.task_i = p.d.task_i;
+  v.sub_off_i = p.d.sub_off_i;
+  v.tab_off = p.d.tab_off;
+  v.coef_off = p.d.coef_off;
+  v.part_off = p.d.part_off;
+  v.tab = p.d.tab;
+  v.coef = p.d.coef;
+  v.part = p.d.part;
+  v.grids = p.d.grids;
+  v.err = p.d.err;
+  return v;
 }
 
 cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s) {

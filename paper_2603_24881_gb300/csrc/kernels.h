@@ -12,6 +12,20 @@ struct KLevels {
 
 KLevels make_klevels(const Plan& p, bool integ);
 
+// Launch shape of a grid kernel: sub-box, warps per block, factor rows, staging, smem.
+struct GridLaunch {
+  int tile[3];
+  int nw, lp, stg;
+  size_t smem;
+};
+cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views, const int4* work,
+                                   long long nwork, const CoefTables* tabs, cudaStream_t s);
+cudaError_t launch_integrate_views(const GridLaunch& cfg, int lext, const PlanView* views,
+                                   const int4* work, long long nwork, const CoefTables* tabs,
+                                   cudaStream_t s);
+cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, GridLaunch* colloc,
+                            GridLaunch* integ1);
+
 cudaError_t launch_tables(const Plan& p, cudaStream_t s);
 cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s);
 cudaError_t launch_collocate(const Plan& p, cudaStream_t s);

@@ -151,7 +151,7 @@ std::vector<PairBox> pairs_view(const std::vector<PairTmp>& pairs) {
 // non-NULL, the number of tasks of every pair.
 int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector<int4>& hot_a,
                 const int* T, LevelInfo* lev, std::vector<long long>* sub_off,
-                std::vector<int4>* task, std::vector<int2>* work, long long* nent_out,
+                std::vector<int4>* task, std::vector<int4>* work, long long* nent_out,
                 long long* nwork_out, long long* nsub_out, std::vector<int>* ranks) {
   const int K = plan->nlev;
   const long long np = (long long)pairs.size();
@@ -231,7 +231,7 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
     long long sidx = w[i].second;
     int k = 0;
     while (k + 1 < K && lev[k + 1].sub_base <= sidx) ++k;
-    (*work)[i] = make_int2(k, (int)(sidx - lev[k].sub_base));
+    (*work)[i] = make_int4(0, k, (int)(sidx - lev[k].sub_base), (int)std::min<long long>(-w[i].first, 1 << 30));
   }
   *nwork_out = (long long)w.size();
   return GPW_OK;

@@ -13,7 +13,7 @@ struct HostArrays {
   std::vector<long long> tab_off, coef_off, part_off;
   std::vector<int4> task_c, task_i;   // 2 int4 per task
   std::vector<long long> sub_off_c, sub_off_i;
-  std::vector<int2> work_c, work_i;
+  std::vector<int4> work_c, work_i;   // {plan slot, level, sub-box, tasks}
   std::vector<int4> groups;
   std::vector<long long> atom_off;
   std::vector<int> atom_list;

@@ -1,0 +1,149 @@
+"""Batched launches and the continuous-batching server: every result equals the same
+request run alone (1e-10 relative in V, 1e-8 Ha in energies, 1e-7 Ha/Bohr in gradients),
+admission respects the device-memory budget, and failures stay with their request."""
+import numpy as np
+import pytest
+
+import workloads
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+RTOL = 1e-10
+
+
+@pytest.fixture(scope="module")
+def gpw():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2603_24881_gb300 as g
+    g.load()
+    return g
+
+
+def _systems():
+    return [workloads.small_water(4, seed=101), workloads.small_water(8, seed=102),
+            workloads.tiny(), workloads.small_water(4, seed=103),
+            workloads.small_water(16, seed=104)]
+
+
+@pytest.fixture(scope="module")
+def alone(gpw):
+    out = []
+    for s in _systems():
+        p = gpw.Plan(s)
+        r = p.fock_grad(s.D)
+        out.append(dict(V=r["V"].cpu().numpy(), grad=r["grad"].cpu().numpy(), EH=r["EH"], Ex=r["Ex"]))
+        p.close()
+    return out
+
+
+def _same(res, ref, grad=True):
+    assert abs(res["EH"] - ref["EH"]) <= 1e-8 and abs(res["Ex"] - ref["Ex"]) <= 1e-8
+    V = np.asarray(res["V"])
+    assert np.max(np.abs(V - ref["V"])) <= RTOL * np.max(np.abs(ref["V"]))
+    if grad:
+        assert np.max(np.abs(np.asarray(res["grad"]) - ref["grad"])) <= 1e-7
+
+
+def test_prepare_reports_footprint(gpw):
+    s = workloads.small_water(8, seed=102)
+    p = gpw.Plan(s, commit=False)
+    est = p.stats()["device_bytes"]
+    assert not p.committed and est > 0
+    p.commit()
+    act = p.stats()["device_bytes"]
+    assert 0.8 * act <= est <= 1.25 * act
+    r = p.fock(s.D)
+    assert np.isfinite(r["EH"])
+
+
+def test_batch_matches_alone(gpw, alone):
+    systems = _systems()
+    plans = [gpw.Plan(s) for s in systems]
+    b = gpw.Batch(8).set(plans)
+    Ds = [torch.as_tensor(s.D, device="cuda") for s in systems]
+    Vs = [torch.empty((p.nao, p.nao), dtype=torch.float64, device="cuda") for p in plans]
+    gs = [torch.empty((p.natm, 3), dtype=torch.float64, device="cuda") for p in plans]
+    E = torch.empty(2 * len(plans), dtype=torch.float64, device="cuda")
+    for _ in range(2):  # the batch is reusable
+        b.fock_grad_async(Ds, Vs, gs, E)
+        torch.cuda.synchronize()
+        e = E.cpu().numpy()
+        for i, ref in enumerate(alone):
+            _same(dict(V=Vs[i].cpu().numpy(), grad=gs[i].cpu().numpy(), EH=e[2 * i], Ex=e[2 * i + 1]), ref)
+    for p in plans:
+        assert p.check_device() == 0
+        p.close()
+    b.close()
+
+
+def test_batch_in_cuda_graph(gpw, alone):
+    systems = _systems()[:3]
+    plans = [gpw.Plan(s) for s in systems]
+    b = gpw.Batch(4).set(plans)
+    Ds = [torch.as_tensor(s.D, device="cuda") for s in systems]
+    Vs = [torch.empty((p.nao, p.nao), dtype=torch.float64, device="cuda") for p in plans]
+    gs = [torch.empty((p.natm, 3), dtype=torch.float64, device="cuda") for p in plans]
+    E = torch.empty(2 * len(plans), dtype=torch.float64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        b.fock_grad_async(Ds, Vs, gs, E, stream=s)  # warm-up outside capture
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        b.fock_grad_async(Ds, Vs, gs, E, stream=s)
+    for V in Vs:
+        V.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    e = E.cpu().numpy()
+    for i in range(len(plans)):
+        _same(dict(V=Vs[i].cpu().numpy(), grad=gs[i].cpu().numpy(), EH=e[2 * i], Ex=e[2 * i + 1]), alone[i])
+    for p in plans:
+        p.close()
+
+
+def test_server_results_equal_alone(gpw, alone):
+    from paper_2603_24881_gb300.serve import Server
+    systems = _systems()
+    with Server(max_batch=3, streams=2) as srv:
+        futs = [srv.submit(s, want_grad=True) for s in systems]
+        # a second wave arrives while the first is in flight
+        futs += [srv.submit(s, want_grad=(i % 2 == 0)) for i, s in enumerate(systems)]
+        res = [f.result(timeout=300) for f in futs]
+        stats = dict(srv.stats)
+    for i, r in enumerate(res):
+        ref = alone[i % len(systems)]
+        _same(dict(V=r.V, grad=r.grad, EH=r.EH, Ex=r.Ex), ref, grad=r.grad is not None)
+    assert stats["admitted"] == len(futs)
+    assert stats["batches"] >= 4  # at most 3 per batch
+
+
+def test_server_memory_budget_and_failures(gpw, alone):
+    from paper_2603_24881_gb300.serve import Server
+    systems = _systems()
+    probe = gpw.Plan(systems[4], commit=False)
+    big = probe.stats()["device_bytes"]
+    probe.close()
+    # budget fits the largest request but not two of them at once
+    budget = int(1.5 * big)
+    huge = workloads.small_water(64, seed=7)
+    fail = lambda s: s is systems[3]
+    with Server(hbm_budget=budget, max_batch=8, streams=2, fail_prepare=fail) as srv:
+        futs = [srv.submit(s, want_grad=True) for s in systems]
+        fh = srv.submit(huge)
+        out = []
+        for i, f in enumerate(futs):
+            if i == 3:
+                with pytest.raises(RuntimeError):
+                    f.result(timeout=300)
+                continue
+            out.append((i, f.result(timeout=300)))
+        with pytest.raises(MemoryError):
+            fh.result(timeout=300)
+        stats = dict(srv.stats)
+    for i, r in out:
+        _same(dict(V=r.V, grad=r.grad, EH=r.EH, Ex=r.Ex), alone[i])
+    assert stats["peak_bytes"] <= budget
+    assert stats["rejected"] == 2
