@@ -67,6 +67,8 @@ def _args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-stride", type=int, default=8)
+    ap.add_argument("--served", type=int, default=400,
+                    help="also run the served request stream with this many requests")
     ap.add_argument("--tile", default=None, help="collocation sub-box t0,t1,t2")
     ap.add_argument("--tile-integ", default=None, help="integration sub-box t0,t1,t2")
     return ap.parse_args()
@@ -186,6 +188,57 @@ def run_reference(a, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ served -----
+def served_bench(nreq: int) -> dict:
+    """The served stream (water boxes of 4..128 molecules, p ~ 1/n, 10% gradients):
+    saturated builds/s of the continuous-batching server, then a replay with Poisson
+    arrivals at 80% of it for p50/p99 latency, against one plain launch sequence per
+    request, and the largest per-request disagreement between the two."""
+    import numpy as np
+    import workloads
+    from paper_2603_24881_gb300.serve import Server, run_plain
+    reqs = workloads.stream_requests(nreq, seed=4)
+    systems = [r.system() for r in reqs]
+    grads = [r.want_grad for r in reqs]
+    with Server() as srv:  # warm-up: kernels, cuFFT and allocator
+        [f.result() for f in [srv.submit(s, g) for s, g in zip(systems[:4], grads[:4])]]
+    with Server() as srv:
+        t0 = time.perf_counter()
+        futs = [srv.submit(s, g) for s, g in zip(systems, grads)]
+        sat = [f.result() for f in futs]
+        t_sat = time.perf_counter() - t0
+        st_sat = dict(srv.stats)
+    rate = 0.8 * nreq / t_sat
+    arr = [r.arrival for r in workloads.stream_requests(nreq, seed=4, rate=rate)]
+    with Server() as srv:
+        t0 = time.perf_counter()
+        futs = []
+        for s, g, ta in zip(systems, grads, arr):
+            dt = ta - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            futs.append(srv.submit(s, g))
+        pois = [f.result() for f in futs]
+        t_pois = max(r.t_done for r in pois) - t0
+    lat = np.array([r.latency for r in pois])
+    plain, t_plain = run_plain(systems, grads)
+    plat = np.array([r.latency for r in plain])
+    dE = max(max(abs(a.EH - b.EH), abs(a.Ex - b.Ex)) for a, b in zip(sat, plain))
+    dV = max(float(np.max(np.abs(a.V - b.V)) / max(np.max(np.abs(b.V)), 1e-300))
+             for a, b in zip(sat, plain))
+    dg = max((float(np.max(np.abs(a.grad - b.grad))) for a, b in zip(sat, plain)
+              if a.grad is not None), default=0.0)
+    return {"requests": nreq, "builds_per_s_saturated": nreq / t_sat,
+            "builds_per_s_poisson": nreq / t_pois, "poisson_rate_per_s": rate,
+            "p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+            "plain_builds_per_s": nreq / t_plain,
+            "plain_p50_ms": 1e3 * float(np.percentile(plat, 50)),
+            "plain_p99_ms": 1e3 * float(np.percentile(plat, 99)),
+            "speedup_vs_plain": t_plain / t_sat, "batches": st_sat["batches"],
+            "max_abs_dE_Ha": dE, "max_rel_dV": dV, "max_abs_dgrad": dg,
+            "stream": "water boxes n in {4,8,16,32,64,128}, p ~ 1/n, 10% gradients, seed 4"}
+
+
 # ------------------------------------------------------------------ main -------
 def main():
     a = _args()
@@ -303,6 +356,7 @@ def main():
             except Exception as ex:  # the CPU oracle is a reported baseline only
                 cpu = {"value": None, "unit": "TFLOP/s", "cores": os.cpu_count(),
                        "kind": "oracle", "sample": f"failed: {ex}"}
+        served = served_bench(a.served) if a.served > 0 else None
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -316,7 +370,7 @@ def main():
                 "pair_points_per_s": st["pair_points"] * a.steps * world / (ms * 1e-3),
                 "plan_ms": plan_ms, "phase_ms_per_step": {k: v / a.steps for k, v in prof["ms"].items()},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
-                "gpu_launches": launches, "clocks": clocks}
+                "gpu_launches": launches, "clocks": clocks, "served": served}
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
