@@ -88,7 +88,7 @@ typedef struct {
   double tau;                 /* screening threshold of Eq. (cut) */
   int flags;                  /* GPW_STRICT */
   int tile[3];                /* sub-box owned by one collocation thread block (grid
-                                 points along a1, a2, a3); {0,0,0} = default {8,8,16} */
+                                 points along a1, a2, a3); {0,0,0} = default {4,8,16} */
   int tile_integ[3];          /* sub-box of one integration thread block;
                                  {0,0,0} = default {4,8,64}.  Supported shapes:
                                  gpw_tile_supported. */

@@ -78,7 +78,7 @@ void free_plan(Plan* P) {
   void* ptrs[] = {d.hot_a, d.hot_b, d.ids, d.ids2, d.geo, d.cab, d.pref, d.tab_off,
                   d.coef_off, d.part_off, d.task_c, d.sub_off_c, d.work_c, d.task_i, d.sub_off_i, d.work_i, d.groups, d.atom_off,
                   d.atom_list, d.tab, d.coef, d.part, d.pgrad, d.grids, d.spec, d.fspec,
-                  d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs, d.view};
+                  d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs, d.view, d.g2tab};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
@@ -109,6 +109,7 @@ long long estimate_bytes(const Plan& P, const HostArrays& H) {
   b += sz(P.tab_total + P.coef_total + P.part_total + 6 * P.npairs + P.grid_total, sizeof(double));
   b += sz(P.spec_total + 2 * P.fine_spec_n, sizeof(cufftDoubleComplex));
   b += sz(2 * P.fine_n + 2 * 304 + 2, sizeof(double)) + sizeof(int) + sizeof(CoefTables) + sizeof(PlanView);
+  b += sz((long long)P.lev[0].N[0] + P.lev[0].N[1] + P.lev[0].N[2], sizeof(double));
   for (int k = 0; k < P.nlev; ++k) {
     size_t ws = 0;
     if (cufftEstimate3d(P.lev[k].N[0], P.lev[k].N[1], P.lev[k].N[2], CUFFT_D2Z, &ws) == CUFFT_SUCCESS)
@@ -155,6 +156,20 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
   GPW_TRY(dalloc(&d.fine_a, P->fine_n, &b));
   GPW_TRY(dalloc(&d.fine_b, P->fine_n, &b));
   GPW_TRY(dalloc(&d.red, 2 * kRedBlocks, &b));
+  {
+    // ((2 pi s)/L_d)^2 per finest-mesh index along each axis, s the signed frequency,
+    // formed exactly as the reference does: (2 pi s)/L, squared
+    const LevelInfo& f = P->lev[0];
+    std::vector<double> g2(f.N[0] + f.N[1] + f.N[2]);
+    int o = 0;
+    for (int dd = 0; dd < 3; ++dd)
+      for (int m = 0; m < f.N[dd]; ++m) {
+        const int sf = m < (f.N[dd] + 1) / 2 ? m : m - f.N[dd];
+        const double g = 2.0 * M_PI * (double)sf / P->L[dd];
+        g2[o++] = g * g;
+      }
+    GPW_TRY(upload(&d.g2tab, g2, &b));
+  }
   GPW_TRY(dalloc(&d.energies, 2, &b));
   GPW_TRY(dalloc(&d.err, 1, &b));
   GPW_CK(cudaMemset(d.err, 0, sizeof(int)));

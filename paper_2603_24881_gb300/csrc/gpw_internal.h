@@ -22,7 +22,7 @@ constexpr int kNc2Max = (kLextMax + 1) * (kLextMax + 2) / 2;                   /
 
 // Default sub-box (tile) owned by one thread block: T0 x T1 x T2 grid points, the last
 // along the fastest grid index.  The shape is a plan parameter (see kTileShapes).
-constexpr int kT0 = 8, kT1 = 8, kT2 = 16;
+constexpr int kT0 = 4, kT1 = 8, kT2 = 16;
 
 // Number of monomials x^l0 y^l1 z^l2 with l0 + l1 + l2 <= L, and of (l1, l2) pairs.
 __host__ __device__ constexpr int nc3(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
@@ -107,6 +107,7 @@ struct DeviceArrays {
   double* fine_a = nullptr;   // finest real scratch
   double* fine_b = nullptr;
   double* red = nullptr;      // reduction partials
+  double* g2tab = nullptr;    // ((2 pi s)/L_d)^2 per finest-mesh index along each axis
   double* energies = nullptr; // E_H, E_x (device)
   int* err = nullptr;         // device error word
   CoefTables* tabs = nullptr;

@@ -271,9 +271,10 @@ struct CollocLayout {
   __host__ __device__ static int buf(int lp) {
     return (lp * (T0 + T1 + T2) + nc3(lp - 1) + 1) & ~1;
   }
-  // per-warp staging: two buffers plus the T1 and T2 intermediates
+  // per-warp staging: two buffers, the T1 and T2 intermediates and two row tables
+  // (T0*T1 ints each: q -> accumulator offset of the row, q -> (i0, i1))
   __host__ __device__ static int stage(int lp) {
-    return 2 * buf(lp) + nc2(lp - 1) * T0 + lp * T0 * T1;
+    return 2 * buf(lp) + nc2(lp - 1) * T0 + lp * T0 * T1 + T0 * T1;
   }
 };
 
@@ -320,6 +321,8 @@ __global__ void __launch_bounds__(NW * 32)
   const int bufn = Lay::buf(lp);
   double* sT1 = stage_base + 2 * bufn;
   double* sT2 = sT1 + nc2(lp - 1) * T0;
+  int* s_row = reinterpret_cast<int*>(sT2 + lp * T0 * T1);
+  int* s_qi = s_row + T0 * T1;
   __syncthreads();
 
   // staging buffer b: [sg0 lp*T0][sg1 lp*T1][sg2 lp*T2][D nc3]
@@ -376,6 +379,13 @@ __global__ void __launch_bounds__(NW * 32)
       const double* sg1 = sg0 + lp * T0;
       const double* sg2 = sg1 + lp * T1;
       const double* sD = sg2 + lp * T2;
+      const int m01 = m0 * m1;
+      // per-task row tables: q = i0 m1 + i1 -> (i0, i1) and accumulator offset of the row
+      for (int q = lane; q < m01; q += 32) {
+        const int i0 = q / m1, i1 = q - i0 * m1;
+        s_qi[q] = i0 | (i1 << 8);
+        s_row[q] = ((tk.u[0] + i0) * T1 + (tk.u[1] + i1)) * T2 + tk.u[2];
+      }
       // T1[c21](i0)
       {
         const float inv = __frcp_rn((float)m0);
@@ -390,57 +400,70 @@ __global__ void __launch_bounds__(NW * 32)
         }
       }
       __syncwarp();
-      // T2[l2](q = i0 m1 + i1); two items per lane in flight (independent FMA chains)
-      const int m01 = m0 * m1;
+      // T2[l2](q): items it = l2 m01 + q, two per lane in flight (independent FMA chains);
+      // the item index advances by 32 with a carry instead of a division per item
       {
-        const float inv01 = __frcp_rn((float)m01), inv1 = __frcp_rn((float)m1);
-        const int items = (L + 1) * m01;
-        for (int base = 0; base < items; base += 64) {
-          const int itA = min(base + lane, items - 1);
-          const int itB = min(base + 32 + lane, items - 1);
-          const int l2A = fdiv(itA, inv01), qA = itA - l2A * m01;
-          const int i0A = fdiv(qA, inv1), i1A = qA - i0A * m1;
-          const int l2B = fdiv(itB, inv01), qB = itB - l2B * m01;
-          const int i0B = fdiv(qB, inv1), i1B = qB - i0B * m1;
-          const int cbA = s_c21b[L][l2A], cbB = s_c21b[L][l2B];
-          const int nA = L - l2A, nB = base + 32 < items ? L - l2B : -1;
+        const int dl = 32 / m01, dq = 32 - dl * m01;
+        int l2A = lane / m01, qA = lane - l2A * m01;
+        for (int base = 0; base < (L + 1) * m01; base += 64) {
+          int l2B = l2A + dl, qB = qA + dq;
+          if (qB >= m01) {
+            qB -= m01;
+            ++l2B;
+          }
+          const int nA = l2A <= L ? L - l2A : -1, nB = l2B <= L ? L - l2B : -1;
+          const int piA = s_qi[qA], piB = s_qi[qB];
+          const int i0A = piA & 255, i1A = piA >> 8, i0B = piB & 255, i1B = piB >> 8;
+          const int cbA = s_c21b[L][min(l2A, L)], cbB = s_c21b[L][min(l2B, L)];
           double a = 0.0, b = 0.0;
           for (int l1 = 0; l1 <= max(nA, nB); ++l1) {
             if (l1 <= nA) a = fma(sT1[(cbA + l1) * T0 + i0A], sg1[l1 * T1 + i1A], a);
             if (l1 <= nB) b = fma(sT1[(cbB + l1) * T0 + i0B], sg1[l1 * T1 + i1B], b);
           }
-          if (base + lane < items) sT2[l2A * (T0 * T1) + qA] = a;
-          if (base + 32 + lane < items) sT2[l2B * (T0 * T1) + qB] = b;
+          if (nA >= 0) sT2[l2A * (T0 * T1) + qA] = a;
+          if (nB >= 0) sT2[l2B * (T0 * T1) + qB] = b;
+          l2A = l2B + dl;
+          qA = qB + dq;
+          if (qA >= m01) {
+            qA -= m01;
+            ++l2A;
+          }
         }
       }
       __syncwarp();
-      // rho(i0,i1,i2) += sum_l2 T2[l2](q) g2[l2](i2); two points per lane in flight
+      // rho(q, i2) += sum_l2 T2[l2](q) g2[l2](i2); items it = q m2 + i2, two per lane in
+      // flight, advanced by 32 with a carry
       {
-        const float inv2 = __frcp_rn((float)m2), inv1 = __frcp_rn((float)m1);
+        const int dq = 32 / m2, di = 32 - dq * m2;
+        int qA = lane / m2, iA = lane - qA * m2;
         const int items = m01 * m2;
-        const int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
         for (int base = 0; base < items; base += 64) {
-          const bool two = base + 32 < items;  // warp-uniform
-          const bool okA = base + lane < items, okB = base + 32 + lane < items;
-          const int itA = min(base + lane, items - 1), itB = min(base + 32 + lane, items - 1);
-          const int qA = fdiv(itA, inv2), i2A = itA - qA * m2;
-          const int i0A = fdiv(qA, inv1), i1A = qA - i0A * m1;
-          const int qB = fdiv(itB, inv2), i2B = itB - qB * m2;
-          const int i0B = fdiv(qB, inv1), i1B = qB - i0B * m1;
-          double* pa = acc + ((u0 + i0A) * T1 + (u1 + i1A)) * T2 + (u2 + i2A);
-          double* pb = acc + ((u0 + i0B) * T1 + (u1 + i1B)) * T2 + (u2 + i2B);
-          if (two) {
+          int qB = qA + dq, iB = iA + di;
+          if (iB >= m2) {
+            iB -= m2;
+            ++qB;
+          }
+          const bool okA = qA < m01, okB = qB < m01;
+          double* pa = acc + s_row[okA ? qA : 0] + iA;
+          double* pb = acc + s_row[okB ? qB : 0] + iB;
+          if (base + 32 < items) {
             double ra = okA ? *pa : 0.0, rb = okB ? *pb : 0.0;
             for (int l2 = 0; l2 <= L; ++l2) {
-              ra = fma(sT2[l2 * (T0 * T1) + qA], sg2[l2 * T2 + i2A], ra);
-              rb = fma(sT2[l2 * (T0 * T1) + qB], sg2[l2 * T2 + i2B], rb);
+              ra = fma(sT2[l2 * (T0 * T1) + (okA ? qA : 0)], sg2[l2 * T2 + iA], ra);
+              rb = fma(sT2[l2 * (T0 * T1) + (okB ? qB : 0)], sg2[l2 * T2 + iB], rb);
             }
             if (okA) *pa = ra;
             if (okB) *pb = rb;
           } else if (okA) {
             double ra = *pa;
-            for (int l2 = 0; l2 <= L; ++l2) ra = fma(sT2[l2 * (T0 * T1) + qA], sg2[l2 * T2 + i2A], ra);
+            for (int l2 = 0; l2 <= L; ++l2) ra = fma(sT2[l2 * (T0 * T1) + qA], sg2[l2 * T2 + iA], ra);
             *pa = ra;
+          }
+          qA = qB + dq;
+          iA = iB + di;
+          if (iA >= m2) {
+            iA -= m2;
+            ++qA;
           }
         }
       }
@@ -671,9 +694,17 @@ __global__ void reduce_parts_kernel(long long np, const KLevels K, const int4* _
     const double* src = part + part_off[p];
     double* dst = coef + coef_off[p];
     for (int c = lane; c < nc; c += 32) {
-      double a = 0.0;
-      for (int r = 0; r < nt; ++r) a += src[(long long)r * nc + c];
-      dst[c] = wgt * a;
+      // four interleaved partial sums keep four loads in flight; fixed order
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int r = 0;
+      for (; r + 3 < nt; r += 4) {
+        a0 += src[(long long)r * nc + c];
+        a1 += src[(long long)(r + 1) * nc + c];
+        a2 += src[(long long)(r + 2) * nc + c];
+        a3 += src[(long long)(r + 3) * nc + c];
+      }
+      for (; r < nt; ++r) a0 += src[(long long)r * nc + c];
+      dst[c] = wgt * ((a0 + a1) + (a2 + a3));
     }
   }
 }
@@ -831,18 +862,32 @@ __global__ void grad_pair_kernel(long long np, const int4* __restrict__ ids,
   out[5] = gB2;
 }
 
+// Per-atom sums of the per-pair gradient sextets: one warp per atom, lanes stride its
+// (pair, side) list in order and a fixed shuffle tree combines them (deterministic).
 __global__ void grad_atom_kernel(int natm, const long long* __restrict__ atom_off,
                                  const int* __restrict__ atom_list,
                                  const double* __restrict__ pgrad, double* __restrict__ grad) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * natm) return;
-  const int atom = t / 3, d = t - 3 * atom;
-  double s = 0.0;
-  for (long long i = atom_off[atom]; i < atom_off[atom + 1]; ++i) {
+  const int lane = threadIdx.x & 31;
+  const int atom = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (atom >= natm) return;
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+  for (long long i = atom_off[atom] + lane; i < atom_off[atom + 1]; i += 32) {
     const int code = atom_list[i];
-    s += pgrad[6LL * (code >> 1) + 3 * (code & 1) + d];
+    const double* g = pgrad + 6LL * (code >> 1) + 3 * (code & 1);
+    s0 += g[0];
+    s1 += g[1];
+    s2 += g[2];
   }
-  grad[t] = s;
+  for (int o = 16; o > 0; o >>= 1) {
+    s0 += __shfl_xor_sync(0xffffffffu, s0, o);
+    s1 += __shfl_xor_sync(0xffffffffu, s1, o);
+    s2 += __shfl_xor_sync(0xffffffffu, s2, o);
+  }
+  if (lane == 0) {
+    grad[3 * atom] = s0;
+    grad[3 * atom + 1] = s1;
+    grad[3 * atom + 2] = s2;
+  }
 }
 
 // ----------------------------------------------------------------------------------
@@ -851,21 +896,17 @@ __global__ void grad_atom_kernel(int natm, const long long* __restrict__ atom_of
 // the reference (Sec. II multigrid, Eq. vHG).
 __device__ __forceinline__ int signed_freq(int m, int N) { return m < (N + 1) / 2 ? m : m - N; }
 
-__device__ __forceinline__ double gsq(int s0, int s1, int s2, const double* Ld) {
-  const double tp = 6.283185307179586;  // 2 pi in double
-  double g0 = __ddiv_rn(__dmul_rn(tp, (double)s0), Ld[0]);
-  double g1 = __ddiv_rn(__dmul_rn(tp, (double)s1), Ld[1]);
-  double g2 = __ddiv_rn(__dmul_rn(tp, (double)s2), Ld[2]);
-  return __dadd_rn(__dadd_rn(__dmul_rn(g0, g0), __dmul_rn(g1, g1)), __dmul_rn(g2, g2));
+// |G|^2 from per-axis tables of ((2 pi s)/L_d)^2 (built on the host, indexed by the
+// finest-mesh index), summed in axis order without FMA.
+__device__ __forceinline__ double gsq(int f0, int f1, int f2, const double* __restrict__ g2t,
+                                      const int* Nf) {
+  return __dadd_rn(__dadd_rn(__ldg(g2t + f0), __ldg(g2t + Nf[0] + f1)),
+                   __ldg(g2t + Nf[0] + Nf[1] + f2));
 }
-
-struct Cell {
-  double L[3];
-};
 
 // Fine spectrum S(G) = sum_k [|G| < G_k] rho^_k(G) / N_k (unnormalised level DFTs):
 // Fourier interpolation of every level onto the finest grid; one C2R then gives rho.
-__global__ void combine_kernel(const KLevels K, const Cell cell,
+__global__ void combine_kernel(const KLevels K, const double* __restrict__ g2t,
                                const cufftDoubleComplex* __restrict__ spec,
                                cufftDoubleComplex* __restrict__ fspec) {
   const LevelInfo& f = K.lv[0];
@@ -878,7 +919,7 @@ __global__ void combine_kernel(const KLevels K, const Cell cell,
     const int m1 = (int)(r % f.N[1]);
     const int m0 = (int)(r / f.N[1]);
     const int s0 = signed_freq(m0, f.N[0]), s1 = signed_freq(m1, f.N[1]), s2 = m2;
-    const double G2 = gsq(s0, s1, s2, cell.L);
+    const double G2 = gsq(m0, m1, m2, g2t, f.N);
     double re = 0.0, im = 0.0;
     for (int k = 0; k < K.nlev; ++k) {
       const LevelInfo& lv = K.lv[k];
@@ -899,7 +940,7 @@ __global__ void combine_kernel(const KLevels K, const Cell cell,
 
 // Level spectrum from fine spectra: T_k(G) = [|G| < G_k] (fa(G) sa + fb(G)), where fa is
 // an unnormalised DFT (sa = 1/N_fine) and fb, if given, is already a normalised spectrum.
-__global__ void restrict_kernel(const KLevels K, const Cell cell, int level,
+__global__ void restrict_kernel(const KLevels K, const double* __restrict__ g2t, int level,
                                 const cufftDoubleComplex* __restrict__ fa,
                                 const cufftDoubleComplex* __restrict__ fb,
                                 cufftDoubleComplex* __restrict__ spec) {
@@ -918,11 +959,11 @@ __global__ void restrict_kernel(const KLevels K, const Cell cell, int level,
     cufftDoubleComplex out;
     out.x = 0.0;
     out.y = 0.0;
-    const double G2 = gsq(s0, s1, s2, cell.L);
+    const int i0 = s0 < 0 ? s0 + f.N[0] : s0;
+    const int i1 = s1 < 0 ? s1 + f.N[1] : s1;
+    const double G2 = gsq(i0, i1, s2, g2t, f.N);
     if (G2 < lv.Gk2 && 2 * abs(s0) <= lv.N[0] - 1 && 2 * abs(s1) <= lv.N[1] - 1 &&
         2 * s2 <= lv.N[2] - 1) {
-      const int i0 = s0 < 0 ? s0 + f.N[0] : s0;
-      const int i1 = s1 < 0 ? s1 + f.N[1] : s1;
       const long long fi = ((long long)i0 * f.N[1] + i1) * fh2 + s2;
       const cufftDoubleComplex z = fa[fi];
       out.x = z.x * inv;
@@ -951,7 +992,7 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
 // Poisson in place on the fine spectrum (Eqs. vH, vHG): S <- 4 pi S / |G|^2, G = 0
 // dropped; E_H = (Omega/2) sum_G |S|^2 4 pi / |G|^2 over the full spectrum (half
 // spectrum weighted by Hermitian symmetry), block partials to red.
-__global__ void poisson_kernel(const KLevels K, const Cell cell, double omega,
+__global__ void poisson_kernel(const KLevels K, const double* __restrict__ g2t, double omega,
                                cufftDoubleComplex* __restrict__ fspec, double* __restrict__ red) {
   __shared__ double sh[kRedThreads];
   const LevelInfo& f = K.lv[0];
@@ -964,9 +1005,7 @@ __global__ void poisson_kernel(const KLevels K, const Cell cell, double omega,
     const long long r = idx / h2;
     const int m1 = (int)(r % f.N[1]);
     const int m0 = (int)(r / f.N[1]);
-    const int s0 = signed_freq(m0, f.N[0]), s1 = signed_freq(m1, f.N[1]);
-    const int s2 = (f.N[2] % 2 == 0 && m2 == f.N[2] / 2) ? -m2 : m2;
-    const double G2 = gsq(s0, s1, s2, cell.L);
+    const double G2 = gsq(m0, m1, m2, g2t, f.N);
     cufftDoubleComplex z = fspec[idx];
     double kern = G2 > 0.0 ? (4.0 * 3.141592653589793) / G2 : 0.0;
     const double mult = (m2 == 0 || (f.N[2] % 2 == 0 && m2 == f.N[2] / 2)) ? 1.0 : 2.0;
@@ -1011,33 +1050,40 @@ int even(int x) { return (x + 1) & ~1; }
 
 constexpr int kNW = 8;
 
-#define GPW_TILE_SHAPES(X) X(8, 8, 16) X(4, 8, 32) X(8, 8, 32) X(4, 8, 64)
+#define GPW_TILE_SHAPES(X) \
+  X(8, 8, 16) X(4, 8, 32) X(8, 8, 32) X(4, 8, 64) X(4, 8, 16) X(4, 4, 16) X(2, 8, 16) X(4, 4, 32)
 
 template <int T0, int T1, int T2>
 size_t colloc_smem(int stg, int nw) {
   return sizeof(int) * kTabInts + sizeof(double) * (size_t)nw * (T0 * T1 * T2 + stg);
 }
 
-// Warps per collocation block: the candidate with the most resident warps per SM
-// (shared memory bounds the blocks per SM; each block reserves 1 KB).
-int pick_colloc_warps(size_t smem_per_sm, size_t (*smem_of)(int, int), int stg, int* nw_out,
-                      size_t* smem_out) {
+template <int T0, int T1, int T2>
+size_t integ_smem(int stg) {
+  return sizeof(int) * kTabInts + sizeof(double) * ((size_t)IntegLayout<T0, T1, T2>::kSV + (size_t)kNW * stg);
+}
+
+// Warps per collocation block: the candidate with the most resident warps per SM, as the
+// occupancy calculator reports it for this shared-memory size (registers included).
+template <int T0, int T1, int T2>
+int pick_colloc_warps(int stg, int* nw_out, size_t* smem_out) {
   int best = 0;
-  for (int nw : {8, 6, 4}) {
-    size_t need = smem_of(stg, nw);
-    int blocks = (int)(smem_per_sm / (need + 1024));
-    blocks = std::min(blocks, 32 / nw);
-    if (blocks * nw > best) {
-      best = blocks * nw;
-      *nw_out = nw;
+  const void* fns[3] = {(const void*)collocate_kernel<T0, T1, T2, 8>,
+                        (const void*)collocate_kernel<T0, T1, T2, 6>,
+                        (const void*)collocate_kernel<T0, T1, T2, 4>};
+  const int nws[3] = {8, 6, 4};
+  for (int i = 0; i < 3; ++i) {
+    const size_t need = colloc_smem<T0, T1, T2>(stg, nws[i]);
+    int blocks = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fns[i], nws[i] * 32, need) != cudaSuccess)
+      continue;
+    if (blocks * nws[i] > best) {
+      best = blocks * nws[i];
+      *nw_out = nws[i];
       *smem_out = need;
     }
   }
   return best;
-}
-template <int T0, int T1, int T2>
-size_t integ_smem(int stg) {
-  return sizeof(int) * kTabInts + sizeof(double) * ((size_t)IntegLayout<T0, T1, T2>::kSV + (size_t)kNW * stg);
 }
 
 }  // namespace
@@ -1060,35 +1106,12 @@ KLevels make_klevels(const Plan& p, bool integ) {
 cudaError_t configure_kernels(Plan* p) {
   const int lp = p->lmax + 1;
   int found = 0;
-  int dev = 0, optin = 0, per_sm = 0;
+  int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e == cudaSuccess)
-    e = cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
   if (e != cudaSuccess) return e;
-#define GPW_TILE_CONF(a, b, c)                                                      \
-  if (p->tile[0] == a && p->tile[1] == b && p->tile[2] == c) {                      \
-    found |= 1;                                                                     \
-    p->stg_colloc = even(CollocLayout<a, b, c>::stage(lp));                         \
-    if (pick_colloc_warps((size_t)per_sm, colloc_smem<a, b, c>, p->stg_colloc,       \
-                          &p->nw_colloc, &p->smem_colloc) == 0)                     \
-      return cudaErrorInvalidValue;                                                 \
-  }                                                                                 \
-  if (p->tile_i[0] == a && p->tile_i[1] == b && p->tile_i[2] == c) {                \
-    found |= 2;                                                                     \
-    p->stg_integ = even(IntegLayout<a, b, c>::stage(p->lmax + 1));                  \
-    p->stg_integ1 = even(IntegLayout<a, b, c>::stage(p->lmax + 2));                 \
-    p->smem_integ = integ_smem<a, b, c>(p->stg_integ);                              \
-    p->smem_integ1 = integ_smem<a, b, c>(p->stg_integ1);                            \
-  }
-  GPW_TILE_SHAPES(GPW_TILE_CONF)
-#undef GPW_TILE_CONF
-  if (found != 3) return cudaErrorInvalidValue;
-  p->nw_integ = kNW;
   // the attribute is per function and shared by all plans: raise it to the device
-  // maximum, each launch asks for what its plan needs
-  if ((size_t)optin < std::max(p->smem_colloc, std::max(p->smem_integ, p->smem_integ1)))
-    return cudaErrorInvalidValue;
+  // maximum (before the occupancy queries below), each launch asks for what it needs
 #define GPW_TILE_ATTR(a, b, c)                                                                    \
   e = cudaFuncSetAttribute(collocate_kernel<a, b, c, 8>,                                          \
                            cudaFuncAttributeMaxDynamicSharedMemorySize, optin);                   \
@@ -1104,6 +1127,26 @@ cudaError_t configure_kernels(Plan* p) {
   if (e != cudaSuccess) return e;
   GPW_TILE_SHAPES(GPW_TILE_ATTR)
 #undef GPW_TILE_ATTR
+#define GPW_TILE_CONF(a, b, c)                                                      \
+  if (p->tile[0] == a && p->tile[1] == b && p->tile[2] == c) {                      \
+    found |= 1;                                                                     \
+    p->stg_colloc = even(CollocLayout<a, b, c>::stage(lp));                         \
+    if (pick_colloc_warps<a, b, c>(p->stg_colloc, &p->nw_colloc, &p->smem_colloc) == 0) \
+      return cudaErrorInvalidValue;                                                 \
+  }                                                                                 \
+  if (p->tile_i[0] == a && p->tile_i[1] == b && p->tile_i[2] == c) {                \
+    found |= 2;                                                                     \
+    p->stg_integ = even(IntegLayout<a, b, c>::stage(p->lmax + 1));                  \
+    p->stg_integ1 = even(IntegLayout<a, b, c>::stage(p->lmax + 2));                 \
+    p->smem_integ = integ_smem<a, b, c>(p->stg_integ);                              \
+    p->smem_integ1 = integ_smem<a, b, c>(p->stg_integ1);                            \
+  }
+  GPW_TILE_SHAPES(GPW_TILE_CONF)
+#undef GPW_TILE_CONF
+  if (found != 3) return cudaErrorInvalidValue;
+  p->nw_integ = kNW;
+  if ((size_t)optin < std::max(p->smem_colloc, std::max(p->smem_integ, p->smem_integ1)))
+    return cudaErrorInvalidValue;
   return cudaSuccess;
 }
 
@@ -1204,8 +1247,7 @@ cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, Grid
   if (tile_c[0] == a && tile_c[1] == b && tile_c[2] == c) {                                 \
     found |= 1;                                                                             \
     colloc->stg = even(CollocLayout<a, b, c>::stage(lmax + 1));                             \
-    if (pick_colloc_warps((size_t)per_sm, colloc_smem<a, b, c>, colloc->stg, &colloc->nw,    \
-                          &colloc->smem) == 0)                                              \
+    if (pick_colloc_warps<a, b, c>(colloc->stg, &colloc->nw, &colloc->smem) == 0)          \
       return cudaErrorInvalidValue;                                                         \
   }                                                                                         \
   if (tile_i[0] == a && tile_i[1] == b && tile_i[2] == c) {                                 \
@@ -1269,30 +1311,28 @@ cudaError_t launch_grad(const Plan& p, const double* D, double* grad, cudaStream
     if (e != cudaSuccess) return e;
   }
   ++p.launches;
-  grad_atom_kernel<<<(3 * p.natm + 127) / 128, 128, 0, s>>>(p.natm, p.d.atom_off, p.d.atom_list,
-                                                            p.d.pgrad, grad);
+  grad_atom_kernel<<<(p.natm + 7) / 8, 256, 0, s>>>(p.natm, p.d.atom_off, p.d.atom_list,
+                                                    p.d.pgrad, grad);
   return cudaGetLastError();
 }
 
 cudaError_t launch_combine(const Plan& p, cudaStream_t s) {
-  Cell c{{p.L[0], p.L[1], p.L[2]}};
   ++p.launches;
-  combine_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p, false), c, p.d.spec, p.d.fspec);
+  combine_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p, false), p.d.g2tab, p.d.spec, p.d.fspec);
   return cudaGetLastError();
 }
 
 cudaError_t launch_restrict(const Plan& p, int level, const cufftDoubleComplex* fa,
                             const cufftDoubleComplex* fb, cudaStream_t s) {
-  Cell c{{p.L[0], p.L[1], p.L[2]}};
   ++p.launches;
-  restrict_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p, false), c, level, fa, fb, p.d.spec);
+  restrict_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p, false), p.d.g2tab, level, fa, fb, p.d.spec);
   return cudaGetLastError();
 }
 
 cudaError_t launch_poisson(const Plan& p, cudaStream_t s) {
-  Cell c{{p.L[0], p.L[1], p.L[2]}};
   ++p.launches;
-  poisson_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(make_klevels(p, false), c, p.omega, p.d.fspec, p.d.red);
+  poisson_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(make_klevels(p, false), p.d.g2tab, p.omega,
+                                                    p.d.fspec, p.d.red);
   return cudaGetLastError();
 }
 
