@@ -227,7 +227,7 @@ void gpw_batch_destroy(gpw_batch_t batch);
 int gpw_check_device(gpw_plan_t plan, int* code, void* stream);
 
 /* Phases timed by the profiler (gpw_profile). */
-#define GPW_PHASE_COEF 0            /* pair D tensors (Eq. rho1 coefficients) */
+#define GPW_PHASE_COEF 0            /* pair D tensors (Eq. rho1) and their x contraction */
 #define GPW_PHASE_COLLOCATE 1       /* collocation kernel (Algorithm 1) */
 #define GPW_PHASE_SPECTRAL 2        /* FFTs, interpolation, Poisson, exchange, restriction */
 #define GPW_PHASE_INTEGRATE 3       /* integration kernel (Algorithm 2) */

@@ -76,7 +76,7 @@ int upload(T** ptr, const std::vector<T>& v, long long* bytes) {
 void free_plan(Plan* P) {
   DeviceArrays& d = P->d;
   void* ptrs[] = {d.hot_a, d.hot_b, d.ids, d.ids2, d.geo, d.cab, d.pref, d.tab_off,
-                  d.coef_off, d.part_off, d.task_c, d.sub_off_c, d.work_c, d.task_i, d.sub_off_i, d.work_i, d.groups, d.atom_off,
+                  d.coef_off, d.part_off, d.xt_off, d.task_c, d.sub_off_c, d.work_c, d.task_i, d.sub_off_i, d.work_i, d.groups, d.atom_off,
                   d.atom_list, d.tab, d.coef, d.part, d.pgrad, d.grids, d.spec, d.fspec,
                   d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs, d.view, d.g2tab};
   for (void* q : ptrs)
@@ -100,7 +100,7 @@ long long estimate_bytes(const Plan& P, const HostArrays& H) {
   long long b = 0;
   b += sz((long long)H.hot_a.size(), sizeof(int4)) * 4;                 // hot_a, hot_b, ids, ids2
   b += sz((long long)H.geo.size(), sizeof(double)) + sz(P.npairs, sizeof(double)) * 2;
-  b += sz(P.npairs, sizeof(long long)) * 3;
+  b += sz(P.npairs, sizeof(long long)) * 4;
   b += sz((long long)H.task_c.size(), sizeof(int4)) + sz((long long)H.task_i.size(), sizeof(int4));
   b += sz((long long)H.sub_off_c.size(), sizeof(long long)) + sz((long long)H.sub_off_i.size(), sizeof(long long));
   b += sz((long long)H.work_c.size(), sizeof(int4)) + sz((long long)H.work_i.size(), sizeof(int4));
@@ -136,6 +136,7 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
   GPW_TRY(upload(&d.tab_off, H.tab_off, &b));
   GPW_TRY(upload(&d.coef_off, H.coef_off, &b));
   GPW_TRY(upload(&d.part_off, H.part_off, &b));
+  GPW_TRY(upload(&d.xt_off, H.xt_off, &b));
   GPW_TRY(upload(&d.task_c, H.task_c, &b));
   GPW_TRY(upload(&d.sub_off_c, H.sub_off_c, &b));
   GPW_TRY(upload(&d.work_c, H.work_c, &b));
@@ -258,6 +259,7 @@ int prep_rho(Plan& P, const double* D, cudaStream_t s) {
   {
     Phase ph(P, GPW_PHASE_COEF, s);
     GPW_CK(launch_pair_coef(P, D, s));
+    GPW_CK(launch_xcontract(P, s));
   }
   GPW_CK(cudaMemsetAsync(P.d.grids, 0, sizeof(double) * (size_t)P.grid_total, s));
   return GPW_OK;

@@ -64,9 +64,11 @@ struct PlanView {
   const long long* tab_off;
   const long long* coef_off;
   const long long* part_off;
+  const long long* xt_off;
   const double* tab;
   const double* coef;
   double* part;
+  const double* xt;
   double* grids;
   int* err;
 };
@@ -83,6 +85,7 @@ struct DeviceArrays {
   long long* tab_off = nullptr;   // 1-D factor tables
   long long* coef_off = nullptr;  // D tensor (rho) / reduced V tensor (stride nc3(L+1))
   long long* part_off = nullptr;  // per-task V tensors (stride nc3(L+1) per task)
+  long long* xt_off = nullptr;    // x-contracted D tables (nc2(L) rows of n0)
   // tasks of the collocation (c) and integration (i) sub-box shapes
   int4* task_c = nullptr;     // 2 per task: {pair, m|L, u, rank}, {t|n per dimension}
   long long* sub_off_c = nullptr;  // CSR offsets over all sub-boxes of all levels
@@ -98,7 +101,7 @@ struct DeviceArrays {
   // tables and buffers
   double* tab = nullptr;
   double* coef = nullptr;     // per call: D tensors / reduced V tensors
-  double* part = nullptr;     // per call: task V tensors
+  double* part = nullptr;     // per call: task V tensors, or the x-contracted D tables
   double* pgrad = nullptr;    // 6 per pair
   double* grids = nullptr;    // level real grids
   cufftDoubleComplex* spec = nullptr;   // level half spectra
@@ -127,7 +130,7 @@ struct Plan {
   LevelInfo lev_i[GPW_MAX_LEVELS];   // same levels, sub-box fields for the integration tile
   long long npairs = 0, nent = 0, nwork = 0, nsub_total = 0, ngroups = 0;
   long long nent_i = 0, nwork_i = 0;
-  long long tab_total = 0, coef_total = 0, part_total = 0;
+  long long tab_total = 0, coef_total = 0, part_total = 0, xt_total = 0;
   long long grid_total = 0, spec_total = 0, fine_n = 0, fine_spec_n = 0;
   long long pair_points = 0;
   long long pair_points_level[GPW_MAX_LEVELS] = {0};

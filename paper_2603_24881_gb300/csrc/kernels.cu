@@ -174,6 +174,37 @@ __global__ void pair_coef_kernel(long long np, const int4* __restrict__ hot_a,
   for (int c = 0; c < nc; ++c) out[c] = acc[c];
 }
 
+// First contraction of collocation, once per pair over its whole box extent n0:
+//   X[l2,l1](i) = sum_{l0 <= L - l1 - l2} D[l0,l1,l2] g0[l0](i),   0 <= i < n0,
+// stored as nc2(L) rows of n0 (row c21 = c21base[l2] + l1).  Every task of the pair reads
+// its m0-column window of it instead of forming the same sums again.  One warp per pair.
+__global__ void xcontract_kernel(long long np, const int4* __restrict__ hot_a,
+                                 const int4* __restrict__ hot_b,
+                                 const long long* __restrict__ tab_off, const double* __restrict__ tab,
+                                 const long long* __restrict__ coef_off,
+                                 const double* __restrict__ coef,
+                                 const long long* __restrict__ xt_off,
+                                 const CoefTables* __restrict__ tabs, double* __restrict__ xt) {
+  const int lane = threadIdx.x & 31;
+  long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long sw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long p = gw; p < np; p += sw) {
+    const int L = hot_a[p].w, n0 = hot_b[p].x;
+    const double* g0 = tab + tab_off[p];
+    const double* Dp = coef + coef_off[p];
+    double* out = xt + xt_off[p];
+    const int items = nc2(L) * n0;
+    for (int it = lane; it < items; it += 32) {
+      const int c21 = it / n0, i = it - c21 * n0;
+      const int dc = __ldg(&tabs->dec21[L][c21]);
+      const int l2 = dc & 255, l1 = (dc >> 8) & 255, b3 = dc >> 16;
+      double a = 0.0;
+      for (int l0 = 0; l0 <= L - l2 - l1; ++l0) a = fma(Dp[b3 + l0], g0[l0 * n0 + i], a);
+      out[(long long)c21 * n0 + i] = a;
+    }
+  }
+}
+
 // A task is one (pair, sub-box copy) intersection, precomputed by the plan as two int4:
 //   r0 = {pair, m0 | m1 << 8 | m2 << 16 | L << 24, u0 | u1 << 8 | u2 << 16, rank}
 //   r1 = {t0 | n0 << 16, t1 | n1 << 16, t2 | n2 << 16, 0}
@@ -266,16 +297,13 @@ __device__ __forceinline__ void stage_tables_async(const double* tb, const Task&
 template <int T0, int T1, int T2>
 struct CollocLayout {
   static constexpr int kTileN = T0 * T1 * T2;
-  // one staging buffer: factor windows + D tensor, for lp = lmax + 1 factor rows (even
+  // one staging buffer: the task's window of the x-contracted table (nc2(lp - 1) rows of
+  // T0) and the y and z factor windows (lp rows of T1, T2), for lp = lmax + 1 (even
   // length keeps 16-byte alignment)
-  __host__ __device__ static int buf(int lp) {
-    return (lp * (T0 + T1 + T2) + nc3(lp - 1) + 1) & ~1;
-  }
-  // per-warp staging: two buffers, the T1 and T2 intermediates and two row tables
-  // (T0*T1 ints each: q -> accumulator offset of the row, q -> (i0, i1))
-  __host__ __device__ static int stage(int lp) {
-    return 2 * buf(lp) + nc2(lp - 1) * T0 + lp * T0 * T1 + T0 * T1;
-  }
+  __host__ __device__ static int buf(int lp) { return (nc2(lp - 1) * T0 + lp * (T1 + T2) + 1) & ~1; }
+  // per-warp staging: two buffers, the T2 intermediate and two row tables (T0*T1 ints
+  // each: q -> accumulator offset of the row, q -> (i0, i1))
+  __host__ __device__ static int stage(int lp) { return 2 * buf(lp) + lp * T0 * T1 + T0 * T1; }
 };
 
 // ----------------------------------------------------------------------------------
@@ -283,11 +311,11 @@ struct CollocLayout {
 // One thread block per sub-box with tasks; warp w takes tasks w, w + NW, ... of the
 // sub-box's list and accumulates into its own copy of the sub-box in shared memory;
 // the NW copies are summed in a fixed order and written once (coalesced, no atomics).
-// Per task, with m the intersection extents:
-//   T1[l2,l1](i0) = sum_l0 D[l0,l1,l2] g0[l0](i0)            nc2(L) m0 FMAs
-//   T2[l2](i0,i1) = sum_l1 T1[l2,l1](i0) g1[l1](i1)          nc2(L) m0 m1
+// Per task, with m the intersection extents and X the pair's x-contracted table
+// (xcontract_kernel, the first of the three contractions):
+//   T2[l2](i0,i1) = sum_l1 X[l2,l1](i0) g1[l1](i1)           nc2(L) m0 m1 FMAs
 //   rho(i0,i1,i2) += sum_l2 T2[l2](i0,i1) g2[l2](i2)         (L+1) m0 m1 m2
-// The next task's record and pair offsets are fetched while the current one computes.
+// The next task's windows are copied in (cp.async) while the current one computes.
 template <int T0, int T1, int T2, int NW>
 __global__ void __launch_bounds__(NW * 32)
     collocate_kernel(const PlanView* __restrict__ views, const int4* __restrict__ work,
@@ -296,7 +324,6 @@ __global__ void __launch_bounds__(NW * 32)
   constexpr int kTileN = T0 * T1 * T2;
   extern __shared__ __align__(16) double sm[];
   int* s_tab = reinterpret_cast<int*>(sm);
-  const int(*s_dec21)[kNc2Max] = reinterpret_cast<const int(*)[kNc2Max]>(s_tab);
   const int(*s_c21b)[kLextMax + 1] = reinterpret_cast<const int(*)[kLextMax + 1]>(
       s_tab + (kLextMax + 1) * (kNc2Max + kNc3Max));
   double* acc_all = sm + kTabInts / 2;
@@ -309,9 +336,9 @@ __global__ void __launch_bounds__(NW * 32)
   const LevelInfo& lv = pv.lc[item.y];
   const int4* __restrict__ task = pv.task_c;
   const long long* __restrict__ tab_off = pv.tab_off;
-  const long long* __restrict__ coef_off = pv.coef_off;
+  const long long* __restrict__ xt_off = pv.xt_off;
   const double* __restrict__ tab = pv.tab;
-  const double* __restrict__ coef = pv.coef;
+  const double* __restrict__ xt = pv.xt;
   double* __restrict__ grids = pv.grids;
   int* __restrict__ err = pv.err;
   const SubBox sb = sub_box<T0, T1, T2>(lv, item.z, pv.sub_off_c);
@@ -319,40 +346,53 @@ __global__ void __launch_bounds__(NW * 32)
   double* acc = acc_all + warp * kTileN;
   double* stage_base = acc_all + NW * kTileN + warp * stg;
   const int bufn = Lay::buf(lp);
-  double* sT1 = stage_base + 2 * bufn;
-  double* sT2 = sT1 + nc2(lp - 1) * T0;
+  const int xrows = nc2(lp - 1);
+  double* sT2 = stage_base + 2 * bufn;
   int* s_row = reinterpret_cast<int*>(sT2 + lp * T0 * T1);
   int* s_qi = s_row + T0 * T1;
   __syncthreads();
 
-  // staging buffer b: [sg0 lp*T0][sg1 lp*T1][sg2 lp*T2][D nc3]
-  auto issue = [&](const Task& tk, long long toff, long long coff, int b) {
-    double* sg0 = stage_base + b * bufn;
-    double* sg1 = sg0 + lp * T0;
+  // staging buffer b: [X window xrows*T0][g1 lp*T1][g2 lp*T2]
+  auto issue = [&](const Task& tk, long long toff, long long xoff, int b) {
+    double* sX = stage_base + b * bufn;
+    double* sg1 = sX + xrows * T0;
     double* sg2 = sg1 + lp * T1;
-    double* sD = sg2 + lp * T2;
-    stage_tables_async<T0, T1, T2>(tab + toff, tk, tk.L + 1, sg0, sg1, sg2, lane);
-    const double* cp = coef + coff;
-    for (int c = lane; c < nc3(tk.L); c += 32) cp_async8(sD + c, cp + c);
+    const int L = tk.L, m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
+    const double* x = xt + xoff + tk.t[0];
+    const double* t1 = tab + toff + (L + 2) * tk.n[0] + tk.t[1];
+    const double* t2 = tab + toff + (L + 2) * (tk.n[0] + tk.n[1]) + tk.t[2];
+    const float i0f = __frcp_rn((float)m0), i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
+    for (int it = lane; it < nc2(L) * m0; it += 32) {
+      const int c = fdiv(it, i0f), i = it - c * m0;
+      cp_async8(sX + c * T0 + i, x + c * tk.n[0] + i);
+    }
+    for (int it = lane; it < (L + 1) * m1; it += 32) {
+      const int l = fdiv(it, i1f), i = it - l * m1;
+      cp_async8(sg1 + l * T1 + i, t1 + l * tk.n[1] + i);
+    }
+    for (int it = lane; it < (L + 1) * m2; it += 32) {
+      const int l = fdiv(it, i2f), i = it - l * m2;
+      cp_async8(sg2 + l * T2 + i, t2 + l * tk.n[2] + i);
+    }
   };
 
   long long e = sb.eb + warp;
   int4 a0 = make_int4(0, 0, 0, 0), a1 = a0, b0 = a0, b1 = a0;
-  long long atoff = 0, acoff = 0, btoff = 0, bcoff = 0;
+  long long btoff = 0, bxoff = 0;
   if (e < sb.ee) {
     a0 = __ldg(task + 2 * e);
     a1 = __ldg(task + 2 * e + 1);
-    atoff = __ldg(tab_off + a0.x);
-    acoff = __ldg(coef_off + a0.x);
+    const long long atoff = __ldg(tab_off + a0.x);
+    const long long axoff = __ldg(xt_off + a0.x);
     const Task tk = decode_task(a0, a1);
-    if (task_ok(tk, tk.L, lp, sb)) issue(tk, atoff, acoff, 0);
+    if (task_ok(tk, tk.L, lp, sb)) issue(tk, atoff, axoff, 0);
     cp_async_commit();
   }
   if (e + NW < sb.ee) {
     b0 = __ldg(task + 2 * (e + NW));
     b1 = __ldg(task + 2 * (e + NW) + 1);
     btoff = __ldg(tab_off + b0.x);
-    bcoff = __ldg(coef_off + b0.x);
+    bxoff = __ldg(xt_off + b0.x);
   }
   int buf = 0;
   for (; e < sb.ee; e += NW, buf ^= 1) {
@@ -361,7 +401,7 @@ __global__ void __launch_bounds__(NW * 32)
     // fetch the next task's windows into the other buffer
     if (e + NW < sb.ee) {
       const Task tn = decode_task(b0, b1);
-      if (task_ok(tn, tn.L, lp, sb)) issue(tn, btoff, bcoff, buf ^ 1);
+      if (task_ok(tn, tn.L, lp, sb)) issue(tn, btoff, bxoff, buf ^ 1);
       cp_async_commit();
     }
     int4 c0 = b0, c1 = b1;
@@ -375,58 +415,37 @@ __global__ void __launch_bounds__(NW * 32)
     if (!task_ok(tk, L, lp, sb)) {
       if (lane == 0) set_err(err, 1);
     } else {
-      const double* sg0 = stage_base + buf * bufn;
-      const double* sg1 = sg0 + lp * T0;
+      const double* sX = stage_base + buf * bufn;
+      const double* sg1 = sX + xrows * T0;
       const double* sg2 = sg1 + lp * T1;
-      const double* sD = sg2 + lp * T2;
       const int m01 = m0 * m1;
+      const float inv1 = __frcp_rn((float)m1), inv01 = __frcp_rn((float)m01);
+      const float inv2 = __frcp_rn((float)m2);
       // per-task row tables: q = i0 m1 + i1 -> (i0, i1) and accumulator offset of the row
       for (int q = lane; q < m01; q += 32) {
-        const int i0 = q / m1, i1 = q - i0 * m1;
+        const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
         s_qi[q] = i0 | (i1 << 8);
         s_row[q] = ((tk.u[0] + i0) * T1 + (tk.u[1] + i1)) * T2 + tk.u[2];
       }
-      // T1[c21](i0)
-      {
-        const float inv = __frcp_rn((float)m0);
-        const int items = nc2(L) * m0;
-        for (int it = lane; it < items; it += 32) {
-          const int c21 = fdiv(it, inv), i0 = it - c21 * m0;
-          const int dc = s_dec21[L][c21];
-          const int l2 = dc & 255, l1 = (dc >> 8) & 255, b3 = dc >> 16;
-          double a = 0.0;
-          for (int l0 = 0; l0 <= L - l2 - l1; ++l0) a = fma(sD[b3 + l0], sg0[l0 * T0 + i0], a);
-          sT1[c21 * T0 + i0] = a;
-        }
-      }
       __syncwarp();
-      // T2[l2](q): items it = l2 m01 + q, two per lane in flight (independent FMA chains);
-      // the item index advances by 32 with a carry instead of a division per item
+      // T2[l2](q): one item it = l2 m01 + q per lane, advanced by 32 with a carry
       {
         const int dl = 32 / m01, dq = 32 - dl * m01;
-        int l2A = lane / m01, qA = lane - l2A * m01;
-        for (int base = 0; base < (L + 1) * m01; base += 64) {
-          int l2B = l2A + dl, qB = qA + dq;
-          if (qB >= m01) {
-            qB -= m01;
-            ++l2B;
+        int l2 = fdiv(lane, inv01), q = lane - l2 * m01;
+        for (int base = 0; base < (L + 1) * m01; base += 32) {
+          if (l2 <= L) {
+            const int pi = s_qi[q];
+            const int i0 = pi & 255, i1 = pi >> 8;
+            const int cb = s_c21b[L][l2];
+            double a = 0.0;
+            for (int l1 = 0; l1 <= L - l2; ++l1) a = fma(sX[(cb + l1) * T0 + i0], sg1[l1 * T1 + i1], a);
+            sT2[l2 * (T0 * T1) + q] = a;
           }
-          const int nA = l2A <= L ? L - l2A : -1, nB = l2B <= L ? L - l2B : -1;
-          const int piA = s_qi[qA], piB = s_qi[qB];
-          const int i0A = piA & 255, i1A = piA >> 8, i0B = piB & 255, i1B = piB >> 8;
-          const int cbA = s_c21b[L][min(l2A, L)], cbB = s_c21b[L][min(l2B, L)];
-          double a = 0.0, b = 0.0;
-          for (int l1 = 0; l1 <= max(nA, nB); ++l1) {
-            if (l1 <= nA) a = fma(sT1[(cbA + l1) * T0 + i0A], sg1[l1 * T1 + i1A], a);
-            if (l1 <= nB) b = fma(sT1[(cbB + l1) * T0 + i0B], sg1[l1 * T1 + i1B], b);
-          }
-          if (nA >= 0) sT2[l2A * (T0 * T1) + qA] = a;
-          if (nB >= 0) sT2[l2B * (T0 * T1) + qB] = b;
-          l2A = l2B + dl;
-          qA = qB + dq;
-          if (qA >= m01) {
-            qA -= m01;
-            ++l2A;
+          q += dq;
+          l2 += dl;
+          if (q >= m01) {
+            q -= m01;
+            ++l2;
           }
         }
       }
@@ -435,7 +454,7 @@ __global__ void __launch_bounds__(NW * 32)
       // flight, advanced by 32 with a carry
       {
         const int dq = 32 / m2, di = 32 - dq * m2;
-        int qA = lane / m2, iA = lane - qA * m2;
+        int qA = fdiv(lane, inv2), iA = lane - qA * m2;
         const int items = m01 * m2;
         for (int base = 0; base < items; base += 64) {
           int qB = qA + dq, iB = iA + di;
@@ -468,20 +487,18 @@ __global__ void __launch_bounds__(NW * 32)
         }
       }
     }
-    long long ctoff = btoff, ccoff = bcoff;
+    long long ctoff = btoff, cxoff = bxoff;
     if (e + 2 * NW < sb.ee) {
       ctoff = __ldg(tab_off + c0.x);
-      ccoff = __ldg(coef_off + c0.x);
+      cxoff = __ldg(xt_off + c0.x);
     }
     __syncwarp();
     a0 = b0;
     a1 = b1;
-    atoff = btoff;
-    acoff = bcoff;
     b0 = c0;
     b1 = c1;
     btoff = ctoff;
-    bcoff = ccoff;
+    bxoff = cxoff;
   }
   cp_async_wait_all();
   __syncthreads();
@@ -1168,6 +1185,15 @@ cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+cudaError_t launch_xcontract(const Plan& p, cudaStream_t s) {
+  if (p.npairs == 0) return cudaSuccess;
+  long long blocks = std::min<long long>((p.npairs + 7) / 8, 152LL * 64);
+  ++p.launches;
+  xcontract_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, p.d.hot_a, p.d.hot_b, p.d.tab_off, p.d.tab,
+                                                p.d.coef_off, p.d.coef, p.d.xt_off, p.d.tabs, p.d.part);
+  return cudaGetLastError();
+}
+
 // Collocation over `nwork` work items of the views in `views` (one plan, or a batch of
 // plans sharing the sub-box shapes); cfg gives the launch shape.
 cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views, const int4* work,
@@ -1276,6 +1302,8 @@ PlanView make_view(const Plan& p) {
   v.tab = p.d.tab;
   v.coef = p.d.coef;
   v.part = p.d.part;
+  v.xt_off = p.d.xt_off;
+  v.xt = p.d.part;
   v.grids = p.d.grids;
   v.err = p.d.err;
   return v;

@@ -28,6 +28,7 @@ cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, Grid
 
 cudaError_t launch_tables(const Plan& p, cudaStream_t s);
 cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s);
+cudaError_t launch_xcontract(const Plan& p, cudaStream_t s);
 cudaError_t launch_collocate(const Plan& p, cudaStream_t s);
 cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s);
 cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s);

@@ -493,6 +493,7 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   H->tab_off.resize(np);
   H->coef_off.resize(np);
   H->part_off.resize(np);
+  H->xt_off.resize(np);
   plan->h_ab.resize(2 * np);
   plan->h_img.resize(3 * np);
   plan->h_lev.resize(np);
@@ -500,7 +501,7 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   plan->h_hi.resize(3 * np);
   plan->pair_a.resize(np);
   plan->pair_b.resize(np);
-  long long tab_total = 0, coef_total = 0;
+  long long tab_total = 0, coef_total = 0, xt_total = 0;
   int lmax = 0;
   for (long long p = 0; p < np; ++p) {
     const PairTmp& t = pairs[p];
@@ -525,6 +526,8 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     tab_total += (long long)(L + 2) * (n[0] + n[1] + n[2]);
     H->coef_off[p] = coef_total;
     coef_total += nc3(L + 1);
+    H->xt_off[p] = xt_total;
+    xt_total += (long long)nc2(L) * n[0];
     long long pts = (long long)n[0] * n[1] * n[2];
     plan->pair_points += pts;
     plan->pair_points_level[t.level] += pts;
@@ -547,6 +550,7 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   plan->lmax = lmax;
   plan->tab_total = tab_total;
   plan->coef_total = coef_total;
+  plan->xt_total = xt_total;
 
   // ---- per-level sub-box task lists (CSR), one task per (pair, sub-box, image shift),
   // for the collocation tile and for the integration tile
@@ -569,7 +573,9 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     H->part_off[p] = part_total;
     part_total += (long long)ranks[p] * nc3(H->hot_a[p].w + 1);
   }
-  plan->part_total = part_total;
+  // the part buffer also holds the x-contracted tables of collocation (never live at the
+  // same time as the task V tensors)
+  plan->part_total = std::max(part_total, xt_total);
 
   // ---- V assembly groups: runs of pairs with the same contracted shell pair
   for (long long p = 0; p < np;) {
