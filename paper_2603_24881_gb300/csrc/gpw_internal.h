@@ -84,7 +84,7 @@ struct DeviceArrays {
   double* pref = nullptr;     // c_a N_a c_b N_b K_ab (K_ab = exp(-a b |A-B|^2/(a+b)))
   long long* tab_off = nullptr;   // 1-D factor tables
   long long* coef_off = nullptr;  // D tensor (rho) / reduced V tensor (stride nc3(L+1))
-  long long* part_off = nullptr;  // per-task V tensors (stride nc3(L+1) per task)
+  long long* part_off = nullptr;  // per-pair block of task W tensors (nc2(L+1) n0 ns12)
   long long* xt_off = nullptr;    // x-contracted D tables (nc2(L) rows of n0)
   // tasks of the collocation (c) and integration (i) sub-box shapes
   int4* task_c = nullptr;     // 2 per task: {pair, m|L, u, rank}, {t|n per dimension}
@@ -101,7 +101,7 @@ struct DeviceArrays {
   // tables and buffers
   double* tab = nullptr;
   double* coef = nullptr;     // per call: D tensors / reduced V tensors
-  double* part = nullptr;     // per call: task V tensors, or the x-contracted D tables
+  double* part = nullptr;     // per call: task W tensors, or the x-contracted D tables
   double* pgrad = nullptr;    // 6 per pair
   double* grids = nullptr;    // level real grids
   cufftDoubleComplex* spec = nullptr;   // level half spectra

@@ -268,22 +268,16 @@ __device__ __forceinline__ bool task_ok(const Task& tk, int lx, int lrows, const
   return ok;
 }
 
-// Issue asynchronous copies of rows l < rows of the three 1-D factor windows of a task
-// into shared memory (row strides P0, P1, P2).
-template <int P0, int P1, int P2>
-__device__ __forceinline__ void stage_tables_async(const double* tb, const Task& tk, int rows,
-                                                   double* sg0, double* sg1, double* sg2,
-                                                   int lane) {
+// Issue asynchronous copies of rows l < rows of the y and z 1-D factor windows of a
+// task into shared memory (row strides P1, P2).
+template <int P1, int P2>
+__device__ __forceinline__ void stage_yz_async(const double* tb, const Task& tk, int rows,
+                                               double* sg1, double* sg2, int lane) {
   const int L = tk.L;
-  const double* t0 = tb + tk.t[0];
   const double* t1 = tb + (L + 2) * tk.n[0] + tk.t[1];
   const double* t2 = tb + (L + 2) * (tk.n[0] + tk.n[1]) + tk.t[2];
-  const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
-  const float i0f = __frcp_rn((float)m0), i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
-  for (int it = lane; it < rows * m0; it += 32) {
-    int l = fdiv(it, i0f), i = it - l * m0;
-    cp_async8(sg0 + l * P0 + i, t0 + l * tk.n[0] + i);
-  }
+  const int m1 = tk.m[1], m2 = tk.m[2];
+  const float i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
   for (int it = lane; it < rows * m1; it += 32) {
     int l = fdiv(it, i1f), i = it - l * m1;
     cp_async8(sg1 + l * P1 + i, t1 + l * tk.n[1] + i);
@@ -291,6 +285,87 @@ __device__ __forceinline__ void stage_tables_async(const double* tb, const Task&
   for (int it = lane; it < rows * m2; it += 32) {
     int l = fdiv(it, i2f), i = it - l * m2;
     cp_async8(sg2 + l * P2 + i, t2 + l * tk.n[2] + i);
+  }
+}
+
+// The two per-task contractions of collocation for a pair of total degree L (a compile-
+// time constant, so both contractions unroll completely):
+//   T2[l2](q) = sum_{l1 <= L - l2} X[l2,l1](i0) g1[l1](i1),   q = i0 m1 + i1
+//   acc(q, i2) += sum_{l2 <= L} T2[l2](q) g2[l2](i2)
+// Items are spread over the lanes flat (it = l2 m01 + q, then it = q m2 + i2) so that
+// partial tasks keep the lanes busy; the item index advances by 32 with a carry.
+template <int L, int T0, int T1, int T2>
+__device__ __forceinline__ void colloc_task(int m01, int m2, const double* __restrict__ sX,
+                                            const double* __restrict__ sg1,
+                                            const double* __restrict__ sg2, double* __restrict__ sT2,
+                                            const int* __restrict__ s_row,
+                                            const int* __restrict__ s_qi, double* __restrict__ acc,
+                                            int lane) {
+  constexpr int Q = T0 * T1;
+  const float inv01 = __frcp_rn((float)m01), inv2 = __frcp_rn((float)m2);
+  {
+    const int dl = fdiv(32, inv01), dq = 32 - dl * m01;
+    int l2 = fdiv(lane, inv01), q = lane - l2 * m01;
+    for (int base = 0; base < (L + 1) * m01; base += 32) {
+      if (l2 <= L) {
+        const int pi = s_qi[q];
+        const double* xr = sX + (l2 * (L + 1) - ((l2 * (l2 - 1)) >> 1)) * T0 + (pi & 255);
+        const double* gr = sg1 + (pi >> 8);
+        double a = 0.0;
+#pragma unroll
+        for (int l1 = 0; l1 <= L; ++l1)
+          if (l1 <= L - l2) a = fma(xr[l1 * T0], gr[l1 * T1], a);
+        sT2[l2 * Q + q] = a;
+      }
+      q += dq;
+      l2 += dl;
+      if (q >= m01) {
+        q -= m01;
+        ++l2;
+      }
+    }
+  }
+  __syncwarp();
+  {
+    const int dq = fdiv(32, inv2), di = 32 - dq * m2;
+    int qA = fdiv(lane, inv2), iA = lane - qA * m2;
+    const int items = m01 * m2;
+    for (int base = 0; base < items; base += 64) {
+      int qB = qA + dq, iB = iA + di;
+      if (iB >= m2) {
+        iB -= m2;
+        ++qB;
+      }
+      const bool okA = qA < m01, okB = qB < m01;
+      const int qa = okA ? qA : 0, qb = okB ? qB : 0;
+      double* pa = acc + s_row[qa] + iA;
+      double* pb = acc + s_row[qb] + iB;
+      const double* ta = sT2 + qa;
+      const double* tb = sT2 + qb;
+      const double* ga = sg2 + iA;
+      const double* gb = sg2 + iB;
+      if (base + 32 < items) {
+        double ra = okA ? *pa : 0.0, rb = okB ? *pb : 0.0;
+#pragma unroll
+        for (int l2 = 0; l2 <= L; ++l2) {
+          ra = fma(ta[l2 * Q], ga[l2 * T2], ra);
+          rb = fma(tb[l2 * Q], gb[l2 * T2], rb);
+        }
+        if (okA) *pa = ra;
+        if (okB) *pb = rb;
+      } else if (okA) {
+        double ra = *pa;
+#pragma unroll
+        for (int l2 = 0; l2 <= L; ++l2) ra = fma(ta[l2 * Q], ga[l2 * T2], ra);
+        *pa = ra;
+      }
+      qA = qB + dq;
+      iA = iB + di;
+      if (iA >= m2) {
+        iA -= m2;
+        ++qA;
+      }
+    }
   }
 }
 
@@ -317,15 +392,13 @@ struct CollocLayout {
 //   rho(i0,i1,i2) += sum_l2 T2[l2](i0,i1) g2[l2](i2)         (L+1) m0 m1 m2
 // The next task's windows are copied in (cp.async) while the current one computes.
 template <int T0, int T1, int T2, int NW>
-__global__ void __launch_bounds__(NW * 32)
+__global__ void __launch_bounds__(NW * 32, 24 / NW)
     collocate_kernel(const PlanView* __restrict__ views, const int4* __restrict__ work,
                      const CoefTables* __restrict__ tabs, int lp, int stg) {
   using Lay = CollocLayout<T0, T1, T2>;
   constexpr int kTileN = T0 * T1 * T2;
   extern __shared__ __align__(16) double sm[];
   int* s_tab = reinterpret_cast<int*>(sm);
-  const int(*s_c21b)[kLextMax + 1] = reinterpret_cast<const int(*)[kLextMax + 1]>(
-      s_tab + (kLextMax + 1) * (kNc2Max + kNc3Max));
   double* acc_all = sm + kTabInts / 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   load_tables(s_tab, tabs, tid, NW * 32);
@@ -419,8 +492,7 @@ __global__ void __launch_bounds__(NW * 32)
       const double* sg1 = sX + xrows * T0;
       const double* sg2 = sg1 + lp * T1;
       const int m01 = m0 * m1;
-      const float inv1 = __frcp_rn((float)m1), inv01 = __frcp_rn((float)m01);
-      const float inv2 = __frcp_rn((float)m2);
+      const float inv1 = __frcp_rn((float)m1);
       // per-task row tables: q = i0 m1 + i1 -> (i0, i1) and accumulator offset of the row
       for (int q = lane; q < m01; q += 32) {
         const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
@@ -428,64 +500,17 @@ __global__ void __launch_bounds__(NW * 32)
         s_row[q] = ((tk.u[0] + i0) * T1 + (tk.u[1] + i1)) * T2 + tk.u[2];
       }
       __syncwarp();
-      // T2[l2](q): one item it = l2 m01 + q per lane, advanced by 32 with a carry
-      {
-        const int dl = 32 / m01, dq = 32 - dl * m01;
-        int l2 = fdiv(lane, inv01), q = lane - l2 * m01;
-        for (int base = 0; base < (L + 1) * m01; base += 32) {
-          if (l2 <= L) {
-            const int pi = s_qi[q];
-            const int i0 = pi & 255, i1 = pi >> 8;
-            const int cb = s_c21b[L][l2];
-            double a = 0.0;
-            for (int l1 = 0; l1 <= L - l2; ++l1) a = fma(sX[(cb + l1) * T0 + i0], sg1[l1 * T1 + i1], a);
-            sT2[l2 * (T0 * T1) + q] = a;
-          }
-          q += dq;
-          l2 += dl;
-          if (q >= m01) {
-            q -= m01;
-            ++l2;
-          }
-        }
+#define GPW_COLLOC_L(LL)                                                                     \
+  case LL:                                                                                   \
+    colloc_task<LL, T0, T1, T2>(m01, m2, sX, sg1, sg2, sT2, s_row, s_qi, acc, lane);          \
+    break;
+      switch (L) {
+        GPW_COLLOC_L(0) GPW_COLLOC_L(1) GPW_COLLOC_L(2) GPW_COLLOC_L(3) GPW_COLLOC_L(4)
+        GPW_COLLOC_L(5) GPW_COLLOC_L(6)
+        default:
+          if (lane == 0) set_err(err, 1);
       }
-      __syncwarp();
-      // rho(q, i2) += sum_l2 T2[l2](q) g2[l2](i2); items it = q m2 + i2, two per lane in
-      // flight, advanced by 32 with a carry
-      {
-        const int dq = 32 / m2, di = 32 - dq * m2;
-        int qA = fdiv(lane, inv2), iA = lane - qA * m2;
-        const int items = m01 * m2;
-        for (int base = 0; base < items; base += 64) {
-          int qB = qA + dq, iB = iA + di;
-          if (iB >= m2) {
-            iB -= m2;
-            ++qB;
-          }
-          const bool okA = qA < m01, okB = qB < m01;
-          double* pa = acc + s_row[okA ? qA : 0] + iA;
-          double* pb = acc + s_row[okB ? qB : 0] + iB;
-          if (base + 32 < items) {
-            double ra = okA ? *pa : 0.0, rb = okB ? *pb : 0.0;
-            for (int l2 = 0; l2 <= L; ++l2) {
-              ra = fma(sT2[l2 * (T0 * T1) + (okA ? qA : 0)], sg2[l2 * T2 + iA], ra);
-              rb = fma(sT2[l2 * (T0 * T1) + (okB ? qB : 0)], sg2[l2 * T2 + iB], rb);
-            }
-            if (okA) *pa = ra;
-            if (okB) *pb = rb;
-          } else if (okA) {
-            double ra = *pa;
-            for (int l2 = 0; l2 <= L; ++l2) ra = fma(sT2[l2 * (T0 * T1) + qA], sg2[l2 * T2 + iA], ra);
-            *pa = ra;
-          }
-          qA = qB + dq;
-          iA = iB + di;
-          if (iA >= m2) {
-            iA -= m2;
-            ++qA;
-          }
-        }
-      }
+#undef GPW_COLLOC_L
     }
     long long ctoff = btoff, cxoff = bxoff;
     if (e + 2 * NW < sb.ee) {
@@ -519,23 +544,22 @@ __global__ void __launch_bounds__(NW * 32)
 // ----------------------------------------------------------------------------------
 // Integration (Algorithm 2 and, with lext = 1, the gradient of Algorithm 3): the
 // thread block stages its sub-box of the level potential in shared memory once; every
-// task contracts it with the pair's 1-D factors (the V tensor of Sec. III A):
+// task contracts it with the pair's 1-D factors (towards the V tensor of Sec. III A):
 //   U[l2](i0,i1) = sum_i2 v(i0,i1,i2) g2[l2](i2)        (Lx+1) m0 m1 m2 FMAs
 //   W[l2,l1](i0) = sum_i1 U[l2](i0,i1) g1[l1](i1)        nc2(Lx) m0 m1
-//   V[l0,l1,l2]  = sum_i0 W[l2,l1](i0) g0[l0](i0)        nc3(Lx) m0
-// and stores V for the task; the per-pair sum over tasks happens in reduce_parts_kernel
-// in a fixed order.  Lx = L + lext.  Shared rows are padded to an odd number of doubles
-// (P = T + 1) so that lanes walking different rows hit different banks.
+// and stores W for the task.  The last contraction, V[l0,l1,l2] = sum_i0 W[l2,l1](i0)
+// g0[l0](i0), is linear in W, so reduce_parts_kernel first sums the W tensors of the
+// pair's tasks that share an x-segment and contracts once per segment (fixed order).
+// Lx = L + lext.  Shared rows are padded to an odd number of doubles (P = T + 1) so
+// that lanes walking different rows hit different banks.
 template <int T0, int T1, int T2>
 struct IntegLayout {
   static constexpr int P0 = T0 + 1, P1 = T1 + 1, P2 = T2 + 1;
   static constexpr int kSV = T0 * T1 * P2;  // padded potential tile
   static constexpr int kUS = T1 * P0;       // one l2 slab of U: [i1][i0]
-  __host__ __device__ static int buf(int lpx) { return (lpx * (P0 + P1 + P2) + 1) & ~1; }
-  // per-warp staging: two factor-window buffers plus the U and W intermediates
-  __host__ __device__ static int stage(int lpx) {
-    return 2 * buf(lpx) + lpx * kUS + nc2(lpx - 1) * P0;
-  }
+  __host__ __device__ static int buf(int lpx) { return (lpx * (P1 + P2) + 1) & ~1; }
+  // per-warp staging: two factor-window buffers plus the U intermediate
+  __host__ __device__ static int stage(int lpx) { return 2 * buf(lpx) + lpx * kUS; }
 };
 
 template <int T0, int T1, int T2, int NW>
@@ -547,8 +571,6 @@ __global__ void __launch_bounds__(NW * 32)
   extern __shared__ __align__(16) double sm[];
   int* s_tab = reinterpret_cast<int*>(sm);
   const int(*s_dec21)[kNc2Max] = reinterpret_cast<const int(*)[kNc2Max]>(s_tab);
-  const int(*s_dec3)[kNc3Max] =
-      reinterpret_cast<const int(*)[kNc3Max]>(s_tab + (kLextMax + 1) * kNc2Max);
   double* sv = sm + kTabInts / 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   load_tables(s_tab, tabs, tid, NW * 32);
@@ -577,13 +599,11 @@ __global__ void __launch_bounds__(NW * 32)
   double* stage_base = sv + Lay::kSV + warp * stg;
   const int bufn = Lay::buf(lpx);
   double* sU = stage_base + 2 * bufn;
-  double* sW = sU + lpx * kUS;
   __syncthreads();
 
   auto issue = [&](const Task& tk, long long toff, int b) {
-    double* sg0 = stage_base + b * bufn;
-    stage_tables_async<P0, P1, P2>(tab + toff, tk, tk.L + lext + 1, sg0, sg0 + lpx * P0,
-                                   sg0 + lpx * (P0 + P1), lane);
+    double* sg1 = stage_base + b * bufn;
+    stage_yz_async<P1, P2>(tab + toff, tk, tk.L + lext + 1, sg1, sg1 + lpx * P1, lane);
   };
 
   long long e = sb.eb + warp;
@@ -624,8 +644,7 @@ __global__ void __launch_bounds__(NW * 32)
     if (!task_ok(tk, Lx, lpx, sb)) {
       if (lane == 0) set_err(err, 3);
     } else {
-      const double* sg0 = stage_base + buf * bufn;
-      const double* sg1 = sg0 + lpx * P0;
+      const double* sg1 = stage_base + buf * bufn;
       const double* sg2 = sg1 + lpx * P1;
       const int m01 = m0 * m1;
       // U[l2](i1, i0): lanes walk consecutive i1 (rows P2 apart: conflict free)
@@ -644,10 +663,11 @@ __global__ void __launch_bounds__(NW * 32)
         }
       }
       __syncwarp();
-      // W[c21](i0): lanes walk consecutive i0
+      // W[c21](i0) -> the task's slot (compact: item it = c21 m0 + i0, coalesced)
       {
         const float inv0 = __frcp_rn((float)m0);
         const int items = nc2(Lx) * m0;
+        double* dst = part + apoff + a1.w;
         for (int it = lane; it < items; it += 32) {
           const int c21 = fdiv(it, inv0), i0 = it - c21 * m0;
           const int dc = s_dec21[Lx][c21];
@@ -656,22 +676,7 @@ __global__ void __launch_bounds__(NW * 32)
           const double* gr = sg1 + l1 * P1;
           double a = 0.0;
           for (int i1 = 0; i1 < m1; ++i1) a = fma(ur[i1 * P0], gr[i1], a);
-          sW[c21 * P0 + i0] = a;
-        }
-      }
-      __syncwarp();
-      // V[c] -> task slot
-      {
-        const int nc = nc3(Lx);
-        double* dst = part + apoff + (long long)tk.rank * nc;
-        for (int c = lane; c < nc; c += 32) {
-          const int dc = s_dec3[Lx][c];
-          const int c21 = dc & 255, l0 = dc >> 8;
-          const double* wr = sW + c21 * P0;
-          const double* gr = sg0 + l0 * P0;
-          double a = 0.0;
-          for (int i0 = 0; i0 < m0; ++i0) a = fma(wr[i0], gr[i0], a);
-          dst[c] = a;
+          dst[it] = a;
         }
       }
     }
@@ -692,36 +697,125 @@ __global__ void __launch_bounds__(NW * 32)
   cp_async_wait_all();
 }
 
-// Per-pair sum of the task V tensors (fixed task order), times the level weight
-// Omega / N_k (Sec. III A).  One warp per pair.
-__global__ void reduce_parts_kernel(long long np, const KLevels K, const int4* __restrict__ hot_a,
-                                    const int4* __restrict__ hot_b, const int4* __restrict__ ids2,
-                                    const long long* __restrict__ part_off,
-                                    const long long* __restrict__ coef_off,
-                                    const double* __restrict__ part, double* __restrict__ coef,
-                                    int lext) {
-  const int lane = threadIdx.x & 31;
+// Extent of the x-segment of a pair box that starts at grid index i (hi = last index of
+// the box): segments end at sub-box boundaries (multiples of T) and at the periodic
+// boundaries of the N-point mesh, as the plan cut the tasks.
+__device__ __forceinline__ int seg_len(int i, int hi, int N, int T) {
+  const int k = i >= 0 ? i / N : -((-i + N - 1) / N);
+  const int ip = i - k * N;
+  const int end = k * N + min((ip / T + 1) * T, N) - 1;
+  return min(hi, end) - i + 1;
+}
+
+// Per-pair V tensor from the task W tensors (the x contraction of the integration),
+//   V[l0,l1,l2] = w_k sum_segments sum_i0 g0[l0](t0 + i0) sum_{tasks of the segment} W[l2,l1](i0)
+// with the level weight w_k = Omega / N_k (Sec. III A); sums in a fixed order.  One warp
+// per pair; T0 = x extent of the integration sub-box.  The pair's x-segments are taken
+// in chunks of at most kRedX points and kRedCap summed values: the lanes stage the
+// chunk's g0 rows and its segment map in shared memory, sum the task W tensors of every
+// (segment, c21, i0) into rows Wsum[c21][x] (flat over the chunk, so the lanes stay
+// busy), then contract them with g0.  When V has fewer than 32 entries, G = 32 / C lane
+// groups (C = nc rounded up to a power of two) take every G-th x and a fixed butterfly
+// of shuffles adds the groups at the end.
+constexpr int kRedCap = 512;
+constexpr int kRedX = 64;
+constexpr int kRedPW = 4;  // warps per block (static shared memory stays under 48 KB)
+__global__ void __launch_bounds__(kRedPW * 32, 6)
+    reduce_parts_kernel(long long np, const KLevels K, int T0, const int4* __restrict__ hot_a,
+                        const int4* __restrict__ hot_b, const int4* __restrict__ ids2,
+                        const long long* __restrict__ part_off,
+                        const long long* __restrict__ coef_off,
+                        const long long* __restrict__ tab_off, const double* __restrict__ tab,
+                        const double* __restrict__ part, const CoefTables* __restrict__ tabs,
+                        double* __restrict__ coef, int lext) {
+  __shared__ double s_w[kRedPW][kRedCap];
+  __shared__ double s_g[kRedPW][(kLextMax + 1) * kRedX];
+  __shared__ int s_seg[kRedPW][kRedX];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long sw = ((long long)gridDim.x * blockDim.x) >> 5;
+  double* sW = s_w[wib];
+  double* sG = s_g[wib];
+  int* sSeg = s_seg[wib];
   for (long long p = gw; p < np; p += sw) {
-    const int Lx = hot_a[p].w + lext;
-    const int nc = nc3(Lx);
-    const int nt = ids2[p].w;
-    const double wgt = K.lv[hot_b[p].w].weight;
+    const int4 ha = hot_a[p], hb = hot_b[p];
+    const int L = ha.w, Lx = L + lext, nc = nc3(Lx), n2c = nc2(Lx), S = nc2(L + 1);
+    const int lo0 = ha.x, n0 = hb.x, hi0 = lo0 + n0 - 1;
+    const LevelInfo& lv = K.lv[hb.w];
+    const int N0 = lv.N[0];
+    int nsx = 0;
+    for (int t0 = 0; t0 < n0; t0 += seg_len(lo0 + t0, hi0, N0, T0)) ++nsx;
+    const int ns12 = ids2[p].w / nsx;
     const double* src = part + part_off[p];
-    double* dst = coef + coef_off[p];
-    for (int c = lane; c < nc; c += 32) {
-      // four interleaved partial sums keep four loads in flight; fixed order
-      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
-      int r = 0;
-      for (; r + 3 < nt; r += 4) {
-        a0 += src[(long long)r * nc + c];
-        a1 += src[(long long)(r + 1) * nc + c];
-        a2 += src[(long long)(r + 2) * nc + c];
-        a3 += src[(long long)(r + 3) * nc + c];
+    const double* g0 = tab + tab_off[p];
+    const float inv2c = __frcp_rn((float)n2c);
+    // lane -> (group g, entries c = cidx + 32 k)
+    int C = 32;
+    while (C >= 2 * nc && C > 1) C >>= 1;
+    const int G = 32 / C, g = lane / C, cidx = lane - g * C;
+    double v[4] = {0.0, 0.0, 0.0, 0.0};
+    int cc[4], cl[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int c = cidx + 32 * k;
+      const int dc = c < nc ? __ldg(&tabs->dec3[Lx][c]) : 0;
+      cc[k] = dc & 255;
+      cl[k] = dc >> 8;
+    }
+    for (int x0 = 0; x0 < n0;) {
+      // chunk [x0, x1): whole segments (one segment always fits)
+      int x1 = x0 + seg_len(lo0 + x0, hi0, N0, T0);
+      while (x1 < n0) {
+        const int m = seg_len(lo0 + x1, hi0, N0, T0);
+        if (n2c * (x1 + m - x0) > kRedCap || x1 + m - x0 > kRedX) break;
+        x1 += m;
       }
-      for (; r < nt; ++r) a0 += src[(long long)r * nc + c];
-      dst[c] = wgt * ((a0 + a1) + (a2 + a3));
+      const int E = x1 - x0;
+      // segment map (x -> segment start, length) and g0 rows of the chunk
+      for (int xr = lane; xr < E; xr += 32) {
+        const int i = lo0 + x0 + xr;
+        const int kk = i >= 0 ? i / N0 : -((-i + N0 - 1) / N0);
+        const int t0 = max(lo0, kk * N0 + ((i - kk * N0) / T0) * T0) - lo0;
+        sSeg[xr] = (t0 - x0) | (seg_len(lo0 + t0, hi0, N0, T0) << 16);
+      }
+      for (int it = lane; it < (Lx + 1) * E; it += 32) {
+        const int l = it / E, xr = it - l * E;
+        sG[it] = __ldg(g0 + (long long)l * n0 + x0 + xr);
+      }
+      __syncwarp();
+      // one sum per (segment, c21, i0); one FP64 add per task W value (the adds, not the
+      // loads, set the pace: loads are unrolled ahead of the add chain)
+      for (int it = lane; it < n2c * E; it += 32) {
+        const int sg = sSeg[fdiv(it, inv2c)];
+        const int tr = sg & 0xffff, m0 = sg >> 16;
+        const int rem = it - n2c * tr;
+        const int c21 = fdiv(rem, __frcp_rn((float)m0)), i0 = rem - c21 * m0;
+        const double* b = src + (long long)S * (x0 + tr) * ns12 + rem;
+        const long long ts = (long long)S * m0;
+        double a = 0.0;
+#pragma unroll 4
+        for (int r = 0; r < ns12; ++r) a += b[r * ts];
+        sW[c21 * E + tr + i0] = a;
+      }
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (cidx + 32 * k < nc) {
+          const double* wr = sW + cc[k] * E;
+          const double* gr = sG + cl[k] * E;
+          for (int xr = g; xr < E; xr += G) v[k] = fma(wr[xr], gr[xr], v[k]);
+        }
+      }
+      __syncwarp();
+      x0 = x1;
+    }
+    for (int o = C; o < 32; o <<= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], o);
+    const double wgt = lv.weight;
+    double* dst = coef + coef_off[p];
+    if (g == 0) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (cidx + 32 * k < nc) dst[cidx + 32 * k] = wgt * v[k];
     }
   }
 }
@@ -798,56 +892,52 @@ __global__ void assemble_V_kernel(long long ngroups, const int4* __restrict__ gr
   }
 }
 
-// Gradient contraction per pair (Algorithm 3).  With X(a, b) the integral of v against
-// the product of the Cartesian components a (on A) and b (on B_T) of the two primitives,
-// contracted from the pair's degree-(L+1) V tensor through Eq. (binomial),
-//   dE/dA_d = w pref sum_{mu,nu} D_mu,nu [ -a_d X(a - e_d, b) + 2 alpha_a X(a + e_d, b) ]
-//   dE/dB_d = w pref sum_{mu,nu} D_mu,nu [ -b_d X(a, b - e_d) + 2 alpha_b X(a, b + e_d) ]
-// (the centre derivative of (x - A)^a exp(-alpha (x - A)^2)).  One thread per pair.
-__device__ __forceinline__ double xelem(int a0, int a1, int a2, int b0, int b1, int b2,
-                                        const double (*pw)[5], const double* V, int Lx,
-                                        const CoefTables* tabs) {
-  if (a0 < 0 || a1 < 0 || a2 < 0 || b0 < 0 || b1 < 0 || b2 < 0) return 0.0;
-  double s = 0.0;
-  for (int t2 = 0; t2 <= b2; ++t2) {
-    const double c2 = binom(b2, t2) * pw[2][b2 - t2];
-    const int k2 = a2 + t2;
-    for (int t1 = 0; t1 <= b1; ++t1) {
-      const double c21 = c2 * binom(b1, t1) * pw[1][b1 - t1];
-      const int base = tabs->dec21[Lx][tabs->c21base[Lx][k2] + a1 + t1] >> 16;
-      double s0 = 0.0;
-      for (int t0 = 0; t0 <= b0; ++t0) s0 += binom(b0, t0) * pw[0][b0 - t0] * V[base + a0 + t0];
-      s += c21 * s0;
-    }
-  }
-  return s;
+// Flat index of the monomial (k0, k1, k2) in the coefficient order of total degree <= M
+// (l2 outer, l1, l0 inner): the l2 blocks before k2, the l1 rows before k1, then k0.
+__device__ __forceinline__ int mono_index(int k0, int k1, int k2, int M) {
+  const int r = M - k2;
+  return nc3(M) - nc3(r) + k1 * (r + 1) - ((k1 * (k1 - 1)) >> 1) + k0;
 }
 
+// Gradient contraction per pair (Algorithm 3).  The centre derivative of the product
+// (x - A)^a exp(-alpha_a (x - A)^2) brings -a_d (x - A)^(a - e_d) + 2 alpha_a (x - A)^(a + e_d);
+// expanding (x - B)^b about A (Eq. binomial) turns the density-matrix block into
+//   Dt[k]   = sum_{mu,nu} D_mu,nu prod_d C(b_d, t_d) (A_d - B_d)^(b_d - t_d),  k = a + t
+//   Dm_d[k] = sum_{mu,nu} D_mu,nu a_d prod_d C(b_d, t_d) (A_d - B_d)^(b_d - t_d),  k = a - e_d + t
+// so that with the pair's degree-(L+1) V tensor
+//   dE/dA_d = w pref [ 2 alpha_a sum_k Dt[k] V[k + e_d] - sum_k Dm_d[k] V[k] ].
+// The product depends on x - A and x - B only, so d/dA + d/dB = -d/dx, and
+//   dE/dB_d = -dE/dA_d - w pref sum_k Dt[k] [ k_d V[k - e_d] - 2 alpha_p (V[k + e_d] + (A_d - P_d) V[k]) ]
+// (the x derivative of (x - A)^k exp(-alpha_p (x - P)^2), summed on the same grid points).
+// One thread per pair.
 __global__ void grad_pair_kernel(long long np, const int4* __restrict__ ids,
                                  const int4* __restrict__ ids2, const double* __restrict__ geo,
                                  const double* __restrict__ pref,
                                  const long long* __restrict__ coef_off,
-                                 const double* __restrict__ coef,
-                                 const CoefTables* __restrict__ tabs, const double* __restrict__ D,
+                                 const double* __restrict__ coef, const double* __restrict__ D,
                                  int nao, double* __restrict__ pgrad) {
   const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (p >= np) return;
   const int4 id = ids[p];
-  const int la = id.x, lb = id.y, Lx = la + lb + 1;
+  const int la = id.x, lb = id.y, L = la + lb, Lx = L + 1;
   const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
   const double* g = geo + 8 * p;
-  const double aa2 = 2.0 * g[6], ab2 = 2.0 * g[7];
-  double pw[3][5];
+  const double aa = g[6], ab = g[7], ap = aa + ab;
+  double pw[3][4], amp[3];
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const double t = g[d] - g[3 + d];
     pw[d][0] = 1.0;
-#pragma unroll
-    for (int k = 1; k < 5; ++k) pw[d][k] = pw[d][k - 1] * t;
+    pw[d][1] = t;
+    pw[d][2] = t * t;
+    pw[d][3] = t * t * t;
+    amp[d] = ab * t / ap;  // A_d - P_d
   }
-  const double* Vp = coef + coef_off[p];
-  const double scale = (double)ids2[p].z * pref[p];
-  double gA0 = 0, gA1 = 0, gA2 = 0, gB0 = 0, gB1 = 0, gB2 = 0;
+  double Dt[nc3(kLmax)];
+  double Dm[3][nc3(kLmax - 1)];
+  const int nt = nc3(L), nm = L >= 1 ? nc3(L - 1) : 0;
+  for (int c = 0; c < nt; ++c) Dt[c] = 0.0;
+  for (int c = 0; c < nm; ++c) Dm[0][c] = Dm[1][c] = Dm[2][c] = 0.0;
   for (int mu = 0; mu < na; ++mu) {
     int a[3];
     cart_comp(la, mu, a);
@@ -855,28 +945,56 @@ __global__ void grad_pair_kernel(long long np, const int4* __restrict__ ids,
     for (int nu = 0; nu < nb; ++nu) {
       int b[3];
       cart_comp(lb, nu, b);
-      const double dmn = scale * Drow[nu];
-      gA0 += dmn * (aa2 * xelem(a[0] + 1, a[1], a[2], b[0], b[1], b[2], pw, Vp, Lx, tabs) -
-                    a[0] * xelem(a[0] - 1, a[1], a[2], b[0], b[1], b[2], pw, Vp, Lx, tabs));
-      gA1 += dmn * (aa2 * xelem(a[0], a[1] + 1, a[2], b[0], b[1], b[2], pw, Vp, Lx, tabs) -
-                    a[1] * xelem(a[0], a[1] - 1, a[2], b[0], b[1], b[2], pw, Vp, Lx, tabs));
-      gA2 += dmn * (aa2 * xelem(a[0], a[1], a[2] + 1, b[0], b[1], b[2], pw, Vp, Lx, tabs) -
-                    a[2] * xelem(a[0], a[1], a[2] - 1, b[0], b[1], b[2], pw, Vp, Lx, tabs));
-      gB0 += dmn * (ab2 * xelem(a[0], a[1], a[2], b[0] + 1, b[1], b[2], pw, Vp, Lx, tabs) -
-                    b[0] * xelem(a[0], a[1], a[2], b[0] - 1, b[1], b[2], pw, Vp, Lx, tabs));
-      gB1 += dmn * (ab2 * xelem(a[0], a[1], a[2], b[0], b[1] + 1, b[2], pw, Vp, Lx, tabs) -
-                    b[1] * xelem(a[0], a[1], a[2], b[0], b[1] - 1, b[2], pw, Vp, Lx, tabs));
-      gB2 += dmn * (ab2 * xelem(a[0], a[1], a[2], b[0], b[1], b[2] + 1, pw, Vp, Lx, tabs) -
-                    b[2] * xelem(a[0], a[1], a[2], b[0], b[1], b[2] - 1, pw, Vp, Lx, tabs));
+      const double dmn = Drow[nu];
+      for (int t2 = 0; t2 <= b[2]; ++t2) {
+        const double c2 = dmn * binom(b[2], t2) * pw[2][b[2] - t2];
+        for (int t1 = 0; t1 <= b[1]; ++t1) {
+          const double c21 = c2 * binom(b[1], t1) * pw[1][b[1] - t1];
+          for (int t0 = 0; t0 <= b[0]; ++t0) {
+            const double c = c21 * binom(b[0], t0) * pw[0][b[0] - t0];
+            const int k0 = a[0] + t0, k1 = a[1] + t1, k2 = a[2] + t2;
+            Dt[mono_index(k0, k1, k2, L)] += c;
+            if (a[0] > 0) Dm[0][mono_index(k0 - 1, k1, k2, L - 1)] += a[0] * c;
+            if (a[1] > 0) Dm[1][mono_index(k0, k1 - 1, k2, L - 1)] += a[1] * c;
+            if (a[2] > 0) Dm[2][mono_index(k0, k1, k2 - 1, L - 1)] += a[2] * c;
+          }
+        }
+      }
     }
   }
+  const double* V = coef + coef_off[p];
+  double sA[3] = {0.0, 0.0, 0.0}, sX[3] = {0.0, 0.0, 0.0}, sC[3] = {0.0, 0.0, 0.0};
+  int c = 0;
+  for (int k2 = 0; k2 <= L; ++k2)
+    for (int k1 = 0; k1 <= L - k2; ++k1)
+      for (int k0 = 0; k0 <= L - k2 - k1; ++k0, ++c) {
+        const double dt = Dt[c];
+        const double v0 = V[mono_index(k0, k1, k2, Lx)];
+        const int k[3] = {k0, k1, k2};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const double vp = V[mono_index(k0 + (d == 0), k1 + (d == 1), k2 + (d == 2), Lx)];
+          const double vm = k[d] > 0 ? V[mono_index(k0 - (d == 0), k1 - (d == 1), k2 - (d == 2), Lx)] : 0.0;
+          sA[d] += dt * vp;
+          sX[d] += dt * (k[d] * vm - 2.0 * ap * (vp + amp[d] * v0));
+        }
+      }
+  c = 0;
+  for (int k2 = 0; k2 < L; ++k2)
+    for (int k1 = 0; k1 < L - k2; ++k1)
+      for (int k0 = 0; k0 < L - k2 - k1; ++k0, ++c) {
+        const double v0 = V[mono_index(k0, k1, k2, Lx)];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) sC[d] += Dm[d][c] * v0;
+      }
+  const double scale = (double)ids2[p].z * pref[p];
   double* out = pgrad + 6 * p;
-  out[0] = gA0;
-  out[1] = gA1;
-  out[2] = gA2;
-  out[3] = gB0;
-  out[4] = gB1;
-  out[5] = gB2;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double gA = scale * (2.0 * aa * sA[d] - sC[d]);
+    out[d] = gA;
+    out[3 + d] = -gA - scale * sX[d];
+  }
 }
 
 // Per-atom sums of the per-pair gradient sextets: one warp per atom, lanes stride its
@@ -1311,11 +1429,11 @@ PlanView make_view(const Plan& p) {
 
 cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s) {
   if (p.npairs == 0) return cudaSuccess;
-  long long blocks = std::min<long long>((p.npairs + 7) / 8, 152LL * 64);
+  long long blocks = std::min<long long>((p.npairs + kRedPW - 1) / kRedPW, 152LL * 128);
   ++p.launches;
-  reduce_parts_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, make_klevels(p, false), p.d.hot_a, p.d.hot_b,
-                                                  p.d.ids2, p.d.part_off, p.d.coef_off, p.d.part,
-                                                  p.d.coef, lext);
+  reduce_parts_kernel<<<(int)blocks, kRedPW * 32, 0, s>>>(
+      p.npairs, make_klevels(p, true), p.tile_i[0], p.d.hot_a, p.d.hot_b, p.d.ids2, p.d.part_off,
+      p.d.coef_off, p.d.tab_off, p.d.tab, p.d.part, p.d.tabs, p.d.coef, lext);
   return cudaGetLastError();
 }
 
@@ -1333,8 +1451,8 @@ cudaError_t launch_grad(const Plan& p, const double* D, double* grad, cudaStream
   if (p.npairs > 0) {
     ++p.launches;
     grad_pair_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
-        p.npairs, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, p.d.coef, p.d.tabs, D,
-        p.nao, p.d.pgrad);
+        p.npairs, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, p.d.coef, D, p.nao,
+        p.d.pgrad);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

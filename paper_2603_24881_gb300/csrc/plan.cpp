@@ -148,11 +148,17 @@ std::vector<PairBox> pairs_view(const std::vector<PairTmp>& pairs) {
 // at the mesh edge), and for every pair each (sub-box, periodic copy) its box meets.
 // Fills lev[k].sub_base, the CSR offsets, the 2-int4 task records (sorted by pair
 // inside every sub-box), the work list (heaviest sub-box first) and, if ranks is
-// non-NULL, the number of tasks of every pair.
+// non-NULL (the integration tasks), the number of tasks of every pair, the size of its
+// block of per-task W tensors (psize) and each task's offset in that block (record
+// r1.w).  A pair's tasks are ranked x-segment first; the W tensor of a task (nc2(L+1)
+// rows of m0) sits at nc2(L+1) (t0 ns12 + r12 m0), with ns12 the number of (y, z)
+// segments and r12 the task's index among them, so the tasks of one x-segment are
+// contiguous and every x-segment block starts at nc2(L+1) t0 ns12.
 int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector<int4>& hot_a,
                 const int* T, LevelInfo* lev, std::vector<long long>* sub_off,
                 std::vector<int4>* task, std::vector<int4>* work, long long* nent_out,
-                long long* nwork_out, long long* nsub_out, std::vector<int>* ranks) {
+                long long* nwork_out, long long* nsub_out, std::vector<int>* ranks,
+                std::vector<long long>* psize) {
   const int K = plan->nlev;
   const long long np = (long long)pairs.size();
   long long nsub = 0;
@@ -177,6 +183,7 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
   *nent_out = nent;
   task->assign(2 * nent, make_int4(0, 0, 0, 0));
   if (ranks) ranks->assign(np, 0);
+  if (psize) psize->assign(np, 0);
   std::vector<long long> fill(count.begin(), count.end() - 1);
   for (long long p = 0; p < np; ++p) {
     const PairBox& t = pairs[p];
@@ -192,6 +199,15 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
       }
     }
     int rank = 0;
+    const long long ns12 = (long long)sg[1].size() * sg[2].size();
+    const long long S = nc2(L + 1);
+    if (psize) {
+      (*psize)[p] = S * n[0] * ns12;
+      if ((*psize)[p] > INT32_MAX) {
+        set_error("gpw_plan: per-pair task block too large");
+        return GPW_ERANGE;
+      }
+    }
     auto isect = [&](int d, const Seg& sgm, int* m, int* u, int* tt) {
       long long s0 = (long long)sgm.j * T[d];
       long long ext = std::min<long long>(T[d], lv.N[d] - s0);
@@ -213,8 +229,9 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
           long long slot = fill[sub]++;
           (*task)[2 * slot] = make_int4((int)p, m[0] | (m[1] << 8) | (m[2] << 16) | (L << 24),
                                         u[0] | (u[1] << 8) | (u[2] << 16), rank);
+          const long long woff = S * ((long long)tt[0] * ns12 + (rank % ns12) * m[0]);
           (*task)[2 * slot + 1] = make_int4(tt[0] | (n[0] << 16), tt[1] | (n[1] << 16),
-                                            tt[2] | (n[2] << 16), 0);
+                                            tt[2] | (n[2] << 16), psize ? (int)woff : 0);
           ++rank;
         }
     if (ranks) (*ranks)[p] = rank;
@@ -555,9 +572,10 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   // ---- per-level sub-box task lists (CSR), one task per (pair, sub-box, image shift),
   // for the collocation tile and for the integration tile
   std::vector<int> ranks;
+  std::vector<long long> psize;
   int rc = build_tasks(plan, pairs_view(pairs), H->hot_a, plan->tile, plan->lev, &H->sub_off_c,
                        &H->task_c, &H->work_c, &plan->nent, &plan->nwork, &plan->nsub_total,
-                       nullptr);
+                       nullptr, nullptr);
   if (rc) return rc;
   for (int k = 0; k < K; ++k) plan->lev_i[k] = plan->lev[k];
   for (int k = 0; k < K; ++k)
@@ -565,16 +583,17 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
       plan->lev_i[k].nsb[d] = (plan->lev[k].N[d] + plan->tile_i[d] - 1) / plan->tile_i[d];
   long long nsub_i = 0;
   rc = build_tasks(plan, pairs_view(pairs), H->hot_a, plan->tile_i, plan->lev_i, &H->sub_off_i,
-                   &H->task_i, &H->work_i, &plan->nent_i, &plan->nwork_i, &nsub_i, &ranks);
+                   &H->task_i, &H->work_i, &plan->nent_i, &plan->nwork_i, &nsub_i, &ranks,
+                   &psize);
   if (rc) return rc;
   long long part_total = 0;
   for (long long p = 0; p < np; ++p) {
     H->ids2[p].w = ranks[p];
     H->part_off[p] = part_total;
-    part_total += (long long)ranks[p] * nc3(H->hot_a[p].w + 1);
+    part_total += psize[p];
   }
   // the part buffer also holds the x-contracted tables of collocation (never live at the
-  // same time as the task V tensors)
+  // same time as the task W tensors)
   plan->part_total = std::max(part_total, xt_total);
 
   // ---- V assembly groups: runs of pairs with the same contracted shell pair
