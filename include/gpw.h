@@ -90,7 +90,7 @@ typedef struct {
   int tile[3];                /* sub-box owned by one collocation thread block (grid
                                  points along a1, a2, a3); {0,0,0} = default {4,8,16} */
   int tile_integ[3];          /* sub-box of one integration thread block;
-                                 {0,0,0} = default {4,8,64}.  Supported shapes:
+                                 {0,0,0} = default {8,8,32}.  Supported shapes:
                                  gpw_tile_supported. */
 } gpw_desc;
 
@@ -133,7 +133,11 @@ int gpw_plan_prepare(const gpw_desc* desc, gpw_plan_t* out);
  * (enqueued on `stream`).  On failure the plan stays prepared and can be retried. */
 int gpw_plan_commit(gpw_plan_t plan, void* stream);
 
-/* 1 if the sub-box shape (t0, t1, t2) has compiled kernels, else 0. */
+/* Which kernels exist for the sub-box shape (t0, t1, t2): a mask of GPW_TILE_COLLOC
+ * (usable as gpw_desc.tile) and GPW_TILE_INTEG (usable as gpw_desc.tile_integ); 0 if
+ * neither. */
+#define GPW_TILE_COLLOC 1
+#define GPW_TILE_INTEG 2
 int gpw_tile_supported(int t0, int t1, int t2);
 
 /* Fill *info (host). */

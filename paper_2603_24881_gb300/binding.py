@@ -51,7 +51,10 @@ class Desc(ctypes.Structure):
                 ("flags", ctypes.c_int), ("tile", ctypes.c_int * 3),
                 ("tile_integ", ctypes.c_int * 3)]
 
-TILES = [(8, 8, 16), (4, 8, 32), (8, 8, 32), (4, 8, 64)]
+# sub-box shapes with compiled kernels (gpw_tile_supported): collocation, integration
+TILES = [(8, 8, 16), (4, 8, 32), (8, 8, 32), (4, 8, 64), (4, 8, 16), (4, 4, 16), (2, 8, 16),
+         (4, 4, 32)]
+TILES_INTEG = TILES + [(8, 8, 64), (8, 4, 64)]
 
 
 class Info(ctypes.Structure):

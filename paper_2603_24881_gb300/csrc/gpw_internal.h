@@ -122,7 +122,7 @@ struct Plan {
   int nao = 0, natm = 0, nlev = 0, lmax = 0;
   int nprim = 0, nshell = 0;
   int tile[3] = {kT0, kT1, kT2};      // collocation sub-box
-  int tile_i[3] = {4, 8, 64};         // integration sub-box
+  int tile_i[3] = {8, 8, 32};         // integration sub-box
   double L[3] = {0, 0, 0};
   double omega = 0;
   double E[GPW_MAX_LEVELS] = {0};

@@ -371,7 +371,6 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
 
 template <int T0, int T1, int T2>
 struct CollocLayout {
-  static constexpr int kTileN = T0 * T1 * T2;
   // one staging buffer: the task's window of the x-contracted table (nc2(lp - 1) rows of
   // T0) and the y and z factor windows (lp rows of T1, T2), for lp = lmax + 1 (even
   // length keeps 16-byte alignment)
@@ -1185,8 +1184,10 @@ int even(int x) { return (x + 1) & ~1; }
 
 constexpr int kNW = 8;
 
-#define GPW_TILE_SHAPES(X) \
+// Sub-box shapes with compiled kernels: collocation, and integration (a superset).
+#define GPW_COLLOC_SHAPES(X) \
   X(8, 8, 16) X(4, 8, 32) X(8, 8, 32) X(4, 8, 64) X(4, 8, 16) X(4, 4, 16) X(2, 8, 16) X(4, 4, 32)
+#define GPW_INTEG_SHAPES(X) GPW_COLLOC_SHAPES(X) X(8, 8, 64) X(8, 4, 64)
 
 template <int T0, int T1, int T2>
 size_t colloc_smem(int stg, int nw) {
@@ -1224,11 +1225,16 @@ int pick_colloc_warps(int stg, int* nw_out, size_t* smem_out) {
 }  // namespace
 
 extern "C" int gpw_tile_supported(int t0, int t1, int t2) {
-#define GPW_TILE_CHECK(a, b, c) \
-  if (t0 == a && t1 == b && t2 == c) return 1;
-  GPW_TILE_SHAPES(GPW_TILE_CHECK)
-#undef GPW_TILE_CHECK
-  return 0;
+  int r = 0;
+#define GPW_TILE_CHECK_C(a, b, c) \
+  if (t0 == a && t1 == b && t2 == c) r |= GPW_TILE_COLLOC;
+#define GPW_TILE_CHECK_I(a, b, c) \
+  if (t0 == a && t1 == b && t2 == c) r |= GPW_TILE_INTEG;
+  GPW_COLLOC_SHAPES(GPW_TILE_CHECK_C)
+  GPW_INTEG_SHAPES(GPW_TILE_CHECK_I)
+#undef GPW_TILE_CHECK_C
+#undef GPW_TILE_CHECK_I
+  return r;
 }
 
 KLevels make_klevels(const Plan& p, bool integ) {
@@ -1256,19 +1262,23 @@ cudaError_t configure_kernels(Plan* p) {
   if (e != cudaSuccess) return e;                                                                 \
   e = cudaFuncSetAttribute(collocate_kernel<a, b, c, 4>,                                          \
                            cudaFuncAttributeMaxDynamicSharedMemorySize, optin);                   \
-  if (e != cudaSuccess) return e;                                                                 \
+  if (e != cudaSuccess) return e;
+#define GPW_TILE_ATTR_I(a, b, c)                                                                  \
   e = cudaFuncSetAttribute(integrate_kernel<a, b, c, kNW>,                                        \
                            cudaFuncAttributeMaxDynamicSharedMemorySize, optin);                   \
   if (e != cudaSuccess) return e;
-  GPW_TILE_SHAPES(GPW_TILE_ATTR)
+  GPW_COLLOC_SHAPES(GPW_TILE_ATTR)
+  GPW_INTEG_SHAPES(GPW_TILE_ATTR_I)
 #undef GPW_TILE_ATTR
+#undef GPW_TILE_ATTR_I
 #define GPW_TILE_CONF(a, b, c)                                                      \
   if (p->tile[0] == a && p->tile[1] == b && p->tile[2] == c) {                      \
     found |= 1;                                                                     \
     p->stg_colloc = even(CollocLayout<a, b, c>::stage(lp));                         \
     if (pick_colloc_warps<a, b, c>(p->stg_colloc, &p->nw_colloc, &p->smem_colloc) == 0) \
       return cudaErrorInvalidValue;                                                 \
-  }                                                                                 \
+  }
+#define GPW_TILE_CONF_I(a, b, c)                                                    \
   if (p->tile_i[0] == a && p->tile_i[1] == b && p->tile_i[2] == c) {                \
     found |= 2;                                                                     \
     p->stg_integ = even(IntegLayout<a, b, c>::stage(p->lmax + 1));                  \
@@ -1276,8 +1286,10 @@ cudaError_t configure_kernels(Plan* p) {
     p->smem_integ = integ_smem<a, b, c>(p->stg_integ);                              \
     p->smem_integ1 = integ_smem<a, b, c>(p->stg_integ1);                            \
   }
-  GPW_TILE_SHAPES(GPW_TILE_CONF)
+  GPW_COLLOC_SHAPES(GPW_TILE_CONF)
+  GPW_INTEG_SHAPES(GPW_TILE_CONF_I)
 #undef GPW_TILE_CONF
+#undef GPW_TILE_CONF_I
   if (found != 3) return cudaErrorInvalidValue;
   p->nw_integ = kNW;
   if ((size_t)optin < std::max(p->smem_colloc, std::max(p->smem_integ, p->smem_integ1)))
@@ -1325,7 +1337,7 @@ cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views,
     return cudaGetLastError();                                                             \
   }
 #define GPW_TILE_COLLOC(a, b, c) GPW_COLLOC_NW(a, b, c, 8) GPW_COLLOC_NW(a, b, c, 6) GPW_COLLOC_NW(a, b, c, 4)
-  GPW_TILE_SHAPES(GPW_TILE_COLLOC)
+  GPW_COLLOC_SHAPES(GPW_TILE_COLLOC)
 #undef GPW_TILE_COLLOC
 #undef GPW_COLLOC_NW
   return cudaErrorInvalidValue;
@@ -1342,7 +1354,7 @@ cudaError_t launch_integrate_views(const GridLaunch& cfg, int lext, const PlanVi
         views, work, tabs, lext, cfg.lp, cfg.stg);                                         \
     return cudaGetLastError();                                                             \
   }
-  GPW_TILE_SHAPES(GPW_TILE_INTEG)
+  GPW_INTEG_SHAPES(GPW_TILE_INTEG)
 #undef GPW_TILE_INTEG
   return cudaErrorInvalidValue;
 }
@@ -1393,14 +1405,17 @@ cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, Grid
     colloc->stg = even(CollocLayout<a, b, c>::stage(lmax + 1));                             \
     if (pick_colloc_warps<a, b, c>(colloc->stg, &colloc->nw, &colloc->smem) == 0)          \
       return cudaErrorInvalidValue;                                                         \
-  }                                                                                         \
+  }
+#define GPW_TILE_BCONF_I(a, b, c)                                                           \
   if (tile_i[0] == a && tile_i[1] == b && tile_i[2] == c) {                                 \
     found |= 2;                                                                             \
     integ1->stg = even(IntegLayout<a, b, c>::stage(lmax + 2));                              \
     integ1->smem = integ_smem<a, b, c>(integ1->stg);                                        \
   }
-  GPW_TILE_SHAPES(GPW_TILE_BCONF)
+  GPW_COLLOC_SHAPES(GPW_TILE_BCONF)
+  GPW_INTEG_SHAPES(GPW_TILE_BCONF_I)
 #undef GPW_TILE_BCONF
+#undef GPW_TILE_BCONF_I
   return found == 3 ? cudaSuccess : cudaErrorInvalidValue;
 }
 

@@ -293,14 +293,15 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   const int K = desc->nlevels;
   plan->nlev = K;
   if (desc->tile[0] || desc->tile[1] || desc->tile[2]) {
-    if (!gpw_tile_supported(desc->tile[0], desc->tile[1], desc->tile[2])) {
+    if (!(gpw_tile_supported(desc->tile[0], desc->tile[1], desc->tile[2]) & GPW_TILE_COLLOC)) {
       set_error("gpw_plan: unsupported tile shape");
       return GPW_EINVAL;
     }
     for (int d = 0; d < 3; ++d) plan->tile[d] = desc->tile[d];
   }
   if (desc->tile_integ[0] || desc->tile_integ[1] || desc->tile_integ[2]) {
-    if (!gpw_tile_supported(desc->tile_integ[0], desc->tile_integ[1], desc->tile_integ[2])) {
+    if (!(gpw_tile_supported(desc->tile_integ[0], desc->tile_integ[1], desc->tile_integ[2]) &
+          GPW_TILE_INTEG)) {
       set_error("gpw_plan: unsupported integration tile shape");
       return GPW_EINVAL;
     }

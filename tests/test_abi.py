@@ -38,3 +38,15 @@ def test_strerror_without_gpu():
     assert lib.gpw_strerror(0) == b"ok"
     assert lib.gpw_strerror(-1) == b"invalid argument"
     assert lib.gpw_strerror(-7) == b"size beyond a fixed limit"
+
+
+def test_tile_support_mask_without_gpu():
+    # host-only query: collocation shapes are integration shapes too; two shapes exist
+    # for integration only; anything else has no kernels
+    lib = gpw.load()
+    for t in binding.TILES:
+        assert lib.gpw_tile_supported(*t) == 3, t
+    for t in set(binding.TILES_INTEG) - set(binding.TILES):
+        assert lib.gpw_tile_supported(*t) == 2, t
+    assert lib.gpw_tile_supported(3, 8, 16) == 0
+    assert lib.gpw_tile_supported(0, 0, 0) == 0

@@ -236,9 +236,23 @@ def test_tile_shapes(gpw, cases, tile):
     assert gp.check_device() == 0
 
 
+@pytest.mark.parametrize("tile_integ", [(8, 8, 64), (8, 4, 64)])
+def test_integration_only_tiles(gpw, cases, tile_integ):
+    s, op = cases["water4"]
+    gp = gpw.Plan(s, tile_integ=tile_integ)
+    assert gp.stats()["tile_integ"] == tile_integ
+    out = gp.fock_grad(s.D)
+    r = op.fock(s.D)
+    assert _rel(out["V"].cpu().numpy(), r["V"]) <= RTOL
+    assert np.max(np.abs(out["grad"].cpu().numpy() - op.grad_levels(s.D, r["v_levels"]))) <= 1e-7
+    assert gp.check_device() == 0
+
+
 def test_unsupported_tile(gpw):
     with pytest.raises(gpw.GpwError):
         gpw.Plan(workloads.tiny(), tile=(3, 8, 16))
+    with pytest.raises(gpw.GpwError):  # an integration-only shape as collocation tile
+        gpw.Plan(workloads.tiny(), tile=(8, 8, 64))
 
 
 def test_mixed_tiles_carbon_like_f_shells(gpw):
