@@ -42,19 +42,34 @@ FP64_PEAK_TFLOPS = 152 * 4 * 2.070e9 / 1e12
 WORKLOAD = "water256"
 WORKLOAD_DESC = ("256 H2O, cubic L=37.3 Bohr, 7168 Cartesian AOs, 280 Ha, 4 levels "
                  "(288/168/96/60), tau=1e-6; step = gpw_fock_grad (V, energies, Hxc gradient)")
-# DRAM bytes per launch of the dominant kernel from one ncu capture, valid while the
-# kernel source is unchanged (sha256 of csrc/kernels.cu at capture time).
+
+
+def _workload_desc(name: str, system, stats) -> str:
+    """What one step computes on the named workload (sizes from the system and plan)."""
+    if name == WORKLOAD:
+        return WORKLOAD_DESC
+    L = float(system.lattice[0][0])
+    mesh = "/".join(str(int(m[0])) for m in stats["meshes"])
+    return (f"{name}: cubic L={L:.2f} Bohr, {system.natm} atoms, {system.nao} Cartesian AOs, "
+            f"{system.cutoff_ha:g} Ha, {stats['nlevels']} levels ({mesh}), tau={system.tau:g}; "
+            f"step = gpw_fock_grad (V, energies, Hxc gradient)")
+
+
+# DRAM bytes per launch of the dominant kernel from one ncu capture of this workload,
+# valid while the kernels and the plan (task lists, work order) are unchanged: sha256 of
+# csrc/kernels.cu + csrc/plan.cpp at capture time.
 TRAFFIC = {
-    # integration at degree L+1, 4x8x64 sub-box: 1.300 GB per launch on water32
-    # (1.413e9 pair-points), scaled by pair-points to water256 (1.027e10)
-    "integrate_ip1": {"bytes_per_launch": 9.451e+09, "src_sha": "e2d367342cdaf6af",
-                      "capture": "profiles/ncu_collocate_integrate_water32.md"},
+    # integration at degree L+1 (8x8x32 sub-box), water256, one launch: read + write
+    "integrate_ip1": {"bytes_per_launch": 1.7964e10, "src_sha": "bc5b10f35232fb61",
+                      "capture": "profiles/launches_water256_fock_grad.md"},
 }
 
 
 def _kernels_sha() -> str:
-    p = os.path.join(ROOT, "paper_2603_24881_gb300", "csrc", "kernels.cu")
-    return hashlib.sha256(open(p, "rb").read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for f in ("kernels.cu", "plan.cpp"):
+        h.update(open(os.path.join(ROOT, "paper_2603_24881_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
 
 
 def _args():
@@ -361,7 +376,7 @@ def main():
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": ms / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64", "data": "synthetic",
-                "config": {"workload": WORKLOAD_DESC, "pairs": st["npairs"],
+                "config": {"workload": _workload_desc(a.workload, s, st), "pairs": st["npairs"],
                            "pair_points": st["pair_points"], "tasks": st["nentries"],
                            "l2": "no flush: plan tables, tasks and grids (>2 GB) exceed L2",
                            "tile": list(st["tile"]), "tile_integ": list(st["tile_integ"]),

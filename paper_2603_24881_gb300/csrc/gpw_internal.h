@@ -24,6 +24,13 @@ constexpr int kNc2Max = (kLextMax + 1) * (kLextMax + 2) / 2;                   /
 // along the fastest grid index.  The shape is a plan parameter (see kTileShapes).
 constexpr int kT0 = 4, kT1 = 8, kT2 = 16;
 
+// Integration work items hold at most max(kChunkMin, ~tasks / kChunkDiv) tasks (about
+// four per resident block of 2 x 152 SMs).
+constexpr long long kChunkMin = 64;
+constexpr long long kChunkDiv = 4 * 2 * 152;
+// Work-list band (items): a few times the blocks resident in one launch.
+constexpr long long kBand = 2048;
+
 // Number of monomials x^l0 y^l1 z^l2 with l0 + l1 + l2 <= L, and of (l1, l2) pairs.
 __host__ __device__ constexpr int nc3(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
 __host__ __device__ constexpr int nc2(int L) { return (L + 1) * (L + 2) / 2; }
@@ -71,6 +78,7 @@ struct PlanView {
   const double* xt;
   double* grids;
   int* err;
+  int chunk_i;  // tasks per integration work item (items carry level | chunk << 4)
 };
 
 struct DeviceArrays {
@@ -123,6 +131,7 @@ struct Plan {
   int nprim = 0, nshell = 0;
   int tile[3] = {kT0, kT1, kT2};      // collocation sub-box
   int tile_i[3] = {8, 8, 32};         // integration sub-box
+  int chunk_i = 0;                    // most tasks per integration work item
   double L[3] = {0, 0, 0};
   double omega = 0;
   double E[GPW_MAX_LEVELS] = {0};

@@ -576,7 +576,7 @@ __global__ void __launch_bounds__(NW * 32)
 
   const int4 item = work[blockIdx.x];
   const PlanView& pv = views[item.x];
-  const LevelInfo& lv = pv.li[item.y];
+  const LevelInfo& lv = pv.li[item.y & 15];
   const int4* __restrict__ task = pv.task_i;
   const long long* __restrict__ tab_off = pv.tab_off;
   const long long* __restrict__ part_off = pv.part_off;
@@ -584,7 +584,9 @@ __global__ void __launch_bounds__(NW * 32)
   const double* __restrict__ grids = pv.grids;
   double* __restrict__ part = pv.part;
   int* __restrict__ err = pv.err;
-  const SubBox sb = sub_box<T0, T1, T2>(lv, item.z, pv.sub_off_i);
+  SubBox sb = sub_box<T0, T1, T2>(lv, item.z, pv.sub_off_i);
+  sb.eb += (long long)(item.y >> 4) * pv.chunk_i;  // this item's chunk of the task list
+  sb.ee = min(sb.ee, sb.eb + pv.chunk_i);
   {
     const double* vin = grids + lv.grid_off;
     const int e12 = sb.ext[1] * sb.ext[2];
@@ -716,6 +718,18 @@ __device__ __forceinline__ int seg_len(int i, int hi, int N, int T) {
 // busy), then contract them with g0.  When V has fewer than 32 entries, G = 32 / C lane
 // groups (C = nc rounded up to a power of two) take every G-th x and a fixed butterfly
 // of shuffles adds the groups at the end.
+// a + b[0] + b[ts] + ... + b[(N-1) ts], added in that order; all N loads are issued
+// before the first add
+template <int N>
+__device__ __forceinline__ double sum_strided(const double* __restrict__ b, long long ts, double a) {
+  double x[N];
+#pragma unroll
+  for (int j = 0; j < N; ++j) x[j] = b[j * ts];
+#pragma unroll
+  for (int j = 0; j < N; ++j) a += x[j];
+  return a;
+}
+
 constexpr int kRedCap = 512;
 constexpr int kRedX = 64;
 constexpr int kRedPW = 4;  // warps per block (static shared memory stays under 48 KB)
@@ -792,8 +806,18 @@ __global__ void __launch_bounds__(kRedPW * 32, 6)
         const double* b = src + (long long)S * (x0 + tr) * ns12 + rem;
         const long long ts = (long long)S * m0;
         double a = 0.0;
-#pragma unroll 4
-        for (int r = 0; r < ns12; ++r) a += b[r * ts];
+        int r = 0;
+        for (; r + 8 <= ns12; r += 8) a = sum_strided<8>(b + r * ts, ts, a);
+        switch (ns12 - r) {
+          case 1: a = sum_strided<1>(b + r * ts, ts, a); break;
+          case 2: a = sum_strided<2>(b + r * ts, ts, a); break;
+          case 3: a = sum_strided<3>(b + r * ts, ts, a); break;
+          case 4: a = sum_strided<4>(b + r * ts, ts, a); break;
+          case 5: a = sum_strided<5>(b + r * ts, ts, a); break;
+          case 6: a = sum_strided<6>(b + r * ts, ts, a); break;
+          case 7: a = sum_strided<7>(b + r * ts, ts, a); break;
+          default: break;
+        }
         sW[c21 * E + tr + i0] = a;
       }
       __syncwarp();
@@ -1439,6 +1463,7 @@ PlanView make_view(const Plan& p) {
   v.xt = p.d.part;
   v.grids = p.d.grids;
   v.err = p.d.err;
+  v.chunk_i = p.chunk_i;
   return v;
 }
 

@@ -158,7 +158,7 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
                 const int* T, LevelInfo* lev, std::vector<long long>* sub_off,
                 std::vector<int4>* task, std::vector<int4>* work, long long* nent_out,
                 long long* nwork_out, long long* nsub_out, std::vector<int>* ranks,
-                std::vector<long long>* psize) {
+                std::vector<long long>* psize, long long* chunk_io) {
   const int K = plan->nlev;
   const long long np = (long long)pairs.size();
   long long nsub = 0;
@@ -237,18 +237,76 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
     if (ranks) (*ranks)[p] = rank;
   }
   *sub_off = count;
-  std::vector<std::pair<long long, long long>> w;  // (-count, global sub)
-  for (long long sidx = 0; sidx < nsub; ++sidx) {
-    long long c = count[sidx + 1] - count[sidx];
-    if (c > 0) w.push_back({-c, sidx});
+  // work items {plan slot, level | chunk << 4, sub-box, tasks}: with chunk_io a sub-box
+  // with more tasks is cut into items of `chunk` consecutive tasks (integration only:
+  // its tasks write separate slots); *chunk_io < 0 asks for the default size
+  long long chunk = 0;
+  if (chunk_io) {
+    chunk = *chunk_io >= 0 ? *chunk_io : std::max(kChunkMin, (nent + kChunkDiv - 1) / kChunkDiv);
+    if (chunk > INT32_MAX) chunk = INT32_MAX;
+    *chunk_io = chunk;
   }
-  std::sort(w.begin(), w.end());
-  work->resize(w.size());
-  for (size_t i = 0; i < w.size(); ++i) {
-    long long sidx = w[i].second;
+  // Order: items in Morton order of their sub-box (per level) are cut into bands of
+  // kBand items; each band runs heaviest first and bands run by decreasing mean weight.
+  // Blocks resident at the same time then work on nearby sub-boxes, whose pairs' factor
+  // tables are shared in L2, while the light items still come last.
+  struct W {
+    long long c, sidx, j;
+    unsigned long long key;
+  };
+  auto spread = [](unsigned long long x) {
+    unsigned long long r = 0;
+    for (int b = 0; b < 20; ++b) r |= ((x >> b) & 1ULL) << (3 * b);
+    return r;
+  };
+  std::vector<W> w;
+  for (long long sidx = 0; sidx < nsub; ++sidx) {
+    const long long c = count[sidx + 1] - count[sidx];
+    if (c <= 0) continue;
     int k = 0;
     while (k + 1 < K && lev[k + 1].sub_base <= sidx) ++k;
-    (*work)[i] = make_int4(0, k, (int)(sidx - lev[k].sub_base), (int)std::min<long long>(-w[i].first, 1 << 30));
+    const long long loc = sidx - lev[k].sub_base;
+    const long long j2 = loc % lev[k].nsb[2], j1 = (loc / lev[k].nsb[2]) % lev[k].nsb[1];
+    const long long j0 = loc / ((long long)lev[k].nsb[2] * lev[k].nsb[1]);
+    const unsigned long long key =
+        ((unsigned long long)k << 60) | (spread(j0) << 2) | (spread(j1) << 1) | spread(j2);
+    if (chunk <= 0 || c <= chunk) {
+      w.push_back({c, sidx, 0, key});
+    } else {
+      for (long long j = 0; j * chunk < c; ++j)
+        w.push_back({std::min(chunk, c - j * chunk), sidx, j, key});
+    }
+  }
+  std::stable_sort(w.begin(), w.end(), [](const W& a, const W& b) { return a.key < b.key; });
+  std::vector<std::pair<double, size_t>> bands;  // (-mean weight, first item)
+  for (size_t b = 0; b < w.size(); b += kBand) {
+    const size_t e = std::min(w.size(), b + (size_t)kBand);
+    std::stable_sort(w.begin() + b, w.begin() + e, [](const W& x, const W& y) { return x.c > y.c; });
+    double sum = 0;
+    for (size_t i = b; i < e; ++i) sum += (double)w[i].c;
+    bands.push_back({-sum / (double)(e - b), b});
+  }
+  std::stable_sort(bands.begin(), bands.end(),
+                   [](const std::pair<double, size_t>& x, const std::pair<double, size_t>& y) {
+                     return x.first < y.first;
+                   });
+  std::vector<W> ordered;
+  ordered.reserve(w.size());
+  for (const auto& bd : bands)
+    for (size_t i = bd.second; i < std::min(w.size(), bd.second + (size_t)kBand); ++i)
+      ordered.push_back(w[i]);
+  w.swap(ordered);
+  work->resize(w.size());
+  for (size_t i = 0; i < w.size(); ++i) {
+    const long long sidx = w[i].sidx;
+    int k = 0;
+    while (k + 1 < K && lev[k + 1].sub_base <= sidx) ++k;
+    if (w[i].j >= (1LL << 27)) {
+      set_error("gpw_plan: too many work chunks in one sub-box");
+      return GPW_ERANGE;
+    }
+    (*work)[i] = make_int4(0, k | (int)(w[i].j << 4), (int)(sidx - lev[k].sub_base),
+                           (int)std::min<long long>(w[i].c, 1 << 30));
   }
   *nwork_out = (long long)w.size();
   return GPW_OK;
@@ -576,16 +634,20 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   std::vector<long long> psize;
   int rc = build_tasks(plan, pairs_view(pairs), H->hot_a, plan->tile, plan->lev, &H->sub_off_c,
                        &H->task_c, &H->work_c, &plan->nent, &plan->nwork, &plan->nsub_total,
-                       nullptr, nullptr);
+                       nullptr, nullptr, nullptr);
   if (rc) return rc;
   for (int k = 0; k < K; ++k) plan->lev_i[k] = plan->lev[k];
   for (int k = 0; k < K; ++k)
     for (int d = 0; d < 3; ++d)
       plan->lev_i[k].nsb[d] = (plan->lev[k].N[d] + plan->tile_i[d] - 1) / plan->tile_i[d];
   long long nsub_i = 0;
+  // integration chunks (auto): about four items per resident block of the whole launch,
+  // so that no sub-box with many tasks is left running alone at the end
+  long long chunk = -1;
   rc = build_tasks(plan, pairs_view(pairs), H->hot_a, plan->tile_i, plan->lev_i, &H->sub_off_i,
                    &H->task_i, &H->work_i, &plan->nent_i, &plan->nwork_i, &nsub_i, &ranks,
-                   &psize);
+                   &psize, &chunk);
+  plan->chunk_i = (int)chunk;
   if (rc) return rc;
   long long part_total = 0;
   for (long long p = 0; p < np; ++p) {
