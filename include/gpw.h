@@ -92,6 +92,10 @@ typedef struct {
   int tile_integ[3];          /* sub-box of one integration thread block;
                                  {0,0,0} = default {8,8,32}.  Supported shapes:
                                  gpw_tile_supported. */
+  int colloc_warps;           /* warps per collocation thread block: 4, 6 or 8; 0 = the
+                                 choice with the most resident warps per SM */
+  int integ_chunk;            /* most (pair, sub-box) tasks per integration work item
+                                 (> 0); 0 = default max(64, tasks / 1216) */
 } gpw_desc;
 
 /* Sizes and work counts of a plan (gpw_plan_query). */
@@ -112,6 +116,8 @@ typedef struct {
   int tile[3];         /* collocation sub-box */
   int tile_integ[3];   /* integration sub-box */
   long long nentries_integ;  /* tasks of the integration sub-box lists */
+  int colloc_warps;    /* warps per collocation block (0 until the plan is committed) */
+  int integ_chunk;     /* most tasks per integration work item */
 } gpw_plan_info;
 
 /* Build a plan: normalise primitives, screen pairs (Eq. cut; pairs a <= b over images T

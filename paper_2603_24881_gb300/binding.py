@@ -49,7 +49,8 @@ class Desc(ctypes.Structure):
                 ("level_ratio", ctypes.c_double), ("meshes", ctypes.c_void_p),
                 ("rel_cutoff", ctypes.c_double), ("tau", ctypes.c_double),
                 ("flags", ctypes.c_int), ("tile", ctypes.c_int * 3),
-                ("tile_integ", ctypes.c_int * 3)]
+                ("tile_integ", ctypes.c_int * 3), ("colloc_warps", ctypes.c_int),
+                ("integ_chunk", ctypes.c_int)]
 
 # sub-box shapes with compiled kernels (gpw_tile_supported): collocation, integration
 TILES = [(8, 8, 16), (4, 8, 32), (8, 8, 32), (4, 8, 64), (4, 8, 16), (4, 4, 16), (2, 8, 16),
@@ -69,7 +70,8 @@ class Info(ctypes.Structure):
                 ("device_bytes", ctypes.c_longlong), ("flops_rho", ctypes.c_double),
                 ("flops_mat", ctypes.c_double), ("flops_ip1", ctypes.c_double),
                 ("tile", ctypes.c_int * 3), ("tile_integ", ctypes.c_int * 3),
-                ("nentries_integ", ctypes.c_longlong)]
+                ("nentries_integ", ctypes.c_longlong), ("colloc_warps", ctypes.c_int),
+                ("integ_chunk", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -160,7 +162,8 @@ class Plan:
     """A libgpw plan for one cell (Sec. II / III A of the paper): screened pairs,
     levels, task lists, grids and FFT plans live on the current CUDA device."""
 
-    def __init__(self, system, stream=None, tile=None, tile_integ=None, commit=True):
+    def __init__(self, system, stream=None, tile=None, tile_integ=None, commit=True,
+                 colloc_warps=None, integ_chunk=None):
         """Prepare the plan on the host (screening, levels, task lists) and, unless
         commit=False, commit it to the current device.  An uncommitted plan reports its
         exact device footprint in stats()["device_bytes"]."""
@@ -200,6 +203,8 @@ class Plan:
         if tile_integ is not None:
             for i in range(3):
                 d.tile_integ[i] = int(tile_integ[i])
+        d.colloc_warps = int(colloc_warps or 0)
+        d.integ_chunk = int(integ_chunk or 0)
         h = ctypes.c_void_p()
         check(self._lib.gpw_plan_prepare(ctypes.byref(d), ctypes.byref(h)), "gpw_plan_prepare")
         self._h = h
@@ -254,7 +259,8 @@ class Plan:
                     flops_rho=i.flops_rho, flops_mat=i.flops_mat, flops_ip1=i.flops_ip1,
                     level_cutoff=[i.level_cutoff[k] for k in range(i.nlevels)],
                     tile=tuple(i.tile), tile_integ=tuple(i.tile_integ),
-                    nentries_integ=i.nentries_integ)
+                    nentries_integ=i.nentries_integ, colloc_warps=i.colloc_warps,
+                    integ_chunk=i.integ_chunk)
 
     def pair_table(self) -> np.ndarray:
         """Screened pairs as int64 rows (a, b, n0, n1, n2, level, lo0..2, hi0..2),

@@ -548,6 +548,8 @@ int gpw_plan_query(gpw_plan_t plan, gpw_plan_info* info) {
   info->tile[2] = P.tile[2];
   for (int d = 0; d < 3; ++d) info->tile_integ[d] = P.tile_i[d];
   info->nentries_integ = P.nent_i;
+  info->colloc_warps = P.committed ? P.nw_colloc : 0;
+  info->integ_chunk = P.chunk_i;
   return GPW_OK;
 }
 
@@ -755,7 +757,8 @@ int gpw_batch_set(gpw_batch_t b, int nplans, const gpw_plan_t* plans, void* stre
     }
     lmax = std::max(lmax, P.lmax);
   }
-  cudaError_t e = gpw::configure_batch(plans[0]->p.tile, plans[0]->p.tile_i, lmax, &b->colloc,
+  cudaError_t e = gpw::configure_batch(plans[0]->p.tile, plans[0]->p.tile_i, lmax,
+                                       plans[0]->p.nw_colloc_req, &b->colloc,
                                        &b->integ1);
   if (e != cudaSuccess) {
     set_error(std::string("gpw_batch_set: ") + cudaGetErrorString(e));
@@ -824,8 +827,13 @@ int gpw_batch_fock_grad_async(gpw_batch_t b, const double* const* D, double* con
     int rc = gpw::prep_rho(b->plans[i]->p, D[i], s);
     if (rc) return rc;
   }
+  // the batched grid passes are timed on the first plan's phase timers (gpw_profile)
   gpw::Plan& P0 = b->plans[0]->p;
-  cudaError_t e = gpw::launch_collocate_views(b->colloc, b->views, b->work_c, b->nwc, P0.d.tabs, s);
+  cudaError_t e;
+  {
+    gpw::Phase ph(P0, GPW_PHASE_COLLOCATE, s);
+    e = gpw::launch_collocate_views(b->colloc, b->views, b->work_c, b->nwc, P0.d.tabs, s);
+  }
   if (e != cudaSuccess) {
     set_error(std::string("batch collocation: ") + cudaGetErrorString(e));
     return GPW_ECUDA;
@@ -834,7 +842,10 @@ int gpw_batch_fock_grad_async(gpw_batch_t b, const double* const* D, double* con
     int rc = gpw::potential_from_levels(b->plans[i]->p, energies_dev + 2 * i, nullptr, nullptr, s);
     if (rc) return rc;
   }
-  e = gpw::launch_integrate_views(b->integ1, 1, b->views, b->work_i, b->nwi, P0.d.tabs, s);
+  {
+    gpw::Phase ph(P0, GPW_PHASE_INTEGRATE_IP1, s);
+    e = gpw::launch_integrate_views(b->integ1, 1, b->views, b->work_i, b->nwi, P0.d.tabs, s);
+  }
   if (e != cudaSuccess) {
     set_error(std::string("batch integration: ") + cudaGetErrorString(e));
     return GPW_ECUDA;

@@ -163,6 +163,7 @@ struct Plan {
   int red_blocks = 0;
   size_t smem_colloc = 0, smem_integ = 0, smem_integ1 = 0;
   int nw_colloc = 8, nw_integ = 8;     // warps per thread block
+  int nw_colloc_req = 0;               // requested collocation warps (0 = occupancy pick)
   int stg_colloc = 0, stg_integ = 0, stg_integ1 = 0;  // per-warp staging doubles
   // profiler: event pairs per phase, recorded on the calling stream when enabled
   bool prof = false;

@@ -1226,13 +1226,14 @@ size_t integ_smem(int stg) {
 // Warps per collocation block: the candidate with the most resident warps per SM, as the
 // occupancy calculator reports it for this shared-memory size (registers included).
 template <int T0, int T1, int T2>
-int pick_colloc_warps(int stg, int* nw_out, size_t* smem_out) {
+int pick_colloc_warps(int stg, int want, int* nw_out, size_t* smem_out) {
   int best = 0;
   const void* fns[3] = {(const void*)collocate_kernel<T0, T1, T2, 8>,
                         (const void*)collocate_kernel<T0, T1, T2, 6>,
                         (const void*)collocate_kernel<T0, T1, T2, 4>};
   const int nws[3] = {8, 6, 4};
   for (int i = 0; i < 3; ++i) {
+    if (want != 0 && nws[i] != want) continue;  // a requested count (still must fit)
     const size_t need = colloc_smem<T0, T1, T2>(stg, nws[i]);
     int blocks = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, fns[i], nws[i] * 32, need) != cudaSuccess)
@@ -1299,7 +1300,8 @@ cudaError_t configure_kernels(Plan* p) {
   if (p->tile[0] == a && p->tile[1] == b && p->tile[2] == c) {                      \
     found |= 1;                                                                     \
     p->stg_colloc = even(CollocLayout<a, b, c>::stage(lp));                         \
-    if (pick_colloc_warps<a, b, c>(p->stg_colloc, &p->nw_colloc, &p->smem_colloc) == 0) \
+    if (pick_colloc_warps<a, b, c>(p->stg_colloc, p->nw_colloc_req, &p->nw_colloc,         \
+                                   &p->smem_colloc) == 0)                                \
       return cudaErrorInvalidValue;                                                 \
   }
 #define GPW_TILE_CONF_I(a, b, c)                                                    \
@@ -1408,7 +1410,8 @@ cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s) {
 }
 
 // Launch shapes for a batch of plans with the same sub-boxes and largest degree lmax.
-cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, GridLaunch* colloc,
+cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int nw_req,
+                            GridLaunch* colloc,
                             GridLaunch* integ1) {
   int dev = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -1427,7 +1430,7 @@ cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, Grid
   if (tile_c[0] == a && tile_c[1] == b && tile_c[2] == c) {                                 \
     found |= 1;                                                                             \
     colloc->stg = even(CollocLayout<a, b, c>::stage(lmax + 1));                             \
-    if (pick_colloc_warps<a, b, c>(colloc->stg, &colloc->nw, &colloc->smem) == 0)          \
+    if (pick_colloc_warps<a, b, c>(colloc->stg, nw_req, &colloc->nw, &colloc->smem) == 0) \
       return cudaErrorInvalidValue;                                                         \
   }
 #define GPW_TILE_BCONF_I(a, b, c)                                                           \

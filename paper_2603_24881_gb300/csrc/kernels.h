@@ -23,7 +23,8 @@ cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views,
 cudaError_t launch_integrate_views(const GridLaunch& cfg, int lext, const PlanView* views,
                                    const int4* work, long long nwork, const CoefTables* tabs,
                                    cudaStream_t s);
-cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, GridLaunch* colloc,
+cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int nw_req,
+                            GridLaunch* colloc,
                             GridLaunch* integ1);
 
 cudaError_t launch_tables(const Plan& p, cudaStream_t s);

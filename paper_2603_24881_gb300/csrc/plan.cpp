@@ -365,6 +365,16 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     }
     for (int d = 0; d < 3; ++d) plan->tile_i[d] = desc->tile_integ[d];
   }
+  if (desc->colloc_warps != 0 && desc->colloc_warps != 4 && desc->colloc_warps != 6 &&
+      desc->colloc_warps != 8) {
+    set_error("gpw_plan: colloc_warps must be 0, 4, 6 or 8");
+    return GPW_EINVAL;
+  }
+  if (desc->integ_chunk < 0) {
+    set_error("gpw_plan: integ_chunk must be >= 0");
+    return GPW_EINVAL;
+  }
+  plan->nw_colloc_req = desc->colloc_warps;
   plan->natm = desc->natm;
   plan->nshell = desc->nshell;
   plan->coords.assign(desc->coords, desc->coords + 3 * desc->natm);
@@ -643,7 +653,7 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   long long nsub_i = 0;
   // integration chunks (auto): about four items per resident block of the whole launch,
   // so that no sub-box with many tasks is left running alone at the end
-  long long chunk = -1;
+  long long chunk = desc->integ_chunk > 0 ? desc->integ_chunk : -1;
   rc = build_tasks(plan, pairs_view(pairs), H->hot_a, plan->tile_i, plan->lev_i, &H->sub_off_i,
                    &H->task_i, &H->work_i, &plan->nent_i, &plan->nwork_i, &nsub_i, &ranks,
                    &psize, &chunk);

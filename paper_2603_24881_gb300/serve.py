@@ -74,19 +74,28 @@ class Server:
 
     hbm_budget: device bytes the plans and buffers of admitted requests may use at once
     (default: 70% of the free device memory at start).  max_batch: most requests per
-    batch.  streams: batches in flight.  host_workers: planning threads.
+    batch.  streams: batches in flight.  host_workers: planning threads.  tile,
+    tile_integ, colloc_warps, integ_chunk: launch shape of every plan (library defaults
+    if None); tune_with: a list of sample cells to run the autotuner on (as one batch)
+    instead, its choice (cached per GPU and workload class) then serves every request.
     """
 
     def __init__(self, hbm_budget: int | None = None, max_batch: int = 32, streams: int = 2,
                  host_workers: int | None = None, tile=None, tile_integ=None,
-                 fail_prepare=None):
+                 colloc_warps=None, integ_chunk=None, tune_with=None, fail_prepare=None):
         import torch
         self.torch = torch
         torch.cuda.init()
         free, _ = torch.cuda.mem_get_info()
         self.budget = int(hbm_budget if hbm_budget is not None else 0.7 * free)
         self.max_batch = int(max_batch)
-        self.tile, self.tile_integ = tile, tile_integ
+        self.plan_kwargs = dict(tile=tile, tile_integ=tile_integ, colloc_warps=colloc_warps,
+                                integ_chunk=integ_chunk)
+        self.choice = None
+        if tune_with:
+            from .autotune import tune
+            self.choice = tune(list(tune_with))
+            self.plan_kwargs = self.choice.plan_kwargs()
         self._fail_prepare = fail_prepare  # test hook: callable(system) -> bool
         self._pool = cf.ThreadPoolExecutor(host_workers or max(2, (os.cpu_count() or 4)))
         self._streams = [torch.cuda.Stream() for _ in range(max(1, streams))]
@@ -134,7 +143,7 @@ class Server:
         try:
             if self._fail_prepare and self._fail_prepare(req.system):
                 raise RuntimeError("plan preparation failed (injected)")
-            req.plan = Plan(req.system, tile=self.tile, tile_integ=self.tile_integ, commit=False)
+            req.plan = Plan(req.system, commit=False, **self.plan_kwargs)
             nao, natm = req.plan.nao, req.plan.natm
             req.bytes = int(req.plan.stats()["device_bytes"]) + 8 * (2 * nao * nao + 3 * natm + 2)
             if req.bytes > self.budget:
