@@ -28,7 +28,7 @@ def _nvcc() -> str:
 
 def _flags():
     return ARCH + ["-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-I", SRC,
-                   "-Xcompiler", "-fPIC,-ffp-contract=off,-O2", "--expt-relaxed-constexpr"]
+                   "-Xcompiler", "-fPIC,-ffp-contract=off,-O2,-fopenmp", "--expt-relaxed-constexpr"]
 
 
 def _stale(out, deps) -> bool:
@@ -66,7 +66,8 @@ def build(force: bool = False, verbose: bool = False) -> str:
             logs = list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + f".tmp{os.getpid()}"
-        run([nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcufft", "-lcudart"])
+        run([nvcc] + ARCH + ["-shared", "-Xcompiler", "-fopenmp", "-o", tmp] + objs +
+            ["-lcufft", "-lcudart"])
         os.replace(tmp, LIB)
     if verbose:
         for l in logs:

@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <omp.h>
+
 #include "gpw_internal.h"
 #include "plan_host.h"
 
@@ -132,6 +134,13 @@ struct PairBox {
   int level, lo[3], hi[3];
 };
 
+// Host threads for a loop over n items: all cores for large plans, one for small ones
+// (a server plans several small cells at once on its own threads).
+int plan_threads(long long n) {
+  if (n < 20000) return 1;
+  return std::max(1, std::min<int>(omp_get_max_threads(), (int)(n / 20000)));
+}
+
 std::vector<PairBox> pairs_view(const std::vector<PairTmp>& pairs) {
   std::vector<PairBox> v(pairs.size());
   for (size_t i = 0; i < pairs.size(); ++i) {
@@ -167,74 +176,106 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
     nsub += (long long)lev[k].nsb[0] * lev[k].nsb[1] * lev[k].nsb[2];
   }
   *nsub_out = nsub;
-  std::vector<long long> count(nsub + 1, 0);
-  std::vector<Seg> sg[3];
-  for (long long p = 0; p < np; ++p) {
-    const PairBox& t = pairs[p];
-    const LevelInfo& lv = lev[t.level];
-    for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
-    for (auto& s0 : sg[0])
-      for (auto& s1 : sg[1])
-        for (auto& s2 : sg[2])
-          count[lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j + 1]++;
+  // Threads take contiguous ranges of pairs; every thread counts its tasks per sub-box,
+  // the counts give each thread its first slot in every sub-box (threads in pair order),
+  // so the task order inside a sub-box is the pair order whatever the thread count.
+  const int nthr = plan_threads(np);
+  std::vector<std::vector<long long>> tslot(nthr);
+#pragma omp parallel num_threads(nthr)
+  {
+    const int th = omp_get_thread_num();
+    const long long p0 = np * th / nthr, p1 = np * (th + 1) / nthr;
+    std::vector<long long>& c = tslot[th];
+    c.assign(nsub, 0);
+    std::vector<Seg> sg[3];
+    for (long long p = p0; p < p1; ++p) {
+      const PairBox& t = pairs[p];
+      const LevelInfo& lv = lev[t.level];
+      for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
+      for (auto& s0 : sg[0])
+        for (auto& s1 : sg[1])
+          for (auto& s2 : sg[2])
+            c[lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j]++;
+    }
   }
-  for (long long i = 0; i < nsub; ++i) count[i + 1] += count[i];
+  std::vector<long long> count(nsub + 1, 0);
+  for (long long i = 0; i < nsub; ++i) {
+    long long run = count[i];
+    for (int th = 0; th < nthr; ++th) {
+      const long long c = tslot[th][i];
+      tslot[th][i] = run;
+      run += c;
+    }
+    count[i + 1] = run;
+  }
   const long long nent = count[nsub];
   *nent_out = nent;
   task->assign(2 * nent, make_int4(0, 0, 0, 0));
   if (ranks) ranks->assign(np, 0);
   if (psize) psize->assign(np, 0);
-  std::vector<long long> fill(count.begin(), count.end() - 1);
-  for (long long p = 0; p < np; ++p) {
-    const PairBox& t = pairs[p];
-    const LevelInfo& lv = lev[t.level];
-    for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
-    const int L = hot_a[p].w;
-    int n[3];
-    for (int d = 0; d < 3; ++d) {
-      n[d] = t.hi[d] - t.lo[d] + 1;
-      if (n[d] > 65535) {
-        set_error("gpw_plan: pair box longer than 65535 grid points");
-        return GPW_ERANGE;
+  int fail = GPW_OK;
+#pragma omp parallel num_threads(nthr)
+  {
+    const int th = omp_get_thread_num();
+    const long long p0 = np * th / nthr, p1 = np * (th + 1) / nthr;
+    std::vector<long long>& fill = tslot[th];
+    std::vector<Seg> sg[3];
+    for (long long p = p0; p < p1; ++p) {
+      const PairBox& t = pairs[p];
+      const LevelInfo& lv = lev[t.level];
+      for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
+      const int L = hot_a[p].w;
+      int n[3];
+      bool bad = false;
+      for (int d = 0; d < 3; ++d) {
+        n[d] = t.hi[d] - t.lo[d] + 1;
+        bad = bad || n[d] > 65535;
       }
-    }
-    int rank = 0;
-    const long long ns12 = (long long)sg[1].size() * sg[2].size();
-    const long long S = nc2(L + 1);
-    if (psize) {
-      (*psize)[p] = S * n[0] * ns12;
-      if ((*psize)[p] > INT32_MAX) {
-        set_error("gpw_plan: per-pair task block too large");
-        return GPW_ERANGE;
+      const long long ns12 = (long long)sg[1].size() * sg[2].size();
+      const long long S = nc2(L + 1);
+      if (psize) {
+        (*psize)[p] = S * n[0] * ns12;
+        bad = bad || (*psize)[p] > INT32_MAX;
       }
+      if (bad) {
+#pragma omp critical(gpw_plan_fail)
+        fail = GPW_ERANGE;
+        continue;
+      }
+      int rank = 0;
+      auto isect = [&](int d, const Seg& sgm, int* m, int* u, int* tt) {
+        long long s0 = (long long)sgm.j * T[d];
+        long long ext = std::min<long long>(T[d], lv.N[d] - s0);
+        long long o = (long long)sgm.k * lv.N[d] + s0;
+        long long a = std::max<long long>(t.lo[d], o);
+        long long b = std::min<long long>(t.hi[d], o + ext - 1);
+        *m = (int)(b - a + 1);
+        *u = (int)(a - o);
+        *tt = (int)(a - t.lo[d]);
+      };
+      for (auto& s0 : sg[0])
+        for (auto& s1 : sg[1])
+          for (auto& s2 : sg[2]) {
+            int m[3], u[3], tt[3];
+            isect(0, s0, &m[0], &u[0], &tt[0]);
+            isect(1, s1, &m[1], &u[1], &tt[1]);
+            isect(2, s2, &m[2], &u[2], &tt[2]);
+            long long sub = lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j;
+            long long slot = fill[sub]++;
+            (*task)[2 * slot] = make_int4((int)p, m[0] | (m[1] << 8) | (m[2] << 16) | (L << 24),
+                                          u[0] | (u[1] << 8) | (u[2] << 16), rank);
+            const long long woff = S * ((long long)tt[0] * ns12 + (rank % ns12) * m[0]);
+            (*task)[2 * slot + 1] = make_int4(tt[0] | (n[0] << 16), tt[1] | (n[1] << 16),
+                                              tt[2] | (n[2] << 16), psize ? (int)woff : 0);
+            ++rank;
+          }
+      if (ranks) (*ranks)[p] = rank;
     }
-    auto isect = [&](int d, const Seg& sgm, int* m, int* u, int* tt) {
-      long long s0 = (long long)sgm.j * T[d];
-      long long ext = std::min<long long>(T[d], lv.N[d] - s0);
-      long long o = (long long)sgm.k * lv.N[d] + s0;
-      long long a = std::max<long long>(t.lo[d], o);
-      long long b = std::min<long long>(t.hi[d], o + ext - 1);
-      *m = (int)(b - a + 1);
-      *u = (int)(a - o);
-      *tt = (int)(a - t.lo[d]);
-    };
-    for (auto& s0 : sg[0])
-      for (auto& s1 : sg[1])
-        for (auto& s2 : sg[2]) {
-          int m[3], u[3], tt[3];
-          isect(0, s0, &m[0], &u[0], &tt[0]);
-          isect(1, s1, &m[1], &u[1], &tt[1]);
-          isect(2, s2, &m[2], &u[2], &tt[2]);
-          long long sub = lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j;
-          long long slot = fill[sub]++;
-          (*task)[2 * slot] = make_int4((int)p, m[0] | (m[1] << 8) | (m[2] << 16) | (L << 24),
-                                        u[0] | (u[1] << 8) | (u[2] << 16), rank);
-          const long long woff = S * ((long long)tt[0] * ns12 + (rank % ns12) * m[0]);
-          (*task)[2 * slot + 1] = make_int4(tt[0] | (n[0] << 16), tt[1] | (n[1] << 16),
-                                            tt[2] | (n[2] << 16), psize ? (int)woff : 0);
-          ++rank;
-        }
-    if (ranks) (*ranks)[p] = rank;
+  }
+  if (fail != GPW_OK) {
+    set_error("gpw_plan: pair box longer than 65535 grid points or per-pair task block "
+              "too large");
+    return fail;
   }
   *sub_off = count;
   // work items {plan slot, level | chunk << 4, sub-box, tasks}: with chunk_io a sub-box
@@ -483,8 +524,13 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     atom_rmax[prims[i].atom] = std::max(atom_rmax[prims[i].atom], prims[i].rcut);
   }
   const double* X = desc->coords;
-  std::vector<PairTmp> pairs;
+  // atoms are screened in parallel (each thread keeps its own pair list); the sort
+  // below fixes one order whatever the thread count
+  const int sthr = plan_threads((long long)prims.size() * prims.size() / 64);
+  std::vector<std::vector<PairTmp>> tpairs(sthr);
+#pragma omp parallel for num_threads(sthr) schedule(dynamic, 1)
   for (int ia = 0; ia < natm; ++ia) {
+    std::vector<PairTmp>& pairs = tpairs[omp_get_thread_num()];
     if (atom_rmax[ia] < 0) continue;
     for (int ib = 0; ib < natm; ++ib) {
       if (atom_rmax[ib] < 0) continue;
@@ -550,6 +596,16 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
                 pairs.push_back(t);
               }
           }
+    }
+  }
+  std::vector<PairTmp> pairs;
+  {
+    size_t total = 0;
+    for (const auto& v : tpairs) total += v.size();
+    pairs.reserve(total);
+    for (auto& v : tpairs) {
+      pairs.insert(pairs.end(), v.begin(), v.end());
+      std::vector<PairTmp>().swap(v);
     }
   }
   // deterministic order: contracted shell pair, then primitives, then image
