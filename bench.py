@@ -238,6 +238,9 @@ def served_bench(nreq: int) -> dict:
         pois = [f.result() for f in futs]
         t_pois = max(r.t_done for r in pois) - t0
     lat = np.array([r.latency for r in pois])
+    plan_ms = np.array([r.t_prepared - r.t_submit for r in pois]) * 1e3
+    wait_ms = np.array([r.t_launch - r.t_prepared for r in pois]) * 1e3
+    run_ms = np.array([r.t_done - r.t_launch for r in pois]) * 1e3
     plain, t_plain = run_plain(systems, grads)
     plat = np.array([r.latency for r in plain])
     dE = max(max(abs(a.EH - b.EH), abs(a.Ex - b.Ex)) for a, b in zip(sat, plain))
@@ -252,6 +255,12 @@ def served_bench(nreq: int) -> dict:
             "plain_p50_ms": 1e3 * float(np.percentile(plat, 50)),
             "plain_p99_ms": 1e3 * float(np.percentile(plat, 99)),
             "speedup_vs_plain": t_plain / t_sat, "batches": st_sat["batches"],
+            "poisson_p50_ms_split": {"host_plan": float(np.percentile(plan_ms, 50)),
+                                     "admission_wait": float(np.percentile(wait_ms, 50)),
+                                     "gpu_batch_and_copy": float(np.percentile(run_ms, 50))},
+            "poisson_p99_ms_split": {"host_plan": float(np.percentile(plan_ms, 99)),
+                                     "admission_wait": float(np.percentile(wait_ms, 99)),
+                                     "gpu_batch_and_copy": float(np.percentile(run_ms, 99))},
             "max_abs_dE_Ha": dE, "max_rel_dV": dV, "max_abs_dgrad": dg,
             "stream": "water boxes n in {4,8,16,32,64,128}, p ~ 1/n, 10% gradients, seed 4"}
 

@@ -9,8 +9,8 @@ Layout
 * ``gpw_oracle.c`` (plain C, built by :func:`build`): screening, collocation,
   integration and the gradient contraction, point by point.
 * this module: primitive normalisation, multigrid meshes and level cutoffs,
-  the spectral steps (Fourier interpolation between levels, Poisson, LDA
-  exchange) written with numpy's FFT, and the assembly of V and the gradient.
+  the spectral steps (Fourier interpolation between levels, Poisson, LDA and
+  PBE exchange) written with numpy's FFT, and the assembly of V and the gradient.
 
 Readings of the paper that this oracle fixes (the CUDA path follows the same
 ones) are listed in the docstring of each function.
@@ -171,6 +171,41 @@ def gvectors(mesh, L):
 
 def _freq_index(mesh):
     return [np.fft.fftfreq(int(m), d=1.0 / int(m)).astype(np.int64) for m in mesh]
+
+
+# PBE exchange (Perdew, Burke, Ernzerhof 1996): enhancement factor
+# F_x(s) = 1 + kappa - kappa / (1 + mu s^2 / kappa), kappa = 0.804 (Lieb-Oxford bound
+# F_x <= 1.804), mu = beta pi^2 / 3 with beta = 0.06672455060314922.
+PBE_KAPPA = 0.804
+PBE_MU = 0.06672455060314922 * math.pi ** 2 / 3.0
+# below this density the exchange energy density and potential are set to zero
+GGA_RHO_MIN = 1e-12
+
+
+def pbe_x_point(rho, sigma):
+    """Spin-unpolarised PBE exchange at points: rho (>= 0 used), sigma = |grad rho|^2.
+    Returns (e, de/drho, de/dsigma) with e the energy per volume,
+    e = e_x^LDA(rho) F_x(s), e_x^LDA = -(3/4)(3/pi)^(1/3) rho^(4/3),
+    s^2 = sigma / (4 k_F^2 rho^2), k_F = (3 pi^2 rho)^(1/3)."""
+    rho = np.asarray(rho, dtype=np.float64)
+    sigma = np.asarray(sigma, dtype=np.float64)
+    ok = rho > GGA_RHO_MIN
+    r = np.where(ok, rho, 1.0)
+    cx = (3.0 / math.pi) ** (1.0 / 3.0)
+    r13 = np.cbrt(r)
+    elda = -0.75 * cx * r * r13            # e_x^LDA
+    delda = -cx * r13                      # d e_x^LDA / d rho
+    kf2 = (3.0 * math.pi ** 2 * r) ** (2.0 / 3.0)
+    ds2_dsigma = 1.0 / (4.0 * kf2 * r * r)
+    s2 = sigma * ds2_dsigma
+    den = 1.0 + PBE_MU * s2 / PBE_KAPPA
+    F = 1.0 + PBE_KAPPA - PBE_KAPPA / den
+    dF = PBE_MU / (den * den)              # dF / d(s^2)
+    e = elda * F
+    dedr = delda * F + elda * dF * (-8.0 / 3.0) * s2 / r
+    deds = elda * dF * ds2_dsigma
+    z = np.zeros_like(e)
+    return np.where(ok, e, z), np.where(ok, dedr, z), np.where(ok, deds, z)
 
 
 # ---------------------------------------------------------------- plan -----
@@ -344,6 +379,44 @@ class Plan:
         omega = float(np.prod(self.L))
         return vx, omega / float(np.prod(self.meshes[0])) * float(np.sum(ex))
 
+    def _deriv(self, spec, d):
+        """Fourier derivative along axis d of a full (numpy-order) spectrum: i G_d spec,
+        with the Nyquist plane of an even axis set to zero (a reading: the derivative of
+        a real field stays real)."""
+        mesh = tuple(int(m) for m in self.meshes[0])
+        f = np.fft.fftfreq(mesh[d], d=1.0 / mesh[d])
+        g = 2.0 * np.pi * f / self.L[d]
+        if mesh[d] % 2 == 0:
+            g[mesh[d] // 2] = 0.0
+        shape = [1, 1, 1]
+        shape[d] = mesh[d]
+        return spec * (1j * g).reshape(shape)
+
+    def pbe_x(self, rho_fine):
+        """GGA exchange (Sec. II, GGA; PBE exchange): the density gradient from the
+        Fourier derivative of rho (grad rho = F^-1(i G rho~)), e and its derivatives at
+        every point (pbe_x_point with rho+ = max(rho, 0)), and the potential
+        v = de/drho - div(2 de/dsigma grad rho), the divergence again a Fourier
+        derivative (the integration by parts that folds the GGA term into the local
+        potential).  E_x = (Omega/N) sum_r e.  Returns (v_x, E_x)."""
+        rs = np.fft.fftn(rho_fine)
+        grad = [np.real(np.fft.ifftn(self._deriv(rs, d))) for d in range(3)]
+        sigma = grad[0] ** 2 + grad[1] ** 2 + grad[2] ** 2
+        e, dedr, deds = pbe_x_point(np.maximum(rho_fine, 0.0), sigma)
+        div = np.zeros_like(rho_fine)
+        for d in range(3):
+            div += np.real(np.fft.ifftn(self._deriv(np.fft.fftn(2.0 * deds * grad[d]), d)))
+        omega = float(np.prod(self.L))
+        return dedr - div, omega / float(np.prod(self.meshes[0])) * float(np.sum(e))
+
+    def xc(self, rho_fine, xc: str = "lda_x"):
+        """Exchange potential and energy of the named functional ("lda_x", "pbe_x")."""
+        if xc == "lda_x":
+            return self.lda_x(rho_fine)
+        if xc == "pbe_x":
+            return self.pbe_x(rho_fine)
+        raise ValueError(f"unknown functional {xc!r}")
+
     # -------------------------------------------------- eval_mat (Alg. 2) --
     def _pair_blocks(self, v_levels, grad_D=None, sel=None, nthreads: int = 0):
         lib = _lib()
@@ -421,21 +494,21 @@ class Plan:
         return g
 
     # -------------------------------------------------- whole build ---------
-    def fock(self, D, nthreads: int = 0):
-        """One Fock build: rho -> combine -> Poisson + LDA-x -> restrict -> V.
-        Returns dict(V, EH, Ex, rho_fine, v_fine, v_levels)."""
+    def fock(self, D, nthreads: int = 0, xc: str = "lda_x"):
+        """One Fock build: rho -> combine -> Poisson + exchange (LDA or PBE) -> restrict
+        -> V.  Returns dict(V, EH, Ex, rho_fine, v_fine, v_levels)."""
         rl = self.rho_levels(D, nthreads=nthreads)
         rho = self.combine(rl)
         vH, EH = self.poisson(rho)
-        vx, Ex = self.lda_x(rho)
+        vx, Ex = self.xc(rho, xc)
         v = vH + vx
         vl = self.restrict(v)
         V = self.mat_levels(vl, nthreads=nthreads)
         return dict(V=V, EH=EH, Ex=Ex, rho_fine=rho, v_fine=v, v_levels=vl, rho_levels=rl)
 
-    def energy(self, D, nthreads: int = 0) -> float:
+    def energy(self, D, nthreads: int = 0, xc: str = "lda_x") -> float:
         rho = self.combine(self.rho_levels(D, nthreads=nthreads))
-        return self.poisson(rho)[1] + self.lda_x(rho)[1]
+        return self.poisson(rho)[1] + self.xc(rho, xc)[1]
 
     def with_coords(self, coords):
         """Frozen plan at new atom positions: same pairs, images, levels and boxes;

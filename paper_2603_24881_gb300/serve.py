@@ -40,6 +40,8 @@ class Result:
     t_done: float
     batch: int
     batch_size: int
+    t_prepared: float = 0.0  # host planning finished
+    t_launch: float = 0.0    # its batch was enqueued on the GPU
 
     @property
     def latency(self) -> float:
@@ -56,6 +58,8 @@ class _Req:
     plan: Plan | None = None
     bytes: int = 0
     error: BaseException | None = None
+    t_prepared: float = 0.0
+    t_launch: float = 0.0
 
 
 @dataclass
@@ -150,6 +154,7 @@ class Server:
                 raise MemoryError(f"request needs {req.bytes} device bytes, budget is {self.budget}")
         except BaseException as ex:  # the request fails alone; the server keeps serving
             req.error = ex
+        req.t_prepared = time.perf_counter()
         with self._cv:
             self._ready.append(req)
             self._cv.notify_all()
@@ -177,6 +182,9 @@ class Server:
         stream = self._streams[slot]
         batch = self._batches[slot]
         bufs = dict(D=[], V=[], g=[], E=None)
+        t = time.perf_counter()
+        for r in reqs:
+            r.t_launch = t
         with torch.cuda.stream(stream):
             for r in reqs:
                 r.plan.commit(stream)
@@ -203,7 +211,7 @@ class Server:
             V = fl.bufs["V"][i].cpu().numpy()
             g = fl.bufs["g"][i].cpu().numpy() if fl.bufs["g"][i] is not None else None
             res = Result(r.rid, float(E[2 * i]), float(E[2 * i + 1]), V, g, r.t_submit, t,
-                         fl.bid, len(fl.reqs))
+                         fl.bid, len(fl.reqs), r.t_prepared, r.t_launch)
             r.plan.close()
             r.plan = None
             r.future.set_result(res)

@@ -15,6 +15,10 @@ pin here is a closed form, a brute-force evaluation, an identity or an invarianc
 * Hartree energy of one Gaussian charge against the analytic G sum and the
   Ewald-corrected isolated self-energy (Eqs. vH, vHG);
 * LDA exchange of a uniform density against Dirac's -(3/4 pi) k_F per electron;
+* PBE exchange (GGA): Dirac exchange for a uniform density, the enhancement factor's
+  limits (1, the Lieb-Oxford 1.804, the gradient-expansion coefficient), the potential
+  as the functional derivative through the Fourier gradient and divergence, and exact
+  uniform-scaling of exchange (E[l^3 rho(l r)] = l E[rho]);
 * gradient contraction (Algorithm 3) against central finite differences;
 * invariance under lattice translations and whole-grid shifts.
 """
@@ -318,3 +322,106 @@ def test_mat_block_matches_full(res):
         blk = p.mat_block(vl, sa, sb)
         ref = V[off[sa]:off[sa + 1], off[sb]:off[sb + 1]]
         assert np.max(np.abs(blk - ref)) < 1e-13 * max(1.0, np.max(np.abs(V)))
+
+
+# ---------------------------------------------------------------- GGA (PBE exchange) --
+
+def _smooth_density(p, seed=5, floor=0.02):
+    """A positive, band-limited density on the finest mesh (random Fourier components
+    inside half the cutoff sphere plus a constant)."""
+    mesh = tuple(int(m) for m in p.meshes[0])
+    rng = np.random.default_rng(seed)
+    g2 = oracle.gvectors(mesh, p.L)
+    spec = (rng.standard_normal(mesh) + 1j * rng.standard_normal(mesh)) * (g2 < 0.25 * p.G[0] ** 2)
+    f = np.real(np.fft.ifftn(spec))
+    f = f / np.max(np.abs(f))
+    return floor + 0.01 * (1.0 + f), spec
+
+
+def test_pbe_x_uniform_density_is_dirac_exchange():
+    s = systems.resolved()
+    p = oracle.Plan(s)
+    c = 0.0123
+    rho = np.full(tuple(p.meshes[0]), c)
+    vx, Ex = p.pbe_x(rho)
+    omega = float(np.prod(np.diag(s.lattice)))
+    kF = (3 * math.pi ** 2 * c) ** (1.0 / 3.0)
+    assert Ex == pytest.approx(-(3.0 / (4 * math.pi)) * kF * c * omega, rel=1e-13)
+    assert np.allclose(vx, -kF / math.pi, rtol=1e-13, atol=0)  # v_x = -k_F/pi
+    vl, El = p.lda_x(rho)
+    assert Ex == pytest.approx(El, rel=1e-14)
+
+
+def test_pbe_x_enhancement_factor_limits():
+    # F_x(0) = 1, F_x -> 1 + kappa = 1.804 (Lieb-Oxford bound) for s -> infinity,
+    # F_x = 1 + mu s^2 + O(s^4) with mu = beta pi^2/3 = 0.21951 (gradient expansion)
+    rho = 0.3
+    kf = (3 * math.pi ** 2 * rho) ** (1.0 / 3.0)
+    elda = -(3.0 / (4 * math.pi)) * kf * rho
+    for s_val, ref, tol in [(0.0, 1.0, 1e-15), (1e6, 1.804, 1e-9)]:
+        sigma = (s_val * 2 * kf * rho) ** 2
+        e, _, _ = oracle.pbe_x_point(rho, sigma)
+        assert float(e) / elda == pytest.approx(ref, rel=tol)
+    s_small = 1e-4
+    e, _, _ = oracle.pbe_x_point(rho, (s_small * 2 * kf * rho) ** 2)
+    assert (float(e) / elda - 1.0) / s_small ** 2 == pytest.approx(0.2195149727645171, rel=1e-6)
+
+
+def test_pbe_x_potential_is_functional_derivative():
+    # (E[rho + h d] - E[rho - h d]) / 2h = (Omega/N) sum_r v(r) d(r), through the Fourier
+    # gradient and divergence
+    s = systems.resolved()
+    p = oracle.Plan(s)
+    rho, _ = _smooth_density(p)
+    dlt, _ = _smooth_density(p, seed=9, floor=0.0)
+    dlt -= dlt.mean()
+    v, E = p.pbe_x(rho)
+    h = 1e-4  # central differences converge as h^2 (1e-2: 2.5e-6, 1e-3: 2.5e-8 relative)
+    fd = (p.pbe_x(rho + h * dlt)[1] - p.pbe_x(rho - h * dlt)[1]) / (2 * h)
+    omega = float(np.prod(np.diag(s.lattice)))
+    assert fd == pytest.approx(omega / rho.size * float(np.sum(v * dlt)), rel=1e-8)
+    # and the gradient term matters: PBE differs from LDA for this density
+    assert abs(E - p.lda_x(rho)[1]) > 1e-3 * abs(E)
+
+
+def test_pbe_x_uniform_scaling():
+    # exchange under uniform scaling rho_l(r) = l^3 rho(l r): E_x[rho_l] = l E_x[rho],
+    # v_l(r) = l v(l r) (a cell shrunk by l with the same mesh samples l^3 rho)
+    import copy
+    s = systems.resolved()
+    p = oracle.Plan(s)
+    rho, _ = _smooth_density(p)
+    v, E = p.pbe_x(rho)
+    lam = 1.7
+    q = copy.copy(p)
+    q.L = p.L / lam
+    vq, Eq = q.pbe_x(lam ** 3 * rho)
+    assert Eq == pytest.approx(lam * E, rel=1e-12)
+    assert np.max(np.abs(vq - lam * v)) <= 1e-12 * np.max(np.abs(lam * v))
+
+
+@pytest.mark.parametrize("xc", ["pbe_x"])
+def test_energy_derivative_wrt_density_matrix_is_V_gga(res, xc):
+    s, p = res
+    out = p.fock(s.D, xc=xc)
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal(s.D.shape)
+    X = X + X.T
+    h = 1e-5
+    fd = (p.energy(s.D + h * X, xc=xc) - p.energy(s.D - h * X, xc=xc)) / (2 * h)
+    assert fd == pytest.approx(float(np.sum(X * out["V"])), rel=1e-7)
+
+
+def test_energy_gradient_matches_finite_differences_gga(res):
+    s, p = res
+    out = p.fock(s.D, xc="pbe_x")
+    g = p.grad_levels(s.D, out["v_levels"])
+    h = 1e-4
+    for atom, d in [(0, 2), (1, 1)]:
+        cp = s.coords.copy()
+        cm = s.coords.copy()
+        cp[atom, d] += h
+        cm[atom, d] -= h
+        fd = (p.with_coords(cp).energy(s.D, xc="pbe_x") -
+              p.with_coords(cm).energy(s.D, xc="pbe_x")) / (2 * h)
+        assert g[atom, d] == pytest.approx(fd, rel=1e-6, abs=1e-7)
