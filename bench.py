@@ -86,6 +86,8 @@ def _args():
                     help="also run the served request stream with this many requests")
     ap.add_argument("--tile", default=None, help="collocation sub-box t0,t1,t2")
     ap.add_argument("--tile-integ", default=None, help="integration sub-box t0,t1,t2")
+    ap.add_argument("--xc", default="lda_x", choices=["lda_x", "pbe_x"],
+                    help="exchange functional (LDA Slater or PBE exchange, a GGA)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the launch shape with the autotuner (cached per GPU/workload)")
     return ap.parse_args()
@@ -294,7 +296,7 @@ def main():
     if a.autotune:
         from paper_2603_24881_gb300.autotune import tune
         shape = tune(s).plan_kwargs()
-    plan = gpw.Plan(s, **shape)
+    plan = gpw.Plan(s, xc=a.xc, **shape)
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0)
     st = plan.stats()
@@ -397,6 +399,7 @@ def main():
                            "tile": list(st["tile"]), "tile_integ": list(st["tile_integ"]),
                            "colloc_warps": st["colloc_warps"], "integ_chunk": st["integ_chunk"],
                            "launch_shape": "autotuned" if a.autotune else "library defaults",
+                           "xc": a.xc,
                            "parallelism": f"replicas x{world}"},
                 "pct_of_fp64_peak": 100.0 * value / world / FP64_PEAK_TFLOPS,
                 "pair_points_per_s": st["pair_points"] * a.steps * world / (ms * 1e-3),

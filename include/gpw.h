@@ -61,6 +61,18 @@ extern "C" {
 /* Flags for gpw_desc.flags */
 #define GPW_STRICT 0            /* default: the truncation definition of the paper */
 
+/* Exchange functional (gpw_desc.xc), spin-unpolarised, on the finest grid:
+ * GPW_XC_LDA_X  Slater exchange v_x = -(3/pi)^(1/3) rho^(1/3) (Sec. II, LDA);
+ * GPW_XC_PBE_X  PBE exchange, a GGA (Sec. II, GGA): grad rho = F^-1(i G rho~(G)),
+ *               e = e_x^LDA(rho) F_x(s), F_x = 1 + kappa - kappa/(1 + mu s^2/kappa),
+ *               s = |grad rho| / (2 (3 pi^2)^(1/3) rho^(4/3)), kappa = 0.804,
+ *               mu = 0.21951; the potential de/drho - div(de/d grad rho) with the
+ *               divergence as F^-1(i G . F(.)) (the integration by parts that folds the
+ *               GGA term into the local potential).  Derivatives take the Nyquist plane
+ *               of an even mesh axis as zero; e = 0 where rho <= 1e-12. */
+#define GPW_XC_LDA_X 0
+#define GPW_XC_PBE_X 1
+
 typedef struct gpw_plan_s* gpw_plan_t;
 typedef struct gpw_batch_s* gpw_batch_t;
 
@@ -96,6 +108,7 @@ typedef struct {
                                  choice with the most resident warps per SM */
   int integ_chunk;            /* most (pair, sub-box) tasks per integration work item
                                  (> 0); 0 = default max(64, tasks / 1216) */
+  int xc;                     /* GPW_XC_LDA_X (0, default) or GPW_XC_PBE_X */
 } gpw_desc;
 
 /* Sizes and work counts of a plan (gpw_plan_query). */
@@ -118,6 +131,7 @@ typedef struct {
   long long nentries_integ;  /* tasks of the integration sub-box lists */
   int colloc_warps;    /* warps per collocation block (0 until the plan is committed) */
   int integ_chunk;     /* most tasks per integration work item */
+  int xc;              /* exchange functional (GPW_XC_*) */
 } gpw_plan_info;
 
 /* Build a plan: normalise primitives, screen pairs (Eq. cut; pairs a <= b over images T

@@ -50,7 +50,10 @@ class Desc(ctypes.Structure):
                 ("rel_cutoff", ctypes.c_double), ("tau", ctypes.c_double),
                 ("flags", ctypes.c_int), ("tile", ctypes.c_int * 3),
                 ("tile_integ", ctypes.c_int * 3), ("colloc_warps", ctypes.c_int),
-                ("integ_chunk", ctypes.c_int)]
+                ("integ_chunk", ctypes.c_int), ("xc", ctypes.c_int)]
+
+# exchange functionals (gpw_desc.xc)
+XC = {"lda_x": 0, "pbe_x": 1}
 
 # sub-box shapes with compiled kernels (gpw_tile_supported): collocation, integration
 TILES = [(8, 8, 16), (4, 8, 32), (8, 8, 32), (4, 8, 64), (4, 8, 16), (4, 4, 16), (2, 8, 16),
@@ -71,7 +74,7 @@ class Info(ctypes.Structure):
                 ("flops_mat", ctypes.c_double), ("flops_ip1", ctypes.c_double),
                 ("tile", ctypes.c_int * 3), ("tile_integ", ctypes.c_int * 3),
                 ("nentries_integ", ctypes.c_longlong), ("colloc_warps", ctypes.c_int),
-                ("integ_chunk", ctypes.c_int)]
+                ("integ_chunk", ctypes.c_int), ("xc", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -163,10 +166,12 @@ class Plan:
     levels, task lists, grids and FFT plans live on the current CUDA device."""
 
     def __init__(self, system, stream=None, tile=None, tile_integ=None, commit=True,
-                 colloc_warps=None, integ_chunk=None):
+                 colloc_warps=None, integ_chunk=None, xc="lda_x"):
         """Prepare the plan on the host (screening, levels, task lists) and, unless
         commit=False, commit it to the current device.  An uncommitted plan reports its
-        exact device footprint in stats()["device_bytes"]."""
+        exact device footprint in stats()["device_bytes"].  tile, tile_integ,
+        colloc_warps, integ_chunk: launch shape (library defaults if None); xc: exchange
+        functional, "lda_x" (Slater) or "pbe_x" (PBE exchange, a GGA)."""
         self._lib = load()
         s = system
         self.system = s
@@ -205,6 +210,9 @@ class Plan:
                 d.tile_integ[i] = int(tile_integ[i])
         d.colloc_warps = int(colloc_warps or 0)
         d.integ_chunk = int(integ_chunk or 0)
+        if xc not in XC:
+            raise ValueError(f"unknown exchange functional {xc!r} (one of {sorted(XC)})")
+        d.xc = XC[xc]
         h = ctypes.c_void_p()
         check(self._lib.gpw_plan_prepare(ctypes.byref(d), ctypes.byref(h)), "gpw_plan_prepare")
         self._h = h
@@ -260,7 +268,8 @@ class Plan:
                     level_cutoff=[i.level_cutoff[k] for k in range(i.nlevels)],
                     tile=tuple(i.tile), tile_integ=tuple(i.tile_integ),
                     nentries_integ=i.nentries_integ, colloc_warps=i.colloc_warps,
-                    integ_chunk=i.integ_chunk)
+                    integ_chunk=i.integ_chunk,
+                    xc={v: k for k, v in XC.items()}.get(i.xc, i.xc))
 
     def pair_table(self) -> np.ndarray:
         """Screened pairs as int64 rows (a, b, n0, n1, n2, level, lo0..2, hi0..2),

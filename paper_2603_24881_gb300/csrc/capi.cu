@@ -78,7 +78,8 @@ void free_plan(Plan* P) {
   void* ptrs[] = {d.hot_a, d.hot_b, d.ids, d.ids2, d.geo, d.cab, d.pref, d.tab_off,
                   d.coef_off, d.part_off, d.xt_off, d.task_c, d.sub_off_c, d.work_c, d.task_i, d.sub_off_i, d.work_i, d.groups, d.atom_off,
                   d.atom_list, d.tab, d.coef, d.part, d.pgrad, d.grids, d.spec, d.fspec,
-                  d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs, d.view, d.g2tab};
+                  d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs, d.view, d.g2tab,
+                  d.g1tab, d.grad3, d.fspec3};
   for (void* q : ptrs)
     if (q) cudaFree(q);
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
@@ -109,7 +110,9 @@ long long estimate_bytes(const Plan& P, const HostArrays& H) {
   b += sz(P.tab_total + P.coef_total + P.part_total + 6 * P.npairs + P.grid_total, sizeof(double));
   b += sz(P.spec_total + 2 * P.fine_spec_n, sizeof(cufftDoubleComplex));
   b += sz(2 * P.fine_n + 2 * 304 + 2, sizeof(double)) + sizeof(int) + sizeof(CoefTables) + sizeof(PlanView);
-  b += sz((long long)P.lev[0].N[0] + P.lev[0].N[1] + P.lev[0].N[2], sizeof(double));
+  b += 2 * sz((long long)P.lev[0].N[0] + P.lev[0].N[1] + P.lev[0].N[2], sizeof(double));
+  if (P.xc == GPW_XC_PBE_X)
+    b += sz(3 * P.fine_n, sizeof(double)) + sz(P.fine_spec_n, sizeof(cufftDoubleComplex));
   for (int k = 0; k < P.nlev; ++k) {
     size_t ws = 0;
     if (cufftEstimate3d(P.lev[k].N[0], P.lev[k].N[1], P.lev[k].N[2], CUFFT_D2Z, &ws) == CUFFT_SUCCESS)
@@ -170,6 +173,19 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
         g2[o++] = g * g;
       }
     GPW_TRY(upload(&d.g2tab, g2, &b));
+    // signed (2 pi s)/L_d for the Fourier derivative, 0 on an even axis' Nyquist plane
+    std::vector<double> g1(g2.size());
+    o = 0;
+    for (int dd = 0; dd < 3; ++dd)
+      for (int m = 0; m < f.N[dd]; ++m) {
+        const int sf = m < (f.N[dd] + 1) / 2 ? m : m - f.N[dd];
+        g1[o++] = (f.N[dd] % 2 == 0 && 2 * m == f.N[dd]) ? 0.0 : 2.0 * M_PI * (double)sf / P->L[dd];
+      }
+    GPW_TRY(upload(&d.g1tab, g1, &b));
+  }
+  if (P->xc == GPW_XC_PBE_X) {
+    GPW_TRY(dalloc(&d.grad3, 3 * P->fine_n, &b));
+    GPW_TRY(dalloc(&d.fspec3, P->fine_spec_n, &b));
   }
   GPW_TRY(dalloc(&d.energies, 2, &b));
   GPW_TRY(dalloc(&d.err, 1, &b));
@@ -373,6 +389,38 @@ int ip1_from_grids(Plan& P, const double* D, double* grad, cudaStream_t s) {
 // rho -> interpolation -> Poisson + exchange -> restricted level potentials in P.d.grids;
 // energies to energies_dev.  Without v_out the Hartree part stays in G space: each level
 // spectrum is mask_k (FFT(v_x)/N + 4 pi S/G^2), one finest-grid C2R fewer.
+// GGA exchange (GPW_XC_PBE_X) after rho(r) is on the finest grid, with fspec = S(G):
+//   grad_d rho = F^-1(i G_d S); fspec <- v_H(G); e, de/drho, w = 2 de/dsigma grad rho;
+//   fa = F(de/drho) - sum_d i G_d F(w_d) (unnormalised), fb = v_H(G): each level keeps
+//   fa/N + fb inside its sphere.  Three more inverse and three more forward transforms
+//   of the finest grid than LDA exchange.
+int gga_potential(Plan& P, const double* rho, double* energies_dev, double* v_out,
+                  cudaStream_t s) {
+  int rc;
+  const long long n = P.fine_n;
+  for (int d = 0; d < 3; ++d) {
+    GPW_CK(launch_fourier_deriv(P, d, P.d.fspec, P.d.fspec2, false, s));
+    if ((rc = fft_z2d(P, 0, P.d.fspec2, P.d.grad3 + d * n, s))) return rc;
+  }
+  GPW_CK(launch_poisson(P, s));  // fspec <- 4 pi S / G^2, E_H
+  GPW_CK(launch_pbe_x(P, rho, P.d.grad3, P.d.fine_a, s));
+  GPW_CK(launch_energy_final(P, 0, kRedBlocks, s));
+  GPW_CK(launch_energy_final(P, 1, kRedBlocks, s));
+  if (energies_dev != P.d.energies)
+    GPW_CK(cudaMemcpyAsync(energies_dev, P.d.energies, 2 * sizeof(double),
+                           cudaMemcpyDeviceToDevice, s));
+  if ((rc = fft_d2z(P, 0, P.d.fine_a, P.d.fspec2, s))) return rc;  // F(de/drho)
+  for (int d = 0; d < 3; ++d) {
+    if ((rc = fft_d2z(P, 0, P.d.grad3 + d * n, P.d.fspec3, s))) return rc;
+    GPW_CK(launch_fourier_deriv(P, d, P.d.fspec3, P.d.fspec2, true, s));  // -= i G_d F(w_d)
+  }
+  if (v_out) {
+    GPW_CK(launch_spec_combine(P, P.d.fspec2, P.d.fspec, P.d.fspec3, s));
+    if ((rc = fft_z2d(P, 0, P.d.fspec3, v_out, s))) return rc;
+  }
+  return restrict_spectra(P, P.d.fspec2, P.d.fspec, s);
+}
+
 int potential_from_levels(Plan& P, double* energies_dev, double* rho_out, double* v_out,
                           cudaStream_t s) {
   int rc = combine(P, s);
@@ -382,6 +430,7 @@ int potential_from_levels(Plan& P, double* energies_dev, double* rho_out, double
   GPW_CK(cudaMemcpyAsync(P.d.fspec2, P.d.fspec, sizeof(cufftDoubleComplex) * (size_t)P.fine_spec_n,
                          cudaMemcpyDeviceToDevice, s));
   if ((rc = fft_z2d(P, 0, P.d.fspec2, rho, s))) return rc;
+  if (P.xc == GPW_XC_PBE_X) return gga_potential(P, rho, energies_dev, v_out, s);
   GPW_CK(launch_poisson(P, s));  // fspec <- 4 pi S / G^2, E_H
   if (v_out) {
     GPW_CK(cudaMemcpyAsync(P.d.fspec2, P.d.fspec,
@@ -550,6 +599,7 @@ int gpw_plan_query(gpw_plan_t plan, gpw_plan_info* info) {
   info->nentries_integ = P.nent_i;
   info->colloc_warps = P.committed ? P.nw_colloc : 0;
   info->integ_chunk = P.chunk_i;
+  info->xc = P.xc;
   return GPW_OK;
 }
 

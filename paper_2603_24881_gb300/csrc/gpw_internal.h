@@ -119,6 +119,9 @@ struct DeviceArrays {
   double* fine_b = nullptr;
   double* red = nullptr;      // reduction partials
   double* g2tab = nullptr;    // ((2 pi s)/L_d)^2 per finest-mesh index along each axis
+  double* g1tab = nullptr;    // (2 pi s)/L_d, 0 on the Nyquist plane of an even axis
+  double* grad3 = nullptr;    // GGA: three finest real grids (grad rho, then de/d grad rho)
+  cufftDoubleComplex* fspec3 = nullptr;  // GGA: finest half spectrum (work)
   double* energies = nullptr; // E_H, E_x (device)
   int* err = nullptr;         // device error word
   CoefTables* tabs = nullptr;
@@ -164,6 +167,7 @@ struct Plan {
   size_t smem_colloc = 0, smem_integ = 0, smem_integ1 = 0;
   int nw_colloc = 8, nw_integ = 8;     // warps per thread block
   int nw_colloc_req = 0;               // requested collocation warps (0 = occupancy pick)
+  int xc = GPW_XC_LDA_X;               // exchange functional
   int stg_colloc = 0, stg_integ = 0, stg_integ1 = 0;  // per-warp staging doubles
   // profiler: event pairs per phase, recorded on the calling stream when enabled
   bool prof = false;

@@ -1195,6 +1195,97 @@ __global__ void lda_kernel(long long n, double wgt, const double* __restrict__ r
   if (threadIdx.x == 0) red[blockIdx.x] = wgt * s;
 }
 
+// Fourier derivative on the finest half spectrum (Sec. II, GGA): out = i G_d in, or
+// out -= i G_d in (subtract).  G_d = (2 pi s)/L_d from a host table that is zero on the
+// Nyquist plane of an even axis.
+__global__ void fourier_deriv_kernel(const KLevels K, const double* __restrict__ g1t, int axis,
+                                     const cufftDoubleComplex* __restrict__ in,
+                                     cufftDoubleComplex* __restrict__ out, int subtract) {
+  const LevelInfo& f = K.lv[0];
+  const int h2 = f.N[2] / 2 + 1;
+  const long long total = (long long)f.N[0] * f.N[1] * h2;
+  const int off = axis == 0 ? 0 : (axis == 1 ? f.N[0] : f.N[0] + f.N[1]);
+  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (long long)gridDim.x * blockDim.x) {
+    const int m2 = (int)(idx % h2);
+    const long long r = idx / h2;
+    const int m1 = (int)(r % f.N[1]);
+    const int m0 = (int)(r / f.N[1]);
+    const int m = axis == 0 ? m0 : (axis == 1 ? m1 : m2);
+    const double g = __ldg(g1t + off + m);
+    const cufftDoubleComplex z = in[idx];
+    if (subtract) {
+      cufftDoubleComplex o = out[idx];
+      o.x += g * z.y;
+      o.y -= g * z.x;
+      out[idx] = o;
+    } else {
+      cufftDoubleComplex o;
+      o.x = -g * z.y;
+      o.y = g * z.x;
+      out[idx] = o;
+    }
+  }
+}
+
+// PBE exchange at every finest-grid point (spin-unpolarised, rho+ = max(rho, 0)):
+//   e = e_x^LDA F_x(s), e_x^LDA = -(3/4)(3/pi)^(1/3) rho^(4/3),
+//   s^2 = sigma / (4 k_F^2 rho^2), k_F^2 = (3 pi^2 rho)^(2/3), sigma = |grad rho|^2,
+//   F_x = 1 + kappa - kappa / (1 + mu s^2 / kappa),
+// writes de/drho to v_rho and 2 de/dsigma grad rho over grad (in place); e = 0 where
+// rho <= 1e-12.  Per-block partial sums of (Omega/N) e.
+__global__ void pbe_x_kernel(long long n, double wgt, const double* __restrict__ rho,
+                             double* __restrict__ gx, double* __restrict__ gy,
+                             double* __restrict__ gz, double* __restrict__ v_rho,
+                             double* __restrict__ red) {
+  __shared__ double sh[kRedThreads];
+  const double cx = 0.98474502184269641;        // (3/pi)^(1/3)
+  const double three_pi2 = 29.608813203268074;  // 3 pi^2
+  const double kappa = 0.804, mu = 0.21951497276451704;
+  double part = 0.0;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const double r = fmax(rho[i], 0.0);
+    const double x = gx[i], y = gy[i], z = gz[i];
+    double e = 0.0, dedr = 0.0, deds = 0.0;
+    if (r > 1e-12) {
+      const double r13 = cbrt(r);
+      const double elda = -0.75 * cx * r * r13;
+      const double delda = -cx * r13;
+      const double c = cbrt(three_pi2 * r);
+      const double ds2 = 1.0 / (4.0 * (c * c) * r * r);  // d s^2 / d sigma
+      const double s2 = (x * x + y * y + z * z) * ds2;
+      const double den = 1.0 + mu * s2 / kappa;
+      const double F = 1.0 + kappa - kappa / den;
+      const double dF = mu / (den * den);
+      e = elda * F;
+      dedr = delda * F + elda * dF * (-8.0 / 3.0) * s2 / r;
+      deds = elda * dF * ds2;
+    }
+    v_rho[i] = dedr;
+    gx[i] = 2.0 * deds * x;
+    gy[i] = 2.0 * deds * y;
+    gz[i] = 2.0 * deds * z;
+    part += e;
+  }
+  const double s = block_sum(part, sh);
+  if (threadIdx.x == 0) red[blockIdx.x] = wgt * s;
+}
+
+// out = fa / N_fine + fb on the finest half spectrum (the potential's spectrum)
+__global__ void spec_combine_kernel(long long total, double inv,
+                                    const cufftDoubleComplex* __restrict__ fa,
+                                    const cufftDoubleComplex* __restrict__ fb,
+                                    cufftDoubleComplex* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    cufftDoubleComplex o;
+    o.x = fa[i].x * inv + fb[i].x;
+    o.y = fa[i].y * inv + fb[i].y;
+    out[i] = o;
+  }
+}
+
 __global__ void energy_final_kernel(const double* __restrict__ red, int nparts,
                                     double* __restrict__ out) {
   __shared__ double sh[kRedThreads];
@@ -1530,6 +1621,32 @@ cudaError_t launch_lda(const Plan& p, const double* rho, const double* vH, doubl
   ++p.launches;
   lda_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(p.fine_n, p.omega / (double)p.fine_n, rho, vH, v_out,
                                                 p.d.red + kRedBlocks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fourier_deriv(const Plan& p, int axis, const cufftDoubleComplex* in,
+                                 cufftDoubleComplex* out, bool subtract, cudaStream_t s) {
+  ++p.launches;
+  fourier_deriv_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p, false), p.d.g1tab, axis, in, out,
+                                               subtract ? 1 : 0);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pbe_x(const Plan& p, const double* rho, double* grad3, double* v_rho,
+                         cudaStream_t s) {
+  ++p.launches;
+  const long long n = p.fine_n;
+  pbe_x_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(n, p.omega / (double)n, rho, grad3,
+                                                  grad3 + n, grad3 + 2 * n, v_rho,
+                                                  p.d.red + kRedBlocks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spec_combine(const Plan& p, const cufftDoubleComplex* fa,
+                                const cufftDoubleComplex* fb, cufftDoubleComplex* out,
+                                cudaStream_t s) {
+  ++p.launches;
+  spec_combine_kernel<<<152 * 8, 256, 0, s>>>(p.fine_spec_n, 1.0 / (double)p.fine_n, fa, fb, out);
   return cudaGetLastError();
 }
 

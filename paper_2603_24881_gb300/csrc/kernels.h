@@ -29,6 +29,13 @@ cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int 
 
 cudaError_t launch_tables(const Plan& p, cudaStream_t s);
 cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s);
+cudaError_t launch_fourier_deriv(const Plan& p, int axis, const cufftDoubleComplex* in,
+                                 cufftDoubleComplex* out, bool subtract, cudaStream_t s);
+cudaError_t launch_pbe_x(const Plan& p, const double* rho, double* grad3, double* v_rho,
+                         cudaStream_t s);
+cudaError_t launch_spec_combine(const Plan& p, const cufftDoubleComplex* fa,
+                                const cufftDoubleComplex* fb, cufftDoubleComplex* out,
+                                cudaStream_t s);
 cudaError_t launch_xcontract(const Plan& p, cudaStream_t s);
 cudaError_t launch_collocate(const Plan& p, cudaStream_t s);
 cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s);

@@ -415,6 +415,11 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     set_error("gpw_plan: integ_chunk must be >= 0");
     return GPW_EINVAL;
   }
+  if (desc->xc != GPW_XC_LDA_X && desc->xc != GPW_XC_PBE_X) {
+    set_error("gpw_plan: unknown exchange functional (xc)");
+    return GPW_EINVAL;
+  }
+  plan->xc = desc->xc;
   plan->nw_colloc_req = desc->colloc_warps;
   plan->natm = desc->natm;
   plan->nshell = desc->nshell;
