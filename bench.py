@@ -269,10 +269,9 @@ def served_bench(nreq: int) -> dict:
 
 # ------------------------------------------------------------------ main -------
 def main():
+    from paper_2603_24881_gb300 import replicas
     a = _args()
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    rank, world, local = replicas.ranks_from_env()
     if a.impl == "reference":
         run_reference(a, rank, world)
         return
@@ -282,11 +281,7 @@ def main():
     import paper_2603_24881_gb300 as gpw
 
     torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    dist = replicas.init(world, "nccl", torch.device("cuda", local))
     gpw.load()
     s = workloads.config(a.workload)
     t0 = time.perf_counter()
@@ -319,8 +314,7 @@ def main():
     plan.profile(True)
     l0 = plan.launches()
     clk = Clocks(_gpu_id(torch)) if rank == 0 else None
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     torch.cuda.synchronize()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -329,21 +323,16 @@ def main():
         step()
     e1.record(stream)
     torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
+    replicas.barrier(dist)
     clocks = clk.stop() if clk else None
     launches = plan.launches() - l0
     prof = plan.profile_read()
     plan.profile(False)
-    ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = replicas.max_over_ranks(dist, e0.elapsed_time(e1), device="cuda")
     err = plan.check_device()
     if err:
         raise RuntimeError(f"device bounds check fired: code {err}")
-    value = flops_step * a.steps * world / (ms * 1e-3) / 1e12
+    value = replicas.whole_job_rate(flops_step * a.steps, world, ms * 1e-3) / 1e12
 
     # dominant kernel: the grid pass with the largest share of device time
     ph_flops = {"collocate": st["flops_rho"], "integrate_ip1": st["flops_ip1"]}
@@ -365,17 +354,13 @@ def main():
                    E=torch.empty(2, dtype=torch.float64, pin_memory=True))
         for _ in range(2):
             plan.fock_grad_host(Dh, out=out)
-        if dist:
-            dist.barrier()
+        replicas.barrier(dist)
         t1 = time.perf_counter()
         for _ in range(a.steps):
             plan.fock_grad_host(Dh, out=out)
-        e2e_s = time.perf_counter() - t1
-        if dist:
-            t = torch.tensor([e2e_s], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_s = float(t.item())
-        e2e = {"value": flops_step * a.steps * world / e2e_s / 1e12, "unit": "TFLOP/s",
+        e2e_s = replicas.max_over_ranks(dist, time.perf_counter() - t1, device="cuda")
+        e2e = {"value": replicas.whole_job_rate(flops_step * a.steps, world, e2e_s) / 1e12,
+               "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(Dh.numel() * 8),
                "d2h_bytes_per_step": int((out["V"].numel() + out["grad"].numel() + 2) * 8),
                "api": "Plan.fock_grad_host (pinned host D in; V, gradient, energies out)"}

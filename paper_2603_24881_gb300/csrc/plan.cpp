@@ -68,18 +68,40 @@ double pair_h(double cab, double kab, int la, int lb, double dA, double dB, doub
   return cab * kab * ipow(r + dA, la) * ipow(r + dB, lb) * r * r * std::exp(-ap * r * r);
 }
 
-double pair_extent(double cab, double kab, int la, int lb, double dA, double dB, double ap,
-                   double tau) {
+// Integer box of a pair (reading of Eq. cut): R = the 64-step bisection root of h = tau,
+// lo_d = ceil((P_d - R) N_d / L_d), hi_d = floor((P_d + R) N_d / L_d).  Both are monotone
+// in R (correctly rounded operations, no contraction) and the final root lies inside every
+// bracket of the bisection, so the bisection stops as soon as both ends of its bracket
+// give the same box: the box is then that of the full 64 steps.  False drops the pair.
+void box_at(double R, const double* P, const double* N, const double* L, int* lo, int* hi) {
+  for (int d = 0; d < 3; ++d) {
+    lo[d] = (int)std::ceil((P[d] - R) * N[d] / L[d]);
+    hi[d] = (int)std::floor((P[d] + R) * N[d] / L[d]);
+  }
+}
+
+bool pair_box(double cab, double kab, int la, int lb, double dA, double dB, double ap,
+              double tau, const double* P, const double* N, const double* L, int* lo_out,
+              int* hi_out) {
   double r0 = std::sqrt((double)(la + lb + 2) / (2.0 * ap));
-  if (pair_h(cab, kab, la, lb, dA, dB, ap, r0) < tau) return -1.0;
+  if (pair_h(cab, kab, la, lb, dA, dB, ap, r0) < tau) return false;
   double hi = r0;
   for (int it = 0; it < 200 && pair_h(cab, kab, la, lb, dA, dB, ap, hi) >= tau; ++it) hi *= 2.0;
   double lo = r0;
   for (int it = 0; it < 64; ++it) {
     double mid = 0.5 * (lo + hi);
     if (pair_h(cab, kab, la, lb, dA, dB, ap, mid) >= tau) lo = mid; else hi = mid;
+    if (it >= 7 && (it & 3) == 3) {
+      int a[3], b[3], c[3], e[3];
+      box_at(lo, P, N, L, a, b);
+      box_at(hi, P, N, L, c, e);
+      bool same = true;
+      for (int d = 0; d < 3; ++d) same = same && a[d] == c[d] && b[d] == e[d];
+      if (same) break;
+    }
   }
-  return hi;
+  box_at(hi, P, N, L, lo_out, hi_out);
+  return true;
 }
 
 bool smooth7(int m) {
@@ -576,9 +598,6 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
                 }
                 double kab = std::exp(-aa * ab * AB2 / ap);
                 double cab = std::fabs(pa.cn * pb.cn);
-                double R = pair_extent(cab, kab, pa.l, pb.l, std::sqrt(dA2), std::sqrt(dB2), ap,
-                                       desc->tau);
-                if (R < 0) continue;
                 int level = 0;
                 for (int k = K - 1; k >= 0; --k)
                   if (plan->E[k] >= rel * ap) {
@@ -586,17 +605,17 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
                     break;
                   }
                 PairTmp t;
+                const double Nl[3] = {(double)mesh[level][0], (double)mesh[level][1],
+                                      (double)mesh[level][2]};
+                if (!pair_box(cab, kab, pa.l, pb.l, std::sqrt(dA2), std::sqrt(dB2), ap,
+                              desc->tau, P, Nl, plan->L, t.lo, t.hi))
+                  continue;
                 t.a = a;
                 t.b = b;
                 t.sa = pa.shell;
                 t.sb = pb.shell;
                 t.level = level;
-                for (int d = 0; d < 3; ++d) {
-                  t.img[d] = nn[d];
-                  double Nd = (double)mesh[level][d];
-                  t.lo[d] = (int)std::ceil((P[d] - R) * Nd / plan->L[d]);
-                  t.hi[d] = (int)std::floor((P[d] + R) * Nd / plan->L[d]);
-                }
+                for (int d = 0; d < 3; ++d) t.img[d] = nn[d];
                 if (t.hi[0] < t.lo[0] || t.hi[1] < t.lo[1] || t.hi[2] < t.lo[2]) continue;
                 pairs.push_back(t);
               }
