@@ -56,6 +56,8 @@ def _lib():
             L.orc_collocate.restype = None
             L.orc_integrate.restype = None
             L.orc_rho_points.restype = None
+            L.orc_collocate_tau.restype = None
+            L.orc_integrate_tau.restype = None
             _LIB = L
     return _LIB
 
@@ -293,6 +295,70 @@ class Plan:
                           ctypes.c_long(D.shape[0]), _p(grids), ctypes.c_int(nthreads))
         return [grids[self.grid_off[k]:self.grid_off[k + 1]].reshape(tuple(self.meshes[k]))
                 for k in range(self.nlev)]
+
+    # -------------------------------------------------- meta-GGA (Sec. II) --
+    def tau_levels(self, D, nthreads: int = 0):
+        """Kinetic energy density of each level, tau_k = (1/2) sum D_mu,nu grad phi_mu .
+        grad phi_nu over the pairs of that level (point by point, like Eq. rho_wrap)."""
+        lib = _lib()
+        D = np.ascontiguousarray(D, dtype=np.float64)
+        total = int(self.grid_off[-1])
+        grids = np.zeros(total)
+        lib.orc_collocate_tau(ctypes.c_long(self.npairs), *self._args(), _p(self.grid_off),
+                              ctypes.c_long(total), _p(D), ctypes.c_long(D.shape[0]), _p(grids),
+                              ctypes.c_int(nthreads))
+        return [grids[self.grid_off[k]:self.grid_off[k + 1]].reshape(tuple(self.meshes[k]))
+                for k in range(self.nlev)]
+
+    def _tau_blocks(self, v_levels, grad_D=None, nthreads: int = 0):
+        lib = _lib()
+        v = np.ascontiguousarray(np.concatenate([np.ascontiguousarray(x).ravel() for x in v_levels]))
+        pr = self.prims
+        na = np.array([(l + 1) * (l + 2) // 2 for l in pr["l"]], dtype=np.int64)
+        if grad_D is None:
+            sizes = na[self.ab[:, 0]] * na[self.ab[:, 1]]
+            xoff = np.zeros(self.npairs + 1, dtype=np.int64)
+            xoff[1:] = np.cumsum(sizes)
+            xout = np.zeros(int(xoff[-1]))
+            gd, nao = None, 0
+        else:
+            xoff = np.zeros(1, dtype=np.int64)
+            xout = np.zeros(6 * self.npairs)
+            gd = np.ascontiguousarray(grad_D, dtype=np.float64)
+            nao = gd.shape[0]
+        lib.orc_integrate_tau(ctypes.c_long(self.npairs), None, ctypes.c_long(self.npairs),
+                              *self._args(), _p(self.grid_off), _p(v),
+                              None if gd is None else _p(gd), ctypes.c_long(nao), _p(xoff),
+                              _p(xout), ctypes.c_int(nthreads))
+        return xoff, xout, na
+
+    def mat_tau_levels(self, v_levels, nthreads: int = 0):
+        """Fock term of a kinetic-energy-density potential (Eq. J_metaGGA):
+        V_mu,nu = sum over pairs (Omega/N_k) sum_r v_k (1/2) grad phi_mu . grad phi_nu,
+        mirror blocks as for eval_mat."""
+        nao = self.sys.nao
+        xoff, xout, na = self._tau_blocks(v_levels, nthreads=nthreads)
+        V = np.zeros((nao, nao))
+        ao = self.prims["ao"]
+        for p in range(self.npairs):
+            a, b = int(self.ab[p, 0]), int(self.ab[p, 1])
+            X = xout[xoff[p]:xoff[p + 1]].reshape(na[a], na[b])
+            ia, ib = int(ao[a]), int(ao[b])
+            V[ia:ia + na[a], ib:ib + na[b]] += X
+            if a < b:
+                V[ib:ib + na[b], ia:ia + na[a]] += X.T
+        return V
+
+    def grad_tau_levels(self, D, v_levels, nthreads: int = 0):
+        """Nuclear gradient of <v, tau(D)> at fixed level potentials v (frozen boxes)."""
+        _, xout, _ = self._tau_blocks(v_levels, grad_D=D, nthreads=nthreads)
+        g = np.zeros((self.sys.natm, 3))
+        atom = self.prims["atom"]
+        for p in range(self.npairs):
+            a, b = int(self.ab[p, 0]), int(self.ab[p, 1])
+            g[atom[a]] += xout[6 * p:6 * p + 3]
+            g[atom[b]] += xout[6 * p + 3:6 * p + 6]
+        return g
 
     def subset(self, idx):
         import copy

@@ -478,3 +478,185 @@ void orc_rho_points(long npairs, const int* ab, const int* img, const int* lev,
     out[s] = acc;
   }
 }
+
+/* ------------------------------------------------------------------------------------
+ * Kinetic energy density of meta-GGA functionals (Sec. II, meta-GGA):
+ *   tau(r) = (1/2) sum_mu,nu D_mu,nu grad phi_mu(r) . grad phi_nu(r),
+ * and the matching Fock term (1/2) int v_tau grad phi_mu . grad phi_nu (Eq. J_metaGGA).
+ * Per dimension, a primitive factor is f(u) = u^c exp(-alpha u^2), u = x - C, with
+ *   f'(u)  = (c u^(c-1) - 2 alpha u^(c+1)) exp(-alpha u^2)
+ *   f''(u) = (c (c-1) u^(c-2) - 2 alpha (2c+1) u^c + 4 alpha^2 u^(c+2)) exp(-alpha u^2).
+ * Everything is evaluated point by point (no factorisation, no recursion).
+ */
+static double orc_f0(double u, int c) { return orc_ipow(u, c); }
+static double orc_f1(double u, int c, double a) {
+  double t = -2.0 * a * orc_ipow(u, c + 1);
+  if (c > 0) t += (double)c * orc_ipow(u, c - 1);
+  return t;
+}
+static double orc_f2(double u, int c, double a) {
+  double t = -2.0 * a * (2.0 * c + 1.0) * orc_ipow(u, c) + 4.0 * a * a * orc_ipow(u, c + 2);
+  if (c > 1) t += (double)c * (c - 1) * orc_ipow(u, c - 2);
+  return t;
+}
+
+/* value, gradient and Hessian (xx, yy, zz, xy, xz, yz) of cn u^c exp(-alpha |u|^2) */
+static void orc_prim_derivs(double cn, const int* c, double alpha, const double* u, double* val,
+                            double* g, double* H) {
+  double e = cn * exp(-alpha * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]));
+  double f0[3], f1[3], f2[3];
+  for (int d = 0; d < 3; ++d) {
+    f0[d] = orc_f0(u[d], c[d]);
+    f1[d] = orc_f1(u[d], c[d], alpha);
+    f2[d] = orc_f2(u[d], c[d], alpha);
+  }
+  *val = e * f0[0] * f0[1] * f0[2];
+  g[0] = e * f1[0] * f0[1] * f0[2];
+  g[1] = e * f0[0] * f1[1] * f0[2];
+  g[2] = e * f0[0] * f0[1] * f1[2];
+  if (H) {
+    H[0] = e * f2[0] * f0[1] * f0[2];
+    H[1] = e * f0[0] * f2[1] * f0[2];
+    H[2] = e * f0[0] * f0[1] * f2[2];
+    H[3] = e * f1[0] * f1[1] * f0[2];
+    H[4] = e * f1[0] * f0[1] * f1[2];
+    H[5] = e * f0[0] * f1[1] * f1[2];
+  }
+}
+
+static int orc_hidx(int d, int e) {
+  if (d == e) return d;
+  if (d > e) { int t = d; d = e; e = t; }
+  return d == 0 ? (e == 1 ? 3 : 4) : 5;
+}
+
+/* tau on every level: w (1/2) sum_ij D_ij grad phi_i^a . grad phi_j^b at every point of
+ * each pair box, folded into the cell; OpenMP over pairs, per-thread grids summed in
+ * thread order. */
+void orc_collocate_tau(long npairs, const int* ab, const int* img, const int* lev,
+                       const int* lo, const int* hi, const double* pc, const int* pl,
+                       const double* pal, const double* pcn, const long* pao, const double* Ld,
+                       const int* mesh, const long* grid_off, long grid_total, const double* D,
+                       long nao, double* grids, int nthreads) {
+  memset(grids, 0, sizeof(double) * grid_total);
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#else
+  nthreads = 1;
+#endif
+  double* priv = (double*)calloc((size_t)nthreads * grid_total, sizeof(double));
+#pragma omp parallel num_threads(nthreads)
+  {
+#ifdef _OPENMP
+    int tid = omp_get_thread_num();
+#else
+    int tid = 0;
+#endif
+    double* g = priv + (size_t)tid * grid_total;
+#pragma omp for schedule(dynamic, 16)
+    for (long p = 0; p < npairs; ++p) {
+      orc_pair_t q;
+      orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, Ld);
+      const int* N = mesh + 3 * q.lev;
+      double h[3] = {Ld[0] / N[0], Ld[1] / N[1], Ld[2] / N[2]};
+      double* gl = g + grid_off[q.lev];
+      for (int i0 = q.lo[0]; i0 <= q.hi[0]; ++i0)
+        for (int i1 = q.lo[1]; i1 <= q.hi[1]; ++i1)
+          for (int i2 = q.lo[2]; i2 <= q.hi[2]; ++i2) {
+            double r[3] = {i0 * h[0], i1 * h[1], i2 * h[2]};
+            double ua[3], ub[3], va, vb, ga[ORC_MAXCART][3], gb[ORC_MAXCART][3];
+            for (int d = 0; d < 3; ++d) {
+              ua[d] = r[d] - q.A[d];
+              ub[d] = r[d] - q.B[d];
+            }
+            for (int i = 0; i < q.na; ++i) orc_prim_derivs(q.cna, q.comp_a[i], q.aa, ua, &va, ga[i], NULL);
+            for (int j = 0; j < q.nb; ++j) orc_prim_derivs(q.cnb, q.comp_b[j], q.ab, ub, &vb, gb[j], NULL);
+            double s = 0.0;
+            for (int i = 0; i < q.na; ++i)
+              for (int j = 0; j < q.nb; ++j)
+                s += D[(q.aoa + i) * nao + (q.aob + j)] *
+                     (ga[i][0] * gb[j][0] + ga[i][1] * gb[j][1] + ga[i][2] * gb[j][2]);
+            gl[(orc_wrap(i0, N[0]) * N[1] + orc_wrap(i1, N[1])) * N[2] + orc_wrap(i2, N[2])] +=
+                0.5 * q.w * s;
+          }
+    }
+  }
+  for (int t = 0; t < nthreads; ++t) {
+    const double* g = priv + (size_t)t * grid_total;
+    for (long i = 0; i < grid_total; ++i) grids[i] += g[i];
+  }
+  free(priv);
+}
+
+/* Per-pair Fock blocks of a kinetic-energy-density potential (Eq. J_metaGGA, level
+ * weight Omega/N_k): X_p[i][j] = (Omega/N_k) sum_r v(r) (1/2) grad phi_i^a . grad phi_j^b.
+ * With grad_D, the nuclear gradient of sum_ij D_ij X_ij instead (6 values per pair):
+ * d/dA of grad phi^a is minus the Hessian of phi^a in x, so
+ *   dA_d = -w (Omega/N_k) sum_r v (1/2) sum_ij D_ij sum_e H^a_de grad_e phi^b, and likewise B. */
+void orc_integrate_tau(long npairs, const long* sel, long nsel, const int* ab, const int* img,
+                       const int* lev, const int* lo, const int* hi, const double* pc,
+                       const int* pl, const double* pal, const double* pcn, const long* pao,
+                       const double* Ld, const int* mesh, const long* grid_off, const double* v,
+                       const double* grad_D, long nao, const long* xoff, double* xout,
+                       int nthreads) {
+  long count = sel ? nsel : npairs;
+  double omega = Ld[0] * Ld[1] * Ld[2];
+#ifdef _OPENMP
+  if (nthreads <= 0) nthreads = omp_get_max_threads();
+#endif
+#pragma omp parallel for schedule(dynamic, 8) num_threads(nthreads > 0 ? nthreads : 1)
+  for (long s = 0; s < count; ++s) {
+    long p = sel ? sel[s] : s;
+    orc_pair_t q;
+    orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, Ld);
+    const int* N = mesh + 3 * q.lev;
+    double h[3] = {Ld[0] / N[0], Ld[1] / N[1], Ld[2] / N[2]};
+    double wgt = omega / ((double)N[0] * N[1] * N[2]);
+    const double* vl = v + grid_off[q.lev];
+    double X[ORC_MAXCART * ORC_MAXCART];
+    double G[6] = {0, 0, 0, 0, 0, 0};
+    memset(X, 0, sizeof(X));
+    for (int i0 = q.lo[0]; i0 <= q.hi[0]; ++i0)
+      for (int i1 = q.lo[1]; i1 <= q.hi[1]; ++i1)
+        for (int i2 = q.lo[2]; i2 <= q.hi[2]; ++i2) {
+          double r[3] = {i0 * h[0], i1 * h[1], i2 * h[2]};
+          double vr = vl[(orc_wrap(i0, N[0]) * N[1] + orc_wrap(i1, N[1])) * N[2] + orc_wrap(i2, N[2])];
+          double ua[3], ub[3], va, vb;
+          double ga[ORC_MAXCART][3], gb[ORC_MAXCART][3], Ha[ORC_MAXCART][6], Hb[ORC_MAXCART][6];
+          for (int d = 0; d < 3; ++d) {
+            ua[d] = r[d] - q.A[d];
+            ub[d] = r[d] - q.B[d];
+          }
+          for (int i = 0; i < q.na; ++i)
+            orc_prim_derivs(q.cna, q.comp_a[i], q.aa, ua, &va, ga[i], grad_D ? Ha[i] : NULL);
+          for (int j = 0; j < q.nb; ++j)
+            orc_prim_derivs(q.cnb, q.comp_b[j], q.ab, ub, &vb, gb[j], grad_D ? Hb[j] : NULL);
+          if (!grad_D) {
+            for (int i = 0; i < q.na; ++i)
+              for (int j = 0; j < q.nb; ++j)
+                X[i * q.nb + j] += vr * 0.5 *
+                    (ga[i][0] * gb[j][0] + ga[i][1] * gb[j][1] + ga[i][2] * gb[j][2]);
+          } else {
+            for (int i = 0; i < q.na; ++i)
+              for (int j = 0; j < q.nb; ++j) {
+                double dij = grad_D[(q.aoa + i) * nao + (q.aob + j)] * vr * 0.5;
+                for (int d = 0; d < 3; ++d) {
+                  double sa = 0.0, sb = 0.0;
+                  for (int e = 0; e < 3; ++e) {
+                    sa += Ha[i][orc_hidx(d, e)] * gb[j][e];
+                    sb += ga[i][e] * Hb[j][orc_hidx(d, e)];
+                  }
+                  G[d] -= dij * sa;
+                  G[3 + d] -= dij * sb;
+                }
+              }
+          }
+        }
+    if (!grad_D) {
+      double* xo = xout + xoff[p];
+      for (int k = 0; k < q.na * q.nb; ++k) xo[k] = wgt * X[k];
+    } else {
+      for (int d = 0; d < 6; ++d) xout[6 * s + d] = q.w * wgt * G[d];
+    }
+  }
+}

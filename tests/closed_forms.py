@@ -203,3 +203,54 @@ def madelung_cubic_background(L, eta=None, nreal=6, nrec=12):
     G2 = G2[G2 > 0]
     rec = 4 * np.pi / omega * float(np.sum(np.exp(-G2 / (4 * eta * eta)) / G2))
     return 0.5 * (real + rec - 2 * eta / math.sqrt(math.pi) - math.pi / (eta * eta * omega))
+
+
+def dov_1d(i, j, a, b, A, B):
+    """int d/dx[(x-A)^i e^(-a (x-A)^2)] d/dx[(x-B)^j e^(-b (x-B)^2)] dx: each derivative
+    is i (x-A)^(i-1) - 2a (x-A)^(i+1) (times the exponential), expanded into overlaps."""
+    s = 4.0 * a * b * overlap_1d(i + 1, j + 1, a, b, A, B)
+    if i > 0:
+        s -= 2.0 * b * i * overlap_1d(i - 1, j + 1, a, b, A, B)
+    if j > 0:
+        s -= 2.0 * a * j * overlap_1d(i + 1, j - 1, a, b, A, B)
+    if i > 0 and j > 0:
+        s += i * j * overlap_1d(i - 1, j - 1, a, b, A, B)
+    return s
+
+
+def dpw_1d(i, j, a, b, A, B, G):
+    """The same with a plane wave exp(i G x) (complex)."""
+    s = 4.0 * a * b * pw_1d(i + 1, j + 1, a, b, A, B, G)
+    if i > 0:
+        s -= 2.0 * b * i * pw_1d(i - 1, j + 1, a, b, A, B, G)
+    if j > 0:
+        s -= 2.0 * a * j * pw_1d(i + 1, j - 1, a, b, A, B, G)
+    if i > 0 and j > 0:
+        s += i * j * pw_1d(i - 1, j - 1, a, b, A, B, G)
+    return s
+
+
+def lattice_grad_overlap(sys, reach=40.0):
+    """T_mu,nu = sum_T int grad phi_mu(r) . grad phi_nu(r - T) dr over all space (the
+    kinetic matrix times 2), one dimension differentiated at a time."""
+    out = 0.0
+    for dd in range(3):
+        out = out + _shell_pair_sum(
+            sys, reach, lambda i, j, a, b, A, B, d, dd=dd:
+            dov_1d(i, j, a, b, A, B) if d == dd else overlap_1d(i, j, a, b, A, B))
+    return out
+
+
+def lattice_grad_pw_matrix(sys, waves, reach=40.0):
+    """T_mu,nu[v] = sum_T int grad phi_mu(r) . grad phi_nu(r - T) v(r) dr for
+    v(r) = sum_k a_k cos(G_k . r) (as lattice_pw_matrix, one dimension differentiated at
+    a time)."""
+    L = np.diag(sys.lattice)
+    tot = 0.0
+    for nk, amp in zip(waves.n, waves.a):
+        G = 2 * np.pi * np.asarray(nk, dtype=float) / L
+        for dd in range(3):
+            tot = tot + amp * _shell_pair_sum(
+                sys, reach, lambda i, j, a, b, A, B, d, G=G, dd=dd:
+                dpw_1d(i, j, a, b, A, B, G[d]) if d == dd else pw_1d(i, j, a, b, A, B, G[d]))
+    return tot

@@ -20,6 +20,10 @@ pin here is a closed form, a brute-force evaluation, an identity or an invarianc
   as the functional derivative through the Fourier gradient and divergence, and exact
   uniform-scaling of exchange (E[l^3 rho(l r)] = l E[rho]);
 * gradient contraction (Algorithm 3) against central finite differences;
+* kinetic energy density (meta-GGA): the integral of tau against (1/2) tr(D T) with the
+  analytic lattice-summed grad-phi overlaps T, its Fock term for a constant and for
+  plane-wave potentials against closed forms, the adjoint identity, and its gradient
+  against finite differences;
 * invariance under lattice translations and whole-grid shifts.
 """
 import math
@@ -425,3 +429,73 @@ def test_energy_gradient_matches_finite_differences_gga(res):
         fd = (p.with_coords(cp).energy(s.D, xc="pbe_x") -
               p.with_coords(cm).energy(s.D, xc="pbe_x")) / (2 * h)
         assert g[atom, d] == pytest.approx(fd, rel=1e-6, abs=1e-7)
+
+
+# ---------------------------------------------------------------- meta-GGA (tau) ----
+
+@pytest.fixture(scope="module")
+def res_tau():
+    # shells up to d (the kinetic-energy-density kernels' range), resolved exponents
+    s = systems.resolved(seed=6, shells=((0, 1), (1, 1), (2, 1)), cutoff=100.0)
+    return s, oracle.Plan(s)
+
+
+@pytest.fixture(scope="module")
+def gradov(res_tau):
+    return cf.lattice_grad_overlap(res_tau[0], reach=20.0)
+
+
+def test_integrated_tau_is_half_trace_DT(res_tau, gradov):
+    # int tau = (1/2) tr(D T), T_mu,nu = sum_T int grad phi_mu . grad phi_nu (analytic)
+    s, p = res_tau
+    tl = p.tau_levels(s.D)
+    omega = float(np.prod(np.diag(s.lattice)))
+    tot = sum(omega / t.size * float(np.sum(t)) for t in tl)
+    assert tot == pytest.approx(0.5 * float(np.sum(s.D * gradov)), rel=1e-10)
+    assert tot > 0  # D = C C^T is positive semidefinite
+
+
+def test_mat_tau_of_constant_is_half_T(res_tau, gradov):
+    s, p = res_tau
+    c = 0.37
+    V = p.mat_tau_levels([np.full(tuple(m), c) for m in p.meshes])
+    assert np.max(np.abs(V - 0.5 * c * gradov)) <= 1e-10 * np.max(np.abs(gradov))
+
+
+def test_mat_tau_of_plane_waves_closed_form(res_tau):
+    s, p = res_tau
+    waves = workloads.PlaneWaves(s.potential.n[:2], s.potential.a[:2])  # two waves suffice
+    V = p.mat_tau_levels([waves.sample(m) for m in p.meshes])
+    ref = 0.5 * cf.lattice_grad_pw_matrix(s, waves, reach=20.0)
+    assert np.max(np.abs(V - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+def test_tau_adjoint_identity(res_tau):
+    # <v, tau(D)> = tr(D V_tau(v)) level by level
+    s, p = res_tau
+    v = [s.potential.sample(m) for m in p.meshes]
+    tl = p.tau_levels(s.D)
+    omega = float(np.prod(np.diag(s.lattice)))
+    lhs = sum(omega / t.size * float(np.sum(t * vv)) for t, vv in zip(tl, v))
+    rhs = float(np.sum(s.D * p.mat_tau_levels(v)))
+    assert lhs == pytest.approx(rhs, rel=1e-12)
+
+
+def test_tau_gradient_matches_finite_differences(res_tau):
+    s, p = res_tau
+    v = [s.potential.sample(m) for m in p.meshes]
+    g = p.grad_tau_levels(s.D, v)
+    omega = float(np.prod(np.diag(s.lattice)))
+
+    def form(coords):
+        tl = p.with_coords(coords).tau_levels(s.D)
+        return sum(omega / t.size * float(np.sum(t * vv)) for t, vv in zip(tl, v))
+
+    h = 1e-4
+    for atom, d in [(0, 2), (1, 0)]:
+        cp = s.coords.copy()
+        cm = s.coords.copy()
+        cp[atom, d] += h
+        cm[atom, d] -= h
+        fd = (form(cp) - form(cm)) / (2 * h)
+        assert g[atom, d] == pytest.approx(fd, rel=1e-6, abs=1e-8)
