@@ -88,6 +88,8 @@ def _args():
     ap.add_argument("--tile-integ", default=None, help="integration sub-box t0,t1,t2")
     ap.add_argument("--xc", default="lda_x", choices=["lda_x", "pbe_x"],
                     help="exchange functional (LDA Slater or PBE exchange, a GGA)")
+    ap.add_argument("--tau", action="store_true",
+                    help="also time the kinetic-energy-density (meta-GGA) kernels")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the launch shape with the autotuner (cached per GPU/workload)")
     return ap.parse_args()
@@ -291,7 +293,7 @@ def main():
     if a.autotune:
         from paper_2603_24881_gb300.autotune import tune
         shape = tune(s).plan_kwargs()
-    plan = gpw.Plan(s, xc=a.xc, **shape)
+    plan = gpw.Plan(s, xc=a.xc, tau=a.tau, **shape)
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0)
     st = plan.stats()
@@ -365,6 +367,35 @@ def main():
                "d2h_bytes_per_step": int((out["V"].numel() + out["grad"].numel() + 2) * 8),
                "api": "Plan.fock_grad_host (pinned host D in; V, gradient, energies out)"}
 
+    tau = None
+    if a.tau:
+        # tau on the finest grid, its Fock term and the gradient for a fixed potential
+        # (the fine Hxc potential of this density), CUDA events, same steps
+        vt = plan.fock(D, want_v=True)["v"]
+        Vt = torch.empty_like(V)
+        tt = torch.empty(plan.fine_mesh, dtype=torch.float64, device="cuda")
+        calls = {"eval_tau": lambda: plan.eval_tau(D, out=tt),
+                 "eval_mat_tau": lambda: plan.eval_mat_tau(vt, out=Vt),
+                 "eval_mat_tau_ip1": lambda: plan.eval_mat_tau_ip1(D, vt, out=g)}
+        tau = {}
+        for name, fn in calls.items():
+            for _ in range(max(1, a.warmup)):
+                fn()
+            ta, tb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            ta.record()
+            for _ in range(a.steps):
+                fn()
+            tb.record()
+            torch.cuda.synchronize()
+            tau[name + "_ms"] = ta.elapsed_time(tb) / a.steps
+        pp = st["pair_points_L"]
+        tau["model_tflops"] = {
+            "eval_tau": sum(2.0 * (l + 3) * n for l, n in enumerate(pp)) / tau["eval_tau_ms"] / 1e9,
+            "eval_mat_tau": sum(2.0 * (l + 3) * n for l, n in enumerate(pp)) / tau["eval_mat_tau_ms"] / 1e9,
+            "eval_mat_tau_ip1": sum(2.0 * (l + 4) * n for l, n in enumerate(pp)) / tau["eval_mat_tau_ip1_ms"] / 1e9}
+        if plan.check_device():
+            raise RuntimeError("device bounds check fired in the tau kernels")
+
     if rank == 0:
         cpu = None
         if not a.no_cpu:
@@ -387,6 +418,7 @@ def main():
                            "xc": a.xc,
                            "parallelism": f"replicas x{world}"},
                 "pct_of_fp64_peak": 100.0 * value / world / FP64_PEAK_TFLOPS,
+                **({"tau": tau} if tau else {}),
                 "pair_points_per_s": st["pair_points"] * a.steps * world / (ms * 1e-3),
                 "plan_ms": plan_ms, "phase_ms_per_step": {k: v / a.steps for k, v in prof["ms"].items()},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,

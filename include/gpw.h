@@ -60,6 +60,9 @@ extern "C" {
 
 /* Flags for gpw_desc.flags */
 #define GPW_STRICT 0            /* default: the truncation definition of the paper */
+#define GPW_TAU 1               /* also build the kinetic-energy-density (meta-GGA) data:
+                                   1-D tables to degree L+3 and larger per-pair buffers;
+                                   shells up to d (gpw_eval_tau, gpw_eval_mat_tau*) */
 
 /* Exchange functional (gpw_desc.xc), spin-unpolarised, on the finest grid:
  * GPW_XC_LDA_X  Slater exchange v_x = -(3/pi)^(1/3) rho^(1/3) (Sec. II, LDA);
@@ -98,7 +101,7 @@ typedef struct {
   double rel_cutoff;          /* a pair of exponent alpha_p goes to the coarsest level
                                  with E_k >= rel_cutoff * alpha_p (40 if <= 0) */
   double tau;                 /* screening threshold of Eq. (cut) */
-  int flags;                  /* GPW_STRICT */
+  int flags;                  /* GPW_STRICT, or GPW_TAU */
   int tile[3];                /* sub-box owned by one collocation thread block (grid
                                  points along a1, a2, a3); {0,0,0} = default {4,8,16} */
   int tile_integ[3];          /* sub-box of one integration thread block;
@@ -201,6 +204,24 @@ int gpw_eval_mat_ip1(gpw_plan_t plan, const double* D, const double* v_fine, dou
 /* As gpw_eval_mat_ip1 with per-level potentials (device, N_k doubles each). */
 int gpw_eval_mat_ip1_levels(gpw_plan_t plan, const double* D, const double* const* v_levels,
                             double* grad, void* stream);
+
+/* Kinetic energy density of meta-GGA functionals (Sec. II, meta-GGA; Eq. J_metaGGA and
+ * the tau terms of Algorithms 2 and 3): tau(r) = (1/2) sum D_mu,nu grad phi_mu . grad phi_nu
+ * collocated on the pairs' levels like rho and Fourier-interpolated to the finest grid,
+ * its Fock term V_mu,nu = (1/2) sum_k sum_pairs (Omega/N_k) sum_r v_k grad phi_mu . grad phi_nu
+ * and the nuclear gradient of <v, tau(D)> at fixed v.  Need a plan built with GPW_TAU
+ * (shells up to d); GPW_EINVAL otherwise.  Arguments as for the rho / V / gradient calls
+ * above (device pointers; outputs overwritten). */
+int gpw_eval_tau(gpw_plan_t plan, const double* D, double* tau_fine, void* stream);
+int gpw_eval_tau_levels(gpw_plan_t plan, const double* D, double* const* tau_levels,
+                        void* stream);
+int gpw_eval_mat_tau(gpw_plan_t plan, const double* v_fine, double* V, void* stream);
+int gpw_eval_mat_tau_levels(gpw_plan_t plan, const double* const* v_levels, double* V,
+                            void* stream);
+int gpw_eval_mat_tau_ip1(gpw_plan_t plan, const double* D, const double* v_fine, double* grad,
+                         void* stream);
+int gpw_eval_mat_tau_ip1_levels(gpw_plan_t plan, const double* D,
+                                const double* const* v_levels, double* grad, void* stream);
 
 /* One Fock build: rho = eval_rho(D); v_H from Eqs. (vH)/(vHG) with G = 0 dropped;
  * Slater exchange v_x = -(3/pi)^(1/3) max(rho,0)^(1/3); v = v_H + v_x restricted to

@@ -24,7 +24,9 @@ ERRORS = {0: "GPW_OK", -1: "GPW_EINVAL", -2: "GPW_ENOMEM", -3: "GPW_ECUDA", -4: 
 
 EXPORTS = ["gpw_plan", "gpw_plan_query", "gpw_plan_update_coords", "gpw_plan_pairs",
            "gpw_eval_rho", "gpw_eval_rho_levels", "gpw_eval_mat", "gpw_eval_mat_levels",
-           "gpw_eval_mat_ip1", "gpw_eval_mat_ip1_levels", "gpw_fock", "gpw_fock_async",
+           "gpw_eval_mat_ip1", "gpw_eval_mat_ip1_levels", "gpw_eval_tau", "gpw_eval_tau_levels",
+           "gpw_eval_mat_tau", "gpw_eval_mat_tau_levels", "gpw_eval_mat_tau_ip1",
+           "gpw_eval_mat_tau_ip1_levels", "gpw_fock", "gpw_fock_async",
            "gpw_fock_grad", "gpw_fock_grad_async", "gpw_tile_supported",
            "gpw_plan_prepare", "gpw_plan_commit", "gpw_batch_create", "gpw_batch_set",
            "gpw_batch_fock_grad_async", "gpw_batch_destroy",
@@ -51,6 +53,8 @@ class Desc(ctypes.Structure):
                 ("flags", ctypes.c_int), ("tile", ctypes.c_int * 3),
                 ("tile_integ", ctypes.c_int * 3), ("colloc_warps", ctypes.c_int),
                 ("integ_chunk", ctypes.c_int), ("xc", ctypes.c_int)]
+
+GPW_TAU = 1  # gpw_desc.flags: kinetic-energy-density kernels
 
 # exchange functionals (gpw_desc.xc)
 XC = {"lda_x": 0, "pbe_x": 1}
@@ -104,6 +108,12 @@ def load(build_if_missing: bool = True):
         L.gpw_eval_mat_levels.argtypes = [vp, vp, vp, vp]
         L.gpw_eval_mat_ip1.argtypes = [vp, vp, vp, vp, vp]
         L.gpw_eval_mat_ip1_levels.argtypes = [vp, vp, vp, vp, vp]
+        L.gpw_eval_tau.argtypes = [vp, vp, vp, vp]
+        L.gpw_eval_tau_levels.argtypes = [vp, vp, vp, vp]
+        L.gpw_eval_mat_tau.argtypes = [vp, vp, vp, vp]
+        L.gpw_eval_mat_tau_levels.argtypes = [vp, vp, vp, vp]
+        L.gpw_eval_mat_tau_ip1.argtypes = [vp, vp, vp, vp, vp]
+        L.gpw_eval_mat_tau_ip1_levels.argtypes = [vp, vp, vp, vp, vp]
         L.gpw_fock.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.gpw_fock_async.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.gpw_fock_grad.argtypes = [vp, vp, vp, vp, vp, vp]
@@ -166,12 +176,13 @@ class Plan:
     levels, task lists, grids and FFT plans live on the current CUDA device."""
 
     def __init__(self, system, stream=None, tile=None, tile_integ=None, commit=True,
-                 colloc_warps=None, integ_chunk=None, xc="lda_x"):
+                 colloc_warps=None, integ_chunk=None, xc="lda_x", tau=False):
         """Prepare the plan on the host (screening, levels, task lists) and, unless
         commit=False, commit it to the current device.  An uncommitted plan reports its
         exact device footprint in stats()["device_bytes"].  tile, tile_integ,
         colloc_warps, integ_chunk: launch shape (library defaults if None); xc: exchange
-        functional, "lda_x" (Slater) or "pbe_x" (PBE exchange, a GGA)."""
+        functional, "lda_x" (Slater) or "pbe_x" (PBE exchange, a GGA); tau: also build the
+        kinetic-energy-density (meta-GGA) kernels' data (shells up to d)."""
         self._lib = load()
         s = system
         self.system = s
@@ -201,7 +212,7 @@ class Plan:
         d.meshes = arr(s.meshes, np.int32) if s.meshes is not None else None
         d.rel_cutoff = float(s.rel_cutoff)
         d.tau = float(s.tau)
-        d.flags = 0
+        d.flags = GPW_TAU if tau else 0
         if tile is not None:
             for i in range(3):
                 d.tile[i] = int(tile[i])
@@ -378,6 +389,63 @@ class Plan:
         ptrs = (ctypes.c_void_p * len(vs))(*[_ptr(v) for v in vs])
         check(self._lib.gpw_eval_mat_ip1_levels(self._h, _ptr(D), ptrs, _ptr(out), _stream(stream)),
               "gpw_eval_mat_ip1_levels")
+        return out
+
+    # -- kinetic energy density (meta-GGA; plans built with tau=True) ----------
+    def eval_tau(self, D, out=None, stream=None):
+        import torch
+        D = _dev_f64(D, (self.nao, self.nao))
+        if out is None:
+            out = torch.empty(self.fine_mesh, dtype=torch.float64, device="cuda")
+        check(self._lib.gpw_eval_tau(self._h, _ptr(D), _ptr(out), _stream(stream)), "gpw_eval_tau")
+        return out
+
+    def eval_tau_levels(self, D, stream=None):
+        D = _dev_f64(D, (self.nao, self.nao))
+        outs = self._levels_out()
+        ptrs = (ctypes.c_void_p * len(outs))(*[_ptr(o) for o in outs])
+        check(self._lib.gpw_eval_tau_levels(self._h, _ptr(D), ptrs, _stream(stream)),
+              "gpw_eval_tau_levels")
+        return outs
+
+    def eval_mat_tau(self, v_fine, out=None, stream=None):
+        import torch
+        v = _dev_f64(v_fine, self.fine_mesh)
+        if out is None:
+            out = torch.empty((self.nao, self.nao), dtype=torch.float64, device="cuda")
+        check(self._lib.gpw_eval_mat_tau(self._h, _ptr(v), _ptr(out), _stream(stream)),
+              "gpw_eval_mat_tau")
+        return out
+
+    def eval_mat_tau_levels(self, v_levels, out=None, stream=None):
+        import torch
+        vs = [_dev_f64(v, m) for v, m in zip(v_levels, self.meshes)]
+        if out is None:
+            out = torch.empty((self.nao, self.nao), dtype=torch.float64, device="cuda")
+        ptrs = (ctypes.c_void_p * len(vs))(*[_ptr(v) for v in vs])
+        check(self._lib.gpw_eval_mat_tau_levels(self._h, ptrs, _ptr(out), _stream(stream)),
+              "gpw_eval_mat_tau_levels")
+        return out
+
+    def eval_mat_tau_ip1(self, D, v_fine, out=None, stream=None):
+        import torch
+        D = _dev_f64(D, (self.nao, self.nao))
+        v = _dev_f64(v_fine, self.fine_mesh)
+        if out is None:
+            out = torch.empty((self.natm, 3), dtype=torch.float64, device="cuda")
+        check(self._lib.gpw_eval_mat_tau_ip1(self._h, _ptr(D), _ptr(v), _ptr(out),
+                                             _stream(stream)), "gpw_eval_mat_tau_ip1")
+        return out
+
+    def eval_mat_tau_ip1_levels(self, D, v_levels, out=None, stream=None):
+        import torch
+        D = _dev_f64(D, (self.nao, self.nao))
+        vs = [_dev_f64(v, m) for v, m in zip(v_levels, self.meshes)]
+        if out is None:
+            out = torch.empty((self.natm, 3), dtype=torch.float64, device="cuda")
+        ptrs = (ctypes.c_void_p * len(vs))(*[_ptr(v) for v in vs])
+        check(self._lib.gpw_eval_mat_tau_ip1_levels(self._h, _ptr(D), ptrs, _ptr(out),
+                                                    _stream(stream)), "gpw_eval_mat_tau_ip1_levels")
         return out
 
     def fock(self, D, want_rho=False, want_v=False, stream=None):

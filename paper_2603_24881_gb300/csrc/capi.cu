@@ -386,6 +386,56 @@ int ip1_from_grids(Plan& P, const double* D, double* grad, cudaStream_t s) {
   return GPW_OK;
 }
 
+// Kinetic energy density on every level (meta-GGA): its coefficient tensors (degree L+2),
+// their x contraction and the collocation pass with the degree raised by 2.
+int tau_levels(Plan& P, const double* D, cudaStream_t s) {
+  if (!P.xr) {
+    set_error("kinetic-energy-density kernels need a plan built with GPW_TAU");
+    return GPW_EINVAL;
+  }
+  {
+    Phase ph(P, GPW_PHASE_COEF, s);
+    GPW_CK(launch_pair_coef_tau(P, D, s));
+    GPW_CK(launch_xcontract(P, s, 2));
+  }
+  GPW_CK(cudaMemsetAsync(P.d.grids, 0, sizeof(double) * (size_t)P.grid_total, s));
+  Phase ph(P, GPW_PHASE_COLLOCATE, s);
+  GPW_CK(launch_collocate(P, s, 2));
+  return GPW_OK;
+}
+
+// Level potentials of tau in P.d.grids -> (1/2) int v grad phi . grad phi (degree L+2
+// V tensors) or, with D, the gradient of <v, tau(D)> (degree L+3).
+int mat_tau_from_grids(Plan& P, double* V, cudaStream_t s) {
+  if (!P.xr) {
+    set_error("kinetic-energy-density kernels need a plan built with GPW_TAU");
+    return GPW_EINVAL;
+  }
+  {
+    Phase ph(P, GPW_PHASE_INTEGRATE, s);
+    GPW_CK(launch_integrate(P, 2, s));
+  }
+  Phase ph(P, GPW_PHASE_ASSEMBLE, s);
+  GPW_CK(launch_reduce_parts(P, 2, s));
+  GPW_CK(launch_assemble_V_tau(P, 2, V, s));
+  return GPW_OK;
+}
+
+int ip1_tau_from_grids(Plan& P, const double* D, double* grad, cudaStream_t s) {
+  if (!P.xr) {
+    set_error("kinetic-energy-density kernels need a plan built with GPW_TAU");
+    return GPW_EINVAL;
+  }
+  {
+    Phase ph(P, GPW_PHASE_INTEGRATE_IP1, s);
+    GPW_CK(launch_integrate(P, 3, s));
+  }
+  Phase ph(P, GPW_PHASE_GRAD, s);
+  GPW_CK(launch_reduce_parts(P, 3, s));
+  GPW_CK(launch_grad_tau(P, D, grad, s));
+  return GPW_OK;
+}
+
 // rho -> interpolation -> Poisson + exchange -> restricted level potentials in P.d.grids;
 // energies to energies_dev.  Without v_out the Hartree part stays in G space: each level
 // spectrum is mask_k (FFT(v_x)/N + 4 pi S/G^2), one finest-grid C2R fewer.
@@ -708,6 +758,70 @@ int gpw_eval_mat_ip1(gpw_plan_t plan, const double* D, const double* v_fine, dou
   return gpw::ip1_from_grids(P, D, grad, s);
 }
 
+int gpw_eval_tau_levels(gpw_plan_t plan, const double* D, double* const* tau_levels,
+                        void* stream) {
+  if (gpw::bad(plan) || !D || !tau_levels) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::tau_levels(P, D, s);
+  if (rc) return rc;
+  for (int k = 0; k < P.nlev; ++k) {
+    if (!tau_levels[k]) continue;
+    const gpw::LevelInfo& lv = P.lev[k];
+    cudaError_t e = cudaMemcpyAsync(tau_levels[k], P.d.grids + lv.grid_off,
+                                    sizeof(double) * (size_t)lv.N[0] * lv.N[1] * lv.N[2],
+                                    cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) {
+      set_error(std::string("eval_tau_levels: ") + cudaGetErrorString(e));
+      return GPW_ECUDA;
+    }
+  }
+  return GPW_OK;
+}
+int gpw_eval_tau(gpw_plan_t plan, const double* D, double* tau_fine, void* stream) {
+  if (gpw::bad(plan) || !D || !tau_fine) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::tau_levels(P, D, s);
+  if (rc) return rc;
+  if ((rc = gpw::combine(P, s))) return rc;
+  return gpw::fft_z2d(P, 0, P.d.fspec, tau_fine, s);
+}
+int gpw_eval_mat_tau(gpw_plan_t plan, const double* v_fine, double* V, void* stream) {
+  if (gpw::bad(plan) || !v_fine || !V) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::restrict_levels(P, v_fine, s);
+  if (rc) return rc;
+  return gpw::mat_tau_from_grids(P, V, s);
+}
+int gpw_eval_mat_tau_levels(gpw_plan_t plan, const double* const* v_levels, double* V,
+                            void* stream) {
+  if (gpw::bad(plan) || !v_levels || !V) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::copy_levels(P, v_levels, s);
+  if (rc) return rc;
+  return gpw::mat_tau_from_grids(P, V, s);
+}
+int gpw_eval_mat_tau_ip1(gpw_plan_t plan, const double* D, const double* v_fine, double* grad,
+                         void* stream) {
+  if (gpw::bad(plan) || !D || !v_fine || !grad) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::restrict_levels(P, v_fine, s);
+  if (rc) return rc;
+  return gpw::ip1_tau_from_grids(P, D, grad, s);
+}
+int gpw_eval_mat_tau_ip1_levels(gpw_plan_t plan, const double* D,
+                                const double* const* v_levels, double* grad, void* stream) {
+  if (gpw::bad(plan) || !D || !v_levels || !grad) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = gpw::copy_levels(P, v_levels, s);
+  if (rc) return rc;
+  return gpw::ip1_tau_from_grids(P, D, grad, s);
+}
 int gpw_eval_mat_ip1_levels(gpw_plan_t plan, const double* D, const double* const* v_levels,
                             double* grad, void* stream) {
   if (gpw::bad(plan) || !D || !v_levels || !grad) return GPW_EINVAL;

@@ -79,6 +79,7 @@ struct PlanView {
   double* grids;
   int* err;
   int chunk_i;  // tasks per integration work item (items carry level | chunk << 4)
+  int xr;       // extra 1-D table rows per dimension (table rows = L + 2 + xr)
 };
 
 struct DeviceArrays {
@@ -165,9 +166,14 @@ struct Plan {
   bool fft_made[GPW_MAX_LEVELS] = {false};
   int red_blocks = 0;
   size_t smem_colloc = 0, smem_integ = 0, smem_integ1 = 0;
+  // kinetic-energy-density passes (GPW_TAU): collocation at degree L+2, integration at
+  // degree L+2 / L+3
+  size_t smem_colloc_t = 0, smem_integ3 = 0;
+  int stg_colloc_t = 0, nw_colloc_t = 8, stg_integ3 = 0;
   int nw_colloc = 8, nw_integ = 8;     // warps per thread block
   int nw_colloc_req = 0;               // requested collocation warps (0 = occupancy pick)
   int xc = GPW_XC_LDA_X;               // exchange functional
+  int xr = 0;                          // extra 1-D table rows (2 with GPW_TAU)
   int stg_colloc = 0, stg_integ = 0, stg_integ1 = 0;  // per-warp staging doubles
   // profiler: event pairs per phase, recorded on the calling stream when enabled
   bool prof = false;

@@ -72,13 +72,14 @@ __device__ __forceinline__ void load_tables(int* dst, const CoefTables* src, int
 
 // ----------------------------------------------------------------------------------
 // 1-D factor tables (Eq. gab_lp with the exponential of Eq. gab):
-//   g_d[l](i) = (x - A_d)^l exp(-alpha_p (x - P_d)^2),  x = (lo_d + i) h_d,  l <= L + 1,
+//   g_d[l](i) = (x - A_d)^l exp(-alpha_p (x - P_d)^2),  x = (lo_d + i) h_d,  l <= L + 1 + xr
+//   (xr = 2 for plans with the kinetic-energy-density kernels),
 // laid out per pair as [d][l][n_d].  Also pref = c_a N_a c_b N_b K_ab.  One warp per pair.
 __global__ void tables_kernel(long long np, const KLevels K, const int4* __restrict__ hot_a,
                               const int4* __restrict__ hot_b, const double* __restrict__ geo,
                               const double* __restrict__ cab,
                               const long long* __restrict__ tab_off, double* __restrict__ tab,
-                              double* __restrict__ pref) {
+                              double* __restrict__ pref, int xr) {
   const int lane = threadIdx.x & 31;
   long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long sw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -110,8 +111,8 @@ __global__ void tables_kernel(long long np, const KLevels K, const int4* __restr
       double u = x - g[d];
       double t = x - P[d];
       double v = exp(-ap * t * t);
-      double* dst = tab + base + (long long)(L + 2) * off + i;
-      for (int l = 0; l <= L + 1; ++l) {
+      double* dst = tab + base + (long long)(L + 2 + xr) * off + i;
+      for (int l = 0; l <= L + 1 + xr; ++l) {
         dst[(long long)l * n[d]] = v;
         v *= u;
       }
@@ -184,12 +185,13 @@ __global__ void xcontract_kernel(long long np, const int4* __restrict__ hot_a,
                                  const long long* __restrict__ coef_off,
                                  const double* __restrict__ coef,
                                  const long long* __restrict__ xt_off,
-                                 const CoefTables* __restrict__ tabs, double* __restrict__ xt) {
+                                 const CoefTables* __restrict__ tabs, double* __restrict__ xt,
+                                 int ldeg) {
   const int lane = threadIdx.x & 31;
   long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long sw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long p = gw; p < np; p += sw) {
-    const int L = hot_a[p].w, n0 = hot_b[p].x;
+    const int L = hot_a[p].w + ldeg, n0 = hot_b[p].x;
     const double* g0 = tab + tab_off[p];
     const double* Dp = coef + coef_off[p];
     double* out = xt + xt_off[p];
@@ -272,10 +274,9 @@ __device__ __forceinline__ bool task_ok(const Task& tk, int lx, int lrows, const
 // task into shared memory (row strides P1, P2).
 template <int P1, int P2>
 __device__ __forceinline__ void stage_yz_async(const double* tb, const Task& tk, int rows,
-                                               double* sg1, double* sg2, int lane) {
-  const int L = tk.L;
-  const double* t1 = tb + (L + 2) * tk.n[0] + tk.t[1];
-  const double* t2 = tb + (L + 2) * (tk.n[0] + tk.n[1]) + tk.t[2];
+                                               int trows, double* sg1, double* sg2, int lane) {
+  const double* t1 = tb + trows * tk.n[0] + tk.t[1];
+  const double* t2 = tb + trows * (tk.n[0] + tk.n[1]) + tk.t[2];
   const int m1 = tk.m[1], m2 = tk.m[2];
   const float i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
   for (int it = lane; it < rows * m1; it += 32) {
@@ -393,7 +394,7 @@ struct CollocLayout {
 template <int T0, int T1, int T2, int NW>
 __global__ void __launch_bounds__(NW * 32, 24 / NW)
     collocate_kernel(const PlanView* __restrict__ views, const int4* __restrict__ work,
-                     const CoefTables* __restrict__ tabs, int lp, int stg) {
+                     const CoefTables* __restrict__ tabs, int lp, int stg, int ldeg) {
   using Lay = CollocLayout<T0, T1, T2>;
   constexpr int kTileN = T0 * T1 * T2;
   extern __shared__ __align__(16) double sm[];
@@ -429,10 +430,11 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     double* sX = stage_base + b * bufn;
     double* sg1 = sX + xrows * T0;
     double* sg2 = sg1 + lp * T1;
-    const int L = tk.L, m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
+    const int L = tk.L + ldeg, m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
+    const int trows = tk.L + 2 + pv.xr;  // table rows of the pair
     const double* x = xt + xoff + tk.t[0];
-    const double* t1 = tab + toff + (L + 2) * tk.n[0] + tk.t[1];
-    const double* t2 = tab + toff + (L + 2) * (tk.n[0] + tk.n[1]) + tk.t[2];
+    const double* t1 = tab + toff + trows * tk.n[0] + tk.t[1];
+    const double* t2 = tab + toff + trows * (tk.n[0] + tk.n[1]) + tk.t[2];
     const float i0f = __frcp_rn((float)m0), i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
     for (int it = lane; it < nc2(L) * m0; it += 32) {
       const int c = fdiv(it, i0f), i = it - c * m0;
@@ -457,7 +459,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     const long long atoff = __ldg(tab_off + a0.x);
     const long long axoff = __ldg(xt_off + a0.x);
     const Task tk = decode_task(a0, a1);
-    if (task_ok(tk, tk.L, lp, sb)) issue(tk, atoff, axoff, 0);
+    if (task_ok(tk, tk.L + ldeg, lp, sb)) issue(tk, atoff, axoff, 0);
     cp_async_commit();
   }
   if (e + NW < sb.ee) {
@@ -473,7 +475,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     // fetch the next task's windows into the other buffer
     if (e + NW < sb.ee) {
       const Task tn = decode_task(b0, b1);
-      if (task_ok(tn, tn.L, lp, sb)) issue(tn, btoff, bxoff, buf ^ 1);
+      if (task_ok(tn, tn.L + ldeg, lp, sb)) issue(tn, btoff, bxoff, buf ^ 1);
       cp_async_commit();
     }
     int4 c0 = b0, c1 = b1;
@@ -482,7 +484,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
       c1 = __ldg(task + 2 * (e + 2 * NW) + 1);
     }
     const Task tk = decode_task(a0, a1);
-    const int L = tk.L;
+    const int L = tk.L + ldeg;
     const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
     if (!task_ok(tk, L, lp, sb)) {
       if (lane == 0) set_err(err, 1);
@@ -604,7 +606,8 @@ __global__ void __launch_bounds__(NW * 32)
 
   auto issue = [&](const Task& tk, long long toff, int b) {
     double* sg1 = stage_base + b * bufn;
-    stage_yz_async<P1, P2>(tab + toff, tk, tk.L + lext + 1, sg1, sg1 + lpx * P1, lane);
+    stage_yz_async<P1, P2>(tab + toff, tk, tk.L + lext + 1, tk.L + 2 + pv.xr, sg1,
+                           sg1 + lpx * P1, lane);
   };
 
   long long e = sb.eb + warp;
@@ -740,7 +743,7 @@ __global__ void __launch_bounds__(kRedPW * 32, 6)
                         const long long* __restrict__ coef_off,
                         const long long* __restrict__ tab_off, const double* __restrict__ tab,
                         const double* __restrict__ part, const CoefTables* __restrict__ tabs,
-                        double* __restrict__ coef, int lext) {
+                        double* __restrict__ coef, int lext, int xr) {
   __shared__ double s_w[kRedPW][kRedCap];
   __shared__ double s_g[kRedPW][(kLextMax + 1) * kRedX];
   __shared__ int s_seg[kRedPW][kRedX];
@@ -752,7 +755,7 @@ __global__ void __launch_bounds__(kRedPW * 32, 6)
   int* sSeg = s_seg[wib];
   for (long long p = gw; p < np; p += sw) {
     const int4 ha = hot_a[p], hb = hot_b[p];
-    const int L = ha.w, Lx = L + lext, nc = nc3(Lx), n2c = nc2(Lx), S = nc2(L + 1);
+    const int L = ha.w, Lx = L + lext, nc = nc3(Lx), n2c = nc2(Lx), S = nc2(L + 1 + xr);
     const int lo0 = ha.x, n0 = hb.x, hi0 = lo0 + n0 - 1;
     const LevelInfo& lv = K.lv[hb.w];
     const int N0 = lv.N[0];
@@ -920,6 +923,26 @@ __global__ void assemble_V_kernel(long long ngroups, const int4* __restrict__ gr
 __device__ __forceinline__ int mono_index(int k0, int k1, int k2, int M) {
   const int r = M - k2;
   return nc3(M) - nc3(r) + k1 * (r + 1) - ((k1 * (k1 - 1)) >> 1) + k0;
+}
+
+// Integral of one shifted pair product (x - A)^a' (x - B)^b' from the pair's V tensor of
+// degree Lx: (x - B)^b' expanded about A (Eq. binomial), pw[d][j] = (A_d - B_d)^j;
+// zero if an exponent is negative (b'_d <= 4).
+__device__ double xelem(int a0, int a1, int a2, int b0, int b1, int b2, const double (*pw)[5],
+                        const double* V, int Lx) {
+  if (a0 < 0 || a1 < 0 || a2 < 0 || b0 < 0 || b1 < 0 || b2 < 0) return 0.0;
+  double s = 0.0;
+  for (int t2 = 0; t2 <= b2; ++t2) {
+    const double c2 = binom(b2, t2) * pw[2][b2 - t2];
+    for (int t1 = 0; t1 <= b1; ++t1) {
+      const double c21 = c2 * binom(b1, t1) * pw[1][b1 - t1];
+      double s0 = 0.0;
+      for (int t0 = 0; t0 <= b0; ++t0)
+        s0 += binom(b0, t0) * pw[0][b0 - t0] * V[mono_index(a0 + t0, a1 + t1, a2 + t2, Lx)];
+      s += c21 * s0;
+    }
+  }
+  return s;
 }
 
 // Gradient contraction per pair (Algorithm 3).  The centre derivative of the product
@@ -1195,6 +1218,253 @@ __global__ void lda_kernel(long long n, double wgt, const double* __restrict__ r
   if (threadIdx.x == 0) red[blockIdx.x] = wgt * s;
 }
 
+// ----------------------------------------------------------------------------------
+// Kinetic energy density of meta-GGA functionals (Sec. II, meta-GGA):
+//   tau(r) = (1/2) sum D_mu,nu grad phi_mu . grad phi_nu,
+// and its Fock term (1/2) int v_tau grad phi_mu . grad phi_nu (Eq. J_metaGGA).  Per
+// dimension d, d/dx_d of (x - A)^a exp(-alpha_a (x - A)^2) is a_d (x - A)^(a - e_d) -
+// 2 alpha_a (x - A)^(a + e_d) (times the exponential), so grad phi_a . grad phi_b is a
+// sum of twelve shifted pair products; expanding (x - B)^b' about A (Eq. binomial) gives
+// a coefficient tensor of degree L + 2 over the monomials (x - A)^k, which the
+// collocation kernel contracts like the density's (its degree raised by 2).
+
+// Term of d/dx_d on a monomial exponent c (shift -1: c_d, shift +1: -2 alpha).
+__device__ __forceinline__ double dcoef(int cd, int shift, double alpha) {
+  return shift < 0 ? (double)cd : -2.0 * alpha;
+}
+
+// Pair coefficient tensor of tau: Dt[k] = w pref (1/2) sum_mu,nu D_mu,nu sum_d sum of the
+// four (a +- e_d, b +- e_d) terms, binomially expanded about A.  One thread per pair.
+__global__ void pair_coef_tau_kernel(long long np, const int4* __restrict__ ids,
+                                     const int4* __restrict__ ids2, const double* __restrict__ geo,
+                                     const double* __restrict__ pref,
+                                     const long long* __restrict__ coef_off,
+                                     const double* __restrict__ D, int nao,
+                                     double* __restrict__ coef) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const int4 id = ids[p];
+  const int la = id.x, lb = id.y, Lt = la + lb + 2;
+  const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
+  const double* g = geo + 8 * p;
+  const double aa = g[6], ab = g[7];
+  double pw[3][4];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double t = g[d] - g[3 + d];
+    pw[d][0] = 1.0;
+    pw[d][1] = t;
+    pw[d][2] = t * t;
+    pw[d][3] = t * t * t;
+  }
+  double acc[nc3(kLmax)];
+  const int nc = nc3(Lt);
+  for (int c = 0; c < nc; ++c) acc[c] = 0.0;
+  const double scale = 0.5 * (double)ids2[p].z * pref[p];
+  for (int mu = 0; mu < na; ++mu) {
+    int a[3];
+    cart_comp(la, mu, a);
+    const double* Drow = D + (long long)(id.z + mu) * nao + id.w;
+    for (int nu = 0; nu < nb; ++nu) {
+      int b[3];
+      cart_comp(lb, nu, b);
+      const double dmn = scale * Drow[nu];
+      for (int d = 0; d < 3; ++d)
+        for (int sa = -1; sa <= 1; sa += 2)
+          for (int sb = -1; sb <= 1; sb += 2) {
+            const double c = dmn * dcoef(a[d], sa, aa) * dcoef(b[d], sb, ab);
+            int a2[3] = {a[0], a[1], a[2]}, b2[3] = {b[0], b[1], b[2]};
+            a2[d] += sa;
+            b2[d] += sb;
+            if (c == 0.0 || a2[d] < 0 || b2[d] < 0) continue;
+            for (int t2 = 0; t2 <= b2[2]; ++t2) {
+              const double c2 = c * binom(b2[2], t2) * pw[2][b2[2] - t2];
+              for (int t1 = 0; t1 <= b2[1]; ++t1) {
+                const double c21 = c2 * binom(b2[1], t1) * pw[1][b2[1] - t1];
+                for (int t0 = 0; t0 <= b2[0]; ++t0)
+                  acc[mono_index(a2[0] + t0, a2[1] + t1, a2[2] + t2, Lt)] +=
+                      c21 * binom(b2[0], t0) * pw[0][b2[0] - t0];
+              }
+            }
+          }
+    }
+  }
+  double* out = coef + coef_off[p];
+  for (int c = 0; c < nc; ++c) out[c] = acc[c];
+}
+
+// (1/2) grad phi_a . grad phi_b integrated against the potential, from the pair's V
+// tensor of degree Lx (xelem: the binomial contraction of one shifted pair product).
+__device__ double xtau(const int* a, const int* b, double aa, double ab, const double (*pw)[5],
+                       const double* V, int Lx) {
+  double s = 0.0;
+  for (int d = 0; d < 3; ++d)
+    for (int sa = -1; sa <= 1; sa += 2)
+      for (int sb = -1; sb <= 1; sb += 2) {
+        const double c = dcoef(a[d], sa, aa) * dcoef(b[d], sb, ab);
+        if (c == 0.0) continue;
+        int a2[3] = {a[0], a[1], a[2]}, b2[3] = {b[0], b[1], b[2]};
+        a2[d] += sa;
+        b2[d] += sb;
+        s += c * xelem(a2[0], a2[1], a2[2], b2[0], b2[1], b2[2], pw, V, Lx);
+      }
+  return 0.5 * s;
+}
+
+// V^tau assembly: one warp per contracted shell pair, lanes over its elements (as
+// assemble_V_kernel, with xtau in place of the plain pair product).
+__global__ void assemble_V_tau_kernel(long long ngroups, const int4* __restrict__ groups,
+                                      const int4* __restrict__ ids, const int4* __restrict__ ids2,
+                                      const double* __restrict__ geo,
+                                      const double* __restrict__ pref,
+                                      const long long* __restrict__ coef_off,
+                                      const double* __restrict__ coef,
+                                      const CoefTables* __restrict__ tabs, int nao, int lext,
+                                      double* __restrict__ V) {
+  const int lane = threadIdx.x & 31;
+  long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  if (gw >= ngroups) return;
+  const int4 gr = groups[gw];
+  const int4 id0 = ids[gr.z];
+  const int la = id0.x, lb = id0.y, Lx = la + lb + lext;
+  const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
+  const bool diag = gr.x == gr.y;
+  for (int el = lane; el < na * nb; el += 32) {
+    const int mu = el / nb, nu = el - mu * nb;
+    int ca[3], cb[3];
+    cart_comp(la, mu, ca);
+    cart_comp(lb, nu, cb);
+    double tot = 0.0;
+    for (int p = gr.z; p < gr.w; ++p) {
+      const double* g = geo + 8LL * p;
+      double pw[3][5];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const double t = g[d] - g[3 + d];
+        pw[d][0] = 1.0;
+#pragma unroll
+        for (int k = 1; k < 5; ++k) pw[d][k] = pw[d][k - 1] * t;
+      }
+      const double* Vp = coef + coef_off[p];
+      double x = xtau(ca, cb, g[6], g[7], pw, Vp, Lx);
+      if (diag && ids2[p].z == 2) {
+        int ca2[3], cb2[3];
+        cart_comp(la, nu, ca2);
+        cart_comp(lb, mu, cb2);
+        x += xtau(ca2, cb2, g[6], g[7], pw, Vp, Lx);
+      }
+      tot += pref[p] * x;
+    }
+    V[(long long)(id0.z + mu) * nao + id0.w + nu] = tot;
+    if (!diag) V[(long long)(id0.w + nu) * nao + id0.z + mu] = tot;
+  }
+}
+
+// Second derivative d^2/dx_d dx_e of a monomial with exponents c: up to four shifted
+// monomials (shift vectors in s, coefficients in w); returns the number of terms.
+__device__ int d2terms(const int* c, int d, int e, double alpha, int (*s)[3], double* w) {
+  int n = 0;
+  if (d != e) {
+    for (int sd = -1; sd <= 1; sd += 2)
+      for (int se = -1; se <= 1; se += 2) {
+        s[n][0] = s[n][1] = s[n][2] = 0;
+        s[n][d] = sd;
+        s[n][e] = se;
+        w[n++] = dcoef(c[d], sd, alpha) * dcoef(c[e], se, alpha);
+      }
+  } else {
+    const double cd = (double)c[d];
+    const int sh[3] = {-2, 0, 2};
+    const double ww[3] = {cd * (cd - 1.0), -2.0 * alpha * (2.0 * cd + 1.0), 4.0 * alpha * alpha};
+    for (int k = 0; k < 3; ++k) {
+      s[n][0] = s[n][1] = s[n][2] = 0;
+      s[n][d] = sh[k];
+      w[n++] = ww[k];
+    }
+  }
+  return n;
+}
+
+// Nuclear gradient of <v_tau, tau(D)> per pair from its degree-(L+3) V tensor: the centre
+// derivative of grad phi_a is minus its Hessian in x, so
+//   dE/dA_d = -w pref (1/2) sum_mu,nu D_mu,nu sum_e <d_d d_e phi_a, d_e phi_b>,
+//   dE/dB_d = -w pref (1/2) sum_mu,nu D_mu,nu sum_e <d_e phi_a, d_d d_e phi_b>,
+// each bracket a sum of shifted pair products (xelem).  One thread per pair.
+__global__ void grad_tau_pair_kernel(long long np, const int4* __restrict__ ids,
+                                     const int4* __restrict__ ids2, const double* __restrict__ geo,
+                                     const double* __restrict__ pref,
+                                     const long long* __restrict__ coef_off,
+                                     const double* __restrict__ coef,
+                                     const CoefTables* __restrict__ tabs,
+                                     const double* __restrict__ D, int nao,
+                                     double* __restrict__ pgrad) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const int4 id = ids[p];
+  const int la = id.x, lb = id.y, Lx = la + lb + 3;
+  const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
+  const double* g = geo + 8 * p;
+  const double aa = g[6], ab = g[7];
+  double pw[3][5];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double t = g[d] - g[3 + d];
+    pw[d][0] = 1.0;
+#pragma unroll
+    for (int k = 1; k < 5; ++k) pw[d][k] = pw[d][k - 1] * t;
+  }
+  const double* Vp = coef + coef_off[p];
+  const double scale = -0.5 * (double)ids2[p].z * pref[p];
+  double gA[3] = {0.0, 0.0, 0.0}, gB[3] = {0.0, 0.0, 0.0};
+  int s2[4][3];
+  double w2[4];
+  for (int mu = 0; mu < na; ++mu) {
+    int a[3];
+    cart_comp(la, mu, a);
+    const double* Drow = D + (long long)(id.z + mu) * nao + id.w;
+    for (int nu = 0; nu < nb; ++nu) {
+      int b[3];
+      cart_comp(lb, nu, b);
+      const double dmn = scale * Drow[nu];
+      for (int d = 0; d < 3; ++d) {
+        double sA = 0.0, sB = 0.0;
+        for (int e = 0; e < 3; ++e) {
+          // <d_d d_e phi_a, d_e phi_b>
+          const int n2a = d2terms(a, d, e, aa, s2, w2);
+          for (int i = 0; i < n2a; ++i)
+            for (int sb = -1; sb <= 1; sb += 2) {
+              const double c = w2[i] * dcoef(b[e], sb, ab);
+              if (c == 0.0) continue;
+              int b2[3] = {b[0], b[1], b[2]};
+              b2[e] += sb;
+              sA += c * xelem(a[0] + s2[i][0], a[1] + s2[i][1], a[2] + s2[i][2], b2[0], b2[1],
+                              b2[2], pw, Vp, Lx);
+            }
+          // <d_e phi_a, d_d d_e phi_b>
+          const int n2b = d2terms(b, d, e, ab, s2, w2);
+          for (int i = 0; i < n2b; ++i)
+            for (int sa = -1; sa <= 1; sa += 2) {
+              const double c = w2[i] * dcoef(a[e], sa, aa);
+              if (c == 0.0) continue;
+              int a2[3] = {a[0], a[1], a[2]};
+              a2[e] += sa;
+              sB += c * xelem(a2[0], a2[1], a2[2], b[0] + s2[i][0], b[1] + s2[i][1],
+                              b[2] + s2[i][2], pw, Vp, Lx);
+            }
+        }
+        gA[d] += dmn * sA;
+        gB[d] += dmn * sB;
+      }
+    }
+  }
+  double* out = pgrad + 6 * p;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    out[d] = gA[d];
+    out[3 + d] = gB[d];
+  }
+}
+
 // Fourier derivative on the finest half spectrum (Sec. II, GGA): out = i G_d in, or
 // out -= i G_d in (subtract).  G_d = (2 pi s)/L_d from a host table that is zero on the
 // Nyquist plane of an even axis.
@@ -1409,6 +1679,25 @@ cudaError_t configure_kernels(Plan* p) {
 #undef GPW_TILE_CONF_I
   if (found != 3) return cudaErrorInvalidValue;
   p->nw_integ = kNW;
+  if (p->xr) {
+#define GPW_TILE_CONF_T(a, b, c)                                                             \
+  if (p->tile[0] == a && p->tile[1] == b && p->tile[2] == c) {                               \
+    p->stg_colloc_t = even(CollocLayout<a, b, c>::stage(p->lmax + 3));                       \
+    if (pick_colloc_warps<a, b, c>(p->stg_colloc_t, p->nw_colloc_req, &p->nw_colloc_t,      \
+                                   &p->smem_colloc_t) == 0)                                 \
+      return cudaErrorInvalidValue;                                                          \
+  }
+#define GPW_TILE_CONF_I3(a, b, c)                                                            \
+  if (p->tile_i[0] == a && p->tile_i[1] == b && p->tile_i[2] == c) {                         \
+    p->stg_integ3 = even(IntegLayout<a, b, c>::stage(p->lmax + 4));                          \
+    p->smem_integ3 = integ_smem<a, b, c>(p->stg_integ3);                                     \
+  }
+    GPW_COLLOC_SHAPES(GPW_TILE_CONF_T)
+    GPW_INTEG_SHAPES(GPW_TILE_CONF_I3)
+#undef GPW_TILE_CONF_T
+#undef GPW_TILE_CONF_I3
+    if ((size_t)optin < std::max(p->smem_colloc_t, p->smem_integ3)) return cudaErrorInvalidValue;
+  }
   if ((size_t)optin < std::max(p->smem_colloc, std::max(p->smem_integ, p->smem_integ1)))
     return cudaErrorInvalidValue;
   return cudaSuccess;
@@ -1419,7 +1708,8 @@ cudaError_t launch_tables(const Plan& p, cudaStream_t s) {
   long long blocks = std::min<long long>((p.npairs + 7) / 8, 152LL * 64);
   ++p.launches;
   tables_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, make_klevels(p, false), p.d.hot_a, p.d.hot_b,
-                                             p.d.geo, p.d.cab, p.d.tab_off, p.d.tab, p.d.pref);
+                                             p.d.geo, p.d.cab, p.d.tab_off, p.d.tab, p.d.pref,
+                                             p.xr);
   return cudaGetLastError();
 }
 
@@ -1432,12 +1722,13 @@ cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_xcontract(const Plan& p, cudaStream_t s) {
+cudaError_t launch_xcontract(const Plan& p, cudaStream_t s, int ldeg) {
   if (p.npairs == 0) return cudaSuccess;
   long long blocks = std::min<long long>((p.npairs + 7) / 8, 152LL * 64);
   ++p.launches;
   xcontract_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, p.d.hot_a, p.d.hot_b, p.d.tab_off, p.d.tab,
-                                                p.d.coef_off, p.d.coef, p.d.xt_off, p.d.tabs, p.d.part);
+                                                p.d.coef_off, p.d.coef, p.d.xt_off, p.d.tabs, p.d.part,
+                                                ldeg);
   return cudaGetLastError();
 }
 
@@ -1450,7 +1741,7 @@ cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views,
 #define GPW_COLLOC_NW(a, b, c, NWV)                                                        \
   if (t0 == a && t1 == b && t2 == c && cfg.nw == NWV) {                                    \
     collocate_kernel<a, b, c, NWV><<<(int)nwork, NWV * 32, cfg.smem, s>>>(                 \
-        views, work, tabs, cfg.lp, cfg.stg);                                               \
+        views, work, tabs, cfg.lp, cfg.stg, cfg.ldeg);                                     \
     return cudaGetLastError();                                                             \
   }
 #define GPW_TILE_COLLOC(a, b, c) GPW_COLLOC_NW(a, b, c, 8) GPW_COLLOC_NW(a, b, c, 6) GPW_COLLOC_NW(a, b, c, 4)
@@ -1476,15 +1767,17 @@ cudaError_t launch_integrate_views(const GridLaunch& cfg, int lext, const PlanVi
   return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_collocate(const Plan& p, cudaStream_t s) {
+cudaError_t launch_collocate(const Plan& p, cudaStream_t s, int ldeg) {
   if (p.nwork == 0) return cudaSuccess;
+  if (ldeg && !p.xr) return cudaErrorInvalidValue;
   ++p.launches;
   GridLaunch cfg;
   for (int d = 0; d < 3; ++d) cfg.tile[d] = p.tile[d];
-  cfg.nw = p.nw_colloc;
-  cfg.lp = p.lmax + 1;
-  cfg.stg = p.stg_colloc;
-  cfg.smem = p.smem_colloc;
+  cfg.nw = ldeg ? p.nw_colloc_t : p.nw_colloc;
+  cfg.lp = p.lmax + 1 + ldeg;
+  cfg.stg = ldeg ? p.stg_colloc_t : p.stg_colloc;
+  cfg.smem = ldeg ? p.smem_colloc_t : p.smem_colloc;
+  cfg.ldeg = ldeg;
   return launch_collocate_views(cfg, p.d.view, p.d.work_c, p.nwork, p.d.tabs, s);
 }
 
@@ -1494,9 +1787,10 @@ cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s) {
   GridLaunch cfg;
   for (int d = 0; d < 3; ++d) cfg.tile[d] = p.tile_i[d];
   cfg.nw = kNW;
+  if (lext > 1 + p.xr) return cudaErrorInvalidValue;
   cfg.lp = p.lmax + lext + 1;
-  cfg.stg = lext ? p.stg_integ1 : p.stg_integ;
-  cfg.smem = lext ? p.smem_integ1 : p.smem_integ;
+  cfg.stg = lext > 1 ? p.stg_integ3 : (lext ? p.stg_integ1 : p.stg_integ);
+  cfg.smem = lext > 1 ? p.smem_integ3 : (lext ? p.smem_integ1 : p.smem_integ);
   return launch_integrate_views(cfg, lext, p.d.view, p.d.work_i, p.nwork_i, p.d.tabs, s);
 }
 
@@ -1558,6 +1852,7 @@ PlanView make_view(const Plan& p) {
   v.grids = p.d.grids;
   v.err = p.d.err;
   v.chunk_i = p.chunk_i;
+  v.xr = p.xr;
   return v;
 }
 
@@ -1567,7 +1862,7 @@ cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s) {
   ++p.launches;
   reduce_parts_kernel<<<(int)blocks, kRedPW * 32, 0, s>>>(
       p.npairs, make_klevels(p, true), p.tile_i[0], p.d.hot_a, p.d.hot_b, p.d.ids2, p.d.part_off,
-      p.d.coef_off, p.d.tab_off, p.d.tab, p.d.part, p.d.tabs, p.d.coef, lext);
+      p.d.coef_off, p.d.tab_off, p.d.tab, p.d.part, p.d.tabs, p.d.coef, lext, p.xr);
   return cudaGetLastError();
 }
 
@@ -1621,6 +1916,40 @@ cudaError_t launch_lda(const Plan& p, const double* rho, const double* vH, doubl
   ++p.launches;
   lda_kernel<<<kRedBlocks, kRedThreads, 0, s>>>(p.fine_n, p.omega / (double)p.fine_n, rho, vH, v_out,
                                                 p.d.red + kRedBlocks);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pair_coef_tau(const Plan& p, const double* D, cudaStream_t s) {
+  if (p.npairs == 0) return cudaSuccess;
+  if (!p.xr) return cudaErrorInvalidValue;
+  ++p.launches;
+  pair_coef_tau_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
+      p.npairs, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, D, p.nao, p.d.coef);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_assemble_V_tau(const Plan& p, int lext, double* V, cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(V, 0, sizeof(double) * (size_t)p.nao * p.nao, s);
+  if (e != cudaSuccess || p.ngroups == 0) return e;
+  ++p.launches;
+  assemble_V_tau_kernel<<<(int)((p.ngroups + 7) / 8), 256, 0, s>>>(
+      p.ngroups, p.d.groups, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, p.d.coef,
+      p.d.tabs, p.nao, lext, V);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_grad_tau(const Plan& p, const double* D, double* grad, cudaStream_t s) {
+  if (p.npairs > 0) {
+    ++p.launches;
+    grad_tau_pair_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
+        p.npairs, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, p.d.coef, p.d.tabs, D,
+        p.nao, p.d.pgrad);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  ++p.launches;
+  grad_atom_kernel<<<(p.natm + 7) / 8, 256, 0, s>>>(p.natm, p.d.atom_off, p.d.atom_list,
+                                                    p.d.pgrad, grad);
   return cudaGetLastError();
 }
 

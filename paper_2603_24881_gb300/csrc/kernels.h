@@ -17,6 +17,7 @@ struct GridLaunch {
   int tile[3];
   int nw, lp, stg;
   size_t smem;
+  int ldeg = 0;  // collocation: degree added to every pair's L (2 for the kinetic density)
 };
 cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views, const int4* work,
                                    long long nwork, const CoefTables* tabs, cudaStream_t s);
@@ -29,6 +30,9 @@ cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int 
 
 cudaError_t launch_tables(const Plan& p, cudaStream_t s);
 cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s);
+cudaError_t launch_pair_coef_tau(const Plan& p, const double* D, cudaStream_t s);
+cudaError_t launch_assemble_V_tau(const Plan& p, int lext, double* V, cudaStream_t s);
+cudaError_t launch_grad_tau(const Plan& p, const double* D, double* grad, cudaStream_t s);
 cudaError_t launch_fourier_deriv(const Plan& p, int axis, const cufftDoubleComplex* in,
                                  cufftDoubleComplex* out, bool subtract, cudaStream_t s);
 cudaError_t launch_pbe_x(const Plan& p, const double* rho, double* grad3, double* v_rho,
@@ -36,8 +40,8 @@ cudaError_t launch_pbe_x(const Plan& p, const double* rho, double* grad3, double
 cudaError_t launch_spec_combine(const Plan& p, const cufftDoubleComplex* fa,
                                 const cufftDoubleComplex* fb, cufftDoubleComplex* out,
                                 cudaStream_t s);
-cudaError_t launch_xcontract(const Plan& p, cudaStream_t s);
-cudaError_t launch_collocate(const Plan& p, cudaStream_t s);
+cudaError_t launch_xcontract(const Plan& p, cudaStream_t s, int ldeg = 0);
+cudaError_t launch_collocate(const Plan& p, cudaStream_t s, int ldeg = 0);
 cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s);
 cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s);
 cudaError_t launch_assemble_V(const Plan& p, int lext, double* V, cudaStream_t s);

@@ -254,7 +254,7 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
         bad = bad || n[d] > 65535;
       }
       const long long ns12 = (long long)sg[1].size() * sg[2].size();
-      const long long S = nc2(L + 1);
+      const long long S = nc2(L + 1 + plan->xr);
       if (psize) {
         (*psize)[p] = S * n[0] * ns12;
         bad = bad || (*psize)[p] > INT32_MAX;
@@ -442,6 +442,17 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     return GPW_EINVAL;
   }
   plan->xc = desc->xc;
+  if (desc->flags & ~GPW_TAU) {
+    set_error("gpw_plan: unknown flags");
+    return GPW_EINVAL;
+  }
+  plan->xr = (desc->flags & GPW_TAU) ? 2 : 0;
+  if (plan->xr && desc->shell_l)
+    for (int sh = 0; sh < desc->nshell; ++sh)
+      if (desc->shell_l[sh] > 2) {
+        set_error("gpw_plan: the kinetic-energy-density kernels (GPW_TAU) support shells up to d");
+        return GPW_EINVAL;
+      }
   plan->nw_colloc_req = desc->colloc_warps;
   plan->natm = desc->natm;
   plan->nshell = desc->nshell;
@@ -689,11 +700,11 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     H->geo[8 * p + 7] = pb.alpha;
     H->cab[p] = pa.cn * pb.cn;
     H->tab_off[p] = tab_total;
-    tab_total += (long long)(L + 2) * (n[0] + n[1] + n[2]);
+    tab_total += (long long)(L + 2 + plan->xr) * (n[0] + n[1] + n[2]);
     H->coef_off[p] = coef_total;
-    coef_total += nc3(L + 1);
+    coef_total += nc3(L + 1 + plan->xr);
     H->xt_off[p] = xt_total;
-    xt_total += (long long)nc2(L) * n[0];
+    xt_total += (long long)nc2(L + plan->xr) * n[0];
     long long pts = (long long)n[0] * n[1] * n[2];
     plan->pair_points += pts;
     plan->pair_points_level[t.level] += pts;
