@@ -90,6 +90,7 @@ void free_plan(Plan* P) {
       cufftDestroy(P->fft_z2d[k]);
     }
   d = DeviceArrays();
+  recycle_host_arrays(P->host);
   delete P->host;
   P->host = nullptr;
   P->committed = false;
@@ -594,6 +595,7 @@ int gpw_plan_commit(gpw_plan_t plan, void* stream) {
       P.host = keep;
       return rc;
     }
+    gpw::recycle_host_arrays(P.host);
     delete P.host;
     P.host = nullptr;
     return GPW_OK;

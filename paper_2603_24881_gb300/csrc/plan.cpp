@@ -11,6 +11,8 @@
 #include <string>
 #include <vector>
 
+#include <mutex>
+
 #include <omp.h>
 
 #include "gpw_internal.h"
@@ -156,6 +158,27 @@ struct PairBox {
   int level, lo[3], hi[3];
 };
 
+// Spare task-record buffers of committed plans, kept with their pages so that the next
+// plan (a server plans one small cell after another) neither faults them in nor zeroes
+// fresh memory.  At most kTaskPoolBytes in total.
+std::mutex g_task_pool_mu;
+std::vector<std::vector<int4>> g_task_pool;
+constexpr size_t kTaskPoolBytes = size_t(1) << 30;
+
+std::vector<int4> take_task_buffer(size_t n) {
+  std::lock_guard<std::mutex> lk(g_task_pool_mu);
+  int best = -1;
+  for (int i = 0; i < (int)g_task_pool.size(); ++i)
+    if (g_task_pool[i].capacity() >= n &&
+        (best < 0 || g_task_pool[i].capacity() < g_task_pool[best].capacity()))
+      best = i;
+  if (best < 0) return {};
+  std::vector<int4> v = std::move(g_task_pool[best]);
+  g_task_pool.erase(g_task_pool.begin() + best);
+  v.clear();
+  return v;
+}
+
 // Host threads for a loop over n items: all cores for large plans, one for small ones
 // (a server plans several small cells at once on its own threads).
 int plan_threads(long long n) {
@@ -232,7 +255,8 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
   }
   const long long nent = count[nsub];
   *nent_out = nent;
-  task->assign(2 * nent, make_int4(0, 0, 0, 0));
+  *task = take_task_buffer((size_t)(2 * nent));
+  task->resize((size_t)(2 * nent));
   if (ranks) ranks->assign(np, 0);
   if (psize) psize->assign(np, 0);
   int fail = GPW_OK;
@@ -264,39 +288,57 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
         fail = GPW_ERANGE;
         continue;
       }
+      // per dimension and segment: packed (m, u, t) fields of the records and the
+      // sub-box coordinate, computed once per pair
+      constexpr size_t kSegMax = 512;
+      int fm[3][kSegMax], fu[3][kSegMax], ft[3][kSegMax];
+      long long fj[3][kSegMax];
+      bool big = false;
+      for (int d = 0; d < 3; ++d) {
+        big = big || sg[d].size() > kSegMax;
+        if (big) break;
+        for (size_t k = 0; k < sg[d].size(); ++k) {
+          const Seg& sgm = sg[d][k];
+          const long long s0 = (long long)sgm.j * T[d];
+          const long long ext = std::min<long long>(T[d], lv.N[d] - s0);
+          const long long o = (long long)sgm.k * lv.N[d] + s0;
+          const long long a = std::max<long long>(t.lo[d], o);
+          const long long b = std::min<long long>(t.hi[d], o + ext - 1);
+          const int shift = 8 * d;
+          fm[d][k] = (int)(b - a + 1) << shift;
+          fu[d][k] = (int)(a - o) << shift;
+          ft[d][k] = (int)(a - t.lo[d]) | (n[d] << 16);
+          fj[d][k] = sgm.j;
+        }
+      }
+      if (big) {
+#pragma omp critical(gpw_plan_fail)
+        fail = GPW_ERANGE;
+        continue;
+      }
+      const int ns0 = (int)sg[0].size(), ns1 = (int)sg[1].size(), ns2 = (int)sg[2].size();
       int rank = 0;
-      auto isect = [&](int d, const Seg& sgm, int* m, int* u, int* tt) {
-        long long s0 = (long long)sgm.j * T[d];
-        long long ext = std::min<long long>(T[d], lv.N[d] - s0);
-        long long o = (long long)sgm.k * lv.N[d] + s0;
-        long long a = std::max<long long>(t.lo[d], o);
-        long long b = std::min<long long>(t.hi[d], o + ext - 1);
-        *m = (int)(b - a + 1);
-        *u = (int)(a - o);
-        *tt = (int)(a - t.lo[d]);
-      };
-      for (auto& s0 : sg[0])
-        for (auto& s1 : sg[1])
-          for (auto& s2 : sg[2]) {
-            int m[3], u[3], tt[3];
-            isect(0, s0, &m[0], &u[0], &tt[0]);
-            isect(1, s1, &m[1], &u[1], &tt[1]);
-            isect(2, s2, &m[2], &u[2], &tt[2]);
-            long long sub = lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j;
-            long long slot = fill[sub]++;
-            (*task)[2 * slot] = make_int4((int)p, m[0] | (m[1] << 8) | (m[2] << 16) | (L << 24),
-                                          u[0] | (u[1] << 8) | (u[2] << 16), rank);
-            const long long woff = S * ((long long)tt[0] * ns12 + (rank % ns12) * m[0]);
-            (*task)[2 * slot + 1] = make_int4(tt[0] | (n[0] << 16), tt[1] | (n[1] << 16),
-                                              tt[2] | (n[2] << 16), psize ? (int)woff : 0);
-            ++rank;
+      for (int k0 = 0; k0 < ns0; ++k0) {
+        const int m0 = fm[0][k0] & 255, tt0 = ft[0][k0] & 0xffff;
+        for (int k1 = 0; k1 < ns1; ++k1) {
+          const long long sub01 = lv.sub_base + (fj[0][k0] * lv.nsb[1] + fj[1][k1]) * lv.nsb[2];
+          for (int k2 = 0; k2 < ns2; ++k2, ++rank) {
+            const long long slot = fill[sub01 + fj[2][k2]]++;
+            const int r12 = k1 * ns2 + k2;
+            (*task)[2 * slot] = make_int4((int)p, fm[0][k0] | fm[1][k1] | fm[2][k2] | (L << 24),
+                                          fu[0][k0] | fu[1][k1] | fu[2][k2], rank);
+            (*task)[2 * slot + 1] =
+                make_int4(ft[0][k0], ft[1][k1], ft[2][k2],
+                          psize ? (int)(S * ((long long)tt0 * ns12 + (long long)r12 * m0)) : 0);
           }
+        }
+      }
       if (ranks) (*ranks)[p] = rank;
     }
   }
   if (fail != GPW_OK) {
-    set_error("gpw_plan: pair box longer than 65535 grid points or per-pair task block "
-              "too large");
+    set_error("gpw_plan: pair box longer than 65535 grid points, more than 512 sub-box "
+              "segments along one axis, or per-pair task block too large");
     return fail;
   }
   *sub_off = count;
@@ -561,6 +603,11 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     atom_prims[prims[i].atom].push_back(i);
     atom_rmax[prims[i].atom] = std::max(atom_rmax[prims[i].atom], prims[i].rcut);
   }
+  // each atom's primitives by decreasing r_cut: the distance test r_a + r_b > |A - B_T|
+  // then fails for all later b once it fails for one (the order of the pairs found does
+  // not matter, they are sorted below)
+  for (auto& v : atom_prims)
+    std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return prims[x].rcut > prims[y].rcut; });
   const double* X = desc->coords;
   // atoms are screened in parallel (each thread keeps its own pair list); the sort
   // below fixes one order whatever the thread count
@@ -592,13 +639,15 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
               AB2 += t * t;
             }
             if (std::sqrt(AB2) >= rsum_max + 1e-9 * (1.0 + rsum_max)) continue;
-            for (int a : atom_prims[ia])
+            const double dist = std::sqrt(AB2);
+            for (int a : atom_prims[ia]) {
+              if (!(dist < prims[a].rcut + atom_rmax[ib])) break;
               for (int b : atom_prims[ib]) {
-                if (a > b) continue;
                 const Prim& pa = prims[a];
                 const Prim& pb = prims[b];
                 double rsum = pa.rcut + pb.rcut;
-                if (!(std::sqrt(AB2) < rsum)) continue;
+                if (!(dist < rsum)) break;
+                if (a > b) continue;
                 double aa = pa.alpha, ab = pb.alpha, ap = aa + ab;
                 double P[3], dA2 = 0.0, dB2 = 0.0;
                 for (int d = 0; d < 3; ++d) {
@@ -630,6 +679,7 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
                 if (t.hi[0] < t.lo[0] || t.hi[1] < t.lo[1] || t.hi[2] < t.lo[2]) continue;
                 pairs.push_back(t);
               }
+            }
           }
     }
   }
@@ -802,6 +852,30 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   plan->fine_n = (long long)plan->lev[0].N[0] * plan->lev[0].N[1] * plan->lev[0].N[2];
   plan->fine_spec_n = (long long)plan->lev[0].N[0] * plan->lev[0].N[1] * (plan->lev[0].N[2] / 2 + 1);
   return GPW_OK;
+}
+
+void recycle_host_arrays(HostArrays* H) {
+  if (!H) return;
+  std::lock_guard<std::mutex> lk(g_task_pool_mu);
+  for (std::vector<int4>* v : {&H->task_c, &H->task_i}) {
+    if (v->capacity() == 0) continue;
+    g_task_pool.push_back(std::move(*v));
+    v->clear();
+  }
+  // keep the largest buffers within the byte cap
+  std::sort(g_task_pool.begin(), g_task_pool.end(),
+            [](const std::vector<int4>& a, const std::vector<int4>& b) {
+              return a.capacity() > b.capacity();
+            });
+  std::vector<std::vector<int4>> kept;
+  size_t total = 0;
+  for (auto& v : g_task_pool) {
+    const size_t b = v.capacity() * sizeof(int4);
+    if (total + b > kTaskPoolBytes) continue;
+    total += b;
+    kept.push_back(std::move(v));
+  }
+  g_task_pool.swap(kept);
 }
 
 void build_coef_tables(CoefTables* t) {

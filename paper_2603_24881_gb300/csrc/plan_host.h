@@ -19,4 +19,8 @@ struct HostArrays {
   std::vector<int> atom_list;
 };
 
+// Return the task-record buffers of a plan that no longer needs them (after commit) to
+// the planner's pool of spare buffers.
+void recycle_host_arrays(HostArrays* H);
+
 }  // namespace gpw
