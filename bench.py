@@ -221,8 +221,14 @@ def served_bench(nreq: int) -> dict:
     reqs = workloads.stream_requests(nreq, seed=4)
     systems = [r.system() for r in reqs]
     grads = [r.want_grad for r in reqs]
-    with Server() as srv:  # warm-up: kernels, cuFFT and allocator
-        [f.result() for f in [srv.submit(s, g) for s, g in zip(systems[:4], grads[:4])]]
+    # warm-up (untimed): one request of every cell size in the stream, so that the CUDA
+    # modules of every kernel and FFT size are loaded and the allocator has seen them
+    first = {}
+    for i, s in enumerate(systems):
+        first.setdefault(int(s.natm), i)
+    warm = sorted(first.values())
+    with Server() as srv:
+        [f.result() for f in [srv.submit(systems[i], True) for i in warm]]
     with Server() as srv:
         t0 = time.perf_counter()
         futs = [srv.submit(s, g) for s, g in zip(systems, grads)]
