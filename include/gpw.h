@@ -315,6 +315,12 @@ int gpw_lda_x_noalloc(const double* rho, long long n, double weight, double* v_x
 /* Release the plan and everything it owns.  NULL is ignored. */
 void gpw_plan_destroy(gpw_plan_t plan);
 
+/* As gpw_plan_destroy, without synchronising the device: the plan's memory returns to
+ * the device pool in stream order on `stream`.  The caller guarantees that every piece of
+ * work that uses the plan has finished or is ordered before `stream` (a server that
+ * waited for a request's batch).  Not a paper operation. */
+void gpw_plan_destroy_async(gpw_plan_t plan, void* stream);
+
 /* Static message for an error code. */
 const char* gpw_strerror(int code);
 

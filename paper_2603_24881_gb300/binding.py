@@ -26,7 +26,7 @@ EXPORTS = ["gpw_plan", "gpw_plan_query", "gpw_plan_update_coords", "gpw_plan_pai
            "gpw_eval_rho", "gpw_eval_rho_levels", "gpw_eval_mat", "gpw_eval_mat_levels",
            "gpw_eval_mat_ip1", "gpw_eval_mat_ip1_levels", "gpw_eval_tau", "gpw_eval_tau_levels",
            "gpw_eval_mat_tau", "gpw_eval_mat_tau_levels", "gpw_eval_mat_tau_ip1",
-           "gpw_eval_mat_tau_ip1_levels", "gpw_fock", "gpw_fock_async",
+           "gpw_eval_mat_tau_ip1_levels", "gpw_plan_destroy_async", "gpw_fock", "gpw_fock_async",
            "gpw_fock_grad", "gpw_fock_grad_async", "gpw_tile_supported",
            "gpw_plan_prepare", "gpw_plan_commit", "gpw_batch_create", "gpw_batch_set",
            "gpw_batch_fock_grad_async", "gpw_batch_destroy",
@@ -131,13 +131,15 @@ def load(build_if_missing: bool = True):
         L.gpw_profile_read.argtypes = [vp, vp, vp, ci, vp]
         L.gpw_plan_destroy.argtypes = [vp]
         L.gpw_plan_destroy.restype = None
+        L.gpw_plan_destroy_async.argtypes = [vp, vp]
+        L.gpw_plan_destroy_async.restype = None
         L.gpw_strerror.argtypes = [ci]
         L.gpw_strerror.restype = ctypes.c_char_p
         L.gpw_last_error.argtypes = []
         L.gpw_last_error.restype = ctypes.c_char_p
         for name in EXPORTS:
-            if name not in ("gpw_plan_destroy", "gpw_strerror", "gpw_last_error",
-                            "gpw_batch_destroy"):
+            if name not in ("gpw_plan_destroy", "gpw_plan_destroy_async", "gpw_strerror",
+                            "gpw_last_error", "gpw_batch_destroy"):
                 getattr(L, name).restype = ci
         _LIB = L
         return L
@@ -255,9 +257,14 @@ class Plan:
         return self
 
     # -- housekeeping -------------------------------------------------------
-    def close(self):
+    def close(self, stream=None):
+        """Release the plan.  With a stream: in stream order on it, without synchronising
+        the device (all work using the plan must have finished or be ordered before it)."""
         if getattr(self, "_h", None) is not None and self._h.value:
-            self._lib.gpw_plan_destroy(self._h)
+            if stream is None:
+                self._lib.gpw_plan_destroy(self._h)
+            else:
+                self._lib.gpw_plan_destroy_async(self._h, ctypes.c_void_p(_stream(stream)))
             self._h = ctypes.c_void_p()
 
     def __del__(self):

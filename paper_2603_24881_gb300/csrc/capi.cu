@@ -3,6 +3,11 @@
 // level <-> finest-grid Fourier interpolation and the Poisson solve, exchange, and the
 // integration / gradient kernels with their fixed-order reductions.
 #include <cuda_runtime.h>
+
+#include <array>
+#include <map>
+#include <memory>
+#include <mutex>
 #include <cufft.h>
 
 #include <algorithm>
@@ -37,6 +42,13 @@ namespace gpw {
 static thread_local std::string g_err;
 void set_error(const std::string& msg) { g_err = msg; }
 
+// A cuFFT handle shared by the plans of the process (see fft_entry).
+struct FftEntry {
+  cufftHandle h;
+  size_t ws = 0;
+  std::mutex mu;
+};
+
 namespace {
 
 #define GPW_CK(x)                                                                   \
@@ -57,10 +69,15 @@ namespace {
     }                                                                               \
   } while (0)
 
+// Plan memory is stream-ordered (cudaMallocAsync / cudaFreeAsync from the device's
+// default pool, kept cached): committing and releasing plans does not synchronise the
+// device, so a server can commit and release requests while other batches run.
+thread_local cudaStream_t g_alloc_stream = nullptr;  // set by create_device (this thread)
+
 template <class T>
 int dalloc(T** ptr, long long count, long long* bytes) {
   size_t b = sizeof(T) * (size_t)std::max<long long>(count, 1);
-  GPW_CK(cudaMalloc((void**)ptr, b));
+  GPW_CK(cudaMallocAsync((void**)ptr, b, g_alloc_stream));
   *bytes += (long long)b;
   return GPW_OK;
 }
@@ -69,26 +86,73 @@ template <class T>
 int upload(T** ptr, const std::vector<T>& v, long long* bytes) {
   int rc = dalloc(ptr, (long long)v.size(), bytes);
   if (rc) return rc;
-  if (!v.empty()) GPW_CK(cudaMemcpy(*ptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice));
+  if (!v.empty())
+    GPW_CK(cudaMemcpyAsync(*ptr, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice,
+                           g_alloc_stream));
   return GPW_OK;
 }
 
-void free_plan(Plan* P) {
+// cuFFT handles shared by all plans of the process, one per (device, mesh, direction),
+// made once without a work area (cufftSetAutoAllocation 0).  A plan owns its work area
+// and sets it, with its stream, right before each execution under the handle's lock, so
+// plans on different streams run the same transform concurrently.
+std::mutex g_fft_mu;
+std::map<std::array<int, 5>, std::unique_ptr<FftEntry>> g_fft;
+
+int fft_entry(const int* N, cufftType type, FftEntry** out) {
+  int dev = 0;
+  GPW_CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_fft_mu);
+  const std::array<int, 5> key = {dev, N[0], N[1], N[2], (int)type};
+  auto it = g_fft.find(key);
+  if (it == g_fft.end()) {
+    std::unique_ptr<FftEntry> e(new FftEntry());
+    GPW_CF(cufftCreate(&e->h));
+    if (cufftSetAutoAllocation(e->h, 0) != CUFFT_SUCCESS ||
+        cufftMakePlan3d(e->h, N[0], N[1], N[2], type, &e->ws) != CUFFT_SUCCESS) {
+      cufftDestroy(e->h);
+      set_error("cufftMakePlan3d failed");
+      return GPW_ECUFFT;
+    }
+    it = g_fft.emplace(key, std::move(e)).first;
+  }
+  *out = it->second.get();
+  return GPW_OK;
+}
+
+// cufftEstimate3d per (mesh, direction), remembered (prepare calls it for every plan)
+std::map<std::array<int, 4>, size_t> g_fft_est;
+
+size_t fft_estimate(const int* N, cufftType type) {
+  std::lock_guard<std::mutex> lk(g_fft_mu);
+  const std::array<int, 4> key = {N[0], N[1], N[2], (int)type};
+  auto it = g_fft_est.find(key);
+  if (it != g_fft_est.end()) return it->second;
+  size_t ws = 0;
+  if (cufftEstimate3d(N[0], N[1], N[2], type, &ws) != CUFFT_SUCCESS) ws = 0;
+  g_fft_est[key] = ws;
+  return ws;
+}
+
+// Release the plan's device memory in stream order on `stream` (the commit stream if
+// NULL); with sync, after all device work so far (the plain destroy's guarantee).
+void free_plan(Plan* P, cudaStream_t stream = nullptr, bool sync = true) {
   DeviceArrays& d = P->d;
   void* ptrs[] = {d.hot_a, d.hot_b, d.ids, d.ids2, d.geo, d.cab, d.pref, d.tab_off,
                   d.coef_off, d.part_off, d.xt_off, d.task_c, d.sub_off_c, d.work_c, d.task_i, d.sub_off_i, d.work_i, d.groups, d.atom_off,
                   d.atom_list, d.tab, d.coef, d.part, d.pgrad, d.grids, d.spec, d.fspec,
                   d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs, d.view, d.g2tab,
-                  d.g1tab, d.grad3, d.fspec3};
+                  d.g1tab, d.grad3, d.fspec3, P->fft_work};
+  bool any = false;
+  for (void* q : ptrs) any = any || q != nullptr;
+  if (any && sync) cudaDeviceSynchronize();
+  cudaStream_t fs = stream ? stream : P->alloc_stream;
   for (void* q : ptrs)
-    if (q) cudaFree(q);
+    if (q) cudaFreeAsync(q, fs);
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
   P->ev_pool.clear();
-  for (int k = 0; k < GPW_MAX_LEVELS; ++k)
-    if (P->fft_made[k]) {
-      cufftDestroy(P->fft_d2z[k]);
-      cufftDestroy(P->fft_z2d[k]);
-    }
+  for (int k = 0; k < GPW_MAX_LEVELS; ++k) P->fft_d2z[k] = P->fft_z2d[k] = nullptr;
+  P->fft_work = nullptr;
   d = DeviceArrays();
   recycle_host_arrays(P->host);
   delete P->host;
@@ -114,13 +178,10 @@ long long estimate_bytes(const Plan& P, const HostArrays& H) {
   b += 2 * sz((long long)P.lev[0].N[0] + P.lev[0].N[1] + P.lev[0].N[2], sizeof(double));
   if (P.xc == GPW_XC_PBE_X)
     b += sz(3 * P.fine_n, sizeof(double)) + sz(P.fine_spec_n, sizeof(cufftDoubleComplex));
-  for (int k = 0; k < P.nlev; ++k) {
-    size_t ws = 0;
-    if (cufftEstimate3d(P.lev[k].N[0], P.lev[k].N[1], P.lev[k].N[2], CUFFT_D2Z, &ws) == CUFFT_SUCCESS)
-      b += (long long)ws;
-    if (cufftEstimate3d(P.lev[k].N[0], P.lev[k].N[1], P.lev[k].N[2], CUFFT_Z2D, &ws) == CUFFT_SUCCESS)
-      b += (long long)ws;
-  }
+  size_t ws = 0;  // one work area: the largest transform of the plan
+  for (int k = 0; k < P.nlev; ++k)
+    ws = std::max(ws, std::max(fft_estimate(P.lev[k].N, CUFFT_D2Z), fft_estimate(P.lev[k].N, CUFFT_Z2D)));
+  b += (long long)ws;
   return b;
 }
 
@@ -128,6 +189,17 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
   long long b = 0;
   DeviceArrays& d = P->d;
   int rc;
+  {
+    // keep freed plan memory in the default pool for the next plans
+    int dev = 0;
+    cudaMemPool_t pool;
+    if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+      unsigned long long thr = ~0ULL;
+      cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+    }
+  }
+  P->alloc_stream = s;
+  g_alloc_stream = s;
 #define GPW_TRY(x) \
   if ((rc = (x)) != GPW_OK) return rc
   GPW_TRY(upload(&d.hot_a, H.hot_a, &b));
@@ -200,21 +272,14 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
 #undef GPW_TRY
 #define GPW_TRY2(x) \
   if ((rc = (x)) != GPW_OK) return rc
+  size_t fws = 0;
   for (int k = 0; k < P->nlev; ++k) {
     const LevelInfo& lv = P->lev[k];
-    GPW_CF(cufftPlan3d(&P->fft_d2z[k], lv.N[0], lv.N[1], lv.N[2], CUFFT_D2Z));
-    if (cufftPlan3d(&P->fft_z2d[k], lv.N[0], lv.N[1], lv.N[2], CUFFT_Z2D) != CUFFT_SUCCESS) {
-      cufftDestroy(P->fft_d2z[k]);
-      set_error("cufftPlan3d Z2D failed");
-      return GPW_ECUFFT;
-    }
-    P->fft_made[k] = true;
-    size_t ws = 0;
-    cufftGetSize(P->fft_d2z[k], &ws);
-    b += (long long)ws;
-    cufftGetSize(P->fft_z2d[k], &ws);
-    b += (long long)ws;
+    GPW_TRY2(fft_entry(lv.N, CUFFT_D2Z, &P->fft_d2z[k]));
+    GPW_TRY2(fft_entry(lv.N, CUFFT_Z2D, &P->fft_z2d[k]));
+    fws = std::max(fws, std::max(P->fft_d2z[k]->ws, P->fft_z2d[k]->ws));
   }
+  GPW_TRY2(dalloc(&P->fft_work, (long long)((fws + sizeof(double) - 1) / sizeof(double)), &b));
   {
     std::vector<PlanView> v(1, PlanView());
     P->device_bytes = b;
@@ -226,20 +291,28 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
   P->work_i_host = H.work_i;
   P->device_bytes = b;
   GPW_CK(launch_tables(*P, s));
+  // the plan is complete for every stream when the commit returns
+  GPW_CK(cudaStreamSynchronize(s));
   P->committed = true;
   return GPW_OK;
 }
 #undef GPW_TRY2
 
 int fft_d2z(Plan& P, int k, const double* in, cufftDoubleComplex* out, cudaStream_t s) {
-  GPW_CF(cufftSetStream(P.fft_d2z[k], s));
-  GPW_CF(cufftExecD2Z(P.fft_d2z[k], const_cast<double*>(in), out));
+  FftEntry* e = P.fft_d2z[k];
+  std::lock_guard<std::mutex> lk(e->mu);
+  GPW_CF(cufftSetStream(e->h, s));
+  GPW_CF(cufftSetWorkArea(e->h, P.fft_work));
+  GPW_CF(cufftExecD2Z(e->h, const_cast<double*>(in), out));
   return GPW_OK;
 }
 
 int fft_z2d(Plan& P, int k, cufftDoubleComplex* in, double* out, cudaStream_t s) {
-  GPW_CF(cufftSetStream(P.fft_z2d[k], s));
-  GPW_CF(cufftExecZ2D(P.fft_z2d[k], in, out));
+  FftEntry* e = P.fft_z2d[k];
+  std::lock_guard<std::mutex> lk(e->mu);
+  GPW_CF(cufftSetStream(e->h, s));
+  GPW_CF(cufftSetWorkArea(e->h, P.fft_work));
+  GPW_CF(cufftExecZ2D(e->h, in, out));
   return GPW_OK;
 }
 
@@ -1096,6 +1169,12 @@ int gpw_profile_read(gpw_plan_t plan, double* ms, long long* count, int nphases,
 void gpw_plan_destroy(gpw_plan_t plan) {
   if (!plan) return;
   gpw::free_plan(&plan->p);
+  delete plan;
+}
+
+void gpw_plan_destroy_async(gpw_plan_t plan, void* stream) {
+  if (!plan) return;
+  gpw::free_plan(&plan->p, (cudaStream_t)stream, false);
   delete plan;
 }
 

@@ -161,9 +161,10 @@ struct Plan {
   bool committed = false;
   struct HostArrays* host = nullptr;       // host staging between prepare and commit
   std::vector<int4> work_c_host, work_i_host;   // copies kept for batch merging
-  cufftHandle fft_d2z[GPW_MAX_LEVELS];
-  cufftHandle fft_z2d[GPW_MAX_LEVELS];
-  bool fft_made[GPW_MAX_LEVELS] = {false};
+  struct FftEntry* fft_d2z[GPW_MAX_LEVELS] = {nullptr};  // shared cuFFT handles (cache)
+  struct FftEntry* fft_z2d[GPW_MAX_LEVELS] = {nullptr};
+  double* fft_work = nullptr;          // this plan's cuFFT work area
+  cudaStream_t alloc_stream = nullptr; // stream of the plan's stream-ordered allocations
   int red_blocks = 0;
   size_t smem_colloc = 0, smem_integ = 0, smem_integ1 = 0;
   // kinetic-energy-density passes (GPW_TAU): collocation at degree L+2, integration at

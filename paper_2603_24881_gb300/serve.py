@@ -212,7 +212,7 @@ class Server:
             g = fl.bufs["g"][i].cpu().numpy() if fl.bufs["g"][i] is not None else None
             res = Result(r.rid, float(E[2 * i]), float(E[2 * i + 1]), V, g, r.t_submit, t,
                          fl.bid, len(fl.reqs), r.t_prepared, r.t_launch)
-            r.plan.close()
+            r.plan.close(stream=fl.stream)  # its batch has finished: no device sync
             r.plan = None
             r.future.set_result(res)
         with self._cv:
