@@ -1,0 +1,88 @@
+"""The host planner of libgpw (gpw_plan_prepare: screening, levels, boxes, task counts)
+on the CPU, no GPU needed: integer pair tables identical to the oracle's independent
+screening, the work counts it reports, and the validation of plan descriptions."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+import systems
+from paper_2603_24881_gb300 import binding
+from paper_2603_24881_gb300.binding import GpwError
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return binding.load()
+
+
+@pytest.mark.parametrize("name", ["tiny", "tiny14", "resolved", "water4", "water32"])
+def test_pair_table_and_counts_match_oracle(lib, name):
+    s = {"tiny": workloads.tiny, "tiny14": systems.tiny14, "resolved": systems.resolved,
+         "water4": lambda: workloads.config("water4"),
+         "water32": lambda: workloads.config("water32")}[name]()
+    p = binding.Plan(s, commit=False)
+    op = oracle.Plan(s)
+    a, b = p.pair_table(), op.pair_table()
+    assert a.shape == b.shape and np.array_equal(a, b), name
+    st = p.stats()
+    assert st["npairs"] == op.npairs and st["pair_points"] == op.pair_points()
+    assert [tuple(m) for m in st["meshes"]] == [tuple(m) for m in op.meshes.tolist()]
+    # model FLOPs: 2 (L+1) per pair-point for rho, 2 (L+2) for the degree-(L+1) pass
+    pts_L = st["pair_points_L"]
+    assert st["flops_rho"] == pytest.approx(sum(2.0 * (L + 1) * n for L, n in enumerate(pts_L)))
+    assert st["flops_ip1"] == pytest.approx(sum(2.0 * (L + 2) * n for L, n in enumerate(pts_L)))
+    assert st["device_bytes"] > 0 and not p.committed
+    p.close()
+
+
+def test_plan_independent_of_thread_count(lib, monkeypatch):
+    # the planner threads over pairs for large cells; its result must not depend on it
+    s = workloads.config("water32")
+    p1 = binding.Plan(s, commit=False)
+    t1, st1 = p1.pair_table(), p1.stats()
+    p1.close()
+    import ctypes.util
+    omp = ctypes.CDLL(ctypes.util.find_library("gomp") or "libgomp.so.1")
+    omp.omp_set_num_threads(1)
+    try:
+        p2 = binding.Plan(s, commit=False)
+        t2, st2 = p2.pair_table(), p2.stats()
+        p2.close()
+    finally:
+        import os
+        omp.omp_set_num_threads(os.cpu_count() or 1)
+    assert np.array_equal(t1, t2)
+    for k in ("nentries", "nentries_integ", "integ_chunk", "device_bytes", "pair_points"):
+        assert st1[k] == st2[k], k
+
+
+def _expect_error(s, **kw):
+    with pytest.raises((GpwError, ValueError)):
+        binding.Plan(s, commit=False, **kw)
+
+
+def test_validation(lib):
+    s = workloads.tiny()
+    _expect_error(s, tile=(3, 8, 16))                 # no kernels for this shape
+    _expect_error(s, tile=(8, 8, 64))                 # integration-only shape
+    _expect_error(s, colloc_warps=5)
+    _expect_error(s, xc="b88")
+    bad = s.with_tau(s.tau)
+    bad.lattice = bad.lattice.copy()
+    bad.lattice[0, 1] = 0.5                           # not orthorhombic
+    _expect_error(bad)
+    neg = s.with_tau(s.tau)
+    neg.exponents = -np.abs(neg.exponents)            # exponents must be positive
+    _expect_error(neg)
+    f = systems.resolved(seed=8, shells=((0, 1), (3, 1)), natm=2)
+    binding.Plan(f, commit=False).close()             # f shells are fine ...
+    _expect_error(f, tau=True)                        # ... but not for the tau kernels
+
+
+def test_tau_plan_sizes(lib):
+    # GPW_TAU plans carry tables to degree L+3 and larger per-pair buffers
+    s = workloads.tiny()
+    a = binding.Plan(s, commit=False).stats()["device_bytes"]
+    b = binding.Plan(s, commit=False, tau=True).stats()["device_bytes"]
+    assert b > a
