@@ -88,6 +88,9 @@ def _args():
     ap.add_argument("--tile-integ", default=None, help="integration sub-box t0,t1,t2")
     ap.add_argument("--xc", default="lda_x", choices=["lda_x", "pbe_x"],
                     help="exchange functional (LDA Slater or PBE exchange, a GGA)")
+    ap.add_argument("--configs", action="store_true",
+                    help="per-call timings of eval_rho / eval_mat / eval_mat_ip1 / fock_grad "
+                         "on every config (one JSON line each) instead of the bench step")
     ap.add_argument("--tau", action="store_true",
                     help="also time the kinetic-energy-density (meta-GGA) kernels")
     ap.add_argument("--autotune", action="store_true",
@@ -276,12 +279,65 @@ def served_bench(nreq: int) -> dict:
 
 
 # ------------------------------------------------------------------ main -------
+def per_config(a):
+    """Per call, on every config: eval_rho, eval_mat, eval_mat_ip1 (finest-grid potential)
+    and gpw_fock_grad, CUDA events, median of 10 after 3 warm-up calls; model FLOPs
+    (2(L+1) per pair-point for rho and V, 2(L+2) for the gradient pass) per second and
+    pair-points per second."""
+    import numpy as np
+    import torch
+    import workloads
+    import paper_2603_24881_gb300 as gpw
+    gpw.load()
+    for name in ("tiny", "water32", "carbon", "water256"):
+        s = workloads.config(name)
+        plan = gpw.Plan(s)
+        st = plan.stats()
+        D = torch.as_tensor(s.D, device="cuda")
+        v = plan.fock(D, want_v=True)["v"]
+        V = torch.empty((plan.nao, plan.nao), dtype=torch.float64, device="cuda")
+        g = torch.empty((plan.natm, 3), dtype=torch.float64, device="cuda")
+        rho = torch.empty(plan.fine_mesh, dtype=torch.float64, device="cuda")
+        E = torch.empty(2, dtype=torch.float64, device="cuda")
+        calls = {"eval_rho": (lambda: plan.eval_rho(D, out=rho), st["flops_rho"]),
+                 "eval_mat": (lambda: plan.eval_mat(v, out=V), st["flops_mat"]),
+                 "eval_mat_ip1": (lambda: plan.eval_mat_ip1(D, v, out=g), st["flops_ip1"]),
+                 "fock_grad": (lambda: plan.fock_grad_async(D, V, g, E),
+                               st["flops_rho"] + st["flops_ip1"])}
+        res = {}
+        for cname, (fn, fl) in calls.items():
+            for _ in range(3):
+                fn()
+            ts = []
+            for _ in range(10):
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record()
+                fn()
+                e1.record()
+                torch.cuda.synchronize()
+                ts.append(e0.elapsed_time(e1))
+            ms = float(np.median(ts))
+            res[cname] = {"ms": ms, "model_tflops": fl / ms / 1e9,
+                          "pct_fp64_peak": 100.0 * fl / ms / 1e9 / FP64_PEAK_TFLOPS,
+                          "pair_points_per_s": st["pair_points"] / (ms * 1e-3)}
+        err = plan.check_device()
+        print(json.dumps({"config": name, "pairs": st["npairs"], "pair_points": st["pair_points"],
+                          "nao": plan.nao, "meshes": [list(m) for m in st["meshes"]],
+                          "calls": res, "device_check": err}), flush=True)
+        plan.close()
+        torch.cuda.empty_cache()
+
+
 def main():
     from paper_2603_24881_gb300 import replicas
     a = _args()
     rank, world, local = replicas.ranks_from_env()
     if a.impl == "reference":
         run_reference(a, rank, world)
+        return
+    if a.configs:
+        if rank == 0:
+            per_config(a)
         return
     import numpy as np
     import torch
