@@ -63,6 +63,12 @@ extern "C" {
 #define GPW_TAU 1               /* also build the kinetic-energy-density (meta-GGA) data:
                                    1-D tables to degree L+3 and larger per-pair buffers;
                                    shells up to d (gpw_eval_tau, gpw_eval_mat_tau*) */
+#define GPW_HOST_TASKS 2        /* build the sub-box task records and work lists on the
+                                   host in gpw_plan_prepare.  Default: the host only
+                                   counts each pair's tasks and gpw_plan_commit builds
+                                   the records on the device (count per grid block,
+                                   prefix sums, fill: the pair-to-block mapping of the
+                                   paper's appendix); both give identical lists. */
 
 /* Exchange functional (gpw_desc.xc), spin-unpolarised, on the finest grid:
  * GPW_XC_LDA_X  Slater exchange v_x = -(3/pi)^(1/3) rho^(1/3) (Sec. II, LDA);
@@ -101,7 +107,7 @@ typedef struct {
   double rel_cutoff;          /* a pair of exponent alpha_p goes to the coarsest level
                                  with E_k >= rel_cutoff * alpha_p (40 if <= 0) */
   double tau;                 /* screening threshold of Eq. (cut) */
-  int flags;                  /* GPW_STRICT, or GPW_TAU */
+  int flags;                  /* GPW_STRICT, or GPW_TAU | GPW_HOST_TASKS */
   int tile[3];                /* sub-box owned by one collocation thread block (grid
                                  points along a1, a2, a3); {0,0,0} = default {4,8,16} */
   int tile_integ[3];          /* sub-box of one integration thread block;
@@ -112,6 +118,9 @@ typedef struct {
   int integ_chunk;            /* most (pair, sub-box) tasks per integration work item
                                  (> 0); 0 = default max(64, tasks / 1216) */
   int xc;                     /* GPW_XC_LDA_X (0, default) or GPW_XC_PBE_X */
+  int host_threads;           /* most host threads the planner uses (>= 0); 0 = OpenMP's
+                                 default (all cores).  A server planning several cells
+                                 at once on its own threads caps each plan here. */
 } gpw_desc;
 
 /* Sizes and work counts of a plan (gpw_plan_query). */
@@ -175,6 +184,15 @@ int gpw_plan_update_coords(gpw_plan_t plan, const double* coords, void* stream);
  * ab (2 ints: primitive indices a <= b), img (3 ints: T = img . diag(L)), level,
  * lo/hi (3 ints each: integer box on the level mesh, inclusive).  Synchronous. */
 int gpw_plan_pairs(gpw_plan_t plan, int* ab, int* img, int* level, int* lo, int* hi);
+
+/* Copy one task list of a committed plan to host buffers (any may be NULL): integ = 0
+ * the collocation list, 1 the integration list.  *nent tasks (8 ints each: the two int4
+ * records p, m | L << 24, u, rank and t0, t1, t2, W offset), *nsub + 1 sub-box CSR
+ * offsets, *nwork work items (4 ints: plan slot, level | chunk << 4, sub-box, tasks).
+ * The counts are written first, so a call with NULL buffers sizes them.  Synchronises
+ * the device. */
+int gpw_plan_task_lists(gpw_plan_t plan, int integ, long long* nent, long long* nsub,
+                        long long* nwork, int* tasks, long long* sub_off, int* work);
 
 /* Density on the finest grid (Eq. rho_wrap + multigrid Fourier interpolation).
  * D: device, nao x nao symmetric.  rho_fine: device, N0*N1*N2 of level 0 (overwritten). */
@@ -248,8 +266,9 @@ int gpw_fock_grad_async(gpw_plan_t plan, const double* D, double* V, double* gra
                         double* energies_dev, void* stream);
 
 /* Batches: the collocation and integration tasks of several plans (cells) run in one
- * launch each, heaviest sub-boxes first across all plans, instead of one launch per
- * plan; the other steps run per plan on the same stream.  Plans of a batch share their
+ * launch each, instead of one launch per plan: every plan's work list is cut into runs
+ * of consecutive items (neighbouring sub-boxes) and the runs of all plans go by
+ * decreasing mean weight.  The other steps run per plan on the same stream.  Plans of a batch share their
  * sub-box shapes and device.  Results per plan are identical to the plan run alone (the
  * same tasks, in the same order per sub-box, with the same reductions). */
 int gpw_batch_create(int max_plans, gpw_batch_t* out);

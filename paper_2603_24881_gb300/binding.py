@@ -23,6 +23,7 @@ ERRORS = {0: "GPW_OK", -1: "GPW_EINVAL", -2: "GPW_ENOMEM", -3: "GPW_ECUDA", -4: 
           -5: "GPW_ETIMEDOUT", -6: "GPW_EDEVICE", -7: "GPW_ERANGE"}
 
 EXPORTS = ["gpw_plan", "gpw_plan_query", "gpw_plan_update_coords", "gpw_plan_pairs",
+           "gpw_plan_task_lists",
            "gpw_eval_rho", "gpw_eval_rho_levels", "gpw_eval_mat", "gpw_eval_mat_levels",
            "gpw_eval_mat_ip1", "gpw_eval_mat_ip1_levels", "gpw_eval_tau", "gpw_eval_tau_levels",
            "gpw_eval_mat_tau", "gpw_eval_mat_tau_levels", "gpw_eval_mat_tau_ip1",
@@ -52,9 +53,11 @@ class Desc(ctypes.Structure):
                 ("rel_cutoff", ctypes.c_double), ("tau", ctypes.c_double),
                 ("flags", ctypes.c_int), ("tile", ctypes.c_int * 3),
                 ("tile_integ", ctypes.c_int * 3), ("colloc_warps", ctypes.c_int),
-                ("integ_chunk", ctypes.c_int), ("xc", ctypes.c_int)]
+                ("integ_chunk", ctypes.c_int), ("xc", ctypes.c_int),
+                ("host_threads", ctypes.c_int)]
 
 GPW_TAU = 1  # gpw_desc.flags: kinetic-energy-density kernels
+GPW_HOST_TASKS = 2  # gpw_desc.flags: task records built on the host (default: device)
 
 # exchange functionals (gpw_desc.xc)
 XC = {"lda_x": 0, "pbe_x": 1}
@@ -102,6 +105,7 @@ def load(build_if_missing: bool = True):
         L.gpw_plan_query.argtypes = [vp, ctypes.POINTER(Info)]
         L.gpw_plan_update_coords.argtypes = [vp, vp, vp]
         L.gpw_plan_pairs.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.gpw_plan_task_lists.argtypes = [vp, ctypes.c_int, vp, vp, vp, vp, vp, vp]
         L.gpw_eval_rho.argtypes = [vp, vp, vp, vp]
         L.gpw_eval_rho_levels.argtypes = [vp, vp, vp, vp]
         L.gpw_eval_mat.argtypes = [vp, vp, vp, vp]
@@ -178,13 +182,16 @@ class Plan:
     levels, task lists, grids and FFT plans live on the current CUDA device."""
 
     def __init__(self, system, stream=None, tile=None, tile_integ=None, commit=True,
-                 colloc_warps=None, integ_chunk=None, xc="lda_x", tau=False):
+                 colloc_warps=None, integ_chunk=None, xc="lda_x", tau=False, host_threads=0,
+                 host_tasks=False):
         """Prepare the plan on the host (screening, levels, task lists) and, unless
         commit=False, commit it to the current device.  An uncommitted plan reports its
         exact device footprint in stats()["device_bytes"].  tile, tile_integ,
         colloc_warps, integ_chunk: launch shape (library defaults if None); xc: exchange
         functional, "lda_x" (Slater) or "pbe_x" (PBE exchange, a GGA); tau: also build the
-        kinetic-energy-density (meta-GGA) kernels' data (shells up to d)."""
+        kinetic-energy-density (meta-GGA) kernels' data (shells up to d); host_threads:
+        most planner threads (0 = all cores); host_tasks: build the sub-box task lists on
+        the host instead of on the device at commit (identical lists)."""
         self._lib = load()
         s = system
         self.system = s
@@ -214,7 +221,7 @@ class Plan:
         d.meshes = arr(s.meshes, np.int32) if s.meshes is not None else None
         d.rel_cutoff = float(s.rel_cutoff)
         d.tau = float(s.tau)
-        d.flags = GPW_TAU if tau else 0
+        d.flags = (GPW_TAU if tau else 0) | (GPW_HOST_TASKS if host_tasks else 0)
         if tile is not None:
             for i in range(3):
                 d.tile[i] = int(tile[i])
@@ -226,6 +233,7 @@ class Plan:
         if xc not in XC:
             raise ValueError(f"unknown exchange functional {xc!r} (one of {sorted(XC)})")
         d.xc = XC[xc]
+        d.host_threads = int(host_threads)
         h = ctypes.c_void_p()
         check(self._lib.gpw_plan_prepare(ctypes.byref(d), ctypes.byref(h)), "gpw_plan_prepare")
         self._h = h
@@ -288,6 +296,24 @@ class Plan:
                     nentries_integ=i.nentries_integ, colloc_warps=i.colloc_warps,
                     integ_chunk=i.integ_chunk,
                     xc={v: k for k, v in XC.items()}.get(i.xc, i.xc))
+
+    def task_lists(self, integ: bool = False):
+        """One task list of the committed plan (gpw_plan_task_lists): the task records
+        (nent x 8 int32), the sub-box CSR offsets (nsub + 1) and the work items
+        (nwork x 4 int32)."""
+        n, ns, nw = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        it = 1 if integ else 0
+        check(self._lib.gpw_plan_task_lists(self._h, it, ctypes.byref(n), ctypes.byref(ns),
+                                            ctypes.byref(nw), None, None, None),
+              "gpw_plan_task_lists")
+        tasks = np.zeros((n.value, 8), np.int32)
+        sub = np.zeros(ns.value + 1, np.int64)
+        work = np.zeros((nw.value, 4), np.int32)
+        P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
+        check(self._lib.gpw_plan_task_lists(self._h, it, ctypes.byref(n), ctypes.byref(ns),
+                                            ctypes.byref(nw), P(tasks), P(sub), P(work)),
+              "gpw_plan_task_lists")
+        return tasks, sub, work
 
     def pair_table(self) -> np.ndarray:
         """Screened pairs as int64 rows (a, b, n0, n1, n2, level, lo0..2, hi0..2),

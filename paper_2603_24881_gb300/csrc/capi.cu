@@ -167,9 +167,22 @@ long long estimate_bytes(const Plan& P, const HostArrays& H) {
   b += sz((long long)H.hot_a.size(), sizeof(int4)) * 4;                 // hot_a, hot_b, ids, ids2
   b += sz((long long)H.geo.size(), sizeof(double)) + sz(P.npairs, sizeof(double)) * 2;
   b += sz(P.npairs, sizeof(long long)) * 4;
-  b += sz((long long)H.task_c.size(), sizeof(int4)) + sz((long long)H.task_i.size(), sizeof(int4));
-  b += sz((long long)H.sub_off_c.size(), sizeof(long long)) + sz((long long)H.sub_off_i.size(), sizeof(long long));
-  b += sz((long long)H.work_c.size(), sizeof(int4)) + sz((long long)H.work_i.size(), sizeof(int4));
+  if (P.tasks_on_device) {
+    // records and offsets are sized by the counts; the work lists by their bound (a
+    // sub-box holds at most one collocation item and 1 + tasks / chunk integration items)
+    b += sz(2 * P.nent, sizeof(int4)) + sz(2 * P.nent_i, sizeof(int4));
+    b += sz(P.nsub_total + 1, sizeof(long long)) + sz(P.nsub_i + 1, sizeof(long long));
+    const long long wc = std::min(P.nsub_total, P.nent);
+    const long long wi = std::min(P.nsub_i, P.nent_i) + (P.chunk_i > 0 ? P.nent_i / P.chunk_i : 0);
+    b += sz(wc, sizeof(int4)) + sz(wi, sizeof(int4));
+    // build scratch beyond the part buffer, released after the commit
+    b += std::max<long long>(0, task_sort_bytes(P) + 16 * (P.npairs + 1) -
+                                    (long long)sizeof(double) * P.part_total);
+  } else {
+    b += sz((long long)H.task_c.size(), sizeof(int4)) + sz((long long)H.task_i.size(), sizeof(int4));
+    b += sz((long long)H.sub_off_c.size(), sizeof(long long)) + sz((long long)H.sub_off_i.size(), sizeof(long long));
+    b += sz((long long)H.work_c.size(), sizeof(int4)) + sz((long long)H.work_i.size(), sizeof(int4));
+  }
   b += sz((long long)H.groups.size(), sizeof(int4)) + sz((long long)H.atom_off.size(), sizeof(long long));
   b += sz((long long)H.atom_list.size(), sizeof(int));
   b += sz(P.tab_total + P.coef_total + P.part_total + 6 * P.npairs + P.grid_total, sizeof(double));
@@ -213,12 +226,14 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
   GPW_TRY(upload(&d.coef_off, H.coef_off, &b));
   GPW_TRY(upload(&d.part_off, H.part_off, &b));
   GPW_TRY(upload(&d.xt_off, H.xt_off, &b));
-  GPW_TRY(upload(&d.task_c, H.task_c, &b));
-  GPW_TRY(upload(&d.sub_off_c, H.sub_off_c, &b));
-  GPW_TRY(upload(&d.work_c, H.work_c, &b));
-  GPW_TRY(upload(&d.task_i, H.task_i, &b));
-  GPW_TRY(upload(&d.sub_off_i, H.sub_off_i, &b));
-  GPW_TRY(upload(&d.work_i, H.work_i, &b));
+  if (!P->tasks_on_device) {
+    GPW_TRY(upload(&d.task_c, H.task_c, &b));
+    GPW_TRY(upload(&d.sub_off_c, H.sub_off_c, &b));
+    GPW_TRY(upload(&d.work_c, H.work_c, &b));
+    GPW_TRY(upload(&d.task_i, H.task_i, &b));
+    GPW_TRY(upload(&d.sub_off_i, H.sub_off_i, &b));
+    GPW_TRY(upload(&d.work_i, H.work_i, &b));
+  }
   GPW_TRY(upload(&d.groups, H.groups, &b));
   GPW_TRY(upload(&d.atom_off, H.atom_off, &b));
   GPW_TRY(upload(&d.atom_list, H.atom_list, &b));
@@ -233,6 +248,8 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
   GPW_TRY(dalloc(&d.fine_a, P->fine_n, &b));
   GPW_TRY(dalloc(&d.fine_b, P->fine_n, &b));
   GPW_TRY(dalloc(&d.red, 2 * kRedBlocks, &b));
+  // device-built task lists (they may use the part buffer as scratch)
+  if (P->tasks_on_device) GPW_TRY(build_tasks_device(P, H, s, &b));
   {
     // ((2 pi s)/L_d)^2 per finest-mesh index along each axis, s the signed frequency,
     // formed exactly as the reference does: (2 pi s)/L, squared
@@ -262,7 +279,7 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
   }
   GPW_TRY(dalloc(&d.energies, 2, &b));
   GPW_TRY(dalloc(&d.err, 1, &b));
-  GPW_CK(cudaMemset(d.err, 0, sizeof(int)));
+  GPW_CK(cudaMemsetAsync(d.err, 0, sizeof(int), s));
   {
     CoefTables t;
     build_coef_tables(&t);
@@ -773,6 +790,33 @@ int gpw_plan_pairs(gpw_plan_t plan, int* ab, int* img, int* level, int* lo, int*
   return GPW_OK;
 }
 
+int gpw_plan_task_lists(gpw_plan_t plan, int integ, long long* nent, long long* nsub,
+                        long long* nwork, int* tasks, long long* sub_off, int* work) {
+  if (gpw::bad(plan) || !nent || !nsub || !nwork || (integ != 0 && integ != 1)) {
+    if (plan && plan->p.committed) set_error("gpw_plan_task_lists: bad arguments");
+    return GPW_EINVAL;
+  }
+  const gpw::Plan& P = plan->p;
+  *nent = integ ? P.nent_i : P.nent;
+  *nsub = integ ? P.nsub_i : P.nsub_total;
+  *nwork = integ ? P.nwork_i : P.nwork;
+  cudaError_t e = cudaDeviceSynchronize();
+  if (e == cudaSuccess && tasks && *nent)
+    e = cudaMemcpy(tasks, integ ? P.d.task_i : P.d.task_c, sizeof(int4) * 2 * (size_t)*nent,
+                   cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && sub_off)
+    e = cudaMemcpy(sub_off, integ ? P.d.sub_off_i : P.d.sub_off_c,
+                   sizeof(long long) * (size_t)(*nsub + 1), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess && work && *nwork)
+    e = cudaMemcpy(work, integ ? P.d.work_i : P.d.work_c, sizeof(int4) * (size_t)*nwork,
+                   cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) {
+    set_error(std::string("gpw_plan_task_lists: ") + cudaGetErrorString(e));
+    return GPW_ECUDA;
+  }
+  return GPW_OK;
+}
+
 int gpw_eval_rho_levels(gpw_plan_t plan, const double* D, double* const* rho_levels,
                         void* stream) {
   if (gpw::bad(plan) || !D || !rho_levels) return GPW_EINVAL;
@@ -1003,34 +1047,57 @@ int gpw_batch_set(gpw_batch_t b, int nplans, const gpw_plan_t* plans, void* stre
     set_error(std::string("gpw_batch_set: ") + cudaGetErrorString(e));
     return GPW_ECUDA;
   }
-  // views and work lists of all plans, each list merged heaviest first
+  // views, and the work lists of all plans merged band by band: every plan's list is
+  // cut into runs of kBand consecutive items (Morton-local sub-boxes, heaviest first
+  // inside), and the runs of all plans go by decreasing mean tasks per item, so blocks
+  // resident together still share their pairs' tables in L2 and light items come last
   std::vector<gpw::PlanView> views(nplans);
-  std::vector<int4> wc, wi;
-  for (int i = 0; i < nplans; ++i) {
-    views[i] = gpw::make_view(plans[i]->p);
-    for (int4 w : plans[i]->p.work_c_host) wc.push_back(make_int4(i, w.y, w.z, w.w));
-    for (int4 w : plans[i]->p.work_i_host) wi.push_back(make_int4(i, w.y, w.z, w.w));
-  }
-  auto heavy = [](const int4& x, const int4& y) {
-    if (x.w != y.w) return x.w > y.w;
-    if (x.x != y.x) return x.x < y.x;
-    if (x.y != y.y) return x.y < y.y;
-    return x.z < y.z;
+  for (int i = 0; i < nplans; ++i) views[i] = gpw::make_view(plans[i]->p);
+  auto merge = [&](bool integ) {
+    struct Run {
+      double mean;
+      int plan;
+      size_t first, n;
+    };
+    std::vector<Run> runs;
+    size_t total = 0;
+    for (int i = 0; i < nplans; ++i) {
+      const std::vector<int4>& w = integ ? plans[i]->p.work_i_host : plans[i]->p.work_c_host;
+      for (size_t a = 0; a < w.size(); a += (size_t)gpw::kBand) {
+        const size_t n = std::min(w.size() - a, (size_t)gpw::kBand);
+        double sum = 0;
+        for (size_t j = a; j < a + n; ++j) sum += (double)w[j].w;
+        runs.push_back({sum / (double)n, i, a, n});
+      }
+      total += w.size();
+    }
+    std::stable_sort(runs.begin(), runs.end(),
+                     [](const Run& x, const Run& y) { return x.mean > y.mean; });
+    std::vector<int4> out;
+    out.reserve(total);
+    for (const Run& r : runs) {
+      const std::vector<int4>& w = integ ? plans[r.plan]->p.work_i_host : plans[r.plan]->p.work_c_host;
+      for (size_t j = r.first; j < r.first + r.n; ++j)
+        out.push_back(make_int4(r.plan, w[j].y, w[j].z, w[j].w));
+    }
+    return out;
   };
-  std::stable_sort(wc.begin(), wc.end(), heavy);
-  std::stable_sort(wi.begin(), wi.end(), heavy);
+  const std::vector<int4> wc = merge(false), wi = merge(true);
+  cudaStream_t s = (cudaStream_t)stream;
+  // grown in stream order on the batch's stream (the previous launch that read the old
+  // list was enqueued there), so other streams' work is not waited for
   auto ensure = [&](int4** ptr, long long* cap, size_t n) -> cudaError_t {
     if ((long long)n <= *cap) return cudaSuccess;
-    if (*ptr) cudaFree(*ptr);
+    if (*ptr) cudaFreeAsync(*ptr, s);
     *ptr = nullptr;
     *cap = 0;
-    cudaError_t r = cudaMalloc((void**)ptr, sizeof(int4) * std::max<size_t>(n, 1));
-    if (r == cudaSuccess) *cap = (long long)n;
+    const size_t want = std::max<size_t>(n + n / 4, 1);
+    cudaError_t r = cudaMallocAsync((void**)ptr, sizeof(int4) * want, s);
+    if (r == cudaSuccess) *cap = (long long)want;
     return r;
   };
   e = ensure(&b->work_c, &b->cap_c, wc.size());
   if (e == cudaSuccess) e = ensure(&b->work_i, &b->cap_i, wi.size());
-  cudaStream_t s = (cudaStream_t)stream;
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(b->views, views.data(), sizeof(gpw::PlanView) * views.size(),
                         cudaMemcpyHostToDevice, s);

@@ -142,7 +142,8 @@ struct Plan {
   LevelInfo lev[GPW_MAX_LEVELS];     // sub-box fields for the collocation tile
   LevelInfo lev_i[GPW_MAX_LEVELS];   // same levels, sub-box fields for the integration tile
   long long npairs = 0, nent = 0, nwork = 0, nsub_total = 0, ngroups = 0;
-  long long nent_i = 0, nwork_i = 0;
+  long long nent_i = 0, nwork_i = 0, nsub_i = 0;
+  bool tasks_on_device = false;  // task records built on the device at commit
   long long tab_total = 0, coef_total = 0, part_total = 0, xt_total = 0;
   long long grid_total = 0, spec_total = 0, fine_n = 0, fine_spec_n = 0;
   long long pair_points = 0;

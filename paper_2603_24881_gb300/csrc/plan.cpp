@@ -141,6 +141,21 @@ struct Seg {
   int k, j;
 };
 
+// most sub-box segments of one pair box along one axis
+constexpr size_t kSegMax = 512;
+
+// Number of sub-box segments of [lo, hi] along an axis of N points cut into sub-boxes of
+// T (the last one of each period clipped): the cells of the unwrapped axis are numbered
+// g = period * nsb + sub-box, and [lo, hi] meets every cell from g(lo) to g(hi).
+long long nseg(int lo, int hi, int N, int T) {
+  const long long nsb = (N + T - 1) / T;
+  auto g = [&](long long i) {
+    const long long q = floordiv(i, N);
+    return q * nsb + (i - q * N) / T;
+  };
+  return g(hi) - g(lo) + 1;
+}
+
 void segments(int lo, int hi, int N, int T, std::vector<Seg>* out) {
   out->clear();
   long long i = lo;
@@ -181,9 +196,14 @@ std::vector<int4> take_task_buffer(size_t n) {
 
 // Host threads for a loop over n items: all cores for large plans, one for small ones
 // (a server plans several small cells at once on its own threads).
+// gpw_desc.host_threads of the plan being built on this thread (0: no cap)
+thread_local int g_host_threads = 0;
+
 int plan_threads(long long n) {
   if (n < 20000) return 1;
-  return std::max(1, std::min<int>(omp_get_max_threads(), (int)(n / 20000)));
+  int cap = omp_get_max_threads();
+  if (g_host_threads > 0) cap = std::min(cap, g_host_threads);
+  return std::max(1, std::min<int>(cap, (int)(n / 20000)));
 }
 
 std::vector<PairBox> pairs_view(const std::vector<PairTmp>& pairs) {
@@ -290,7 +310,6 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
       }
       // per dimension and segment: packed (m, u, t) fields of the records and the
       // sub-box coordinate, computed once per pair
-      constexpr size_t kSegMax = 512;
       int fm[3][kSegMax], fu[3][kSegMax], ft[3][kSegMax];
       long long fj[3][kSegMax];
       bool big = false;
@@ -342,15 +361,73 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
     return fail;
   }
   *sub_off = count;
-  // work items {plan slot, level | chunk << 4, sub-box, tasks}: with chunk_io a sub-box
-  // with more tasks is cut into items of `chunk` consecutive tasks (integration only:
-  // its tasks write separate slots); *chunk_io < 0 asks for the default size
   long long chunk = 0;
   if (chunk_io) {
-    chunk = *chunk_io >= 0 ? *chunk_io : std::max(kChunkMin, (nent + kChunkDiv - 1) / kChunkDiv);
-    if (chunk > INT32_MAX) chunk = INT32_MAX;
+    chunk = *chunk_io >= 0 ? *chunk_io : default_chunk(nent);
     *chunk_io = chunk;
   }
+  return order_work(K, lev, count, chunk, work, nwork_out);
+}
+
+// The task counts of build_tasks without the records, which the device builds at commit
+// (tasks.cu): sets lev[k].sub_base and *nsub_out, the exclusive prefix sums toff (np + 1)
+// of the pairs' task counts in pair order and *nent_out, and, for the integration shape,
+// each pair's task count (ranks) and W block size (psize).  Same limits as build_tasks.
+int count_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector<int4>& hot_a,
+                const int* T, LevelInfo* lev, long long* nsub_out, std::vector<long long>* toff,
+                long long* nent_out, std::vector<int>* ranks, std::vector<long long>* psize) {
+  const int K = plan->nlev;
+  const long long np = (long long)pairs.size();
+  long long nsub = 0;
+  for (int k = 0; k < K; ++k) {
+    lev[k].sub_base = nsub;
+    nsub += (long long)lev[k].nsb[0] * lev[k].nsb[1] * lev[k].nsb[2];
+  }
+  *nsub_out = nsub;
+  toff->assign(np + 1, 0);
+  if (ranks) ranks->assign(np, 0);
+  if (psize) psize->assign(np, 0);
+  bool bad = false;
+  for (long long p = 0; p < np; ++p) {
+    const PairBox& t = pairs[p];
+    const LevelInfo& lv = lev[t.level];
+    long long ns[3];
+    int n[3];
+    for (int d = 0; d < 3; ++d) {
+      n[d] = t.hi[d] - t.lo[d] + 1;
+      ns[d] = nseg(t.lo[d], t.hi[d], lv.N[d], T[d]);
+      bad = bad || n[d] > 65535 || ns[d] > (long long)kSegMax;
+    }
+    const long long c = ns[0] * ns[1] * ns[2];
+    if (psize) {
+      (*psize)[p] = nc2(hot_a[p].w + 1 + plan->xr) * n[0] * ns[1] * ns[2];
+      bad = bad || (*psize)[p] > INT32_MAX;
+    }
+    if (ranks) (*ranks)[p] = (int)c;
+    (*toff)[p + 1] = (*toff)[p] + c;
+  }
+  if (bad) {
+    set_error("gpw_plan: pair box longer than 65535 grid points, more than 512 sub-box "
+              "segments along one axis, or per-pair task block too large");
+    return GPW_ERANGE;
+  }
+  *nent_out = (*toff)[np];
+  return GPW_OK;
+}
+
+}  // namespace
+
+long long default_chunk(long long nent) {
+  return std::min<long long>(INT32_MAX, std::max(kChunkMin, (nent + kChunkDiv - 1) / kChunkDiv));
+}
+
+// Work list of one task-list shape from its sub-box CSR offsets `count` (nsub + 1):
+// items {plan slot, level | chunk << 4, sub-box, tasks}; with chunk > 0 a sub-box with
+// more tasks is cut into items of `chunk` consecutive tasks (integration only: its tasks
+// write separate slots).
+int order_work(int K, const LevelInfo* lev, const std::vector<long long>& count, long long chunk,
+               std::vector<int4>* work, long long* nwork_out) {
+  const long long nsub = (long long)count.size() - 1;
   // Order: items in Morton order of their sub-box (per level) are cut into bands of
   // kBand items; each band runs heaviest first and bands run by decreasing mean weight.
   // Blocks resident at the same time then work on nearby sub-boxes, whose pairs' factor
@@ -417,8 +494,6 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
   return GPW_OK;
 }
 
-}  // namespace
-
 int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   if (!desc || !plan || !H) {
     set_error("gpw_plan: NULL argument");
@@ -484,7 +559,12 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     return GPW_EINVAL;
   }
   plan->xc = desc->xc;
-  if (desc->flags & ~GPW_TAU) {
+  if (desc->host_threads < 0) {
+    set_error("gpw_plan: host_threads must be >= 0");
+    return GPW_EINVAL;
+  }
+  g_host_threads = desc->host_threads;
+  if (desc->flags & ~(GPW_TAU | GPW_HOST_TASKS)) {
     set_error("gpw_plan: unknown flags");
     return GPW_EINVAL;
   }
@@ -783,9 +863,17 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   // for the collocation tile and for the integration tile
   std::vector<int> ranks;
   std::vector<long long> psize;
-  int rc = build_tasks(plan, pairs_view(pairs), H->hot_a, plan->tile, plan->lev, &H->sub_off_c,
-                       &H->task_c, &H->work_c, &plan->nent, &plan->nwork, &plan->nsub_total,
-                       nullptr, nullptr, nullptr);
+  // by default only the per-pair task counts are taken here and the device builds the
+  // records at commit; GPW_HOST_TASKS builds them on the host
+  const bool host_tasks = (desc->flags & GPW_HOST_TASKS) != 0;
+  plan->tasks_on_device = !host_tasks;
+  const std::vector<PairBox> pv = pairs_view(pairs);
+  int rc = host_tasks
+               ? build_tasks(plan, pv, H->hot_a, plan->tile, plan->lev, &H->sub_off_c, &H->task_c,
+                             &H->work_c, &plan->nent, &plan->nwork, &plan->nsub_total, nullptr,
+                             nullptr, nullptr)
+               : count_tasks(plan, pv, H->hot_a, plan->tile, plan->lev, &plan->nsub_total,
+                             &H->toff_c, &plan->nent, nullptr, nullptr);
   if (rc) return rc;
   for (int k = 0; k < K; ++k) plan->lev_i[k] = plan->lev[k];
   for (int k = 0; k < K; ++k)
@@ -795,10 +883,16 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   // integration chunks (auto): about four items per resident block of the whole launch,
   // so that no sub-box with many tasks is left running alone at the end
   long long chunk = desc->integ_chunk > 0 ? desc->integ_chunk : -1;
-  rc = build_tasks(plan, pairs_view(pairs), H->hot_a, plan->tile_i, plan->lev_i, &H->sub_off_i,
-                   &H->task_i, &H->work_i, &plan->nent_i, &plan->nwork_i, &nsub_i, &ranks,
-                   &psize, &chunk);
+  if (host_tasks) {
+    rc = build_tasks(plan, pv, H->hot_a, plan->tile_i, plan->lev_i, &H->sub_off_i, &H->task_i,
+                     &H->work_i, &plan->nent_i, &plan->nwork_i, &nsub_i, &ranks, &psize, &chunk);
+  } else {
+    rc = count_tasks(plan, pv, H->hot_a, plan->tile_i, plan->lev_i, &nsub_i, &H->toff_i,
+                     &plan->nent_i, &ranks, &psize);
+    if (chunk < 0) chunk = default_chunk(plan->nent_i);
+  }
   plan->chunk_i = (int)chunk;
+  plan->nsub_i = nsub_i;
   if (rc) return rc;
   long long part_total = 0;
   for (long long p = 0; p < np; ++p) {

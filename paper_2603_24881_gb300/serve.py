@@ -3,9 +3,11 @@
 Requests (a cell + its density matrix, optionally asking for the gradient) arrive at any
 time.  Each one is planned on a host thread (gpw_plan_prepare: screening and task lists
 on the CPU, which also yields the exact device footprint).  A GPU thread admits prepared
-requests in arrival order while their footprints fit the device-memory budget, commits
-their plans, and launches them together as one batch (gpw_batch_fock_grad_async: one
-collocation and one integration launch for all cells of the batch).  Up to `streams`
+requests in arrival order while their footprints fit the device-memory budget; commit
+threads upload each admitted plan and its density matrix on their own streams; the GPU
+thread launches committed requests together as one batch (gpw_batch_fock_grad_async:
+one collocation and one integration launch for all cells of the batch), and a finisher
+thread copies results back and releases each plan in stream order.  Up to `streams`
 batches are in flight at once on separate CUDA streams, so requests that arrive while
 others run are admitted into the next batch as soon as slots and memory free up, and
 their work overlaps on the device.  Each request's plan, pair lists and grids stay on the
@@ -60,6 +62,7 @@ class _Req:
     error: BaseException | None = None
     t_prepared: float = 0.0
     t_launch: float = 0.0
+    bufs: dict | None = None  # device D, V, grad of the request (after commit)
 
 
 @dataclass
@@ -78,7 +81,8 @@ class Server:
 
     hbm_budget: device bytes the plans and buffers of admitted requests may use at once
     (default: 70% of the free device memory at start).  max_batch: most requests per
-    batch.  streams: batches in flight.  host_workers: planning threads.  tile,
+    batch.  streams: batches in flight.  host_workers: planning threads (default half
+    the cores, each plan using cores / host_workers threads).  tile,
     tile_integ, colloc_warps, integ_chunk: launch shape of every plan (library defaults
     if None); tune_with: a list of sample cells to run the autotuner on (as one batch)
     instead, its choice (cached per GPU and workload class) then serves every request.
@@ -101,10 +105,21 @@ class Server:
             self.choice = tune(list(tune_with))
             self.plan_kwargs = self.choice.plan_kwargs()
         self._fail_prepare = fail_prepare  # test hook: callable(system) -> bool
-        self._pool = cf.ThreadPoolExecutor(host_workers or max(2, (os.cpu_count() or 4)))
+        # planning threads, each plan capped at an equal share of the cores so that the
+        # planners' thread teams do not oversubscribe the host the GPU threads run on
+        cores = os.cpu_count() or 4
+        workers = host_workers or max(2, cores // 2)
+        self.plan_kwargs["host_threads"] = max(1, cores // workers)
+        self._pool = cf.ThreadPoolExecutor(workers, thread_name_prefix="gpw-plan")
+        self._commits = cf.ThreadPoolExecutor(4, thread_name_prefix="gpw-commit")
+        self._finisher = cf.ThreadPoolExecutor(2, thread_name_prefix="gpw-finish")
+        self._tls = threading.local()
         self._streams = [torch.cuda.Stream() for _ in range(max(1, streams))]
         self._batches = [Batch(self.max_batch) for _ in self._streams]
-        self._ready = collections.deque()
+        self._ready = collections.deque()    # prepared, waiting for admission
+        self._staged = collections.deque()   # committed, waiting for a batch
+        self._committing = 0
+        self._finishing = 0
         self._flights: list[_Flight] = []
         self._used = 0
         self._rid = 0
@@ -133,6 +148,8 @@ class Server:
             self._stop = True
             self._cv.notify_all()
         self._gpu.join()
+        self._commits.shutdown(wait=True)
+        self._finisher.shutdown(wait=True)
         for b in self._batches:
             b.close()
 
@@ -161,62 +178,98 @@ class Server:
 
     # -------------------------------------------------------------- GPU side --
     def _admit(self):
-        """Take prepared requests in arrival order while they fit the memory budget."""
-        out = []
-        while self._ready and len(out) < self.max_batch:
+        """Admit prepared requests in arrival order while they fit the memory budget and
+        hand them to the commit threads (called with the lock held)."""
+        while self._ready:
             req = self._ready[0]
             if req.error is not None:
                 self._ready.popleft()
                 self.stats["rejected"] += 1
                 req.future.set_exception(req.error)
                 continue
-            if self._used + req.bytes > self.budget and (out or self._flights):
+            busy = self._flights or self._staged or self._committing or self._finishing
+            if self._used + req.bytes > self.budget and busy:
                 break
             self._ready.popleft()
             self._used += req.bytes
-            out.append(req)
-        return out
+            self.stats["peak_bytes"] = max(self.stats["peak_bytes"], self._used)
+            self._committing += 1
+            self._commits.submit(self._commit, req)
+
+    def _commit(self, req: _Req):
+        """Commit thread: the plan and the request's buffers on this thread's stream."""
+        torch = self.torch
+        st = getattr(self._tls, "stream", None)
+        if st is None:
+            # high priority: the plan's table kernel takes SMs as soon as blocks of the
+            # running batches retire instead of queueing behind them
+            st = self._tls.stream = torch.cuda.Stream(priority=-1)
+        try:
+            with torch.cuda.stream(st):
+                req.plan.commit(st)
+                D = torch.as_tensor(np.ascontiguousarray(req.system.D), device="cuda")
+                V = torch.empty((req.plan.nao, req.plan.nao), dtype=torch.float64, device="cuda")
+                g = (torch.empty((req.plan.natm, 3), dtype=torch.float64, device="cuda")
+                     if req.want_grad else None)
+            st.synchronize()
+            req.bufs = dict(D=D, V=V, g=g)
+            ok = True
+        except BaseException as ex:
+            ok = False
+            err = ex
+        with self._cv:
+            self._committing -= 1
+            if ok:
+                self._staged.append(req)
+            else:
+                self._used -= req.bytes
+                self.stats["rejected"] += 1
+            self._cv.notify_all()
+        if not ok:
+            if req.plan is not None:
+                req.plan.close()
+                req.plan = None
+            req.future.set_exception(err)
 
     def _launch(self, reqs, slot: int):
         torch = self.torch
         stream = self._streams[slot]
         batch = self._batches[slot]
-        bufs = dict(D=[], V=[], g=[], E=None)
         t = time.perf_counter()
         for r in reqs:
             r.t_launch = t
+            for x in r.bufs.values():
+                if x is not None:
+                    x.record_stream(stream)  # the allocator keeps them until this batch ends
         with torch.cuda.stream(stream):
-            for r in reqs:
-                r.plan.commit(stream)
-                bufs["D"].append(torch.as_tensor(np.ascontiguousarray(r.system.D), device="cuda"))
-                bufs["V"].append(torch.empty((r.plan.nao, r.plan.nao), dtype=torch.float64, device="cuda"))
-                bufs["g"].append(torch.empty((r.plan.natm, 3), dtype=torch.float64, device="cuda")
-                                 if r.want_grad else None)
-            bufs["E"] = torch.empty(2 * len(reqs), dtype=torch.float64, device="cuda")
+            E = torch.empty(2 * len(reqs), dtype=torch.float64, device="cuda")
             batch.set([r.plan for r in reqs], stream)
-            batch.fock_grad_async(bufs["D"], bufs["V"], bufs["g"], bufs["E"], stream)
+            batch.fock_grad_async([r.bufs["D"] for r in reqs], [r.bufs["V"] for r in reqs],
+                                  [r.bufs["g"] for r in reqs], E, stream)
             ev = torch.cuda.Event()
             ev.record(stream)
         self.stats["batches"] += 1
         self.stats["admitted"] += len(reqs)
         bid = self._bid
         self._bid += 1
-        return _Flight(bid, reqs, stream, ev, bufs, batch, sum(r.bytes for r in reqs))
+        return _Flight(bid, reqs, stream, ev, dict(E=E), batch, sum(r.bytes for r in reqs))
 
     def _complete(self, fl: _Flight):
-        fl.event.synchronize()
+        """Finisher thread: copy the results of a finished batch back and release plans."""
         E = fl.bufs["E"].cpu().numpy()
         t = time.perf_counter()
         for i, r in enumerate(fl.reqs):
-            V = fl.bufs["V"][i].cpu().numpy()
-            g = fl.bufs["g"][i].cpu().numpy() if fl.bufs["g"][i] is not None else None
+            V = r.bufs["V"].cpu().numpy()
+            g = r.bufs["g"].cpu().numpy() if r.bufs["g"] is not None else None
             res = Result(r.rid, float(E[2 * i]), float(E[2 * i + 1]), V, g, r.t_submit, t,
                          fl.bid, len(fl.reqs), r.t_prepared, r.t_launch)
             r.plan.close(stream=fl.stream)  # its batch has finished: no device sync
             r.plan = None
+            r.bufs = None
             r.future.set_result(res)
         with self._cv:
             self._used -= fl.nbytes
+            self._finishing -= 1
             self._cv.notify_all()
 
     def _free_slot(self):
@@ -227,24 +280,31 @@ class Server:
         return None
 
     def _gpu_loop(self):
-        torch = self.torch
         while True:
-            # retire finished batches first: frees memory and slots for new arrivals
+            # hand finished batches to the finisher: frees their stream slots at once
             done = [f for f in self._flights if f.event.query()]
-            for f in done:
-                self._flights.remove(f)
-                self._complete(f)
             with self._cv:
+                for f in done:
+                    self._flights.remove(f)
+                    self._finishing += 1
+            for f in done:
+                self._finisher.submit(self._complete, f)
+            reqs, slot = [], None
+            with self._cv:
+                self._admit()
                 slot = self._free_slot()
-                reqs = self._admit() if slot is not None else []
+                if slot is not None:
+                    while self._staged and len(reqs) < self.max_batch:
+                        reqs.append(self._staged.popleft())
                 if not reqs:
-                    if self._stop and not self._ready and not self._flights:
+                    idle = not (self._ready or self._staged or self._committing or
+                                self._flights or self._finishing)
+                    if self._stop and idle:
                         return
                     if not self._flights:
-                        self._cv.wait(timeout=0.05)
+                        self._cv.wait(timeout=0.005)
                         continue
             if reqs:
-                self.stats["peak_bytes"] = max(self.stats["peak_bytes"], self._used)
                 try:
                     fl = self._launch(reqs, slot)
                     self._flights.append(fl)
@@ -257,9 +317,12 @@ class Server:
                             r.plan.close()
                         r.future.set_exception(ex)
             elif self._flights:
-                # wait for the oldest batch (with a bound, to keep admitting arrivals)
+                # wait briefly for the oldest batch, staying responsive to new arrivals
                 t0 = time.perf_counter()
                 while not self._flights[0].event.query() and time.perf_counter() - t0 < 0.002:
+                    with self._cv:
+                        if self._staged and self._free_slot() is not None:
+                            break
                     time.sleep(0.0002)
 
 

@@ -34,6 +34,13 @@ def test_pair_table_and_counts_match_oracle(lib, name):
     assert st["flops_ip1"] == pytest.approx(sum(2.0 * (L + 2) * n for L, n in enumerate(pts_L)))
     assert st["device_bytes"] > 0 and not p.committed
     p.close()
+    # the host-built task lists (GPW_HOST_TASKS) count the same tasks as the per-pair
+    # counts the device build starts from
+    h = binding.Plan(s, commit=False, host_tasks=True)
+    sh = h.stats()
+    h.close()
+    for k in ("nentries", "nentries_integ", "integ_chunk", "npairs", "pair_points"):
+        assert sh[k] == st[k], (name, k)
 
 
 def test_plan_independent_of_thread_count(lib, monkeypatch):
@@ -52,9 +59,12 @@ def test_plan_independent_of_thread_count(lib, monkeypatch):
     finally:
         import os
         omp.omp_set_num_threads(os.cpu_count() or 1)
-    assert np.array_equal(t1, t2)
+    p3 = binding.Plan(s, commit=False, host_threads=2)  # the per-plan cap of a server
+    t3, st3 = p3.pair_table(), p3.stats()
+    p3.close()
+    assert np.array_equal(t1, t2) and np.array_equal(t1, t3)
     for k in ("nentries", "nentries_integ", "integ_chunk", "device_bytes", "pair_points"):
-        assert st1[k] == st2[k], k
+        assert st1[k] == st2[k] == st3[k], k
 
 
 def _expect_error(s, **kw):
@@ -68,6 +78,7 @@ def test_validation(lib):
     _expect_error(s, tile=(8, 8, 64))                 # integration-only shape
     _expect_error(s, colloc_warps=5)
     _expect_error(s, xc="b88")
+    _expect_error(s, host_threads=-1)
     bad = s.with_tau(s.tau)
     bad.lattice = bad.lattice.copy()
     bad.lattice[0, 1] = 0.5                           # not orthorhombic
