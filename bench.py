@@ -60,7 +60,7 @@ def _workload_desc(name: str, system, stats) -> str:
 # csrc/kernels.cu + csrc/plan.cpp at capture time.
 TRAFFIC = {
     # integration at degree L+1 (8x8x32 sub-box), water256, one launch: read + write
-    "integrate_ip1": {"bytes_per_launch": 1.7989e10, "src_sha": "553009c19fab1b7a",
+    "integrate_ip1": {"bytes_per_launch": 1.7982e10, "src_sha": "497a9e5dc44092fe",
                       "capture": "profiles/launches_water256_fock_grad.md"},
 }
 

@@ -388,6 +388,8 @@ int count_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
   if (ranks) ranks->assign(np, 0);
   if (psize) psize->assign(np, 0);
   bool bad = false;
+  const int nthr = plan_threads(np);
+#pragma omp parallel for num_threads(nthr) schedule(static) reduction(|| : bad)
   for (long long p = 0; p < np; ++p) {
     const PairBox& t = pairs[p];
     const LevelInfo& lv = lev[t.level];
@@ -404,8 +406,9 @@ int count_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
       bad = bad || (*psize)[p] > INT32_MAX;
     }
     if (ranks) (*ranks)[p] = (int)c;
-    (*toff)[p + 1] = (*toff)[p] + c;
+    (*toff)[p + 1] = c;
   }
+  for (long long p = 0; p < np; ++p) (*toff)[p + 1] += (*toff)[p];
   if (bad) {
     set_error("gpw_plan: pair box longer than 65535 grid points, more than 512 sub-box "
               "segments along one axis, or per-pair task block too large");
@@ -773,16 +776,33 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
       std::vector<PairTmp>().swap(v);
     }
   }
-  // deterministic order: contracted shell pair, then primitives, then image
-  std::sort(pairs.begin(), pairs.end(), [](const PairTmp& x, const PairTmp& y) {
-    if (x.sa != y.sa) return x.sa < y.sa;
-    if (x.sb != y.sb) return x.sb < y.sb;
-    if (x.a != y.a) return x.a < y.a;
-    if (x.b != y.b) return x.b < y.b;
-    for (int d = 0; d < 3; ++d)
-      if (x.img[d] != y.img[d]) return x.img[d] < y.img[d];
-    return false;
-  });
+  // deterministic order: contracted shell pair, then primitives, then image.  The keys
+  // are unique, so the order does not depend on how it is reached: the pairs are
+  // bucketed by their first shell and the buckets sorted in parallel.
+  {
+    auto less = [](const PairTmp& x, const PairTmp& y) {
+      if (x.sa != y.sa) return x.sa < y.sa;
+      if (x.sb != y.sb) return x.sb < y.sb;
+      if (x.a != y.a) return x.a < y.a;
+      if (x.b != y.b) return x.b < y.b;
+      for (int d = 0; d < 3; ++d)
+        if (x.img[d] != y.img[d]) return x.img[d] < y.img[d];
+      return false;
+    };
+    const int nsh = desc->nshell;
+    std::vector<long long> boff(nsh + 1, 0);
+    for (const PairTmp& t : pairs) boff[t.sa + 1]++;
+    for (int i = 0; i < nsh; ++i) boff[i + 1] += boff[i];
+    std::vector<PairTmp> sorted(pairs.size());
+    {
+      std::vector<long long> fill(boff.begin(), boff.end() - 1);
+      for (const PairTmp& t : pairs) sorted[fill[t.sa]++] = t;
+    }
+    const int sthr2 = plan_threads((long long)pairs.size());
+#pragma omp parallel for num_threads(sthr2) schedule(dynamic, 4)
+    for (int i = 0; i < nsh; ++i) std::sort(sorted.begin() + boff[i], sorted.begin() + boff[i + 1], less);
+    pairs.swap(sorted);
+  }
   const long long np = (long long)pairs.size();
   plan->npairs = np;
   if (np > (1LL << 31) - 1) {
@@ -808,14 +828,14 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   plan->h_hi.resize(3 * np);
   plan->pair_a.resize(np);
   plan->pair_b.resize(np);
-  long long tab_total = 0, coef_total = 0, xt_total = 0;
-  int lmax = 0;
+  // per-pair records in parallel, then the offsets and statistics in pair order
+  const int pthr = plan_threads(np);
+#pragma omp parallel for num_threads(pthr) schedule(static)
   for (long long p = 0; p < np; ++p) {
     const PairTmp& t = pairs[p];
     const Prim& pa = prims[t.a];
     const Prim& pb = prims[t.b];
-    int L = pa.l + pb.l;
-    lmax = std::max(lmax, L);
+    const int L = pa.l + pb.l;
     int n[3];
     for (int d = 0; d < 3; ++d) n[d] = t.hi[d] - t.lo[d] + 1;
     H->hot_a[p] = make_int4(t.lo[0], t.lo[1], t.lo[2], L);
@@ -829,20 +849,6 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     H->geo[8 * p + 6] = pa.alpha;
     H->geo[8 * p + 7] = pb.alpha;
     H->cab[p] = pa.cn * pb.cn;
-    H->tab_off[p] = tab_total;
-    tab_total += (long long)(L + 2 + plan->xr) * (n[0] + n[1] + n[2]);
-    H->coef_off[p] = coef_total;
-    coef_total += nc3(L + 1 + plan->xr);
-    H->xt_off[p] = xt_total;
-    xt_total += (long long)nc2(L + plan->xr) * n[0];
-    long long pts = (long long)n[0] * n[1] * n[2];
-    plan->pair_points += pts;
-    plan->pair_points_level[t.level] += pts;
-    plan->pair_points_L[L] += pts;
-    plan->npairs_level[t.level] += 1;
-    plan->flops_rho += 2.0 * (L + 1) * (double)pts;
-    plan->flops_mat += 2.0 * (L + 1) * (double)pts;
-    plan->flops_ip1 += 2.0 * (L + 2) * (double)pts;
     plan->h_ab[2 * p] = t.a;
     plan->h_ab[2 * p + 1] = t.b;
     plan->pair_a[p] = t.a;
@@ -853,6 +859,27 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
       plan->h_hi[3 * p + d] = t.hi[d];
     }
     plan->h_lev[p] = t.level;
+  }
+  long long tab_total = 0, coef_total = 0, xt_total = 0;
+  int lmax = 0;
+  for (long long p = 0; p < np; ++p) {
+    const int L = H->hot_a[p].w, lev = H->hot_b[p].w;
+    const int n[3] = {H->hot_b[p].x, H->hot_b[p].y, H->hot_b[p].z};
+    lmax = std::max(lmax, L);
+    H->tab_off[p] = tab_total;
+    tab_total += (long long)(L + 2 + plan->xr) * (n[0] + n[1] + n[2]);
+    H->coef_off[p] = coef_total;
+    coef_total += nc3(L + 1 + plan->xr);
+    H->xt_off[p] = xt_total;
+    xt_total += (long long)nc2(L + plan->xr) * n[0];
+    long long pts = (long long)n[0] * n[1] * n[2];
+    plan->pair_points += pts;
+    plan->pair_points_level[lev] += pts;
+    plan->pair_points_L[L] += pts;
+    plan->npairs_level[lev] += 1;
+    plan->flops_rho += 2.0 * (L + 1) * (double)pts;
+    plan->flops_mat += 2.0 * (L + 1) * (double)pts;
+    plan->flops_ip1 += 2.0 * (L + 2) * (double)pts;
   }
   plan->lmax = lmax;
   plan->tab_total = tab_total;

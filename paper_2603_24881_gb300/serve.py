@@ -82,7 +82,7 @@ class Server:
     hbm_budget: device bytes the plans and buffers of admitted requests may use at once
     (default: 70% of the free device memory at start).  max_batch: most requests per
     batch.  streams: batches in flight.  host_workers: planning threads (default half
-    the cores, each plan using cores / host_workers threads).  tile,
+    the cores; each plan uses its share of the cores among the plans being made).  tile,
     tile_integ, colloc_warps, integ_chunk: launch shape of every plan (library defaults
     if None); tune_with: a list of sample cells to run the autotuner on (as one batch)
     instead, its choice (cached per GPU and workload class) then serves every request.
@@ -105,11 +105,12 @@ class Server:
             self.choice = tune(list(tune_with))
             self.plan_kwargs = self.choice.plan_kwargs()
         self._fail_prepare = fail_prepare  # test hook: callable(system) -> bool
-        # planning threads, each plan capped at an equal share of the cores so that the
-        # planners' thread teams do not oversubscribe the host the GPU threads run on
-        cores = os.cpu_count() or 4
-        workers = host_workers or max(2, cores // 2)
-        self.plan_kwargs["host_threads"] = max(1, cores // workers)
+        # planning threads; each plan takes an equal share of the cores among the plans
+        # being made at its start, so that the planners' thread teams do not oversubscribe
+        # the host the GPU threads run on, and a large cell planned alone gets them all
+        self._cores = os.cpu_count() or 4
+        workers = host_workers or max(2, self._cores // 2)
+        self._planning = 0
         self._pool = cf.ThreadPoolExecutor(workers, thread_name_prefix="gpw-plan")
         self._commits = cf.ThreadPoolExecutor(4, thread_name_prefix="gpw-commit")
         self._finisher = cf.ThreadPoolExecutor(2, thread_name_prefix="gpw-finish")
@@ -161,10 +162,13 @@ class Server:
 
     # ------------------------------------------------------------- host side --
     def _prepare(self, req: _Req):
+        with self._cv:
+            self._planning += 1
+            share = max(1, self._cores // self._planning)
         try:
             if self._fail_prepare and self._fail_prepare(req.system):
                 raise RuntimeError("plan preparation failed (injected)")
-            req.plan = Plan(req.system, commit=False, **self.plan_kwargs)
+            req.plan = Plan(req.system, commit=False, host_threads=share, **self.plan_kwargs)
             nao, natm = req.plan.nao, req.plan.natm
             req.bytes = int(req.plan.stats()["device_bytes"]) + 8 * (2 * nao * nao + 3 * natm + 2)
             if req.bytes > self.budget:
@@ -173,6 +177,7 @@ class Server:
             req.error = ex
         req.t_prepared = time.perf_counter()
         with self._cv:
+            self._planning -= 1
             self._ready.append(req)
             self._cv.notify_all()
 
