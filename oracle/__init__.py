@@ -53,6 +53,9 @@ def _lib():
             L.orc_rcut.restype = ctypes.c_double
             L.orc_rcut.argtypes = [ctypes.c_double, ctypes.c_int, ctypes.c_double, ctypes.c_double]
             L.orc_pairs.restype = ctypes.c_long
+            L.orc_pairs_lat.restype = ctypes.c_long
+            L.orc_volume.restype = ctypes.c_double
+            L.orc_volume.argtypes = [ctypes.c_void_p]
             L.orc_collocate.restype = None
             L.orc_integrate.restype = None
             L.orc_rho_points.restype = None
@@ -135,15 +138,36 @@ def _smooth7_even(n: int) -> int:
         m += 1
 
 
+def is_orthorhombic(lattice) -> bool:
+    lat = np.asarray(lattice, dtype=np.float64)
+    return bool(np.all(lat == np.diag(np.diag(lat))))
+
+
+def lattice_lengths(lattice):
+    """|R_d| of the lattice rows (the diagonal of an orthorhombic lattice, exactly)."""
+    lat = np.asarray(lattice, dtype=np.float64)
+    if is_orthorhombic(lat):
+        return np.diag(lat).astype(np.float64)
+    return np.sqrt(np.sum(lat * lat, axis=1))
+
+
+def reciprocal(lattice):
+    """Rows b_d with b_d . R_e = delta_de (no 2 pi): the fractional coordinate of r
+    along R_d is b_d . r."""
+    lat = np.asarray(lattice, dtype=np.float64)
+    return np.ascontiguousarray(np.linalg.inv(lat).T)
+
+
 def level_grids(sys):
     """Level meshes and cutoffs (Sec. II multigrid; constants are readings).
 
-    With explicit meshes: E_k = G_k^2 / 2 with G_k = min_d 2 pi floor((N_kd - 1)/2) / L_d.
+    With explicit meshes: E_k = G_k^2 / 2 with G_k = min_d 2 pi floor((N_kd - 1)/2) / |R_d|.
     Otherwise E_k = E_cut / ratio^k and N_kd = smallest even 7-smooth integer
-    >= 2 ceil(G_k L_d / 2 pi) + 1, G_k = sqrt(2 E_k).  Returns (meshes (K,3),
-    E (K,), G (K,)).
+    >= 2 ceil(G_k |R_d| / 2 pi) + 1, G_k = sqrt(2 E_k): every plane wave with |G| < G_k,
+    G = 2 pi sum_d m_d b_d, has |m_d| = |G . R_d| / 2 pi <= (N_kd - 1) / 2.  For an
+    orthorhombic cell |R_d| = L_d.  Returns (meshes (K,3), E (K,), G (K,)).
     """
-    L = np.diag(sys.lattice).astype(np.float64)
+    L = lattice_lengths(sys.lattice)
     K = int(sys.nlevels)
     meshes = np.zeros((K, 3), dtype=np.int32)
     E = np.zeros(K)
@@ -165,10 +189,20 @@ def level_grids(sys):
     return meshes, E, G
 
 
-def gvectors(mesh, L):
-    """|G|^2 on the full FFT grid of `mesh` (numpy fftfreq order), orthorhombic."""
-    g = [2.0 * np.pi * np.fft.fftfreq(int(mesh[d]), d=1.0 / int(mesh[d])) / L[d] for d in range(3)]
-    return (g[0][:, None, None] ** 2 + g[1][None, :, None] ** 2 + g[2][None, None, :] ** 2)
+def gvectors(mesh, lattice):
+    """|G|^2 on the full FFT grid of `mesh` (numpy fftfreq order).  `lattice` is the
+    3 x 3 lattice (rows R_d) or, for an orthorhombic cell, its three lengths:
+    G = 2 pi sum_d m_d b_d with the reciprocal rows b_d."""
+    lat = np.asarray(lattice, dtype=np.float64)
+    if lat.ndim == 1 or is_orthorhombic(lat):
+        L = lat if lat.ndim == 1 else np.diag(lat)
+        g = [2.0 * np.pi * np.fft.fftfreq(int(mesh[d]), d=1.0 / int(mesh[d])) / L[d] for d in range(3)]
+        return (g[0][:, None, None] ** 2 + g[1][None, :, None] ** 2 + g[2][None, None, :] ** 2)
+    B = reciprocal(lat)
+    m = [np.fft.fftfreq(int(mesh[d]), d=1.0 / int(mesh[d])) for d in range(3)]
+    G = [2.0 * np.pi * (m[0][:, None, None] * B[0, c] + m[1][None, :, None] * B[1, c] +
+                        m[2][None, None, :] * B[2, c]) for c in range(3)]
+    return G[0] ** 2 + G[1] ** 2 + G[2] ** 2
 
 
 def _freq_index(mesh):
@@ -222,9 +256,11 @@ class Plan:
 
     def __init__(self, sys, prims=None):
         self.sys = sys
-        self.L = np.ascontiguousarray(np.diag(sys.lattice).astype(np.float64))
-        if not np.allclose(sys.lattice, np.diag(self.L)):
-            raise ValueError("oracle supports orthorhombic cells only")
+        self.lat = np.ascontiguousarray(np.asarray(sys.lattice, dtype=np.float64).reshape(3, 3))
+        self.ortho = is_orthorhombic(self.lat)
+        # orthorhombic lengths (the meta-GGA and GGA steps are orthorhombic only)
+        self.L = np.ascontiguousarray(np.diag(self.lat).astype(np.float64))
+        self.omega = float(np.prod(self.L)) if self.ortho else float(_lib().orc_volume(_p(self.lat)))
         self.prims = prims or primitives(sys)
         self.meshes, self.E, self.G = level_grids(sys)
         self.nlev = len(self.E)
@@ -248,11 +284,21 @@ class Plan:
             lo = np.zeros((cap, 3), np.int32)
             hi = np.zeros((cap, 3), np.int32)
             R = np.zeros(cap)
-            n = lib.orc_pairs(ctypes.c_int(len(pr["l"])), _p(pr["center"]), _p(pr["l"]),
-                              _p(pr["alpha"]), _p(pr["cn"]), _p(self.rcut), _p(self.L),
-                              ctypes.c_int(self.nlev), _p(self.meshes), _p(self.E),
-                              ctypes.c_double(self.sys.rel_cutoff), ctypes.c_double(self.sys.tau),
-                              ctypes.c_long(cap), _p(ab), _p(img), _p(lev), _p(lo), _p(hi), _p(R))
+            if self.ortho:
+                n = lib.orc_pairs(ctypes.c_int(len(pr["l"])), _p(pr["center"]), _p(pr["l"]),
+                                  _p(pr["alpha"]), _p(pr["cn"]), _p(self.rcut), _p(self.L),
+                                  ctypes.c_int(self.nlev), _p(self.meshes), _p(self.E),
+                                  ctypes.c_double(self.sys.rel_cutoff),
+                                  ctypes.c_double(self.sys.tau), ctypes.c_long(cap), _p(ab),
+                                  _p(img), _p(lev), _p(lo), _p(hi), _p(R))
+            else:
+                rec = reciprocal(self.lat)
+                n = lib.orc_pairs_lat(ctypes.c_int(len(pr["l"])), _p(pr["center"]), _p(pr["l"]),
+                                      _p(pr["alpha"]), _p(pr["cn"]), _p(self.rcut), _p(self.lat),
+                                      _p(rec), ctypes.c_int(self.nlev), _p(self.meshes),
+                                      _p(self.E), ctypes.c_double(self.sys.rel_cutoff),
+                                      ctypes.c_double(self.sys.tau), ctypes.c_long(cap), _p(ab),
+                                      _p(img), _p(lev), _p(lo), _p(hi), _p(R))
             if n <= cap:
                 break
             cap = int(n)
@@ -273,11 +319,17 @@ class Plan:
         order = np.lexsort(t[:, ::-1].T)
         return t[order].astype(np.int64)
 
-    def _args(self):
+    def _args(self, lengths=False):
+        """Pair arrays for the C oracle, with the lattice rows (or, for the orthorhombic
+        meta-GGA functions, the three lengths)."""
         pr = self.prims
         return (_p(self.ab), _p(self.img), _p(self.lev), _p(self.lo), _p(self.hi),
                 _p(pr["center"]), _p(pr["l"]), _p(pr["alpha"]), _p(pr["cn"]), _p(pr["ao"]),
-                _p(self.L), _p(self.meshes))
+                _p(self.L if lengths else self.lat), _p(self.meshes))
+
+    def _ortho_only(self, what):
+        if not self.ortho:
+            raise ValueError(f"{what}: orthorhombic cells only")
 
     # -------------------------------------------------- eval_rho (Alg. 1) --
     def rho_levels(self, D, mode: str = "separable", nthreads: int = 0, pairs=None):
@@ -290,6 +342,8 @@ class Plan:
         total = int(self.grid_off[-1])
         grids = np.zeros(total)
         sub = self if pairs is None else self.subset(pairs)
+        if not self.ortho:
+            mode = "plain"  # the separable factorisation holds for orthorhombic cells only
         lib.orc_collocate(ctypes.c_int(0 if mode == "plain" else 1), ctypes.c_long(sub.npairs),
                           *sub._args(), _p(self.grid_off), ctypes.c_long(total), _p(D),
                           ctypes.c_long(D.shape[0]), _p(grids), ctypes.c_int(nthreads))
@@ -300,17 +354,19 @@ class Plan:
     def tau_levels(self, D, nthreads: int = 0):
         """Kinetic energy density of each level, tau_k = (1/2) sum D_mu,nu grad phi_mu .
         grad phi_nu over the pairs of that level (point by point, like Eq. rho_wrap)."""
+        self._ortho_only("tau_levels")
         lib = _lib()
         D = np.ascontiguousarray(D, dtype=np.float64)
         total = int(self.grid_off[-1])
         grids = np.zeros(total)
-        lib.orc_collocate_tau(ctypes.c_long(self.npairs), *self._args(), _p(self.grid_off),
+        lib.orc_collocate_tau(ctypes.c_long(self.npairs), *self._args(True), _p(self.grid_off),
                               ctypes.c_long(total), _p(D), ctypes.c_long(D.shape[0]), _p(grids),
                               ctypes.c_int(nthreads))
         return [grids[self.grid_off[k]:self.grid_off[k + 1]].reshape(tuple(self.meshes[k]))
                 for k in range(self.nlev)]
 
     def _tau_blocks(self, v_levels, grad_D=None, nthreads: int = 0):
+        self._ortho_only("meta-GGA integrals")
         lib = _lib()
         v = np.ascontiguousarray(np.concatenate([np.ascontiguousarray(x).ravel() for x in v_levels]))
         pr = self.prims
@@ -327,7 +383,7 @@ class Plan:
             gd = np.ascontiguousarray(grad_D, dtype=np.float64)
             nao = gd.shape[0]
         lib.orc_integrate_tau(ctypes.c_long(self.npairs), None, ctypes.c_long(self.npairs),
-                              *self._args(), _p(self.grid_off), _p(v),
+                              *self._args(True), _p(self.grid_off), _p(v),
                               None if gd is None else _p(gd), ctypes.c_long(nao), _p(xoff),
                               _p(xout), ctypes.c_int(nthreads))
         return xoff, xout, na
@@ -392,7 +448,7 @@ class Plan:
             mesh = self.meshes[k]
             Nk = float(np.prod(mesh))
             rk = np.fft.fftn(rho_levels[k])
-            g2 = gvectors(mesh, self.L)
+            g2 = gvectors(mesh, self.lat)
             mask = g2 < self.G[k] ** 2
             f = _freq_index(mesh)
             idx = np.nonzero(mask)
@@ -411,7 +467,7 @@ class Plan:
         for k in range(self.nlev):
             mesh = tuple(int(m) for m in self.meshes[k])
             Nk = float(np.prod(mesh))
-            g2 = gvectors(mesh, self.L)
+            g2 = gvectors(mesh, self.lat)
             mask = g2 < self.G[k] ** 2
             f = _freq_index(mesh)
             idx = np.nonzero(mask)
@@ -425,12 +481,12 @@ class Plan:
         """Hartree potential, Eqs. (vH) and (vHG): v~(G) = 4 pi rho~(G)/|G|^2 for
         G != 0, 0 at G = 0.  E_H = (1/2)(Omega/N) sum_r rho v_H."""
         fine = self.meshes[0]
-        g2 = gvectors(fine, self.L)
+        g2 = gvectors(fine, self.lat)
         rs = np.fft.fftn(rho_fine)
         with np.errstate(divide="ignore", invalid="ignore"):
             k = np.where(g2 > 0, 4.0 * np.pi / np.where(g2 > 0, g2, 1.0), 0.0)
         vH = np.real(np.fft.ifftn(rs * k))
-        omega = float(np.prod(self.L))
+        omega = self.omega
         EH = 0.5 * omega / float(np.prod(fine)) * float(np.sum(rho_fine * vH))
         return vH, EH
 
@@ -442,13 +498,14 @@ class Plan:
         cx = (3.0 / np.pi) ** (1.0 / 3.0)
         vx = -cx * np.cbrt(rp)
         ex = -0.75 * cx * rp * np.cbrt(rp)
-        omega = float(np.prod(self.L))
+        omega = self.omega
         return vx, omega / float(np.prod(self.meshes[0])) * float(np.sum(ex))
 
     def _deriv(self, spec, d):
         """Fourier derivative along axis d of a full (numpy-order) spectrum: i G_d spec,
         with the Nyquist plane of an even axis set to zero (a reading: the derivative of
         a real field stays real)."""
+        self._ortho_only("Fourier derivative")
         mesh = tuple(int(m) for m in self.meshes[0])
         f = np.fft.fftfreq(mesh[d], d=1.0 / mesh[d])
         g = 2.0 * np.pi * f / self.L[d]
@@ -472,7 +529,7 @@ class Plan:
         div = np.zeros_like(rho_fine)
         for d in range(3):
             div += np.real(np.fft.ifftn(self._deriv(np.fft.fftn(2.0 * deds * grad[d]), d)))
-        omega = float(np.prod(self.L))
+        omega = self.omega
         return dedr - div, omega / float(np.prod(self.meshes[0])) * float(np.sum(e))
 
     def xc(self, rho_fine, xc: str = "lda_x"):

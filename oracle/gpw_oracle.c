@@ -21,8 +21,14 @@
  *   - the nuclear-gradient contraction of Algorithm 3: D, v and the analytic
  *     derivative of each primitive with respect to its centre.
  *
- * Orthorhombic cells only (diagonal lattice); all arithmetic in double.
- * Build with -ffp-contract=off so that the screening decisions are reproducible.
+ * Lattices: `lat` holds the three lattice vectors as rows (lat[3 d + c] = component c of
+ * R_d); grid point (i0, i1, i2) of an N-point level mesh sits at sum_d (i_d / N_d) R_d
+ * and an image is T = sum_d n_d R_d.  With a diagonal lattice every formula reduces to
+ * the orthorhombic one operation for operation (the off-diagonal terms add exact
+ * zeros).  The separable mode and the meta-GGA functions are orthorhombic only; a
+ * non-orthogonal cell (App., non-orthogonal lattices) is evaluated point by point.
+ * All arithmetic in double.  Build with -ffp-contract=off so that the screening
+ * decisions are reproducible.
  */
 #include <math.h>
 #include <stdint.h>
@@ -54,6 +60,30 @@ static double orc_ipow(double x, int n) {
 }
 
 /* f(r) = cn * r^(l+2) * exp(-alpha r^2), Eq. (cut) with the r^2 volume factor. */
+/* grid step vectors of a level: H[d][c] = R_dc / N_d */
+static void orc_steps(const double* lat, const int* N, double H[3][3]) {
+  for (int d = 0; d < 3; ++d)
+    for (int c = 0; c < 3; ++c) H[d][c] = lat[3 * d + c] / (double)N[d];
+}
+
+/* Cartesian position of grid index (i0, i1, i2): sum_d i_d H[d] */
+static void orc_point(const double H[3][3], long i0, long i1, long i2, double* r) {
+  for (int c = 0; c < 3; ++c) r[c] = ((double)i0 * H[0][c] + (double)i1 * H[1][c]) + (double)i2 * H[2][c];
+}
+
+static int orc_diagonal(const double* lat) {
+  return lat[1] == 0.0 && lat[2] == 0.0 && lat[3] == 0.0 && lat[5] == 0.0 && lat[6] == 0.0 &&
+         lat[7] == 0.0;
+}
+
+/* cell volume |det R| ((L0 L1) L2 for a diagonal lattice) */
+double orc_volume(const double* lat) {
+  if (orc_diagonal(lat)) return lat[0] * lat[4] * lat[8];
+  double d = lat[0] * (lat[4] * lat[8] - lat[5] * lat[7]) - lat[1] * (lat[3] * lat[8] - lat[5] * lat[6]) +
+             lat[2] * (lat[3] * lat[7] - lat[4] * lat[6]);
+  return fabs(d);
+}
+
 static double orc_prim_f(double cn, int l, double alpha, double r) {
   return cn * orc_ipow(r, l + 2) * exp(-alpha * r * r);
 }
@@ -169,6 +199,82 @@ long orc_pairs(int npr, const double* pc, const int* pl, const double* pal,
   return n;
 }
 
+/*
+ * orc_pairs for any lattice (rows of lat; rec = the reciprocal rows b_d with
+ * b_d . R_e = delta_de).  Images: |f_d(A - B - T)| <= |A - B - T| |b_d| for the
+ * fractional coordinate f_d = b_d . r, so n_d runs over
+ * [ceil(f_d(A - B) - rsum |b_d|), floor(f_d(A - B) + rsum |b_d|)].  Box on the level
+ * mesh: lo_d = ceil((f_d(P) - R_p |b_d|) N_d), hi_d = floor((f_d(P) + R_p |b_d|) N_d),
+ * the grid points whose fractional coordinate along R_d can lie within R_p of P.
+ */
+long orc_pairs_lat(int npr, const double* pc, const int* pl, const double* pal,
+                   const double* pcn, const double* prc, const double* lat, const double* rec,
+                   int nlev, const int* mesh, const double* Ek, double rel, double tau, long cap,
+                   int* out_ab, int* out_img, int* out_lev, int* out_lo, int* out_hi,
+                   double* out_R) {
+  double blen[3];
+  for (int d = 0; d < 3; ++d)
+    blen[d] = sqrt(rec[3 * d] * rec[3 * d] + rec[3 * d + 1] * rec[3 * d + 1] + rec[3 * d + 2] * rec[3 * d + 2]);
+  long n = 0;
+  for (int a = 0; a < npr; ++a) {
+    if (prc[a] < 0) continue;
+    for (int b = a; b < npr; ++b) {
+      if (prc[b] < 0) continue;
+      double rsum = prc[a] + prc[b];
+      int nlo[3], nhi[3];
+      for (int d = 0; d < 3; ++d) {
+        double f = 0.0;
+        for (int c = 0; c < 3; ++c) f += rec[3 * d + c] * (pc[3 * a + c] - pc[3 * b + c]);
+        nlo[d] = (int)ceil(f - rsum * blen[d]);
+        nhi[d] = (int)floor(f + rsum * blen[d]);
+      }
+      for (int n0 = nlo[0]; n0 <= nhi[0]; ++n0)
+        for (int n1 = nlo[1]; n1 <= nhi[1]; ++n1)
+          for (int n2 = nlo[2]; n2 <= nhi[2]; ++n2) {
+            int nn[3] = {n0, n1, n2};
+            double B[3], AB2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+              B[c] = pc[3 * b + c] + (((double)n0 * lat[c] + (double)n1 * lat[3 + c]) + (double)n2 * lat[6 + c]);
+              double t = pc[3 * a + c] - B[c];
+              AB2 += t * t;
+            }
+            if (!(sqrt(AB2) < rsum)) continue;
+            double aa = pal[a], ab = pal[b], ap = aa + ab;
+            double P[3], dA2 = 0.0, dB2 = 0.0;
+            for (int c = 0; c < 3; ++c) {
+              P[c] = (aa * pc[3 * a + c] + ab * B[c]) / ap;
+              double ta = P[c] - pc[3 * a + c], tb = P[c] - B[c];
+              dA2 += ta * ta;
+              dB2 += tb * tb;
+            }
+            double kab = exp(-aa * ab * AB2 / ap);
+            double cab = fabs(pcn[a] * pcn[b]);
+            double R = orc_pair_extent(cab, kab, pl[a], pl[b], sqrt(dA2), sqrt(dB2), ap, tau);
+            if (R < 0) continue;
+            int lev = 0;
+            for (int k = nlev - 1; k >= 0; --k)
+              if (Ek[k] >= rel * ap) { lev = k; break; }
+            if (n < cap) {
+              out_ab[2 * n] = a;
+              out_ab[2 * n + 1] = b;
+              for (int d = 0; d < 3; ++d) {
+                double f = 0.0;
+                for (int c = 0; c < 3; ++c) f += rec[3 * d + c] * P[c];
+                double Nd = (double)mesh[3 * lev + d];
+                out_img[3 * n + d] = nn[d];
+                out_lo[3 * n + d] = (int)ceil((f - R * blen[d]) * Nd);
+                out_hi[3 * n + d] = (int)floor((f + R * blen[d]) * Nd);
+              }
+              out_lev[n] = lev;
+              out_R[n] = R;
+            }
+            ++n;
+          }
+    }
+  }
+  return n;
+}
+
 static inline long orc_wrap(long i, long n) {
   long r = i % n;
   return r < 0 ? r + n : r;
@@ -186,7 +292,7 @@ typedef struct {
 static void orc_load_pair(orc_pair_t* q, long p, const int* ab, const int* img, const int* lev,
                           const int* lo, const int* hi, const double* pc, const int* pl,
                           const double* pal, const double* pcn, const long* pao,
-                          const double* Ld) {
+                          const double* lat) {
   q->a = ab[2 * p];
   q->b = ab[2 * p + 1];
   q->la = pl[q->a];
@@ -195,7 +301,8 @@ static void orc_load_pair(orc_pair_t* q, long p, const int* ab, const int* img, 
   q->nb = orc_cart(q->lb, q->comp_b);
   for (int d = 0; d < 3; ++d) {
     q->A[d] = pc[3 * q->a + d];
-    q->B[d] = pc[3 * q->b + d] + (double)img[3 * p + d] * Ld[d];
+    q->B[d] = pc[3 * q->b + d] + (((double)img[3 * p] * lat[d] + (double)img[3 * p + 1] * lat[3 + d]) +
+                                   (double)img[3 * p + 2] * lat[6 + d]);
     q->lo[d] = lo[3 * p + d];
     q->hi[d] = hi[3 * p + d];
   }
@@ -255,7 +362,7 @@ static void orc_pair_1d(const orc_pair_t* q, int d, double h, double* fa, double
  */
 void orc_collocate(int mode, long npairs, const int* ab, const int* img, const int* lev,
                    const int* lo, const int* hi, const double* pc, const int* pl,
-                   const double* pal, const double* pcn, const long* pao, const double* Ld,
+                   const double* pal, const double* pcn, const long* pao, const double* lat,
                    const int* mesh, const long* grid_off, long grid_total, const double* D,
                    long nao, double* grids, int nthreads) {
   memset(grids, 0, sizeof(double) * grid_total);
@@ -276,9 +383,11 @@ void orc_collocate(int mode, long npairs, const int* ab, const int* img, const i
 #pragma omp for schedule(dynamic, 16)
     for (long p = 0; p < npairs; ++p) {
       orc_pair_t q;
-      orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, Ld);
+      orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, lat);
       const int* N = mesh + 3 * q.lev;
-      double h[3] = {Ld[0] / N[0], Ld[1] / N[1], Ld[2] / N[2]};
+      double H[3][3];
+      orc_steps(lat, N, H);
+      double h[3] = {H[0][0], H[1][1], H[2][2]};  /* separable mode: diagonal lattices */
       double* gl = g + grid_off[q.lev];
       int n[3] = {q.hi[0] - q.lo[0] + 1, q.hi[1] - q.lo[1] + 1, q.hi[2] - q.lo[2] + 1};
       if (n[0] <= 0 || n[1] <= 0 || n[2] <= 0) continue;
@@ -286,7 +395,9 @@ void orc_collocate(int mode, long npairs, const int* ab, const int* img, const i
         for (int i0 = q.lo[0]; i0 <= q.hi[0]; ++i0)
           for (int i1 = q.lo[1]; i1 <= q.hi[1]; ++i1)
             for (int i2 = q.lo[2]; i2 <= q.hi[2]; ++i2) {
-              double v = orc_pair_point_plain(&q, D, nao, i0 * h[0], i1 * h[1], i2 * h[2]);
+              double r[3];
+              orc_point(H, i0, i1, i2, r);
+              double v = orc_pair_point_plain(&q, D, nao, r[0], r[1], r[2]);
               gl[(orc_wrap(i0, N[0]) * N[1] + orc_wrap(i1, N[1])) * N[2] + orc_wrap(i2, N[2])] += v;
             }
       } else {
@@ -361,11 +472,11 @@ static double orc_dpoly(double u, int i, double alpha) {
 void orc_integrate(long npairs, const long* sel, long nsel, const int* ab, const int* img,
                    const int* lev, const int* lo, const int* hi, const double* pc,
                    const int* pl, const double* pal, const double* pcn, const long* pao,
-                   const double* Ld, const int* mesh, const long* grid_off, const double* v,
+                   const double* lat, const int* mesh, const long* grid_off, const double* v,
                    const double* grad_D, long nao, const long* xoff, double* xout,
                    int nthreads) {
   long count = sel ? nsel : npairs;
-  double omega = Ld[0] * Ld[1] * Ld[2];
+  double omega = orc_volume(lat);
 #ifdef _OPENMP
   if (nthreads <= 0) nthreads = omp_get_max_threads();
 #endif
@@ -373,9 +484,10 @@ void orc_integrate(long npairs, const long* sel, long nsel, const int* ab, const
   for (long s = 0; s < count; ++s) {
     long p = sel ? sel[s] : s;
     orc_pair_t q;
-    orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, Ld);
+    orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, lat);
     const int* N = mesh + 3 * q.lev;
-    double h[3] = {Ld[0] / N[0], Ld[1] / N[1], Ld[2] / N[2]};
+    double H[3][3];
+    orc_steps(lat, N, H);
     double wgt = omega / ((double)N[0] * N[1] * N[2]);
     const double* vl = v + grid_off[q.lev];
     double X[ORC_MAXCART * ORC_MAXCART];
@@ -384,7 +496,9 @@ void orc_integrate(long npairs, const long* sel, long nsel, const int* ab, const
     for (int i0 = q.lo[0]; i0 <= q.hi[0]; ++i0)
       for (int i1 = q.lo[1]; i1 <= q.hi[1]; ++i1)
         for (int i2 = q.lo[2]; i2 <= q.hi[2]; ++i2) {
-          double x = i0 * h[0], y = i1 * h[1], z = i2 * h[2];
+          double r[3];
+          orc_point(H, i0, i1, i2, r);
+          double x = r[0], y = r[1], z = r[2];
           double vr = vl[(orc_wrap(i0, N[0]) * N[1] + orc_wrap(i1, N[1])) * N[2] +
                          orc_wrap(i2, N[2])];
           double ra[3] = {x - q.A[0], y - q.A[1], z - q.A[2]};
@@ -443,11 +557,12 @@ void orc_integrate(long npairs, const long* sel, long nsel, const int* ab, const
  */
 void orc_rho_points(long npairs, const int* ab, const int* img, const int* lev,
                     const int* lo, const int* hi, const double* pc, const int* pl,
-                    const double* pal, const double* pcn, const long* pao, const double* Ld,
+                    const double* pal, const double* pcn, const long* pao, const double* lat,
                     const int* mesh, int level, long npts, const int* pts, const double* D,
                     long nao, double* out, int nthreads) {
   const int* N = mesh + 3 * level;
-  double h[3] = {Ld[0] / N[0], Ld[1] / N[1], Ld[2] / N[2]};
+  double H[3][3];
+  orc_steps(lat, N, H);
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
   for (long s = 0; s < npts; ++s) {
     double acc = 0.0;
@@ -465,14 +580,16 @@ void orc_rho_points(long npairs, const int* ab, const int* img, const int* lev,
       }
       if (skip) continue;
       orc_pair_t q;
-      orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, Ld);
+      orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, lat);
       for (int a0 = k0[0]; a0 <= k1[0]; ++a0)
         for (int a1 = k0[1]; a1 <= k1[1]; ++a1)
           for (int a2 = k0[2]; a2 <= k1[2]; ++a2) {
             long i0 = pts[3 * s] + (long)a0 * N[0];
             long i1 = pts[3 * s + 1] + (long)a1 * N[1];
             long i2 = pts[3 * s + 2] + (long)a2 * N[2];
-            acc += orc_pair_point_plain(&q, D, nao, i0 * h[0], i1 * h[1], i2 * h[2]);
+            double r[3];
+            orc_point(H, i0, i1, i2, r);
+            acc += orc_pair_point_plain(&q, D, nao, r[0], r[1], r[2]);
           }
     }
     out[s] = acc;
@@ -556,7 +673,8 @@ void orc_collocate_tau(long npairs, const int* ab, const int* img, const int* le
 #pragma omp for schedule(dynamic, 16)
     for (long p = 0; p < npairs; ++p) {
       orc_pair_t q;
-      orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, Ld);
+      const double lat9[9] = {Ld[0], 0.0, 0.0, 0.0, Ld[1], 0.0, 0.0, 0.0, Ld[2]};
+      orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, lat9);
       const int* N = mesh + 3 * q.lev;
       double h[3] = {Ld[0] / N[0], Ld[1] / N[1], Ld[2] / N[2]};
       double* gl = g + grid_off[q.lev];
@@ -608,7 +726,8 @@ void orc_integrate_tau(long npairs, const long* sel, long nsel, const int* ab, c
   for (long s = 0; s < count; ++s) {
     long p = sel ? sel[s] : s;
     orc_pair_t q;
-    orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, Ld);
+    const double lat9[9] = {Ld[0], 0.0, 0.0, 0.0, Ld[1], 0.0, 0.0, 0.0, Ld[2]};
+    orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, lat9);
     const int* N = mesh + 3 * q.lev;
     double h[3] = {Ld[0] / N[0], Ld[1] / N[1], Ld[2] / N[2]};
     double wgt = omega / ((double)N[0] * N[1] * N[2]);

@@ -85,6 +85,8 @@ def _contracted(sys):
 
 
 def _images(L, reach):
+    """Integer image triples covering |T| <= reach; L = the lattice's reach per index
+    step along each axis (its lengths for an orthorhombic cell, 1 / |b_d| otherwise)."""
     n = [int(math.ceil(reach / L[d])) + 1 for d in range(3)]
     return [(i, j, k) for i in range(-n[0], n[0] + 1) for j in range(-n[1], n[1] + 1)
             for k in range(-n[2], n[2] + 1)]
@@ -93,11 +95,13 @@ def _images(L, reach):
 def _shell_pair_sum(sys, reach, one_d):
     """Sum over images T and primitive pairs of a shell pair of products of 1-D
     factors one_d(i, j, a, b, A_d, B_d, d) -> matrix [nao, nao]."""
-    L = np.diag(sys.lattice)
+    lat = np.asarray(sys.lattice, dtype=float)
+    # images T = n . lat; along axis d, |n_d| <= |T| |b_d| with b_d the reciprocal rows
+    step = 1.0 / np.linalg.norm(np.linalg.inv(lat).T, axis=1)
     off = sys.ao_offsets()
     nao = int(off[-1])
     out = np.zeros((nao, nao))
-    imgs = np.array(_images(L, reach), dtype=float)
+    imgs = np.array(_images(step, reach), dtype=float)
     for sa in range(sys.nshell):
         la = int(sys.shell_l[sa])
         ca = _cart(la)
@@ -110,7 +114,7 @@ def _shell_pair_sum(sys, reach, one_d):
             B0 = sys.coords[int(sys.shell_atom[sb])]
             blk = np.zeros((len(ca), len(cb)), dtype=complex)
             for T in imgs:
-                B = B0 + T * L
+                B = B0 + T @ lat
                 if np.sum((A - B) ** 2) > reach * reach:
                     continue
                 for ka in range(int(sys.shell_nprim[sa])):
@@ -135,12 +139,18 @@ def lattice_overlap(sys, reach=40.0):
 
 def lattice_pw_matrix(sys, waves, reach=40.0):
     """V_mu,nu = sum_T int phi_mu(r) v(r) phi_nu(r - T) dr for
-    v(r) = sum_k a_k cos(G_k . r), G_k = 2 pi n_k / L (one wave at a time: the
-    3-D integral of exp(i G.r) factorises, and cos is its real part)."""
-    L = np.diag(sys.lattice)
+    v(r) = sum_k a_k cos(G_k . r), G_k = 2 pi sum_d n_kd b_d with the reciprocal rows b_d
+    (2 pi n_k / L for an orthorhombic cell; one wave at a time: the 3-D integral of
+    exp(i G.r) factorises over Cartesian axes, and cos is its real part)."""
+    lat = np.asarray(sys.lattice, dtype=float)
+    ortho = bool(np.all(lat == np.diag(np.diag(lat))))
+    rec = np.linalg.inv(lat).T
     tot = 0.0
     for nk, amp in zip(waves.n, waves.a):
-        G = 2 * np.pi * np.asarray(nk, dtype=float) / L
+        if ortho:
+            G = 2 * np.pi * np.asarray(nk, dtype=float) / np.diag(lat)
+        else:
+            G = 2 * np.pi * (np.asarray(nk, dtype=float) @ rec)
         tot = tot + amp * _shell_pair_sum(
             sys, reach, lambda i, j, a, b, A, B, d, G=G: pw_1d(i, j, a, b, A, B, G[d]))
     return tot

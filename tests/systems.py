@@ -45,3 +45,30 @@ def single_gaussian(alpha: float, L: float, cutoff: float = 200.0, nlevels: int 
 def tiny14() -> System:
     """The tiny workload at tau = 1e-14."""
     return workloads.tiny().with_tau(1e-14)
+
+
+TRICLINIC = np.array([[1.0, 0.0, 0.0], [0.28, 0.96, 0.0], [-0.21, 0.17, 0.95]])
+
+
+def skewed(seed: int = 5, L: float = 6.0, lattice=None, **kw) -> System:
+    """The `resolved` system in a non-orthogonal cell: lattice rows L * TRICLINIC (or
+    `lattice`), atoms at the same fractional positions."""
+    s = resolved(seed=seed, L=L, **kw)
+    lat = np.asarray(lattice if lattice is not None else L * TRICLINIC, dtype=np.float64)
+    frac = s.coords / L
+    s.lattice = lat
+    s.coords = np.ascontiguousarray(frac @ lat)
+    s.name = "skewed"
+    return s
+
+
+def sheared(s: System) -> System:
+    """The same crystal as the orthorhombic (cubic-mesh) system s, described with the
+    lattice rows (R0, R0 + R1, R2): the same lattice, so the same images and, with
+    N0 = N1, the same grid points (skewed point (i, j, k) = cubic point (i + j, j, k))."""
+    import copy
+    out = copy.copy(s)
+    lat = np.asarray(s.lattice, dtype=np.float64)
+    out.lattice = np.ascontiguousarray(np.array([lat[0], lat[0] + lat[1], lat[2]]))
+    out.name = s.name + "-sheared"
+    return out

@@ -399,6 +399,8 @@ def test_pbe_x_uniform_scaling():
     lam = 1.7
     q = copy.copy(p)
     q.L = p.L / lam
+    q.lat = p.lat / lam
+    q.omega = float(np.prod(q.L))
     vq, Eq = q.pbe_x(lam ** 3 * rho)
     assert Eq == pytest.approx(lam * E, rel=1e-12)
     assert np.max(np.abs(vq - lam * v)) <= 1e-12 * np.max(np.abs(lam * v))
@@ -499,3 +501,81 @@ def test_tau_gradient_matches_finite_differences(res_tau):
         cm[atom, d] -= h
         fd = (form(cp) - form(cm)) / (2 * h)
         assert g[atom, d] == pytest.approx(fd, rel=1e-6, abs=1e-8)
+
+
+# ------------------------------------------- non-orthogonal cells (App., lattices) --
+@pytest.fixture(scope="module")
+def res_skew():
+    s = systems.skewed(shells=((0, 1), (1, 1), (2, 1)), natm=2)
+    return s, oracle.Plan(s)
+
+
+def test_skew_integrated_density_is_trace_DS(res_skew):
+    # a triclinic cell: the level densities integrate to Tr(D S), S the lattice sum of
+    # the analytic overlaps over Cartesian image vectors T = n . R
+    s, p = res_skew
+    rl = p.rho_levels(s.D)
+    N = sum(p.omega / float(np.prod(m)) * float(r.sum()) for m, r in zip(p.meshes, rl))
+    S = cf.lattice_overlap(s, reach=30.0)
+    assert N == pytest.approx(float(np.sum(s.D * S)), rel=1e-11)
+
+
+def test_skew_mat_of_plane_waves_closed_form(res_skew):
+    # v(r) = sum a cos(G . r) with G = 2 pi n . B (reciprocal rows B): the fractional
+    # samples of the waves on every level, and V against the analytic lattice sums
+    s, p = res_skew
+    pw = s.potential
+    vl = p.restrict(pw.sample(p.meshes[0]))
+    for k in range(p.nlev):
+        assert np.max(np.abs(vl[k] - pw.sample(p.meshes[k]))) < 1e-12
+    V = p.mat_levels(vl)
+    ref = cf.lattice_pw_matrix(s, pw, reach=20.0)
+    assert np.max(np.abs(V - ref)) < 1e-10 * max(1.0, np.max(np.abs(ref)))
+
+
+def test_skew_energy_gradient_matches_finite_differences(res_skew):
+    s, p = res_skew
+    out = p.fock(s.D)
+    g = p.grad_levels(s.D, out["v_levels"])
+    h = 1e-4
+    for atom, d in [(0, 0), (1, 1), (1, 2)]:
+        cp = s.coords.copy()
+        cm = s.coords.copy()
+        cp[atom, d] += h
+        cm[atom, d] -= h
+        fd = (p.with_coords(cp).energy(s.D) - p.with_coords(cm).energy(s.D)) / (2 * h)
+        assert g[atom, d] == pytest.approx(fd, rel=1e-6, abs=1e-7)
+
+
+def test_sheared_description_of_a_cubic_cell():
+    # one cubic crystal described by rows (R0, R1, R2) and by (R0, R0 + R1, R2), with the
+    # same explicit meshes: the same lattice, images and grid points (skewed point
+    # (i, j, k) is cubic point (i + j mod N, j, k)).  The longer row R0 + R1 gives the
+    # sheared description level spheres sqrt(2) smaller (Sec. II multigrid: the sphere
+    # must fit the mesh along every row), so the meshes are taken 1.6 times finer than
+    # the cutoff asks, which leaves the resolved densities' spectra below 1e-11 outside
+    # either sphere; the two descriptions then agree up to that and the pair boxes.
+    s = systems.resolved(seed=7, shells=((0, 1), (1, 1), (2, 1)), natm=2, nlevels=2)
+    p = oracle.Plan(s)
+    s.meshes = np.array([[oracle._smooth7_even(int(1.6 * m)) for m in row] for row in p.meshes])
+    s.cutoff_ha = 0.0
+    # the sheared levels' cutoffs are half the cubic ones, so pairs may sit on other
+    # levels: a level keeps a pair's spectrum down to exp(-E_k / (2 alpha_p)) <=
+    # exp(-rel / 2), made negligible here by rel = 100
+    s.rel_cutoff = 100.0
+    p = oracle.Plan(s)
+    q = oracle.Plan(systems.sheared(s))
+    a, b = p.fock(s.D), q.fock(s.D)
+    N = int(p.meshes[0][0])
+    i = np.arange(N)
+    perm = (i[:, None] + i[None, :]) % N  # cubic x index of skewed (i, j)
+    rho_b_on_a = np.empty_like(a["rho_fine"])
+    rho_b_on_a[perm, i[None, :], :] = b["rho_fine"]
+    scale = np.max(np.abs(a["rho_fine"]))
+    assert np.max(np.abs(rho_b_on_a - a["rho_fine"])) <= 1e-9 * scale
+    assert b["EH"] == pytest.approx(a["EH"], rel=1e-9)
+    assert b["Ex"] == pytest.approx(a["Ex"], rel=1e-9)
+    assert np.max(np.abs(b["V"] - a["V"])) <= 1e-9 * np.max(np.abs(a["V"]))
+    ga = p.grad_levels(s.D, a["v_levels"])
+    gb = q.grad_levels(s.D, b["v_levels"])
+    assert np.max(np.abs(gb - ga)) <= 1e-8
