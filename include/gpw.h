@@ -15,12 +15,15 @@
  *   - fock:         rho -> Poisson (Eqs. vH, vHG) + LDA exchange -> V.
  *
  * Conventions
- *   Units: Bohr and Hartree.  Only orthorhombic cells (diagonal lattice).
+ *   Units: Bohr and Hartree.  Any lattice (rows a1, a2, a3).  Non-orthogonal cells
+ *   (App., non-orthogonal lattices) take the LDA Fock build and gradient with 4x8x16
+ *   sub-boxes; GGA exchange and the kinetic-energy-density kernels need an
+ *   orthorhombic (diagonal) lattice.
  *   Shells are Cartesian with angular momentum 0..3; within a shell the AO order is
  *   lexicographic with x^l first (d: xx, xy, xz, yy, yz, zz).  AOs follow the shell
  *   order of the descriptor.
  *   Grids are C order [N0][N1][N2] along a1, a2, a3; point (i0,i1,i2) sits at
- *   (i0 L0/N0, i1 L1/N1, i2 L2/N2).  Level 0 is the finest grid.
+ *   (i0/N0) a1 + (i1/N1) a2 + (i2/N2) a3.  Level 0 is the finest grid.
  *   Matrices are row-major nao x nao doubles.
  *
  * Ownership and memory
@@ -48,7 +51,7 @@ extern "C" {
 #endif
 
 #define GPW_OK 0
-#define GPW_EINVAL -1     /* bad argument: l > 3, non-orthogonal lattice, bad mesh, NULL */
+#define GPW_EINVAL -1     /* bad argument: l > 3, degenerate lattice, bad mesh, NULL */
 #define GPW_ENOMEM -2     /* device or host allocation failed */
 #define GPW_ECUDA -3      /* CUDA runtime error */
 #define GPW_ECUFFT -4     /* cuFFT error */
@@ -89,7 +92,10 @@ typedef struct gpw_batch_s* gpw_batch_t;
  * plane-wave cutoff and multigrid levels, screening threshold tau of Eq. (cut).
  * All pointers are host memory, read during gpw_plan only. */
 typedef struct {
-  double lattice[9];          /* rows a1, a2, a3 (Bohr); must be diagonal */
+  double lattice[9];          /* rows a1, a2, a3 (Bohr), linearly independent; a
+                                 non-diagonal lattice is a non-orthogonal cell: images
+                                 T = n . rows, boxes from the reciprocal rows, meshes
+                                 from the row lengths |a_d| */
   int natm;
   const double* coords;       /* natm x 3 atom positions (Bohr) */
   int nshell;
@@ -150,9 +156,14 @@ typedef struct {
  * with |A - B - T| < r_a + r_b, Sec. III A), assign levels, build the per-level
  * sub-box task lists, allocate grids/spectra/cuFFT plans, and precompute the 1-D
  * Gaussian factor tables of Eq. (gab_lp) on the device (enqueued on `stream`).
- * Returns GPW_EINVAL for a non-diagonal lattice, l > 3, nlevels outside
- * 1..GPW_MAX_LEVELS, non-positive exponents, or meshes too small for the
- * cutoff sphere.  *out is set only on success. */
+ * On a non-orthogonal cell the 1-D tables hold the diagonal part of the Gaussian in
+ * grid units along the rows, the grid kernels multiply in the cross factors
+ * exp(-2 alpha_p G_de eta_d eta_e) (the row-to-row terms of the appendix recursion), and
+ * pair tensors are re-expanded between Cartesian and row monomials.
+ * Returns GPW_EINVAL for a degenerate lattice, l > 3, nlevels outside
+ * 1..GPW_MAX_LEVELS, non-positive exponents, meshes too small for the cutoff sphere,
+ * or GGA / GPW_TAU / other sub-boxes on a non-orthogonal cell.  *out is set only on
+ * success. */
 int gpw_plan(const gpw_desc* desc, void* stream, gpw_plan_t* out);
 
 /* Host phase of gpw_plan only: screening, levels and task lists on the CPU, no device

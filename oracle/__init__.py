@@ -144,18 +144,26 @@ def is_orthorhombic(lattice) -> bool:
 
 
 def lattice_lengths(lattice):
-    """|R_d| of the lattice rows (the diagonal of an orthorhombic lattice, exactly)."""
+    """|R_d| of the lattice rows (the diagonal of an orthorhombic lattice, exactly),
+    sqrt(x^2 + y^2 + z^2) summed in that order."""
     lat = np.asarray(lattice, dtype=np.float64)
     if is_orthorhombic(lat):
         return np.diag(lat).astype(np.float64)
-    return np.sqrt(np.sum(lat * lat, axis=1))
+    return np.array([math.sqrt(float(r[0]) * float(r[0]) + float(r[1]) * float(r[1]) +
+                               float(r[2]) * float(r[2])) for r in lat])
 
 
 def reciprocal(lattice):
-    """Rows b_d with b_d . R_e = delta_de (no 2 pi): the fractional coordinate of r
-    along R_d is b_d . r."""
-    lat = np.asarray(lattice, dtype=np.float64)
-    return np.ascontiguousarray(np.linalg.inv(lat).T)
+    """Rows b_d with b_d . R_e = delta_de (no 2 pi): b_0 = R_1 x R_2 / V, b_1 = R_2 x R_0 / V,
+    b_2 = R_0 x R_1 / V, V = R_0 . (R_1 x R_2), each operation in double in that order, so
+    that the fractional coordinate b_d . r of a screening decision is reproducible."""
+    R = [[float(x) for x in row] for row in np.asarray(lattice, dtype=np.float64)]
+    cr = []
+    for d in range(3):
+        a, b = R[(d + 1) % 3], R[(d + 2) % 3]
+        cr.append([a[1] * b[2] - a[2] * b[1], a[2] * b[0] - a[0] * b[2], a[0] * b[1] - a[1] * b[0]])
+    V = R[0][0] * cr[0][0] + R[0][1] * cr[0][1] + R[0][2] * cr[0][2]
+    return np.ascontiguousarray(np.array([[c / V for c in row] for row in cr]))
 
 
 def level_grids(sys):

@@ -142,7 +142,7 @@ void free_plan(Plan* P, cudaStream_t stream = nullptr, bool sync = true) {
                   d.coef_off, d.part_off, d.xt_off, d.task_c, d.sub_off_c, d.work_c, d.task_i, d.sub_off_i, d.work_i, d.groups, d.atom_off,
                   d.atom_list, d.tab, d.coef, d.part, d.pgrad, d.grids, d.spec, d.fspec,
                   d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs, d.view, d.g2tab,
-                  d.g1tab, d.grad3, d.fspec3, P->fft_work};
+                  d.g1tab, d.grad3, d.fspec3, d.mono_t, P->fft_work};
   bool any = false;
   for (void* q : ptrs) any = any || q != nullptr;
   if (any && sync) cudaDeviceSynchronize();
@@ -191,6 +191,7 @@ long long estimate_bytes(const Plan& P, const HostArrays& H) {
   b += 2 * sz((long long)P.lev[0].N[0] + P.lev[0].N[1] + P.lev[0].N[2], sizeof(double));
   if (P.xc == GPW_XC_PBE_X)
     b += sz(3 * P.fine_n, sizeof(double)) + sz(P.fine_spec_n, sizeof(cufftDoubleComplex));
+  if (P.skew) b += sz((long long)H.mono_t.size(), sizeof(double));
   size_t ws = 0;  // one work area: the largest transform of the plan
   for (int k = 0; k < P.nlev; ++k)
     ws = std::max(ws, std::max(fft_estimate(P.lev[k].N, CUFFT_D2Z), fft_estimate(P.lev[k].N, CUFFT_Z2D)));
@@ -256,12 +257,16 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
     const LevelInfo& f = P->lev[0];
     std::vector<double> g2(f.N[0] + f.N[1] + f.N[2]);
     int o = 0;
-    for (int dd = 0; dd < 3; ++dd)
+    for (int dd = 0; dd < 3; ++dd) {
+      // non-orthogonal cell: (2 pi s |b_d|)^2, the cross terms are added by the kernels
+      const double bl = std::sqrt(P->rec[3 * dd] * P->rec[3 * dd] + P->rec[3 * dd + 1] * P->rec[3 * dd + 1] +
+                                  P->rec[3 * dd + 2] * P->rec[3 * dd + 2]);
       for (int m = 0; m < f.N[dd]; ++m) {
         const int sf = m < (f.N[dd] + 1) / 2 ? m : m - f.N[dd];
-        const double g = 2.0 * M_PI * (double)sf / P->L[dd];
+        const double g = P->skew ? 2.0 * M_PI * (double)sf * bl : 2.0 * M_PI * (double)sf / P->L[dd];
         g2[o++] = g * g;
       }
+    }
     GPW_TRY(upload(&d.g2tab, g2, &b));
     // signed (2 pi s)/L_d for the Fourier derivative, 0 on an even axis' Nyquist plane
     std::vector<double> g1(g2.size());
@@ -277,6 +282,7 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
     GPW_TRY(dalloc(&d.grad3, 3 * P->fine_n, &b));
     GPW_TRY(dalloc(&d.fspec3, P->fine_spec_n, &b));
   }
+  if (P->skew) GPW_TRY(upload(&d.mono_t, H.mono_t, &b));
   GPW_TRY(dalloc(&d.energies, 2, &b));
   GPW_TRY(dalloc(&d.err, 1, &b));
   GPW_CK(cudaMemsetAsync(d.err, 0, sizeof(int), s));
@@ -755,7 +761,11 @@ int gpw_plan_update_coords(gpw_plan_t plan, const double* coords, void* stream) 
     const int ia = P.prim_atom[a], ib = P.prim_atom[b];
     for (int d = 0; d < 3; ++d) {
       geo[8 * p + d] = coords[3 * ia + d];
-      geo[8 * p + 3 + d] = coords[3 * ib + d] + (double)P.h_img[3 * p + d] * P.L[d];
+      geo[8 * p + 3 + d] =
+          P.skew ? coords[3 * ib + d] + (((double)P.h_img[3 * p] * P.lat[d] +
+                                           (double)P.h_img[3 * p + 1] * P.lat[3 + d]) +
+                                          (double)P.h_img[3 * p + 2] * P.lat[6 + d])
+                 : coords[3 * ib + d] + (double)P.h_img[3 * p + d] * P.L[d];
     }
     geo[8 * p + 6] = P.prim_alpha[a];
     geo[8 * p + 7] = P.prim_alpha[b];
@@ -1038,11 +1048,15 @@ int gpw_batch_set(gpw_batch_t b, int nplans, const gpw_plan_t* plans, void* stre
       set_error("gpw_batch_set: plans of a batch must live on one device");
       return GPW_EINVAL;
     }
+    if (P.skew != P0.skew) {
+      set_error("gpw_batch_set: a batch holds orthorhombic or non-orthogonal cells, not both");
+      return GPW_EINVAL;
+    }
     lmax = std::max(lmax, P.lmax);
   }
   cudaError_t e = gpw::configure_batch(plans[0]->p.tile, plans[0]->p.tile_i, lmax,
                                        plans[0]->p.nw_colloc_req, &b->colloc,
-                                       &b->integ1);
+                                       &b->integ1, plans[0]->p.skew ? 1 : 0);
   if (e != cudaSuccess) {
     set_error(std::string("gpw_batch_set: ") + cudaGetErrorString(e));
     return GPW_ECUDA;

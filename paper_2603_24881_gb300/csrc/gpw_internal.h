@@ -31,6 +31,19 @@ constexpr long long kChunkDiv = 4 * 2 * 152;
 // Work-list band (items): a few times the blocks resident in one launch.
 constexpr long long kBand = 2048;
 
+// Non-orthogonal cells: the Cartesian monomials (r - A)^k of degree n <= kSkewDeg are
+// re-expanded in the grid-unit displacements xi_d along the lattice rows,
+// (r - A)_c = sum_d (R_d)_c / N_d xi_d; per level and degree n a block of
+// nh(n) x nh(n) coefficients (row: Cartesian monomial, column: lattice monomial, both
+// numbered l2 outer, l1 inner), blocks at mono_off(n), levels kMonoStride apart.
+constexpr int kSkewDeg = 7;
+__host__ __device__ constexpr int nh(int n) { return (n + 1) * (n + 2) / 2; }
+__host__ __device__ constexpr int mono_off(int n) {
+  return n == 0 ? 0 : mono_off(n - 1) + nh(n - 1) * nh(n - 1);
+}
+constexpr int kMonoStride = mono_off(kSkewDeg + 1);
+__host__ __device__ constexpr int hidx(int n, int k1, int k2) { return k2 * (n + 1) - (k2 * (k2 - 1)) / 2 + k1; }
+
 // Number of monomials x^l0 y^l1 z^l2 with l0 + l1 + l2 <= L, and of (l1, l2) pairs.
 __host__ __device__ constexpr int nc3(int L) { return (L + 1) * (L + 2) * (L + 3) / 6; }
 __host__ __device__ constexpr int nc2(int L) { return (L + 1) * (L + 2) / 2; }
@@ -57,6 +70,12 @@ struct LevelInfo {
   double Gk2;            // cutoff sphere: |G|^2 < Gk2
   double weight;         // Omega / (N0 N1 N2)
   double h[3];           // grid spacing L_d / N_d
+  // non-orthogonal cells: metric of the grid step vectors dR_d = R_d / N_d
+  // (dR0.dR0, dR1.dR1, dR2.dR2, dR0.dR1, dR0.dR2, dR1.dR2) and the map from Cartesian
+  // positions to grid units, x_d = sum_c fr[3 d + c] r_c (fr = N_d times the
+  // reciprocal row b_d)
+  double gm[6];
+  double fr[9];
 };
 
 // Everything a grid kernel needs from one plan, in device memory, so that one launch can
@@ -80,6 +99,9 @@ struct PlanView {
   int* err;
   int chunk_i;  // tasks per integration work item (items carry level | chunk << 4)
   int xr;       // extra 1-D table rows per dimension (table rows = L + 2 + xr)
+  int skew;     // non-orthogonal cell: the grid kernels apply the cross factors
+  const double* geo;
+  const int4* hot_a;
 };
 
 struct DeviceArrays {
@@ -121,6 +143,7 @@ struct DeviceArrays {
   double* red = nullptr;      // reduction partials
   double* g2tab = nullptr;    // ((2 pi s)/L_d)^2 per finest-mesh index along each axis
   double* g1tab = nullptr;    // (2 pi s)/L_d, 0 on the Nyquist plane of an even axis
+  double* mono_t = nullptr;   // non-orthogonal cells: monomial transforms per level
   double* grad3 = nullptr;    // GGA: three finest real grids (grad rho, then de/d grad rho)
   cufftDoubleComplex* fspec3 = nullptr;  // GGA: finest half spectrum (work)
   double* energies = nullptr; // E_H, E_x (device)
@@ -136,8 +159,11 @@ struct Plan {
   int tile[3] = {kT0, kT1, kT2};      // collocation sub-box
   int tile_i[3] = {8, 8, 32};         // integration sub-box
   int chunk_i = 0;                    // most tasks per integration work item
-  double L[3] = {0, 0, 0};
+  double L[3] = {0, 0, 0};   // lattice lengths |R_d|
   double omega = 0;
+  bool skew = false;         // non-orthogonal cell (App., non-orthogonal lattices)
+  double lat[9] = {0};       // lattice rows R_d
+  double rec[9] = {0};       // reciprocal rows b_d (b_d . R_e = delta_de)
   double E[GPW_MAX_LEVELS] = {0};
   LevelInfo lev[GPW_MAX_LEVELS];     // sub-box fields for the collocation tile
   LevelInfo lev_i[GPW_MAX_LEVELS];   // same levels, sub-box fields for the integration tile

@@ -79,7 +79,7 @@ __global__ void tables_kernel(long long np, const KLevels K, const int4* __restr
                               const int4* __restrict__ hot_b, const double* __restrict__ geo,
                               const double* __restrict__ cab,
                               const long long* __restrict__ tab_off, double* __restrict__ tab,
-                              double* __restrict__ pref, int xr) {
+                              double* __restrict__ pref, int xr, int skew) {
   const int lane = threadIdx.x & 31;
   long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long sw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -103,14 +103,33 @@ __global__ void tables_kernel(long long np, const KLevels K, const int4* __restr
     const int lo[3] = {ha.x, ha.y, ha.z};
     const int ntot = n[0] + n[1] + n[2];
     const long long base = tab_off[p];
+    // non-orthogonal cell: A and P in grid units along the rows (x_d = fr_d . r)
+    double ag[3] = {0.0, 0.0, 0.0}, pg[3] = {0.0, 0.0, 0.0};
+    if (skew) {
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        ag[d] = lv.fr[3 * d] * g[0] + lv.fr[3 * d + 1] * g[1] + lv.fr[3 * d + 2] * g[2];
+        pg[d] = lv.fr[3 * d] * P[0] + lv.fr[3 * d + 1] * P[1] + lv.fr[3 * d + 2] * P[2];
+      }
+    }
     for (int it = lane; it < ntot; it += 32) {
       int d = it < n[0] ? 0 : (it < n[0] + n[1] ? 1 : 2);
       int off = d == 0 ? 0 : (d == 1 ? n[0] : n[0] + n[1]);
       int i = it - off;
-      double x = (double)(lo[d] + i) * lv.h[d];
-      double u = x - g[d];
-      double t = x - P[d];
-      double v = exp(-ap * t * t);
+      double u, v;
+      if (skew) {
+        // xi^l exp(-alpha_p |dR_d|^2 eta^2): the diagonal part of |r - P|^2 on the grid;
+        // the cross terms between rows are applied by the grid kernels
+        const double x = (double)(lo[d] + i);
+        u = x - ag[d];
+        const double t = x - pg[d];
+        v = exp(-ap * lv.gm[d] * t * t);
+      } else {
+        double x = (double)(lo[d] + i) * lv.h[d];
+        u = x - g[d];
+        double t = x - P[d];
+        v = exp(-ap * t * t);
+      }
       double* dst = tab + base + (long long)(L + 2 + xr) * off + i;
       for (int l = 0; l <= L + 1 + xr; ++l) {
         dst[(long long)l * n[d]] = v;
@@ -295,13 +314,13 @@ __device__ __forceinline__ void stage_yz_async(const double* tb, const Task& tk,
 //   acc(q, i2) += sum_{l2 <= L} T2[l2](q) g2[l2](i2)
 // Items are spread over the lanes flat (it = l2 m01 + q, then it = q m2 + i2) so that
 // partial tasks keep the lanes busy; the item index advances by 32 with a carry.
-template <int L, int T0, int T1, int T2>
+template <int L, int T0, int T1, int T2, bool SK = false>
 __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __restrict__ sX,
                                             const double* __restrict__ sg1,
                                             const double* __restrict__ sg2, double* __restrict__ sT2,
                                             const int* __restrict__ s_row,
                                             const int* __restrict__ s_qi, double* __restrict__ acc,
-                                            int lane) {
+                                            int lane, const double* __restrict__ sE = nullptr) {
   constexpr int Q = T0 * T1;
   const float inv01 = __frcp_rn((float)m01), inv2 = __frcp_rn((float)m2);
   {
@@ -345,7 +364,24 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
       const double* tb = sT2 + qb;
       const double* ga = sg2 + iA;
       const double* gb = sg2 + iB;
-      if (base + 32 < items) {
+      if constexpr (SK) {
+        // non-orthogonal cell: the pair value times its cross factor E(q, i2)
+        if (base + 32 < items) {
+          double sa = 0.0, sb = 0.0;
+#pragma unroll
+          for (int l2 = 0; l2 <= L; ++l2) {
+            sa = fma(ta[l2 * Q], ga[l2 * T2], sa);
+            sb = fma(tb[l2 * Q], gb[l2 * T2], sb);
+          }
+          if (okA) *pa = fma(sE[qa * T2 + iA], sa, *pa);
+          if (okB) *pb = fma(sE[qb * T2 + iB], sb, *pb);
+        } else if (okA) {
+          double sa = 0.0;
+#pragma unroll
+          for (int l2 = 0; l2 <= L; ++l2) sa = fma(ta[l2 * Q], ga[l2 * T2], sa);
+          *pa = fma(sE[qa * T2 + iA], sa, *pa);
+        }
+      } else if (base + 32 < items) {
         double ra = okA ? *pa : 0.0, rb = okB ? *pb : 0.0;
 #pragma unroll
         for (int l2 = 0; l2 <= L; ++l2) {
@@ -370,6 +406,57 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
   }
 }
 
+// Non-orthogonal cells (App., non-orthogonal lattices): on the grid of a level,
+// |r - P|^2 = sum_de G_de eta_d eta_e with eta_d the grid-unit offset of the point from P
+// along row d and G the metric of the step vectors.  The 1-D tables hold the diagonal
+// part; a task's cross factor is
+//   E(i0, i1, i2) = R01(i0, i1) R02(i0, i2) R12(i1, i2),  Rde = exp(-2 alpha_p G_de eta_d eta_e),
+// each R row geometric in its second index (eta = eta0 + i): one lane per row takes two
+// exp and multiplies along the row.  Rows go to sR ([T0][T1], [T0][T2], [T1][T2]).
+template <int T0, int T1, int T2>
+struct SkewRows {
+  static constexpr int kSize = T0 * T1 + T0 * T2 + T1 * T2;
+  static_assert(2 * T0 + T1 <= 32, "one lane per cross-factor row");
+};
+
+template <int T0, int T1, int T2>
+__device__ __forceinline__ void skew_rows(const PlanView& pv, const LevelInfo& lv, const Task& tk,
+                                          double* __restrict__ sR, int lane) {
+  const double* g = pv.geo + 8 * (long long)tk.p;
+  const double aa = g[6], ab = g[7], ap = aa + ab;
+  const int4 ha = __ldg(pv.hot_a + tk.p);
+  const int lo[3] = {ha.x, ha.y, ha.z};
+  double eta0[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    double pgd = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) pgd += lv.fr[3 * d + c] * ((aa * g[c] + ab * g[3 + c]) / ap);
+    eta0[d] = (double)(lo[d] + tk.t[d]) - pgd;
+  }
+  const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
+  // row r: (first axis, second axis, metric entry, row index, destination, stride)
+  int d, e, gi, i, stride, len;
+  double* dst;
+  if (lane < m0) {
+    d = 0; e = 1; gi = 3; i = lane; dst = sR + i * T1; stride = T1; len = m1;
+  } else if (lane < 2 * m0) {
+    d = 0; e = 2; gi = 4; i = lane - m0; dst = sR + T0 * T1 + i * T2; stride = T2; len = m2;
+  } else if (lane < 2 * m0 + m1) {
+    d = 1; e = 2; gi = 5; i = lane - 2 * m0; dst = sR + T0 * T1 + T0 * T2 + i * T2; stride = T2; len = m2;
+  } else {
+    return;
+  }
+  (void)stride;
+  const double c = -2.0 * ap * lv.gm[gi] * (eta0[d] + (double)i);
+  double v = exp(c * eta0[e]);
+  const double r = exp(c);
+  for (int j = 0; j < len; ++j) {
+    dst[j] = v;
+    v *= r;
+  }
+}
+
 template <int T0, int T1, int T2>
 struct CollocLayout {
   // one staging buffer: the task's window of the x-contracted table (nc2(lp - 1) rows of
@@ -391,7 +478,7 @@ struct CollocLayout {
 //   T2[l2](i0,i1) = sum_l1 X[l2,l1](i0) g1[l1](i1)           nc2(L) m0 m1 FMAs
 //   rho(i0,i1,i2) += sum_l2 T2[l2](i0,i1) g2[l2](i2)         (L+1) m0 m1 m2
 // The next task's windows are copied in (cp.async) while the current one computes.
-template <int T0, int T1, int T2, int NW>
+template <int T0, int T1, int T2, int NW, bool SK = false>
 __global__ void __launch_bounds__(NW * 32, 24 / NW)
     collocate_kernel(const PlanView* __restrict__ views, const int4* __restrict__ work,
                      const CoefTables* __restrict__ tabs, int lp, int stg, int ldeg) {
@@ -423,6 +510,10 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
   double* sT2 = stage_base + 2 * bufn;
   int* s_row = reinterpret_cast<int*>(sT2 + lp * T0 * T1);
   int* s_qi = s_row + T0 * T1;
+  // non-orthogonal cells: the task's cross factors E[q][i2] and their rows, after the
+  // regular per-warp staging
+  double* sE = stage_base + ((Lay::stage(lp) + 1) & ~1);
+  double* sR = sE + T0 * T1 * T2;
   __syncthreads();
 
   // staging buffer b: [X window xrows*T0][g1 lp*T1][g2 lp*T2]
@@ -500,10 +591,23 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
         s_qi[q] = i0 | (i1 << 8);
         s_row[q] = ((tk.u[0] + i0) * T1 + (tk.u[1] + i1)) * T2 + tk.u[2];
       }
+      if constexpr (SK) {
+        skew_rows<T0, T1, T2>(pv, lv, tk, sR, lane);
+        __syncwarp();
+        const double* r01 = sR;
+        const double* r02 = sR + T0 * T1;
+        const double* r12 = r02 + T0 * T2;
+        const float inv2 = __frcp_rn((float)m2);
+        for (int it = lane; it < m01 * m2; it += 32) {
+          const int q = fdiv(it, inv2), i2 = it - q * m2;
+          const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
+          sE[q * T2 + i2] = r01[i0 * T1 + i1] * r02[i0 * T2 + i2] * r12[i1 * T2 + i2];
+        }
+      }
       __syncwarp();
 #define GPW_COLLOC_L(LL)                                                                     \
   case LL:                                                                                   \
-    colloc_task<LL, T0, T1, T2>(m01, m2, sX, sg1, sg2, sT2, s_row, s_qi, acc, lane);          \
+    colloc_task<LL, T0, T1, T2, SK>(m01, m2, sX, sg1, sg2, sT2, s_row, s_qi, acc, lane, sE);  \
     break;
       switch (L) {
         GPW_COLLOC_L(0) GPW_COLLOC_L(1) GPW_COLLOC_L(2) GPW_COLLOC_L(3) GPW_COLLOC_L(4)
@@ -563,7 +667,7 @@ struct IntegLayout {
   __host__ __device__ static int stage(int lpx) { return 2 * buf(lpx) + lpx * kUS; }
 };
 
-template <int T0, int T1, int T2, int NW>
+template <int T0, int T1, int T2, int NW, bool SK = false>
 __global__ void __launch_bounds__(NW * 32)
     integrate_kernel(const PlanView* __restrict__ views, const int4* __restrict__ work,
                      const CoefTables* __restrict__ tabs, int lext, int lpx, int stg) {
@@ -602,6 +706,10 @@ __global__ void __launch_bounds__(NW * 32)
   double* stage_base = sv + Lay::kSV + warp * stg;
   const int bufn = Lay::buf(lpx);
   double* sU = stage_base + 2 * bufn;
+  // non-orthogonal cells: the task's window of the potential times its cross factors,
+  // and the factor rows, after the regular per-warp staging
+  double* sVE = stage_base + ((Lay::stage(lpx) + 1) & ~1);
+  double* sR = sVE + Lay::kSV;
   __syncthreads();
 
   auto issue = [&](const Task& tk, long long toff, int b) {
@@ -651,15 +759,33 @@ __global__ void __launch_bounds__(NW * 32)
       const double* sg1 = stage_base + buf * bufn;
       const double* sg2 = sg1 + lpx * P1;
       const int m01 = m0 * m1;
+      const double* vbase = sv;
+      int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
+      if constexpr (SK) {
+        skew_rows<T0, T1, T2>(pv, lv, tk, sR, lane);
+        __syncwarp();
+        const double* r01 = sR;
+        const double* r02 = sR + T0 * T1;
+        const double* r12 = r02 + T0 * T2;
+        const float inv2 = __frcp_rn((float)m2), inv1 = __frcp_rn((float)m1);
+        for (int it = lane; it < m01 * m2; it += 32) {
+          const int q = fdiv(it, inv2), i2 = it - q * m2;
+          const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
+          sVE[(i0 * T1 + i1) * P2 + i2] = sv[((u0 + i0) * T1 + (u1 + i1)) * P2 + u2 + i2] *
+                                          (r01[i0 * T1 + i1] * r02[i0 * T2 + i2] * r12[i1 * T2 + i2]);
+        }
+        __syncwarp();
+        vbase = sVE;
+        u0 = u1 = u2 = 0;
+      }
       // U[l2](i1, i0): lanes walk consecutive i1 (rows P2 apart: conflict free)
       {
         const float inv01 = __frcp_rn((float)m01), inv1 = __frcp_rn((float)m1);
         const int items = (Lx + 1) * m01;
-        const int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
         for (int it = lane; it < items; it += 32) {
           const int l2 = fdiv(it, inv01), q = it - l2 * m01;
           const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
-          const double* vr = sv + ((u0 + i0) * T1 + (u1 + i1)) * P2 + u2;
+          const double* vr = vbase + ((u0 + i0) * T1 + (u1 + i1)) * P2 + u2;
           const double* gr = sg2 + l2 * P2;
           double a = 0.0;
           for (int i2 = 0; i2 < m2; ++i2) a = fma(vr[i2], gr[i2], a);
@@ -843,6 +969,47 @@ __global__ void __launch_bounds__(kRedPW * 32, 6)
       for (int k = 0; k < 4; ++k)
         if (cidx + 32 * k < nc) dst[cidx + 32 * k] = wgt * v[k];
     }
+  }
+}
+
+// Non-orthogonal cells: re-expand a pair's tensor over the monomials of degree <= L + lext
+// (flat order of mono_index) between Cartesian monomials (r - A)^k and grid-unit lattice
+// monomials xi^k' of the pair's level, with T the level's transform ((r - A)^k =
+// sum_k' T[k][k'] xi^k', degree by degree):
+//   dir 0, density coefficients:  C'[k'] = sum_k T[k][k'] C[k]   (Cartesian -> lattice)
+//   dir 1, potential moments:      W[k]  = sum_k' T[k][k'] W'[k'] (lattice -> Cartesian)
+// One thread per pair.
+__device__ __forceinline__ int mono_index(int k0, int k1, int k2, int M);
+
+__global__ void mono_transform_kernel(long long np, const int4* __restrict__ hot_a,
+                                      const int4* __restrict__ hot_b,
+                                      const long long* __restrict__ coef_off,
+                                      double* __restrict__ coef, const double* __restrict__ mono_t,
+                                      int lext, int dir) {
+  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= np) return;
+  const int L = hot_a[p].w + lext;
+  const double* T = mono_t + (long long)kMonoStride * hot_b[p].w;
+  double* c = coef + coef_off[p];
+  double in[kNc3Max];
+  const int nc = nc3(L);
+  for (int i = 0; i < nc; ++i) in[i] = c[i];
+  for (int n = 0; n <= L; ++n) {
+    const double* blk = T + mono_off(n);
+    const int m = nh(n);
+    for (int a2 = 0; a2 <= n; ++a2)
+      for (int a1 = 0; a1 <= n - a2; ++a1) {
+        const int ha = hidx(n, a1, a2);
+        double acc = 0.0;
+        for (int b2 = 0; b2 <= n; ++b2)
+          for (int b1 = 0; b1 <= n - b2; ++b1) {
+            const int hb = hidx(n, b1, b2);
+            // dir 0: output lattice a from Cartesian b (T[b][a]); dir 1: the transpose
+            const double t = dir == 0 ? blk[hb * m + ha] : blk[ha * m + hb];
+            acc = fma(t, in[mono_index(n - b1 - b2, b1, b2, L)], acc);
+          }
+        c[mono_index(n - a1 - a2, a1, a2, L)] = acc;
+      }
   }
 }
 
@@ -1085,6 +1252,18 @@ __device__ __forceinline__ double gsq(int f0, int f1, int f2, const double* __re
                    __ldg(g2t + Nf[0] + Nf[1] + f2));
 }
 
+// |G|^2 of a non-orthogonal cell: the per-axis tables hold (2 pi s_d |b_d|)^2, plus the
+// cross terms 2 (2 pi)^2 (b_d . b_e) s_d s_e of G = 2 pi sum_d s_d b_d.
+__device__ __forceinline__ double gsq_k(int f0, int f1, int f2, const double* __restrict__ g2t,
+                                        const int* Nf, const KLevels& K) {
+  double g = gsq(f0, f1, f2, g2t, Nf);
+  if (K.skew) {
+    const double s0 = signed_freq(f0, Nf[0]), s1 = signed_freq(f1, Nf[1]), s2 = signed_freq(f2, Nf[2]);
+    g += K.gq[0] * s0 * s1 + K.gq[1] * s0 * s2 + K.gq[2] * s1 * s2;
+  }
+  return g;
+}
+
 // Fine spectrum S(G) = sum_k [|G| < G_k] rho^_k(G) / N_k (unnormalised level DFTs):
 // Fourier interpolation of every level onto the finest grid; one C2R then gives rho.
 __global__ void combine_kernel(const KLevels K, const double* __restrict__ g2t,
@@ -1100,7 +1279,7 @@ __global__ void combine_kernel(const KLevels K, const double* __restrict__ g2t,
     const int m1 = (int)(r % f.N[1]);
     const int m0 = (int)(r / f.N[1]);
     const int s0 = signed_freq(m0, f.N[0]), s1 = signed_freq(m1, f.N[1]), s2 = m2;
-    const double G2 = gsq(m0, m1, m2, g2t, f.N);
+    const double G2 = gsq_k(m0, m1, m2, g2t, f.N, K);
     double re = 0.0, im = 0.0;
     for (int k = 0; k < K.nlev; ++k) {
       const LevelInfo& lv = K.lv[k];
@@ -1142,7 +1321,7 @@ __global__ void restrict_kernel(const KLevels K, const double* __restrict__ g2t,
     out.y = 0.0;
     const int i0 = s0 < 0 ? s0 + f.N[0] : s0;
     const int i1 = s1 < 0 ? s1 + f.N[1] : s1;
-    const double G2 = gsq(i0, i1, s2, g2t, f.N);
+    const double G2 = gsq_k(i0, i1, s2, g2t, f.N, K);
     if (G2 < lv.Gk2 && 2 * abs(s0) <= lv.N[0] - 1 && 2 * abs(s1) <= lv.N[1] - 1 &&
         2 * s2 <= lv.N[2] - 1) {
       const long long fi = ((long long)i0 * f.N[1] + i1) * fh2 + s2;
@@ -1186,7 +1365,7 @@ __global__ void poisson_kernel(const KLevels K, const double* __restrict__ g2t, 
     const long long r = idx / h2;
     const int m1 = (int)(r % f.N[1]);
     const int m0 = (int)(r / f.N[1]);
-    const double G2 = gsq(m0, m1, m2, g2t, f.N);
+    const double G2 = gsq_k(m0, m1, m2, g2t, f.N, K);
     cufftDoubleComplex z = fspec[idx];
     double kern = G2 > 0.0 ? (4.0 * 3.141592653589793) / G2 : 0.0;
     const double mult = (m2 == 0 || (f.N[2] % 2 == 0 && m2 == f.N[2] / 2)) ? 1.0 : 2.0;
@@ -1574,6 +1753,12 @@ constexpr int kNW = 8;
   X(8, 8, 16) X(4, 8, 32) X(8, 8, 32) X(4, 8, 64) X(4, 8, 16) X(4, 4, 16) X(2, 8, 16) X(4, 4, 32)
 #define GPW_INTEG_SHAPES(X) GPW_COLLOC_SHAPES(X) X(8, 8, 64) X(8, 4, 64)
 
+// per-warp staging doubles of the non-orthogonal variants (cross factors and their rows)
+template <int T0, int T1, int T2>
+int colloc_skew_extra() { return T0 * T1 * T2 + SkewRows<T0, T1, T2>::kSize; }
+template <int T0, int T1, int T2>
+int integ_skew_extra() { return IntegLayout<T0, T1, T2>::kSV + SkewRows<T0, T1, T2>::kSize; }
+
 template <int T0, int T1, int T2>
 size_t colloc_smem(int stg, int nw) {
   return sizeof(int) * kTabInts + sizeof(double) * (size_t)nw * (T0 * T1 * T2 + stg);
@@ -1586,12 +1771,12 @@ size_t integ_smem(int stg) {
 
 // Warps per collocation block: the candidate with the most resident warps per SM, as the
 // occupancy calculator reports it for this shared-memory size (registers included).
-template <int T0, int T1, int T2>
+template <int T0, int T1, int T2, bool SK = false>
 int pick_colloc_warps(int stg, int want, int* nw_out, size_t* smem_out) {
   int best = 0;
-  const void* fns[3] = {(const void*)collocate_kernel<T0, T1, T2, 8>,
-                        (const void*)collocate_kernel<T0, T1, T2, 6>,
-                        (const void*)collocate_kernel<T0, T1, T2, 4>};
+  const void* fns[3] = {(const void*)collocate_kernel<T0, T1, T2, 8, SK>,
+                        (const void*)collocate_kernel<T0, T1, T2, 6, SK>,
+                        (const void*)collocate_kernel<T0, T1, T2, 4, SK>};
   const int nws[3] = {8, 6, 4};
   for (int i = 0; i < 3; ++i) {
     if (want != 0 && nws[i] != want) continue;  // a requested count (still must fit)
@@ -1627,6 +1812,14 @@ KLevels make_klevels(const Plan& p, bool integ) {
   KLevels k;
   for (int i = 0; i < GPW_MAX_LEVELS; ++i) k.lv[i] = integ ? p.lev_i[i] : p.lev[i];
   k.nlev = p.nlev;
+  k.skew = p.skew ? 1 : 0;
+  const double tp2 = 2.0 * (2.0 * M_PI) * (2.0 * M_PI);
+  const int pd[3][2] = {{0, 1}, {0, 2}, {1, 2}};
+  for (int i = 0; i < 3; ++i) {
+    const double* bd = p.rec + 3 * pd[i][0];
+    const double* be = p.rec + 3 * pd[i][1];
+    k.gq[i] = p.skew ? tp2 * (bd[0] * be[0] + bd[1] * be[1] + bd[2] * be[2]) : 0.0;
+  }
   return k;
 }
 
@@ -1657,6 +1850,33 @@ cudaError_t configure_kernels(Plan* p) {
   GPW_INTEG_SHAPES(GPW_TILE_ATTR_I)
 #undef GPW_TILE_ATTR
 #undef GPW_TILE_ATTR_I
+  // the non-orthogonal variants (4x8x16 sub-boxes)
+  for (const void* f : {(const void*)collocate_kernel<kT0, kT1, kT2, 8, true>,
+                        (const void*)collocate_kernel<kT0, kT1, kT2, 6, true>,
+                        (const void*)collocate_kernel<kT0, kT1, kT2, 4, true>,
+                        (const void*)integrate_kernel<kT0, kT1, kT2, kNW, true>}) {
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
+    if (e != cudaSuccess) return e;
+  }
+  if (p->skew) {
+    if (!(p->tile[0] == kT0 && p->tile[1] == kT1 && p->tile[2] == kT2 && p->tile_i[0] == kT0 &&
+          p->tile_i[1] == kT1 && p->tile_i[2] == kT2) || p->xr)
+      return cudaErrorInvalidValue;
+    using CL = CollocLayout<kT0, kT1, kT2>;
+    using IL = IntegLayout<kT0, kT1, kT2>;
+    p->stg_colloc = even(even(CL::stage(lp)) + colloc_skew_extra<kT0, kT1, kT2>());
+    if (pick_colloc_warps<kT0, kT1, kT2, true>(p->stg_colloc, p->nw_colloc_req, &p->nw_colloc,
+                                                &p->smem_colloc) == 0)
+      return cudaErrorInvalidValue;
+    p->stg_integ = even(even(IL::stage(p->lmax + 1)) + integ_skew_extra<kT0, kT1, kT2>());
+    p->stg_integ1 = even(even(IL::stage(p->lmax + 2)) + integ_skew_extra<kT0, kT1, kT2>());
+    p->smem_integ = integ_smem<kT0, kT1, kT2>(p->stg_integ);
+    p->smem_integ1 = integ_smem<kT0, kT1, kT2>(p->stg_integ1);
+    p->nw_integ = kNW;
+    if ((size_t)optin < std::max(p->smem_colloc, std::max(p->smem_integ, p->smem_integ1)))
+      return cudaErrorInvalidValue;
+    return cudaSuccess;
+  }
 #define GPW_TILE_CONF(a, b, c)                                                      \
   if (p->tile[0] == a && p->tile[1] == b && p->tile[2] == c) {                      \
     found |= 1;                                                                     \
@@ -1709,7 +1929,7 @@ cudaError_t launch_tables(const Plan& p, cudaStream_t s) {
   ++p.launches;
   tables_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, make_klevels(p, false), p.d.hot_a, p.d.hot_b,
                                              p.d.geo, p.d.cab, p.d.tab_off, p.d.tab, p.d.pref,
-                                             p.xr);
+                                             p.xr, p.skew ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -1719,6 +1939,11 @@ cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s) {
   pair_coef_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
       p.npairs, p.d.hot_a, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, p.d.tabs, D,
       p.nao, p.d.coef);
+  if (p.skew) {
+    ++p.launches;
+    mono_transform_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
+        p.npairs, p.d.hot_a, p.d.hot_b, p.d.coef_off, p.d.coef, p.d.mono_t, 0, 0);
+  }
   return cudaGetLastError();
 }
 
@@ -1738,6 +1963,21 @@ cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views,
                                    long long nwork, const CoefTables* tabs, cudaStream_t s) {
   if (nwork == 0) return cudaSuccess;
   const int t0 = cfg.tile[0], t1 = cfg.tile[1], t2 = cfg.tile[2];
+  if (cfg.skew) {
+    if (!(t0 == kT0 && t1 == kT1 && t2 == kT2) || cfg.ldeg) return cudaErrorInvalidValue;
+    if (cfg.nw == 8)
+      collocate_kernel<kT0, kT1, kT2, 8, true><<<(int)nwork, 8 * 32, cfg.smem, s>>>(
+          views, work, tabs, cfg.lp, cfg.stg, 0);
+    else if (cfg.nw == 6)
+      collocate_kernel<kT0, kT1, kT2, 6, true><<<(int)nwork, 6 * 32, cfg.smem, s>>>(
+          views, work, tabs, cfg.lp, cfg.stg, 0);
+    else if (cfg.nw == 4)
+      collocate_kernel<kT0, kT1, kT2, 4, true><<<(int)nwork, 4 * 32, cfg.smem, s>>>(
+          views, work, tabs, cfg.lp, cfg.stg, 0);
+    else
+      return cudaErrorInvalidValue;
+    return cudaGetLastError();
+  }
 #define GPW_COLLOC_NW(a, b, c, NWV)                                                        \
   if (t0 == a && t1 == b && t2 == c && cfg.nw == NWV) {                                    \
     collocate_kernel<a, b, c, NWV><<<(int)nwork, NWV * 32, cfg.smem, s>>>(                 \
@@ -1756,6 +1996,12 @@ cudaError_t launch_integrate_views(const GridLaunch& cfg, int lext, const PlanVi
                                    cudaStream_t s) {
   if (nwork == 0) return cudaSuccess;
   const int t0 = cfg.tile[0], t1 = cfg.tile[1], t2 = cfg.tile[2];
+  if (cfg.skew) {
+    if (!(t0 == kT0 && t1 == kT1 && t2 == kT2) || lext > 1) return cudaErrorInvalidValue;
+    integrate_kernel<kT0, kT1, kT2, kNW, true><<<(int)nwork, kNW * 32, cfg.smem, s>>>(
+        views, work, tabs, lext, cfg.lp, cfg.stg);
+    return cudaGetLastError();
+  }
 #define GPW_TILE_INTEG(a, b, c)                                                            \
   if (t0 == a && t1 == b && t2 == c) {                                                     \
     integrate_kernel<a, b, c, kNW><<<(int)nwork, kNW * 32, cfg.smem, s>>>(                 \
@@ -1778,6 +2024,7 @@ cudaError_t launch_collocate(const Plan& p, cudaStream_t s, int ldeg) {
   cfg.stg = ldeg ? p.stg_colloc_t : p.stg_colloc;
   cfg.smem = ldeg ? p.smem_colloc_t : p.smem_colloc;
   cfg.ldeg = ldeg;
+  cfg.skew = p.skew ? 1 : 0;
   return launch_collocate_views(cfg, p.d.view, p.d.work_c, p.nwork, p.d.tabs, s);
 }
 
@@ -1791,13 +2038,14 @@ cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s) {
   cfg.lp = p.lmax + lext + 1;
   cfg.stg = lext > 1 ? p.stg_integ3 : (lext ? p.stg_integ1 : p.stg_integ);
   cfg.smem = lext > 1 ? p.smem_integ3 : (lext ? p.smem_integ1 : p.smem_integ);
+  cfg.skew = p.skew ? 1 : 0;
   return launch_integrate_views(cfg, lext, p.d.view, p.d.work_i, p.nwork_i, p.d.tabs, s);
 }
 
 // Launch shapes for a batch of plans with the same sub-boxes and largest degree lmax.
 cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int nw_req,
                             GridLaunch* colloc,
-                            GridLaunch* integ1) {
+                            GridLaunch* integ1, int skew) {
   int dev = 0, per_sm = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess)
@@ -1828,7 +2076,22 @@ cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int 
   GPW_INTEG_SHAPES(GPW_TILE_BCONF_I)
 #undef GPW_TILE_BCONF
 #undef GPW_TILE_BCONF_I
-  return found == 3 ? cudaSuccess : cudaErrorInvalidValue;
+  if (found != 3) return cudaErrorInvalidValue;
+  colloc->skew = integ1->skew = skew;
+  if (skew) {
+    // non-orthogonal plans: the cross-factor variants and their larger staging
+    if (!(tile_c[0] == kT0 && tile_c[1] == kT1 && tile_c[2] == kT2 && tile_i[0] == kT0 &&
+          tile_i[1] == kT1 && tile_i[2] == kT2))
+      return cudaErrorInvalidValue;
+    colloc->stg = even(even(CollocLayout<kT0, kT1, kT2>::stage(lmax + 1)) +
+                       colloc_skew_extra<kT0, kT1, kT2>());
+    if (pick_colloc_warps<kT0, kT1, kT2, true>(colloc->stg, nw_req, &colloc->nw, &colloc->smem) == 0)
+      return cudaErrorInvalidValue;
+    integ1->stg = even(even(IntegLayout<kT0, kT1, kT2>::stage(lmax + 2)) +
+                       integ_skew_extra<kT0, kT1, kT2>());
+    integ1->smem = integ_smem<kT0, kT1, kT2>(integ1->stg);
+  }
+  return cudaSuccess;
 }
 
 PlanView make_view(const Plan& p) {
@@ -1853,6 +2116,9 @@ PlanView make_view(const Plan& p) {
   v.err = p.d.err;
   v.chunk_i = p.chunk_i;
   v.xr = p.xr;
+  v.skew = p.skew ? 1 : 0;
+  v.geo = p.d.geo;
+  v.hot_a = p.d.hot_a;
   return v;
 }
 
@@ -1863,6 +2129,11 @@ cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s) {
   reduce_parts_kernel<<<(int)blocks, kRedPW * 32, 0, s>>>(
       p.npairs, make_klevels(p, true), p.tile_i[0], p.d.hot_a, p.d.hot_b, p.d.ids2, p.d.part_off,
       p.d.coef_off, p.d.tab_off, p.d.tab, p.d.part, p.d.tabs, p.d.coef, lext, p.xr);
+  if (p.skew) {
+    ++p.launches;
+    mono_transform_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
+        p.npairs, p.d.hot_a, p.d.hot_b, p.d.coef_off, p.d.coef, p.d.mono_t, lext, 1);
+  }
   return cudaGetLastError();
 }
 

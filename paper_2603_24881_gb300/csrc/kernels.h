@@ -8,6 +8,8 @@ namespace gpw {
 struct KLevels {
   LevelInfo lv[GPW_MAX_LEVELS];
   int nlev;
+  int skew;       // non-orthogonal cell: |G|^2 has cross terms
+  double gq[3];   // their coefficients 2 (2 pi)^2 (b0.b1, b0.b2, b1.b2)
 };
 
 KLevels make_klevels(const Plan& p, bool integ);
@@ -18,6 +20,7 @@ struct GridLaunch {
   int nw, lp, stg;
   size_t smem;
   int ldeg = 0;  // collocation: degree added to every pair's L (2 for the kinetic density)
+  int skew = 0;  // non-orthogonal cells: the kernels with cross factors
 };
 cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views, const int4* work,
                                    long long nwork, const CoefTables* tabs, cudaStream_t s);
@@ -26,7 +29,7 @@ cudaError_t launch_integrate_views(const GridLaunch& cfg, int lext, const PlanVi
                                    cudaStream_t s);
 cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int nw_req,
                             GridLaunch* colloc,
-                            GridLaunch* integ1);
+                            GridLaunch* integ1, int skew = 0);
 
 cudaError_t launch_tables(const Plan& p, cudaStream_t s);
 cudaError_t launch_pair_coef(const Plan& p, const double* D, cudaStream_t s);

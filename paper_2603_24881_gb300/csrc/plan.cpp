@@ -82,9 +82,33 @@ void box_at(double R, const double* P, const double* N, const double* L, int* lo
   }
 }
 
+// The box of a non-orthogonal cell (App., non-orthogonal lattices): the grid points whose
+// fractional coordinate along R_d lies within R |b_d| of that of P,
+//   lo_d = ceil((f_d(P) - R |b_d|) N_d),  hi_d = floor((f_d(P) + R |b_d|) N_d),
+// f_d(P) = b_d . P summed over x, y, z in that order; monotone in R like box_at.
+struct SkewBox {
+  const double* rec;   // reciprocal rows b_d
+  double blen[3];      // |b_d|
+};
+
+void box_at_skew(double R, const double* P, const double* N, const SkewBox& sk, int* lo, int* hi) {
+  for (int d = 0; d < 3; ++d) {
+    double f = 0.0;
+    for (int c = 0; c < 3; ++c) f += sk.rec[3 * d + c] * P[c];
+    lo[d] = (int)std::ceil((f - R * sk.blen[d]) * N[d]);
+    hi[d] = (int)std::floor((f + R * sk.blen[d]) * N[d]);
+  }
+}
+
 bool pair_box(double cab, double kab, int la, int lb, double dA, double dB, double ap,
               double tau, const double* P, const double* N, const double* L, int* lo_out,
-              int* hi_out) {
+              int* hi_out, const SkewBox* sk = nullptr) {
+  auto box = [&](double R, int* lo, int* hi) {
+    if (sk)
+      box_at_skew(R, P, N, *sk, lo, hi);
+    else
+      box_at(R, P, N, L, lo, hi);
+  };
   double r0 = std::sqrt((double)(la + lb + 2) / (2.0 * ap));
   if (pair_h(cab, kab, la, lb, dA, dB, ap, r0) < tau) return false;
   double hi = r0;
@@ -95,14 +119,14 @@ bool pair_box(double cab, double kab, int la, int lb, double dA, double dB, doub
     if (pair_h(cab, kab, la, lb, dA, dB, ap, mid) >= tau) lo = mid; else hi = mid;
     if (it >= 7 && (it & 3) == 3) {
       int a[3], b[3], c[3], e[3];
-      box_at(lo, P, N, L, a, b);
-      box_at(hi, P, N, L, c, e);
+      box(lo, a, b);
+      box(hi, c, e);
       bool same = true;
       for (int d = 0; d < 3; ++d) same = same && a[d] == c[d] && b[d] == e[d];
       if (same) break;
     }
   }
-  box_at(hi, P, N, L, lo_out, hi_out);
+  box(hi, lo_out, hi_out);
   return true;
 }
 
@@ -420,6 +444,47 @@ int count_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
 
 }  // namespace
 
+// Monomial transforms of a non-orthogonal cell, per level (layout: gpw_internal.h): the
+// Cartesian monomial prod_c (r - A)_c^(k_c) with (r - A)_c = sum_d M_cd xi_d,
+// M_cd = (R_d)_c / N_d, expanded by multiplying out the linear forms one at a time.
+void build_mono_transforms(const Plan& P, std::vector<double>* out) {
+  out->assign((size_t)kMonoStride * P.nlev, 0.0);
+  constexpr int D = kSkewDeg + 1;
+  for (int k = 0; k < P.nlev; ++k) {
+    double M[3][3];
+    for (int c = 0; c < 3; ++c)
+      for (int d = 0; d < 3; ++d) M[c][d] = P.lat[3 * d + c] / P.lev[k].N[d];
+    double* blk = out->data() + (size_t)kMonoStride * k;
+    for (int n = 0; n <= kSkewDeg; ++n)
+      for (int c2 = 0; c2 <= n; ++c2)
+        for (int c1 = 0; c1 <= n - c2; ++c1) {
+          const int kc[3] = {n - c1 - c2, c1, c2};
+          // poly[x0][x1][x2]: coefficient of xi0^x0 xi1^x1 xi2^x2
+          std::vector<double> poly(D * D * D, 0.0), nxt(D * D * D);
+          poly[0] = 1.0;
+          int deg = 0;
+          for (int c = 0; c < 3; ++c)
+            for (int r = 0; r < kc[c]; ++r) {
+              std::fill(nxt.begin(), nxt.end(), 0.0);
+              for (int x2 = 0; x2 <= deg; ++x2)
+                for (int x1 = 0; x1 <= deg - x2; ++x1) {
+                  const int x0 = deg - x1 - x2;
+                  const double v = poly[(x0 * D + x1) * D + x2];
+                  if (v == 0.0) continue;
+                  nxt[((x0 + 1) * D + x1) * D + x2] += v * M[c][0];
+                  nxt[(x0 * D + x1 + 1) * D + x2] += v * M[c][1];
+                  nxt[(x0 * D + x1) * D + x2 + 1] += v * M[c][2];
+                }
+              poly.swap(nxt);
+              ++deg;
+            }
+          double* row = blk + mono_off(n) + (size_t)hidx(n, c1, c2) * nh(n);
+          for (int x2 = 0; x2 <= n; ++x2)
+            for (int x1 = 0; x1 <= n - x2; ++x1) row[hidx(n, x1, x2)] = poly[((n - x1 - x2) * D + x1) * D + x2];
+        }
+  }
+}
+
 long long default_chunk(long long nent) {
   return std::min<long long>(INT32_MAX, std::max(kChunkMin, (nent + kChunkDiv - 1) / kChunkDiv));
 }
@@ -503,20 +568,42 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     return GPW_EINVAL;
   }
   const double* lat = desc->lattice;
+  for (int i = 0; i < 9; ++i) plan->lat[i] = lat[i];
+  plan->skew = false;
   for (int i = 0; i < 3; ++i)
     for (int j = 0; j < 3; ++j)
-      if (i != j && lat[3 * i + j] != 0.0) {
-        set_error("gpw_plan: only orthorhombic (diagonal) lattices are supported");
+      if (i != j && lat[3 * i + j] != 0.0) plan->skew = true;
+  if (!plan->skew) {
+    for (int d = 0; d < 3; ++d) {
+      plan->L[d] = lat[4 * d];
+      if (!(plan->L[d] > 0)) {
+        set_error("gpw_plan: lattice lengths must be positive");
         return GPW_EINVAL;
       }
-  for (int d = 0; d < 3; ++d) {
-    plan->L[d] = lat[4 * d];
-    if (!(plan->L[d] > 0)) {
-      set_error("gpw_plan: lattice lengths must be positive");
+    }
+    plan->omega = plan->L[0] * plan->L[1] * plan->L[2];
+  } else {
+    // rows R_d, lengths |R_d|, reciprocal rows b_0 = R_1 x R_2 / V, b_1 = R_2 x R_0 / V,
+    // b_2 = R_0 x R_1 / V with V = R_0 . (R_1 x R_2)
+    const double* R[3] = {lat, lat + 3, lat + 6};
+    double cr[3][3];
+    for (int d = 0; d < 3; ++d) {
+      const double* a = R[(d + 1) % 3];
+      const double* b = R[(d + 2) % 3];
+      cr[d][0] = a[1] * b[2] - a[2] * b[1];
+      cr[d][1] = a[2] * b[0] - a[0] * b[2];
+      cr[d][2] = a[0] * b[1] - a[1] * b[0];
+      plan->L[d] = std::sqrt(R[d][0] * R[d][0] + R[d][1] * R[d][1] + R[d][2] * R[d][2]);
+    }
+    const double V = R[0][0] * cr[0][0] + R[0][1] * cr[0][1] + R[0][2] * cr[0][2];
+    if (!(std::fabs(V) > 0) || !std::isfinite(V)) {
+      set_error("gpw_plan: the lattice rows must be linearly independent");
       return GPW_EINVAL;
     }
+    for (int d = 0; d < 3; ++d)
+      for (int c = 0; c < 3; ++c) plan->rec[3 * d + c] = cr[d][c] / V;
+    plan->omega = std::fabs(V);
   }
-  plan->omega = plan->L[0] * plan->L[1] * plan->L[2];
   if (desc->nlevels < 1 || desc->nlevels > GPW_MAX_LEVELS) {
     set_error("gpw_plan: nlevels must be in 1..GPW_MAX_LEVELS");
     return GPW_EINVAL;
@@ -578,6 +665,25 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
         set_error("gpw_plan: the kinetic-energy-density kernels (GPW_TAU) support shells up to d");
         return GPW_EINVAL;
       }
+  if (plan->skew) {
+    // the non-orthogonal kernels: LDA exchange, no kinetic-energy density, 4x8x16
+    // sub-boxes for both passes
+    if (plan->xc != GPW_XC_LDA_X || plan->xr) {
+      set_error("gpw_plan: non-orthogonal cells support the LDA Fock build and gradient only");
+      return GPW_EINVAL;
+    }
+    const bool tc = desc->tile[0] || desc->tile[1] || desc->tile[2];
+    const bool ti = desc->tile_integ[0] || desc->tile_integ[1] || desc->tile_integ[2];
+    if ((tc && !(desc->tile[0] == kT0 && desc->tile[1] == kT1 && desc->tile[2] == kT2)) ||
+        (ti && !(desc->tile_integ[0] == kT0 && desc->tile_integ[1] == kT1 &&
+                 desc->tile_integ[2] == kT2))) {
+      set_error("gpw_plan: non-orthogonal cells use the 4x8x16 sub-box for both passes");
+      return GPW_EINVAL;
+    }
+    plan->tile_i[0] = kT0;
+    plan->tile_i[1] = kT1;
+    plan->tile_i[2] = kT2;
+  }
   plan->nw_colloc_req = desc->colloc_warps;
   plan->natm = desc->natm;
   plan->nshell = desc->nshell;
@@ -628,6 +734,19 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     }
     for (int d = 0; d < 3; ++d) lv.nsb[d] = (lv.N[d] + plan->tile[d] - 1) / plan->tile[d];
     lv.weight = plan->omega / ((double)lv.N[0] * lv.N[1] * lv.N[2]);
+    for (int i = 0; i < 6; ++i) lv.gm[i] = 0.0;
+    for (int i = 0; i < 9; ++i) lv.fr[i] = 0.0;
+    if (plan->skew) {
+      static const int pd[6][2] = {{0, 0}, {1, 1}, {2, 2}, {0, 1}, {0, 2}, {1, 2}};
+      for (int i = 0; i < 6; ++i) {
+        const int d = pd[i][0], e = pd[i][1];
+        double g = 0.0;
+        for (int c = 0; c < 3; ++c) g += (lat[3 * d + c] / lv.N[d]) * (lat[3 * e + c] / lv.N[e]);
+        lv.gm[i] = g;
+      }
+      for (int d = 0; d < 3; ++d)
+        for (int c = 0; c < 3; ++c) lv.fr[3 * d + c] = lv.N[d] * plan->rec[3 * d + c];
+    }
   }
   for (int k = 1; k < K; ++k)
     if (plan->E[k] > plan->E[k - 1]) {
@@ -692,6 +811,12 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   for (auto& v : atom_prims)
     std::stable_sort(v.begin(), v.end(), [&](int x, int y) { return prims[x].rcut > prims[y].rcut; });
   const double* X = desc->coords;
+  SkewBox skb;
+  skb.rec = plan->rec;
+  for (int d = 0; d < 3; ++d)
+    skb.blen[d] = std::sqrt(plan->rec[3 * d] * plan->rec[3 * d] +
+                            plan->rec[3 * d + 1] * plan->rec[3 * d + 1] +
+                            plan->rec[3 * d + 2] * plan->rec[3 * d + 2]);
   // atoms are screened in parallel (each thread keeps its own pair list); the sort
   // below fixes one order whatever the thread count
   const int sthr = plan_threads((long long)prims.size() * prims.size() / 64);
@@ -705,11 +830,19 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
       double rsum_max = atom_rmax[ia] + atom_rmax[ib];
       int nlo[3], nhi[3];
       for (int d = 0; d < 3; ++d) {
-        double dd = X[3 * ia + d] - X[3 * ib + d];
-        // one more image on each side than the atom-level bound: the exact
-        // per-primitive distance test below decides
-        nlo[d] = (int)std::floor((dd - rsum_max) / plan->L[d]) - 1;
-        nhi[d] = (int)std::ceil((dd + rsum_max) / plan->L[d]) + 1;
+        if (!plan->skew) {
+          double dd = X[3 * ia + d] - X[3 * ib + d];
+          // one more image on each side than the atom-level bound: the exact
+          // per-primitive distance test below decides
+          nlo[d] = (int)std::floor((dd - rsum_max) / plan->L[d]) - 1;
+          nhi[d] = (int)std::ceil((dd + rsum_max) / plan->L[d]) + 1;
+        } else {
+          // |f_d(A - B - T)| <= |A - B - T| |b_d| along the reciprocal row b_d
+          double f = 0.0;
+          for (int c = 0; c < 3; ++c) f += plan->rec[3 * d + c] * (X[3 * ia + c] - X[3 * ib + c]);
+          nlo[d] = (int)std::floor(f - rsum_max * skb.blen[d]) - 1;
+          nhi[d] = (int)std::ceil(f + rsum_max * skb.blen[d]) + 1;
+        }
       }
       for (int n0 = nlo[0]; n0 <= nhi[0]; ++n0)
         for (int n1 = nlo[1]; n1 <= nhi[1]; ++n1)
@@ -717,7 +850,9 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
             const int nn[3] = {n0, n1, n2};
             double Bt[3], AB2 = 0.0;
             for (int d = 0; d < 3; ++d) {
-              Bt[d] = X[3 * ib + d] + (double)nn[d] * plan->L[d];
+              Bt[d] = plan->skew ? X[3 * ib + d] + (((double)n0 * lat[d] + (double)n1 * lat[3 + d]) +
+                                                    (double)n2 * lat[6 + d])
+                                 : X[3 * ib + d] + (double)nn[d] * plan->L[d];
               double t = X[3 * ia + d] - Bt[d];
               AB2 += t * t;
             }
@@ -751,7 +886,8 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
                 const double Nl[3] = {(double)mesh[level][0], (double)mesh[level][1],
                                       (double)mesh[level][2]};
                 if (!pair_box(cab, kab, pa.l, pb.l, std::sqrt(dA2), std::sqrt(dB2), ap,
-                              desc->tau, P, Nl, plan->L, t.lo, t.hi))
+                              desc->tau, P, Nl, plan->L, t.lo, t.hi,
+                              plan->skew ? &skb : nullptr))
                   continue;
                 t.a = a;
                 t.b = b;
@@ -844,7 +980,10 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     H->ids2[p] = make_int4(pa.atom, pb.atom, t.a < t.b ? 2 : 1, 0);
     for (int d = 0; d < 3; ++d) {
       H->geo[8 * p + d] = X[3 * pa.atom + d];
-      H->geo[8 * p + 3 + d] = X[3 * pb.atom + d] + (double)t.img[d] * plan->L[d];
+      H->geo[8 * p + 3 + d] =
+          plan->skew ? X[3 * pb.atom + d] + (((double)t.img[0] * lat[d] + (double)t.img[1] * lat[3 + d]) +
+                                             (double)t.img[2] * lat[6 + d])
+                     : X[3 * pb.atom + d] + (double)t.img[d] * plan->L[d];
     }
     H->geo[8 * p + 6] = pa.alpha;
     H->geo[8 * p + 7] = pb.alpha;
@@ -930,6 +1069,8 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   // the part buffer also holds the x-contracted tables of collocation (never live at the
   // same time as the task W tensors)
   plan->part_total = std::max(part_total, xt_total);
+
+  if (plan->skew) build_mono_transforms(*plan, &H->mono_t);
 
   // ---- V assembly groups: runs of pairs with the same contracted shell pair
   for (long long p = 0; p < np;) {

@@ -14,11 +14,15 @@ struct HostArrays {
   std::vector<int4> task_c, task_i;   // 2 int4 per task
   std::vector<long long> sub_off_c, sub_off_i;
   std::vector<long long> toff_c, toff_i;  // per-pair task prefix sums (device-built lists)
+  std::vector<double> mono_t;  // non-orthogonal cells: monomial transforms per level
   std::vector<int4> work_c, work_i;   // {plan slot, level, sub-box, tasks}
   std::vector<int4> groups;
   std::vector<long long> atom_off;
   std::vector<int> atom_list;
 };
+
+// Monomial transforms of a non-orthogonal cell (one block per level).
+void build_mono_transforms(const Plan& P, std::vector<double>* out);
 
 // Default integration chunk for nent tasks: max(kChunkMin, ceil(nent / kChunkDiv)).
 long long default_chunk(long long nent);

@@ -47,7 +47,7 @@ def tiny14() -> System:
     return workloads.tiny().with_tau(1e-14)
 
 
-TRICLINIC = np.array([[1.0, 0.0, 0.0], [0.28, 0.96, 0.0], [-0.21, 0.17, 0.95]])
+TRICLINIC = workloads.TRICLINIC
 
 
 def skewed(seed: int = 5, L: float = 6.0, lattice=None, **kw) -> System:

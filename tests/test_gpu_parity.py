@@ -193,8 +193,7 @@ def test_empty_screening(gpw):
 def test_invalid_inputs(gpw):
     s = workloads.tiny()
     bad = s.with_coords(s.coords)
-    bad.lattice = s.lattice.copy()
-    bad.lattice[0, 1] = 0.5
+    bad.lattice = np.array([[5.0, 0.0, 0.0], [5.0, 0.0, 0.0], [0.0, 0.0, 5.0]])  # dependent rows
     with pytest.raises(gpw.GpwError) as e:
         gpw.Plan(bad)
     assert e.value.code == -1

@@ -16,11 +16,15 @@ def lib():
     return binding.load()
 
 
-@pytest.mark.parametrize("name", ["tiny", "tiny14", "resolved", "water4", "water32"])
+@pytest.mark.parametrize("name", ["tiny", "tiny14", "resolved", "water4", "water32", "skewed",
+                                  "sheared", "water4_triclinic"])
 def test_pair_table_and_counts_match_oracle(lib, name):
     s = {"tiny": workloads.tiny, "tiny14": systems.tiny14, "resolved": systems.resolved,
          "water4": lambda: workloads.config("water4"),
-         "water32": lambda: workloads.config("water32")}[name]()
+         "water32": lambda: workloads.config("water32"),
+         "skewed": systems.skewed,
+         "sheared": lambda: systems.sheared(systems.resolved(seed=7)),
+         "water4_triclinic": lambda: workloads.config("water4_triclinic")}[name]()
     p = binding.Plan(s, commit=False)
     op = oracle.Plan(s)
     a, b = p.pair_table(), op.pair_table()
@@ -79,9 +83,17 @@ def test_validation(lib):
     _expect_error(s, colloc_warps=5)
     _expect_error(s, xc="b88")
     _expect_error(s, host_threads=-1)
+    sk = systems.skewed()
+    binding.Plan(sk, commit=False).close()           # a triclinic cell plans ...
+    _expect_error(sk, xc="pbe_x")                     # ... with LDA exchange only
+    _expect_error(sk, tau=True)
+    _expect_error(sk, tile=(8, 8, 32))                # and the 4x8x16 sub-boxes
+    flat = sk.with_tau(sk.tau)
+    flat.lattice = np.array([[6.0, 0.0, 0.0], [6.0, 0.0, 0.0], [0.0, 0.0, 6.0]])
+    _expect_error(flat)                               # dependent rows
     bad = s.with_tau(s.tau)
     bad.lattice = bad.lattice.copy()
-    bad.lattice[0, 1] = 0.5                           # not orthorhombic
+    bad.lattice[1, 1] = -bad.lattice[1, 1]            # negative length of an orthorhombic cell
     _expect_error(bad)
     neg = s.with_tau(s.tau)
     neg.exponents = -np.abs(neg.exponents)            # exponents must be positive

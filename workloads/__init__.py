@@ -259,6 +259,24 @@ def water256(seed: int = 3) -> System:
     return water_box(256, 37.3, seed, name="water256")
 
 
+# a triclinic cell shape (rows; angles about 74, 103 and 79 degrees), volume 0.912 L^3
+TRICLINIC = np.array([[1.0, 0.0, 0.0], [0.28, 0.96, 0.0], [-0.21, 0.17, 0.95]])
+
+
+def triclinic(s: System) -> System:
+    """The cubic system s moved into a triclinic cell of the same volume: lattice rows
+    L' TRICLINIC with L'^3 det(TRICLINIC) = L^3, every atom at the same fractional
+    position (molecules are sheared with the cell: a synthetic non-orthogonal input)."""
+    import copy
+    L = float(s.lattice[0, 0])
+    scale = L / float(np.linalg.det(TRICLINIC)) ** (1.0 / 3.0)
+    out = copy.copy(s)
+    out.lattice = np.ascontiguousarray(scale * TRICLINIC)
+    out.coords = np.ascontiguousarray((s.coords / L) @ out.lattice)
+    out.name = s.name + "-triclinic"
+    return out
+
+
 def small_water(nwat: int = 4, seed: int = 11, **kw) -> System:
     """A water box at the 32-water density: L = 18.64 (n/32)^(1/3)."""
     return water_box(nwat, 18.64 * (nwat / 32.0) ** (1.0 / 3.0), seed, **kw)
@@ -329,9 +347,13 @@ def stream_requests(count: int = 400, seed: int = 4, rate: float | None = None):
 
 
 def config(name: str) -> System:
-    """Named workloads: tiny, water32, carbon, water256, water4."""
+    """Named workloads: tiny, water32, carbon, water256, water4, water8 and the triclinic
+    water4, water32 and water256 (non-orthogonal cells)."""
     return {
         "tiny": tiny, "water32": water32, "carbon": carbon, "water256": water256,
         "water4": lambda: small_water(4, seed=11),
         "water8": lambda: small_water(8, seed=12),
+        "water4_triclinic": lambda: triclinic(small_water(4, seed=11)),
+        "water32_triclinic": lambda: triclinic(water32()),
+        "water256_triclinic": lambda: triclinic(water256()),
     }[name]()
