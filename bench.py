@@ -48,9 +48,15 @@ def _workload_desc(name: str, system, stats) -> str:
     """What one step computes on the named workload (sizes from the system and plan)."""
     if name == WORKLOAD:
         return WORKLOAD_DESC
-    L = float(system.lattice[0][0])
-    mesh = "/".join(str(int(m[0])) for m in stats["meshes"])
-    return (f"{name}: cubic L={L:.2f} Bohr, {system.natm} atoms, {system.nao} Cartesian AOs, "
+    import numpy as np
+    lat = np.asarray(system.lattice, dtype=float)
+    mesh = "/".join("x".join(str(int(x)) for x in m) for m in stats["meshes"])
+    if np.all(lat == np.diag(np.diag(lat))):
+        cell = f"orthorhombic L={'/'.join(f'{x:.2f}' for x in np.diag(lat))} Bohr"
+    else:
+        cell = ("triclinic rows " + " ".join("(" + ",".join(f"{x:.2f}" for x in r) + ")" for r in lat)
+                + " Bohr")
+    return (f"{name}: {cell}, {system.natm} atoms, {system.nao} Cartesian AOs, "
             f"{system.cutoff_ha:g} Ha, {stats['nlevels']} levels ({mesh}), tau={system.tau:g}; "
             f"step = gpw_fock_grad (V, energies, Hxc gradient)")
 
@@ -289,7 +295,7 @@ def per_config(a):
     import workloads
     import paper_2603_24881_gb300 as gpw
     gpw.load()
-    for name in ("tiny", "water32", "carbon", "water256"):
+    for name in ("tiny", "water32", "carbon", "water256", "water32_triclinic", "water256_triclinic"):
         s = workloads.config(name)
         plan = gpw.Plan(s)
         st = plan.stats()
@@ -403,7 +409,7 @@ def main():
     dom = max(ph_flops, key=lambda k: prof["ms"][k])
     per_launch_ms = prof["ms"][dom] / max(prof["count"][dom], 1)
     achieved = ph_flops[dom] / (per_launch_ms * 1e-3) / 1e12
-    tr = TRAFFIC.get(dom)
+    tr = TRAFFIC.get(dom) if a.workload == WORKLOAD else None
     traffic = tr["bytes_per_launch"] if tr and tr.get("src_sha") == _kernels_sha() else None
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,

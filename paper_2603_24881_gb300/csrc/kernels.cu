@@ -136,6 +136,27 @@ __global__ void tables_kernel(long long np, const KLevels K, const int4* __restr
         v *= u;
       }
     }
+    if (skew) {
+      // cross-factor row seeds (layout at skew_seeds): for the row pairs (0,1), (0,2), (1,2)
+      // and every box position x along the first row, U[x] = exp(c a_d(x) a_e(0)) and
+      // Q[x] = exp(c a_d(x)), a_d(x) = lo_d + x - p_d, c = -2 alpha_p G_de, so that
+      // exp(c a_d(x) a_e(y)) = U[x] Q[x]^y
+      double* sd = tab + base + (long long)(L + 2 + xr) * ntot;
+      const int pd[3][3] = {{0, 1, 3}, {0, 2, 4}, {1, 2, 5}};
+      const int soff[3] = {0, 2 * n[0], 4 * n[0]};
+      const int items = 2 * n[0] + n[1];
+      for (int it = lane; it < items; it += 32) {
+        const int k = it < n[0] ? 0 : (it < 2 * n[0] ? 1 : 2);
+        const int x = it - (k == 0 ? 0 : (k == 1 ? n[0] : 2 * n[0]));
+        const int d = pd[k][0], e = pd[k][1];
+        const double c = -2.0 * ap * lv.gm[pd[k][2]];
+        const double ad = (double)(lo[d] + x) - pg[d];
+        const double ae = (double)lo[e] - pg[e];
+        const int len = k == 2 ? n[1] : n[0];
+        sd[soff[k] + x] = exp(c * ad * ae);
+        sd[soff[k] + len + x] = exp(c * ad);
+      }
+    }
   }
 }
 
@@ -320,7 +341,7 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
                                             const double* __restrict__ sg2, double* __restrict__ sT2,
                                             const int* __restrict__ s_row,
                                             const int* __restrict__ s_qi, double* __restrict__ acc,
-                                            int lane, const double* __restrict__ sE = nullptr) {
+                                            int lane, const double* __restrict__ sR = nullptr) {
   constexpr int Q = T0 * T1;
   const float inv01 = __frcp_rn((float)m01), inv2 = __frcp_rn((float)m2);
   {
@@ -335,6 +356,7 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
 #pragma unroll
         for (int l1 = 0; l1 <= L; ++l1)
           if (l1 <= L - l2) a = fma(xr[l1 * T0], gr[l1 * T1], a);
+        if constexpr (SK) a *= sR[(pi & 255) * T1 + (pi >> 8)];  // R01(i0, i1)
         sT2[l2 * Q + q] = a;
       }
       q += dq;
@@ -365,7 +387,10 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
       const double* ga = sg2 + iA;
       const double* gb = sg2 + iB;
       if constexpr (SK) {
-        // non-orthogonal cell: the pair value times its cross factor E(q, i2)
+        // non-orthogonal cell: R01 is in T2 already; times R02(i0, i2) R12(i1, i2)
+        const double* r02 = sR + T0 * T1;
+        const double* r12 = r02 + T0 * T2;
+        const int pa_i = s_qi[qa], pb_i = s_qi[qb];
         if (base + 32 < items) {
           double sa = 0.0, sb = 0.0;
 #pragma unroll
@@ -373,13 +398,15 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
             sa = fma(ta[l2 * Q], ga[l2 * T2], sa);
             sb = fma(tb[l2 * Q], gb[l2 * T2], sb);
           }
-          if (okA) *pa = fma(sE[qa * T2 + iA], sa, *pa);
-          if (okB) *pb = fma(sE[qb * T2 + iB], sb, *pb);
+          const double ea = r02[(pa_i & 255) * T2 + iA] * r12[(pa_i >> 8) * T2 + iA];
+          const double eb = r02[(pb_i & 255) * T2 + iB] * r12[(pb_i >> 8) * T2 + iB];
+          if (okA) *pa = fma(ea, sa, *pa);
+          if (okB) *pb = fma(eb, sb, *pb);
         } else if (okA) {
           double sa = 0.0;
 #pragma unroll
           for (int l2 = 0; l2 <= L; ++l2) sa = fma(ta[l2 * Q], ga[l2 * T2], sa);
-          *pa = fma(sE[qa * T2 + iA], sa, *pa);
+          *pa = fma(r02[(pa_i & 255) * T2 + iA] * r12[(pa_i >> 8) * T2 + iA], sa, *pa);
         }
       } else if (base + 32 < items) {
         double ra = okA ? *pa : 0.0, rb = okB ? *pb : 0.0;
@@ -417,43 +444,49 @@ template <int T0, int T1, int T2>
 struct SkewRows {
   static constexpr int kSize = T0 * T1 + T0 * T2 + T1 * T2;
   static_assert(2 * T0 + T1 <= 32, "one lane per cross-factor row");
+  // seeds per pair after its 1-D tables: U01, Q01, U02, Q02 (n0 each), U12, Q12 (n1 each)
 };
 
-template <int T0, int T1, int T2>
-__device__ __forceinline__ void skew_rows(const PlanView& pv, const LevelInfo& lv, const Task& tk,
-                                          double* __restrict__ sR, int lane) {
-  const double* g = pv.geo + 8 * (long long)tk.p;
-  const double aa = g[6], ab = g[7], ap = aa + ab;
-  const int4 ha = __ldg(pv.hot_a + tk.p);
-  const int lo[3] = {ha.x, ha.y, ha.z};
-  double eta0[3];
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    double pgd = 0.0;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) pgd += lv.fr[3 * d + c] * ((aa * g[c] + ab * g[3 + c]) / ap);
-    eta0[d] = (double)(lo[d] + tk.t[d]) - pgd;
+// x^n for a small non-negative integer n, by squaring
+__device__ __forceinline__ double ipow_d(double x, int n) {
+  double r = 1.0;
+  while (n > 0) {
+    if (n & 1) r *= x;
+    x *= x;
+    n >>= 1;
   }
+  return r;
+}
+
+// The task's cross-factor rows from the pair's seeds (tables_kernel): row i of the pair
+// (d, e) starts at U[x] Q[x]^(t_e) (x = t_d + i) and advances by Q[x] per step along e.
+template <int T0, int T1, int T2>
+__device__ __forceinline__ void skew_rows(const PlanView& pv, const Task& tk, long long toff,
+                                          double* __restrict__ sR, int lane) {
   const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
-  // row r: (first axis, second axis, metric entry, row index, destination, stride)
-  int d, e, gi, i, stride, len;
+  const int n0 = tk.n[0], n1 = tk.n[1];
+  const double* sd = pv.tab + toff + (long long)(tk.L + 2 + pv.xr) * (n0 + n1 + tk.n[2]);
+  int i, len, te;
+  const double* U;
   double* dst;
   if (lane < m0) {
-    d = 0; e = 1; gi = 3; i = lane; dst = sR + i * T1; stride = T1; len = m1;
+    i = lane; U = sd; te = tk.t[1]; len = m1; dst = sR + i * T1;
+    U += tk.t[0] + i;
   } else if (lane < 2 * m0) {
-    d = 0; e = 2; gi = 4; i = lane - m0; dst = sR + T0 * T1 + i * T2; stride = T2; len = m2;
+    i = lane - m0; U = sd + 2 * n0; te = tk.t[2]; len = m2; dst = sR + T0 * T1 + i * T2;
+    U += tk.t[0] + i;
   } else if (lane < 2 * m0 + m1) {
-    d = 1; e = 2; gi = 5; i = lane - 2 * m0; dst = sR + T0 * T1 + T0 * T2 + i * T2; stride = T2; len = m2;
+    i = lane - 2 * m0; U = sd + 4 * n0; te = tk.t[2]; len = m2; dst = sR + T0 * T1 + T0 * T2 + i * T2;
+    U += tk.t[1] + i;
   } else {
     return;
   }
-  (void)stride;
-  const double c = -2.0 * ap * lv.gm[gi] * (eta0[d] + (double)i);
-  double v = exp(c * eta0[e]);
-  const double r = exp(c);
+  // Q[x] sits one row length after U[x]: n0 for the pairs (0,1), (0,2); n1 for (1,2)
+  const double q = U[lane < 2 * m0 ? n0 : n1];
+  double v = U[0] * ipow_d(q, te);
   for (int j = 0; j < len; ++j) {
     dst[j] = v;
-    v *= r;
+    v *= q;
   }
 }
 
@@ -510,10 +543,8 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
   double* sT2 = stage_base + 2 * bufn;
   int* s_row = reinterpret_cast<int*>(sT2 + lp * T0 * T1);
   int* s_qi = s_row + T0 * T1;
-  // non-orthogonal cells: the task's cross factors E[q][i2] and their rows, after the
-  // regular per-warp staging
-  double* sE = stage_base + ((Lay::stage(lp) + 1) & ~1);
-  double* sR = sE + T0 * T1 * T2;
+  // non-orthogonal cells: the task's cross-factor rows, after the regular per-warp staging
+  double* sR = stage_base + ((Lay::stage(lp) + 1) & ~1);
   __syncthreads();
 
   // staging buffer b: [X window xrows*T0][g1 lp*T1][g2 lp*T2]
@@ -591,23 +622,11 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
         s_qi[q] = i0 | (i1 << 8);
         s_row[q] = ((tk.u[0] + i0) * T1 + (tk.u[1] + i1)) * T2 + tk.u[2];
       }
-      if constexpr (SK) {
-        skew_rows<T0, T1, T2>(pv, lv, tk, sR, lane);
-        __syncwarp();
-        const double* r01 = sR;
-        const double* r02 = sR + T0 * T1;
-        const double* r12 = r02 + T0 * T2;
-        const float inv2 = __frcp_rn((float)m2);
-        for (int it = lane; it < m01 * m2; it += 32) {
-          const int q = fdiv(it, inv2), i2 = it - q * m2;
-          const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
-          sE[q * T2 + i2] = r01[i0 * T1 + i1] * r02[i0 * T2 + i2] * r12[i1 * T2 + i2];
-        }
-      }
+      if constexpr (SK) skew_rows<T0, T1, T2>(pv, tk, __ldg(tab_off + tk.p), sR, lane);
       __syncwarp();
 #define GPW_COLLOC_L(LL)                                                                     \
   case LL:                                                                                   \
-    colloc_task<LL, T0, T1, T2, SK>(m01, m2, sX, sg1, sg2, sT2, s_row, s_qi, acc, lane, sE);  \
+    colloc_task<LL, T0, T1, T2, SK>(m01, m2, sX, sg1, sg2, sT2, s_row, s_qi, acc, lane, sR);  \
     break;
       switch (L) {
         GPW_COLLOC_L(0) GPW_COLLOC_L(1) GPW_COLLOC_L(2) GPW_COLLOC_L(3) GPW_COLLOC_L(4)
@@ -762,9 +781,8 @@ __global__ void __launch_bounds__(NW * 32)
       const double* vbase = sv;
       int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
       if constexpr (SK) {
-        skew_rows<T0, T1, T2>(pv, lv, tk, sR, lane);
+        skew_rows<T0, T1, T2>(pv, tk, __ldg(tab_off + tk.p), sR, lane);
         __syncwarp();
-        const double* r01 = sR;
         const double* r02 = sR + T0 * T1;
         const double* r12 = r02 + T0 * T2;
         const float inv2 = __frcp_rn((float)m2), inv1 = __frcp_rn((float)m1);
@@ -772,7 +790,7 @@ __global__ void __launch_bounds__(NW * 32)
           const int q = fdiv(it, inv2), i2 = it - q * m2;
           const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
           sVE[(i0 * T1 + i1) * P2 + i2] = sv[((u0 + i0) * T1 + (u1 + i1)) * P2 + u2 + i2] *
-                                          (r01[i0 * T1 + i1] * r02[i0 * T2 + i2] * r12[i1 * T2 + i2]);
+                                          (r02[i0 * T2 + i2] * r12[i1 * T2 + i2]);
         }
         __syncwarp();
         vbase = sVE;
@@ -789,6 +807,7 @@ __global__ void __launch_bounds__(NW * 32)
           const double* gr = sg2 + l2 * P2;
           double a = 0.0;
           for (int i2 = 0; i2 < m2; ++i2) a = fma(vr[i2], gr[i2], a);
+          if constexpr (SK) a *= sR[i0 * T1 + i1];  // R01(i0, i1)
           sU[l2 * kUS + i1 * P0 + i0] = a;
         }
       }
@@ -1755,7 +1774,7 @@ constexpr int kNW = 8;
 
 // per-warp staging doubles of the non-orthogonal variants (cross factors and their rows)
 template <int T0, int T1, int T2>
-int colloc_skew_extra() { return T0 * T1 * T2 + SkewRows<T0, T1, T2>::kSize; }
+int colloc_skew_extra() { return SkewRows<T0, T1, T2>::kSize; }
 template <int T0, int T1, int T2>
 int integ_skew_extra() { return IntegLayout<T0, T1, T2>::kSV + SkewRows<T0, T1, T2>::kSize; }
 
