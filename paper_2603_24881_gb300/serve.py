@@ -298,9 +298,15 @@ class Server:
             with self._cv:
                 self._admit()
                 slot = self._free_slot()
-                if slot is not None:
+                if slot is not None and self._staged:
+                    # one batch holds cells of one kind (orthorhombic or not), oldest first
+                    kind = _skewed(self._staged[0].system)
+                    keep = collections.deque()
                     while self._staged and len(reqs) < self.max_batch:
-                        reqs.append(self._staged.popleft())
+                        r = self._staged.popleft()
+                        (reqs if _skewed(r.system) == kind else keep).append(r)
+                    keep.extend(self._staged)
+                    self._staged = keep
                 if not reqs:
                     idle = not (self._ready or self._staged or self._committing or
                                 self._flights or self._finishing)
@@ -329,6 +335,12 @@ class Server:
                         if self._staged and self._free_slot() is not None:
                             break
                     time.sleep(0.0002)
+
+
+def _skewed(system) -> bool:
+    """Non-orthogonal cell (a non-diagonal lattice): its plans batch only with their kind."""
+    lat = np.asarray(system.lattice, dtype=np.float64)
+    return bool(np.any(lat != np.diag(np.diag(lat))))
 
 
 def run_plain(systems, want_grads):

@@ -147,3 +147,21 @@ def test_server_memory_budget_and_failures(gpw, alone):
         _same(dict(V=r.V, grad=r.grad, EH=r.EH, Ex=r.Ex), alone[i])
     assert stats["peak_bytes"] <= budget
     assert stats["rejected"] == 2
+
+
+def test_server_mixes_cell_kinds(gpw):
+    # orthorhombic and triclinic requests in one stream: batches hold one kind each and
+    # every result equals its request run alone
+    from paper_2603_24881_gb300.serve import Server
+    systems = [workloads.small_water(4, seed=111), workloads.triclinic(workloads.small_water(4, seed=112)),
+               workloads.small_water(4, seed=113), workloads.triclinic(workloads.small_water(4, seed=114))]
+    ref = []
+    for s in systems:
+        p = gpw.Plan(s)
+        r = p.fock_grad(s.D)
+        ref.append(dict(V=r["V"].cpu().numpy(), grad=r["grad"].cpu().numpy(), EH=r["EH"], Ex=r["Ex"]))
+        p.close()
+    with Server(max_batch=4, streams=2) as srv:
+        res = [f.result(timeout=300) for f in [srv.submit(s, want_grad=True) for s in systems]]
+    for r, a in zip(res, ref):
+        _same(dict(V=r.V, grad=r.grad, EH=r.EH, Ex=r.Ex), a)
