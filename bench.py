@@ -160,10 +160,11 @@ def _gpu_id(torch) -> str:
 
 
 # ------------------------------------------------------------------ oracle -----
-def oracle_sample(sys_, stride: int, offset: int = 0, threads: int = 0):
+def oracle_sample(sys_, stride: int, offset: int = 0, threads: int = 0, ops=None):
     """Time the CPU oracle (as it stands) on every stride-th pair of the workload:
     separable collocation, integration and the gradient contraction.  Returns
-    (model flops, seconds, pairs, pair-points, threads)."""
+    (model flops, seconds, pairs, pair-points, threads); `ops`, if a dict, receives the
+    seconds of each of the three."""
     import numpy as np
     import oracle
     p = oracle.Plan(sys_)
@@ -177,18 +178,33 @@ def oracle_sample(sys_, stride: int, offset: int = 0, threads: int = 0):
     nthr = threads or os.cpu_count() or 1
     t0 = time.perf_counter()
     sub.rho_levels(sys_.D, mode="separable", nthreads=nthr)
+    t1 = time.perf_counter()
     sub._pair_blocks(vl, nthreads=nthr)
+    t2 = time.perf_counter()
     sub._pair_blocks(vl, grad_D=sys_.D, nthreads=nthr)
-    dt = time.perf_counter() - t0
-    return flops, dt, len(idx), float(pts.sum()), nthr
+    t3 = time.perf_counter()
+    if ops is not None:
+        ops.update(eval_rho=t1 - t0, eval_mat=t2 - t1, eval_mat_ip1=t3 - t2)
+    return flops, t3 - t0, len(idx), float(pts.sum()), nthr
 
 
 def cpu_baseline(sys_, stride: int) -> dict:
-    f, dt, n, pts, nthr = oracle_sample(sys_, stride)
+    """The oracle on all host threads, and on one thread over a 16 times smaller sample:
+    model TFLOP/s, seconds and pair-points/s of each operation."""
+    ops = {}
+    f, dt, n, pts, nthr = oracle_sample(sys_, stride, ops=ops)
+    ops1 = {}
+    f1, dt1, n1, pts1, _ = oracle_sample(sys_, 16 * stride, threads=1, ops=ops1)
+    per = lambda o, p: {k: {"s": v, "pair_points_per_s": p / v} for k, v in o.items()}
     return {"value": f / dt / 1e12, "unit": "TFLOP/s", "cores": nthr, "kind": "oracle",
             "sample": f"every {stride}th screened pair of {WORKLOAD} ({n} pairs, {pts:.3e} "
                       f"pair-points): separable collocation + integration + gradient "
-                      f"contraction, {dt:.1f} s on {nthr} threads"}
+                      f"contraction, {dt:.1f} s on {nthr} threads",
+            "ops": per(ops, pts),
+            "single_thread": {"value": f1 / dt1 / 1e12, "unit": "TFLOP/s", "cores": 1,
+                              "sample": f"every {16 * stride}th pair ({n1} pairs, {pts1:.3e} "
+                                        f"pair-points), {dt1:.1f} s",
+                              "ops": per(ops1, pts1)}}
 
 
 def run_reference(a, rank, world):
