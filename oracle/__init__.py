@@ -510,18 +510,30 @@ class Plan:
         return vx, omega / float(np.prod(self.meshes[0])) * float(np.sum(ex))
 
     def _deriv(self, spec, d):
-        """Fourier derivative along axis d of a full (numpy-order) spectrum: i G_d spec,
-        with the Nyquist plane of an even axis set to zero (a reading: the derivative of
-        a real field stays real)."""
-        self._ortho_only("Fourier derivative")
+        """Fourier derivative along Cartesian axis d of a full (numpy-order) spectrum:
+        i G_d spec, with the Nyquist plane of an even axis set to zero (a reading: the
+        derivative of a real field stays real)."""
         mesh = tuple(int(m) for m in self.meshes[0])
-        f = np.fft.fftfreq(mesh[d], d=1.0 / mesh[d])
-        g = 2.0 * np.pi * f / self.L[d]
-        if mesh[d] % 2 == 0:
-            g[mesh[d] // 2] = 0.0
-        shape = [1, 1, 1]
-        shape[d] = mesh[d]
-        return spec * (1j * g).reshape(shape)
+        if self.ortho:
+            f = np.fft.fftfreq(mesh[d], d=1.0 / mesh[d])
+            g = 2.0 * np.pi * f / self.L[d]
+            if mesh[d] % 2 == 0:
+                g[mesh[d] // 2] = 0.0
+            shape = [1, 1, 1]
+            shape[d] = mesh[d]
+            return spec * (1j * g).reshape(shape)
+        # non-orthogonal cell: Cartesian component d of G = 2 pi sum_e m_e b_e, with the
+        # Nyquist frequency of an even mesh axis taken as zero (as above, per axis)
+        B = reciprocal(self.lat)
+        m = []
+        for e in range(3):
+            f = np.fft.fftfreq(mesh[e], d=1.0 / mesh[e])
+            if mesh[e] % 2 == 0:
+                f[mesh[e] // 2] = 0.0
+            m.append(f)
+        g = 2.0 * np.pi * (m[0][:, None, None] * B[0, d] + m[1][None, :, None] * B[1, d] +
+                           m[2][None, None, :] * B[2, d])
+        return spec * (1j * g)
 
     def pbe_x(self, rho_fine):
         """GGA exchange (Sec. II, GGA; PBE exchange): the density gradient from the

@@ -274,7 +274,9 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
     for (int dd = 0; dd < 3; ++dd)
       for (int m = 0; m < f.N[dd]; ++m) {
         const int sf = m < (f.N[dd] + 1) / 2 ? m : m - f.N[dd];
-        g1[o++] = (f.N[dd] % 2 == 0 && 2 * m == f.N[dd]) ? 0.0 : 2.0 * M_PI * (double)sf / P->L[dd];
+        g1[o++] = (f.N[dd] % 2 == 0 && 2 * m == f.N[dd])
+                      ? 0.0
+                      : (P->skew ? 2.0 * M_PI * (double)sf : 2.0 * M_PI * (double)sf / P->L[dd]);
       }
     GPW_TRY(upload(&d.g1tab, g1, &b));
   }

@@ -1680,7 +1680,11 @@ __global__ void fourier_deriv_kernel(const KLevels K, const double* __restrict__
     const int m1 = (int)(r % f.N[1]);
     const int m0 = (int)(r / f.N[1]);
     const int m = axis == 0 ? m0 : (axis == 1 ? m1 : m2);
-    const double g = __ldg(g1t + off + m);
+    // orthorhombic: the axis table holds (2 pi s)/L_d; non-orthogonal: the tables hold
+    // 2 pi s per mesh axis and the Cartesian component is sum_d 2 pi s_d (b_d)_axis
+    const double g = K.skew ? __ldg(g1t + m0) * K.rec[axis] + __ldg(g1t + f.N[0] + m1) * K.rec[3 + axis] +
+                                  __ldg(g1t + f.N[0] + f.N[1] + m2) * K.rec[6 + axis]
+                            : __ldg(g1t + off + m);
     const cufftDoubleComplex z = in[idx];
     if (subtract) {
       cufftDoubleComplex o = out[idx];
@@ -1839,6 +1843,7 @@ KLevels make_klevels(const Plan& p, bool integ) {
     const double* be = p.rec + 3 * pd[i][1];
     k.gq[i] = p.skew ? tp2 * (bd[0] * be[0] + bd[1] * be[1] + bd[2] * be[2]) : 0.0;
   }
+  for (int i = 0; i < 9; ++i) k.rec[i] = p.rec[i];
   return k;
 }
 

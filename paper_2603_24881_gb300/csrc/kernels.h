@@ -10,6 +10,7 @@ struct KLevels {
   int nlev;
   int skew;       // non-orthogonal cell: |G|^2 has cross terms
   double gq[3];   // their coefficients 2 (2 pi)^2 (b0.b1, b0.b2, b1.b2)
+  double rec[9];  // reciprocal rows b_d (Cartesian G = 2 pi sum_d s_d b_d)
 };
 
 KLevels make_klevels(const Plan& p, bool integ);

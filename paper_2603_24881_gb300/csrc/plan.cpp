@@ -666,10 +666,10 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
         return GPW_EINVAL;
       }
   if (plan->skew) {
-    // the non-orthogonal kernels: LDA exchange, no kinetic-energy density, 4x8x16
-    // sub-boxes for both passes
-    if (plan->xc != GPW_XC_LDA_X || plan->xr) {
-      set_error("gpw_plan: non-orthogonal cells support the LDA Fock build and gradient only");
+    // the non-orthogonal kernels: no kinetic-energy density, 4x8x16 sub-boxes for both
+    // passes
+    if (plan->xr) {
+      set_error("gpw_plan: the kinetic-energy-density kernels need an orthorhombic cell");
       return GPW_EINVAL;
     }
     const bool tc = desc->tile[0] || desc->tile[1] || desc->tile[2];

@@ -130,3 +130,18 @@ def test_skew_batch_and_limits(gpw):
     with pytest.raises(gpw.GpwError):
         gpw.Batch(2).set([plans[0], gpw.Plan(systems.resolved())])
     batch.close()
+
+
+def test_skew_gga_parity(gpw):
+    # PBE exchange in a triclinic cell: Cartesian Fourier derivatives from the
+    # reciprocal rows, against the oracle
+    s = CASES["skewed_spd"]()
+    op = oracle.Plan(s)
+    gp = gpw.Plan(s, xc="pbe_x")
+    out = gp.fock_grad(s.D)
+    r = op.fock(s.D, xc="pbe_x")
+    assert abs(out["EH"] - r["EH"]) <= 1e-8 and abs(out["Ex"] - r["Ex"]) <= 1e-8
+    assert _rel(out["V"].cpu().numpy(), r["V"]) <= RTOL
+    assert np.max(np.abs(out["grad"].cpu().numpy() - op.grad_levels(s.D, r["v_levels"]))) <= 1e-7
+    f = gp.fock(s.D, want_v=True)
+    assert _rel(f["v"].cpu().numpy(), r["v_fine"]) <= RTOL

@@ -579,3 +579,41 @@ def test_sheared_description_of_a_cubic_cell():
     ga = p.grad_levels(s.D, a["v_levels"])
     gb = q.grad_levels(s.D, b["v_levels"])
     assert np.max(np.abs(gb - ga)) <= 1e-8
+
+
+def test_skew_gga_energy_derivatives(res_skew):
+    # PBE exchange in a triclinic cell: dE/dD = V and the energy gradient against
+    # central differences (the Cartesian Fourier derivatives from the reciprocal rows)
+    s, p = res_skew
+    out = p.fock(s.D, xc="pbe_x")
+    rng = np.random.default_rng(4)
+    X = rng.standard_normal(s.D.shape)
+    X = X + X.T
+    h = 1e-5
+    fd = (p.energy(s.D + h * X, xc="pbe_x") - p.energy(s.D - h * X, xc="pbe_x")) / (2 * h)
+    assert fd == pytest.approx(float(np.sum(X * out["V"])), rel=1e-7)
+    g = p.grad_levels(s.D, out["v_levels"])
+    h = 1e-4
+    for atom, d in [(0, 2), (1, 0)]:
+        cp = s.coords.copy()
+        cm = s.coords.copy()
+        cp[atom, d] += h
+        cm[atom, d] -= h
+        fd = (p.with_coords(cp).energy(s.D, xc="pbe_x") -
+              p.with_coords(cm).energy(s.D, xc="pbe_x")) / (2 * h)
+        assert g[atom, d] == pytest.approx(fd, rel=1e-6, abs=1e-7)
+
+
+def test_sheared_description_gga():
+    # PBE exchange of the sheared description against the cubic one (odd meshes, so no
+    # Nyquist plane: the two descriptions' derivatives are the same functions)
+    s = systems.resolved(seed=7, shells=((0, 1), (1, 1), (2, 1)), natm=2, nlevels=2)
+    p = oracle.Plan(s)
+    s.meshes = np.array([[oracle._smooth7_even(int(1.6 * m)) + 1 for m in row] for row in p.meshes])
+    s.cutoff_ha = 0.0
+    s.rel_cutoff = 100.0
+    a = oracle.Plan(s).fock(s.D, xc="pbe_x")
+    b = oracle.Plan(systems.sheared(s)).fock(s.D, xc="pbe_x")
+    assert b["Ex"] == pytest.approx(a["Ex"], rel=1e-9)
+    assert b["EH"] == pytest.approx(a["EH"], rel=1e-9)
+    assert np.max(np.abs(b["V"] - a["V"])) <= 1e-9 * np.max(np.abs(a["V"]))
