@@ -16,9 +16,7 @@
  *
  * Conventions
  *   Units: Bohr and Hartree.  Any lattice (rows a1, a2, a3).  Non-orthogonal cells
- *   (App., non-orthogonal lattices) take the Fock build and gradient with LDA or PBE
- *   exchange and 4x8x16 sub-boxes; the kinetic-energy-density kernels need an
- *   orthorhombic (diagonal) lattice.
+ *   (App., non-orthogonal lattices) use 4x8x16 sub-boxes for both grid passes.
  *   Shells are Cartesian with angular momentum 0..3; within a shell the AO order is
  *   lexicographic with x^l first (d: xx, xy, xz, yy, yz, zz).  AOs follow the shell
  *   order of the descriptor.
@@ -162,8 +160,7 @@ typedef struct {
  * pair tensors are re-expanded between Cartesian and row monomials.
  * Returns GPW_EINVAL for a degenerate lattice, l > 3, nlevels outside
  * 1..GPW_MAX_LEVELS, non-positive exponents, meshes too small for the cutoff sphere,
- * or GPW_TAU / other sub-boxes on a non-orthogonal cell.  *out is set only on
- * success. */
+ * or other sub-boxes on a non-orthogonal cell.  *out is set only on success. */
 int gpw_plan(const gpw_desc* desc, void* stream, gpw_plan_t* out);
 
 /* Host phase of gpw_plan only: screening, levels and task lists on the CPU, no device

@@ -266,7 +266,7 @@ class Plan:
         self.sys = sys
         self.lat = np.ascontiguousarray(np.asarray(sys.lattice, dtype=np.float64).reshape(3, 3))
         self.ortho = is_orthorhombic(self.lat)
-        # orthorhombic lengths (the meta-GGA and GGA steps are orthorhombic only)
+        # lattice lengths along the rows of an orthorhombic cell
         self.L = np.ascontiguousarray(np.diag(self.lat).astype(np.float64))
         self.omega = float(np.prod(self.L)) if self.ortho else float(_lib().orc_volume(_p(self.lat)))
         self.prims = prims or primitives(sys)
@@ -327,13 +327,12 @@ class Plan:
         order = np.lexsort(t[:, ::-1].T)
         return t[order].astype(np.int64)
 
-    def _args(self, lengths=False):
-        """Pair arrays for the C oracle, with the lattice rows (or, for the orthorhombic
-        meta-GGA functions, the three lengths)."""
+    def _args(self):
+        """Pair arrays for the C oracle, with the lattice rows."""
         pr = self.prims
         return (_p(self.ab), _p(self.img), _p(self.lev), _p(self.lo), _p(self.hi),
                 _p(pr["center"]), _p(pr["l"]), _p(pr["alpha"]), _p(pr["cn"]), _p(pr["ao"]),
-                _p(self.L if lengths else self.lat), _p(self.meshes))
+                _p(self.lat), _p(self.meshes))
 
     def _ortho_only(self, what):
         if not self.ortho:
@@ -362,19 +361,17 @@ class Plan:
     def tau_levels(self, D, nthreads: int = 0):
         """Kinetic energy density of each level, tau_k = (1/2) sum D_mu,nu grad phi_mu .
         grad phi_nu over the pairs of that level (point by point, like Eq. rho_wrap)."""
-        self._ortho_only("tau_levels")
         lib = _lib()
         D = np.ascontiguousarray(D, dtype=np.float64)
         total = int(self.grid_off[-1])
         grids = np.zeros(total)
-        lib.orc_collocate_tau(ctypes.c_long(self.npairs), *self._args(True), _p(self.grid_off),
+        lib.orc_collocate_tau(ctypes.c_long(self.npairs), *self._args(), _p(self.grid_off),
                               ctypes.c_long(total), _p(D), ctypes.c_long(D.shape[0]), _p(grids),
                               ctypes.c_int(nthreads))
         return [grids[self.grid_off[k]:self.grid_off[k + 1]].reshape(tuple(self.meshes[k]))
                 for k in range(self.nlev)]
 
     def _tau_blocks(self, v_levels, grad_D=None, nthreads: int = 0):
-        self._ortho_only("meta-GGA integrals")
         lib = _lib()
         v = np.ascontiguousarray(np.concatenate([np.ascontiguousarray(x).ravel() for x in v_levels]))
         pr = self.prims
@@ -391,7 +388,7 @@ class Plan:
             gd = np.ascontiguousarray(grad_D, dtype=np.float64)
             nao = gd.shape[0]
         lib.orc_integrate_tau(ctypes.c_long(self.npairs), None, ctypes.c_long(self.npairs),
-                              *self._args(True), _p(self.grid_off), _p(v),
+                              *self._args(), _p(self.grid_off), _p(v),
                               None if gd is None else _p(gd), ctypes.c_long(nao), _p(xoff),
                               _p(xout), ctypes.c_int(nthreads))
         return xoff, xout, na

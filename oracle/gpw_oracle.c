@@ -25,8 +25,8 @@
  * R_d); grid point (i0, i1, i2) of an N-point level mesh sits at sum_d (i_d / N_d) R_d
  * and an image is T = sum_d n_d R_d.  With a diagonal lattice every formula reduces to
  * the orthorhombic one operation for operation (the off-diagonal terms add exact
- * zeros).  The separable mode and the meta-GGA functions are orthorhombic only; a
- * non-orthogonal cell (App., non-orthogonal lattices) is evaluated point by point.
+ * zeros).  The separable mode is orthorhombic only; a non-orthogonal cell (App.,
+ * non-orthogonal lattices) is evaluated point by point.
  * All arithmetic in double.  Build with -ffp-contract=off so that the screening
  * decisions are reproducible.
  */
@@ -652,7 +652,7 @@ static int orc_hidx(int d, int e) {
  * thread order. */
 void orc_collocate_tau(long npairs, const int* ab, const int* img, const int* lev,
                        const int* lo, const int* hi, const double* pc, const int* pl,
-                       const double* pal, const double* pcn, const long* pao, const double* Ld,
+                       const double* pal, const double* pcn, const long* pao, const double* lat,
                        const int* mesh, const long* grid_off, long grid_total, const double* D,
                        long nao, double* grids, int nthreads) {
   memset(grids, 0, sizeof(double) * grid_total);
@@ -673,15 +673,16 @@ void orc_collocate_tau(long npairs, const int* ab, const int* img, const int* le
 #pragma omp for schedule(dynamic, 16)
     for (long p = 0; p < npairs; ++p) {
       orc_pair_t q;
-      const double lat9[9] = {Ld[0], 0.0, 0.0, 0.0, Ld[1], 0.0, 0.0, 0.0, Ld[2]};
-      orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, lat9);
+      orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, lat);
       const int* N = mesh + 3 * q.lev;
-      double h[3] = {Ld[0] / N[0], Ld[1] / N[1], Ld[2] / N[2]};
+      double H[3][3];
+      orc_steps(lat, N, H);
       double* gl = g + grid_off[q.lev];
       for (int i0 = q.lo[0]; i0 <= q.hi[0]; ++i0)
         for (int i1 = q.lo[1]; i1 <= q.hi[1]; ++i1)
           for (int i2 = q.lo[2]; i2 <= q.hi[2]; ++i2) {
-            double r[3] = {i0 * h[0], i1 * h[1], i2 * h[2]};
+            double r[3];
+            orc_point(H, i0, i1, i2, r);
             double ua[3], ub[3], va, vb, ga[ORC_MAXCART][3], gb[ORC_MAXCART][3];
             for (int d = 0; d < 3; ++d) {
               ua[d] = r[d] - q.A[d];
@@ -714,11 +715,11 @@ void orc_collocate_tau(long npairs, const int* ab, const int* img, const int* le
 void orc_integrate_tau(long npairs, const long* sel, long nsel, const int* ab, const int* img,
                        const int* lev, const int* lo, const int* hi, const double* pc,
                        const int* pl, const double* pal, const double* pcn, const long* pao,
-                       const double* Ld, const int* mesh, const long* grid_off, const double* v,
+                       const double* lat, const int* mesh, const long* grid_off, const double* v,
                        const double* grad_D, long nao, const long* xoff, double* xout,
                        int nthreads) {
   long count = sel ? nsel : npairs;
-  double omega = Ld[0] * Ld[1] * Ld[2];
+  double omega = orc_volume(lat);
 #ifdef _OPENMP
   if (nthreads <= 0) nthreads = omp_get_max_threads();
 #endif
@@ -726,10 +727,10 @@ void orc_integrate_tau(long npairs, const long* sel, long nsel, const int* ab, c
   for (long s = 0; s < count; ++s) {
     long p = sel ? sel[s] : s;
     orc_pair_t q;
-    const double lat9[9] = {Ld[0], 0.0, 0.0, 0.0, Ld[1], 0.0, 0.0, 0.0, Ld[2]};
-    orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, lat9);
+    orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, lat);
     const int* N = mesh + 3 * q.lev;
-    double h[3] = {Ld[0] / N[0], Ld[1] / N[1], Ld[2] / N[2]};
+    double H[3][3];
+    orc_steps(lat, N, H);
     double wgt = omega / ((double)N[0] * N[1] * N[2]);
     const double* vl = v + grid_off[q.lev];
     double X[ORC_MAXCART * ORC_MAXCART];
@@ -738,7 +739,8 @@ void orc_integrate_tau(long npairs, const long* sel, long nsel, const int* ab, c
     for (int i0 = q.lo[0]; i0 <= q.hi[0]; ++i0)
       for (int i1 = q.lo[1]; i1 <= q.hi[1]; ++i1)
         for (int i2 = q.lo[2]; i2 <= q.hi[2]; ++i2) {
-          double r[3] = {i0 * h[0], i1 * h[1], i2 * h[2]};
+          double r[3];
+          orc_point(H, i0, i1, i2, r);
           double vr = vl[(orc_wrap(i0, N[0]) * N[1] + orc_wrap(i1, N[1])) * N[2] + orc_wrap(i2, N[2])];
           double ua[3], ub[3], va, vb;
           double ga[ORC_MAXCART][3], gb[ORC_MAXCART][3], Ha[ORC_MAXCART][6], Hb[ORC_MAXCART][6];

@@ -1884,7 +1884,7 @@ cudaError_t configure_kernels(Plan* p) {
   }
   if (p->skew) {
     if (!(p->tile[0] == kT0 && p->tile[1] == kT1 && p->tile[2] == kT2 && p->tile_i[0] == kT0 &&
-          p->tile_i[1] == kT1 && p->tile_i[2] == kT2) || p->xr)
+          p->tile_i[1] == kT1 && p->tile_i[2] == kT2))
       return cudaErrorInvalidValue;
     using CL = CollocLayout<kT0, kT1, kT2>;
     using IL = IntegLayout<kT0, kT1, kT2>;
@@ -1899,6 +1899,16 @@ cudaError_t configure_kernels(Plan* p) {
     p->nw_integ = kNW;
     if ((size_t)optin < std::max(p->smem_colloc, std::max(p->smem_integ, p->smem_integ1)))
       return cudaErrorInvalidValue;
+    if (p->xr) {
+      // kinetic-energy density: collocation at degree L+2, integration at L+2 / L+3
+      p->stg_colloc_t = even(even(CL::stage(p->lmax + 3)) + colloc_skew_extra<kT0, kT1, kT2>());
+      if (pick_colloc_warps<kT0, kT1, kT2, true>(p->stg_colloc_t, p->nw_colloc_req,
+                                                  &p->nw_colloc_t, &p->smem_colloc_t) == 0)
+        return cudaErrorInvalidValue;
+      p->stg_integ3 = even(even(IL::stage(p->lmax + 4)) + integ_skew_extra<kT0, kT1, kT2>());
+      p->smem_integ3 = integ_smem<kT0, kT1, kT2>(p->stg_integ3);
+      if ((size_t)optin < std::max(p->smem_colloc_t, p->smem_integ3)) return cudaErrorInvalidValue;
+    }
     return cudaSuccess;
   }
 #define GPW_TILE_CONF(a, b, c)                                                      \
@@ -1988,16 +1998,16 @@ cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views,
   if (nwork == 0) return cudaSuccess;
   const int t0 = cfg.tile[0], t1 = cfg.tile[1], t2 = cfg.tile[2];
   if (cfg.skew) {
-    if (!(t0 == kT0 && t1 == kT1 && t2 == kT2) || cfg.ldeg) return cudaErrorInvalidValue;
+    if (!(t0 == kT0 && t1 == kT1 && t2 == kT2)) return cudaErrorInvalidValue;
     if (cfg.nw == 8)
       collocate_kernel<kT0, kT1, kT2, 8, true><<<(int)nwork, 8 * 32, cfg.smem, s>>>(
-          views, work, tabs, cfg.lp, cfg.stg, 0);
+          views, work, tabs, cfg.lp, cfg.stg, cfg.ldeg);
     else if (cfg.nw == 6)
       collocate_kernel<kT0, kT1, kT2, 6, true><<<(int)nwork, 6 * 32, cfg.smem, s>>>(
-          views, work, tabs, cfg.lp, cfg.stg, 0);
+          views, work, tabs, cfg.lp, cfg.stg, cfg.ldeg);
     else if (cfg.nw == 4)
       collocate_kernel<kT0, kT1, kT2, 4, true><<<(int)nwork, 4 * 32, cfg.smem, s>>>(
-          views, work, tabs, cfg.lp, cfg.stg, 0);
+          views, work, tabs, cfg.lp, cfg.stg, cfg.ldeg);
     else
       return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -2021,7 +2031,7 @@ cudaError_t launch_integrate_views(const GridLaunch& cfg, int lext, const PlanVi
   if (nwork == 0) return cudaSuccess;
   const int t0 = cfg.tile[0], t1 = cfg.tile[1], t2 = cfg.tile[2];
   if (cfg.skew) {
-    if (!(t0 == kT0 && t1 == kT1 && t2 == kT2) || lext > 1) return cudaErrorInvalidValue;
+    if (!(t0 == kT0 && t1 == kT1 && t2 == kT2)) return cudaErrorInvalidValue;
     integrate_kernel<kT0, kT1, kT2, kNW, true><<<(int)nwork, kNW * 32, cfg.smem, s>>>(
         views, work, tabs, lext, cfg.lp, cfg.stg);
     return cudaGetLastError();
@@ -2220,6 +2230,11 @@ cudaError_t launch_pair_coef_tau(const Plan& p, const double* D, cudaStream_t s)
   ++p.launches;
   pair_coef_tau_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
       p.npairs, p.d.ids, p.d.ids2, p.d.geo, p.d.pref, p.d.coef_off, D, p.nao, p.d.coef);
+  if (p.skew) {
+    ++p.launches;
+    mono_transform_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(
+        p.npairs, p.d.hot_a, p.d.hot_b, p.d.coef_off, p.d.coef, p.d.mono_t, 2, 0);
+  }
   return cudaGetLastError();
 }
 

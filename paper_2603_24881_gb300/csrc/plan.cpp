@@ -666,12 +666,7 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
         return GPW_EINVAL;
       }
   if (plan->skew) {
-    // the non-orthogonal kernels: no kinetic-energy density, 4x8x16 sub-boxes for both
-    // passes
-    if (plan->xr) {
-      set_error("gpw_plan: the kinetic-energy-density kernels need an orthorhombic cell");
-      return GPW_EINVAL;
-    }
+    // the non-orthogonal kernels use 4x8x16 sub-boxes for both passes
     const bool tc = desc->tile[0] || desc->tile[1] || desc->tile[2];
     const bool ti = desc->tile_integ[0] || desc->tile_integ[1] || desc->tile_integ[2];
     if ((tc && !(desc->tile[0] == kT0 && desc->tile[1] == kT1 && desc->tile[2] == kT2)) ||

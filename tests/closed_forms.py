@@ -255,10 +255,15 @@ def lattice_grad_pw_matrix(sys, waves, reach=40.0):
     """T_mu,nu[v] = sum_T int grad phi_mu(r) . grad phi_nu(r - T) v(r) dr for
     v(r) = sum_k a_k cos(G_k . r) (as lattice_pw_matrix, one dimension differentiated at
     a time)."""
-    L = np.diag(sys.lattice)
+    lat = np.asarray(sys.lattice, dtype=float)
+    ortho = bool(np.all(lat == np.diag(np.diag(lat))))
+    rec = np.linalg.inv(lat).T
     tot = 0.0
     for nk, amp in zip(waves.n, waves.a):
-        G = 2 * np.pi * np.asarray(nk, dtype=float) / L
+        if ortho:
+            G = 2 * np.pi * np.asarray(nk, dtype=float) / np.diag(lat)
+        else:
+            G = 2 * np.pi * (np.asarray(nk, dtype=float) @ rec)
         for dd in range(3):
             tot = tot + amp * _shell_pair_sum(
                 sys, reach, lambda i, j, a, b, A, B, d, G=G, dd=dd:

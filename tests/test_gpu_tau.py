@@ -24,11 +24,14 @@ def gpw():
     return g
 
 
-@pytest.fixture(scope="module", params=["tiny", "resolved_d"])
+@pytest.fixture(scope="module", params=["tiny", "resolved_d", "triclinic_d"])
 def case(request):
     s = {"tiny": workloads.tiny,
          "resolved_d": lambda: systems.resolved(seed=6, shells=((0, 1), (1, 1), (2, 1)),
-                                                cutoff=100.0)}[request.param]()
+                                                cutoff=100.0),
+         # a non-orthogonal cell: the cross-factor kernels at degree L+2 / L+3
+         "triclinic_d": lambda: systems.skewed(seed=6, shells=((0, 1), (1, 1), (2, 1)),
+                                               cutoff=100.0)}[request.param]()
     return request.param, s, oracle.Plan(s)
 
 

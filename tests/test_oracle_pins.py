@@ -617,3 +617,17 @@ def test_sheared_description_gga():
     assert b["Ex"] == pytest.approx(a["Ex"], rel=1e-9)
     assert b["EH"] == pytest.approx(a["EH"], rel=1e-9)
     assert np.max(np.abs(b["V"] - a["V"])) <= 1e-9 * np.max(np.abs(a["V"]))
+
+
+def test_skew_tau_closed_forms(res_skew):
+    # kinetic-energy density in a triclinic cell: int tau = (1/2) tr(D T) and the tau
+    # Fock term of plane waves, against the analytic lattice sums over Cartesian images
+    s, p = res_skew
+    tl = p.tau_levels(s.D)
+    tot = sum(p.omega / t.size * float(np.sum(t)) for t in tl)
+    T = cf.lattice_grad_overlap(s, reach=20.0)
+    assert tot == pytest.approx(0.5 * float(np.sum(s.D * T)), rel=1e-10)
+    waves = workloads.PlaneWaves(s.potential.n[:2], s.potential.a[:2])
+    V = p.mat_tau_levels([waves.sample(m) for m in p.meshes])
+    ref = 0.5 * cf.lattice_grad_pw_matrix(s, waves, reach=20.0)
+    assert np.max(np.abs(V - ref)) <= 1e-9 * np.max(np.abs(ref))

@@ -84,9 +84,9 @@ def test_validation(lib):
     _expect_error(s, xc="b88")
     _expect_error(s, host_threads=-1)
     sk = systems.skewed()
-    binding.Plan(sk, commit=False).close()           # a triclinic cell plans (LDA or PBE) ...
+    binding.Plan(sk, commit=False).close()           # a triclinic cell plans (LDA, PBE, tau)
     binding.Plan(sk, commit=False, xc="pbe_x").close()
-    _expect_error(sk, tau=True)                       # ... without the tau kernels
+    binding.Plan(systems.skewed(shells=((0, 1), (2, 1))), commit=False, tau=True).close()
     _expect_error(sk, tile=(8, 8, 32))                # and the 4x8x16 sub-boxes
     flat = sk.with_tau(sk.tau)
     flat.lattice = np.array([[6.0, 0.0, 0.0], [6.0, 0.0, 0.0], [0.0, 0.0, 6.0]])
