@@ -101,7 +101,7 @@ def _shell_pair_sum(sys, reach, one_d):
     off = sys.ao_offsets()
     nao = int(off[-1])
     out = np.zeros((nao, nao))
-    imgs = np.array(_images(step, reach), dtype=float)
+    imgs = np.array(_images(step, reach), dtype=float) @ lat  # Cartesian image vectors
     for sa in range(sys.nshell):
         la = int(sys.shell_l[sa])
         ca = _cart(la)
@@ -114,7 +114,7 @@ def _shell_pair_sum(sys, reach, one_d):
             B0 = sys.coords[int(sys.shell_atom[sb])]
             blk = np.zeros((len(ca), len(cb)), dtype=complex)
             for T in imgs:
-                B = B0 + T @ lat
+                B = B0 + T
                 if np.sum((A - B) ** 2) > reach * reach:
                     continue
                 for ka in range(int(sys.shell_nprim[sa])):
