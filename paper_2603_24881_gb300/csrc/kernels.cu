@@ -443,7 +443,9 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
 template <int T0, int T1, int T2>
 struct SkewRows {
   static constexpr int kSize = T0 * T1 + T0 * T2 + T1 * T2;
-  static_assert(2 * T0 + T1 <= 32, "one lane per cross-factor row");
+  // a task's seeds staged in shared memory: U01, Q01, U02, Q02 (T0 each), U12, Q12 (T1)
+  static constexpr int kSeeds = 4 * T0 + 2 * T1;
+  static_assert(2 * T0 + T1 <= 32 && kSeeds <= 64, "one lane per cross-factor row");
   // seeds per pair after its 1-D tables: U01, Q01, U02, Q02 (n0 each), U12, Q12 (n1 each)
 };
 
@@ -458,32 +460,45 @@ __device__ __forceinline__ double ipow_d(double x, int n) {
   return r;
 }
 
-// The task's cross-factor rows from the pair's seeds (tables_kernel): row i of the pair
-// (d, e) starts at U[x] Q[x]^(t_e) (x = t_d + i) and advances by Q[x] per step along e.
+// Stage a task's cross-factor seeds (tables_kernel, after the pair's 1-D tables) into
+// shared memory with cp.async, next to its other windows: U and Q at the task's rows.
 template <int T0, int T1, int T2>
-__device__ __forceinline__ void skew_rows(const PlanView& pv, const Task& tk, long long toff,
+__device__ __forceinline__ void stage_seeds(const double* __restrict__ tab, long long toff,
+                                            const Task& tk, int xr, double* __restrict__ sS,
+                                            int lane) {
+  const int n0 = tk.n[0], n1 = tk.n[1], m0 = tk.m[0], m1 = tk.m[1];
+  const double* sd = tab + toff + (long long)(tk.L + 2 + xr) * (n0 + n1 + tk.n[2]);
+  if (lane < 4 * m0) {
+    const int k = lane / m0, i = lane - k * m0;  // k: U01, Q01, U02, Q02
+    cp_async8(sS + k * T0 + i, sd + k * n0 + tk.t[0] + i);
+  } else if (lane < 4 * m0 + 2 * m1) {
+    const int r = lane - 4 * m0, k = r / m1, i = r - k * m1;  // U12, Q12
+    cp_async8(sS + 4 * T0 + k * T1 + i, sd + 4 * n0 + k * n1 + tk.t[1] + i);
+  }
+}
+
+// The task's cross-factor rows from its staged seeds: row i of the pair (d, e) starts at
+// U[i] Q[i]^(t_e) and advances by Q[i] per step along e.
+template <int T0, int T1, int T2>
+__device__ __forceinline__ void skew_rows(const double* __restrict__ sS, const Task& tk,
                                           double* __restrict__ sR, int lane) {
   const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
-  const int n0 = tk.n[0], n1 = tk.n[1];
-  const double* sd = pv.tab + toff + (long long)(tk.L + 2 + pv.xr) * (n0 + n1 + tk.n[2]);
-  int i, len, te;
-  const double* U;
+  int len, te;
+  double u, q;
   double* dst;
   if (lane < m0) {
-    i = lane; U = sd; te = tk.t[1]; len = m1; dst = sR + i * T1;
-    U += tk.t[0] + i;
+    u = sS[lane]; q = sS[T0 + lane]; te = tk.t[1]; len = m1; dst = sR + lane * T1;
   } else if (lane < 2 * m0) {
-    i = lane - m0; U = sd + 2 * n0; te = tk.t[2]; len = m2; dst = sR + T0 * T1 + i * T2;
-    U += tk.t[0] + i;
+    const int i = lane - m0;
+    u = sS[2 * T0 + i]; q = sS[3 * T0 + i]; te = tk.t[2]; len = m2; dst = sR + T0 * T1 + i * T2;
   } else if (lane < 2 * m0 + m1) {
-    i = lane - 2 * m0; U = sd + 4 * n0; te = tk.t[2]; len = m2; dst = sR + T0 * T1 + T0 * T2 + i * T2;
-    U += tk.t[1] + i;
+    const int i = lane - 2 * m0;
+    u = sS[4 * T0 + i]; q = sS[4 * T0 + T1 + i]; te = tk.t[2]; len = m2;
+    dst = sR + T0 * T1 + T0 * T2 + i * T2;
   } else {
     return;
   }
-  // Q[x] sits one row length after U[x]: n0 for the pairs (0,1), (0,2); n1 for (1,2)
-  const double q = U[lane < 2 * m0 ? n0 : n1];
-  double v = U[0] * ipow_d(q, te);
+  double v = u * ipow_d(q, te);
   for (int j = 0; j < len; ++j) {
     dst[j] = v;
     v *= q;
@@ -543,8 +558,10 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
   double* sT2 = stage_base + 2 * bufn;
   int* s_row = reinterpret_cast<int*>(sT2 + lp * T0 * T1);
   int* s_qi = s_row + T0 * T1;
-  // non-orthogonal cells: the task's cross-factor rows, after the regular per-warp staging
+  // non-orthogonal cells: the task's cross-factor rows and two seed buffers (one per
+  // staging buffer), after the regular per-warp staging
   double* sR = stage_base + ((Lay::stage(lp) + 1) & ~1);
+  double* sSeed = sR + SkewRows<T0, T1, T2>::kSize;
   __syncthreads();
 
   // staging buffer b: [X window xrows*T0][g1 lp*T1][g2 lp*T2]
@@ -570,6 +587,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
       const int l = fdiv(it, i2f), i = it - l * m2;
       cp_async8(sg2 + l * T2 + i, t2 + l * tk.n[2] + i);
     }
+    if constexpr (SK) stage_seeds<T0, T1, T2>(tab, toff, tk, pv.xr, sSeed + b * SkewRows<T0, T1, T2>::kSeeds, lane);
   };
 
   long long e = sb.eb + warp;
@@ -622,7 +640,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
         s_qi[q] = i0 | (i1 << 8);
         s_row[q] = ((tk.u[0] + i0) * T1 + (tk.u[1] + i1)) * T2 + tk.u[2];
       }
-      if constexpr (SK) skew_rows<T0, T1, T2>(pv, tk, __ldg(tab_off + tk.p), sR, lane);
+      if constexpr (SK) skew_rows<T0, T1, T2>(sSeed + buf * SkewRows<T0, T1, T2>::kSeeds, tk, sR, lane);
       __syncwarp();
 #define GPW_COLLOC_L(LL)                                                                     \
   case LL:                                                                                   \
@@ -729,12 +747,14 @@ __global__ void __launch_bounds__(NW * 32)
   // and the factor rows, after the regular per-warp staging
   double* sVE = stage_base + ((Lay::stage(lpx) + 1) & ~1);
   double* sR = sVE + Lay::kSV;
+  double* sSeed = sR + SkewRows<T0, T1, T2>::kSize;
   __syncthreads();
 
   auto issue = [&](const Task& tk, long long toff, int b) {
     double* sg1 = stage_base + b * bufn;
     stage_yz_async<P1, P2>(tab + toff, tk, tk.L + lext + 1, tk.L + 2 + pv.xr, sg1,
                            sg1 + lpx * P1, lane);
+    if constexpr (SK) stage_seeds<T0, T1, T2>(tab, toff, tk, pv.xr, sSeed + b * SkewRows<T0, T1, T2>::kSeeds, lane);
   };
 
   long long e = sb.eb + warp;
@@ -781,7 +801,7 @@ __global__ void __launch_bounds__(NW * 32)
       const double* vbase = sv;
       int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
       if constexpr (SK) {
-        skew_rows<T0, T1, T2>(pv, tk, __ldg(tab_off + tk.p), sR, lane);
+        skew_rows<T0, T1, T2>(sSeed + buf * SkewRows<T0, T1, T2>::kSeeds, tk, sR, lane);
         __syncwarp();
         const double* r02 = sR + T0 * T1;
         const double* r12 = r02 + T0 * T2;
@@ -1778,9 +1798,11 @@ constexpr int kNW = 8;
 
 // per-warp staging doubles of the non-orthogonal variants (cross factors and their rows)
 template <int T0, int T1, int T2>
-int colloc_skew_extra() { return SkewRows<T0, T1, T2>::kSize; }
+int colloc_skew_extra() { return SkewRows<T0, T1, T2>::kSize + 2 * SkewRows<T0, T1, T2>::kSeeds; }
 template <int T0, int T1, int T2>
-int integ_skew_extra() { return IntegLayout<T0, T1, T2>::kSV + SkewRows<T0, T1, T2>::kSize; }
+int integ_skew_extra() {
+  return IntegLayout<T0, T1, T2>::kSV + SkewRows<T0, T1, T2>::kSize + 2 * SkewRows<T0, T1, T2>::kSeeds;
+}
 
 template <int T0, int T1, int T2>
 size_t colloc_smem(int stg, int nw) {

@@ -36,11 +36,6 @@ CASES = {
 }
 
 
-@pytest.fixture(scope="module")
-def cases():
-    return {k: (f(), None) for k, f in CASES.items()}
-
-
 @pytest.mark.parametrize("name", list(CASES))
 def test_skew_parity(gpw, name):
     s = CASES[name]()
