@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the CPU oracle.
 
-Tolerances (stated in the north-star of this path): 1e-10 relative (max-norm over
+Tolerances: 1e-10 relative (max-norm over
 the array) for rho and V, 1e-8 Ha for energies, 1e-7 Ha/Bohr for gradients.
 Integer plan data (pair sets, images, levels, boxes) must match exactly.
 """
