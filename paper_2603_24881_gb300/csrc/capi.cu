@@ -253,7 +253,7 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
   if (P->tasks_on_device) GPW_TRY(build_tasks_device(P, H, s, &b));
   {
     // ((2 pi s)/L_d)^2 per finest-mesh index along each axis, s the signed frequency,
-    // formed exactly as the reference does: (2 pi s)/L, squared
+    // formed as (2 pi s)/L, then squared, as the oracle forms it
     const LevelInfo& f = P->lev[0];
     std::vector<double> g2(f.N[0] + f.N[1] + f.N[2]);
     int o = 0;

@@ -1280,7 +1280,7 @@ __global__ void grad_atom_kernel(int natm, const long long* __restrict__ atom_of
 // ----------------------------------------------------------------------------------
 // Spectral steps.  |G|^2 is formed exactly as ((2 pi s)/L)^2 summed in index order,
 // without FMA contraction, so the strict sphere test |G| < G_k is the same decision as
-// the reference (Sec. II multigrid, Eq. vHG).
+// the oracle's (Sec. II multigrid, Eq. vHG).  Non-orthogonal cells add the cross terms.
 __device__ __forceinline__ int signed_freq(int m, int N) { return m < (N + 1) / 2 ? m : m - N; }
 
 // |G|^2 from per-axis tables of ((2 pi s)/L_d)^2 (built on the host, indexed by the
