@@ -140,3 +140,26 @@ def test_skew_gga_parity(gpw):
     assert np.max(np.abs(out["grad"].cpu().numpy() - op.grad_levels(s.D, r["v_levels"]))) <= 1e-7
     f = gp.fock(s.D, want_v=True)
     assert _rel(f["v"].cpu().numpy(), r["v_fine"]) <= RTOL
+
+
+def test_skew_edge_cases(gpw):
+    # no screened pair in a triclinic cell: zero density, V and energies
+    s = CASES["skewed_spd"]().with_tau(1e6)
+    gp = gpw.Plan(s)
+    assert gp.stats()["npairs"] == 0
+    out = gp.fock(s.D, want_rho=True)
+    assert float(out["rho"].abs().max()) == 0.0 and float(out["V"].abs().max()) == 0.0
+    assert out["EH"] == 0.0 and out["Ex"] == 0.0
+    # one level with odd, unequal explicit meshes (ragged sub-boxes on every axis)
+    s = CASES["skewed_spd"]()
+    s.nlevels = 1
+    s.meshes = np.array([[45, 39, 51]])
+    s.cutoff_ha = 0.0
+    op = oracle.Plan(s)
+    gp = gpw.Plan(s)
+    assert np.array_equal(gp.pair_table(), op.pair_table())
+    out = gp.fock_grad(s.D)
+    r = op.fock(s.D)
+    assert abs(out["EH"] - r["EH"]) <= 1e-8 and abs(out["Ex"] - r["Ex"]) <= 1e-8
+    assert _rel(out["V"].cpu().numpy(), r["V"]) <= RTOL
+    assert np.max(np.abs(out["grad"].cpu().numpy() - op.grad_levels(s.D, r["v_levels"]))) <= 1e-7
