@@ -86,6 +86,8 @@ class Server:
     tile_integ, colloc_warps, integ_chunk: launch shape of every plan (library defaults
     if None); tune_with: a list of sample cells to run the autotuner on (as one batch)
     instead, its choice (cached per GPU and workload class) then serves every request.
+    Non-orthogonal cells plan with 4x8x16 sub-boxes for both passes, so a request of that
+    kind fails alone under another explicit shape; batches hold one kind of cell.
     """
 
     def __init__(self, hbm_budget: int | None = None, max_batch: int = 32, streams: int = 2,

@@ -21,10 +21,11 @@ def gpw():
     return g
 
 
-@pytest.mark.parametrize("name", ["resolved", "water4"])
+@pytest.mark.parametrize("name", ["resolved", "water4", "triclinic"])
 def test_energy_backward_matches_oracle_and_fd(gpw, name):
     from paper_2603_24881_gb300 import autograd as ag
-    s = systems.resolved() if name == "resolved" else workloads.config("water4")
+    s = {"resolved": systems.resolved, "water4": lambda: workloads.config("water4"),
+         "triclinic": lambda: systems.skewed(shells=((0, 1), (1, 1), (2, 1)), natm=2)}[name]()
     plan = gpw.Plan(s)
     op = oracle.Plan(s)
     D = torch.as_tensor(s.D, device="cuda").requires_grad_(True)
