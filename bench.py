@@ -311,7 +311,8 @@ def per_config(a):
     import workloads
     import paper_2603_24881_gb300 as gpw
     gpw.load()
-    for name in ("tiny", "water32", "carbon", "water256", "water32_triclinic", "water256_triclinic"):
+    for name in ("tiny", "water32", "carbon", "water256", "water32_triclinic", "water256_triclinic",
+                 "water32_hexagonal", "water256_hexagonal"):
         s = workloads.config(name)
         plan = gpw.Plan(s)
         st = plan.stats()

@@ -341,7 +341,8 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
                                             const double* __restrict__ sg2, double* __restrict__ sT2,
                                             const int* __restrict__ s_row,
                                             const int* __restrict__ s_qi, double* __restrict__ acc,
-                                            int lane, const double* __restrict__ sR = nullptr) {
+                                            int lane, const double* __restrict__ sR = nullptr,
+                                            bool zc = true) {
   constexpr int Q = T0 * T1;
   const float inv01 = __frcp_rn((float)m01), inv2 = __frcp_rn((float)m2);
   {
@@ -386,8 +387,11 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
       const double* tb = sT2 + qb;
       const double* ga = sg2 + iA;
       const double* gb = sg2 + iB;
-      if constexpr (SK) {
+      bool zcross = false;
+      if constexpr (SK) zcross = zc;
+      if (zcross) {
         // non-orthogonal cell: R01 is in T2 already; times R02(i0, i2) R12(i1, i2)
+        // (zc false: the third row is orthogonal to the others, R02 = R12 = 1)
         const double* r02 = sR + T0 * T1;
         const double* r12 = r02 + T0 * T2;
         const int pa_i = s_qi[qa], pb_i = s_qi[qb];
@@ -481,8 +485,9 @@ __device__ __forceinline__ void stage_seeds(const double* __restrict__ tab, long
 // U[i] Q[i]^(t_e) and advances by Q[i] per step along e.
 template <int T0, int T1, int T2>
 __device__ __forceinline__ void skew_rows(const double* __restrict__ sS, const Task& tk,
-                                          double* __restrict__ sR, int lane) {
+                                          double* __restrict__ sR, int lane, bool zc) {
   const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
+  if (!zc && lane >= m0) return;  // third row orthogonal to the others: R01 only
   int len, te;
   double u, q;
   double* dst;
@@ -562,6 +567,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
   // staging buffer), after the regular per-warp staging
   double* sR = stage_base + ((Lay::stage(lp) + 1) & ~1);
   double* sSeed = sR + SkewRows<T0, T1, T2>::kSize;
+  const bool zc = pv.skew != 2;  // cross terms with the third row (R02, R12) present
   __syncthreads();
 
   // staging buffer b: [X window xrows*T0][g1 lp*T1][g2 lp*T2]
@@ -640,11 +646,11 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
         s_qi[q] = i0 | (i1 << 8);
         s_row[q] = ((tk.u[0] + i0) * T1 + (tk.u[1] + i1)) * T2 + tk.u[2];
       }
-      if constexpr (SK) skew_rows<T0, T1, T2>(sSeed + buf * SkewRows<T0, T1, T2>::kSeeds, tk, sR, lane);
+      if constexpr (SK) skew_rows<T0, T1, T2>(sSeed + buf * SkewRows<T0, T1, T2>::kSeeds, tk, sR, lane, zc);
       __syncwarp();
 #define GPW_COLLOC_L(LL)                                                                     \
   case LL:                                                                                   \
-    colloc_task<LL, T0, T1, T2, SK>(m01, m2, sX, sg1, sg2, sT2, s_row, s_qi, acc, lane, sR);  \
+    colloc_task<LL, T0, T1, T2, SK>(m01, m2, sX, sg1, sg2, sT2, s_row, s_qi, acc, lane, sR, zc); \
     break;
       switch (L) {
         GPW_COLLOC_L(0) GPW_COLLOC_L(1) GPW_COLLOC_L(2) GPW_COLLOC_L(3) GPW_COLLOC_L(4)
@@ -748,6 +754,7 @@ __global__ void __launch_bounds__(NW * 32)
   double* sVE = stage_base + ((Lay::stage(lpx) + 1) & ~1);
   double* sR = sVE + Lay::kSV;
   double* sSeed = sR + SkewRows<T0, T1, T2>::kSize;
+  const bool zc = pv.skew != 2;  // cross terms with the third row (R02, R12) present
   __syncthreads();
 
   auto issue = [&](const Task& tk, long long toff, int b) {
@@ -801,8 +808,10 @@ __global__ void __launch_bounds__(NW * 32)
       const double* vbase = sv;
       int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
       if constexpr (SK) {
-        skew_rows<T0, T1, T2>(sSeed + buf * SkewRows<T0, T1, T2>::kSeeds, tk, sR, lane);
+        skew_rows<T0, T1, T2>(sSeed + buf * SkewRows<T0, T1, T2>::kSeeds, tk, sR, lane, zc);
         __syncwarp();
+      }
+      if (SK && zc) {
         const double* r02 = sR + T0 * T1;
         const double* r12 = r02 + T0 * T2;
         const float inv2 = __frcp_rn((float)m2), inv1 = __frcp_rn((float)m1);
@@ -2172,7 +2181,11 @@ PlanView make_view(const Plan& p) {
   v.err = p.d.err;
   v.chunk_i = p.chunk_i;
   v.xr = p.xr;
-  v.skew = p.skew ? 1 : 0;
+  // 1: general non-orthogonal cell; 2: the third row orthogonal to the first two
+  // (hexagonal, monoclinic with unique axis c), only the R01 cross factor
+  bool zc = false;
+  for (int k = 0; k < p.nlev; ++k) zc = zc || p.lev[k].gm[4] != 0.0 || p.lev[k].gm[5] != 0.0;
+  v.skew = p.skew ? (zc ? 1 : 2) : 0;
   v.geo = p.d.geo;
   v.hot_a = p.d.hot_a;
   return v;

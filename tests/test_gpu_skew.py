@@ -33,6 +33,9 @@ CASES = {
     "skewed_spd": lambda: systems.skewed(shells=((0, 1), (1, 1), (2, 1)), natm=2),
     "skewed_f": lambda: systems.skewed(seed=8, shells=((0, 1), (1, 1), (2, 1), (3, 1)), natm=3),
     "sheared": lambda: systems.sheared(systems.resolved(seed=7, shells=((0, 1), (1, 1), (2, 1)), natm=2)),
+    # third row orthogonal to the first two: the kernels' R01-only path
+    "hexagonal": lambda: systems.skewed(seed=9, shells=((0, 1), (1, 1), (2, 1), (3, 1)), natm=2,
+                                        lattice=6.0 * workloads.HEXAGONAL),
 }
 
 
@@ -108,14 +111,14 @@ def test_sheared_equals_cubic_on_gpu(gpw):
 
 
 def test_skew_batch_and_limits(gpw):
-    ss = [CASES["skewed_spd"](), CASES["skewed_f"]()]
+    ss = [CASES["skewed_spd"](), CASES["skewed_f"](), CASES["hexagonal"]()]
     plans = [gpw.Plan(s) for s in ss]
     alone = [p.fock_grad(s.D) for p, s in zip(plans, ss)]
-    batch = gpw.Batch(2).set(plans)
+    batch = gpw.Batch(3).set(plans)
     Ds = [torch.as_tensor(s.D, device="cuda") for s in ss]
     Vs = [torch.empty((p.nao, p.nao), dtype=torch.float64, device="cuda") for p in plans]
     gs = [torch.empty((p.natm, 3), dtype=torch.float64, device="cuda") for p in plans]
-    E = torch.empty(4, dtype=torch.float64, device="cuda")
+    E = torch.empty(6, dtype=torch.float64, device="cuda")
     batch.fock_grad_async(Ds, Vs, gs, E)
     torch.cuda.synchronize()
     for i, a in enumerate(alone):

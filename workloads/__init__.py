@@ -263,18 +263,32 @@ def water256(seed: int = 3) -> System:
 TRICLINIC = np.array([[1.0, 0.0, 0.0], [0.28, 0.96, 0.0], [-0.21, 0.17, 0.95]])
 
 
+# a hexagonal cell shape (rows a, b at 120 degrees, c orthogonal to both, c/a = 1.1),
+# volume (sqrt(3)/2) 1.1 L^3
+HEXAGONAL = np.array([[1.0, 0.0, 0.0], [-0.5, math.sqrt(3.0) / 2.0, 0.0], [0.0, 0.0, 1.1]])
+
+
+def hexagonal(s: System) -> System:
+    """The cubic system s moved into a hexagonal cell of the same volume (as triclinic)."""
+    return _reshape_cell(s, HEXAGONAL, "hexagonal")
+
+
+def _reshape_cell(s: System, shape, name) -> System:
+    import copy
+    L = float(s.lattice[0, 0])
+    scale = L / float(np.linalg.det(shape)) ** (1.0 / 3.0)
+    out = copy.copy(s)
+    out.lattice = np.ascontiguousarray(scale * np.asarray(shape, dtype=np.float64))
+    out.coords = np.ascontiguousarray((s.coords / L) @ out.lattice)
+    out.name = s.name + "-" + name
+    return out
+
+
 def triclinic(s: System) -> System:
     """The cubic system s moved into a triclinic cell of the same volume: lattice rows
     L' TRICLINIC with L'^3 det(TRICLINIC) = L^3, every atom at the same fractional
     position (molecules are sheared with the cell: a synthetic non-orthogonal input)."""
-    import copy
-    L = float(s.lattice[0, 0])
-    scale = L / float(np.linalg.det(TRICLINIC)) ** (1.0 / 3.0)
-    out = copy.copy(s)
-    out.lattice = np.ascontiguousarray(scale * TRICLINIC)
-    out.coords = np.ascontiguousarray((s.coords / L) @ out.lattice)
-    out.name = s.name + "-triclinic"
-    return out
+    return _reshape_cell(s, TRICLINIC, "triclinic")
 
 
 def small_water(nwat: int = 4, seed: int = 11, **kw) -> System:
@@ -348,7 +362,8 @@ def stream_requests(count: int = 400, seed: int = 4, rate: float | None = None):
 
 def config(name: str) -> System:
     """Named workloads: tiny, water32, carbon, water256, water4, water8 and the triclinic
-    water4, water32 and water256 (non-orthogonal cells)."""
+    water4, water32 and water256 and the hexagonal water32 and water256 (non-orthogonal
+    cells)."""
     return {
         "tiny": tiny, "water32": water32, "carbon": carbon, "water256": water256,
         "water4": lambda: small_water(4, seed=11),
@@ -356,4 +371,6 @@ def config(name: str) -> System:
         "water4_triclinic": lambda: triclinic(small_water(4, seed=11)),
         "water32_triclinic": lambda: triclinic(water32()),
         "water256_triclinic": lambda: triclinic(water256()),
+        "water32_hexagonal": lambda: hexagonal(water32()),
+        "water256_hexagonal": lambda: hexagonal(water256()),
     }[name]()
