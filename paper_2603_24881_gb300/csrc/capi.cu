@@ -1037,8 +1037,10 @@ int gpw_batch_set(gpw_batch_t b, int nplans, const gpw_plan_t* plans, void* stre
     return GPW_EINVAL;
   }
   int lmax = 0;
+  int skew_kind = 0;  // 1: a plan needs every cross factor, 2: R01 only (kernels' layout)
   for (int i = 0; i < nplans; ++i) {
     if (gpw::bad(plans[i])) return GPW_EINVAL;
+    if (plans[i]->p.skew) skew_kind = (plans[i]->p.skew_zc || skew_kind == 1) ? 1 : 2;
     const gpw::Plan& P = plans[i]->p;
     const gpw::Plan& P0 = plans[0]->p;
     for (int d = 0; d < 3; ++d)
@@ -1058,7 +1060,7 @@ int gpw_batch_set(gpw_batch_t b, int nplans, const gpw_plan_t* plans, void* stre
   }
   cudaError_t e = gpw::configure_batch(plans[0]->p.tile, plans[0]->p.tile_i, lmax,
                                        plans[0]->p.nw_colloc_req, &b->colloc,
-                                       &b->integ1, plans[0]->p.skew ? 1 : 0);
+                                       &b->integ1, skew_kind);
   if (e != cudaSuccess) {
     set_error(std::string("gpw_batch_set: ") + cudaGetErrorString(e));
     return GPW_ECUDA;

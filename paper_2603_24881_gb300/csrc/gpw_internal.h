@@ -162,6 +162,7 @@ struct Plan {
   double L[3] = {0, 0, 0};   // lattice lengths |R_d|
   double omega = 0;
   bool skew = false;         // non-orthogonal cell (App., non-orthogonal lattices)
+  bool skew_zc = false;      // ... whose third row is not orthogonal to the first two
   double lat[9] = {0};       // lattice rows R_d
   double rec[9] = {0};       // reciprocal rows b_d (b_d . R_e = delta_de)
   double E[GPW_MAX_LEVELS] = {0};

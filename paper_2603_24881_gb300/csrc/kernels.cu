@@ -335,7 +335,9 @@ __device__ __forceinline__ void stage_yz_async(const double* tb, const Task& tk,
 //   acc(q, i2) += sum_{l2 <= L} T2[l2](q) g2[l2](i2)
 // Items are spread over the lanes flat (it = l2 m01 + q, then it = q m2 + i2) so that
 // partial tasks keep the lanes busy; the item index advances by 32 with a carry.
-template <int L, int T0, int T1, int T2, bool SK = false>
+// SK: 0 orthogonal rows; 1 non-orthogonal, every cross factor (R01 always, R02 and R12
+// when zc); 2 non-orthogonal with the third row orthogonal to the others (R01 only)
+template <int L, int T0, int T1, int T2, int SK = 0>
 __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __restrict__ sX,
                                             const double* __restrict__ sg1,
                                             const double* __restrict__ sg2, double* __restrict__ sT2,
@@ -357,7 +359,7 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
 #pragma unroll
         for (int l1 = 0; l1 <= L; ++l1)
           if (l1 <= L - l2) a = fma(xr[l1 * T0], gr[l1 * T1], a);
-        if constexpr (SK) a *= sR[(pi & 255) * T1 + (pi >> 8)];  // R01(i0, i1)
+        if constexpr (SK != 0) a *= sR[(pi & 255) * T1 + (pi >> 8)];  // R01(i0, i1)
         sT2[l2 * Q + q] = a;
       }
       q += dq;
@@ -388,7 +390,7 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
       const double* ga = sg2 + iA;
       const double* gb = sg2 + iB;
       bool zcross = false;
-      if constexpr (SK) zcross = zc;
+      if constexpr (SK == 1) zcross = zc;
       if (zcross) {
         // non-orthogonal cell: R01 is in T2 already; times R02(i0, i2) R12(i1, i2)
         // (zc false: the third row is orthogonal to the others, R02 = R12 = 1)
@@ -531,7 +533,7 @@ struct CollocLayout {
 //   T2[l2](i0,i1) = sum_l1 X[l2,l1](i0) g1[l1](i1)           nc2(L) m0 m1 FMAs
 //   rho(i0,i1,i2) += sum_l2 T2[l2](i0,i1) g2[l2](i2)         (L+1) m0 m1 m2
 // The next task's windows are copied in (cp.async) while the current one computes.
-template <int T0, int T1, int T2, int NW, bool SK = false>
+template <int T0, int T1, int T2, int NW, int SK = 0>
 __global__ void __launch_bounds__(NW * 32, 24 / NW)
     collocate_kernel(const PlanView* __restrict__ views, const int4* __restrict__ work,
                      const CoefTables* __restrict__ tabs, int lp, int stg, int ldeg) {
@@ -567,7 +569,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
   // staging buffer), after the regular per-warp staging
   double* sR = stage_base + ((Lay::stage(lp) + 1) & ~1);
   double* sSeed = sR + SkewRows<T0, T1, T2>::kSize;
-  const bool zc = pv.skew != 2;  // cross terms with the third row (R02, R12) present
+  const bool zc = SK == 1 && pv.skew != 2;  // cross terms with the third row (R02, R12)
   __syncthreads();
 
   // staging buffer b: [X window xrows*T0][g1 lp*T1][g2 lp*T2]
@@ -593,7 +595,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
       const int l = fdiv(it, i2f), i = it - l * m2;
       cp_async8(sg2 + l * T2 + i, t2 + l * tk.n[2] + i);
     }
-    if constexpr (SK) stage_seeds<T0, T1, T2>(tab, toff, tk, pv.xr, sSeed + b * SkewRows<T0, T1, T2>::kSeeds, lane);
+    if constexpr (SK != 0) stage_seeds<T0, T1, T2>(tab, toff, tk, pv.xr, sSeed + b * SkewRows<T0, T1, T2>::kSeeds, lane);
   };
 
   long long e = sb.eb + warp;
@@ -646,7 +648,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
         s_qi[q] = i0 | (i1 << 8);
         s_row[q] = ((tk.u[0] + i0) * T1 + (tk.u[1] + i1)) * T2 + tk.u[2];
       }
-      if constexpr (SK) skew_rows<T0, T1, T2>(sSeed + buf * SkewRows<T0, T1, T2>::kSeeds, tk, sR, lane, zc);
+      if constexpr (SK != 0) skew_rows<T0, T1, T2>(sSeed + buf * SkewRows<T0, T1, T2>::kSeeds, tk, sR, lane, zc);
       __syncwarp();
 #define GPW_COLLOC_L(LL)                                                                     \
   case LL:                                                                                   \
@@ -710,7 +712,7 @@ struct IntegLayout {
   __host__ __device__ static int stage(int lpx) { return 2 * buf(lpx) + lpx * kUS; }
 };
 
-template <int T0, int T1, int T2, int NW, bool SK = false>
+template <int T0, int T1, int T2, int NW, int SK = 0>
 __global__ void __launch_bounds__(NW * 32)
     integrate_kernel(const PlanView* __restrict__ views, const int4* __restrict__ work,
                      const CoefTables* __restrict__ tabs, int lext, int lpx, int stg) {
@@ -751,17 +753,19 @@ __global__ void __launch_bounds__(NW * 32)
   double* sU = stage_base + 2 * bufn;
   // non-orthogonal cells: the task's window of the potential times its cross factors,
   // and the factor rows, after the regular per-warp staging
-  double* sVE = stage_base + ((Lay::stage(lpx) + 1) & ~1);
-  double* sR = sVE + Lay::kSV;
+  // (the potential window times the cross factors last: plans whose third row is
+  // orthogonal to the others do not use it and are launched without it)
+  double* sR = stage_base + ((Lay::stage(lpx) + 1) & ~1);
   double* sSeed = sR + SkewRows<T0, T1, T2>::kSize;
-  const bool zc = pv.skew != 2;  // cross terms with the third row (R02, R12) present
+  double* sVE = sSeed + 2 * SkewRows<T0, T1, T2>::kSeeds;
+  const bool zc = SK == 1 && pv.skew != 2;  // cross terms with the third row (R02, R12)
   __syncthreads();
 
   auto issue = [&](const Task& tk, long long toff, int b) {
     double* sg1 = stage_base + b * bufn;
     stage_yz_async<P1, P2>(tab + toff, tk, tk.L + lext + 1, tk.L + 2 + pv.xr, sg1,
                            sg1 + lpx * P1, lane);
-    if constexpr (SK) stage_seeds<T0, T1, T2>(tab, toff, tk, pv.xr, sSeed + b * SkewRows<T0, T1, T2>::kSeeds, lane);
+    if constexpr (SK != 0) stage_seeds<T0, T1, T2>(tab, toff, tk, pv.xr, sSeed + b * SkewRows<T0, T1, T2>::kSeeds, lane);
   };
 
   long long e = sb.eb + warp;
@@ -807,11 +811,11 @@ __global__ void __launch_bounds__(NW * 32)
       const int m01 = m0 * m1;
       const double* vbase = sv;
       int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
-      if constexpr (SK) {
+      if constexpr (SK != 0) {
         skew_rows<T0, T1, T2>(sSeed + buf * SkewRows<T0, T1, T2>::kSeeds, tk, sR, lane, zc);
         __syncwarp();
       }
-      if (SK && zc) {
+      if (SK == 1 && zc) {
         const double* r02 = sR + T0 * T1;
         const double* r12 = r02 + T0 * T2;
         const float inv2 = __frcp_rn((float)m2), inv1 = __frcp_rn((float)m1);
@@ -836,7 +840,7 @@ __global__ void __launch_bounds__(NW * 32)
           const double* gr = sg2 + l2 * P2;
           double a = 0.0;
           for (int i2 = 0; i2 < m2; ++i2) a = fma(vr[i2], gr[i2], a);
-          if constexpr (SK) a *= sR[i0 * T1 + i1];  // R01(i0, i1)
+          if constexpr (SK != 0) a *= sR[i0 * T1 + i1];  // R01(i0, i1)
           sU[l2 * kUS + i1 * P0 + i0] = a;
         }
       }
@@ -1809,8 +1813,9 @@ constexpr int kNW = 8;
 template <int T0, int T1, int T2>
 int colloc_skew_extra() { return SkewRows<T0, T1, T2>::kSize + 2 * SkewRows<T0, T1, T2>::kSeeds; }
 template <int T0, int T1, int T2>
-int integ_skew_extra() {
-  return IntegLayout<T0, T1, T2>::kSV + SkewRows<T0, T1, T2>::kSize + 2 * SkewRows<T0, T1, T2>::kSeeds;
+int integ_skew_extra(bool zc) {
+  return (zc ? IntegLayout<T0, T1, T2>::kSV : 0) + SkewRows<T0, T1, T2>::kSize +
+         2 * SkewRows<T0, T1, T2>::kSeeds;
 }
 
 template <int T0, int T1, int T2>
@@ -1825,7 +1830,7 @@ size_t integ_smem(int stg) {
 
 // Warps per collocation block: the candidate with the most resident warps per SM, as the
 // occupancy calculator reports it for this shared-memory size (registers included).
-template <int T0, int T1, int T2, bool SK = false>
+template <int T0, int T1, int T2, int SK = 0>
 int pick_colloc_warps(int stg, int want, int* nw_out, size_t* smem_out) {
   int best = 0;
   const void* fns[3] = {(const void*)collocate_kernel<T0, T1, T2, 8, SK>,
@@ -1906,10 +1911,14 @@ cudaError_t configure_kernels(Plan* p) {
 #undef GPW_TILE_ATTR
 #undef GPW_TILE_ATTR_I
   // the non-orthogonal variants (4x8x16 sub-boxes)
-  for (const void* f : {(const void*)collocate_kernel<kT0, kT1, kT2, 8, true>,
-                        (const void*)collocate_kernel<kT0, kT1, kT2, 6, true>,
-                        (const void*)collocate_kernel<kT0, kT1, kT2, 4, true>,
-                        (const void*)integrate_kernel<kT0, kT1, kT2, kNW, true>}) {
+  for (const void* f : {(const void*)collocate_kernel<kT0, kT1, kT2, 8, 1>,
+                        (const void*)collocate_kernel<kT0, kT1, kT2, 6, 1>,
+                        (const void*)collocate_kernel<kT0, kT1, kT2, 4, 1>,
+                        (const void*)integrate_kernel<kT0, kT1, kT2, kNW, 1>,
+                        (const void*)collocate_kernel<kT0, kT1, kT2, 8, 2>,
+                        (const void*)collocate_kernel<kT0, kT1, kT2, 6, 2>,
+                        (const void*)collocate_kernel<kT0, kT1, kT2, 4, 2>,
+                        (const void*)integrate_kernel<kT0, kT1, kT2, kNW, 2>}) {
     e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, optin);
     if (e != cudaSuccess) return e;
   }
@@ -1919,12 +1928,14 @@ cudaError_t configure_kernels(Plan* p) {
       return cudaErrorInvalidValue;
     using CL = CollocLayout<kT0, kT1, kT2>;
     using IL = IntegLayout<kT0, kT1, kT2>;
+    const bool zc = p->skew_zc;
+    const auto pick = zc ? pick_colloc_warps<kT0, kT1, kT2, 1> : pick_colloc_warps<kT0, kT1, kT2, 2>;
     p->stg_colloc = even(even(CL::stage(lp)) + colloc_skew_extra<kT0, kT1, kT2>());
-    if (pick_colloc_warps<kT0, kT1, kT2, true>(p->stg_colloc, p->nw_colloc_req, &p->nw_colloc,
+    if (pick(p->stg_colloc, p->nw_colloc_req, &p->nw_colloc,
                                                 &p->smem_colloc) == 0)
       return cudaErrorInvalidValue;
-    p->stg_integ = even(even(IL::stage(p->lmax + 1)) + integ_skew_extra<kT0, kT1, kT2>());
-    p->stg_integ1 = even(even(IL::stage(p->lmax + 2)) + integ_skew_extra<kT0, kT1, kT2>());
+    p->stg_integ = even(even(IL::stage(p->lmax + 1)) + integ_skew_extra<kT0, kT1, kT2>(zc));
+    p->stg_integ1 = even(even(IL::stage(p->lmax + 2)) + integ_skew_extra<kT0, kT1, kT2>(zc));
     p->smem_integ = integ_smem<kT0, kT1, kT2>(p->stg_integ);
     p->smem_integ1 = integ_smem<kT0, kT1, kT2>(p->stg_integ1);
     p->nw_integ = kNW;
@@ -1933,10 +1944,10 @@ cudaError_t configure_kernels(Plan* p) {
     if (p->xr) {
       // kinetic-energy density: collocation at degree L+2, integration at L+2 / L+3
       p->stg_colloc_t = even(even(CL::stage(p->lmax + 3)) + colloc_skew_extra<kT0, kT1, kT2>());
-      if (pick_colloc_warps<kT0, kT1, kT2, true>(p->stg_colloc_t, p->nw_colloc_req,
+      if (pick(p->stg_colloc_t, p->nw_colloc_req,
                                                   &p->nw_colloc_t, &p->smem_colloc_t) == 0)
         return cudaErrorInvalidValue;
-      p->stg_integ3 = even(even(IL::stage(p->lmax + 4)) + integ_skew_extra<kT0, kT1, kT2>());
+      p->stg_integ3 = even(even(IL::stage(p->lmax + 4)) + integ_skew_extra<kT0, kT1, kT2>(zc));
       p->smem_integ3 = integ_smem<kT0, kT1, kT2>(p->stg_integ3);
       if ((size_t)optin < std::max(p->smem_colloc_t, p->smem_integ3)) return cudaErrorInvalidValue;
     }
@@ -2030,18 +2041,16 @@ cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views,
   const int t0 = cfg.tile[0], t1 = cfg.tile[1], t2 = cfg.tile[2];
   if (cfg.skew) {
     if (!(t0 == kT0 && t1 == kT1 && t2 == kT2)) return cudaErrorInvalidValue;
-    if (cfg.nw == 8)
-      collocate_kernel<kT0, kT1, kT2, 8, true><<<(int)nwork, 8 * 32, cfg.smem, s>>>(
-          views, work, tabs, cfg.lp, cfg.stg, cfg.ldeg);
-    else if (cfg.nw == 6)
-      collocate_kernel<kT0, kT1, kT2, 6, true><<<(int)nwork, 6 * 32, cfg.smem, s>>>(
-          views, work, tabs, cfg.lp, cfg.stg, cfg.ldeg);
-    else if (cfg.nw == 4)
-      collocate_kernel<kT0, kT1, kT2, 4, true><<<(int)nwork, 4 * 32, cfg.smem, s>>>(
-          views, work, tabs, cfg.lp, cfg.stg, cfg.ldeg);
-    else
-      return cudaErrorInvalidValue;
-    return cudaGetLastError();
+#define GPW_COLLOC_SK(NWV, SKV)                                                            \
+  if (cfg.nw == NWV && cfg.skew == SKV) {                                                  \
+    collocate_kernel<kT0, kT1, kT2, NWV, SKV><<<(int)nwork, NWV * 32, cfg.smem, s>>>(      \
+        views, work, tabs, cfg.lp, cfg.stg, cfg.ldeg);                                     \
+    return cudaGetLastError();                                                             \
+  }
+    GPW_COLLOC_SK(8, 1) GPW_COLLOC_SK(6, 1) GPW_COLLOC_SK(4, 1)
+    GPW_COLLOC_SK(8, 2) GPW_COLLOC_SK(6, 2) GPW_COLLOC_SK(4, 2)
+#undef GPW_COLLOC_SK
+    return cudaErrorInvalidValue;
   }
 #define GPW_COLLOC_NW(a, b, c, NWV)                                                        \
   if (t0 == a && t1 == b && t2 == c && cfg.nw == NWV) {                                    \
@@ -2063,8 +2072,12 @@ cudaError_t launch_integrate_views(const GridLaunch& cfg, int lext, const PlanVi
   const int t0 = cfg.tile[0], t1 = cfg.tile[1], t2 = cfg.tile[2];
   if (cfg.skew) {
     if (!(t0 == kT0 && t1 == kT1 && t2 == kT2)) return cudaErrorInvalidValue;
-    integrate_kernel<kT0, kT1, kT2, kNW, true><<<(int)nwork, kNW * 32, cfg.smem, s>>>(
-        views, work, tabs, lext, cfg.lp, cfg.stg);
+    if (cfg.skew == 1)
+      integrate_kernel<kT0, kT1, kT2, kNW, 1><<<(int)nwork, kNW * 32, cfg.smem, s>>>(
+          views, work, tabs, lext, cfg.lp, cfg.stg);
+    else
+      integrate_kernel<kT0, kT1, kT2, kNW, 2><<<(int)nwork, kNW * 32, cfg.smem, s>>>(
+          views, work, tabs, lext, cfg.lp, cfg.stg);
     return cudaGetLastError();
   }
 #define GPW_TILE_INTEG(a, b, c)                                                            \
@@ -2089,7 +2102,7 @@ cudaError_t launch_collocate(const Plan& p, cudaStream_t s, int ldeg) {
   cfg.stg = ldeg ? p.stg_colloc_t : p.stg_colloc;
   cfg.smem = ldeg ? p.smem_colloc_t : p.smem_colloc;
   cfg.ldeg = ldeg;
-  cfg.skew = p.skew ? 1 : 0;
+  cfg.skew = p.skew ? (p.skew_zc ? 1 : 2) : 0;
   return launch_collocate_views(cfg, p.d.view, p.d.work_c, p.nwork, p.d.tabs, s);
 }
 
@@ -2103,7 +2116,7 @@ cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s) {
   cfg.lp = p.lmax + lext + 1;
   cfg.stg = lext > 1 ? p.stg_integ3 : (lext ? p.stg_integ1 : p.stg_integ);
   cfg.smem = lext > 1 ? p.smem_integ3 : (lext ? p.smem_integ1 : p.smem_integ);
-  cfg.skew = p.skew ? 1 : 0;
+  cfg.skew = p.skew ? (p.skew_zc ? 1 : 2) : 0;
   return launch_integrate_views(cfg, lext, p.d.view, p.d.work_i, p.nwork_i, p.d.tabs, s);
 }
 
@@ -2150,10 +2163,11 @@ cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int 
       return cudaErrorInvalidValue;
     colloc->stg = even(even(CollocLayout<kT0, kT1, kT2>::stage(lmax + 1)) +
                        colloc_skew_extra<kT0, kT1, kT2>());
-    if (pick_colloc_warps<kT0, kT1, kT2, true>(colloc->stg, nw_req, &colloc->nw, &colloc->smem) == 0)
+    const auto pick = skew == 1 ? pick_colloc_warps<kT0, kT1, kT2, 1> : pick_colloc_warps<kT0, kT1, kT2, 2>;
+    if (pick(colloc->stg, nw_req, &colloc->nw, &colloc->smem) == 0)
       return cudaErrorInvalidValue;
     integ1->stg = even(even(IntegLayout<kT0, kT1, kT2>::stage(lmax + 2)) +
-                       integ_skew_extra<kT0, kT1, kT2>());
+                       integ_skew_extra<kT0, kT1, kT2>(skew == 1));
     integ1->smem = integ_smem<kT0, kT1, kT2>(integ1->stg);
   }
   return cudaSuccess;
@@ -2183,9 +2197,7 @@ PlanView make_view(const Plan& p) {
   v.xr = p.xr;
   // 1: general non-orthogonal cell; 2: the third row orthogonal to the first two
   // (hexagonal, monoclinic with unique axis c), only the R01 cross factor
-  bool zc = false;
-  for (int k = 0; k < p.nlev; ++k) zc = zc || p.lev[k].gm[4] != 0.0 || p.lev[k].gm[5] != 0.0;
-  v.skew = p.skew ? (zc ? 1 : 2) : 0;
+  v.skew = p.skew ? (p.skew_zc ? 1 : 2) : 0;
   v.geo = p.d.geo;
   v.hot_a = p.d.hot_a;
   return v;

@@ -743,6 +743,9 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
         for (int c = 0; c < 3; ++c) lv.fr[3 * d + c] = lv.N[d] * plan->rec[3 * d + c];
     }
   }
+  plan->skew_zc = false;
+  for (int k = 0; k < K; ++k)
+    plan->skew_zc = plan->skew_zc || plan->lev[k].gm[4] != 0.0 || plan->lev[k].gm[5] != 0.0;
   for (int k = 1; k < K; ++k)
     if (plan->E[k] > plan->E[k - 1]) {
       set_error("gpw_plan: level cutoffs must decrease from level 0");
