@@ -137,24 +137,28 @@ __global__ void tables_kernel(long long np, const KLevels K, const int4* __restr
       }
     }
     if (skew) {
-      // cross-factor row seeds (layout at skew_seeds): for the row pairs (0,1), (0,2), (1,2)
-      // and every box position x along the first row, U[x] = exp(c a_d(x) a_e(0)) and
-      // Q[x] = exp(c a_d(x)), a_d(x) = lo_d + x - p_d, c = -2 alpha_p G_de, so that
-      // exp(c a_d(x) a_e(y)) = U[x] Q[x]^y
+      // cross-factor tables over the pair box, after the 1-D tables: for the row pairs
+      // (0,1), (0,2), (1,2), R_de[x][y] = exp(c a_d(x) a_e(y)), a_d(x) = lo_d + x - p_d,
+      // c = -2 alpha_p G_de; each row is geometric in y (two exp, then products)
       double* sd = tab + base + (long long)(L + 2 + xr) * ntot;
       const int pd[3][3] = {{0, 1, 3}, {0, 2, 4}, {1, 2, 5}};
-      const int soff[3] = {0, 2 * n[0], 4 * n[0]};
-      const int items = 2 * n[0] + n[1];
-      for (int it = lane; it < items; it += 32) {
+      const long long soff[3] = {0, (long long)n[0] * n[1], (long long)n[0] * (n[1] + n[2])};
+      const int rows = 2 * n[0] + n[1];
+      for (int it = lane; it < rows; it += 32) {
         const int k = it < n[0] ? 0 : (it < 2 * n[0] ? 1 : 2);
         const int x = it - (k == 0 ? 0 : (k == 1 ? n[0] : 2 * n[0]));
         const int d = pd[k][0], e = pd[k][1];
         const double c = -2.0 * ap * lv.gm[pd[k][2]];
         const double ad = (double)(lo[d] + x) - pg[d];
         const double ae = (double)lo[e] - pg[e];
-        const int len = k == 2 ? n[1] : n[0];
-        sd[soff[k] + x] = exp(c * ad * ae);
-        sd[soff[k] + len + x] = exp(c * ad);
+        const int len = n[e];
+        double v = exp(c * ad * ae);
+        const double q = exp(c * ad);
+        double* row = sd + soff[k] + (long long)x * len;
+        for (int y = 0; y < len; ++y) {
+          row[y] = v;
+          v *= q;
+        }
       }
     }
   }
@@ -448,67 +452,37 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
 // exp and multiplies along the row.  Rows go to sR ([T0][T1], [T0][T2], [T1][T2]).
 template <int T0, int T1, int T2>
 struct SkewRows {
+  // a task's windows of the pair's cross-factor tables: R01 [T0][T1], R02 [T0][T2],
+  // R12 [T1][T2] (the pair's tables follow its 1-D tables: R01 [n0][n1], R02 [n0][n2],
+  // R12 [n1][n2])
   static constexpr int kSize = T0 * T1 + T0 * T2 + T1 * T2;
-  // a task's seeds staged in shared memory: U01, Q01, U02, Q02 (T0 each), U12, Q12 (T1)
-  static constexpr int kSeeds = 4 * T0 + 2 * T1;
-  static_assert(2 * T0 + T1 <= 32 && kSeeds <= 64, "one lane per cross-factor row");
-  // seeds per pair after its 1-D tables: U01, Q01, U02, Q02 (n0 each), U12, Q12 (n1 each)
 };
 
-// x^n for a small non-negative integer n, by squaring
-__device__ __forceinline__ double ipow_d(double x, int n) {
-  double r = 1.0;
-  while (n > 0) {
-    if (n & 1) r *= x;
-    x *= x;
-    n >>= 1;
-  }
-  return r;
-}
-
-// Stage a task's cross-factor seeds (tables_kernel, after the pair's 1-D tables) into
-// shared memory with cp.async, next to its other windows: U and Q at the task's rows.
+// Stage a task's windows of its pair's cross-factor tables (tables_kernel) into shared
+// memory with cp.async, next to its other windows: R01 always, R02 and R12 when zc.
 template <int T0, int T1, int T2>
-__device__ __forceinline__ void stage_seeds(const double* __restrict__ tab, long long toff,
-                                            const Task& tk, int xr, double* __restrict__ sS,
-                                            int lane) {
-  const int n0 = tk.n[0], n1 = tk.n[1], m0 = tk.m[0], m1 = tk.m[1];
-  const double* sd = tab + toff + (long long)(tk.L + 2 + xr) * (n0 + n1 + tk.n[2]);
-  if (lane < 4 * m0) {
-    const int k = lane / m0, i = lane - k * m0;  // k: U01, Q01, U02, Q02
-    cp_async8(sS + k * T0 + i, sd + k * n0 + tk.t[0] + i);
-  } else if (lane < 4 * m0 + 2 * m1) {
-    const int r = lane - 4 * m0, k = r / m1, i = r - k * m1;  // U12, Q12
-    cp_async8(sS + 4 * T0 + k * T1 + i, sd + 4 * n0 + k * n1 + tk.t[1] + i);
-  }
-}
-
-// The task's cross-factor rows from its staged seeds: row i of the pair (d, e) starts at
-// U[i] Q[i]^(t_e) and advances by Q[i] per step along e.
-template <int T0, int T1, int T2>
-__device__ __forceinline__ void skew_rows(const double* __restrict__ sS, const Task& tk,
-                                          double* __restrict__ sR, int lane, bool zc) {
+__device__ __forceinline__ void stage_cross(const double* __restrict__ tab, long long toff,
+                                            const Task& tk, int xr, double* __restrict__ sR,
+                                            int lane, bool zc) {
+  const int n0 = tk.n[0], n1 = tk.n[1], n2 = tk.n[2];
   const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
-  if (!zc && lane >= m0) return;  // third row orthogonal to the others: R01 only
-  int len, te;
-  double u, q;
-  double* dst;
-  if (lane < m0) {
-    u = sS[lane]; q = sS[T0 + lane]; te = tk.t[1]; len = m1; dst = sR + lane * T1;
-  } else if (lane < 2 * m0) {
-    const int i = lane - m0;
-    u = sS[2 * T0 + i]; q = sS[3 * T0 + i]; te = tk.t[2]; len = m2; dst = sR + T0 * T1 + i * T2;
-  } else if (lane < 2 * m0 + m1) {
-    const int i = lane - 2 * m0;
-    u = sS[4 * T0 + i]; q = sS[4 * T0 + T1 + i]; te = tk.t[2]; len = m2;
-    dst = sR + T0 * T1 + T0 * T2 + i * T2;
-  } else {
-    return;
+  const int t0 = tk.t[0], t1 = tk.t[1], t2 = tk.t[2];
+  const double* sd = tab + toff + (long long)(tk.L + 2 + xr) * (n0 + n1 + n2);
+  const float i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
+  for (int it = lane; it < m0 * m1; it += 32) {
+    const int i = fdiv(it, i1f), j = it - i * m1;
+    cp_async8(sR + i * T1 + j, sd + (long long)(t0 + i) * n1 + t1 + j);
   }
-  double v = u * ipow_d(q, te);
-  for (int j = 0; j < len; ++j) {
-    dst[j] = v;
-    v *= q;
+  if (!zc) return;
+  const double* r02 = sd + (long long)n0 * n1;
+  const double* r12 = r02 + (long long)n0 * n2;
+  for (int it = lane; it < m0 * m2; it += 32) {
+    const int i = fdiv(it, i2f), j = it - i * m2;
+    cp_async8(sR + T0 * T1 + i * T2 + j, r02 + (long long)(t0 + i) * n2 + t2 + j);
+  }
+  for (int it = lane; it < m1 * m2; it += 32) {
+    const int i = fdiv(it, i2f), j = it - i * m2;
+    cp_async8(sR + T0 * T1 + T0 * T2 + i * T2 + j, r12 + (long long)(t1 + i) * n2 + t2 + j);
   }
 }
 
@@ -565,10 +539,9 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
   double* sT2 = stage_base + 2 * bufn;
   int* s_row = reinterpret_cast<int*>(sT2 + lp * T0 * T1);
   int* s_qi = s_row + T0 * T1;
-  // non-orthogonal cells: the task's cross-factor rows and two seed buffers (one per
-  // staging buffer), after the regular per-warp staging
-  double* sR = stage_base + ((Lay::stage(lp) + 1) & ~1);
-  double* sSeed = sR + SkewRows<T0, T1, T2>::kSize;
+  // non-orthogonal cells: the task's cross-factor windows, one per staging buffer, after
+  // the regular per-warp staging
+  double* sRb = stage_base + ((Lay::stage(lp) + 1) & ~1);
   const bool zc = SK == 1 && pv.skew != 2;  // cross terms with the third row (R02, R12)
   __syncthreads();
 
@@ -595,7 +568,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
       const int l = fdiv(it, i2f), i = it - l * m2;
       cp_async8(sg2 + l * T2 + i, t2 + l * tk.n[2] + i);
     }
-    if constexpr (SK != 0) stage_seeds<T0, T1, T2>(tab, toff, tk, pv.xr, sSeed + b * SkewRows<T0, T1, T2>::kSeeds, lane);
+    if constexpr (SK != 0) stage_cross<T0, T1, T2>(tab, toff, tk, pv.xr, sRb + b * SkewRows<T0, T1, T2>::kSize, lane, zc);
   };
 
   long long e = sb.eb + warp;
@@ -648,7 +621,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
         s_qi[q] = i0 | (i1 << 8);
         s_row[q] = ((tk.u[0] + i0) * T1 + (tk.u[1] + i1)) * T2 + tk.u[2];
       }
-      if constexpr (SK != 0) skew_rows<T0, T1, T2>(sSeed + buf * SkewRows<T0, T1, T2>::kSeeds, tk, sR, lane, zc);
+      const double* sR = sRb + buf * SkewRows<T0, T1, T2>::kSize;
       __syncwarp();
 #define GPW_COLLOC_L(LL)                                                                     \
   case LL:                                                                                   \
@@ -755,9 +728,8 @@ __global__ void __launch_bounds__(NW * 32)
   // and the factor rows, after the regular per-warp staging
   // (the potential window times the cross factors last: plans whose third row is
   // orthogonal to the others do not use it and are launched without it)
-  double* sR = stage_base + ((Lay::stage(lpx) + 1) & ~1);
-  double* sSeed = sR + SkewRows<T0, T1, T2>::kSize;
-  double* sVE = sSeed + 2 * SkewRows<T0, T1, T2>::kSeeds;
+  double* sRb = stage_base + ((Lay::stage(lpx) + 1) & ~1);
+  double* sVE = sRb + 2 * SkewRows<T0, T1, T2>::kSize;
   const bool zc = SK == 1 && pv.skew != 2;  // cross terms with the third row (R02, R12)
   __syncthreads();
 
@@ -765,7 +737,7 @@ __global__ void __launch_bounds__(NW * 32)
     double* sg1 = stage_base + b * bufn;
     stage_yz_async<P1, P2>(tab + toff, tk, tk.L + lext + 1, tk.L + 2 + pv.xr, sg1,
                            sg1 + lpx * P1, lane);
-    if constexpr (SK != 0) stage_seeds<T0, T1, T2>(tab, toff, tk, pv.xr, sSeed + b * SkewRows<T0, T1, T2>::kSeeds, lane);
+    if constexpr (SK != 0) stage_cross<T0, T1, T2>(tab, toff, tk, pv.xr, sRb + b * SkewRows<T0, T1, T2>::kSize, lane, zc);
   };
 
   long long e = sb.eb + warp;
@@ -811,10 +783,7 @@ __global__ void __launch_bounds__(NW * 32)
       const int m01 = m0 * m1;
       const double* vbase = sv;
       int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
-      if constexpr (SK != 0) {
-        skew_rows<T0, T1, T2>(sSeed + buf * SkewRows<T0, T1, T2>::kSeeds, tk, sR, lane, zc);
-        __syncwarp();
-      }
+      const double* sR = sRb + buf * SkewRows<T0, T1, T2>::kSize;
       if (SK == 1 && zc) {
         const double* r02 = sR + T0 * T1;
         const double* r12 = r02 + T0 * T2;
@@ -1811,11 +1780,10 @@ constexpr int kNW = 8;
 
 // per-warp staging doubles of the non-orthogonal variants (cross factors and their rows)
 template <int T0, int T1, int T2>
-int colloc_skew_extra() { return SkewRows<T0, T1, T2>::kSize + 2 * SkewRows<T0, T1, T2>::kSeeds; }
+int colloc_skew_extra() { return 2 * SkewRows<T0, T1, T2>::kSize; }
 template <int T0, int T1, int T2>
 int integ_skew_extra(bool zc) {
-  return (zc ? IntegLayout<T0, T1, T2>::kSV : 0) + SkewRows<T0, T1, T2>::kSize +
-         2 * SkewRows<T0, T1, T2>::kSeeds;
+  return (zc ? IntegLayout<T0, T1, T2>::kSV : 0) + 2 * SkewRows<T0, T1, T2>::kSize;
 }
 
 template <int T0, int T1, int T2>

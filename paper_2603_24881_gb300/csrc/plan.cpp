@@ -1005,8 +1005,9 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     lmax = std::max(lmax, L);
     H->tab_off[p] = tab_total;
     tab_total += (long long)(L + 2 + plan->xr) * (n[0] + n[1] + n[2]);
-    // non-orthogonal cells: the cross-factor row seeds after the 1-D tables
-    if (plan->skew) tab_total += 2LL * (2 * n[0] + n[1]);
+    // non-orthogonal cells: the cross-factor tables R01, R02, R12 after the 1-D tables
+    if (plan->skew)
+      tab_total += (long long)n[0] * n[1] + (long long)n[0] * n[2] + (long long)n[1] * n[2];
     H->coef_off[p] = coef_total;
     coef_total += nc3(L + 1 + plan->xr);
     H->xt_off[p] = xt_total;
