@@ -1,5 +1,6 @@
-"""Full-size parity on sampled outputs (water256 as timed by bench.py, and carbon with f
-shells), with the plans in their default launch configuration.
+"""Full-size parity on sampled outputs (water256 as timed by bench.py, carbon with f
+shells, and water256 in a triclinic cell), with the plans in their default launch
+configuration.
 
 The oracle cannot build whole grids at this size in seconds, so it computes one by one:
 the integer pair table (all of it), level densities at sampled grid points, V shell
@@ -27,7 +28,7 @@ def gpw():
     return g
 
 
-@pytest.fixture(scope="module", params=["water256", "carbon"])
+@pytest.fixture(scope="module", params=["water256", "carbon", "water256_triclinic"])
 def big(request, gpw):
     s = workloads.config(request.param)
     gp = gpw.Plan(s)
@@ -99,7 +100,7 @@ def test_fused_path_consistent_and_adjoint(big, gpw):
     g = gp.eval_mat_ip1(s.D, f["v"])
     assert float((fg["grad"] - g).abs().max()) <= 1e-7
     rho, v = f["rho"], f["v"]
-    omega = float(np.prod(np.diag(s.lattice)))
+    omega = float(abs(np.linalg.det(np.asarray(s.lattice, dtype=float))))  # any lattice
     lhs = omega / rho.numel() * float((rho * v).sum())
     rhs = float((torch.as_tensor(s.D, device="cuda") * V).sum())
     assert abs(lhs - rhs) <= 1e-10 * abs(lhs)
