@@ -451,7 +451,7 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
 // each R row geometric in its second index (eta = eta0 + i): one lane per row takes two
 // exp and multiplies along the row.  Rows go to sR ([T0][T1], [T0][T2], [T1][T2]).
 template <int T0, int T1, int T2>
-struct SkewRows {
+struct CrossWindows {
   // a task's windows of the pair's cross-factor tables: R01 [T0][T1], R02 [T0][T2],
   // R12 [T1][T2] (the pair's tables follow its 1-D tables: R01 [n0][n1], R02 [n0][n2],
   // R12 [n1][n2])
@@ -568,7 +568,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
       const int l = fdiv(it, i2f), i = it - l * m2;
       cp_async8(sg2 + l * T2 + i, t2 + l * tk.n[2] + i);
     }
-    if constexpr (SK != 0) stage_cross<T0, T1, T2>(tab, toff, tk, pv.xr, sRb + b * SkewRows<T0, T1, T2>::kSize, lane, zc);
+    if constexpr (SK != 0) stage_cross<T0, T1, T2>(tab, toff, tk, pv.xr, sRb + b * CrossWindows<T0, T1, T2>::kSize, lane, zc);
   };
 
   long long e = sb.eb + warp;
@@ -621,7 +621,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
         s_qi[q] = i0 | (i1 << 8);
         s_row[q] = ((tk.u[0] + i0) * T1 + (tk.u[1] + i1)) * T2 + tk.u[2];
       }
-      const double* sR = sRb + buf * SkewRows<T0, T1, T2>::kSize;
+      const double* sR = sRb + buf * CrossWindows<T0, T1, T2>::kSize;
       __syncwarp();
 #define GPW_COLLOC_L(LL)                                                                     \
   case LL:                                                                                   \
@@ -729,7 +729,7 @@ __global__ void __launch_bounds__(NW * 32)
   // (the potential window times the cross factors last: plans whose third row is
   // orthogonal to the others do not use it and are launched without it)
   double* sRb = stage_base + ((Lay::stage(lpx) + 1) & ~1);
-  double* sVE = sRb + 2 * SkewRows<T0, T1, T2>::kSize;
+  double* sVE = sRb + 2 * CrossWindows<T0, T1, T2>::kSize;
   const bool zc = SK == 1 && pv.skew != 2;  // cross terms with the third row (R02, R12)
   __syncthreads();
 
@@ -737,7 +737,7 @@ __global__ void __launch_bounds__(NW * 32)
     double* sg1 = stage_base + b * bufn;
     stage_yz_async<P1, P2>(tab + toff, tk, tk.L + lext + 1, tk.L + 2 + pv.xr, sg1,
                            sg1 + lpx * P1, lane);
-    if constexpr (SK != 0) stage_cross<T0, T1, T2>(tab, toff, tk, pv.xr, sRb + b * SkewRows<T0, T1, T2>::kSize, lane, zc);
+    if constexpr (SK != 0) stage_cross<T0, T1, T2>(tab, toff, tk, pv.xr, sRb + b * CrossWindows<T0, T1, T2>::kSize, lane, zc);
   };
 
   long long e = sb.eb + warp;
@@ -783,7 +783,7 @@ __global__ void __launch_bounds__(NW * 32)
       const int m01 = m0 * m1;
       const double* vbase = sv;
       int u0 = tk.u[0], u1 = tk.u[1], u2 = tk.u[2];
-      const double* sR = sRb + buf * SkewRows<T0, T1, T2>::kSize;
+      const double* sR = sRb + buf * CrossWindows<T0, T1, T2>::kSize;
       if (SK == 1 && zc) {
         const double* r02 = sR + T0 * T1;
         const double* r12 = r02 + T0 * T2;
@@ -1780,10 +1780,10 @@ constexpr int kNW = 8;
 
 // per-warp staging doubles of the non-orthogonal variants (cross factors and their rows)
 template <int T0, int T1, int T2>
-int colloc_skew_extra() { return 2 * SkewRows<T0, T1, T2>::kSize; }
+int colloc_skew_extra() { return 2 * CrossWindows<T0, T1, T2>::kSize; }
 template <int T0, int T1, int T2>
 int integ_skew_extra(bool zc) {
-  return (zc ? IntegLayout<T0, T1, T2>::kSV : 0) + 2 * SkewRows<T0, T1, T2>::kSize;
+  return (zc ? IntegLayout<T0, T1, T2>::kSV : 0) + 2 * CrossWindows<T0, T1, T2>::kSize;
 }
 
 template <int T0, int T1, int T2>
