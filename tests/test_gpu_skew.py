@@ -166,3 +166,23 @@ def test_skew_edge_cases(gpw):
     assert abs(out["EH"] - r["EH"]) <= 1e-8 and abs(out["Ex"] - r["Ex"]) <= 1e-8
     assert _rel(out["V"].cpu().numpy(), r["V"]) <= RTOL
     assert np.max(np.abs(out["grad"].cpu().numpy() - op.grad_levels(s.D, r["v_levels"]))) <= 1e-7
+
+
+def test_skew_gradient_matches_gpu_finite_differences(gpw):
+    # central differences of the GPU energy with the plan frozen (gpw_plan_update_coords
+    # moves the centres: images along the lattice rows, tables and cross factors rebuilt)
+    s = CASES["skewed_spd"]()
+    gp = gpw.Plan(s)
+    g = gp.fock_grad(s.D)["grad"].cpu().numpy()
+    h = 1e-4
+    for atom, d in [(0, 0), (1, 2)]:
+        e = []
+        for sgn in (1, -1):
+            c = s.coords.copy()
+            c[atom, d] += sgn * h
+            gp.update_coords(c)
+            o = gp.fock(s.D)
+            e.append(o["EH"] + o["Ex"])
+        gp.update_coords(s.coords)
+        fd = (e[0] - e[1]) / (2 * h)
+        assert abs(fd - g[atom, d]) <= 1e-6 * max(1.0, abs(g[atom, d]))
