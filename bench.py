@@ -66,7 +66,7 @@ def _workload_desc(name: str, system, stats) -> str:
 # csrc/kernels.cu + csrc/plan.cpp at capture time.
 TRAFFIC = {
     # integration at degree L+1 (8x8x32 sub-box), water256, one launch: read + write
-    "integrate_ip1": {"bytes_per_launch": 1.7973e10, "src_sha": "22e87322b526b3de",
+    "integrate_ip1": {"bytes_per_launch": 1.7974e10, "src_sha": "db862321085d373d",
                       "capture": "profiles/launches_water256_fock_grad.md"},
 }
 
