@@ -111,16 +111,40 @@ static double orc_pair_h(double cab, double kab, int la, int lb, double dA, doub
   return cab * kab * orc_ipow(r + dA, la) * orc_ipow(r + dB, lb) * r * r * exp(-ap * r * r);
 }
 
-/* Pair extent R_p: largest root of h(r) = tau on r >= sqrt((la+lb+2)/(2 ap)),
- * where h decreases; -1 when h is already below tau there (pair dropped). */
+/* d log h / dr = la/(r+dA) + lb/(r+dB) + 2/r - 2 ap r: strictly decreasing in r, so h has
+ * a single maximum, at the zero of this function, never beyond sqrt((la+lb+2)/(2 ap)). */
+static double orc_pair_dlogh(int la, int lb, double dA, double dB, double ap, double r) {
+  return (double)la / (r + dA) + (double)lb / (r + dB) + 2.0 / r - 2.0 * ap * r;
+}
+
+/* Pair extent R_p: the largest root of h(r) = tau (Eq. cut applied to the pair), -1 when
+ * h stays below tau for every r (pair dropped).  With r0 = sqrt((la+lb+2)/(2 ap)):
+ *   h(r0) >= tau: the root lies beyond r0, where h decreases; bracket it by doubling and
+ *     bisect 64 times;
+ *   h(r0) <  tau: the maximum r* of h lies in (0, r0] (64 bisection steps on the sign of
+ *     d log h / dr); h(r*) < tau drops the pair, otherwise the root is bisected 64 times
+ *     on [r*, r0], where h decreases.
+ * The returned value is the upper end of the final bracket: h(R_p) < tau. */
 static double orc_pair_extent(double cab, double kab, int la, int lb, double dA, double dB,
                               double ap, double tau) {
   double r0 = sqrt((double)(la + lb + 2) / (2.0 * ap));
-  if (orc_pair_h(cab, kab, la, lb, dA, dB, ap, r0) < tau) return -1.0;
-  double hi = r0;
-  for (int it = 0; it < 200 && orc_pair_h(cab, kab, la, lb, dA, dB, ap, hi) >= tau; ++it)
-    hi *= 2.0;
-  double lo = r0;
+  double lo, hi;
+  if (orc_pair_h(cab, kab, la, lb, dA, dB, ap, r0) >= tau) {
+    hi = r0;
+    for (int it = 0; it < 200 && orc_pair_h(cab, kab, la, lb, dA, dB, ap, hi) >= tau; ++it)
+      hi *= 2.0;
+    lo = r0;
+  } else {
+    double a = 0.0, b = r0;
+    for (int it = 0; it < 64; ++it) {
+      double mid = 0.5 * (a + b);
+      if (orc_pair_dlogh(la, lb, dA, dB, ap, mid) > 0.0) a = mid; else b = mid;
+    }
+    double rs = a > 0.0 ? a : b;
+    if (orc_pair_h(cab, kab, la, lb, dA, dB, ap, rs) < tau) return -1.0;
+    lo = rs;
+    hi = r0;
+  }
   for (int it = 0; it < 64; ++it) {
     double mid = 0.5 * (lo + hi);
     if (orc_pair_h(cab, kab, la, lb, dA, dB, ap, mid) >= tau) lo = mid; else hi = mid;

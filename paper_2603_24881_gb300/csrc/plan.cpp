@@ -100,6 +100,16 @@ void box_at_skew(double R, const double* P, const double* N, const SkewBox& sk, 
   }
 }
 
+// d log h / dr: strictly decreasing in r, so h has one maximum, at r* <= r0.
+double pair_dlogh(int la, int lb, double dA, double dB, double ap, double r) {
+  return (double)la / (r + dA) + (double)lb / (r + dB) + 2.0 / r - 2.0 * ap * r;
+}
+
+// R_p = the largest root of h = tau.  With r0 = sqrt((la+lb+2)/(2 ap)): if h(r0) >= tau the
+// root lies beyond r0 (bracketed by doubling); otherwise the maximum r* of h in (0, r0] is
+// found by 64 bisection steps on the sign of d log h / dr, h(r*) < tau drops the pair, and
+// the root is bisected on [r*, r0].  Either way h decreases on the bracket of the final
+// bisection, whose upper end is R_p.
 bool pair_box(double cab, double kab, int la, int lb, double dA, double dB, double ap,
               double tau, const double* P, const double* N, const double* L, int* lo_out,
               int* hi_out, const SkewBox* sk = nullptr) {
@@ -110,10 +120,22 @@ bool pair_box(double cab, double kab, int la, int lb, double dA, double dB, doub
       box_at(R, P, N, L, lo, hi);
   };
   double r0 = std::sqrt((double)(la + lb + 2) / (2.0 * ap));
-  if (pair_h(cab, kab, la, lb, dA, dB, ap, r0) < tau) return false;
-  double hi = r0;
-  for (int it = 0; it < 200 && pair_h(cab, kab, la, lb, dA, dB, ap, hi) >= tau; ++it) hi *= 2.0;
-  double lo = r0;
+  double lo, hi;
+  if (pair_h(cab, kab, la, lb, dA, dB, ap, r0) >= tau) {
+    hi = r0;
+    for (int it = 0; it < 200 && pair_h(cab, kab, la, lb, dA, dB, ap, hi) >= tau; ++it) hi *= 2.0;
+    lo = r0;
+  } else {
+    double a = 0.0, b = r0;
+    for (int it = 0; it < 64; ++it) {
+      double mid = 0.5 * (a + b);
+      if (pair_dlogh(la, lb, dA, dB, ap, mid) > 0.0) a = mid; else b = mid;
+    }
+    double rs = a > 0.0 ? a : b;
+    if (pair_h(cab, kab, la, lb, dA, dB, ap, rs) < tau) return false;
+    lo = rs;
+    hi = r0;
+  }
   for (int it = 0; it < 64; ++it) {
     double mid = 0.5 * (lo + hi);
     if (pair_h(cab, kab, la, lb, dA, dB, ap, mid) >= tau) lo = mid; else hi = mid;

@@ -27,6 +27,7 @@ def test_header_declares_the_path():
 
 
 def test_library_exports_every_declared_symbol():
+    gpw.load()  # builds the library in-tree when it is missing
     lib = ctypes.CDLL(gpw.lib_path())
     for n in _declared():
         assert hasattr(lib, n), n
