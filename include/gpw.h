@@ -148,6 +148,9 @@ typedef struct {
   int colloc_warps;    /* warps per collocation block (0 until the plan is committed) */
   int integ_chunk;     /* most tasks per integration work item */
   int xc;              /* exchange functional (GPW_XC_*) */
+  double volume;       /* cell volume Omega = |det(lattice)| (Bohr^3) */
+  double weight[GPW_MAX_LEVELS];  /* grid weight Omega / N_k of level k: the quadrature
+                                     weight of eval_mat, the gradient and the energies */
 } gpw_plan_info;
 
 /* Build a plan: normalise primitives, screen pairs (Eq. cut; pairs a <= b over images T
@@ -189,8 +192,9 @@ int gpw_plan_query(gpw_plan_t plan, gpw_plan_info* info);
 int gpw_plan_update_coords(gpw_plan_t plan, const double* coords, void* stream);
 
 /* Copy the screened pair table to host arrays of plan.npairs rows (any may be NULL):
- * ab (2 ints: primitive indices a <= b), img (3 ints: T = img . diag(L)), level,
- * lo/hi (3 ints each: integer box on the level mesh, inclusive).  Synchronous. */
+ * ab (2 ints: primitive indices a <= b), img (3 ints n: the image T = sum_d n_d R_d of b
+ * over the lattice rows R_d, n . diag(L) for an orthorhombic cell), level, lo/hi (3 ints
+ * each: integer box on the level mesh along the rows, inclusive).  Synchronous. */
 int gpw_plan_pairs(gpw_plan_t plan, int* ab, int* img, int* level, int* lo, int* hi);
 
 /* Copy one task list of a committed plan to host buffers (any may be NULL): integ = 0
@@ -288,9 +292,18 @@ int gpw_batch_set(gpw_batch_t batch, int nplans, const gpw_plan_t* plans, void* 
 /* gpw_fock_grad_async for every attached plan i: D[i], V[i] device nao_i x nao_i,
  * grad[i] device natm_i x 3 (grad or grad[i] may be NULL to skip the gradient),
  * energies_dev device 2*nplans doubles (E_H, E_x of plan i at 2i, 2i+1).  Allocates
- * nothing and does not synchronise, so the sequence can be captured in a CUDA graph. */
+ * nothing and does not synchronise, so the sequence can be captured in a CUDA graph.
+ * A captured graph holds the plan set, launch shapes and device work lists in force at
+ * capture: every later gpw_batch_set (which may free and refill those lists) makes it
+ * invalid, and it must not be replayed after one.  Capture again when
+ * gpw_batch_generation has changed; destroying a plan of the set also invalidates it. */
 int gpw_batch_fock_grad_async(gpw_batch_t batch, const double* const* D, double* const* V,
                               double* const* grad, double* energies_dev, void* stream);
+
+/* Number of successful gpw_batch_set calls on the batch so far (0 after create): a graph
+ * captured at generation g is valid only while the generation is still g.  Not a paper
+ * operation. */
+int gpw_batch_generation(gpw_batch_t batch, long long* generation);
 
 void gpw_batch_destroy(gpw_batch_t batch);
 
@@ -334,8 +347,13 @@ int gpw_profile_read(gpw_plan_t plan, double* ms, long long* count, int nphases,
  * The working memory is one fixed 32 KB array in the library's device image, shared by
  * every call on a GPU and keeping the last call's contents (each call writes what it
  * reads, so nothing needs clearing); calls whose executions overlap on the GPU race on
- * it.  The first call on each device looks up the array's address with that device
- * current; make that first call before any stream capture.  Asynchronous on `stream`. */
+ * it.  The first call in each CUDA context (normally once per device) looks up the
+ * array's device address, and with lazy module loading (CUDA's default) that lookup loads
+ * the library's device image onto the device, which may allocate inside the driver: make
+ * that first call during set-up, with the device current and before any stream capture.
+ * Later calls in the same context reuse the address; a context created later (after a
+ * device reset, or another context on the device) has its own first call.
+ * Asynchronous on `stream`. */
 int gpw_lda_x_noalloc(const double* rho, long long n, double weight, double* v_x, double* e_x,
                       void* stream);
 

@@ -28,7 +28,9 @@
  * zeros).  The separable mode is orthorhombic only; a non-orthogonal cell (App.,
  * non-orthogonal lattices) is evaluated point by point.
  * All arithmetic in double.  Build with -ffp-contract=off so that the screening
- * decisions are reproducible.
+ * decisions are reproducible.  Collocation runs OpenMP over pairs with a static
+ * pair-to-thread map into per-thread grids summed in thread order, so a density is
+ * reproducible bit for bit at a given thread count.
  */
 #include <math.h>
 #include <stdint.h>
@@ -404,7 +406,7 @@ void orc_collocate(int mode, long npairs, const int* ab, const int* img, const i
     int tid = 0;
 #endif
     double* g = priv + (size_t)tid * grid_total;
-#pragma omp for schedule(dynamic, 16)
+#pragma omp for schedule(static, 16)  /* fixed pair-to-thread map: deterministic sums */
     for (long p = 0; p < npairs; ++p) {
       orc_pair_t q;
       orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, lat);
@@ -694,7 +696,7 @@ void orc_collocate_tau(long npairs, const int* ab, const int* img, const int* le
     int tid = 0;
 #endif
     double* g = priv + (size_t)tid * grid_total;
-#pragma omp for schedule(dynamic, 16)
+#pragma omp for schedule(static, 16)  /* fixed pair-to-thread map: deterministic sums */
     for (long p = 0; p < npairs; ++p) {
       orc_pair_t q;
       orc_load_pair(&q, p, ab, img, lev, lo, hi, pc, pl, pal, pcn, pao, lat);

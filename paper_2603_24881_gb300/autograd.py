@@ -32,8 +32,9 @@ def _set_coords(plan, coords):
 
 
 def _scale(plan):
-    L = np.diag(np.asarray(plan.system.lattice, dtype=np.float64))
-    return float(np.prod(plan.fine_mesh)) / float(np.prod(L))
+    """N_fine / Omega: the inverse of the finest level's grid weight, as the plan
+    reports it (Omega = |det lattice| for any cell)."""
+    return 1.0 / plan.stats()["weight"][0]
 
 
 class _Rho(torch.autograd.Function):

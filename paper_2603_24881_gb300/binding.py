@@ -30,7 +30,7 @@ EXPORTS = ["gpw_plan", "gpw_plan_query", "gpw_plan_update_coords", "gpw_plan_pai
            "gpw_eval_mat_tau_ip1_levels", "gpw_plan_destroy_async", "gpw_fock", "gpw_fock_async",
            "gpw_fock_grad", "gpw_fock_grad_async", "gpw_tile_supported",
            "gpw_plan_prepare", "gpw_plan_commit", "gpw_batch_create", "gpw_batch_set",
-           "gpw_batch_fock_grad_async", "gpw_batch_destroy",
+           "gpw_batch_fock_grad_async", "gpw_batch_generation", "gpw_batch_destroy",
            "gpw_check_device", "gpw_profile", "gpw_profile_read", "gpw_plan_destroy",
            "gpw_strerror", "gpw_last_error"]
 PHASES = ["coef", "collocate", "spectral", "integrate", "assemble", "integrate_ip1", "grad"]
@@ -81,7 +81,8 @@ class Info(ctypes.Structure):
                 ("flops_mat", ctypes.c_double), ("flops_ip1", ctypes.c_double),
                 ("tile", ctypes.c_int * 3), ("tile_integ", ctypes.c_int * 3),
                 ("nentries_integ", ctypes.c_longlong), ("colloc_warps", ctypes.c_int),
-                ("integ_chunk", ctypes.c_int), ("xc", ctypes.c_int)]
+                ("integ_chunk", ctypes.c_int), ("xc", ctypes.c_int),
+                ("volume", ctypes.c_double), ("weight", ctypes.c_double * GPW_MAX_LEVELS)]
 
 
 def lib_path() -> str:
@@ -129,6 +130,7 @@ def load(build_if_missing: bool = True):
         L.gpw_batch_set.argtypes = [vp, ci, vp, vp]
         L.gpw_batch_fock_grad_async.argtypes = [vp, vp, vp, vp, vp, vp]
         L.gpw_batch_destroy.argtypes = [vp]
+        L.gpw_batch_generation.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
         L.gpw_batch_destroy.restype = None
         L.gpw_check_device.argtypes = [vp, ctypes.POINTER(ci), vp]
         L.gpw_profile.argtypes = [vp, ci]
@@ -295,7 +297,8 @@ class Plan:
                     tile=tuple(i.tile), tile_integ=tuple(i.tile_integ),
                     nentries_integ=i.nentries_integ, colloc_warps=i.colloc_warps,
                     integ_chunk=i.integ_chunk,
-                    xc={v: k for k, v in XC.items()}.get(i.xc, i.xc))
+                    xc={v: k for k, v in XC.items()}.get(i.xc, i.xc),
+                    volume=i.volume, weight=[i.weight[k] for k in range(i.nlevels)])
 
     def task_lists(self, integ: bool = False):
         """One task list of the committed plan (gpw_plan_task_lists): the task records
@@ -572,6 +575,14 @@ class Batch:
               "gpw_batch_set")
         self.plans = list(plans)
         return self
+
+    @property
+    def generation(self) -> int:
+        """Successful set() calls so far: a CUDA graph captured from fock_grad_async is
+        valid only while this is unchanged (gpw_batch_generation)."""
+        g = ctypes.c_longlong()
+        check(self._lib.gpw_batch_generation(self._h, ctypes.byref(g)), "gpw_batch_generation")
+        return int(g.value)
 
     def fock_grad_async(self, Ds, Vs, grads, energies, stream=None):
         n = len(self.plans)

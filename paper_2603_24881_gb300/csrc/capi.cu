@@ -35,6 +35,7 @@ struct gpw_batch_s {
   long long cap_c = 0, cap_i = 0, nwc = 0, nwi = 0;
   gpw::GridLaunch colloc, integ1;
   std::vector<gpw_plan_t> plans;
+  long long generation = 0;             // successful gpw_batch_set calls
 };
 
 namespace gpw {
@@ -750,6 +751,8 @@ int gpw_plan_query(gpw_plan_t plan, gpw_plan_info* info) {
   info->colloc_warps = P.committed ? P.nw_colloc : 0;
   info->integ_chunk = P.chunk_i;
   info->xc = P.xc;
+  info->volume = P.omega;
+  for (int k = 0; k < P.nlev; ++k) info->weight[k] = P.lev[k].weight;
   return GPW_OK;
 }
 
@@ -1132,6 +1135,13 @@ int gpw_batch_set(gpw_batch_t b, int nplans, const gpw_plan_t* plans, void* stre
   b->nwc = (long long)wc.size();
   b->nwi = (long long)wi.size();
   b->plans.assign(plans, plans + nplans);
+  ++b->generation;
+  return GPW_OK;
+}
+
+int gpw_batch_generation(gpw_batch_t b, long long* generation) {
+  if (!b || !generation) return GPW_EINVAL;
+  *generation = b->generation;
   return GPW_OK;
 }
 

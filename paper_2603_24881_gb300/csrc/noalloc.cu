@@ -7,11 +7,15 @@
 // linked into a process whose CUDA context and memory budget belong to someone else.
 // Every other libgpw call needs a plan, and building a plan allocates.  This entry point
 // needs none: the caller passes the density and the two outputs, and the only working
-// memory is a fixed array in the library's own device image, reserved when the library is
-// loaded onto a GPU and held by that GPU until the process exits.
+// memory is a fixed array in the library's own device image, held by each GPU that loaded
+// it until the process exits.  With lazy module loading (CUDA's default) the image, and so
+// the array, is loaded onto a device by the first call there (its address lookup), and
+// that load may allocate inside the driver: make the first call on each device during
+// set-up.  Later calls allocate nothing.
 //
 // It is the allocation-free variant of the exchange step of gpw_fock, whose kernel keeps
 // its per-block partial energies in plan-owned scratch.
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <mutex>
@@ -36,9 +40,51 @@ static_assert((long long)kNaMaxBlocks * kNaChunk == GPW_LDA_NOALLOC_MAX_POINTS,
 // host code must use the address obtained with cudaGetSymbolAddress.
 static __device__ __align__(256) double g_lda_noalloc_partials[kNaMaxBlocks];
 
-constexpr int kNaMaxDevices = 64;
 std::mutex g_na_mutex;
-double* g_na_scratch[kNaMaxDevices] = {};
+
+// Scratch addresses by CUDA context id, filled round robin.
+constexpr int kNaCache = 64;
+unsigned long long g_na_ctx[kNaCache] = {};
+double* g_na_ptr[kNaCache] = {};
+int g_na_next = 0;
+
+double* cached_scratch(unsigned long long ctx) {
+  for (int i = 0; i < kNaCache; ++i)
+    if (g_na_ptr[i] && g_na_ctx[i] == ctx) return g_na_ptr[i];
+  return nullptr;
+}
+
+void cache_scratch(unsigned long long ctx, double* p) {
+  g_na_ctx[g_na_next] = ctx;
+  g_na_ptr[g_na_next] = p;
+  g_na_next = (g_na_next + 1) % kNaCache;
+}
+
+// Process-unique id of the current context (cuCtxGetCurrent + cuCtxGetId, reached through
+// the runtime's driver entry points: no link against the driver library).  False when no
+// context is current or the driver does not provide them.
+bool current_context_id(unsigned long long* id) {
+  using GetCurrent = CUresult (*)(CUcontext*);
+  using GetId = CUresult (*)(CUcontext, unsigned long long*);
+  static GetCurrent get_current = nullptr;
+  static GetId get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<GetCurrent>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<GetId>(f);
+  });
+  if (!get_current || !get_id) return false;
+  CUcontext c = nullptr;
+  if (get_current(&c) != CUDA_SUCCESS || !c) return false;
+  return get_id(c, id) == CUDA_SUCCESS;
+}
 
 __global__ void lda_noalloc_blocks(const double* __restrict__ rho, long long n,
                                    double* __restrict__ vx, double* __restrict__ partials) {
@@ -94,17 +140,22 @@ extern "C" int gpw_lda_x_noalloc(const double* rho, long long n, double weight, 
   }
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kNaMaxDevices) {
+  if (e != cudaSuccess) {
     gpw::set_error(std::string("gpw_lda_x_noalloc: no usable current device: ") +
                    cudaGetErrorString(e));
     return GPW_ECUDA;
   }
+  // The array's device address belongs to the current context: it is cached per context
+  // (keyed by the context's process-unique id, so a context created after a device reset
+  // is never given an address of the old one).  The first call in a context looks it up,
+  // which with lazy module loading also loads the library's device image there.
   double* scratch = nullptr;
   {
-    // first call on a device: look up the scratch array's device address (the device is
-    // current); later calls reuse it
     std::lock_guard<std::mutex> lock(g_na_mutex);
-    if (!g_na_scratch[dev]) {
+    unsigned long long ctx = 0;
+    const bool have_ctx = current_context_id(&ctx);
+    if (have_ctx) scratch = cached_scratch(ctx);
+    if (!scratch) {
       void* p = nullptr;
       e = cudaGetSymbolAddress(&p, g_lda_noalloc_partials);
       if (e != cudaSuccess || !p) {
@@ -112,13 +163,14 @@ extern "C" int gpw_lda_x_noalloc(const double* rho, long long n, double weight, 
                        cudaGetErrorString(e));
         return GPW_ECUDA;
       }
-      g_na_scratch[dev] = static_cast<double*>(p);
+      scratch = static_cast<double*>(p);
+      // the lookup has made the device's primary context current if none was
+      if (have_ctx || current_context_id(&ctx)) cache_scratch(ctx, scratch);
     }
-    scratch = g_na_scratch[dev];
   }
+  cudaStream_t s = (cudaStream_t)stream;
   // every block writes its partial before the total reads it: nothing needs clearing
   const int nblocks = (int)((n + kNaChunk - 1) / kNaChunk);
-  cudaStream_t s = (cudaStream_t)stream;
   lda_noalloc_blocks<<<nblocks, kNaThreads, 0, s>>>(rho, n, v_x, scratch);
   e = cudaGetLastError();
   if (e == cudaSuccess) {

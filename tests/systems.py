@@ -72,3 +72,60 @@ def sheared(s: System) -> System:
     out.lattice = np.ascontiguousarray(np.array([lat[0], lat[0] + lat[1], lat[2]]))
     out.name = s.name + "-sheared"
     return out
+
+
+def rotation(seed: int) -> np.ndarray:
+    """A seeded rotation, uniform on SO(3)."""
+    return workloads._rotation(np.random.default_rng(seed))
+
+
+def rotated(s: System, Q: np.ndarray) -> System:
+    """The crystal s turned by the rotation Q: lattice rows R_d -> Q R_d and atoms
+    A -> Q A (so no row stays on an axis), same meshes and fractional grid points.  The
+    Cartesian shell components are those of the new frame, so the density matrix is the
+    one of the turned frame only after cart_rotation(); D is kept as it is here."""
+    import copy
+    out = copy.copy(s)
+    Q = np.asarray(Q, dtype=np.float64)
+    out.lattice = np.ascontiguousarray(np.asarray(s.lattice, dtype=np.float64) @ Q.T)
+    out.coords = np.ascontiguousarray(np.asarray(s.coords, dtype=np.float64) @ Q.T)
+    out.name = s.name + "-rotated"
+    return out
+
+
+def cart_rotation(l: int, Q: np.ndarray) -> np.ndarray:
+    """M with old monomial mu = sum_kappa M[mu, kappa] new monomial kappa, for the
+    degree-l Cartesian monomials (x^l first) of a frame turned by Q (u_new = Q u_old,
+    so u_old_c = sum_e Q[e, c] u_new_e): expanded by polynomial multiplication."""
+    comps = [(ix, iy, l - ix - iy) for ix in range(l, -1, -1) for iy in range(l - ix, -1, -1)]
+    index = {c: i for i, c in enumerate(comps)}
+    M = np.zeros((len(comps), len(comps)))
+    for mu, m in enumerate(comps):
+        poly = {(0, 0, 0): 1.0}
+        for c in range(3):
+            for _ in range(m[c]):
+                nxt = {}
+                for e_, coef in poly.items():
+                    for e in range(3):
+                        k = list(e_)
+                        k[e] += 1
+                        k = tuple(k)
+                        nxt[k] = nxt.get(k, 0.0) + coef * Q[e, c]
+                poly = nxt
+        for k, coef in poly.items():
+            M[mu, index[k]] += coef
+    return M
+
+
+def basis_rotation(s: System, Q: np.ndarray) -> np.ndarray:
+    """Block-diagonal nao x nao matrix of cart_rotation over the shells of s:
+    phi_old = M phi_new, so D_new = M^T D M gives the same density and
+    V_old = M V_new M^T."""
+    blocks = [cart_rotation(int(l), Q) for l in s.shell_l]
+    n = sum(b.shape[0] for b in blocks)
+    M = np.zeros((n, n))
+    o = 0
+    for b in blocks:
+        M[o:o + b.shape[0], o:o + b.shape[0]] = b
+        o += b.shape[0]
+    return M

@@ -100,6 +100,26 @@ def test_batch_in_cuda_graph(gpw, alone):
     e = E.cpu().numpy()
     for i in range(len(plans)):
         _same(dict(V=Vs[i].cpu().numpy(), grad=gs[i].cpu().numpy(), EH=e[2 * i], Ex=e[2 * i + 1]), alone[i])
+    # a later set (here a smaller plan set) invalidates the graph: the generation tells,
+    # and a graph captured again runs the new set
+    gen = b.generation
+    assert gen == 1
+    b.set(plans[1:])
+    assert b.generation == gen + 1
+    g2 = torch.cuda.CUDAGraph()
+    E2 = torch.empty(2 * (len(plans) - 1), dtype=torch.float64, device="cuda")
+    with torch.cuda.graph(g2, stream=s):
+        b.fock_grad_async(Ds[1:], Vs[1:], gs[1:], E2, stream=s)
+    for V in Vs:
+        V.zero_()
+    g2.replay()
+    torch.cuda.synchronize()
+    e = E2.cpu().numpy()
+    for j, i in enumerate(range(1, len(plans))):
+        _same(dict(V=Vs[i].cpu().numpy(), grad=gs[i].cpu().numpy(), EH=e[2 * j], Ex=e[2 * j + 1]), alone[i])
+    assert float(Vs[0].abs().max()) == 0.0
+    del g, g2
+    b.close()
     for p in plans:
         p.close()
 

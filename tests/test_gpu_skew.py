@@ -36,6 +36,9 @@ CASES = {
     # third row orthogonal to the first two: the kernels' R01-only path
     "hexagonal": lambda: systems.skewed(seed=9, shells=((0, 1), (1, 1), (2, 1), (3, 1)), natm=2,
                                         lattice=6.0 * workloads.HEXAGONAL),
+    # a triclinic cell turned by a seeded rotation: no lattice row on an axis
+    "rotated": lambda: systems.rotated(systems.skewed(seed=6, shells=((0, 1), (1, 1), (2, 1), (3, 1)),
+                                                      natm=2), systems.rotation(12)),
 }
 
 

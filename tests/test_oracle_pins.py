@@ -631,3 +631,46 @@ def test_skew_tau_closed_forms(res_skew):
     V = p.mat_tau_levels([waves.sample(m) for m in p.meshes])
     ref = 0.5 * cf.lattice_grad_pw_matrix(s, waves, reach=20.0)
     assert np.max(np.abs(V - ref)) <= 1e-9 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("base", ["triclinic", "cubic"])
+def test_rotated_cell_is_the_same_crystal(base):
+    # A crystal turned by a seeded rotation Q (lattice rows and atoms), so that no row of
+    # the lattice is triangular: with the same fractional meshes every level density on
+    # the grid, E_H and E_x are those of the unturned crystal once D is expressed in the
+    # turned Cartesian components (D' = M^T D M), V transforms back as V = M V' M^T and
+    # the gradient turns with the atoms (g' = g Q^T).  The cubic cell goes through the
+    # separable orthorhombic evaluation and its rotation through the point-by-point one.
+    if base == "triclinic":
+        s = systems.skewed(seed=6, shells=((0, 1), (1, 1), (2, 1), (3, 1)), natm=2)
+    else:
+        s = systems.resolved(seed=6, shells=((0, 1), (1, 1), (2, 1), (3, 1)), natm=2)
+    Q = systems.rotation(12)
+    r = systems.rotated(s, Q)
+    assert np.all(np.abs(r.lattice[np.triu_indices(3, 1)]) > 1e-3)
+    M = systems.basis_rotation(s, Q)
+    p, q = oracle.Plan(s), oracle.Plan(r)
+    assert np.array_equal(p.meshes, q.meshes)
+    Dr = M.T @ s.D @ M
+    a, b = p.fock(s.D), q.fock(Dr)
+    for x, y in zip(a["rho_levels"], b["rho_levels"]):
+        assert np.max(np.abs(x - y)) <= 1e-10 * np.max(np.abs(x))
+    assert b["EH"] == pytest.approx(a["EH"], rel=1e-10)
+    assert b["Ex"] == pytest.approx(a["Ex"], rel=1e-10)
+    assert np.max(np.abs(M @ b["V"] @ M.T - a["V"])) <= 1e-10 * np.max(np.abs(a["V"]))
+    ga = p.grad_levels(s.D, a["v_levels"])
+    gb = q.grad_levels(Dr, b["v_levels"])
+    assert np.max(np.abs(gb - ga @ Q.T)) <= 1e-9 * max(1.0, np.max(np.abs(ga)))
+
+
+def test_collocation_is_reproducible_bit_for_bit():
+    # the oracle sums per-thread grids over a fixed pair-to-thread map
+    s = workloads.tiny()
+    p = oracle.Plan(s)
+    for nt in (1, 3):
+        a = p.rho_levels(s.D, nthreads=nt)
+        b = p.rho_levels(s.D, nthreads=nt)
+        assert all(np.array_equal(x, y) for x, y in zip(a, b))
+    t = p.tau_levels(s.D, nthreads=3)
+    u = p.tau_levels(s.D, nthreads=3)
+    assert all(np.array_equal(x, y) for x, y in zip(t, u))
