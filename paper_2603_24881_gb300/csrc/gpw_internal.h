@@ -17,8 +17,10 @@ namespace gpw {
 constexpr int kShellLmax = 3;                   // Cartesian shells up to f
 constexpr int kLmax = 2 * kShellLmax;           // la + lb
 constexpr int kLextMax = kLmax + 1;             // one more for the centre derivatives
-constexpr int kNc3Max = (kLextMax + 1) * (kLextMax + 2) * (kLextMax + 3) / 6;  // 120
-constexpr int kNc2Max = (kLextMax + 1) * (kLextMax + 2) / 2;                   // 36
+// highest degree of any pair tensor: the kinetic-energy-density gradient (L + 3)
+constexpr int kDegMax = kLmax + 3;
+constexpr int kNc3Max = (kDegMax + 1) * (kDegMax + 2) * (kDegMax + 3) / 6;  // 220
+constexpr int kNc2Max = (kDegMax + 1) * (kDegMax + 2) / 2;                   // 55
 
 // Default sub-box (tile) owned by one thread block: T0 x T1 x T2 grid points, the last
 // along the fastest grid index.  The shape is a plan parameter (see kTileShapes).
@@ -36,7 +38,7 @@ constexpr long long kBand = 2048;
 // (r - A)_c = sum_d (R_d)_c / N_d xi_d; per level and degree n a block of
 // nh(n) x nh(n) coefficients (row: Cartesian monomial, column: lattice monomial, both
 // numbered l2 outer, l1 inner), blocks at mono_off(n), levels kMonoStride apart.
-constexpr int kSkewDeg = 7;
+constexpr int kSkewDeg = kDegMax;
 __host__ __device__ constexpr int nh(int n) { return (n + 1) * (n + 2) / 2; }
 __host__ __device__ constexpr int mono_off(int n) {
   return n == 0 ? 0 : mono_off(n - 1) + nh(n - 1) * nh(n - 1);
@@ -51,13 +53,13 @@ __host__ __device__ constexpr int nc2(int L) { return (L + 1) * (L + 2) / 2; }
 // Flat order of the pair coefficient tensors D[l0,l1,l2] / V[l0,l1,l2] of total degree
 // <= L (Eqs. rho1 and the V tensor of Sec. III A):
 //   for l2 in 0..L, for l1 in 0..L-l2 (the (l2,l1) index c21), for l0 in 0..L-l2-l1.
-// Decode tables for every L <= kLextMax live in one small device array:
+// Decode tables for every L <= kDegMax live in one small device array:
 //   dec21[L][c21] = l2 | l1 << 8 | base3 << 16   (base3 = flat index of (0,l1,l2))
 //   dec3[L][c]    = c21 | l0 << 8
 struct CoefTables {
-  int dec21[kLextMax + 1][kNc2Max];
-  int dec3[kLextMax + 1][kNc3Max];
-  int c21base[kLextMax + 1][kLextMax + 1];  // c21 of (l2, 0)
+  int dec21[kDegMax + 1][kNc2Max];
+  int dec3[kDegMax + 1][kNc3Max];
+  int c21base[kDegMax + 1][kDegMax + 1];  // c21 of (l2, 0)
 };
 void build_coef_tables(CoefTables* t);
 

@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdint>
 
 #include "gpw_internal.h"
@@ -24,9 +25,11 @@ namespace gpw {
 
 namespace {
 
-constexpr int kTabInts = (kLextMax + 1) * (kNc2Max + kNc3Max + kLextMax + 1);
-static_assert(kTabInts % 4 == 0, "table block must keep 16-byte alignment");
-static_assert(sizeof(CoefTables) == kTabInts * sizeof(int), "CoefTables layout");
+// The integration kernel keeps the dec21 block of the decode tables (the first member of
+// CoefTables) in shared memory, padded to a whole number of int4.
+constexpr int kDec21Ints = (((kDegMax + 1) * kNc2Max) + 3) & ~3;
+static_assert(offsetof(CoefTables, dec21) == 0, "dec21 leads CoefTables");
+static_assert(sizeof(CoefTables) >= kDec21Ints * sizeof(int), "CoefTables layout");
 
 __device__ __forceinline__ int fdiv(int x, float inv) {
   // exact floor(x / m) for 0 <= x < 4096, m <= 512, inv = 1/m rounded to fp32
@@ -48,10 +51,12 @@ __device__ __forceinline__ void cart_comp(int l, int idx, int* c) {
   c[0] = c[1] = c[2] = 0;
 }
 
-__constant__ double c_binom[5][5] = {{1, 0, 0, 0, 0}, {1, 1, 0, 0, 0}, {1, 2, 1, 0, 0},
-                                     {1, 3, 3, 1, 0}, {1, 4, 6, 4, 1}};
+__constant__ double c_binom[6][6] = {{1, 0, 0, 0, 0, 0}, {1, 1, 0, 0, 0, 0},
+                                     {1, 2, 1, 0, 0, 0}, {1, 3, 3, 1, 0, 0},
+                                     {1, 4, 6, 4, 1, 0}, {1, 5, 10, 10, 5, 1}};
 
-__device__ __forceinline__ double binom(int n, int k) { return c_binom[n][k]; }  // n <= 4
+// n <= 5: an f exponent plus two (the second centre derivative of an f function)
+__device__ __forceinline__ double binom(int n, int k) { return c_binom[n][k]; }
 
 __device__ __forceinline__ void set_err(int* err, int code) { atomicCAS(err, 0, code); }
 
@@ -64,10 +69,10 @@ __device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-__device__ __forceinline__ void load_tables(int* dst, const CoefTables* src, int tid, int nthr) {
+__device__ __forceinline__ void load_dec21(int* dst, const CoefTables* src, int tid, int nthr) {
   const int4* s4 = reinterpret_cast<const int4*>(src);
   int4* d4 = reinterpret_cast<int4*>(dst);
-  for (int i = tid; i < kTabInts / 4; i += nthr) d4[i] = s4[i];
+  for (int i = tid; i < kDec21Ints / 4; i += nthr) d4[i] = s4[i];
 }
 
 // ----------------------------------------------------------------------------------
@@ -514,10 +519,8 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
   using Lay = CollocLayout<T0, T1, T2>;
   constexpr int kTileN = T0 * T1 * T2;
   extern __shared__ __align__(16) double sm[];
-  int* s_tab = reinterpret_cast<int*>(sm);
-  double* acc_all = sm + kTabInts / 2;
+  double* acc_all = sm;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  load_tables(s_tab, tabs, tid, NW * 32);
   for (int i = tid; i < NW * kTileN; i += NW * 32) acc_all[i] = 0.0;
 
   const int4 item = work[blockIdx.x];
@@ -629,7 +632,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     break;
       switch (L) {
         GPW_COLLOC_L(0) GPW_COLLOC_L(1) GPW_COLLOC_L(2) GPW_COLLOC_L(3) GPW_COLLOC_L(4)
-        GPW_COLLOC_L(5) GPW_COLLOC_L(6)
+        GPW_COLLOC_L(5) GPW_COLLOC_L(6) GPW_COLLOC_L(7) GPW_COLLOC_L(8)
         default:
           if (lane == 0) set_err(err, 1);
       }
@@ -694,9 +697,9 @@ __global__ void __launch_bounds__(NW * 32)
   extern __shared__ __align__(16) double sm[];
   int* s_tab = reinterpret_cast<int*>(sm);
   const int(*s_dec21)[kNc2Max] = reinterpret_cast<const int(*)[kNc2Max]>(s_tab);
-  double* sv = sm + kTabInts / 2;
+  double* sv = sm + kDec21Ints / 2;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  load_tables(s_tab, tabs, tid, NW * 32);
+  load_dec21(s_tab, tabs, tid, NW * 32);
 
   const int4 item = work[blockIdx.x];
   const PlanView& pv = views[item.x];
@@ -883,6 +886,9 @@ __device__ __forceinline__ double sum_strided(const double* __restrict__ b, long
 constexpr int kRedCap = 512;
 constexpr int kRedX = 64;
 constexpr int kRedPW = 4;  // warps per block (static shared memory stays under 48 KB)
+// NK: V entries per lane in steps of 32 (nc3(Lx) <= 32 NK); 4 up to degree kLextMax, 8 for
+// the kinetic-energy-density tensors (degree up to kDegMax, 220 entries)
+template <int NK>
 __global__ void __launch_bounds__(kRedPW * 32, 6)
     reduce_parts_kernel(long long np, const KLevels K, int T0, const int4* __restrict__ hot_a,
                         const int4* __restrict__ hot_b, const int4* __restrict__ ids2,
@@ -891,8 +897,10 @@ __global__ void __launch_bounds__(kRedPW * 32, 6)
                         const long long* __restrict__ tab_off, const double* __restrict__ tab,
                         const double* __restrict__ part, const CoefTables* __restrict__ tabs,
                         double* __restrict__ coef, int lext, int xr) {
+  constexpr int kRows = NK == 4 ? kLextMax + 1 : kDegMax + 1;
+  static_assert(nc3(kRows - 1) <= 32 * NK, "entries per lane");
   __shared__ double s_w[kRedPW][kRedCap];
-  __shared__ double s_g[kRedPW][(kLextMax + 1) * kRedX];
+  __shared__ double s_g[kRedPW][kRows * kRedX];
   __shared__ int s_seg[kRedPW][kRedX];
   const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -916,10 +924,11 @@ __global__ void __launch_bounds__(kRedPW * 32, 6)
     int C = 32;
     while (C >= 2 * nc && C > 1) C >>= 1;
     const int G = 32 / C, g = lane / C, cidx = lane - g * C;
-    double v[4] = {0.0, 0.0, 0.0, 0.0};
-    int cc[4], cl[4];
+    double v[NK];
+    int cc[NK], cl[NK];
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
+    for (int k = 0; k < NK; ++k) {
+      v[k] = 0.0;
       const int c = cidx + 32 * k;
       const int dc = c < nc ? __ldg(&tabs->dec3[Lx][c]) : 0;
       cc[k] = dc & 255;
@@ -972,7 +981,7 @@ __global__ void __launch_bounds__(kRedPW * 32, 6)
       }
       __syncwarp();
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < NK; ++k) {
         if (cidx + 32 * k < nc) {
           const double* wr = sW + cc[k] * E;
           const double* gr = sG + cl[k] * E;
@@ -987,7 +996,7 @@ __global__ void __launch_bounds__(kRedPW * 32, 6)
     double* dst = coef + coef_off[p];
     if (g == 0) {
 #pragma unroll
-      for (int k = 0; k < 4; ++k)
+      for (int k = 0; k < NK; ++k)
         if (cidx + 32 * k < nc) dst[cidx + 32 * k] = wgt * v[k];
     }
   }
@@ -1042,7 +1051,7 @@ __global__ void mono_transform_kernel(long long np, const int4* __restrict__ hot
 // together with their transpose.
 __device__ double contract_elem(const int* ca, const int* cb, const double pw[3][4],
                                 const double* V, int L, const int (*dec21)[kNc2Max],
-                                const int (*c21b)[kLextMax + 1]) {
+                                const int (*c21b)[kDegMax + 1]) {
   double s = 0.0;
   for (int t2 = 0; t2 <= cb[2]; ++t2) {
     const double c2 = binom(cb[2], t2) * pw[2][cb[2] - t2];
@@ -1115,8 +1124,8 @@ __device__ __forceinline__ int mono_index(int k0, int k1, int k2, int M) {
 
 // Integral of one shifted pair product (x - A)^a' (x - B)^b' from the pair's V tensor of
 // degree Lx: (x - B)^b' expanded about A (Eq. binomial), pw[d][j] = (A_d - B_d)^j;
-// zero if an exponent is negative (b'_d <= 4).
-__device__ double xelem(int a0, int a1, int a2, int b0, int b1, int b2, const double (*pw)[5],
+// zero if an exponent is negative (b'_d <= 5).
+__device__ double xelem(int a0, int a1, int a2, int b0, int b1, int b2, const double (*pw)[6],
                         const double* V, int Lx) {
   if (a0 < 0 || a1 < 0 || a2 < 0 || b0 < 0 || b1 < 0 || b2 < 0) return 0.0;
   double s = 0.0;
@@ -1448,16 +1457,15 @@ __global__ void pair_coef_tau_kernel(long long np, const int4* __restrict__ ids,
   const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
   const double* g = geo + 8 * p;
   const double aa = g[6], ab = g[7];
-  double pw[3][4];
+  double pw[3][5];  // (A_d - B_d)^j, j <= lb + 1
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const double t = g[d] - g[3 + d];
     pw[d][0] = 1.0;
-    pw[d][1] = t;
-    pw[d][2] = t * t;
-    pw[d][3] = t * t * t;
+#pragma unroll
+    for (int k = 1; k < 5; ++k) pw[d][k] = pw[d][k - 1] * t;
   }
-  double acc[nc3(kLmax)];
+  double acc[nc3(kLmax + 2)];
   const int nc = nc3(Lt);
   for (int c = 0; c < nc; ++c) acc[c] = 0.0;
   const double scale = 0.5 * (double)ids2[p].z * pref[p];
@@ -1495,7 +1503,7 @@ __global__ void pair_coef_tau_kernel(long long np, const int4* __restrict__ ids,
 
 // (1/2) grad phi_a . grad phi_b integrated against the potential, from the pair's V
 // tensor of degree Lx (xelem: the binomial contraction of one shifted pair product).
-__device__ double xtau(const int* a, const int* b, double aa, double ab, const double (*pw)[5],
+__device__ double xtau(const int* a, const int* b, double aa, double ab, const double (*pw)[6],
                        const double* V, int Lx) {
   double s = 0.0;
   for (int d = 0; d < 3; ++d)
@@ -1537,13 +1545,13 @@ __global__ void assemble_V_tau_kernel(long long ngroups, const int4* __restrict_
     double tot = 0.0;
     for (int p = gr.z; p < gr.w; ++p) {
       const double* g = geo + 8LL * p;
-      double pw[3][5];
+      double pw[3][6];
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const double t = g[d] - g[3 + d];
         pw[d][0] = 1.0;
 #pragma unroll
-        for (int k = 1; k < 5; ++k) pw[d][k] = pw[d][k - 1] * t;
+        for (int k = 1; k < 6; ++k) pw[d][k] = pw[d][k - 1] * t;
       }
       const double* Vp = coef + coef_off[p];
       double x = xtau(ca, cb, g[6], g[7], pw, Vp, Lx);
@@ -1605,13 +1613,13 @@ __global__ void grad_tau_pair_kernel(long long np, const int4* __restrict__ ids,
   const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
   const double* g = geo + 8 * p;
   const double aa = g[6], ab = g[7];
-  double pw[3][5];
+  double pw[3][6];  // (A_d - B_d)^j, j <= lb + 2
 #pragma unroll
   for (int d = 0; d < 3; ++d) {
     const double t = g[d] - g[3 + d];
     pw[d][0] = 1.0;
 #pragma unroll
-    for (int k = 1; k < 5; ++k) pw[d][k] = pw[d][k - 1] * t;
+    for (int k = 1; k < 6; ++k) pw[d][k] = pw[d][k - 1] * t;
   }
   const double* Vp = coef + coef_off[p];
   const double scale = -0.5 * (double)ids2[p].z * pref[p];
@@ -1788,12 +1796,12 @@ int integ_skew_extra(bool zc) {
 
 template <int T0, int T1, int T2>
 size_t colloc_smem(int stg, int nw) {
-  return sizeof(int) * kTabInts + sizeof(double) * (size_t)nw * (T0 * T1 * T2 + stg);
+  return sizeof(double) * (size_t)nw * (T0 * T1 * T2 + stg);
 }
 
 template <int T0, int T1, int T2>
 size_t integ_smem(int stg) {
-  return sizeof(int) * kTabInts + sizeof(double) * ((size_t)IntegLayout<T0, T1, T2>::kSV + (size_t)kNW * stg);
+  return sizeof(int) * kDec21Ints + sizeof(double) * ((size_t)IntegLayout<T0, T1, T2>::kSV + (size_t)kNW * stg);
 }
 
 // Warps per collocation block: the candidate with the most resident warps per SM, as the
@@ -2026,9 +2034,9 @@ cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views,
         views, work, tabs, cfg.lp, cfg.stg, cfg.ldeg);                                     \
     return cudaGetLastError();                                                             \
   }
-#define GPW_TILE_COLLOC(a, b, c) GPW_COLLOC_NW(a, b, c, 8) GPW_COLLOC_NW(a, b, c, 6) GPW_COLLOC_NW(a, b, c, 4)
-  GPW_COLLOC_SHAPES(GPW_TILE_COLLOC)
-#undef GPW_TILE_COLLOC
+#define GPW_LAUNCH_COLLOC(a, b, c) GPW_COLLOC_NW(a, b, c, 8) GPW_COLLOC_NW(a, b, c, 6) GPW_COLLOC_NW(a, b, c, 4)
+  GPW_COLLOC_SHAPES(GPW_LAUNCH_COLLOC)
+#undef GPW_LAUNCH_COLLOC
 #undef GPW_COLLOC_NW
   return cudaErrorInvalidValue;
 }
@@ -2048,14 +2056,14 @@ cudaError_t launch_integrate_views(const GridLaunch& cfg, int lext, const PlanVi
           views, work, tabs, lext, cfg.lp, cfg.stg);
     return cudaGetLastError();
   }
-#define GPW_TILE_INTEG(a, b, c)                                                            \
+#define GPW_LAUNCH_INTEG(a, b, c)                                                            \
   if (t0 == a && t1 == b && t2 == c) {                                                     \
     integrate_kernel<a, b, c, kNW><<<(int)nwork, kNW * 32, cfg.smem, s>>>(                 \
         views, work, tabs, lext, cfg.lp, cfg.stg);                                         \
     return cudaGetLastError();                                                             \
   }
-  GPW_INTEG_SHAPES(GPW_TILE_INTEG)
-#undef GPW_TILE_INTEG
+  GPW_INTEG_SHAPES(GPW_LAUNCH_INTEG)
+#undef GPW_LAUNCH_INTEG
   return cudaErrorInvalidValue;
 }
 
@@ -2175,9 +2183,14 @@ cudaError_t launch_reduce_parts(const Plan& p, int lext, cudaStream_t s) {
   if (p.npairs == 0) return cudaSuccess;
   long long blocks = std::min<long long>((p.npairs + kRedPW - 1) / kRedPW, 152LL * 128);
   ++p.launches;
-  reduce_parts_kernel<<<(int)blocks, kRedPW * 32, 0, s>>>(
-      p.npairs, make_klevels(p, true), p.tile_i[0], p.d.hot_a, p.d.hot_b, p.d.ids2, p.d.part_off,
-      p.d.coef_off, p.d.tab_off, p.d.tab, p.d.part, p.d.tabs, p.d.coef, lext, p.xr);
+  if (p.lmax + lext <= kLextMax)
+    reduce_parts_kernel<4><<<(int)blocks, kRedPW * 32, 0, s>>>(
+        p.npairs, make_klevels(p, true), p.tile_i[0], p.d.hot_a, p.d.hot_b, p.d.ids2, p.d.part_off,
+        p.d.coef_off, p.d.tab_off, p.d.tab, p.d.part, p.d.tabs, p.d.coef, lext, p.xr);
+  else
+    reduce_parts_kernel<8><<<(int)blocks, kRedPW * 32, 0, s>>>(
+        p.npairs, make_klevels(p, true), p.tile_i[0], p.d.hot_a, p.d.hot_b, p.d.ids2, p.d.part_off,
+        p.d.coef_off, p.d.tab_off, p.d.tab, p.d.part, p.d.tabs, p.d.coef, lext, p.xr);
   if (p.skew) {
     ++p.launches;
     mono_transform_kernel<<<(int)((p.npairs + 127) / 128), 128, 0, s>>>(

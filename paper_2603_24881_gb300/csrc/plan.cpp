@@ -126,6 +126,24 @@ bool pair_box(double cab, double kab, int la, int lb, double dA, double dB, doub
     for (int it = 0; it < 200 && pair_h(cab, kab, la, lb, dA, dB, ap, hi) >= tau; ++it) hi *= 2.0;
     lo = r0;
   } else {
+    // Most pairs that reach here peak far below tau: a closed-form upper bound of h
+    // rejects them before the bisection.  With D = max(dA, dB) and L = la + lb,
+    // (r+dA)^la (r+dB)^lb <= (r+D)^L <= 2^(L-1) (r^L + D^L) (L >= 1), and
+    // max r^k exp(-ap r^2) = (k / (2 e ap))^(k/2), so
+    //   h <= C 2^(L-1) [((L+2) / (2 e ap))^((L+2)/2) + D^L / (e ap)]   (C / (e ap) for L = 0).
+    // The margin keeps the decision that of the bisection despite rounding.
+    const int L = la + lb;
+    const double D = dA > dB ? dA : dB;
+    const double eap = M_E * ap;
+    double bound;
+    if (L == 0) {
+      bound = cab * kab / eap;
+    } else {
+      const double k = (double)(L + 2);
+      bound = cab * kab * ipow(2.0, L - 1) *
+              (std::pow(k / (2.0 * eap), 0.5 * k) + ipow(D, L) / eap);
+    }
+    if (bound < tau * (1.0 - 1e-12)) return false;
     double a = 0.0, b = r0;
     for (int it = 0; it < 64; ++it) {
       double mid = 0.5 * (a + b);
@@ -681,12 +699,6 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     return GPW_EINVAL;
   }
   plan->xr = (desc->flags & GPW_TAU) ? 2 : 0;
-  if (plan->xr && desc->shell_l)
-    for (int sh = 0; sh < desc->nshell; ++sh)
-      if (desc->shell_l[sh] > 2) {
-        set_error("gpw_plan: the kinetic-energy-density kernels (GPW_TAU) support shells up to d");
-        return GPW_EINVAL;
-      }
   if (plan->skew) {
     // the non-orthogonal kernels use 4x8x16 sub-boxes for both passes
     const bool tc = desc->tile[0] || desc->tile[1] || desc->tile[2];
@@ -1165,7 +1177,7 @@ void recycle_host_arrays(HostArrays* H) {
 
 void build_coef_tables(CoefTables* t) {
   std::memset(t, 0, sizeof(*t));
-  for (int L = 0; L <= kLextMax; ++L) {
+  for (int L = 0; L <= kDegMax; ++L) {
     int c21 = 0, flat = 0;
     for (int l2 = 0; l2 <= L; ++l2) {
       t->c21base[L][l2] = c21;

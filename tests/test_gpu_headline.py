@@ -9,9 +9,10 @@ launch configuration.
   with the oracle's own level potentials, to 1e-7 Ha/Bohr.
 * Central finite differences of the GPU energy on the same atoms, all three directions
   (h = 1e-4 Bohr, pair set and boxes frozen through gpw_plan_update_coords), against the
-  GPU gradient.  The difference quotient carries a truncation error h^2 E'''/6; the
-  Richardson combination of h and h/2 removes it to O(h^4) and is held to 1e-7 Ha/Bohr,
-  the plain quotient at h to 1e-6.
+  GPU gradient to 1e-7 Ha/Bohr.  At h = 1e-4 the quotient's truncation error h^2 E'''/6
+  and its rounding error (the ~3e4 Ha energy is summed over 2.4e7 points, a few 1e-12
+  Ha, divided by 2h) both stay near 1e-8; a smaller h would trade the first for more of
+  the second.
 """
 import numpy as np
 import pytest
@@ -87,11 +88,8 @@ def test_gradient_against_finite_differences(water256):
         for at in _atoms(s):
             for d in range(3):
                 fd = quotient(at, d, h)
-                fd2 = quotient(at, d, h / 2)
-                rich = (4.0 * fd2 - fd) / 3.0
                 g = float(res["grad"][at, d])
-                assert abs(fd - g) <= 1e-6, (at, d, fd, g)
-                assert abs(rich - g) <= 1e-7, (at, d, rich, fd, g)
+                assert abs(fd - g) <= 1e-7, (at, d, fd, g)
     finally:
         gp.update_coords(s.coords)
     assert gp.check_device() == 0

@@ -24,14 +24,23 @@ def gpw():
     return g
 
 
-@pytest.fixture(scope="module", params=["tiny", "resolved_d", "triclinic_d"])
+SPDF = ((0, 1), (1, 1), (2, 1), (3, 1))
+
+
+@pytest.fixture(scope="module", params=["tiny", "resolved_d", "triclinic_d", "resolved_f",
+                                        "triclinic_f", "rotated_f"])
 def case(request):
     s = {"tiny": workloads.tiny,
          "resolved_d": lambda: systems.resolved(seed=6, shells=((0, 1), (1, 1), (2, 1)),
                                                 cutoff=100.0),
          # a non-orthogonal cell: the cross-factor kernels at degree L+2 / L+3
          "triclinic_d": lambda: systems.skewed(seed=6, shells=((0, 1), (1, 1), (2, 1)),
-                                               cutoff=100.0)}[request.param]()
+                                               cutoff=100.0),
+         # f shells: (f|f) pairs reach degree 8 (tau) and 9 (its gradient)
+         "resolved_f": lambda: systems.resolved(seed=6, shells=SPDF, cutoff=100.0),
+         "triclinic_f": lambda: systems.skewed(seed=7, shells=SPDF, cutoff=100.0),
+         "rotated_f": lambda: systems.rotated(systems.skewed(seed=8, shells=SPDF, cutoff=100.0),
+                                              systems.rotation(13))}[request.param]()
     return request.param, s, oracle.Plan(s)
 
 
@@ -86,10 +95,7 @@ def test_tau_plan_keeps_the_density_path(gpw, case):
     assert float((a["grad"] - b["grad"]).abs().max()) <= 1e-12
 
 
-def test_tau_needs_the_flag_and_d_shells(gpw):
+def test_tau_needs_the_flag(gpw):
     s = workloads.tiny()
     with pytest.raises(gpw.GpwError):
         gpw.Plan(s).eval_tau(s.D)
-    f = systems.resolved(seed=8, shells=((0, 1), (3, 1)), natm=2)
-    with pytest.raises(gpw.GpwError):
-        gpw.Plan(f, tau=True)

@@ -437,8 +437,8 @@ def test_energy_gradient_matches_finite_differences_gga(res):
 
 @pytest.fixture(scope="module")
 def res_tau():
-    # shells up to d (the kinetic-energy-density kernels' range), resolved exponents
-    s = systems.resolved(seed=6, shells=((0, 1), (1, 1), (2, 1)), cutoff=100.0)
+    # shells up to f (the kinetic-energy-density kernels' range), resolved exponents
+    s = systems.resolved(seed=6, shells=((0, 1), (1, 1), (2, 1), (3, 1)), cutoff=100.0)
     return s, oracle.Plan(s)
 
 
