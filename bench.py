@@ -273,6 +273,11 @@ def served_bench(nreq: int) -> dict:
         pois = [f.result() for f in futs]
         t_pois = max(r.t_done for r in pois) - t0
     lat = np.array([r.latency for r in pois])
+    nwat = np.array([int(sy.natm) // 3 for sy in systems])
+    by_size = {int(n): {"requests": int(np.sum(nwat == n)),
+                        "p50_ms": 1e3 * float(np.percentile(lat[nwat == n], 50)),
+                        "p99_ms": 1e3 * float(np.percentile(lat[nwat == n], 99))}
+               for n in sorted(set(nwat.tolist()))}
     plan_ms = np.array([r.t_prepared - r.t_submit for r in pois]) * 1e3
     wait_ms = np.array([r.t_launch - r.t_prepared for r in pois]) * 1e3
     run_ms = np.array([r.t_done - r.t_launch for r in pois]) * 1e3
@@ -296,6 +301,7 @@ def served_bench(nreq: int) -> dict:
             "poisson_p99_ms_split": {"host_plan": float(np.percentile(plan_ms, 99)),
                                      "admission_wait": float(np.percentile(wait_ms, 99)),
                                      "gpu_batch_and_copy": float(np.percentile(run_ms, 99))},
+            "poisson_latency_by_waters": by_size,
             "max_abs_dE_Ha": dE, "max_rel_dV": dV, "max_abs_dgrad": dg,
             "stream": "water boxes n in {4,8,16,32,64,128}, p ~ 1/n, 10% gradients, seed 4"}
 

@@ -53,7 +53,7 @@ extern "C" {
 #define GPW_ENOMEM -2     /* device or host allocation failed */
 #define GPW_ECUDA -3      /* CUDA runtime error */
 #define GPW_ECUFFT -4     /* cuFFT error */
-#define GPW_ETIMEDOUT -5  /* a bounded wait gave up */
+#define GPW_ETIMEDOUT -5  /* a bounded wait gave up (gpw_stream_wait) */
 #define GPW_EDEVICE -6    /* a kernel's bounds check set the device error word */
 #define GPW_ERANGE -7     /* a size is beyond a fixed limit of the library */
 
@@ -240,7 +240,8 @@ int gpw_eval_mat_ip1_levels(gpw_plan_t plan, const double* D, const double* cons
  * collocated on the pairs' levels like rho and Fourier-interpolated to the finest grid,
  * its Fock term V_mu,nu = (1/2) sum_k sum_pairs (Omega/N_k) sum_r v_k grad phi_mu . grad phi_nu
  * and the nuclear gradient of <v, tau(D)> at fixed v.  Need a plan built with GPW_TAU
- * (shells up to d); GPW_EINVAL otherwise.  Arguments as for the rho / V / gradient calls
+ * (shells up to f: the pair tensors reach degree L + 2 = 8 and, for the gradient,
+ * L + 3 = 9); GPW_EINVAL otherwise.  Arguments as for the rho / V / gradient calls
  * above (device pointers; outputs overwritten). */
 int gpw_eval_tau(gpw_plan_t plan, const double* D, double* tau_fine, void* stream);
 int gpw_eval_tau_levels(gpw_plan_t plan, const double* D, double* const* tau_levels,
@@ -356,6 +357,13 @@ int gpw_profile_read(gpw_plan_t plan, double* ms, long long* count, int nphases,
  * Asynchronous on `stream`. */
 int gpw_lda_x_noalloc(const double* rho, long long n, double weight, double* v_x, double* e_x,
                       void* stream);
+
+/* Bounded host wait: returns GPW_OK once every piece of work enqueued on `stream` so far
+ * has finished, or GPW_ETIMEDOUT when that has not happened within timeout_s seconds
+ * (>= 0; the work is not cancelled and keeps running).  Polls cudaStreamQuery with short
+ * sleeps, so the calling thread does not spin a core.  GPW_ECUDA if the stream reports
+ * an error.  Not a paper operation: a server uses it to put a deadline on a batch. */
+int gpw_stream_wait(void* stream, double timeout_s);
 
 /* Release the plan and everything it owns.  NULL is ignored. */
 void gpw_plan_destroy(gpw_plan_t plan);

@@ -32,7 +32,7 @@ EXPORTS = ["gpw_plan", "gpw_plan_query", "gpw_plan_update_coords", "gpw_plan_pai
            "gpw_plan_prepare", "gpw_plan_commit", "gpw_batch_create", "gpw_batch_set",
            "gpw_batch_fock_grad_async", "gpw_batch_generation", "gpw_batch_destroy",
            "gpw_check_device", "gpw_profile", "gpw_profile_read", "gpw_plan_destroy",
-           "gpw_strerror", "gpw_last_error"]
+           "gpw_stream_wait", "gpw_strerror", "gpw_last_error"]
 PHASES = ["coef", "collocate", "spectral", "integrate", "assemble", "integrate_ip1", "grad"]
 
 
@@ -131,6 +131,7 @@ def load(build_if_missing: bool = True):
         L.gpw_batch_fock_grad_async.argtypes = [vp, vp, vp, vp, vp, vp]
         L.gpw_batch_destroy.argtypes = [vp]
         L.gpw_batch_generation.argtypes = [vp, ctypes.POINTER(ctypes.c_longlong)]
+        L.gpw_stream_wait.argtypes = [vp, cd]
         L.gpw_batch_destroy.restype = None
         L.gpw_check_device.argtypes = [vp, ctypes.POINTER(ci), vp]
         L.gpw_profile.argtypes = [vp, ci]
@@ -166,6 +167,16 @@ def _stream(stream=None) -> int:
     if stream is None:
         stream = torch.cuda.current_stream()
     return int(stream.cuda_stream)
+
+
+def stream_wait(stream, timeout_s: float) -> bool:
+    """Bounded host wait on a CUDA stream (gpw_stream_wait): True once its work so far has
+    finished, False when timeout_s passed first (the work keeps running)."""
+    rc = load().gpw_stream_wait(ctypes.c_void_p(_stream(stream)), float(timeout_s))
+    if rc == -5:
+        return False
+    check(rc, "gpw_stream_wait")
+    return True
 
 
 def _dev_f64(x, shape=None):

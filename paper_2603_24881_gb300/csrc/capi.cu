@@ -11,6 +11,8 @@
 #include <cufft.h>
 
 #include <algorithm>
+#include <chrono>
+#include <thread>
 #include <cstring>
 #include <memory>
 #include <new>
@@ -1137,6 +1139,32 @@ int gpw_batch_set(gpw_batch_t b, int nplans, const gpw_plan_t* plans, void* stre
   b->plans.assign(plans, plans + nplans);
   ++b->generation;
   return GPW_OK;
+}
+
+int gpw_stream_wait(void* stream, double timeout_s) {
+  if (!(timeout_s >= 0.0)) {
+    set_error("gpw_stream_wait: timeout must be >= 0");
+    return GPW_EINVAL;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const auto t0 = std::chrono::steady_clock::now();
+  std::chrono::microseconds nap(20);
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(s);
+    if (e == cudaSuccess) return GPW_OK;
+    if (e != cudaErrorNotReady) {
+      set_error(std::string("gpw_stream_wait: ") + cudaGetErrorString(e));
+      return GPW_ECUDA;
+    }
+    const double waited =
+        std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (waited >= timeout_s) {
+      set_error("gpw_stream_wait: the stream's work did not finish within the timeout");
+      return GPW_ETIMEDOUT;
+    }
+    std::this_thread::sleep_for(nap);
+    nap = std::min(nap * 2, std::chrono::microseconds(1000));
+  }
 }
 
 int gpw_batch_generation(gpw_batch_t b, long long* generation) {

@@ -16,6 +16,20 @@ device until its result has been copied back; then the memory is released.
 Per-request results are those of the request run alone (the same tasks, in the same
 order per sub-box, with the same reductions); the tests check this within the stated
 tolerances.
+
+Batches are formed by :class:`BatchPolicy` (host-only, tested without a GPU): the oldest
+waiting request opens a batch, which takes later requests of the same kind of cell in
+arrival order while the batch's estimated work (pair-points) stays under a cap, so that
+small cells are not held behind a large one.  A request may carry a deadline: if it has
+not been launched by then it fails with GPW_ETIMEDOUT, and if its batch is still running
+then its future fails with GPW_ETIMEDOUT at once (the batch finishes and its memory is
+released as usual).  A request whose future is cancelled before launch is dropped.
+
+Batches are launched directly, not through CUDA graphs: every batch holds a different set
+of plans, so a captured graph would be replayed exactly once and its capture and
+instantiation would cost what the launches cost.  A caller that repeats one batch (the
+same cells with new density matrices, as in SCF iterations) can capture
+Batch.fock_grad_async once and replay it (gpw_batch_generation tells when it is stale).
 """
 from __future__ import annotations
 
@@ -28,7 +42,9 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from .binding import Batch, Plan
+from .binding import Batch, GpwError, Plan, stream_wait
+
+GPW_ETIMEDOUT = -5
 
 
 @dataclass
@@ -57,12 +73,54 @@ class _Req:
     want_grad: bool
     future: cf.Future
     t_submit: float
+    deadline: float | None = None  # absolute time (perf_counter) or None
     plan: Plan | None = None
     bytes: int = 0
+    cost: float = 0.0  # estimated GPU work: pair-points of the plan
+    kind: bool = False  # non-orthogonal cell
     error: BaseException | None = None
     t_prepared: float = 0.0
     t_launch: float = 0.0
     bufs: dict | None = None  # device D, V, grad of the request (after commit)
+    done: bool = False  # its future has been resolved
+
+
+class BatchPolicy:
+    """Which staged requests go into the next batch (host-only: no CUDA, so it is tested
+    on the CPU).  A request is anything with the attributes kind, cost and deadline.
+
+    max_batch: most requests per batch.  batch_cost: cap on a batch's summed cost
+    (pair-points); a request costlier than the cap opens a batch of its own, and the
+    oldest request always opens the next batch, so no request starves."""
+
+    def __init__(self, max_batch: int = 32, batch_cost: float = 3.0e9):
+        self.max_batch = int(max_batch)
+        self.batch_cost = float(batch_cost)
+
+    @staticmethod
+    def expired(req, now: float) -> bool:
+        return req.deadline is not None and now > req.deadline
+
+    def form(self, staged, now: float):
+        """Split `staged` (oldest first) into (batch, keep, expired): expired requests are
+        past their deadline; the batch is the oldest live request plus later ones of its
+        kind, in order, while the count stays <= max_batch and the summed cost <= max(cap,
+        cost of the oldest); keep is the rest, in order."""
+        expired = [r for r in staged if self.expired(r, now)]
+        live = [r for r in staged if not self.expired(r, now)]
+        if not live:
+            return [], [], expired
+        first = live[0]
+        cap = max(self.batch_cost, first.cost)
+        batch, keep, total = [first], [], first.cost
+        for r in live[1:]:
+            if (r.kind == first.kind and len(batch) < self.max_batch and
+                    total + r.cost <= cap):
+                batch.append(r)
+                total += r.cost
+            else:
+                keep.append(r)
+        return batch, keep, expired
 
 
 @dataclass
@@ -92,13 +150,15 @@ class Server:
 
     def __init__(self, hbm_budget: int | None = None, max_batch: int = 32, streams: int = 2,
                  host_workers: int | None = None, tile=None, tile_integ=None,
-                 colloc_warps=None, integ_chunk=None, tune_with=None, fail_prepare=None):
+                 colloc_warps=None, integ_chunk=None, tune_with=None, fail_prepare=None,
+                 batch_cost: float = 3.0e9):
         import torch
         self.torch = torch
         torch.cuda.init()
         free, _ = torch.cuda.mem_get_info()
         self.budget = int(hbm_budget if hbm_budget is not None else 0.7 * free)
         self.max_batch = int(max_batch)
+        self.policy = BatchPolicy(self.max_batch, batch_cost)
         self.plan_kwargs = dict(tile=tile, tile_integ=tile_integ, colloc_warps=colloc_warps,
                                 integ_chunk=integ_chunk)
         self.choice = None
@@ -129,27 +189,43 @@ class Server:
         self._bid = 0
         self._cv = threading.Condition()
         self._stop = False
-        self.stats = dict(batches=0, admitted=0, rejected=0, max_in_flight=0, peak_bytes=0)
+        self.stats = dict(batches=0, admitted=0, rejected=0, max_in_flight=0, peak_bytes=0,
+                          timed_out=0, cancelled=0)
         self._gpu = threading.Thread(target=self._gpu_loop, name="gpw-serve", daemon=True)
         self._gpu.start()
 
     # ------------------------------------------------------------------ API --
-    def submit(self, system, want_grad: bool = False) -> cf.Future:
-        """Queue one Fock build (plus gradient if want_grad); returns a Future[Result]."""
+    def submit(self, system, want_grad: bool = False, deadline_s: float | None = None) -> cf.Future:
+        """Queue one Fock build (plus gradient if want_grad); returns a Future[Result].
+        deadline_s: seconds from now; past it the future fails with GpwError
+        (GPW_ETIMEDOUT).  Cancelling the future before its batch is launched drops it."""
         fut: cf.Future = cf.Future()
         with self._cv:
             rid = self._rid
             self._rid += 1
-        req = _Req(rid, system, bool(want_grad), fut, time.perf_counter())
+        t = time.perf_counter()
+        req = _Req(rid, system, bool(want_grad), fut, t,
+                   None if deadline_s is None else t + float(deadline_s))
         self._pool.submit(self._prepare, req)
         return fut
 
-    def close(self):
-        """Finish every submitted request, then stop."""
+    def close(self, timeout_s: float | None = None):
+        """Finish every submitted request, then stop.  With timeout_s, the wait for the
+        batches still on the GPU is bounded (gpw_stream_wait) and a TimeoutError is raised
+        if they have not finished."""
         self._pool.shutdown(wait=True)  # all preparations have reached the ready queue
         with self._cv:
             self._stop = True
             self._cv.notify_all()
+        if timeout_s is not None:
+            t_end = time.perf_counter() + float(timeout_s)
+            while self._gpu.is_alive():
+                for f in list(self._flights):
+                    if not stream_wait(f.stream, max(0.0, t_end - time.perf_counter())):
+                        raise TimeoutError("batches still running on the GPU at the timeout")
+                self._gpu.join(timeout=0.01)
+                if time.perf_counter() > t_end and self._gpu.is_alive():
+                    raise TimeoutError("server did not drain within the timeout")
         self._gpu.join()
         self._commits.shutdown(wait=True)
         self._finisher.shutdown(wait=True)
@@ -172,7 +248,10 @@ class Server:
                 raise RuntimeError("plan preparation failed (injected)")
             req.plan = Plan(req.system, commit=False, host_threads=share, **self.plan_kwargs)
             nao, natm = req.plan.nao, req.plan.natm
-            req.bytes = int(req.plan.stats()["device_bytes"]) + 8 * (2 * nao * nao + 3 * natm + 2)
+            st = req.plan.stats()
+            req.bytes = int(st["device_bytes"]) + 8 * (2 * nao * nao + 3 * natm + 2)
+            req.cost = float(st["pair_points"])
+            req.kind = _skewed(req.system)
             if req.bytes > self.budget:
                 raise MemoryError(f"request needs {req.bytes} device bytes, budget is {self.budget}")
         except BaseException as ex:  # the request fails alone; the server keeps serving
@@ -187,12 +266,25 @@ class Server:
     def _admit(self):
         """Admit prepared requests in arrival order while they fit the memory budget and
         hand them to the commit threads (called with the lock held)."""
+        now = time.perf_counter()
         while self._ready:
             req = self._ready[0]
+            if req.error is None and req.future.cancelled():
+                self._ready.popleft()
+                self.stats["cancelled"] += 1
+                req.plan.close()
+                req.plan = None
+                continue
+            if req.error is None and self.policy.expired(req, now):
+                req.error = GpwError(GPW_ETIMEDOUT, "serve", "deadline passed before launch")
+                self.stats["timed_out"] += 1
+                req.plan.close()
+                req.plan = None
             if req.error is not None:
                 self._ready.popleft()
                 self.stats["rejected"] += 1
-                req.future.set_exception(req.error)
+                if not req.future.cancelled():
+                    req.future.set_exception(req.error)
                 continue
             busy = self._flights or self._staged or self._committing or self._finishing
             if self._used + req.bytes > self.budget and busy:
@@ -266,14 +358,19 @@ class Server:
         E = fl.bufs["E"].cpu().numpy()
         t = time.perf_counter()
         for i, r in enumerate(fl.reqs):
-            V = r.bufs["V"].cpu().numpy()
-            g = r.bufs["g"].cpu().numpy() if r.bufs["g"] is not None else None
-            res = Result(r.rid, float(E[2 * i]), float(E[2 * i + 1]), V, g, r.t_submit, t,
-                         fl.bid, len(fl.reqs), r.t_prepared, r.t_launch)
+            with self._cv:
+                late = r.done  # its deadline passed while the batch ran
+                r.done = True
+            if not late:
+                V = r.bufs["V"].cpu().numpy()
+                g = r.bufs["g"].cpu().numpy() if r.bufs["g"] is not None else None
+                res = Result(r.rid, float(E[2 * i]), float(E[2 * i + 1]), V, g, r.t_submit, t,
+                             fl.bid, len(fl.reqs), r.t_prepared, r.t_launch)
             r.plan.close(stream=fl.stream)  # its batch has finished: no device sync
             r.plan = None
             r.bufs = None
-            r.future.set_result(res)
+            if not late:
+                r.future.set_result(res)
         with self._cv:
             self._used -= fl.nbytes
             self._finishing -= 1
@@ -285,6 +382,27 @@ class Server:
             if id(s) not in busy:
                 return i
         return None
+
+    def _drop(self, r: _Req, err: BaseException | None):
+        """Release a staged request that will not run (expired or cancelled)."""
+        self._used -= r.bytes
+        if r.plan is not None:
+            r.plan.close()
+            r.plan = None
+        r.bufs = None
+        r.done = True
+        if err is not None and not r.future.cancelled():
+            r.future.set_exception(err)
+
+    def _expire_in_flight(self, now: float):
+        """Futures of running requests past their deadline fail now (lock held)."""
+        for f in self._flights:
+            for r in f.reqs:
+                if not r.done and self.policy.expired(r, now):
+                    r.done = True
+                    self.stats["timed_out"] += 1
+                    r.future.set_exception(GpwError(GPW_ETIMEDOUT, "serve",
+                                                    "deadline passed while its batch ran"))
 
     def _gpu_loop(self):
         while True:
@@ -298,17 +416,24 @@ class Server:
                 self._finisher.submit(self._complete, f)
             reqs, slot = [], None
             with self._cv:
+                now = time.perf_counter()
+                self._expire_in_flight(now)
                 self._admit()
                 slot = self._free_slot()
                 if slot is not None and self._staged:
-                    # one batch holds cells of one kind (orthorhombic or not), oldest first
-                    kind = _skewed(self._staged[0].system)
-                    keep = collections.deque()
-                    while self._staged and len(reqs) < self.max_batch:
-                        r = self._staged.popleft()
-                        (reqs if _skewed(r.system) == kind else keep).append(r)
-                    keep.extend(self._staged)
-                    self._staged = keep
+                    # the policy picks the batch: one kind of cell, oldest first, its work
+                    # capped; expired and cancelled requests leave here
+                    batch, keep, expired = self.policy.form(list(self._staged), now)
+                    self._staged = collections.deque(keep)
+                    for r in expired:
+                        self.stats["timed_out"] += 1
+                        self._drop(r, GpwError(GPW_ETIMEDOUT, "serve", "deadline passed before launch"))
+                    for r in batch:
+                        if r.future.set_running_or_notify_cancel():
+                            reqs.append(r)
+                        else:
+                            self.stats["cancelled"] += 1
+                            self._drop(r, None)
                 if not reqs:
                     idle = not (self._ready or self._staged or self._committing or
                                 self._flights or self._finishing)

@@ -185,3 +185,37 @@ def test_server_mixes_cell_kinds(gpw):
         res = [f.result(timeout=300) for f in [srv.submit(s, want_grad=True) for s in systems]]
     for r, a in zip(res, ref):
         _same(dict(V=r.V, grad=r.grad, EH=r.EH, Ex=r.Ex), a)
+
+
+def test_deadlines_and_cancellation(gpw, alone):
+    from paper_2603_24881_gb300.serve import Server
+    systems = _systems()
+    with Server(max_batch=3, streams=2) as srv:
+        late = srv.submit(systems[0], deadline_s=0.0)          # expired before launch
+        keep = [srv.submit(s, want_grad=True, deadline_s=300.0) for s in systems]
+        gone = srv.submit(systems[1])
+        gone.cancel()                                           # cancelled while planning
+        res = [f.result(timeout=300) for f in keep]
+        with pytest.raises(gpw.GpwError) as ei:
+            late.result(timeout=300)
+        assert ei.value.code == -5
+        assert gone.cancelled()
+        stats = dict(srv.stats)
+    for i, r in enumerate(res):
+        _same(dict(V=r.V, grad=r.grad, EH=r.EH, Ex=r.Ex), alone[i])
+    assert stats["timed_out"] >= 1 and stats["cancelled"] == 1
+
+
+def test_stream_wait_is_bounded(gpw):
+    from paper_2603_24881_gb300.binding import stream_wait
+    s = torch.cuda.Stream()
+    a = torch.ones((6144, 6144), dtype=torch.float64, device="cuda")
+    torch.cuda.synchronize()
+    with torch.cuda.stream(s):
+        b = a @ a  # about half a second of FP64 work
+    assert stream_wait(s, 0.0) is False                       # still running: gives up
+    assert stream_wait(s, 120.0) is True                      # then finishes
+    assert stream_wait(s, 0.0) is True                        # nothing left
+    assert float(b[0, 0]) == 6144.0
+    with pytest.raises(gpw.GpwError):
+        stream_wait(s, -1.0)

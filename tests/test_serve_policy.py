@@ -1,0 +1,69 @@
+"""The server's batch formation and deadlines on the host (no GPU): the policy the GPU
+thread applies to its staged requests."""
+from dataclasses import dataclass
+
+from paper_2603_24881_gb300.serve import BatchPolicy
+
+
+@dataclass
+class R:
+    name: str
+    cost: float
+    kind: bool = False
+    deadline: float | None = None
+
+
+def names(rs):
+    return [r.name for r in rs]
+
+
+def test_oldest_opens_the_batch_and_order_is_kept():
+    p = BatchPolicy(max_batch=8, batch_cost=10.0)
+    staged = [R("a", 3), R("b", 3), R("c", 3), R("d", 3)]
+    batch, keep, exp = p.form(staged, now=0.0)
+    assert names(batch) == ["a", "b", "c"] and names(keep) == ["d"] and exp == []
+
+
+def test_large_request_runs_alone_and_small_ones_pass_it():
+    p = BatchPolicy(max_batch=8, batch_cost=10.0)
+    staged = [R("s1", 1), R("big", 50), R("s2", 1), R("s3", 1)]
+    batch, keep, _ = p.form(staged, now=0.0)
+    assert names(batch) == ["s1", "s2", "s3"] and names(keep) == ["big"]
+    batch, keep, _ = p.form(keep + [R("s4", 1)], now=0.0)
+    # the oldest (large) request opens its own batch, over the cap
+    assert names(batch) == ["big"] and names(keep) == ["s4"]
+
+
+def test_one_kind_of_cell_per_batch_and_max_batch():
+    p = BatchPolicy(max_batch=2, batch_cost=100.0)
+    staged = [R("o1", 1), R("k1", 1, kind=True), R("o2", 1), R("o3", 1)]
+    batch, keep, _ = p.form(staged, now=0.0)
+    assert names(batch) == ["o1", "o2"] and names(keep) == ["k1", "o3"]
+
+
+def test_expired_requests_leave_before_the_batch_is_formed():
+    p = BatchPolicy(max_batch=8, batch_cost=100.0)
+    staged = [R("late", 1, deadline=1.0), R("ok", 1, deadline=5.0), R("free", 1)]
+    batch, keep, exp = p.form(staged, now=2.0)
+    assert names(exp) == ["late"] and names(batch) == ["ok", "free"] and keep == []
+    assert BatchPolicy.expired(staged[0], 2.0) and not BatchPolicy.expired(staged[1], 2.0)
+    assert p.form([R("x", 1, deadline=0.5)], now=1.0) == ([], [], [staged[0].__class__("x", 1, deadline=0.5)])
+
+
+def test_every_request_is_placed_exactly_once():
+    import random
+    rng = random.Random(3)
+    p = BatchPolicy(max_batch=5, batch_cost=7.0)
+    staged = [R(str(i), rng.choice([0.5, 1, 2, 4, 9]), kind=rng.random() < 0.3,
+                deadline=rng.choice([None, 3.0, 10.0])) for i in range(60)]
+    seen = []
+    now = 0.0
+    while staged:
+        batch, keep, exp = p.form(staged, now)
+        assert len(batch) <= 5 and len({r.kind for r in batch}) <= 1
+        if len(batch) > 1:
+            assert sum(r.cost for r in batch) <= max(7.0, batch[0].cost)
+        seen += batch + exp
+        staged = keep
+        now += 0.25
+    assert sorted(int(r.name) for r in seen) == list(range(60))
