@@ -101,6 +101,9 @@ def _args():
                     help="also time the kinetic-energy-density (meta-GGA) kernels")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the launch shape with the autotuner (cached per GPU/workload)")
+    ap.add_argument("--fast-prune", action="store_true",
+                    help="GPW_FAST_BLOCK_PRUNE: per-block value screening of the collocation "
+                         "tasks (tau-sized changes, outside the strict definition)")
     return ap.parse_args()
 
 
@@ -232,6 +235,25 @@ def run_reference(a, rank, world):
             "e2e": {"value": val, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def fp64_dgemm_tflops(torch, n: int = 6144, reps: int = 3) -> float:
+    """cuBLAS DGEMM rate on this GPU in this run (context for the FP64 peak): best of
+    `reps` n x n x n products after one warm-up, CUDA events."""
+    g = torch.Generator(device="cuda").manual_seed(0)
+    a = torch.rand((n, n), dtype=torch.float64, device="cuda", generator=g)
+    b = torch.rand((n, n), dtype=torch.float64, device="cuda", generator=g)
+    c = a @ b
+    best = float("inf")
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        torch.matmul(a, b, out=c)
+        e1.record()
+        e1.synchronize()
+        best = min(best, e0.elapsed_time(e1))
+    del a, b, c
+    return 2.0 * n ** 3 / (best * 1e-3) / 1e12
 
 
 # ------------------------------------------------------------------ served -----
@@ -384,7 +406,7 @@ def main():
     if a.autotune:
         from paper_2603_24881_gb300.autotune import tune
         shape = tune(s).plan_kwargs()
-    plan = gpw.Plan(s, xc=a.xc, tau=a.tau, **shape)
+    plan = gpw.Plan(s, xc=a.xc, tau=a.tau, fast_prune=a.fast_prune, **shape)
     torch.cuda.synchronize()
     plan_ms = 1e3 * (time.perf_counter() - t0)
     st = plan.stats()
@@ -437,7 +459,8 @@ def main():
     roofline = {"bound": "alu", "kernel": dom, "achieved": achieved, "peak": FP64_PEAK_TFLOPS,
                 "unit": "TFLOP/s", "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                 "peak_source": "FP64 pipe: 152 SMs x 4 FLOP/clk x 2.07 GHz (no FP64 figure in "
-                               "MEASURED_PEAKS.json)"}
+                               "MEASURED_PEAKS.json)",
+                "dgemm_tflops_measured": fp64_dgemm_tflops(torch)}
 
     e2e = None
     if not a.no_e2e:
@@ -456,7 +479,8 @@ def main():
                "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(Dh.numel() * 8),
                "d2h_bytes_per_step": int((out["V"].numel() + out["grad"].numel() + 2) * 8),
-               "api": "Plan.fock_grad_host (pinned host D in; V, gradient, energies out)"}
+               "api": "gpw_fock_grad_host through the C ABI (pinned host D in; V, gradient, "
+                      "energies out; copies inside the timed region)"}
 
     tau = None
     if a.tau:
@@ -506,7 +530,7 @@ def main():
                            "tile": list(st["tile"]), "tile_integ": list(st["tile_integ"]),
                            "colloc_warps": st["colloc_warps"], "integ_chunk": st["integ_chunk"],
                            "launch_shape": "autotuned" if a.autotune else "library defaults",
-                           "xc": a.xc,
+                           "xc": a.xc, **({"screening": "GPW_FAST_BLOCK_PRUNE"} if a.fast_prune else {}),
                            "parallelism": f"replicas x{world}"},
                 "pct_of_fp64_peak": 100.0 * value / world / FP64_PEAK_TFLOPS,
                 **({"tau": tau} if tau else {}),

@@ -70,6 +70,17 @@ extern "C" {
                                    the records on the device (count per grid block,
                                    prefix sums, fill: the pair-to-block mapping of the
                                    paper's appendix); both give identical lists. */
+#define GPW_FAST_BLOCK_PRUNE 4  /* per-block value screening (App. Alg. 5): drop from the
+                                   collocation task lists every (pair, sub-box) task whose
+                                   part of the pair box lies wholly farther than R_p from
+                                   the pair centre P (every point there has its Eq. cut
+                                   bound below tau).  Which points are dropped depends on
+                                   the sub-box shape, so this is outside the strict
+                                   definition: densities and energies move by tau-sized
+                                   amounts (checked at 1e-6 relative).  Integration keeps
+                                   every task.  Orthorhombic cells use the distance to the
+                                   task's box; non-orthogonal cells its largest distance
+                                   across the lattice-plane slabs, a lower bound. */
 
 /* Exchange functional (gpw_desc.xc), spin-unpolarised, on the finest grid:
  * GPW_XC_LDA_X  Slater exchange v_x = -(3/pi)^(1/3) rho^(1/3) (Sec. II, LDA);
@@ -111,7 +122,8 @@ typedef struct {
   double rel_cutoff;          /* a pair of exponent alpha_p goes to the coarsest level
                                  with E_k >= rel_cutoff * alpha_p (40 if <= 0) */
   double tau;                 /* screening threshold of Eq. (cut) */
-  int flags;                  /* GPW_STRICT, or GPW_TAU | GPW_HOST_TASKS */
+  int flags;                  /* GPW_STRICT, or GPW_TAU | GPW_HOST_TASKS |
+                                 GPW_FAST_BLOCK_PRUNE */
   int tile[3];                /* sub-box owned by one collocation thread block (grid
                                  points along a1, a2, a3); {0,0,0} = default {4,8,16} */
   int tile_integ[3];          /* sub-box of one integration thread block;
@@ -273,6 +285,16 @@ int gpw_fock_async(gpw_plan_t plan, const double* D, double* V, double* energies
  * grad (device natm x 3), energies (host, 2 doubles; the call synchronises `stream`). */
 int gpw_fock_grad(gpw_plan_t plan, const double* D, double* V, double* grad, double* energies,
                   void* stream);
+
+/* gpw_fock_grad from and to HOST memory: D (host nao x nao) is copied to the device, the
+ * Fock build and gradient run on `stream`, and V (host nao x nao), grad (host natm x 3)
+ * and energies (host, 2 doubles) are copied back; returns after synchronising `stream`.
+ * Pinned (page-locked) host buffers give full-rate copies; pageable ones work too.  The
+ * first call on a plan allocates the plan's device copies of D, V and the gradient
+ * (2 nao^2 + 3 natm doubles, kept until the plan is destroyed); later calls allocate
+ * nothing.  Not a paper operation: the end-to-end form of the same build. */
+int gpw_fock_grad_host(gpw_plan_t plan, const double* D, double* V, double* grad,
+                       double* energies, void* stream);
 
 /* As gpw_fock_grad with the energies written to device memory (2 doubles), no sync. */
 int gpw_fock_grad_async(gpw_plan_t plan, const double* D, double* V, double* grad,

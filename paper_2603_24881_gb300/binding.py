@@ -28,7 +28,7 @@ EXPORTS = ["gpw_plan", "gpw_plan_query", "gpw_plan_update_coords", "gpw_plan_pai
            "gpw_eval_mat_ip1", "gpw_eval_mat_ip1_levels", "gpw_eval_tau", "gpw_eval_tau_levels",
            "gpw_eval_mat_tau", "gpw_eval_mat_tau_levels", "gpw_eval_mat_tau_ip1",
            "gpw_eval_mat_tau_ip1_levels", "gpw_plan_destroy_async", "gpw_fock", "gpw_fock_async",
-           "gpw_fock_grad", "gpw_fock_grad_async", "gpw_tile_supported",
+           "gpw_fock_grad", "gpw_fock_grad_async", "gpw_fock_grad_host", "gpw_tile_supported",
            "gpw_plan_prepare", "gpw_plan_commit", "gpw_batch_create", "gpw_batch_set",
            "gpw_batch_fock_grad_async", "gpw_batch_generation", "gpw_batch_destroy",
            "gpw_check_device", "gpw_profile", "gpw_profile_read", "gpw_plan_destroy",
@@ -58,6 +58,7 @@ class Desc(ctypes.Structure):
 
 GPW_TAU = 1  # gpw_desc.flags: kinetic-energy-density kernels
 GPW_HOST_TASKS = 2  # gpw_desc.flags: task records built on the host (default: device)
+GPW_FAST_BLOCK_PRUNE = 4  # gpw_desc.flags: per-block value screening of the collocation tasks
 
 # exchange functionals (gpw_desc.xc)
 XC = {"lda_x": 0, "pbe_x": 1}
@@ -123,6 +124,7 @@ def load(build_if_missing: bool = True):
         L.gpw_fock_async.argtypes = [vp, vp, vp, vp, vp, vp, vp]
         L.gpw_fock_grad.argtypes = [vp, vp, vp, vp, vp, vp]
         L.gpw_fock_grad_async.argtypes = [vp, vp, vp, vp, vp, vp]
+        L.gpw_fock_grad_host.argtypes = [vp, vp, vp, vp, vp, vp]
         L.gpw_tile_supported.argtypes = [ci, ci, ci]
         L.gpw_plan_prepare.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(vp)]
         L.gpw_plan_commit.argtypes = [vp, vp]
@@ -196,15 +198,17 @@ class Plan:
 
     def __init__(self, system, stream=None, tile=None, tile_integ=None, commit=True,
                  colloc_warps=None, integ_chunk=None, xc="lda_x", tau=False, host_threads=0,
-                 host_tasks=False):
+                 host_tasks=False, fast_prune=False):
         """Prepare the plan on the host (screening, levels, task lists) and, unless
         commit=False, commit it to the current device.  An uncommitted plan reports its
         exact device footprint in stats()["device_bytes"].  tile, tile_integ,
         colloc_warps, integ_chunk: launch shape (library defaults if None); xc: exchange
         functional, "lda_x" (Slater) or "pbe_x" (PBE exchange, a GGA); tau: also build the
-        kinetic-energy-density (meta-GGA) kernels' data (shells up to d); host_threads:
-        most planner threads (0 = all cores); host_tasks: build the sub-box task lists on
-        the host instead of on the device at commit (identical lists)."""
+        kinetic-energy-density (meta-GGA) kernels' data; host_threads: most planner
+        threads (0 = all cores); host_tasks: build the sub-box task lists on the host
+        instead of on the device at commit (identical lists); fast_prune: leave out of
+        the collocation lists the (pair, sub-box) tasks wholly beyond the pair's extent
+        (GPW_FAST_BLOCK_PRUNE: tau-sized changes, outside the strict definition)."""
         self._lib = load()
         s = system
         self.system = s
@@ -234,7 +238,8 @@ class Plan:
         d.meshes = arr(s.meshes, np.int32) if s.meshes is not None else None
         d.rel_cutoff = float(s.rel_cutoff)
         d.tau = float(s.tau)
-        d.flags = (GPW_TAU if tau else 0) | (GPW_HOST_TASKS if host_tasks else 0)
+        d.flags = ((GPW_TAU if tau else 0) | (GPW_HOST_TASKS if host_tasks else 0) |
+                   (GPW_FAST_BLOCK_PRUNE if fast_prune else 0))
         if tile is not None:
             for i in range(3):
                 d.tile[i] = int(tile[i])
@@ -329,9 +334,10 @@ class Plan:
               "gpw_plan_task_lists")
         return tasks, sub, work
 
-    def pair_table(self) -> np.ndarray:
+    def pair_table(self, sort: bool = True) -> np.ndarray:
         """Screened pairs as int64 rows (a, b, n0, n1, n2, level, lo0..2, hi0..2),
-        sorted lexicographically."""
+        sorted lexicographically (sort=False: in the plan's pair order, the pair index of
+        the task records)."""
         n = int(self.info.npairs)
         ab = np.zeros((n, 2), np.int32)
         img = np.zeros((n, 3), np.int32)
@@ -341,7 +347,7 @@ class Plan:
         P = lambda a: a.ctypes.data_as(ctypes.c_void_p)
         check(self._lib.gpw_plan_pairs(self._h, P(ab), P(img), P(lev), P(lo), P(hi)), "gpw_plan_pairs")
         t = np.concatenate([ab, img, lev[:, None], lo, hi], axis=1).astype(np.int64)
-        return t[np.lexsort(t[:, ::-1].T)]
+        return t[np.lexsort(t[:, ::-1].T)] if sort else t
 
     def update_coords(self, coords, stream=None):
         c = np.ascontiguousarray(np.asarray(coords, dtype=np.float64))
@@ -513,36 +519,21 @@ class Plan:
         return out
 
     def fock_grad_host(self, D_host, out=None, stream=None):
-        """End-to-end Fock build plus Hxc gradient from HOST memory: copies D in
-        (pinned host -> device), runs gpw_fock_grad_async on the stream, copies V,
-        the gradient and the two energies back, synchronises.
-        Returns dict(V, grad, EH, Ex) of host tensors."""
+        """End-to-end Fock build plus Hxc gradient from HOST memory through the C ABI
+        (gpw_fock_grad_host: D copied in, the build on the stream, V, the gradient and the
+        two energies copied back, synchronised).  D_host: a contiguous float64 host tensor
+        (pinned for full-rate copies).  Returns dict(V, grad, E) of host tensors."""
         import torch
-        st = torch.cuda.current_stream() if stream is None else stream
-        ws = self._host_ws()
-        ws["D"].copy_(D_host, non_blocking=True)
-        self.fock_grad_async(ws["D"], ws["V"], ws["g"], ws["E"], stream=st)
         if out is None:
             out = dict(V=torch.empty((self.nao, self.nao), dtype=torch.float64, pin_memory=True),
                        grad=torch.empty((self.natm, 3), dtype=torch.float64, pin_memory=True),
                        E=torch.empty(2, dtype=torch.float64, pin_memory=True))
-        out["V"].copy_(ws["V"], non_blocking=True)
-        out["grad"].copy_(ws["g"], non_blocking=True)
-        out["E"].copy_(ws["E"], non_blocking=True)
-        st.synchronize()
+        for t in (D_host, out["V"], out["grad"], out["E"]):
+            if t.device.type != "cpu" or t.dtype != torch.float64 or not t.is_contiguous():
+                raise ValueError("fock_grad_host takes contiguous float64 host tensors")
+        check(self._lib.gpw_fock_grad_host(self._h, _ptr(D_host), _ptr(out["V"]), _ptr(out["grad"]),
+                                           _ptr(out["E"]), _stream(stream)), "gpw_fock_grad_host")
         return out
-
-    def _host_ws(self):
-        import torch
-        ws = getattr(self, "_ws", None)
-        if ws is None:
-            dev = dict(dtype=torch.float64, device="cuda")
-            ws = dict(D=torch.empty((self.nao, self.nao), **dev),
-                      V=torch.empty((self.nao, self.nao), **dev),
-                      E=torch.empty(2, **dev), v=torch.empty(self.fine_mesh, **dev),
-                      g=torch.empty((self.natm, 3), **dev))
-            self._ws = ws
-        return ws
 
     def fock_grad(self, D, stream=None):
         """Fock build and Hxc gradient in one pass (gpw_fock_grad).

@@ -145,7 +145,8 @@ void free_plan(Plan* P, cudaStream_t stream = nullptr, bool sync = true) {
                   d.coef_off, d.part_off, d.xt_off, d.task_c, d.sub_off_c, d.work_c, d.task_i, d.sub_off_i, d.work_i, d.groups, d.atom_off,
                   d.atom_list, d.tab, d.coef, d.part, d.pgrad, d.grids, d.spec, d.fspec,
                   d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs, d.view, d.g2tab,
-                  d.g1tab, d.grad3, d.fspec3, d.mono_t, P->fft_work};
+                  d.g1tab, d.grad3, d.fspec3, d.mono_t, d.xfer_D, d.xfer_V, d.xfer_g,
+                  P->fft_work};
   bool any = false;
   for (void* q : ptrs) any = any || q != nullptr;
   if (any && sync) cudaDeviceSynchronize();
@@ -1009,6 +1010,44 @@ int gpw_fock_grad(gpw_plan_t plan, const double* D, double* V, double* grad, dou
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     set_error(std::string("gpw_fock_grad: ") + cudaGetErrorString(e));
+    return GPW_ECUDA;
+  }
+  return GPW_OK;
+}
+
+int gpw_fock_grad_host(gpw_plan_t plan, const double* D, double* V, double* grad,
+                       double* energies, void* stream) {
+  if (gpw::bad(plan) || !D || !V || !grad || !energies) return GPW_EINVAL;
+  gpw::Plan& P = plan->p;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t nn = sizeof(double) * (size_t)P.nao * (size_t)P.nao;
+  const size_t ng = sizeof(double) * 3 * (size_t)P.natm;
+  cudaError_t e = cudaSuccess;
+  if (!P.d.xfer_D) {
+    // first call: the plan's device copies of D, V and the gradient, kept with the plan
+    e = cudaMallocAsync((void**)&P.d.xfer_D, nn, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P.d.xfer_V, nn, s);
+    if (e == cudaSuccess) e = cudaMallocAsync((void**)&P.d.xfer_g, ng, s);
+    if (e != cudaSuccess) {
+      set_error(std::string("gpw_fock_grad_host: ") + cudaGetErrorString(e));
+      return GPW_ENOMEM;
+    }
+    P.device_bytes += (long long)(2 * nn + ng);
+  }
+  e = cudaMemcpyAsync(P.d.xfer_D, D, nn, cudaMemcpyHostToDevice, s);
+  if (e != cudaSuccess) {
+    set_error(std::string("gpw_fock_grad_host: ") + cudaGetErrorString(e));
+    return GPW_ECUDA;
+  }
+  int rc = gpw::fock_grad_async(P, P.d.xfer_D, P.d.xfer_V, P.d.xfer_g, P.d.energies, s);
+  if (rc) return rc;
+  e = cudaMemcpyAsync(V, P.d.xfer_V, nn, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(grad, P.d.xfer_g, ng, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(energies, P.d.energies, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_error(std::string("gpw_fock_grad_host: ") + cudaGetErrorString(e));
     return GPW_ECUDA;
   }
   return GPW_OK;

@@ -150,6 +150,11 @@ struct DeviceArrays {
   cufftDoubleComplex* fspec3 = nullptr;  // GGA: finest half spectrum (work)
   double* energies = nullptr; // E_H, E_x (device)
   int* err = nullptr;         // device error word
+  double4* prune = nullptr;   // GPW_FAST_BLOCK_PRUNE: per pair {f_0(P), f_1(P), f_2(P), R_p}
+  // gpw_fock_grad_host: device copies of D, V and the gradient (made by its first call)
+  double* xfer_D = nullptr;
+  double* xfer_V = nullptr;
+  double* xfer_g = nullptr;
   CoefTables* tabs = nullptr;
   PlanView* view = nullptr;   // this plan's view (device)
 };
@@ -173,6 +178,9 @@ struct Plan {
   long long npairs = 0, nent = 0, nwork = 0, nsub_total = 0, ngroups = 0;
   long long nent_i = 0, nwork_i = 0, nsub_i = 0;
   bool tasks_on_device = false;  // task records built on the device at commit
+  bool prune = false;            // GPW_FAST_BLOCK_PRUNE: collocation tasks screened per block
+  double prune_blen[3] = {0, 0, 0};  // |b_d| of the block screening (1 / L_d orthorhombic)
+  double prune_lam = 0;      // a lower bound of the lattice metric's smallest eigenvalue
   long long tab_total = 0, coef_total = 0, part_total = 0, xt_total = 0;
   long long grid_total = 0, spec_total = 0, fine_n = 0, fine_spec_n = 0;
   long long pair_points = 0;

@@ -112,7 +112,7 @@ double pair_dlogh(int la, int lb, double dA, double dB, double ap, double r) {
 // bisection, whose upper end is R_p.
 bool pair_box(double cab, double kab, int la, int lb, double dA, double dB, double ap,
               double tau, const double* P, const double* N, const double* L, int* lo_out,
-              int* hi_out, const SkewBox* sk = nullptr) {
+              int* hi_out, const SkewBox* sk = nullptr, double* R_out = nullptr) {
   auto box = [&](double R, int* lo, int* hi) {
     if (sk)
       box_at_skew(R, P, N, *sk, lo, hi);
@@ -167,7 +167,34 @@ bool pair_box(double cab, double kab, int la, int lb, double dA, double dB, doub
     }
   }
   box(hi, lo_out, hi_out);
+  if (R_out) *R_out = hi;  // an upper bound of the root (the bisection may stop early)
   return true;
+}
+
+// A lower bound of the smallest eigenvalue of the lattice metric M_de = R_d . R_e (the
+// closed form for a symmetric 3 x 3 matrix, then 1e-9 relative taken off for rounding):
+// |sum_d f_d R_d|^2 >= lam |f|^2 for every fractional displacement f.
+double metric_lambda_min(const double* lat) {
+  double M[3][3];
+  for (int d = 0; d < 3; ++d)
+    for (int e = 0; e < 3; ++e)
+      M[d][e] = lat[3 * d] * lat[3 * e] + lat[3 * d + 1] * lat[3 * e + 1] + lat[3 * d + 2] * lat[3 * e + 2];
+  const double tr = (M[0][0] + M[1][1] + M[2][2]) / 3.0;
+  const double p1 = M[0][1] * M[0][1] + M[0][2] * M[0][2] + M[1][2] * M[1][2];
+  const double p2 = (M[0][0] - tr) * (M[0][0] - tr) + (M[1][1] - tr) * (M[1][1] - tr) +
+                    (M[2][2] - tr) * (M[2][2] - tr) + 2.0 * p1;
+  const double p = std::sqrt(p2 / 6.0);
+  if (!(p > 0.0)) return tr * (1.0 - 1e-9);
+  double B[3][3];
+  for (int d = 0; d < 3; ++d)
+    for (int e = 0; e < 3; ++e) B[d][e] = (M[d][e] - (d == e ? tr : 0.0)) / p;
+  const double det = B[0][0] * (B[1][1] * B[2][2] - B[1][2] * B[2][1]) -
+                     B[0][1] * (B[1][0] * B[2][2] - B[1][2] * B[2][0]) +
+                     B[0][2] * (B[1][0] * B[2][1] - B[1][1] * B[2][0]);
+  const double r = std::max(-1.0, std::min(1.0, det / 2.0));
+  const double phi = std::acos(r) / 3.0;
+  const double lmin = tr + 2.0 * p * std::cos(phi + 2.0 * M_PI / 3.0);
+  return std::max(0.0, lmin) * (1.0 - 1e-9);
 }
 
 bool smooth7(int m) {
@@ -199,6 +226,7 @@ struct PairTmp {
   int img[3];
   int level;
   int lo[3], hi[3];
+  double4 q;  // GPW_FAST_BLOCK_PRUNE: fractional coordinates of P and R_p
 };
 
 struct Seg {
@@ -235,6 +263,7 @@ void segments(int lo, int hi, int N, int T, std::vector<Seg>* out) {
 
 struct PairBox {
   int level, lo[3], hi[3];
+  double4 q;  // GPW_FAST_BLOCK_PRUNE: fractional coordinates of P and R_p
 };
 
 // Spare task-record buffers of committed plans, kept with their pages so that the next
@@ -274,6 +303,7 @@ std::vector<PairBox> pairs_view(const std::vector<PairTmp>& pairs) {
   std::vector<PairBox> v(pairs.size());
   for (size_t i = 0; i < pairs.size(); ++i) {
     v[i].level = pairs[i].level;
+    v[i].q = pairs[i].q;
     for (int d = 0; d < 3; ++d) {
       v[i].lo[d] = pairs[i].lo[d];
       v[i].hi[d] = pairs[i].hi[d];
@@ -296,7 +326,22 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
                 const int* T, LevelInfo* lev, std::vector<long long>* sub_off,
                 std::vector<int4>* task, std::vector<int4>* work, long long* nent_out,
                 long long* nwork_out, long long* nsub_out, std::vector<int>* ranks,
-                std::vector<long long>* psize, long long* chunk_io) {
+                std::vector<long long>* psize, long long* chunk_io, bool prune = false) {
+  // GPW_FAST_BLOCK_PRUNE (collocation lists only): tasks whose box lies wholly beyond R_p
+  // are left out; the others keep their rank among all of the pair's tasks
+  auto beyond = [&](const PairBox& t, const LevelInfo& lv, const long long* a, const long long* b) {
+    if (!prune) return false;
+    const int ai[3] = {(int)a[0], (int)a[1], (int)a[2]}, bi[3] = {(int)b[0], (int)b[1], (int)b[2]};
+    return block_beyond(t.q, ai, bi, lv.N, plan->prune_blen, !plan->skew, plan->prune_lam);
+  };
+  // unwrapped grid range [a, b] of segment s of [lo, hi] along an axis of N points
+  auto seg_range = [](int lo, int hi, int N, int Td, const Seg& s, long long* a, long long* b) {
+    const long long s0 = (long long)s.j * Td;
+    const long long ext = std::min<long long>(Td, N - s0);
+    const long long o = (long long)s.k * N + s0;
+    *a = std::max<long long>(lo, o);
+    *b = std::min<long long>(hi, o + ext - 1);
+  };
   const int K = plan->nlev;
   const long long np = (long long)pairs.size();
   long long nsub = 0;
@@ -321,10 +366,18 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
       const PairBox& t = pairs[p];
       const LevelInfo& lv = lev[t.level];
       for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
-      for (auto& s0 : sg[0])
-        for (auto& s1 : sg[1])
-          for (auto& s2 : sg[2])
+      long long a[3], b[3];
+      for (auto& s0 : sg[0]) {
+        seg_range(t.lo[0], t.hi[0], lv.N[0], T[0], s0, &a[0], &b[0]);
+        for (auto& s1 : sg[1]) {
+          seg_range(t.lo[1], t.hi[1], lv.N[1], T[1], s1, &a[1], &b[1]);
+          for (auto& s2 : sg[2]) {
+            seg_range(t.lo[2], t.hi[2], lv.N[2], T[2], s2, &a[2], &b[2]);
+            if (beyond(t, lv, a, b)) continue;
             c[lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j]++;
+          }
+        }
+      }
     }
   }
   std::vector<long long> count(nsub + 1, 0);
@@ -375,7 +428,7 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
       // per dimension and segment: packed (m, u, t) fields of the records and the
       // sub-box coordinate, computed once per pair
       int fm[3][kSegMax], fu[3][kSegMax], ft[3][kSegMax];
-      long long fj[3][kSegMax];
+      long long fj[3][kSegMax], fa[3][kSegMax], fb[3][kSegMax];
       bool big = false;
       for (int d = 0; d < 3; ++d) {
         big = big || sg[d].size() > kSegMax;
@@ -392,6 +445,8 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
           fu[d][k] = (int)(a - o) << shift;
           ft[d][k] = (int)(a - t.lo[d]) | (n[d] << 16);
           fj[d][k] = sgm.j;
+          fa[d][k] = a;
+          fb[d][k] = b;
         }
       }
       if (big) {
@@ -406,6 +461,11 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
         for (int k1 = 0; k1 < ns1; ++k1) {
           const long long sub01 = lv.sub_base + (fj[0][k0] * lv.nsb[1] + fj[1][k1]) * lv.nsb[2];
           for (int k2 = 0; k2 < ns2; ++k2, ++rank) {
+            if (prune) {
+              const long long a[3] = {fa[0][k0], fa[1][k1], fa[2][k2]};
+              const long long b[3] = {fb[0][k0], fb[1][k1], fb[2][k2]};
+              if (beyond(t, lv, a, b)) continue;
+            }
             const long long slot = fill[sub01 + fj[2][k2]]++;
             const int r12 = k1 * ns2 + k2;
             (*task)[2 * slot] = make_int4((int)p, fm[0][k0] | fm[1][k1] | fm[2][k2] | (L << 24),
@@ -694,7 +754,7 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     return GPW_EINVAL;
   }
   g_host_threads = desc->host_threads;
-  if (desc->flags & ~(GPW_TAU | GPW_HOST_TASKS)) {
+  if (desc->flags & ~(GPW_TAU | GPW_HOST_TASKS | GPW_FAST_BLOCK_PRUNE)) {
     set_error("gpw_plan: unknown flags");
     return GPW_EINVAL;
   }
@@ -849,6 +909,9 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     skb.blen[d] = std::sqrt(plan->rec[3 * d] * plan->rec[3 * d] +
                             plan->rec[3 * d + 1] * plan->rec[3 * d + 1] +
                             plan->rec[3 * d + 2] * plan->rec[3 * d + 2]);
+  plan->prune = (desc->flags & GPW_FAST_BLOCK_PRUNE) != 0;
+  for (int d = 0; d < 3; ++d) plan->prune_blen[d] = plan->skew ? skb.blen[d] : 1.0 / plan->L[d];
+  plan->prune_lam = plan->skew ? metric_lambda_min(plan->lat) : 0.0;
   // atoms are screened in parallel (each thread keeps its own pair list); the sort
   // below fixes one order whatever the thread count
   const int sthr = plan_threads((long long)prims.size() * prims.size() / 64);
@@ -917,10 +980,26 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
                 PairTmp t;
                 const double Nl[3] = {(double)mesh[level][0], (double)mesh[level][1],
                                       (double)mesh[level][2]};
+                double Rp = 0.0;
                 if (!pair_box(cab, kab, pa.l, pb.l, std::sqrt(dA2), std::sqrt(dB2), ap,
                               desc->tau, P, Nl, plan->L, t.lo, t.hi,
-                              plan->skew ? &skb : nullptr))
+                              plan->skew ? &skb : nullptr, &Rp))
                   continue;
+                if (plan->prune) {
+                  // P's fractional coordinates as the boxes take them, and R_p
+                  double fp[3];
+                  for (int d = 0; d < 3; ++d) {
+                    if (plan->skew) {
+                      fp[d] = 0.0;
+                      for (int c = 0; c < 3; ++c) fp[d] += plan->rec[3 * d + c] * P[c];
+                    } else {
+                      fp[d] = P[d] / plan->L[d];
+                    }
+                  }
+                  t.q = make_double4(fp[0], fp[1], fp[2], Rp);
+                } else {
+                  t.q = make_double4(0.0, 0.0, 0.0, 0.0);
+                }
                 t.a = a;
                 t.b = b;
                 t.sa = pa.shell;
@@ -1069,10 +1148,14 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   const bool host_tasks = (desc->flags & GPW_HOST_TASKS) != 0;
   plan->tasks_on_device = !host_tasks;
   const std::vector<PairBox> pv = pairs_view(pairs);
+  if (plan->prune && !host_tasks) {
+    H->prune.resize(pv.size());
+    for (size_t p = 0; p < pv.size(); ++p) H->prune[p] = pv[p].q;
+  }
   int rc = host_tasks
                ? build_tasks(plan, pv, H->hot_a, plan->tile, plan->lev, &H->sub_off_c, &H->task_c,
                              &H->work_c, &plan->nent, &plan->nwork, &plan->nsub_total, nullptr,
-                             nullptr, nullptr)
+                             nullptr, nullptr, plan->prune)
                : count_tasks(plan, pv, H->hot_a, plan->tile, plan->lev, &plan->nsub_total,
                              &H->toff_c, &plan->nent, nullptr, nullptr);
   if (rc) return rc;

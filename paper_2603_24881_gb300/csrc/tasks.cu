@@ -29,7 +29,37 @@ struct TaskGeom {
   long long np, nent, nsub;
   int xr;
   int integ;  // integration records: offset of the task's W tensor in r1.w
+  int prune;  // GPW_FAST_BLOCK_PRUNE on this list: tasks beyond R_p get the key nsub
+  int ortho;
+  double blen[3];
+  double lam;
 };
+
+// block_beyond (plan_host.h) with every rounding spelt out, so that it decides as the host
+// builder does: the task box [a_d, b_d] lies wholly farther than R_p from P
+__device__ __forceinline__ bool block_beyond_d(const double4 q, const long long* a,
+                                               const long long* b, const int* N,
+                                               const double* blen, int ortho, double lam) {
+  const double fp[3] = {q.x, q.y, q.z};
+  double f[3], s[3];
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const double fa = __ddiv_rn((double)a[d], (double)N[d]);
+    const double fb = __ddiv_rn((double)b[d], (double)N[d]);
+    f[d] = fp[d] < fa ? __dsub_rn(fa, fp[d]) : (fp[d] > fb ? __dsub_rn(fp[d], fb) : 0.0);
+    s[d] = __ddiv_rn(f[d], blen[d]);
+  }
+  const double R2 = __dmul_rn(q.w, q.w);
+  if (ortho) {
+    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(s[0], s[0]), __dmul_rn(s[1], s[1])),
+                                __dmul_rn(s[2], s[2]));
+    return r2 > R2;
+  }
+  if (fmax(s[0], fmax(s[1], s[2])) > q.w) return true;
+  const double f2 = __dadd_rn(__dadd_rn(__dmul_rn(f[0], f[0]), __dmul_rn(f[1], f[1])),
+                              __dmul_rn(f[2], f[2]));
+  return __dmul_rn(lam, f2) > R2;
+}
 
 __host__ __device__ __forceinline__ long long floordiv_d(long long a, long long b) {
   long long q = a / b;
@@ -109,19 +139,30 @@ __host__ __device__ __forceinline__ TaskPos locate(const TaskGeom& G, const int4
   return q;
 }
 
-// sub-box key of every task, and the identity permutation
+// sub-box key of every task, and the identity permutation; a task left out by the block
+// screening gets the key nsub, past every sub-box, so the sort puts it after them all
 __global__ void task_keys_kernel(TaskGeom G, const int4* __restrict__ hot_a,
                                  const int4* __restrict__ hot_b,
-                                 const long long* __restrict__ toff, unsigned* __restrict__ keys,
+                                 const long long* __restrict__ toff,
+                                 const double4* __restrict__ pq, unsigned* __restrict__ keys,
                                  unsigned* __restrict__ vals) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < G.nent;
        t += (long long)gridDim.x * blockDim.x) {
     const TaskPos q = locate(G, hot_a, hot_b, toff, t);
     const int lev = q.b.w;
-    const long long j0 = segment(q.a.x, q.b.x, G.N[lev][0], G.T[0], G.nsb[lev][0], q.k0, 0).j;
-    const long long j1 = segment(q.a.y, q.b.y, G.N[lev][1], G.T[1], G.nsb[lev][1], q.k1, 1).j;
-    const long long j2 = segment(q.a.z, q.b.z, G.N[lev][2], G.T[2], G.nsb[lev][2], q.k2, 2).j;
-    keys[t] = (unsigned)(G.sub_base[lev] + (j0 * G.nsb[lev][1] + j1) * G.nsb[lev][2] + j2);
+    const SegD s0 = segment(q.a.x, q.b.x, G.N[lev][0], G.T[0], G.nsb[lev][0], q.k0, 0);
+    const SegD s1 = segment(q.a.y, q.b.y, G.N[lev][1], G.T[1], G.nsb[lev][1], q.k1, 1);
+    const SegD s2 = segment(q.a.z, q.b.z, G.N[lev][2], G.T[2], G.nsb[lev][2], q.k2, 2);
+    unsigned key = (unsigned)(G.sub_base[lev] + (s0.j * G.nsb[lev][1] + s1.j) * G.nsb[lev][2] + s2.j);
+    if (G.prune) {
+      // the task box: from its start in the pair box (t) and its length (m)
+      const long long a[3] = {(long long)q.a.x + (s0.t & 0xffff), (long long)q.a.y + (s1.t & 0xffff),
+                              (long long)q.a.z + (s2.t & 0xffff)};
+      const long long b[3] = {a[0] + (s0.m & 255) - 1, a[1] + ((s1.m >> 8) & 255) - 1,
+                              a[2] + ((s2.m >> 16) & 255) - 1};
+      if (block_beyond_d(pq[q.p], a, b, G.N[lev], G.blen, G.ortho, G.lam)) key = (unsigned)G.nsub;
+    }
+    keys[t] = key;
     vals[t] = (unsigned)t;
   }
 }
@@ -204,6 +245,10 @@ TaskGeom geom(const Plan& P, bool integ) {
   G.nsub = integ ? P.nsub_i : P.nsub_total;
   G.xr = P.xr;
   G.integ = integ ? 1 : 0;
+  G.prune = (P.prune && !integ) ? 1 : 0;
+  G.ortho = P.skew ? 0 : 1;
+  for (int d = 0; d < 3; ++d) G.blen[d] = P.prune_blen[d];
+  G.lam = P.prune_lam;
   return G;
 }
 
@@ -250,7 +295,14 @@ int build_tasks_device(Plan* P, HostArrays& H, cudaStream_t s, long long* bytes)
   for (int i = 0; i < 4; ++i) kv[i] = reinterpret_cast<unsigned*>(scratch + 2 * toff_b + i * kv_b);
   void* tmp = scratch + 2 * toff_b + 4 * kv_b;
   int out = GPW_OK;
+  double4* pq = nullptr;  // the block screening's per-pair data (fractional P, R_p)
   auto body = [&]() -> int {
+    if (P->prune) {
+      GPW_TCK(cudaMallocAsync((void**)&pq, sizeof(double4) * (size_t)std::max<long long>(np, 1), s));
+      if (np > 0)
+        GPW_TCK(cudaMemcpyAsync(pq, H.prune.data(), sizeof(double4) * (size_t)np,
+                                cudaMemcpyHostToDevice, s));
+    }
     GPW_TCK(cudaMemcpyAsync(toff_c, H.toff_c.data(), sizeof(long long) * (size_t)(np + 1),
                             cudaMemcpyHostToDevice, s));
     GPW_TCK(cudaMemcpyAsync(toff_i, H.toff_i.data(), sizeof(long long) * (size_t)(np + 1),
@@ -268,7 +320,7 @@ int build_tasks_device(Plan* P, HostArrays& H, cudaStream_t s, long long* bytes)
         const long long* toff = integ ? toff_i : toff_c;
         const int threads = 256;
         const int blocks = (int)std::min<long long>((G.nent + threads - 1) / threads, 152 * 16);
-        task_keys_kernel<<<blocks, threads, 0, s>>>(G, d.hot_a, d.hot_b, toff, kv[0], kv[2]);
+        task_keys_kernel<<<blocks, threads, 0, s>>>(G, d.hot_a, d.hot_b, toff, pq, kv[0], kv[2]);
         GPW_TCK(cudaGetLastError());
         cub::DoubleBuffer<unsigned> keys(kv[0], kv[1]), vals(kv[2], kv[3]);
         size_t tb = temp;
@@ -291,6 +343,8 @@ int build_tasks_device(Plan* P, HostArrays& H, cudaStream_t s, long long* bytes)
     GPW_TCK(cudaMemcpyAsync(H.sub_off_i.data(), d.sub_off_i, sizeof(long long) * H.sub_off_i.size(),
                             cudaMemcpyDeviceToHost, s));
     GPW_TCK(cudaStreamSynchronize(s));
+    // the block screening's dropped tasks sit past the last sub-box's
+    P->nent = H.sub_off_c[(size_t)P->nsub_total];
     int r = order_work(P->nlev, P->lev, H.sub_off_c, 0, &H.work_c, &P->nwork);
     if (!r) r = order_work(P->nlev, P->lev_i, H.sub_off_i, P->chunk_i, &H.work_i, &P->nwork_i);
     if (r) return r;
@@ -306,6 +360,7 @@ int build_tasks_device(Plan* P, HostArrays& H, cudaStream_t s, long long* bytes)
   };
   out = body();
   if (own) cudaFreeAsync(scratch, s);
+  if (pq) cudaFreeAsync(pq, s);
   return out;
 }
 

@@ -91,30 +91,37 @@ class BatchPolicy:
 
     max_batch: most requests per batch.  batch_cost: cap on a batch's summed cost
     (pair-points); a request costlier than the cap opens a batch of its own, and the
-    oldest request always opens the next batch, so no request starves."""
+    oldest request always opens the next batch, so no request starves.  small_cost: the
+    most a request may cost to ride in a small-request batch (form(small_only=True)),
+    which the server launches on a high-priority stream."""
 
-    def __init__(self, max_batch: int = 32, batch_cost: float = 3.0e9):
+    def __init__(self, max_batch: int = 32, batch_cost: float = 2.0e9,
+                 small_cost: float = 4.0e8):
         self.max_batch = int(max_batch)
         self.batch_cost = float(batch_cost)
+        self.small_cost = float(small_cost)
 
     @staticmethod
     def expired(req, now: float) -> bool:
         return req.deadline is not None and now > req.deadline
 
-    def form(self, staged, now: float):
+    def form(self, staged, now: float, small_only: bool = False):
         """Split `staged` (oldest first) into (batch, keep, expired): expired requests are
-        past their deadline; the batch is the oldest live request plus later ones of its
-        kind, in order, while the count stays <= max_batch and the summed cost <= max(cap,
-        cost of the oldest); keep is the rest, in order."""
+        past their deadline; the batch is the oldest live request (the oldest small one
+        with small_only) plus later ones of its kind (small ones with small_only), in
+        order, while the count stays <= max_batch and the summed cost <= max(cap, cost of
+        its first request); keep is the rest, in order."""
         expired = [r for r in staged if self.expired(r, now)]
         live = [r for r in staged if not self.expired(r, now)]
-        if not live:
-            return [], [], expired
-        first = live[0]
+        fits = (lambda r: r.cost <= self.small_cost) if small_only else (lambda r: True)
+        i0 = next((i for i, r in enumerate(live) if fits(r)), None)
+        if i0 is None:
+            return [], live, expired
+        first = live[i0]
         cap = max(self.batch_cost, first.cost)
-        batch, keep, total = [first], [], first.cost
-        for r in live[1:]:
-            if (r.kind == first.kind and len(batch) < self.max_batch and
+        batch, keep, total = [first], live[:i0], first.cost
+        for r in live[i0 + 1:]:
+            if (r.kind == first.kind and fits(r) and len(batch) < self.max_batch and
                     total + r.cost <= cap):
                 batch.append(r)
                 total += r.cost
@@ -146,19 +153,23 @@ class Server:
     instead, its choice (cached per GPU and workload class) then serves every request.
     Non-orthogonal cells plan with 4x8x16 sub-boxes for both passes, so a request of that
     kind fails alone under another explicit shape; batches hold one kind of cell.
+    batch_cost: most pair-points (estimated GPU work) per batch, beyond its first
+    request; small_cost: the most a request may cost to ride the priority lane;
+    priority_lane: one more stream, of high priority, for batches of small requests.
     """
 
     def __init__(self, hbm_budget: int | None = None, max_batch: int = 32, streams: int = 2,
                  host_workers: int | None = None, tile=None, tile_integ=None,
                  colloc_warps=None, integ_chunk=None, tune_with=None, fail_prepare=None,
-                 batch_cost: float = 3.0e9):
+                 batch_cost: float = 2.0e9, small_cost: float = 4.0e8,
+                 priority_lane: bool = True):
         import torch
         self.torch = torch
         torch.cuda.init()
         free, _ = torch.cuda.mem_get_info()
         self.budget = int(hbm_budget if hbm_budget is not None else 0.7 * free)
         self.max_batch = int(max_batch)
-        self.policy = BatchPolicy(self.max_batch, batch_cost)
+        self.policy = BatchPolicy(self.max_batch, batch_cost, small_cost)
         self.plan_kwargs = dict(tile=tile, tile_integ=tile_integ, colloc_warps=colloc_warps,
                                 integ_chunk=integ_chunk)
         self.choice = None
@@ -178,6 +189,12 @@ class Server:
         self._finisher = cf.ThreadPoolExecutor(2, thread_name_prefix="gpw-finish")
         self._tls = threading.local()
         self._streams = [torch.cuda.Stream() for _ in range(max(1, streams))]
+        # the priority lane: one more stream, of high priority, for batches of small
+        # requests only; the block scheduler gives its blocks the SMs as soon as blocks of
+        # the running large batches retire, so small cells do not queue behind them
+        self._lane = len(self._streams) if priority_lane else None
+        if priority_lane:
+            self._streams.append(torch.cuda.Stream(priority=-1))
         self._batches = [Batch(self.max_batch) for _ in self._streams]
         self._ready = collections.deque()    # prepared, waiting for admission
         self._staged = collections.deque()   # committed, waiting for a batch
@@ -376,10 +393,21 @@ class Server:
             self._finishing -= 1
             self._cv.notify_all()
 
-    def _free_slot(self):
+    def _launchable(self) -> bool:
+        """A batch could be launched now (lock held): staged requests and a free regular
+        slot, or the priority lane free and a small request staged."""
+        if not self._staged:
+            return False
+        if self._free_slot() is not None:
+            return True
+        return (self._lane is not None and self._free_slot(lane=True) is not None and
+                any(r.cost <= self.policy.small_cost for r in self._staged))
+
+    def _free_slot(self, lane: bool = False):
+        """A free stream slot: a regular one, or with lane=True the priority lane."""
         busy = {id(f.stream) for f in self._flights}
         for i, s in enumerate(self._streams):
-            if id(s) not in busy:
+            if (i == self._lane) == lane and id(s) not in busy:
                 return i
         return None
 
@@ -419,11 +447,17 @@ class Server:
                 now = time.perf_counter()
                 self._expire_in_flight(now)
                 self._admit()
-                slot = self._free_slot()
-                if slot is not None and self._staged:
+                slot, small = None, False
+                if self._staged:
+                    slot = self._free_slot()
+                    if slot is None and self._lane is not None:
+                        slot, small = self._free_slot(lane=True), True
+                if slot is not None:
                     # the policy picks the batch: one kind of cell, oldest first, its work
-                    # capped; expired and cancelled requests leave here
-                    batch, keep, expired = self.policy.form(list(self._staged), now)
+                    # capped (small requests only on the priority lane); expired and
+                    # cancelled requests leave here
+                    batch, keep, expired = self.policy.form(list(self._staged), now,
+                                                            small_only=small)
                     self._staged = collections.deque(keep)
                     for r in expired:
                         self.stats["timed_out"] += 1
@@ -459,7 +493,7 @@ class Server:
                 t0 = time.perf_counter()
                 while not self._flights[0].event.query() and time.perf_counter() - t0 < 0.002:
                     with self._cv:
-                        if self._staged and self._free_slot() is not None:
+                        if self._launchable():
                             break
                     time.sleep(0.0002)
 

@@ -264,3 +264,23 @@ def test_mixed_tiles_carbon_like_f_shells(gpw):
     assert _rel(out["V"].cpu().numpy(), r["V"]) <= RTOL
     assert abs(out["EH"] - r["EH"]) <= 1e-8 and abs(out["Ex"] - r["Ex"]) <= 1e-8
     assert np.max(np.abs(out["grad"].cpu().numpy() - op.grad_levels(s.D, r["v_levels"]))) <= 1e-7
+
+
+def test_fock_grad_from_host_buffers(gpw):
+    # gpw_fock_grad_host (host D in, host V / gradient / energies out, through the C ABI)
+    # runs the same build as the device-pointer call: identical results, pinned or
+    # pageable host memory, and repeated calls on the plan's kept device copies
+    s = workloads.config("water4")
+    p = gpw.Plan(s)
+    ref = p.fock_grad(s.D)
+    for pinned in (True, False):
+        Dh = torch.as_tensor(np.ascontiguousarray(s.D))
+        if pinned:
+            Dh = Dh.pin_memory()
+        for _ in range(2):
+            out = p.fock_grad_host(Dh)
+            assert torch.equal(out["V"], ref["V"].cpu())
+            assert torch.equal(out["grad"], ref["grad"].cpu())
+            assert float(out["E"][0]) == ref["EH"] and float(out["E"][1]) == ref["Ex"]
+    assert p.check_device() == 0
+    p.close()

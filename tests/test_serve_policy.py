@@ -67,3 +67,12 @@ def test_every_request_is_placed_exactly_once():
         staged = keep
         now += 0.25
     assert sorted(int(r.name) for r in seen) == list(range(60))
+
+
+def test_small_only_batches_for_the_priority_lane():
+    p = BatchPolicy(max_batch=8, batch_cost=10.0, small_cost=2.0)
+    staged = [R("big", 5), R("s1", 1), R("mid", 3), R("s2", 1), R("k", 1, kind=True)]
+    batch, keep, _ = p.form(staged, now=0.0, small_only=True)
+    assert names(batch) == ["s1", "s2"] and names(keep) == ["big", "mid", "k"]
+    batch, keep, _ = p.form([R("big", 5)], now=0.0, small_only=True)
+    assert batch == [] and names(keep) == ["big"]
