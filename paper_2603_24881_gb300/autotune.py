@@ -50,7 +50,10 @@ def signature(systems) -> str:
     """Workload class of a cell or a list of cells (order-independent)."""
     items = []
     for s in systems:
-        L = np.round(np.diag(np.asarray(s.lattice, dtype=np.float64)), 6).tolist()
+        # the cell by its metric R R^T (so the shape, not the orientation) and whether
+        # the rows are axis-aligned (which selects the orthorhombic kernels)
+        lat = np.asarray(s.lattice, dtype=np.float64)
+        L = [np.round(lat @ lat.T, 6).tolist(), bool(np.all(lat == np.diag(np.diag(lat))))]
         lcount = np.bincount(np.asarray(s.shell_l, dtype=np.int64), minlength=4).tolist()
         items.append(json.dumps([L, int(np.asarray(s.coords).shape[0]), lcount,
                                  int(np.asarray(s.exponents).size), float(s.cutoff_ha),

@@ -57,3 +57,18 @@ def test_no_usable_candidate_raises(tmp_path):
     with pytest.raises(GpwError):
         autotune.tune(workloads.tiny(), cache_path=str(tmp_path / "t.json"), measure=m,
                       tiles=[(4, 8, 16)])
+
+
+def test_signature_tells_cell_shapes_apart():
+    import numpy as np
+    import systems
+    s = systems.resolved(seed=5)
+    t = systems.skewed(seed=5)
+    r = systems.rotated(t, systems.rotation(12))
+    # the triclinic cell differs from the cubic one; turning a cell keeps its metric, but
+    # a cubic cell turned off the axes runs the non-orthogonal kernels
+    assert autotune.signature([s]) != autotune.signature([t])
+    assert autotune.signature([t]) == autotune.signature([r])
+    rc = systems.rotated(s, systems.rotation(12))
+    assert not np.all(rc.lattice == np.diag(np.diag(rc.lattice)))
+    assert autotune.signature([s]) != autotune.signature([rc])
