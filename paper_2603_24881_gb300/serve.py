@@ -345,7 +345,8 @@ class Server:
             if req.plan is not None:
                 req.plan.close()
                 req.plan = None
-            req.future.set_exception(err)
+            if not req.future.cancelled():
+                req.future.set_exception(err)
 
     def _launch(self, reqs, slot: int):
         torch = self.torch
