@@ -61,13 +61,14 @@ def _workload_desc(name: str, system, stats) -> str:
             f"step = gpw_fock_grad (V, energies, Hxc gradient)")
 
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture of this workload,
-# valid while the kernels and the plan (task lists, work order) are unchanged: sha256 of
-# csrc/kernels.cu + csrc/plan.cpp at capture time.
+# DRAM bytes per launch of the dominant kernel from one ncu capture (of a smaller case,
+# scaled by the work it processes), valid while the kernels and the plan (task lists,
+# work order) are unchanged: sha256 of csrc/kernels.cu + csrc/plan.cpp at capture time.
 TRAFFIC = {
-    # integration at degree L+1 (8x8x32 sub-box), water256, one launch: read + write
-    "integrate_ip1": {"bytes_per_launch": 1.7974e10, "src_sha": "db862321085d373d",
-                      "capture": "profiles/launches_water256_fock_grad.md"},
+    # integration at degree L+1 (8x8x32 sub-box): read + write of one 32-water launch
+    # (1.808 GB) scaled by pair-points to the 256-water launch
+    "integrate_ip1": {"bytes_per_launch": 1.3144e10, "src_sha": "bbf6d27648d4682b",
+                      "capture": "profiles/integrate_traffic_water32.md"},
 }
 
 
