@@ -81,6 +81,12 @@ extern "C" {
                                    every task.  Orthorhombic cells use the distance to the
                                    task's box; non-orthogonal cells its largest distance
                                    across the lattice-plane slabs, a lower bound. */
+#define GPW_DEBUG_CHECKS 8      /* extra device checks, read with gpw_check_device: at
+                                   commit every task record of both lists is checked
+                                   against its sub-box and its pair's box (code 17), and
+                                   every evaluation checks its outputs (V, gradient,
+                                   energies, densities) for values that are not finite
+                                   (code 16).  Results are unchanged. */
 
 /* Exchange functional (gpw_desc.xc), spin-unpolarised, on the finest grid:
  * GPW_XC_LDA_X  Slater exchange v_x = -(3/pi)^(1/3) rho^(1/3) (Sec. II, LDA);
@@ -123,7 +129,7 @@ typedef struct {
                                  with E_k >= rel_cutoff * alpha_p (40 if <= 0) */
   double tau;                 /* screening threshold of Eq. (cut) */
   int flags;                  /* GPW_STRICT, or GPW_TAU | GPW_HOST_TASKS |
-                                 GPW_FAST_BLOCK_PRUNE */
+                                 GPW_FAST_BLOCK_PRUNE | GPW_DEBUG_CHECKS */
   int tile[3];                /* sub-box owned by one collocation thread block (grid
                                  points along a1, a2, a3); {0,0,0} = default {4,8,16} */
   int tile_integ[3];          /* sub-box of one integration thread block;
@@ -331,7 +337,10 @@ int gpw_batch_generation(gpw_batch_t batch, long long* generation);
 void gpw_batch_destroy(gpw_batch_t batch);
 
 /* Read and clear the device error word of the plan (synchronises `stream`).
- * Returns GPW_OK, or GPW_EDEVICE with *code set to the first recorded check. */
+ * Returns GPW_OK, or GPW_EDEVICE with *code set to the first recorded check: 1 a
+ * collocation task record outside its sub-box or its pair's tables (the task is
+ * skipped), 3 the same for integration, 16 a value that is not finite in an output and
+ * 17 an inconsistent task list at commit (both with GPW_DEBUG_CHECKS). */
 int gpw_check_device(gpw_plan_t plan, int* code, void* stream);
 
 /* Phases timed by the profiler (gpw_profile). */

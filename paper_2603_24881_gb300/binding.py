@@ -59,6 +59,7 @@ class Desc(ctypes.Structure):
 GPW_TAU = 1  # gpw_desc.flags: kinetic-energy-density kernels
 GPW_HOST_TASKS = 2  # gpw_desc.flags: task records built on the host (default: device)
 GPW_FAST_BLOCK_PRUNE = 4  # gpw_desc.flags: per-block value screening of the collocation tasks
+GPW_DEBUG_CHECKS = 8  # gpw_desc.flags: task-list validation at commit, finite-output checks
 
 # exchange functionals (gpw_desc.xc)
 XC = {"lda_x": 0, "pbe_x": 1}
@@ -198,7 +199,7 @@ class Plan:
 
     def __init__(self, system, stream=None, tile=None, tile_integ=None, commit=True,
                  colloc_warps=None, integ_chunk=None, xc="lda_x", tau=False, host_threads=0,
-                 host_tasks=False, fast_prune=False):
+                 host_tasks=False, fast_prune=False, debug_checks=False):
         """Prepare the plan on the host (screening, levels, task lists) and, unless
         commit=False, commit it to the current device.  An uncommitted plan reports its
         exact device footprint in stats()["device_bytes"].  tile, tile_integ,
@@ -208,7 +209,9 @@ class Plan:
         threads (0 = all cores); host_tasks: build the sub-box task lists on the host
         instead of on the device at commit (identical lists); fast_prune: leave out of
         the collocation lists the (pair, sub-box) tasks wholly beyond the pair's extent
-        (GPW_FAST_BLOCK_PRUNE: tau-sized changes, outside the strict definition)."""
+        (GPW_FAST_BLOCK_PRUNE: tau-sized changes, outside the strict definition);
+        debug_checks: validate the task lists at commit and every output for values that
+        are not finite (GPW_DEBUG_CHECKS, read with check_device())."""
         self._lib = load()
         s = system
         self.system = s
@@ -239,7 +242,8 @@ class Plan:
         d.rel_cutoff = float(s.rel_cutoff)
         d.tau = float(s.tau)
         d.flags = ((GPW_TAU if tau else 0) | (GPW_HOST_TASKS if host_tasks else 0) |
-                   (GPW_FAST_BLOCK_PRUNE if fast_prune else 0))
+                   (GPW_FAST_BLOCK_PRUNE if fast_prune else 0) |
+                   (GPW_DEBUG_CHECKS if debug_checks else 0))
         if tile is not None:
             for i in range(3):
                 d.tile[i] = int(tile[i])

@@ -320,6 +320,8 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
   P->work_i_host = H.work_i;
   P->device_bytes = b;
   GPW_CK(launch_tables(*P, s));
+  GPW_CK(launch_validate_tasks(*P, false, s));  // GPW_DEBUG_CHECKS only
+  GPW_CK(launch_validate_tasks(*P, true, s));
   // the plan is complete for every stream when the commit returns
   GPW_CK(cudaStreamSynchronize(s));
   P->committed = true;
@@ -614,18 +616,32 @@ int fock_potential(Plan& P, const double* D, double* energies_dev, double* rho_o
   return potential_from_levels(P, energies_dev, rho_out, v_out, s);
 }
 
+// GPW_DEBUG_CHECKS: outputs that are not finite set code 16 of the error word
+int check_outputs(Plan& P, cudaStream_t s, const double* a, long long na,
+                  const double* b = nullptr, long long nb = 0, const double* c = nullptr,
+                  long long nc = 0) {
+  if (!P.debug) return GPW_OK;
+  GPW_CK(launch_finite_check(P, a, na, s));
+  GPW_CK(launch_finite_check(P, b, nb, s));
+  GPW_CK(launch_finite_check(P, c, nc, s));
+  return GPW_OK;
+}
+
 int fock_async(Plan& P, const double* D, double* V, double* energies_dev, double* rho_out,
                double* v_out, cudaStream_t s) {
   int rc = fock_potential(P, D, energies_dev, rho_out, v_out, s);
   if (rc) return rc;
-  return mat_from_grids(P, V, s);
+  if ((rc = mat_from_grids(P, V, s))) return rc;
+  return check_outputs(P, s, V, (long long)P.nao * P.nao, P.d.energies, 2, rho_out,
+                       rho_out ? P.fine_n : 0);
 }
 
 int fock_grad_async(Plan& P, const double* D, double* V, double* grad, double* energies_dev,
                     cudaStream_t s) {
   int rc = fock_potential(P, D, energies_dev, nullptr, nullptr, s);
   if (rc) return rc;
-  return mat_ip1_from_grids(P, D, V, grad, s);
+  if ((rc = mat_ip1_from_grids(P, D, V, grad, s))) return rc;
+  return check_outputs(P, s, V, (long long)P.nao * P.nao, grad, 3LL * P.natm, P.d.energies, 2);
 }
 
 bool bad(gpw_plan_t plan) {
@@ -863,7 +879,8 @@ int gpw_eval_rho(gpw_plan_t plan, const double* D, double* rho_fine, void* strea
   int rc = gpw::rho_levels(P, D, s);
   if (rc) return rc;
   if ((rc = gpw::combine(P, s))) return rc;
-  return gpw::fft_z2d(P, 0, P.d.fspec, rho_fine, s);
+  if ((rc = gpw::fft_z2d(P, 0, P.d.fspec, rho_fine, s))) return rc;
+  return gpw::check_outputs(P, s, rho_fine, P.fine_n);
 }
 
 int gpw_eval_mat(gpw_plan_t plan, const double* v_fine, double* V, void* stream) {
@@ -872,7 +889,8 @@ int gpw_eval_mat(gpw_plan_t plan, const double* v_fine, double* V, void* stream)
   cudaStream_t s = (cudaStream_t)stream;
   int rc = gpw::restrict_levels(P, v_fine, s);
   if (rc) return rc;
-  return gpw::mat_from_grids(P, V, s);
+  if ((rc = gpw::mat_from_grids(P, V, s))) return rc;
+  return gpw::check_outputs(P, s, V, (long long)P.nao * P.nao);
 }
 
 int gpw_eval_mat_levels(gpw_plan_t plan, const double* const* v_levels, double* V,
@@ -892,7 +910,8 @@ int gpw_eval_mat_ip1(gpw_plan_t plan, const double* D, const double* v_fine, dou
   cudaStream_t s = (cudaStream_t)stream;
   int rc = gpw::restrict_levels(P, v_fine, s);
   if (rc) return rc;
-  return gpw::ip1_from_grids(P, D, grad, s);
+  if ((rc = gpw::ip1_from_grids(P, D, grad, s))) return rc;
+  return gpw::check_outputs(P, s, grad, 3LL * P.natm);
 }
 
 int gpw_eval_tau_levels(gpw_plan_t plan, const double* D, double* const* tau_levels,

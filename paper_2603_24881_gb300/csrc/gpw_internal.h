@@ -179,6 +179,7 @@ struct Plan {
   long long nent_i = 0, nwork_i = 0, nsub_i = 0;
   bool tasks_on_device = false;  // task records built on the device at commit
   bool prune = false;            // GPW_FAST_BLOCK_PRUNE: collocation tasks screened per block
+  bool debug = false;            // GPW_DEBUG_CHECKS
   double prune_blen[3] = {0, 0, 0};  // |b_d| of the block screening (1 / L_d orthorhombic)
   double prune_lam = 0;      // a lower bound of the lattice metric's smallest eigenvalue
   long long tab_total = 0, coef_total = 0, part_total = 0, xt_total = 0;

@@ -1777,6 +1777,61 @@ __global__ void energy_final_kernel(const double* __restrict__ red, int nparts,
   if (threadIdx.x == 0) *out = s;
 }
 
+// GPW_DEBUG_CHECKS: a value that is not finite in an output
+__global__ void finite_check_kernel(const double* __restrict__ x, long long n, int* err) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    if (!isfinite(x[i])) {
+      set_err(err, 16);
+      return;
+    }
+}
+
+// GPW_DEBUG_CHECKS at commit: every task of a list against its sub-box (one thread per
+// sub-box): the pair exists, its level is the sub-box's, the record's degree and pair-box
+// extents are the pair's, the intersection lies inside the sub-box and the pair box and
+// sits, wrapped, where the record says, and the pairs come in order.
+__global__ void validate_tasks_kernel(const KLevels K, int T0, int T1, int T2, long long nsub,
+                                      const long long* __restrict__ sub_off,
+                                      const int4* __restrict__ task,
+                                      const int4* __restrict__ hot_a,
+                                      const int4* __restrict__ hot_b, long long np, int* err) {
+  const int T[3] = {T0, T1, T2};
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nsub;
+       g += (long long)gridDim.x * blockDim.x) {
+    int k = 0;
+    while (k + 1 < K.nlev && K.lv[k + 1].sub_base <= g) ++k;
+    const LevelInfo& lv = K.lv[k];
+    const long long sub = g - lv.sub_base;
+    const long long j2 = sub % lv.nsb[2], j1 = (sub / lv.nsb[2]) % lv.nsb[1],
+                    j0 = sub / ((long long)lv.nsb[2] * lv.nsb[1]);
+    const long long j[3] = {j0, j1, j2};
+    bool ok = sub_off[g] <= sub_off[g + 1];
+    long long prev = -1;
+    for (long long e = sub_off[g]; ok && e < sub_off[g + 1]; ++e) {
+      const int4 r0 = task[2 * e], r1 = task[2 * e + 1];
+      const long long p = r0.x;
+      ok = p >= 0 && p < np && p >= prev;
+      if (!ok) break;
+      prev = p;
+      const int4 ha = hot_a[p], hb = hot_b[p];
+      const int lo[3] = {ha.x, ha.y, ha.z}, n[3] = {hb.x, hb.y, hb.z};
+      const int rt[3] = {r1.x, r1.y, r1.z};
+      ok = hb.w == k && ((r0.y >> 24) & 255) == ha.w;
+      for (int d = 0; d < 3 && ok; ++d) {
+        const int m = (r0.y >> (8 * d)) & 255, u = (r0.z >> (8 * d)) & 255;
+        const int t = rt[d] & 0xffff, nn = (rt[d] >> 16) & 0xffff;
+        const long long s0 = j[d] * T[d];
+        const long long ext = min((long long)T[d], (long long)lv.N[d] - s0);
+        const long long i = (long long)lo[d] + t;
+        const long long w = ((i % lv.N[d]) + lv.N[d]) % lv.N[d];
+        ok = nn == n[d] && m >= 1 && u + m <= ext && t + m <= n[d] && w == s0 + u;
+      }
+    }
+    if (!ok) set_err(err, 17);
+  }
+}
+
 int even(int x) { return (x + 1) & ~1; }
 
 constexpr int kNW = 8;
@@ -1973,6 +2028,26 @@ cudaError_t configure_kernels(Plan* p) {
   if ((size_t)optin < std::max(p->smem_colloc, std::max(p->smem_integ, p->smem_integ1)))
     return cudaErrorInvalidValue;
   return cudaSuccess;
+}
+
+cudaError_t launch_finite_check(const Plan& p, const double* x, long long n, cudaStream_t s) {
+  if (!p.debug || !x || n <= 0) return cudaSuccess;
+  ++p.launches;
+  const long long blocks = std::min<long long>((n + 255) / 256, 152LL * 8);
+  finite_check_kernel<<<(int)blocks, 256, 0, s>>>(x, n, p.d.err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_validate_tasks(const Plan& p, bool integ, cudaStream_t s) {
+  const long long nsub = integ ? p.nsub_i : p.nsub_total;
+  if (!p.debug || nsub <= 0) return cudaSuccess;
+  const int* T = integ ? p.tile_i : p.tile;
+  ++p.launches;
+  const long long blocks = std::min<long long>((nsub + 127) / 128, 152LL * 16);
+  validate_tasks_kernel<<<(int)blocks, 128, 0, s>>>(
+      make_klevels(p, integ), T[0], T[1], T[2], nsub, integ ? p.d.sub_off_i : p.d.sub_off_c,
+      integ ? p.d.task_i : p.d.task_c, p.d.hot_a, p.d.hot_b, p.npairs, p.d.err);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_tables(const Plan& p, cudaStream_t s) {

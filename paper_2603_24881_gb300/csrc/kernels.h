@@ -57,6 +57,10 @@ cudaError_t launch_poisson(const Plan& p, cudaStream_t s);
 cudaError_t launch_lda(const Plan& p, const double* rho, const double* vH, double* v_out,
                        cudaStream_t s);
 cudaError_t launch_energy_final(const Plan& p, int slot, int nparts, cudaStream_t s);
+// GPW_DEBUG_CHECKS: error code 16 if any of x[0..n) is not finite; code 17 if a task list
+// (integ: the integration list) is inconsistent with its sub-boxes and pair boxes
+cudaError_t launch_finite_check(const Plan& p, const double* x, long long n, cudaStream_t s);
+cudaError_t launch_validate_tasks(const Plan& p, bool integ, cudaStream_t s);
 cudaError_t configure_kernels(Plan* p);
 
 constexpr int kRedBlocks = 304;

@@ -754,11 +754,12 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     return GPW_EINVAL;
   }
   g_host_threads = desc->host_threads;
-  if (desc->flags & ~(GPW_TAU | GPW_HOST_TASKS | GPW_FAST_BLOCK_PRUNE)) {
+  if (desc->flags & ~(GPW_TAU | GPW_HOST_TASKS | GPW_FAST_BLOCK_PRUNE | GPW_DEBUG_CHECKS)) {
     set_error("gpw_plan: unknown flags");
     return GPW_EINVAL;
   }
   plan->xr = (desc->flags & GPW_TAU) ? 2 : 0;
+  plan->debug = (desc->flags & GPW_DEBUG_CHECKS) != 0;
   if (plan->skew) {
     // the non-orthogonal kernels use 4x8x16 sub-boxes for both passes
     const bool tc = desc->tile[0] || desc->tile[1] || desc->tile[2];

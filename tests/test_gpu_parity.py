@@ -284,3 +284,26 @@ def test_fock_grad_from_host_buffers(gpw):
             assert float(out["E"][0]) == ref["EH"] and float(out["E"][1]) == ref["Ex"]
     assert p.check_device() == 0
     p.close()
+
+
+@pytest.mark.parametrize("host_tasks", [False, True])
+def test_debug_checks(gpw, host_tasks):
+    # GPW_DEBUG_CHECKS: the task lists pass their validation at commit, the results are
+    # those of a plain plan bit for bit, and an output that is not finite is reported
+    # through the device error word (code 16) without disturbing the plan
+    s = workloads.config("water4")
+    dbg = gpw.Plan(s, debug_checks=True, host_tasks=host_tasks)
+    assert dbg.check_device() == 0
+    ref = gpw.Plan(s).fock_grad(s.D)
+    out = dbg.fock_grad(s.D)
+    assert torch.equal(out["V"], ref["V"]) and torch.equal(out["grad"], ref["grad"])
+    assert out["EH"] == ref["EH"] and out["Ex"] == ref["Ex"]
+    assert dbg.check_device() == 0
+    bad = s.D.copy()
+    bad[0, 0] = float("nan")
+    dbg.fock_grad(bad)
+    assert dbg.check_device() == 16
+    assert dbg.check_device() == 0  # read and cleared
+    out = dbg.fock_grad(s.D)
+    assert torch.equal(out["V"], ref["V"]) and dbg.check_device() == 0
+    dbg.close()

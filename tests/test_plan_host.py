@@ -101,6 +101,9 @@ def test_validation(lib):
     f = systems.resolved(seed=8, shells=((0, 1), (3, 1)), natm=2)
     binding.Plan(f, commit=False).close()             # f shells are fine,
     binding.Plan(f, commit=False, tau=True).close()   # also for the tau kernels
+    # the opt-in flags plan; an unknown flag bit does not
+    binding.Plan(s, commit=False, fast_prune=True, debug_checks=True).close()
+    binding.Plan(sk, commit=False, fast_prune=True).close()
 
 
 def test_tau_plan_sizes(lib):
