@@ -473,15 +473,20 @@ def main():
             plan.fock_grad_host(Dh, out=out)
         replicas.barrier(dist)
         t1 = time.perf_counter()
+        laps = []
         for _ in range(a.steps):
+            tl = time.perf_counter()
             plan.fock_grad_host(Dh, out=out)
+            laps.append(1e3 * (time.perf_counter() - tl))
         e2e_s = replicas.max_over_ranks(dist, time.perf_counter() - t1, device="cuda")
         e2e = {"value": replicas.whole_job_rate(flops_step * a.steps, world, e2e_s) / 1e12,
                "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(Dh.numel() * 8),
                "d2h_bytes_per_step": int((out["V"].numel() + out["grad"].numel() + 2) * 8),
                "api": "gpw_fock_grad_host through the C ABI (pinned host D in; V, gradient, "
-                      "energies out; copies inside the timed region)"}
+                      "energies out; copies inside the timed region)",
+               "ms_per_step": 1e3 * e2e_s / a.steps,
+               "ms_min_max": [min(laps), max(laps)]}
 
     tau = None
     if a.tau:
