@@ -5,8 +5,12 @@
   for an upstream gradient g on the grid (with respect to the raw array),
   dL/dD = (N/Omega) eval_mat(g) and dL/dR = (N/Omega) eval_mat_ip1(D, g), because
   sum_r g(r) rho(r) = (N/Omega) <g, rho> and <v, rho(D)> = tr(D eval_mat(v)).
-* :func:`energy` — E_H + E_x of one Fock build.  Forward is gpw_fock_grad (one pass);
-  backward returns dE/dD = V and dE/dR = the Hxc gradient contraction (Algorithm 3).
+* :func:`tau` — the finest-grid kinetic energy density tau(D, R) (meta-GGA), the same way
+  with the tau integration directions: dL/dD = (N/Omega) eval_mat_tau(g) and
+  dL/dR = (N/Omega) eval_mat_tau_ip1(D, g) (the plan needs tau=True).
+* :func:`energy` — E_H + E_x of one Fock build (the plan's exchange functional, LDA or
+  PBE).  Forward is gpw_fock_grad (one pass); backward returns dE/dD = V and dE/dR = the
+  Hxc gradient contraction (Algorithm 3).
 
 D is treated as symmetric: the gradient with respect to D is the gradient of
 E((D + D^T)/2).  Atom positions R move the Gaussians with the plan's pair set and boxes
@@ -19,7 +23,7 @@ from __future__ import annotations
 import numpy as np
 import torch
 
-__all__ = ["rho", "energy"]
+__all__ = ["rho", "tau", "energy"]
 
 
 def _set_coords(plan, coords):
@@ -58,6 +62,27 @@ class _Rho(torch.autograd.Function):
         return gD, gR, None
 
 
+class _Tau(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, D, coords, plan):
+        _set_coords(plan, coords)
+        Dd = D.detach().to("cuda", torch.float64).contiguous()
+        out = plan.eval_tau(Dd)
+        ctx.plan = plan
+        ctx.save_for_backward(Dd)
+        return out
+
+    @staticmethod
+    def backward(ctx, g):
+        plan = ctx.plan
+        (D,) = ctx.saved_tensors
+        g = g.detach().to("cuda", torch.float64).contiguous()
+        s = _scale(plan)
+        gD = plan.eval_mat_tau(g) * s if ctx.needs_input_grad[0] else None
+        gR = plan.eval_mat_tau_ip1(D, g) * s if ctx.needs_input_grad[1] else None
+        return gD, gR, None
+
+
 class _Energy(torch.autograd.Function):
     @staticmethod
     def forward(ctx, D, coords, plan):
@@ -79,6 +104,12 @@ def rho(D, coords, plan):
     """Finest-grid density of D with the atoms at coords (natm x 3, or None to keep the
     plan's geometry); differentiable in both."""
     return _Rho.apply(D, coords, plan)
+
+
+def tau(D, coords, plan):
+    """Finest-grid kinetic energy density (1/2) sum D grad phi . grad phi of D with the
+    atoms at coords (or None); differentiable in both.  The plan needs tau=True."""
+    return _Tau.apply(D, coords, plan)
 
 
 def energy(D, coords, plan):

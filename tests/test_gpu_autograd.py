@@ -89,3 +89,51 @@ def test_rho_backward_is_the_adjoint(gpw, name):
     plan.update_coords(s.coords)
     fd = (Lp - Lm) / (2 * hr)
     assert abs(fd - float(R.grad[at, d])) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_tau_backward_is_the_adjoint(gpw):
+    # the tau wrapper: gradients with respect to D and the atoms from the tau integration
+    # directions, against central differences of the forward (boxes frozen)
+    from paper_2603_24881_gb300 import autograd as ag
+    s = systems.resolved(seed=6, shells=((0, 1), (1, 1), (2, 1), (3, 1)), cutoff=100.0)
+    plan = gpw.Plan(s, tau=True)
+    D = torch.as_tensor(s.D, device="cuda").requires_grad_(True)
+    R = torch.as_tensor(s.coords, device="cuda").requires_grad_(True)
+    t = ag.tau(D, R, plan)
+    w = torch.randn(t.shape, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(7))
+    (w * t).sum().backward()
+    X = torch.randn(D.shape, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(8))
+    X = X + X.T
+    h = 1e-3
+    fd = (float((w * plan.eval_tau(D.detach() + h * X)).sum()) -
+          float((w * plan.eval_tau(D.detach() - h * X)).sum())) / (2 * h)
+    assert abs(fd - float((D.grad * X).sum())) <= 1e-8 * max(1.0, abs(fd))
+    at, d, hr = 1, 2, 1e-4
+    c = s.coords.copy()
+    c[at, d] += hr
+    plan.update_coords(c)
+    Lp = float((w * plan.eval_tau(D.detach())).sum())
+    c[at, d] -= 2 * hr
+    plan.update_coords(c)
+    Lm = float((w * plan.eval_tau(D.detach())).sum())
+    plan.update_coords(s.coords)
+    fd = (Lp - Lm) / (2 * hr)
+    assert abs(fd - float(R.grad[at, d])) <= 1e-6 * max(1.0, abs(fd))
+
+
+def test_energy_backward_pbe_exchange(gpw):
+    # the energy wrapper with a GGA plan (PBE exchange): dE/dD = V and dE/dR against the
+    # oracle's PBE build and its analytic gradient
+    from paper_2603_24881_gb300 import autograd as ag
+    s = systems.resolved(seed=5, shells=((0, 1), (1, 1), (2, 1)), natm=2)
+    plan = gpw.Plan(s, xc="pbe_x")
+    op = oracle.Plan(s)
+    D = torch.as_tensor(s.D, device="cuda").requires_grad_(True)
+    R = torch.as_tensor(s.coords, device="cuda").requires_grad_(True)
+    E = ag.energy(D, R, plan)
+    E.backward()
+    ref = op.fock(s.D, xc="pbe_x")
+    assert abs(float(E.detach()) - (ref["EH"] + ref["Ex"])) <= 1e-8
+    assert float(np.max(np.abs(D.grad.cpu().numpy() - ref["V"]))) <= 1e-10 * np.max(np.abs(ref["V"]))
+    g = op.grad_levels(s.D, ref["v_levels"])
+    assert float(np.max(np.abs(R.grad.cpu().numpy() - g))) <= 1e-7
