@@ -63,6 +63,11 @@ struct CoefTables {
 };
 void build_coef_tables(CoefTables* t);
 
+// GPW_FAST_BLOCK_PRUNE: a pair's centre in fractional coordinates and its extent R_p
+struct alignas(16) PairQ {
+  double x, y, z, w;
+};
+
 struct LevelInfo {
   int N[3];
   int nsb[3];            // sub-boxes per dimension (ceil(N / tile))
@@ -150,7 +155,7 @@ struct DeviceArrays {
   cufftDoubleComplex* fspec3 = nullptr;  // GGA: finest half spectrum (work)
   double* energies = nullptr; // E_H, E_x (device)
   int* err = nullptr;         // device error word
-  double4* prune = nullptr;   // GPW_FAST_BLOCK_PRUNE: per pair {f_0(P), f_1(P), f_2(P), R_p}
+  PairQ* prune = nullptr;   // GPW_FAST_BLOCK_PRUNE: per pair {f_0(P), f_1(P), f_2(P), R_p}
   // gpw_fock_grad_host: device copies of D, V and the gradient (made by its first call)
   double* xfer_D = nullptr;
   double* xfer_V = nullptr;

@@ -1122,26 +1122,6 @@ __device__ __forceinline__ int mono_index(int k0, int k1, int k2, int M) {
   return nc3(M) - nc3(r) + k1 * (r + 1) - ((k1 * (k1 - 1)) >> 1) + k0;
 }
 
-// Integral of one shifted pair product (x - A)^a' (x - B)^b' from the pair's V tensor of
-// degree Lx: (x - B)^b' expanded about A (Eq. binomial), pw[d][j] = (A_d - B_d)^j;
-// zero if an exponent is negative (b'_d <= 5).
-__device__ double xelem(int a0, int a1, int a2, int b0, int b1, int b2, const double (*pw)[6],
-                        const double* V, int Lx) {
-  if (a0 < 0 || a1 < 0 || a2 < 0 || b0 < 0 || b1 < 0 || b2 < 0) return 0.0;
-  double s = 0.0;
-  for (int t2 = 0; t2 <= b2; ++t2) {
-    const double c2 = binom(b2, t2) * pw[2][b2 - t2];
-    for (int t1 = 0; t1 <= b1; ++t1) {
-      const double c21 = c2 * binom(b1, t1) * pw[1][b1 - t1];
-      double s0 = 0.0;
-      for (int t0 = 0; t0 <= b0; ++t0)
-        s0 += binom(b0, t0) * pw[0][b0 - t0] * V[mono_index(a0 + t0, a1 + t1, a2 + t2, Lx)];
-      s += c21 * s0;
-    }
-  }
-  return s;
-}
-
 // Gradient contraction per pair (Algorithm 3).  The centre derivative of the product
 // (x - A)^a exp(-alpha_a (x - A)^2) brings -a_d (x - A)^(a - e_d) + 2 alpha_a (x - A)^(a + e_d);
 // expanding (x - B)^b about A (Eq. binomial) turns the density-matrix block into
@@ -1501,21 +1481,85 @@ __global__ void pair_coef_tau_kernel(long long np, const int4* __restrict__ ids,
   for (int c = 0; c < nc; ++c) out[c] = acc[c];
 }
 
+// Coefficients of the i-th derivative of (x - X)^c e^{-alpha (x - X)^2}: sum over the
+// returned shifts s of w_s (x - X)^(c + s) (times the exponential); returns the count.
+__device__ __forceinline__ int deriv_terms(int c, int i, double alpha, int* sh, double* w) {
+  const double cd = (double)c;
+  if (i == 0) {
+    sh[0] = 0;
+    w[0] = 1.0;
+    return 1;
+  }
+  if (i == 1) {
+    sh[0] = -1;
+    w[0] = cd;
+    sh[1] = 1;
+    w[1] = -2.0 * alpha;
+    return 2;
+  }
+  sh[0] = -2;
+  w[0] = cd * (cd - 1.0);
+  sh[1] = 0;
+  w[1] = -2.0 * alpha * (2.0 * cd + 1.0);
+  sh[2] = 2;
+  w[2] = 4.0 * alpha * alpha;
+  return 3;
+}
+
+// 1-D product u^(i) w^(j) in powers of (x - A): out[k], k <= a + b + i + j (<= 9);
+// pw[m] = (A - B)^m.
+__device__ __forceinline__ void prod_1d(int a, int b, int i, int j, double aa, double ab,
+                                       const double* pw, double* out) {
+#pragma unroll
+  for (int k = 0; k < 10; ++k) out[k] = 0.0;
+  int su[3], sw[3];
+  double wu[3], ww[3];
+  const int nu = deriv_terms(a, i, aa, su, wu), nw = deriv_terms(b, j, ab, sw, ww);
+  for (int p = 0; p < nu; ++p) {
+    const int ea = a + su[p];
+    if (ea < 0 || wu[p] == 0.0) continue;
+    for (int q = 0; q < nw; ++q) {
+      const int eb = b + sw[q];
+      if (eb < 0 || ww[q] == 0.0) continue;
+      const double c = wu[p] * ww[q];
+      // (x - B)^eb = sum_m C(eb, m) (A - B)^(eb - m) (x - A)^m
+      for (int m = 0; m <= eb; ++m) out[ea + m] += c * binom(eb, m) * pw[eb - m];
+    }
+  }
+}
+
+// sum_{k0,k1,k2} f0[k0] f1[k1] f2[k2] V[k0,k1,k2] over k_c <= n_c (n0 + n1 + n2 <= Lx)
+__device__ __forceinline__ double contract3(const double* f0, int n0, const double* f1, int n1,
+                                            const double* f2, int n2, const double* V, int Lx) {
+  double s0 = 0.0;
+  for (int k0 = 0; k0 <= n0; ++k0) {
+    if (f0[k0] == 0.0) continue;
+    double s1 = 0.0;
+    for (int k1 = 0; k1 <= n1; ++k1) {
+      if (f1[k1] == 0.0) continue;
+      double s2 = 0.0;
+      for (int k2 = 0; k2 <= n2; ++k2) s2 = fma(f2[k2], V[mono_index(k0, k1, k2, Lx)], s2);
+      s1 = fma(f1[k1], s2, s1);
+    }
+    s0 = fma(f0[k0], s1, s0);
+  }
+  return s0;
+}
+
 // (1/2) grad phi_a . grad phi_b integrated against the potential, from the pair's V
-// tensor of degree Lx (xelem: the binomial contraction of one shifted pair product).
+// tensor of degree Lx: per dimension d the product d_d phi_a d_d phi_b is the 1-D factor
+// u' w' in d times u w in the other two, each expanded in powers of (x - A).
 __device__ double xtau(const int* a, const int* b, double aa, double ab, const double (*pw)[6],
                        const double* V, int Lx) {
-  double s = 0.0;
-  for (int d = 0; d < 3; ++d)
-    for (int sa = -1; sa <= 1; sa += 2)
-      for (int sb = -1; sb <= 1; sb += 2) {
-        const double c = dcoef(a[d], sa, aa) * dcoef(b[d], sb, ab);
-        if (c == 0.0) continue;
-        int a2[3] = {a[0], a[1], a[2]}, b2[3] = {b[0], b[1], b[2]};
-        a2[d] += sa;
-        b2[d] += sb;
-        s += c * xelem(a2[0], a2[1], a2[2], b2[0], b2[1], b2[2], pw, V, Lx);
-      }
+  double P0[3][10], P1[3][10];
+  for (int c = 0; c < 3; ++c) {
+    prod_1d(a[c], b[c], 0, 0, aa, ab, pw[c], P0[c]);
+    prod_1d(a[c], b[c], 1, 1, aa, ab, pw[c], P1[c]);
+  }
+  const int n0[3] = {a[0] + b[0], a[1] + b[1], a[2] + b[2]};
+  double s = contract3(P1[0], n0[0] + 2, P0[1], n0[1], P0[2], n0[2], V, Lx);
+  s += contract3(P0[0], n0[0], P1[1], n0[1] + 2, P0[2], n0[2], V, Lx);
+  s += contract3(P0[0], n0[0], P0[1], n0[1], P1[2], n0[2] + 2, V, Lx);
   return 0.5 * s;
 }
 
@@ -1568,36 +1612,18 @@ __global__ void assemble_V_tau_kernel(long long ngroups, const int4* __restrict_
   }
 }
 
-// Second derivative d^2/dx_d dx_e of a monomial with exponents c: up to four shifted
-// monomials (shift vectors in s, coefficients in w); returns the number of terms.
-__device__ int d2terms(const int* c, int d, int e, double alpha, int (*s)[3], double* w) {
-  int n = 0;
-  if (d != e) {
-    for (int sd = -1; sd <= 1; sd += 2)
-      for (int se = -1; se <= 1; se += 2) {
-        s[n][0] = s[n][1] = s[n][2] = 0;
-        s[n][d] = sd;
-        s[n][e] = se;
-        w[n++] = dcoef(c[d], sd, alpha) * dcoef(c[e], se, alpha);
-      }
-  } else {
-    const double cd = (double)c[d];
-    const int sh[3] = {-2, 0, 2};
-    const double ww[3] = {cd * (cd - 1.0), -2.0 * alpha * (2.0 * cd + 1.0), 4.0 * alpha * alpha};
-    for (int k = 0; k < 3; ++k) {
-      s[n][0] = s[n][1] = s[n][2] = 0;
-      s[n][d] = sh[k];
-      w[n++] = ww[k];
-    }
-  }
-  return n;
-}
-
 // Nuclear gradient of <v_tau, tau(D)> per pair from its degree-(L+3) V tensor: the centre
 // derivative of grad phi_a is minus its Hessian in x, so
 //   dE/dA_d = -w pref (1/2) sum_mu,nu D_mu,nu sum_e <d_d d_e phi_a, d_e phi_b>,
-//   dE/dB_d = -w pref (1/2) sum_mu,nu D_mu,nu sum_e <d_e phi_a, d_d d_e phi_b>,
-// each bracket a sum of shifted pair products (xelem).  One thread per pair.
+//   dE/dB_d = -w pref (1/2) sum_mu,nu D_mu,nu sum_e <d_e phi_a, d_d d_e phi_b>.
+// Every bracket is a product over the three dimensions of 1-D factors
+// u^(i)(x) w^(j)(x), u = (x - A)^a e^{-alpha_a (x - A)^2} and w likewise about B, i and j
+// the derivative orders in that dimension: (2,1) or (1,0)/(1,1) for the A brackets,
+// (1,2) or (0,1)/(1,1) for the B brackets, (0,0) elsewhere.  Per (mu, nu) the six 1-D
+// products of each dimension are expanded once in powers of (x - A) (Eq. binomial), and
+// each bracket is the triple contraction of three of them with V.  One thread per pair
+// (pairs of one class are adjacent, so the threads of a warp do equal work).
+
 __global__ void grad_tau_pair_kernel(long long np, const int4* __restrict__ ids,
                                      const int4* __restrict__ ids2, const double* __restrict__ geo,
                                      const double* __restrict__ pref,
@@ -1623,9 +1649,11 @@ __global__ void grad_tau_pair_kernel(long long np, const int4* __restrict__ ids,
   }
   const double* Vp = coef + coef_off[p];
   const double scale = -0.5 * (double)ids2[p].z * pref[p];
+  // derivative orders (i, j) of the six 1-D products: 00, 10, 01, 11, 21, 12
+  const int ti[6] = {0, 1, 0, 1, 2, 1}, tj[6] = {0, 0, 1, 1, 1, 2};
   double gA[3] = {0.0, 0.0, 0.0}, gB[3] = {0.0, 0.0, 0.0};
-  int s2[4][3];
-  double w2[4];
+  double P[3][6][10];
+  int deg[3][6];
   for (int mu = 0; mu < na; ++mu) {
     int a[3];
     cart_comp(la, mu, a);
@@ -1634,31 +1662,29 @@ __global__ void grad_tau_pair_kernel(long long np, const int4* __restrict__ ids,
       int b[3];
       cart_comp(lb, nu, b);
       const double dmn = scale * Drow[nu];
+      for (int c = 0; c < 3; ++c)
+        for (int t = 0; t < 6; ++t) {
+          prod_1d(a[c], b[c], ti[t], tj[t], aa, ab, pw[c], P[c][t]);
+          deg[c][t] = a[c] + b[c] + ti[t] + tj[t];
+        }
       for (int d = 0; d < 3; ++d) {
+        const int e1 = (d + 1) % 3, e2 = (d + 2) % 3;
+        // types per dimension of the brackets, dimension order (d, e1, e2) mapped to (0,1,2)
+        int tA[3][3], tB[3][3];
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 3; ++c) tA[r][c] = tB[r][c] = 0;
+        tA[0][d] = 4;                 // e = d: (2,1) in d
+        tA[1][d] = 1; tA[1][e1] = 3;  // e = e1: (1,0) in d, (1,1) in e1
+        tA[2][d] = 1; tA[2][e2] = 3;
+        tB[0][d] = 5;                 // e = d: (1,2) in d
+        tB[1][d] = 2; tB[1][e1] = 3;  // e = e1: (0,1) in d, (1,1) in e1
+        tB[2][d] = 2; tB[2][e2] = 3;
         double sA = 0.0, sB = 0.0;
-        for (int e = 0; e < 3; ++e) {
-          // <d_d d_e phi_a, d_e phi_b>
-          const int n2a = d2terms(a, d, e, aa, s2, w2);
-          for (int i = 0; i < n2a; ++i)
-            for (int sb = -1; sb <= 1; sb += 2) {
-              const double c = w2[i] * dcoef(b[e], sb, ab);
-              if (c == 0.0) continue;
-              int b2[3] = {b[0], b[1], b[2]};
-              b2[e] += sb;
-              sA += c * xelem(a[0] + s2[i][0], a[1] + s2[i][1], a[2] + s2[i][2], b2[0], b2[1],
-                              b2[2], pw, Vp, Lx);
-            }
-          // <d_e phi_a, d_d d_e phi_b>
-          const int n2b = d2terms(b, d, e, ab, s2, w2);
-          for (int i = 0; i < n2b; ++i)
-            for (int sa = -1; sa <= 1; sa += 2) {
-              const double c = w2[i] * dcoef(a[e], sa, aa);
-              if (c == 0.0) continue;
-              int a2[3] = {a[0], a[1], a[2]};
-              a2[e] += sa;
-              sB += c * xelem(a2[0], a2[1], a2[2], b[0] + s2[i][0], b[1] + s2[i][1],
-                              b[2] + s2[i][2], pw, Vp, Lx);
-            }
+        for (int r = 0; r < 3; ++r) {
+          sA += contract3(P[0][tA[r][0]], deg[0][tA[r][0]], P[1][tA[r][1]], deg[1][tA[r][1]],
+                          P[2][tA[r][2]], deg[2][tA[r][2]], Vp, Lx);
+          sB += contract3(P[0][tB[r][0]], deg[0][tB[r][0]], P[1][tB[r][1]], deg[1][tB[r][1]],
+                          P[2][tB[r][2]], deg[2][tB[r][2]], Vp, Lx);
         }
         gA[d] += dmn * sA;
         gB[d] += dmn * sB;

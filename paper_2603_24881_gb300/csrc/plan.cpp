@@ -226,7 +226,7 @@ struct PairTmp {
   int img[3];
   int level;
   int lo[3], hi[3];
-  double4 q;  // GPW_FAST_BLOCK_PRUNE: fractional coordinates of P and R_p
+  PairQ q;  // GPW_FAST_BLOCK_PRUNE: fractional coordinates of P and R_p
 };
 
 struct Seg {
@@ -263,7 +263,7 @@ void segments(int lo, int hi, int N, int T, std::vector<Seg>* out) {
 
 struct PairBox {
   int level, lo[3], hi[3];
-  double4 q;  // GPW_FAST_BLOCK_PRUNE: fractional coordinates of P and R_p
+  PairQ q;  // GPW_FAST_BLOCK_PRUNE: fractional coordinates of P and R_p
 };
 
 // Spare task-record buffers of committed plans, kept with their pages so that the next
@@ -997,9 +997,9 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
                       fp[d] = P[d] / plan->L[d];
                     }
                   }
-                  t.q = make_double4(fp[0], fp[1], fp[2], Rp);
+                  t.q = PairQ{fp[0], fp[1], fp[2], Rp};
                 } else {
-                  t.q = make_double4(0.0, 0.0, 0.0, 0.0);
+                  t.q = PairQ{0.0, 0.0, 0.0, 0.0};
                 }
                 t.a = a;
                 t.b = b;

@@ -15,7 +15,7 @@ struct HostArrays {
   std::vector<int4> task_c, task_i;   // 2 int4 per task
   std::vector<long long> sub_off_c, sub_off_i;
   std::vector<long long> toff_c, toff_i;  // per-pair task prefix sums (device-built lists)
-  std::vector<double4> prune;  // GPW_FAST_BLOCK_PRUNE: per pair {f_0(P), f_1(P), f_2(P), R_p}
+  std::vector<PairQ> prune;  // GPW_FAST_BLOCK_PRUNE: per pair {f_0(P), f_1(P), f_2(P), R_p}
   std::vector<double> mono_t;  // non-orthogonal cells: monomial transforms per level
   std::vector<int4> work_c, work_i;   // {plan slot, level, sub-box, tasks}
   std::vector<int4> groups;
@@ -52,7 +52,7 @@ long long task_sort_bytes(const Plan& P);
 // the largest slab distance df_d / blen_d and sqrt(lam sum df_d^2).  Plain correctly
 // rounded operations, so that the host and the device builders (which spell out every
 // rounding) decide alike.
-inline bool block_beyond(const double4& q, const int* a, const int* b, const int* N,
+inline bool block_beyond(const PairQ& q, const int* a, const int* b, const int* N,
                          const double* blen, bool ortho, double lam) {
   const double fp[3] = {q.x, q.y, q.z};
   double f[3], s[3];

@@ -37,7 +37,7 @@ struct TaskGeom {
 
 // block_beyond (plan_host.h) with every rounding spelt out, so that it decides as the host
 // builder does: the task box [a_d, b_d] lies wholly farther than R_p from P
-__device__ __forceinline__ bool block_beyond_d(const double4 q, const long long* a,
+__device__ __forceinline__ bool block_beyond_d(const PairQ q, const long long* a,
                                                const long long* b, const int* N,
                                                const double* blen, int ortho, double lam) {
   const double fp[3] = {q.x, q.y, q.z};
@@ -144,7 +144,7 @@ __host__ __device__ __forceinline__ TaskPos locate(const TaskGeom& G, const int4
 __global__ void task_keys_kernel(TaskGeom G, const int4* __restrict__ hot_a,
                                  const int4* __restrict__ hot_b,
                                  const long long* __restrict__ toff,
-                                 const double4* __restrict__ pq, unsigned* __restrict__ keys,
+                                 const PairQ* __restrict__ pq, unsigned* __restrict__ keys,
                                  unsigned* __restrict__ vals) {
   for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < G.nent;
        t += (long long)gridDim.x * blockDim.x) {
@@ -295,12 +295,12 @@ int build_tasks_device(Plan* P, HostArrays& H, cudaStream_t s, long long* bytes)
   for (int i = 0; i < 4; ++i) kv[i] = reinterpret_cast<unsigned*>(scratch + 2 * toff_b + i * kv_b);
   void* tmp = scratch + 2 * toff_b + 4 * kv_b;
   int out = GPW_OK;
-  double4* pq = nullptr;  // the block screening's per-pair data (fractional P, R_p)
+  PairQ* pq = nullptr;  // the block screening's per-pair data (fractional P, R_p)
   auto body = [&]() -> int {
     if (P->prune) {
-      GPW_TCK(cudaMallocAsync((void**)&pq, sizeof(double4) * (size_t)std::max<long long>(np, 1), s));
+      GPW_TCK(cudaMallocAsync((void**)&pq, sizeof(PairQ) * (size_t)std::max<long long>(np, 1), s));
       if (np > 0)
-        GPW_TCK(cudaMemcpyAsync(pq, H.prune.data(), sizeof(double4) * (size_t)np,
+        GPW_TCK(cudaMemcpyAsync(pq, H.prune.data(), sizeof(PairQ) * (size_t)np,
                                 cudaMemcpyHostToDevice, s));
     }
     GPW_TCK(cudaMemcpyAsync(toff_c, H.toff_c.data(), sizeof(long long) * (size_t)(np + 1),
