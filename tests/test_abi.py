@@ -51,3 +51,12 @@ def test_tile_support_mask_without_gpu():
         assert lib.gpw_tile_supported(*t) == 2, t
     assert lib.gpw_tile_supported(3, 8, 16) == 0
     assert lib.gpw_tile_supported(0, 0, 0) == 0
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    # no CPU fallback: without the built library (and without building it) loading raises
+    monkeypatch.setattr(binding, "_LIB", None)
+    monkeypatch.setattr(binding._build, "LIB", str(tmp_path / "libgpw.so"))
+    import pytest
+    with pytest.raises(RuntimeError):
+        binding.load(build_if_missing=False)
