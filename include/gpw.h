@@ -12,7 +12,8 @@
  *   - eval_mat:     the two-electron Fock matrix of Eq. (J) / (J_wrap) for a given
  *                   real-space potential, integrated on the same levels;
  *   - eval_mat_ip1: the Hxc part of the nuclear gradient (Algorithm 3);
- *   - fock:         rho -> Poisson (Eqs. vH, vHG) + LDA exchange -> V.
+ *   - fock:         rho -> Poisson (Eqs. vH, vHG) + LDA or PBE exchange -> V;
+ *   - the kinetic-energy density of meta-GGA functionals, its Fock term and gradient.
  *
  * Conventions
  *   Units: Bohr and Hartree.  Any lattice (rows a1, a2, a3).  Non-orthogonal cells
@@ -28,7 +29,8 @@
  *   The caller owns every D, rho, v, V and gradient buffer: device memory, FP64,
  *   contiguous, unless a parameter says "host".  The plan owns its pair tables,
  *   level grids, spectra, cuFFT plans and scratch, all allocated by gpw_plan; the
- *   evaluation calls allocate nothing.
+ *   evaluation calls allocate nothing (gpw_fock_grad_host makes the plan's device
+ *   copies of its host buffers on its first call).
  *
  * Streams
  *   Every call is asynchronous on `stream` (a cudaStream_t; NULL = legacy default)
@@ -63,7 +65,7 @@ extern "C" {
 #define GPW_STRICT 0            /* default: the truncation definition of the paper */
 #define GPW_TAU 1               /* also build the kinetic-energy-density (meta-GGA) data:
                                    1-D tables to degree L+3 and larger per-pair buffers;
-                                   shells up to d (gpw_eval_tau, gpw_eval_mat_tau*) */
+                                   shells up to f (gpw_eval_tau, gpw_eval_mat_tau*) */
 #define GPW_HOST_TASKS 2        /* build the sub-box task records and work lists on the
                                    host in gpw_plan_prepare.  Default: the host only
                                    counts each pair's tasks and gpw_plan_commit builds
@@ -79,8 +81,10 @@ extern "C" {
                                    definition: densities and energies move by tau-sized
                                    amounts (checked at 1e-6 relative).  Integration keeps
                                    every task.  Orthorhombic cells use the distance to the
-                                   task's box; non-orthogonal cells its largest distance
-                                   across the lattice-plane slabs, a lower bound. */
+                                   task's box; non-orthogonal cells two lower bounds of it
+                                   (the largest distance across the lattice-plane slabs,
+                                   and the fractional distance times the square root of the
+                                   lattice metric's smallest eigenvalue). */
 #define GPW_DEBUG_CHECKS 8      /* extra device checks, read with gpw_check_device: at
                                    commit every task record of both lists is checked
                                    against its sub-box and its pair's box (code 17), and
@@ -155,7 +159,8 @@ typedef struct {
   long long pair_points;                 /* sum over pairs of box volumes */
   long long pair_points_level[GPW_MAX_LEVELS];
   long long pair_points_L[8];            /* by la + lb */
-  long long nentries;                    /* (pair, sub-box) tasks */
+  long long nentries;                    /* (pair, sub-box) collocation tasks (those kept,
+                                            once committed with GPW_FAST_BLOCK_PRUNE) */
   long long device_bytes;                /* device memory owned by the plan */
   double flops_rho;    /* model FP64 flops of one eval_rho grid pass: 2 (L+1) per pair-point */
   double flops_mat;    /* same for eval_mat */
@@ -219,8 +224,9 @@ int gpw_plan_pairs(gpw_plan_t plan, int* ab, int* img, int* level, int* lo, int*
  * the collocation list, 1 the integration list.  *nent tasks (8 ints each: the two int4
  * records p, m | L << 24, u, rank and t0, t1, t2, W offset), *nsub + 1 sub-box CSR
  * offsets, *nwork work items (4 ints: plan slot, level | chunk << 4, sub-box, tasks).
- * The counts are written first, so a call with NULL buffers sizes them.  Synchronises
- * the device. */
+ * The counts are written first, so a call with NULL buffers sizes them.  With
+ * GPW_FAST_BLOCK_PRUNE the collocation list holds the tasks kept (their rank field still
+ * numbers all of the pair's tasks).  Synchronises the device. */
 int gpw_plan_task_lists(gpw_plan_t plan, int integ, long long* nent, long long* nsub,
                         long long* nwork, int* tasks, long long* sub_off, int* work);
 
