@@ -142,7 +142,7 @@ size_t fft_estimate(const int* N, cufftType type) {
 void free_plan(Plan* P, cudaStream_t stream = nullptr, bool sync = true) {
   DeviceArrays& d = P->d;
   void* ptrs[] = {d.hot_a, d.hot_b, d.ids, d.ids2, d.geo, d.cab, d.pref, d.tab_off,
-                  d.coef_off, d.part_off, d.xt_off, d.task_c, d.sub_off_c, d.work_c, d.task_i, d.sub_off_i, d.work_i, d.groups, d.atom_off,
+                  d.coef_off, d.part_off, d.xt_off, d.yt_off, d.task_c, d.sub_off_c, d.work_c, d.task_i, d.sub_off_i, d.work_i, d.groups, d.atom_off,
                   d.atom_list, d.tab, d.coef, d.part, d.pgrad, d.grids, d.spec, d.fspec,
                   d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs, d.view, d.g2tab,
                   d.g1tab, d.grad3, d.fspec3, d.mono_t, d.xfer_D, d.xfer_V, d.xfer_g,
@@ -170,7 +170,7 @@ long long estimate_bytes(const Plan& P, const HostArrays& H) {
   long long b = 0;
   b += sz((long long)H.hot_a.size(), sizeof(int4)) * 4;                 // hot_a, hot_b, ids, ids2
   b += sz((long long)H.geo.size(), sizeof(double)) + sz(P.npairs, sizeof(double)) * 2;
-  b += sz(P.npairs, sizeof(long long)) * 4;
+  b += sz(P.npairs, sizeof(long long)) * 5;  // tab, coef, part, xt and yt offsets
   if (P.tasks_on_device) {
     // records and offsets are sized by the counts; the work lists by their bound (a
     // sub-box holds at most one collocation item and 1 + tasks / chunk integration items)
@@ -231,6 +231,7 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
   GPW_TRY(upload(&d.coef_off, H.coef_off, &b));
   GPW_TRY(upload(&d.part_off, H.part_off, &b));
   GPW_TRY(upload(&d.xt_off, H.xt_off, &b));
+  GPW_TRY(upload(&d.yt_off, H.yt_off, &b));
   if (!P->tasks_on_device) {
     GPW_TRY(upload(&d.task_c, H.task_c, &b));
     GPW_TRY(upload(&d.sub_off_c, H.sub_off_c, &b));

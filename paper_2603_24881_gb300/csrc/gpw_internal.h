@@ -98,10 +98,12 @@ struct PlanView {
   const long long* coef_off;
   const long long* part_off;
   const long long* xt_off;
+  const long long* yt_off;
   const double* tab;
   const double* coef;
   double* part;
   const double* xt;
+  const double* yt;
   double* grids;
   int* err;
   int chunk_i;  // tasks per integration work item (items carry level | chunk << 4)
@@ -124,6 +126,7 @@ struct DeviceArrays {
   long long* coef_off = nullptr;  // D tensor (rho) / reduced V tensor (stride nc3(L+1))
   long long* part_off = nullptr;  // per-pair block of task W tensors (nc2(L+1) n0 ns12)
   long long* xt_off = nullptr;    // x-contracted D tables (nc2(L) rows of n0)
+  long long* yt_off = nullptr;    // x- and y-contracted D tables (L+1 planes of n0 x n1)
   // tasks of the collocation (c) and integration (i) sub-box shapes
   int4* task_c = nullptr;     // 2 per task: {pair, m|L, u, rank}, {t|n per dimension}
   long long* sub_off_c = nullptr;  // CSR offsets over all sub-boxes of all levels
@@ -188,6 +191,7 @@ struct Plan {
   double prune_blen[3] = {0, 0, 0};  // |b_d| of the block screening (1 / L_d orthorhombic)
   double prune_lam = 0;      // a lower bound of the lattice metric's smallest eigenvalue
   long long tab_total = 0, coef_total = 0, part_total = 0, xt_total = 0;
+  long long yt_base = 0, yt_total = 0;  // the y-contracted tables: part[yt_base, + yt_total)
   long long grid_total = 0, spec_total = 0, fine_n = 0, fine_spec_n = 0;
   long long pair_points = 0;
   long long pair_points_level[GPW_MAX_LEVELS] = {0};

@@ -256,6 +256,45 @@ __global__ void xcontract_kernel(long long np, const int4* __restrict__ hot_a,
   }
 }
 
+// Second contraction of collocation, also once per pair, over its box extents n0 x n1:
+//   Y[l2](i0, i1) = sum_{l1 <= L - l2} X[l2,l1](i0) g1[l1](i1)
+// (times the cross factor R01(i0, i1) of a non-orthogonal cell), stored as L + 1 planes of
+// n0 x n1 (i1 fastest).  A pair box spans several sub-boxes along z; each of those tasks
+// reads its m0 x m1 window of Y and is left with the z contraction alone.  One warp per
+// pair, one lane per (i0, i1): the l2 and l1 loops run the pair's trip counts in every
+// lane, and the lanes write consecutive entries.
+__global__ void ycontract_kernel(long long np, const int4* __restrict__ hot_a,
+                                 const int4* __restrict__ hot_b,
+                                 const long long* __restrict__ tab_off, const double* __restrict__ tab,
+                                 const long long* __restrict__ xt_off, const double* __restrict__ xt,
+                                 const long long* __restrict__ yt_off, double* __restrict__ yt,
+                                 int ldeg, int xr, int skew) {
+  const int lane = threadIdx.x & 31;
+  long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long sw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long p = gw; p < np; p += sw) {
+    const int Lp = hot_a[p].w, L = Lp + ldeg;
+    const int n0 = hot_b[p].x, n1 = hot_b[p].y, n2 = hot_b[p].z;
+    const int trows = Lp + 2 + xr;  // rows of each 1-D table of the pair
+    const double* g1 = tab + tab_off[p] + (long long)trows * n0;
+    const double* r01 = tab + tab_off[p] + (long long)trows * (n0 + n1 + n2);  // [n0][n1]
+    const double* X = xt + xt_off[p];
+    double* out = yt + yt_off[p];
+    const long long n01 = (long long)n0 * n1;
+    for (long long it = lane; it < n01; it += 32) {
+      const int i0 = (int)(it / n1), i1 = (int)(it - (long long)i0 * n1);
+      const double f = skew ? r01[it] : 1.0;
+      int row = 0;  // X row of (l2, 0): rows run over l2, then l1 <= L - l2
+      for (int l2 = 0; l2 <= L; ++l2) {
+        double a = 0.0;
+        for (int l1 = 0; l1 <= L - l2; ++l1) a = fma(X[(long long)(row + l1) * n0 + i0], g1[l1 * n1 + i1], a);
+        row += L + 1 - l2;
+        out[l2 * n01 + it] = skew ? a * f : a;
+      }
+    }
+  }
+}
+
 // A task is one (pair, sub-box copy) intersection, precomputed by the plan as two int4:
 //   r0 = {pair, m0 | m1 << 8 | m2 << 16 | L << 24, u0 | u1 << 8 | u2 << 16, rank}
 //   r1 = {t0 | n0 << 16, t1 | n1 << 16, t2 | n2 << 16, 0}
@@ -338,48 +377,25 @@ __device__ __forceinline__ void stage_yz_async(const double* tb, const Task& tk,
   }
 }
 
-// The two per-task contractions of collocation for a pair of total degree L (a compile-
-// time constant, so both contractions unroll completely):
-//   T2[l2](q) = sum_{l1 <= L - l2} X[l2,l1](i0) g1[l1](i1),   q = i0 m1 + i1
+// The per-task contraction of collocation for a pair of total degree L (a compile-time
+// constant, so it unrolls completely), from the task's window of the pair's y-contracted
+// table (ycontract_kernel) staged as sT2[l2 Q + q], q = i0 m1 + i1:
 //   acc(q, i2) += sum_{l2 <= L} T2[l2](q) g2[l2](i2)
-// Items are spread over the lanes flat (it = l2 m01 + q, then it = q m2 + i2) so that
-// partial tasks keep the lanes busy; the item index advances by 32 with a carry.
-// SK: 0 orthogonal rows; 1 non-orthogonal, every cross factor (R01 always, R02 and R12
-// when zc); 2 non-orthogonal with the third row orthogonal to the others (R01 only)
+// The items (q, i2) are spread over the lanes flat so that partial tasks keep the lanes
+// busy; the item index advances by 32 with a carry.
+// SK: 0 orthogonal rows or, on a non-orthogonal cell, only the R01 cross factor (folded
+// into the table); 1 non-orthogonal cells, of which those with zc (the third row not
+// orthogonal to the others) also take R02(i0, i2) R12(i1, i2) at every point, from the
+// windows in sR ([T0][T2] then [T1][T2])
 template <int L, int T0, int T1, int T2, int SK = 0>
-__device__ __forceinline__ void colloc_task(int m01, int m2, const double* __restrict__ sX,
-                                            const double* __restrict__ sg1,
-                                            const double* __restrict__ sg2, double* __restrict__ sT2,
+__device__ __forceinline__ void colloc_task(int m01, int m2, const double* __restrict__ sT2,
+                                            const double* __restrict__ sg2,
                                             const int* __restrict__ s_row,
                                             const int* __restrict__ s_qi, double* __restrict__ acc,
                                             int lane, const double* __restrict__ sR = nullptr,
-                                            bool zc = true) {
+                                            bool zc = false) {
   constexpr int Q = T0 * T1;
-  const float inv01 = __frcp_rn((float)m01), inv2 = __frcp_rn((float)m2);
-  {
-    const int dl = fdiv(32, inv01), dq = 32 - dl * m01;
-    int l2 = fdiv(lane, inv01), q = lane - l2 * m01;
-    for (int base = 0; base < (L + 1) * m01; base += 32) {
-      if (l2 <= L) {
-        const int pi = s_qi[q];
-        const double* xr = sX + (l2 * (L + 1) - ((l2 * (l2 - 1)) >> 1)) * T0 + (pi & 255);
-        const double* gr = sg1 + (pi >> 8);
-        double a = 0.0;
-#pragma unroll
-        for (int l1 = 0; l1 <= L; ++l1)
-          if (l1 <= L - l2) a = fma(xr[l1 * T0], gr[l1 * T1], a);
-        if constexpr (SK != 0) a *= sR[(pi & 255) * T1 + (pi >> 8)];  // R01(i0, i1)
-        sT2[l2 * Q + q] = a;
-      }
-      q += dq;
-      l2 += dl;
-      if (q >= m01) {
-        q -= m01;
-        ++l2;
-      }
-    }
-  }
-  __syncwarp();
+  const float inv2 = __frcp_rn((float)m2);
   {
     const int dq = fdiv(32, inv2), di = 32 - dq * m2;
     int qA = fdiv(lane, inv2), iA = lane - qA * m2;
@@ -402,8 +418,8 @@ __device__ __forceinline__ void colloc_task(int m01, int m2, const double* __res
       if constexpr (SK == 1) zcross = zc;
       if (zcross) {
         // non-orthogonal cell: R01 is in T2 already; times R02(i0, i2) R12(i1, i2)
-        // (zc false: the third row is orthogonal to the others, R02 = R12 = 1)
-        const double* r02 = sR + T0 * T1;
+        // (zc false: the plan's third row is orthogonal to the others, R02 = R12 = 1)
+        const double* r02 = sR;
         const double* r12 = r02 + T0 * T2;
         const int pa_i = s_qi[qa], pb_i = s_qi[qb];
         if (base + 32 < items) {
@@ -491,15 +507,41 @@ __device__ __forceinline__ void stage_cross(const double* __restrict__ tab, long
   }
 }
 
+// Collocation's cross-factor windows (non-orthogonal cells with every cross term): R02
+// [T0][T2] then R12 [T1][T2] (R01 is in the y-contracted table)
+template <int T0, int T1, int T2>
+struct CrossWindowsZ {
+  static constexpr int kSize = T0 * T2 + T1 * T2;
+};
+
+template <int T0, int T1, int T2>
+__device__ __forceinline__ void stage_cross_z(const double* __restrict__ tab, long long toff,
+                                              const Task& tk, int xr, double* __restrict__ sR,
+                                              int lane) {
+  const int n0 = tk.n[0], n1 = tk.n[1], n2 = tk.n[2];
+  const int m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
+  const int t0 = tk.t[0], t1 = tk.t[1], t2 = tk.t[2];
+  const double* r02 = tab + toff + (long long)(tk.L + 2 + xr) * (n0 + n1 + n2) + (long long)n0 * n1;
+  const double* r12 = r02 + (long long)n0 * n2;
+  const float i2f = __frcp_rn((float)m2);
+  for (int it = lane; it < m0 * m2; it += 32) {
+    const int i = fdiv(it, i2f), j = it - i * m2;
+    cp_async8(sR + i * T2 + j, r02 + (long long)(t0 + i) * n2 + t2 + j);
+  }
+  for (int it = lane; it < m1 * m2; it += 32) {
+    const int i = fdiv(it, i2f), j = it - i * m2;
+    cp_async8(sR + T0 * T2 + i * T2 + j, r12 + (long long)(t1 + i) * n2 + t2 + j);
+  }
+}
+
 template <int T0, int T1, int T2>
 struct CollocLayout {
-  // one staging buffer: the task's window of the x-contracted table (nc2(lp - 1) rows of
-  // T0) and the y and z factor windows (lp rows of T1, T2), for lp = lmax + 1 (even
-  // length keeps 16-byte alignment)
-  __host__ __device__ static int buf(int lp) { return (nc2(lp - 1) * T0 + lp * (T1 + T2) + 1) & ~1; }
-  // per-warp staging: two buffers, the T2 intermediate and two row tables (T0*T1 ints
-  // each: q -> accumulator offset of the row, q -> (i0, i1))
-  __host__ __device__ static int stage(int lp) { return 2 * buf(lp) + lp * T0 * T1 + T0 * T1; }
+  // one staging buffer: the task's window of the y-contracted table (lp planes of T0 T1,
+  // compact: plane l2, entry q = i0 m1 + i1) and its z factor window (lp rows of T2)
+  __host__ __device__ static int buf(int lp) { return (lp * (T0 * T1 + T2) + 1) & ~1; }
+  // per-warp staging: two buffers and two row tables (T0*T1 ints each: q -> accumulator
+  // offset of the row, q -> (i0, i1))
+  __host__ __device__ static int stage(int lp) { return 2 * buf(lp) + T0 * T1; }
 };
 
 // ----------------------------------------------------------------------------------
@@ -507,10 +549,10 @@ struct CollocLayout {
 // One thread block per sub-box with tasks; warp w takes tasks w, w + NW, ... of the
 // sub-box's list and accumulates into its own copy of the sub-box in shared memory;
 // the NW copies are summed in a fixed order and written once (coalesced, no atomics).
-// Per task, with m the intersection extents and X the pair's x-contracted table
-// (xcontract_kernel, the first of the three contractions):
-//   T2[l2](i0,i1) = sum_l1 X[l2,l1](i0) g1[l1](i1)           nc2(L) m0 m1 FMAs
-//   rho(i0,i1,i2) += sum_l2 T2[l2](i0,i1) g2[l2](i2)         (L+1) m0 m1 m2
+// The first two of the three contractions are done once per pair beforehand
+// (xcontract_kernel, ycontract_kernel); per task, with m the intersection extents and T2
+// the pair's y-contracted table, only the third remains:
+//   rho(i0,i1,i2) += sum_l2 T2[l2](t0+i0, t1+i1) g2[l2](t2+i2)        (L+1) m0 m1 m2 FMAs
 // The next task's windows are copied in (cp.async) while the current one computes.
 template <int T0, int T1, int T2, int NW, int SK = 0>
 __global__ void __launch_bounds__(NW * 32, 24 / NW)
@@ -528,9 +570,9 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
   const LevelInfo& lv = pv.lc[item.y];
   const int4* __restrict__ task = pv.task_c;
   const long long* __restrict__ tab_off = pv.tab_off;
-  const long long* __restrict__ xt_off = pv.xt_off;
+  const long long* __restrict__ yt_off = pv.yt_off;
   const double* __restrict__ tab = pv.tab;
-  const double* __restrict__ xt = pv.xt;
+  const double* __restrict__ yt = pv.yt;
   double* __restrict__ grids = pv.grids;
   int* __restrict__ err = pv.err;
   const SubBox sb = sub_box<T0, T1, T2>(lv, item.z, pv.sub_off_c);
@@ -538,40 +580,37 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
   double* acc = acc_all + warp * kTileN;
   double* stage_base = acc_all + NW * kTileN + warp * stg;
   const int bufn = Lay::buf(lp);
-  const int xrows = nc2(lp - 1);
-  double* sT2 = stage_base + 2 * bufn;
-  int* s_row = reinterpret_cast<int*>(sT2 + lp * T0 * T1);
-  int* s_qi = s_row + T0 * T1;
+  constexpr int Q = T0 * T1;
+  int* s_row = reinterpret_cast<int*>(stage_base + 2 * bufn);
+  int* s_qi = s_row + Q;
   // non-orthogonal cells: the task's cross-factor windows, one per staging buffer, after
   // the regular per-warp staging
   double* sRb = stage_base + ((Lay::stage(lp) + 1) & ~1);
   const bool zc = SK == 1 && pv.skew != 2;  // cross terms with the third row (R02, R12)
   __syncthreads();
 
-  // staging buffer b: [X window xrows*T0][g1 lp*T1][g2 lp*T2]
-  auto issue = [&](const Task& tk, long long toff, long long xoff, int b) {
-    double* sX = stage_base + b * bufn;
-    double* sg1 = sX + xrows * T0;
-    double* sg2 = sg1 + lp * T1;
+  // staging buffer b: [T2 window lp planes of Q][g2 window lp rows of T2]
+  auto issue = [&](const Task& tk, long long toff, long long yoff, int b) {
+    double* sY = stage_base + b * bufn;
+    double* sg2 = sY + lp * Q;
     const int L = tk.L + ldeg, m0 = tk.m[0], m1 = tk.m[1], m2 = tk.m[2];
+    const int m01 = m0 * m1, n1 = tk.n[1];
+    const long long n01 = (long long)tk.n[0] * n1;
     const int trows = tk.L + 2 + pv.xr;  // table rows of the pair
-    const double* x = xt + xoff + tk.t[0];
-    const double* t1 = tab + toff + trows * tk.n[0] + tk.t[1];
+    const double* y = yt + yoff + (long long)tk.t[0] * n1 + tk.t[1];
     const double* t2 = tab + toff + trows * (tk.n[0] + tk.n[1]) + tk.t[2];
-    const float i0f = __frcp_rn((float)m0), i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
-    for (int it = lane; it < nc2(L) * m0; it += 32) {
-      const int c = fdiv(it, i0f), i = it - c * m0;
-      cp_async8(sX + c * T0 + i, x + c * tk.n[0] + i);
-    }
-    for (int it = lane; it < (L + 1) * m1; it += 32) {
-      const int l = fdiv(it, i1f), i = it - l * m1;
-      cp_async8(sg1 + l * T1 + i, t1 + l * tk.n[1] + i);
+    const float i01f = __frcp_rn((float)m01), i1f = __frcp_rn((float)m1), i2f = __frcp_rn((float)m2);
+    for (int it = lane; it < (L + 1) * m01; it += 32) {
+      const int l = fdiv(it, i01f), q = it - l * m01;
+      const int i0 = fdiv(q, i1f), i1 = q - i0 * m1;
+      cp_async8(sY + l * Q + q, y + l * n01 + (long long)i0 * n1 + i1);
     }
     for (int it = lane; it < (L + 1) * m2; it += 32) {
       const int l = fdiv(it, i2f), i = it - l * m2;
       cp_async8(sg2 + l * T2 + i, t2 + l * tk.n[2] + i);
     }
-    if constexpr (SK != 0) stage_cross<T0, T1, T2>(tab, toff, tk, pv.xr, sRb + b * CrossWindows<T0, T1, T2>::kSize, lane, zc);
+    if constexpr (SK == 1)
+      if (zc) stage_cross_z<T0, T1, T2>(tab, toff, tk, pv.xr, sRb + b * CrossWindowsZ<T0, T1, T2>::kSize, lane);
   };
 
   long long e = sb.eb + warp;
@@ -581,7 +620,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     a0 = __ldg(task + 2 * e);
     a1 = __ldg(task + 2 * e + 1);
     const long long atoff = __ldg(tab_off + a0.x);
-    const long long axoff = __ldg(xt_off + a0.x);
+    const long long axoff = __ldg(yt_off + a0.x);
     const Task tk = decode_task(a0, a1);
     if (task_ok(tk, tk.L + ldeg, lp, sb)) issue(tk, atoff, axoff, 0);
     cp_async_commit();
@@ -590,7 +629,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     b0 = __ldg(task + 2 * (e + NW));
     b1 = __ldg(task + 2 * (e + NW) + 1);
     btoff = __ldg(tab_off + b0.x);
-    bxoff = __ldg(xt_off + b0.x);
+    bxoff = __ldg(yt_off + b0.x);
   }
   int buf = 0;
   for (; e < sb.ee; e += NW, buf ^= 1) {
@@ -613,9 +652,8 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     if (!task_ok(tk, L, lp, sb)) {
       if (lane == 0) set_err(err, 1);
     } else {
-      const double* sX = stage_base + buf * bufn;
-      const double* sg1 = sX + xrows * T0;
-      const double* sg2 = sg1 + lp * T1;
+      const double* sY = stage_base + buf * bufn;
+      const double* sg2 = sY + lp * Q;
       const int m01 = m0 * m1;
       const float inv1 = __frcp_rn((float)m1);
       // per-task row tables: q = i0 m1 + i1 -> (i0, i1) and accumulator offset of the row
@@ -624,11 +662,11 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
         s_qi[q] = i0 | (i1 << 8);
         s_row[q] = ((tk.u[0] + i0) * T1 + (tk.u[1] + i1)) * T2 + tk.u[2];
       }
-      const double* sR = sRb + buf * CrossWindows<T0, T1, T2>::kSize;
+      const double* sR = sRb + buf * CrossWindowsZ<T0, T1, T2>::kSize;
       __syncwarp();
-#define GPW_COLLOC_L(LL)                                                                     \
-  case LL:                                                                                   \
-    colloc_task<LL, T0, T1, T2, SK>(m01, m2, sX, sg1, sg2, sT2, s_row, s_qi, acc, lane, sR, zc); \
+#define GPW_COLLOC_L(LL)                                                              \
+  case LL:                                                                            \
+    colloc_task<LL, T0, T1, T2, SK>(m01, m2, sY, sg2, s_row, s_qi, acc, lane, sR, zc); \
     break;
       switch (L) {
         GPW_COLLOC_L(0) GPW_COLLOC_L(1) GPW_COLLOC_L(2) GPW_COLLOC_L(3) GPW_COLLOC_L(4)
@@ -641,7 +679,7 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
     long long ctoff = btoff, cxoff = bxoff;
     if (e + 2 * NW < sb.ee) {
       ctoff = __ldg(tab_off + c0.x);
-      cxoff = __ldg(xt_off + c0.x);
+      cxoff = __ldg(yt_off + c0.x);
     }
     __syncwarp();
     a0 = b0;
@@ -1869,7 +1907,13 @@ constexpr int kNW = 8;
 
 // per-warp staging doubles of the non-orthogonal variants (cross factors and their rows)
 template <int T0, int T1, int T2>
-int colloc_skew_extra() { return 2 * CrossWindows<T0, T1, T2>::kSize; }
+int colloc_skew_extra(bool zc) { return zc ? 2 * CrossWindowsZ<T0, T1, T2>::kSize : 0; }
+// collocation staging of the non-orthogonal variants (SK = 1 with every cross term adds
+// the R02 and R12 windows)
+template <int T0, int T1, int T2>
+int colloc_skew_stage(bool zc, int lp) {
+  return even(even(CollocLayout<T0, T1, T2>::stage(lp)) + colloc_skew_extra<T0, T1, T2>(zc));
+}
 template <int T0, int T1, int T2>
 int integ_skew_extra(bool zc) {
   return (zc ? IntegLayout<T0, T1, T2>::kSV : 0) + 2 * CrossWindows<T0, T1, T2>::kSize;
@@ -1983,11 +2027,10 @@ cudaError_t configure_kernels(Plan* p) {
     if (!(p->tile[0] == kT0 && p->tile[1] == kT1 && p->tile[2] == kT2 && p->tile_i[0] == kT0 &&
           p->tile_i[1] == kT1 && p->tile_i[2] == kT2))
       return cudaErrorInvalidValue;
-    using CL = CollocLayout<kT0, kT1, kT2>;
     using IL = IntegLayout<kT0, kT1, kT2>;
     const bool zc = p->skew_zc;
     const auto pick = zc ? pick_colloc_warps<kT0, kT1, kT2, 1> : pick_colloc_warps<kT0, kT1, kT2, 2>;
-    p->stg_colloc = even(even(CL::stage(lp)) + colloc_skew_extra<kT0, kT1, kT2>());
+    p->stg_colloc = colloc_skew_stage<kT0, kT1, kT2>(zc, lp);
     if (pick(p->stg_colloc, p->nw_colloc_req, &p->nw_colloc,
                                                 &p->smem_colloc) == 0)
       return cudaErrorInvalidValue;
@@ -2000,7 +2043,7 @@ cudaError_t configure_kernels(Plan* p) {
       return cudaErrorInvalidValue;
     if (p->xr) {
       // kinetic-energy density: collocation at degree L+2, integration at L+2 / L+3
-      p->stg_colloc_t = even(even(CL::stage(p->lmax + 3)) + colloc_skew_extra<kT0, kT1, kT2>());
+      p->stg_colloc_t = colloc_skew_stage<kT0, kT1, kT2>(zc, p->lmax + 3);
       if (pick(p->stg_colloc_t, p->nw_colloc_req,
                                                   &p->nw_colloc_t, &p->smem_colloc_t) == 0)
         return cudaErrorInvalidValue;
@@ -2107,6 +2150,10 @@ cudaError_t launch_xcontract(const Plan& p, cudaStream_t s, int ldeg) {
   xcontract_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, p.d.hot_a, p.d.hot_b, p.d.tab_off, p.d.tab,
                                                 p.d.coef_off, p.d.coef, p.d.xt_off, p.d.tabs, p.d.part,
                                                 ldeg);
+  ++p.launches;
+  ycontract_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, p.d.hot_a, p.d.hot_b, p.d.tab_off, p.d.tab,
+                                                p.d.xt_off, p.d.part, p.d.yt_off, p.d.part + p.yt_base,
+                                                ldeg, p.xr, p.skew ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -2238,8 +2285,7 @@ cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int 
     if (!(tile_c[0] == kT0 && tile_c[1] == kT1 && tile_c[2] == kT2 && tile_i[0] == kT0 &&
           tile_i[1] == kT1 && tile_i[2] == kT2))
       return cudaErrorInvalidValue;
-    colloc->stg = even(even(CollocLayout<kT0, kT1, kT2>::stage(lmax + 1)) +
-                       colloc_skew_extra<kT0, kT1, kT2>());
+    colloc->stg = colloc_skew_stage<kT0, kT1, kT2>(skew == 1, lmax + 1);
     const auto pick = skew == 1 ? pick_colloc_warps<kT0, kT1, kT2, 1> : pick_colloc_warps<kT0, kT1, kT2, 2>;
     if (pick(colloc->stg, nw_req, &colloc->nw, &colloc->smem) == 0)
       return cudaErrorInvalidValue;
@@ -2268,6 +2314,8 @@ PlanView make_view(const Plan& p) {
   v.part = p.d.part;
   v.xt_off = p.d.xt_off;
   v.xt = p.d.part;
+  v.yt_off = p.d.yt_off;
+  v.yt = p.d.part + p.yt_base;
   v.grids = p.d.grids;
   v.err = p.d.err;
   v.chunk_i = p.chunk_i;

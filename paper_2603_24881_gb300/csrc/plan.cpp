@@ -1069,6 +1069,7 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   H->coef_off.resize(np);
   H->part_off.resize(np);
   H->xt_off.resize(np);
+  H->yt_off.resize(np);
   plan->h_ab.resize(2 * np);
   plan->h_img.resize(3 * np);
   plan->h_lev.resize(np);
@@ -1111,7 +1112,7 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     }
     plan->h_lev[p] = t.level;
   }
-  long long tab_total = 0, coef_total = 0, xt_total = 0;
+  long long tab_total = 0, coef_total = 0, xt_total = 0, yt_total = 0;
   int lmax = 0;
   for (long long p = 0; p < np; ++p) {
     const int L = H->hot_a[p].w, lev = H->hot_b[p].w;
@@ -1126,6 +1127,8 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     coef_total += nc3(L + 1 + plan->xr);
     H->xt_off[p] = xt_total;
     xt_total += (long long)nc2(L + plan->xr) * n[0];
+    H->yt_off[p] = yt_total;
+    yt_total += (long long)(L + 1 + plan->xr) * n[0] * n[1];
     long long pts = (long long)n[0] * n[1] * n[2];
     plan->pair_points += pts;
     plan->pair_points_level[lev] += pts;
@@ -1139,6 +1142,8 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   plan->tab_total = tab_total;
   plan->coef_total = coef_total;
   plan->xt_total = xt_total;
+  plan->yt_base = (xt_total + 1) & ~1LL;  // after the x-contracted tables, 16-byte aligned
+  plan->yt_total = yt_total;
 
   // ---- per-level sub-box task lists (CSR), one task per (pair, sub-box, image shift),
   // for the collocation tile and for the integration tile
@@ -1187,7 +1192,9 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   }
   // the part buffer also holds the x-contracted tables of collocation (never live at the
   // same time as the task W tensors)
-  plan->part_total = std::max(part_total, xt_total);
+  // the part buffer holds the task W tensors of the integration, or the two contracted D
+  // tables of the collocation
+  plan->part_total = std::max(part_total, plan->yt_base + yt_total);
 
   if (plan->skew) build_mono_transforms(*plan, &H->mono_t);
 

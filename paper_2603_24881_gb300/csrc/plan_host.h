@@ -11,7 +11,7 @@ namespace gpw {
 struct HostArrays {
   std::vector<int4> hot_a, hot_b, ids, ids2;
   std::vector<double> geo, cab;
-  std::vector<long long> tab_off, coef_off, part_off, xt_off;
+  std::vector<long long> tab_off, coef_off, part_off, xt_off, yt_off;
   std::vector<int4> task_c, task_i;   // 2 int4 per task
   std::vector<long long> sub_off_c, sub_off_i;
   std::vector<long long> toff_c, toff_i;  // per-pair task prefix sums (device-built lists)

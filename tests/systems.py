@@ -129,3 +129,38 @@ def basis_rotation(s: System, Q: np.ndarray) -> np.ndarray:
         M[o:o + b.shape[0], o:o + b.shape[0]] = b
         o += b.shape[0]
     return M
+
+
+def permuted_atoms(s: System, perm) -> tuple:
+    """The same crystal with its atoms listed in another order: new atom i is old atom
+    perm[i], its shells keep their order and are listed atom by atom in the new order, D
+    is reindexed to the new AO order.  Returns (system, ao) with ao[new AO] = old AO, so
+    that quantities indexed by AOs or atoms of the new system are the old ones taken at
+    ao and perm."""
+    import copy
+    perm = np.asarray(perm, dtype=np.int64)
+    off = s.ao_offsets()
+    shells = [sh for a in perm for sh in range(s.nshell) if s.shell_atom[sh] == a]
+    inv = np.empty_like(perm)
+    inv[perm] = np.arange(len(perm))
+    ao = np.concatenate([np.arange(off[sh], off[sh + 1]) for sh in shells]).astype(np.int64)
+    exps, coefs, nprim, poff = [], [], [], []
+    k = 0
+    for sh in shells:
+        o, n = int(s.shell_prim_off[sh]), int(s.shell_nprim[sh])
+        exps.append(s.exponents[o:o + n])
+        coefs.append(s.coeffs[o:o + n])
+        nprim.append(n)
+        poff.append(k)
+        k += n
+    out = copy.copy(s)
+    out.coords = np.ascontiguousarray(s.coords[perm])
+    out.shell_atom = np.ascontiguousarray(inv[s.shell_atom[shells]].astype(np.int32))
+    out.shell_l = np.ascontiguousarray(s.shell_l[shells].astype(np.int32))
+    out.shell_nprim = np.array(nprim, dtype=np.int32)
+    out.shell_prim_off = np.array(poff, dtype=np.int32)
+    out.exponents = np.ascontiguousarray(np.concatenate(exps))
+    out.coeffs = np.ascontiguousarray(np.concatenate(coefs))
+    out.D = np.ascontiguousarray(s.D[np.ix_(ao, ao)])
+    out.name = s.name + "-permuted"
+    return out, ao

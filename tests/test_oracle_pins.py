@@ -674,3 +674,22 @@ def test_collocation_is_reproducible_bit_for_bit():
     t = p.tau_levels(s.D, nthreads=3)
     u = p.tau_levels(s.D, nthreads=3)
     assert all(np.array_equal(x, y) for x, y in zip(t, u))
+
+
+def test_permuting_atoms_permutes_V_and_gradient():
+    # the atoms of a cell listed in another order (shells and D reindexed with them): the
+    # same level densities and energies, V and the gradient reindexed (tau small enough
+    # that a last-bit change of a pair centre cannot move a box edge across a grid point)
+    s = systems.resolved(seed=9, shells=((0, 1), (1, 1), (2, 1)), natm=3).with_tau(1e-14)
+    perm = np.array([2, 0, 1])
+    r, ao = systems.permuted_atoms(s, perm)
+    p, q = oracle.Plan(s), oracle.Plan(r)
+    a, b = p.fock(s.D), q.fock(r.D)
+    for x, y in zip(a["rho_levels"], b["rho_levels"]):
+        assert np.max(np.abs(x - y)) <= 1e-12 * np.max(np.abs(x))
+    assert b["EH"] == pytest.approx(a["EH"], rel=1e-12)
+    assert b["Ex"] == pytest.approx(a["Ex"], rel=1e-12)
+    assert np.max(np.abs(b["V"] - a["V"][np.ix_(ao, ao)])) <= 1e-12 * np.max(np.abs(a["V"]))
+    ga = p.grad_levels(s.D, a["v_levels"])
+    gb = q.grad_levels(r.D, b["v_levels"])
+    assert np.max(np.abs(gb - ga[perm])) <= 1e-11 * max(1.0, np.max(np.abs(ga)))
