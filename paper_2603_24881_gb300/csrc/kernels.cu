@@ -261,14 +261,41 @@ __global__ void xcontract_kernel(long long np, const int4* __restrict__ hot_a,
 // (times the cross factor R01(i0, i1) of a non-orthogonal cell), stored as L + 1 planes of
 // n0 x n1 (i1 fastest).  A pair box spans several sub-boxes along z; each of those tasks
 // reads its m0 x m1 window of Y and is left with the z contraction alone.  One warp per
-// pair, one lane per (i0, i1): the l2 and l1 loops run the pair's trip counts in every
-// lane, and the lanes write consecutive entries.
+// pair, one lane per (i0, i1), the pair's degree a compile-time constant: a lane keeps
+// its g1 column in registers and the lanes write consecutive entries.
+template <int L, bool SKEW>
+__device__ __forceinline__ void ycontract_pair(int n0, int n1, const double* __restrict__ X,
+                                               const double* __restrict__ g1,
+                                               const double* __restrict__ r01,
+                                               double* __restrict__ out, int lane) {
+  const long long n01 = (long long)n0 * n1;
+  for (long long it = lane; it < n01; it += 32) {
+    const int i0 = (int)(it / n1), i1 = (int)(it - (long long)i0 * n1);
+    double g[L + 1];
+#pragma unroll
+    for (int l1 = 0; l1 <= L; ++l1) g[l1] = g1[l1 * n1 + i1];
+    double f = 1.0;
+    if constexpr (SKEW) f = r01[it];
+    const double* x = X + i0;
+#pragma unroll
+    for (int l2 = 0; l2 <= L; ++l2) {
+      // X row of (l2, l1): l2 (L + 1) - l2 (l2 - 1) / 2 + l1
+      const int row = l2 * (L + 1) - ((l2 * (l2 - 1)) >> 1);
+      double a = 0.0;
+#pragma unroll
+      for (int l1 = 0; l1 <= L - l2; ++l1) a = fma(x[(long long)(row + l1) * n0], g[l1], a);
+      if constexpr (SKEW) a *= f;
+      out[l2 * n01 + it] = a;
+    }
+  }
+}
+
 __global__ void ycontract_kernel(long long np, const int4* __restrict__ hot_a,
                                  const int4* __restrict__ hot_b,
                                  const long long* __restrict__ tab_off, const double* __restrict__ tab,
                                  const long long* __restrict__ xt_off, const double* __restrict__ xt,
                                  const long long* __restrict__ yt_off, double* __restrict__ yt,
-                                 int ldeg, int xr, int skew) {
+                                 int ldeg, int xr, int skew, int* __restrict__ err) {
   const int lane = threadIdx.x & 31;
   long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const long long sw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -277,20 +304,22 @@ __global__ void ycontract_kernel(long long np, const int4* __restrict__ hot_a,
     const int n0 = hot_b[p].x, n1 = hot_b[p].y, n2 = hot_b[p].z;
     const int trows = Lp + 2 + xr;  // rows of each 1-D table of the pair
     const double* g1 = tab + tab_off[p] + (long long)trows * n0;
-    const double* r01 = tab + tab_off[p] + (long long)trows * (n0 + n1 + n2);  // [n0][n1]
+    const double* r01 = skew ? tab + tab_off[p] + (long long)trows * (n0 + n1 + n2) : nullptr;  // [n0][n1]
     const double* X = xt + xt_off[p];
     double* out = yt + yt_off[p];
-    const long long n01 = (long long)n0 * n1;
-    for (long long it = lane; it < n01; it += 32) {
-      const int i0 = (int)(it / n1), i1 = (int)(it - (long long)i0 * n1);
-      const double f = skew ? r01[it] : 1.0;
-      int row = 0;  // X row of (l2, 0): rows run over l2, then l1 <= L - l2
-      for (int l2 = 0; l2 <= L; ++l2) {
-        double a = 0.0;
-        for (int l1 = 0; l1 <= L - l2; ++l1) a = fma(X[(long long)(row + l1) * n0 + i0], g1[l1 * n1 + i1], a);
-        row += L + 1 - l2;
-        out[l2 * n01 + it] = skew ? a * f : a;
-      }
+    switch (L) {
+#define GPW_YC(LL) \
+  case LL:         \
+    if (skew)      \
+      ycontract_pair<LL, true>(n0, n1, X, g1, r01, out, lane); \
+    else           \
+      ycontract_pair<LL, false>(n0, n1, X, g1, r01, out, lane); \
+    break;
+      GPW_YC(0) GPW_YC(1) GPW_YC(2) GPW_YC(3) GPW_YC(4) GPW_YC(5) GPW_YC(6) GPW_YC(7) GPW_YC(8)
+      GPW_YC(9)
+#undef GPW_YC
+      default:
+        if (lane == 0) set_err(err, 1);
     }
   }
 }
@@ -2153,7 +2182,7 @@ cudaError_t launch_xcontract(const Plan& p, cudaStream_t s, int ldeg) {
   ++p.launches;
   ycontract_kernel<<<(int)blocks, 256, 0, s>>>(p.npairs, p.d.hot_a, p.d.hot_b, p.d.tab_off, p.d.tab,
                                                 p.d.xt_off, p.d.part, p.d.yt_off, p.d.part + p.yt_base,
-                                                ldeg, p.xr, p.skew ? 1 : 0);
+                                                ldeg, p.xr, p.skew ? 1 : 0, p.d.err);
   return cudaGetLastError();
 }
 

@@ -93,13 +93,15 @@ class BatchPolicy:
     (pair-points); a request costlier than the cap opens a batch of its own, and the
     oldest request always opens the next batch, so no request starves.  small_cost: the
     most a request may cost to ride in a small-request batch (form(small_only=True)),
-    which the server launches on a high-priority stream."""
+    which the server launches on a high-priority stream; lane_cost: the cap on such a
+    batch's summed cost (None: batch_cost), which keeps the high-priority batches short."""
 
     def __init__(self, max_batch: int = 32, batch_cost: float = 2.0e9,
-                 small_cost: float = 4.0e8):
+                 small_cost: float = 4.0e8, lane_cost: float | None = None):
         self.max_batch = int(max_batch)
         self.batch_cost = float(batch_cost)
         self.small_cost = float(small_cost)
+        self.lane_cost = float(batch_cost if lane_cost is None else lane_cost)
 
     @staticmethod
     def expired(req, now: float) -> bool:
@@ -110,7 +112,8 @@ class BatchPolicy:
         past their deadline; the batch is the oldest live request (the oldest small one
         with small_only) plus later ones of its kind (small ones with small_only), in
         order, while the count stays <= max_batch and the summed cost <= max(cap, cost of
-        its first request); keep is the rest, in order."""
+        its first request), cap = lane_cost with small_only, else batch_cost; keep is the
+        rest, in order."""
         expired = [r for r in staged if self.expired(r, now)]
         live = [r for r in staged if not self.expired(r, now)]
         fits = (lambda r: r.cost <= self.small_cost) if small_only else (lambda r: True)
@@ -118,7 +121,7 @@ class BatchPolicy:
         if i0 is None:
             return [], live, expired
         first = live[i0]
-        cap = max(self.batch_cost, first.cost)
+        cap = max(self.lane_cost if small_only else self.batch_cost, first.cost)
         batch, keep, total = [first], live[:i0], first.cost
         for r in live[i0 + 1:]:
             if (r.kind == first.kind and fits(r) and len(batch) < self.max_batch and
@@ -155,21 +158,26 @@ class Server:
     kind fails alone under another explicit shape; batches hold one kind of cell.
     batch_cost: most pair-points (estimated GPU work) per batch, beyond its first
     request; small_cost: the most a request may cost to ride the priority lane;
-    priority_lane: one more stream, of high priority, for batches of small requests.
+    lane_cost: the cap on a priority-lane batch's work (default batch_cost);
+    priority_lane: one more stream for batches of small requests; lane_priority: its
+    CUDA stream priority (-1 high: its blocks take the SMs first; 0 the same as the
+    regular streams: its blocks queue with theirs, so the lane only spares small requests
+    the wait for a free batch slot).
     """
 
     def __init__(self, hbm_budget: int | None = None, max_batch: int = 32, streams: int = 2,
                  host_workers: int | None = None, tile=None, tile_integ=None,
                  colloc_warps=None, integ_chunk=None, tune_with=None, fail_prepare=None,
                  batch_cost: float = 2.0e9, small_cost: float = 4.0e8,
-                 priority_lane: bool = True):
+                 priority_lane: bool = True, lane_priority: int = -1,
+                 lane_cost: float | None = None):
         import torch
         self.torch = torch
         torch.cuda.init()
         free, _ = torch.cuda.mem_get_info()
         self.budget = int(hbm_budget if hbm_budget is not None else 0.7 * free)
         self.max_batch = int(max_batch)
-        self.policy = BatchPolicy(self.max_batch, batch_cost, small_cost)
+        self.policy = BatchPolicy(self.max_batch, batch_cost, small_cost, lane_cost)
         self.plan_kwargs = dict(tile=tile, tile_integ=tile_integ, colloc_warps=colloc_warps,
                                 integ_chunk=integ_chunk)
         self.choice = None
@@ -194,7 +202,7 @@ class Server:
         # the running large batches retire, so small cells do not queue behind them
         self._lane = len(self._streams) if priority_lane else None
         if priority_lane:
-            self._streams.append(torch.cuda.Stream(priority=-1))
+            self._streams.append(torch.cuda.Stream(priority=int(lane_priority)))
         self._batches = [Batch(self.max_batch) for _ in self._streams]
         self._ready = collections.deque()    # prepared, waiting for admission
         self._staged = collections.deque()   # committed, waiting for a batch

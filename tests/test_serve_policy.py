@@ -76,3 +76,13 @@ def test_small_only_batches_for_the_priority_lane():
     assert names(batch) == ["s1", "s2"] and names(keep) == ["big", "mid", "k"]
     batch, keep, _ = p.form([R("big", 5)], now=0.0, small_only=True)
     assert batch == [] and names(keep) == ["big"]
+
+
+def test_lane_batches_have_their_own_cap():
+    p = BatchPolicy(max_batch=8, batch_cost=10.0, small_cost=2.0, lane_cost=3.0)
+    staged = [R("s1", 1), R("s2", 1), R("s3", 1), R("s4", 1)]
+    batch, keep, _ = p.form(staged, now=0.0, small_only=True)
+    assert names(batch) == ["s1", "s2", "s3"] and names(keep) == ["s4"]
+    batch, keep, _ = p.form(staged, now=0.0)            # the regular cap
+    assert names(batch) == ["s1", "s2", "s3", "s4"] and keep == []
+    assert BatchPolicy(batch_cost=7.0).lane_cost == 7.0   # default: the regular cap
