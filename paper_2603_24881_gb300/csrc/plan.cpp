@@ -301,7 +301,9 @@ int plan_threads(long long n) {
 
 std::vector<PairBox> pairs_view(const std::vector<PairTmp>& pairs) {
   std::vector<PairBox> v(pairs.size());
-  for (size_t i = 0; i < pairs.size(); ++i) {
+  const int nthr = plan_threads((long long)pairs.size());
+#pragma omp parallel for num_threads(nthr) schedule(static)
+  for (long long i = 0; i < (long long)pairs.size(); ++i) {
     v[i].level = pairs[i].level;
     v[i].q = pairs[i].q;
     for (int d = 0; d < 3; ++d) {
@@ -915,7 +917,9 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   plan->prune_lam = plan->skew ? metric_lambda_min(plan->lat) : 0.0;
   // atoms are screened in parallel (each thread keeps its own pair list); the sort
   // below fixes one order whatever the thread count
-  const int sthr = plan_threads((long long)prims.size() * prims.size() / 64);
+  // (the work is about one candidate pair per two primitive pairs within reach: 4.4e5
+  // for the 32-water cell's 832 primitives)
+  const int sthr = plan_threads((long long)prims.size() * prims.size() / 2);
   std::vector<std::vector<PairTmp>> tpairs(sthr);
 #pragma omp parallel for num_threads(sthr) schedule(dynamic, 1)
   for (int ia = 0; ia < natm; ++ia) {
@@ -1014,42 +1018,100 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
           }
     }
   }
-  std::vector<PairTmp> pairs;
-  {
-    size_t total = 0;
-    for (const auto& v : tpairs) total += v.size();
-    pairs.reserve(total);
-    for (auto& v : tpairs) {
-      pairs.insert(pairs.end(), v.begin(), v.end());
-      std::vector<PairTmp>().swap(v);
-    }
-  }
   // deterministic order: contracted shell pair, then primitives, then image.  The keys
   // are unique, so the order does not depend on how it is reached: the pairs are
-  // bucketed by their first shell and the buckets sorted in parallel.
+  // bucketed by their first shell and the buckets sorted in parallel.  Where the fields
+  // fit, each pair's key is packed into 64 bits in that order (shells 16 bits each, the
+  // primitives' places in their shells 4 bits each, the image 8 bits per component): the
+  // threads' lists scatter (key, source) records into the buckets in parallel, the
+  // buckets are sorted, and the pairs are gathered once in key order.
+  std::vector<PairTmp> pairs;
   {
-    auto less = [](const PairTmp& x, const PairTmp& y) {
-      if (x.sa != y.sa) return x.sa < y.sa;
-      if (x.sb != y.sb) return x.sb < y.sb;
-      if (x.a != y.a) return x.a < y.a;
-      if (x.b != y.b) return x.b < y.b;
-      for (int d = 0; d < 3; ++d)
-        if (x.img[d] != y.img[d]) return x.img[d] < y.img[d];
-      return false;
-    };
     const int nsh = desc->nshell;
-    std::vector<long long> boff(nsh + 1, 0);
-    for (const PairTmp& t : pairs) boff[t.sa + 1]++;
-    for (int i = 0; i < nsh; ++i) boff[i + 1] += boff[i];
-    std::vector<PairTmp> sorted(pairs.size());
-    {
-      std::vector<long long> fill(boff.begin(), boff.end() - 1);
-      for (const PairTmp& t : pairs) sorted[fill[t.sa]++] = t;
+    const int nt = (int)tpairs.size();
+    std::vector<long long> tbase(nt + 1, 0);
+    for (int t = 0; t < nt; ++t) tbase[t + 1] = tbase[t] + (long long)tpairs[t].size();
+    const long long total = tbase[nt];
+    std::vector<int> shell_first(nsh + 1, 0);
+    bool packable = nsh <= 65536;
+    for (int i = 0; i < nsh; ++i) {
+      shell_first[i + 1] = shell_first[i] + desc->shell_nprim[i];
+      packable = packable && desc->shell_nprim[i] <= 16;
     }
-    const int sthr2 = plan_threads((long long)pairs.size());
+    // per thread list and bucket: counts, then the start of its run in the bucket
+    std::vector<long long> cnt((size_t)nt * (nsh + 1), 0);
+#pragma omp parallel for num_threads(nt) schedule(static, 1) reduction(&& : packable)
+    for (int t = 0; t < nt; ++t) {
+      long long* c = cnt.data() + (size_t)t * (nsh + 1);
+      for (const PairTmp& q : tpairs[t]) {
+        ++c[q.sa];
+        for (int d = 0; d < 3; ++d) packable = packable && q.img[d] >= -128 && q.img[d] < 128;
+      }
+    }
+    std::vector<long long> boff(nsh + 1, 0);
+    {
+      long long run = 0;
+      for (int i = 0; i < nsh; ++i) {
+        boff[i] = run;
+        for (int t = 0; t < nt; ++t) {
+          long long& c = cnt[(size_t)t * (nsh + 1) + i];
+          const long long n = c;
+          c = run;  // now the start of thread t's run in bucket i
+          run += n;
+        }
+      }
+      boff[nsh] = run;
+    }
+    const int sthr2 = plan_threads(total);
+    pairs.resize(total);
+    if (packable) {
+      struct KeyIdx {
+        uint64_t key;
+        long long src;  // tbase[thread] + index in its list
+      };
+      std::vector<KeyIdx> kv(total);
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+      for (int t = 0; t < nt; ++t) {
+        long long* c = cnt.data() + (size_t)t * (nsh + 1);
+        const std::vector<PairTmp>& v = tpairs[t];
+        for (size_t i = 0; i < v.size(); ++i) {
+          const PairTmp& q = v[i];
+          uint64_t k = (uint64_t)q.sa << 48 | (uint64_t)q.sb << 32 |
+                       (uint64_t)(q.a - shell_first[q.sa]) << 28 |
+                       (uint64_t)(q.b - shell_first[q.sb]) << 24;
+          for (int d = 0; d < 3; ++d) k |= (uint64_t)(q.img[d] + 128) << (16 - 8 * d);
+          kv[c[q.sa]++] = KeyIdx{k, tbase[t] + (long long)i};
+        }
+      }
 #pragma omp parallel for num_threads(sthr2) schedule(dynamic, 4)
-    for (int i = 0; i < nsh; ++i) std::sort(sorted.begin() + boff[i], sorted.begin() + boff[i + 1], less);
-    pairs.swap(sorted);
+      for (int i = 0; i < nsh; ++i)
+        std::sort(kv.begin() + boff[i], kv.begin() + boff[i + 1],
+                  [](const KeyIdx& x, const KeyIdx& y) { return x.key < y.key; });
+#pragma omp parallel for num_threads(sthr2) schedule(static)
+      for (long long j = 0; j < total; ++j) {
+        const long long src = kv[j].src;
+        const int t = (int)(std::upper_bound(tbase.begin(), tbase.end(), src) - tbase.begin()) - 1;
+        pairs[j] = tpairs[t][src - tbase[t]];
+      }
+    } else {
+      auto less = [](const PairTmp& x, const PairTmp& y) {
+        if (x.sa != y.sa) return x.sa < y.sa;
+        if (x.sb != y.sb) return x.sb < y.sb;
+        if (x.a != y.a) return x.a < y.a;
+        if (x.b != y.b) return x.b < y.b;
+        for (int d = 0; d < 3; ++d)
+          if (x.img[d] != y.img[d]) return x.img[d] < y.img[d];
+        return false;
+      };
+#pragma omp parallel for num_threads(nt) schedule(static, 1)
+      for (int t = 0; t < nt; ++t) {
+        long long* c = cnt.data() + (size_t)t * (nsh + 1);
+        for (const PairTmp& q : tpairs[t]) pairs[c[q.sa]++] = q;
+      }
+#pragma omp parallel for num_threads(sthr2) schedule(dynamic, 4)
+      for (int i = 0; i < nsh; ++i) std::sort(pairs.begin() + boff[i], pairs.begin() + boff[i + 1], less);
+    }
+    std::vector<std::vector<PairTmp>>().swap(tpairs);
   }
   const long long np = (long long)pairs.size();
   plan->npairs = np;
@@ -1190,8 +1252,6 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     H->part_off[p] = part_total;
     part_total += psize[p];
   }
-  // the part buffer also holds the x-contracted tables of collocation (never live at the
-  // same time as the task W tensors)
   // the part buffer holds the task W tensors of the integration, or the two contracted D
   // tables of the collocation
   plan->part_total = std::max(part_total, plan->yt_base + yt_total);
