@@ -262,7 +262,8 @@ def served_bench(nreq: int) -> dict:
     """The served stream (water boxes of 4..128 molecules, p ~ 1/n, 10% gradients):
     saturated builds/s of the continuous-batching server, then a replay with Poisson
     arrivals at 80% of it for p50/p99 latency, against one plain launch sequence per
-    request, and the largest per-request disagreement between the two."""
+    request, and the largest per-request disagreement between the two; the same two
+    runs with the optional priority lane for small cells, for comparison."""
     import numpy as np
     import workloads
     from paper_2603_24881_gb300.serve import Server, run_plain
@@ -277,24 +278,33 @@ def served_bench(nreq: int) -> dict:
     warm = sorted(first.values())
     with Server() as srv:
         [f.result() for f in [srv.submit(systems[i], True) for i in warm]]
-    with Server() as srv:
-        t0 = time.perf_counter()
-        futs = [srv.submit(s, g) for s, g in zip(systems, grads)]
-        sat = [f.result() for f in futs]
-        t_sat = time.perf_counter() - t0
-        st_sat = dict(srv.stats)
+
+    def saturated(**kw):
+        with Server(**kw) as srv:
+            t0 = time.perf_counter()
+            futs = [srv.submit(s, g) for s, g in zip(systems, grads)]
+            res = [f.result() for f in futs]
+            return res, time.perf_counter() - t0, dict(srv.stats)
+
+    def poisson(rate, **kw):
+        arr = [r.arrival for r in workloads.stream_requests(nreq, seed=4, rate=rate)]
+        with Server(**kw) as srv:
+            t0 = time.perf_counter()
+            futs = []
+            for s, g, ta in zip(systems, grads, arr):
+                dt = ta - (time.perf_counter() - t0)
+                if dt > 0:
+                    time.sleep(dt)
+                futs.append(srv.submit(s, g))
+            res = [f.result() for f in futs]
+            return res, max(r.t_done for r in res) - t0
+
+    sat, t_sat, st_sat = saturated()
     rate = 0.8 * nreq / t_sat
-    arr = [r.arrival for r in workloads.stream_requests(nreq, seed=4, rate=rate)]
-    with Server() as srv:
-        t0 = time.perf_counter()
-        futs = []
-        for s, g, ta in zip(systems, grads, arr):
-            dt = ta - (time.perf_counter() - t0)
-            if dt > 0:
-                time.sleep(dt)
-            futs.append(srv.submit(s, g))
-        pois = [f.result() for f in futs]
-        t_pois = max(r.t_done for r in pois) - t0
+    pois, t_pois = poisson(rate)
+    _, t_sat_l, _ = saturated(priority_lane=True)
+    pois_l, _ = poisson(0.8 * nreq / t_sat_l, priority_lane=True)
+    lat_l = np.array([r.latency for r in pois_l])
     lat = np.array([r.latency for r in pois])
     nwat = np.array([int(sy.natm) // 3 for sy in systems])
     by_size = {int(n): {"requests": int(np.sum(nwat == n)),
@@ -326,6 +336,9 @@ def served_bench(nreq: int) -> dict:
                                      "gpu_batch_and_copy": float(np.percentile(run_ms, 99))},
             "poisson_latency_by_waters": by_size,
             "max_abs_dE_Ha": dE, "max_rel_dV": dV, "max_abs_dgrad": dg,
+            "with_priority_lane": {"builds_per_s_saturated": nreq / t_sat_l,
+                                   "p50_ms": 1e3 * float(np.percentile(lat_l, 50)),
+                                   "p99_ms": 1e3 * float(np.percentile(lat_l, 99))},
             "stream": "water boxes n in {4,8,16,32,64,128}, p ~ 1/n, 10% gradients, seed 4"}
 
 

@@ -25,6 +25,12 @@ not been launched by then it fails with GPW_ETIMEDOUT, and if its batch is still
 then its future fails with GPW_ETIMEDOUT at once (the batch finishes and its memory is
 released as usual).  A request whose future is cancelled before launch is dropped.
 
+An optional priority lane (Server(priority_lane=True)) adds a stream of high CUDA priority
+that takes batches of small requests only, so that they need not wait for a free batch
+slot or for the blocks of a large batch: it halves the median latency of a mixed stream
+and costs the large cells' tail (their blocks yield the SMs to the lane's), so it is off
+by default.
+
 Batches are launched directly, not through CUDA graphs: every batch holds a different set
 of plans, so a captured graph would be replayed exactly once and its capture and
 instantiation would cost what the launches cost.  A caller that repeats one batch (the
@@ -96,7 +102,7 @@ class BatchPolicy:
     which the server launches on a high-priority stream; lane_cost: the cap on such a
     batch's summed cost (None: batch_cost), which keeps the high-priority batches short."""
 
-    def __init__(self, max_batch: int = 32, batch_cost: float = 2.0e9,
+    def __init__(self, max_batch: int = 32, batch_cost: float = 1.5e9,
                  small_cost: float = 4.0e8, lane_cost: float | None = None):
         self.max_batch = int(max_batch)
         self.batch_cost = float(batch_cost)
@@ -165,11 +171,11 @@ class Server:
     the wait for a free batch slot).
     """
 
-    def __init__(self, hbm_budget: int | None = None, max_batch: int = 32, streams: int = 2,
+    def __init__(self, hbm_budget: int | None = None, max_batch: int = 32, streams: int = 3,
                  host_workers: int | None = None, tile=None, tile_integ=None,
                  colloc_warps=None, integ_chunk=None, tune_with=None, fail_prepare=None,
-                 batch_cost: float = 2.0e9, small_cost: float = 4.0e8,
-                 priority_lane: bool = True, lane_priority: int = -1,
+                 batch_cost: float = 1.5e9, small_cost: float = 4.0e8,
+                 priority_lane: bool = False, lane_priority: int = -1,
                  lane_cost: float | None = None):
         import torch
         self.torch = torch

@@ -140,6 +140,20 @@ def test_server_results_equal_alone(gpw, alone):
     assert stats["batches"] >= 4  # at most 3 per batch
 
 
+def test_server_with_priority_lane_equals_alone(gpw, alone):
+    # the optional priority lane (small requests on a high-priority stream) changes where
+    # and when batches run, not their results
+    from paper_2603_24881_gb300.serve import Server
+    systems = _systems()
+    with Server(max_batch=3, streams=1, priority_lane=True) as srv:
+        futs = [srv.submit(s, want_grad=True) for s in systems + systems]
+        res = [f.result(timeout=300) for f in futs]
+        stats = dict(srv.stats)
+    for i, r in enumerate(res):
+        _same(dict(V=r.V, grad=r.grad, EH=r.EH, Ex=r.Ex), alone[i % len(systems)])
+    assert stats["admitted"] == len(futs)
+
+
 def test_server_memory_budget_and_failures(gpw, alone):
     from paper_2603_24881_gb300.serve import Server
     systems = _systems()
