@@ -112,3 +112,22 @@ def test_tau_plan_sizes(lib):
     a = binding.Plan(s, commit=False).stats()["device_bytes"]
     b = binding.Plan(s, commit=False, tau=True).stats()["device_bytes"]
     assert b > a
+
+
+@pytest.mark.parametrize("name", ["water32", "many_primitives"])
+def test_pair_order_is_shell_pair_primitives_image(lib, name):
+    # the plan's own pair order (the pair index of the task records) is by contracted
+    # shell pair, then primitives, then image; the 17-primitive shell takes the planner's
+    # general sort instead of its packed 64-bit keys, and both give that order and the
+    # oracle's pair set
+    s = (workloads.config("water32") if name == "water32" else
+         systems.resolved(seed=3, shells=((0, 17), (1, 2)), natm=2, tau=1e-8))
+    p = binding.Plan(s, commit=False)
+    t = p.pair_table(sort=False)
+    p.close()
+    sh = oracle.primitives(s)["shell"]
+    key = np.column_stack([sh[t[:, 0]], sh[t[:, 1]], t[:, 0], t[:, 1], t[:, 2], t[:, 3], t[:, 4]])
+    order = np.lexsort(key[:, ::-1].T)
+    assert np.array_equal(order, np.arange(len(t)))
+    ref = oracle.Plan(s).pair_table()
+    assert np.array_equal(t[np.lexsort(t[:, ::-1].T)], ref)
