@@ -66,8 +66,8 @@ def _workload_desc(name: str, system, stats) -> str:
 # work order) are unchanged: sha256 of csrc/kernels.cu + csrc/plan.cpp at capture time.
 TRAFFIC = {
     # integration at degree L+1 (8x8x32 sub-box): read + write of one 32-water launch
-    # (1.806 GB) scaled by pair-points to the 256-water launch
-    "integrate_ip1": {"bytes_per_launch": 1.3126e+10, "src_sha": "ff8daf3a7663c72c",
+    # (1.804 GB) scaled by pair-points to the 256-water launch
+    "integrate_ip1": {"bytes_per_launch": 1.3113e+10, "src_sha": "3c2de7f0d0be42da",
                       "capture": "profiles/integrate_traffic_water32.md"},
 }
 

@@ -1135,6 +1135,10 @@ __device__ double contract_elem(const int* ca, const int* cb, const double pw[3]
   return s;
 }
 
+// One warp per contracted shell pair (group of primitive pairs); a group with fewer than
+// 32 elements spreads its pairs over G = 32 / C lane groups (C = the element count rounded
+// up to a power of two): lane group g sums the pairs g, g + G, ... of the group for its
+// element, and a fixed butterfly of shuffles adds the groups.
 __global__ void assemble_V_kernel(long long ngroups, const int4* __restrict__ groups,
                                   const int4* __restrict__ ids, const int4* __restrict__ ids2,
                                   const double* __restrict__ geo, const double* __restrict__ pref,
@@ -1149,36 +1153,47 @@ __global__ void assemble_V_kernel(long long ngroups, const int4* __restrict__ gr
   const int4 id0 = ids[gr.z];
   const int la = id0.x, lb = id0.y, Lx = la + lb + lext;
   const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
+  const int nel = na * nb;
   const bool diag = gr.x == gr.y;
-  for (int el = lane; el < na * nb; el += 32) {
-    const int mu = el / nb, nu = el - mu * nb;
-    int ca[3], cb[3];
-    cart_comp(la, mu, ca);
-    cart_comp(lb, nu, cb);
+  int C = 1;
+  while (C < nel && C < 32) C <<= 1;
+  const int G = 32 / C, g = lane / C, e = lane - g * C;
+  for (int base = 0; base < nel; base += C) {
+    const int el = base + e;
     double tot = 0.0;
-    for (int p = gr.z; p < gr.w; ++p) {
-      const double* g = geo + 8LL * p;
-      double pw[3][4];
+    if (el < nel) {
+      const int mu = el / nb, nu = el - mu * nb;
+      int ca[3], cb[3];
+      cart_comp(la, mu, ca);
+      cart_comp(lb, nu, cb);
+      for (int p = gr.z + g; p < gr.w; p += G) {
+        const double* gp = geo + 8LL * p;
+        double pw[3][4];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        double ab = g[d] - g[3 + d];
-        pw[d][0] = 1.0;
-        pw[d][1] = ab;
-        pw[d][2] = ab * ab;
-        pw[d][3] = ab * ab * ab;
+        for (int d = 0; d < 3; ++d) {
+          double ab = gp[d] - gp[3 + d];
+          pw[d][0] = 1.0;
+          pw[d][1] = ab;
+          pw[d][2] = ab * ab;
+          pw[d][3] = ab * ab * ab;
+        }
+        const double* Vp = coef + coef_off[p];
+        double x = contract_elem(ca, cb, pw, Vp, Lx, tabs->dec21, tabs->c21base);
+        if (diag && ids2[p].z == 2) {
+          int ca2[3], cb2[3];
+          cart_comp(la, nu, ca2);
+          cart_comp(lb, mu, cb2);
+          x += contract_elem(ca2, cb2, pw, Vp, Lx, tabs->dec21, tabs->c21base);
+        }
+        tot += pref[p] * x;
       }
-      const double* Vp = coef + coef_off[p];
-      double x = contract_elem(ca, cb, pw, Vp, Lx, tabs->dec21, tabs->c21base);
-      if (diag && ids2[p].z == 2) {
-        int ca2[3], cb2[3];
-        cart_comp(la, nu, ca2);
-        cart_comp(lb, mu, cb2);
-        x += contract_elem(ca2, cb2, pw, Vp, Lx, tabs->dec21, tabs->c21base);
-      }
-      tot += pref[p] * x;
     }
-    V[(long long)(id0.z + mu) * nao + id0.w + nu] = tot;
-    if (!diag) V[(long long)(id0.w + nu) * nao + id0.z + mu] = tot;
+    for (int o = C; o < 32; o <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (g == 0 && el < nel) {
+      const int mu = el / nb, nu = el - mu * nb;
+      V[(long long)(id0.z + mu) * nao + id0.w + nu] = tot;
+      if (!diag) V[(long long)(id0.w + nu) * nao + id0.z + mu] = tot;
+    }
   }
 }
 
@@ -1630,8 +1645,9 @@ __device__ double xtau(const int* a, const int* b, double aa, double ab, const d
   return 0.5 * s;
 }
 
-// V^tau assembly: one warp per contracted shell pair, lanes over its elements (as
-// assemble_V_kernel, with xtau in place of the plain pair product).
+// V^tau assembly: one warp per contracted shell pair, lanes over its elements and lane
+// groups over its pairs (as assemble_V_kernel, with xtau in place of the plain pair
+// product).
 __global__ void assemble_V_tau_kernel(long long ngroups, const int4* __restrict__ groups,
                                       const int4* __restrict__ ids, const int4* __restrict__ ids2,
                                       const double* __restrict__ geo,
@@ -1647,35 +1663,46 @@ __global__ void assemble_V_tau_kernel(long long ngroups, const int4* __restrict_
   const int4 id0 = ids[gr.z];
   const int la = id0.x, lb = id0.y, Lx = la + lb + lext;
   const int na = (la + 1) * (la + 2) / 2, nb = (lb + 1) * (lb + 2) / 2;
+  const int nel = na * nb;
   const bool diag = gr.x == gr.y;
-  for (int el = lane; el < na * nb; el += 32) {
-    const int mu = el / nb, nu = el - mu * nb;
-    int ca[3], cb[3];
-    cart_comp(la, mu, ca);
-    cart_comp(lb, nu, cb);
+  int C = 1;
+  while (C < nel && C < 32) C <<= 1;
+  const int G = 32 / C, g = lane / C, e = lane - g * C;
+  for (int base = 0; base < nel; base += C) {
+    const int el = base + e;
     double tot = 0.0;
-    for (int p = gr.z; p < gr.w; ++p) {
-      const double* g = geo + 8LL * p;
-      double pw[3][6];
+    if (el < nel) {
+      const int mu = el / nb, nu = el - mu * nb;
+      int ca[3], cb[3];
+      cart_comp(la, mu, ca);
+      cart_comp(lb, nu, cb);
+      for (int p = gr.z + g; p < gr.w; p += G) {
+        const double* gp = geo + 8LL * p;
+        double pw[3][6];
 #pragma unroll
-      for (int d = 0; d < 3; ++d) {
-        const double t = g[d] - g[3 + d];
-        pw[d][0] = 1.0;
+        for (int d = 0; d < 3; ++d) {
+          const double t = gp[d] - gp[3 + d];
+          pw[d][0] = 1.0;
 #pragma unroll
-        for (int k = 1; k < 6; ++k) pw[d][k] = pw[d][k - 1] * t;
+          for (int k = 1; k < 6; ++k) pw[d][k] = pw[d][k - 1] * t;
+        }
+        const double* Vp = coef + coef_off[p];
+        double x = xtau(ca, cb, gp[6], gp[7], pw, Vp, Lx);
+        if (diag && ids2[p].z == 2) {
+          int ca2[3], cb2[3];
+          cart_comp(la, nu, ca2);
+          cart_comp(lb, mu, cb2);
+          x += xtau(ca2, cb2, gp[6], gp[7], pw, Vp, Lx);
+        }
+        tot += pref[p] * x;
       }
-      const double* Vp = coef + coef_off[p];
-      double x = xtau(ca, cb, g[6], g[7], pw, Vp, Lx);
-      if (diag && ids2[p].z == 2) {
-        int ca2[3], cb2[3];
-        cart_comp(la, nu, ca2);
-        cart_comp(lb, mu, cb2);
-        x += xtau(ca2, cb2, g[6], g[7], pw, Vp, Lx);
-      }
-      tot += pref[p] * x;
     }
-    V[(long long)(id0.z + mu) * nao + id0.w + nu] = tot;
-    if (!diag) V[(long long)(id0.w + nu) * nao + id0.z + mu] = tot;
+    for (int o = C; o < 32; o <<= 1) tot += __shfl_xor_sync(0xffffffffu, tot, o);
+    if (g == 0 && el < nel) {
+      const int mu = el / nb, nu = el - mu * nb;
+      V[(long long)(id0.z + mu) * nao + id0.w + nu] = tot;
+      if (!diag) V[(long long)(id0.w + nu) * nao + id0.z + mu] = tot;
+    }
   }
 }
 
