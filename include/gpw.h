@@ -344,7 +344,8 @@ void gpw_batch_destroy(gpw_batch_t batch);
 
 /* Read and clear the device error word of the plan (synchronises `stream`).
  * Returns GPW_OK, or GPW_EDEVICE with *code set to the first recorded check: 1 a
- * collocation task record outside its sub-box or its pair's tables (the task is
+ * collocation task record outside its sub-box or its pair's tables, or a pair degree
+ * beyond the compiled collocation bodies (the task, or the pair's contracted table, is
  * skipped), 3 the same for integration, 16 a value that is not finite in an output and
  * 17 an inconsistent task list at commit (both with GPW_DEBUG_CHECKS). */
 int gpw_check_device(gpw_plan_t plan, int* code, void* stream);

@@ -44,6 +44,7 @@ cudaError_t launch_pbe_x(const Plan& p, const double* rho, double* grad3, double
 cudaError_t launch_spec_combine(const Plan& p, const cufftDoubleComplex* fa,
                                 const cufftDoubleComplex* fb, cufftDoubleComplex* out,
                                 cudaStream_t s);
+// the x and then the y contraction of collocation, once per pair (ldeg: degree raise)
 cudaError_t launch_xcontract(const Plan& p, cudaStream_t s, int ldeg = 0);
 cudaError_t launch_collocate(const Plan& p, cudaStream_t s, int ldeg = 0);
 cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s);
