@@ -92,7 +92,8 @@ def _args():
     ap.add_argument("--served", type=int, default=400,
                     help="also run the served request stream with this many requests")
     ap.add_argument("--tile", default=None, help="collocation sub-box t0,t1,t2")
-    ap.add_argument("--tile-integ", default=None, help="integration sub-box t0,t1,t2")
+    ap.add_argument("--tile-integ", default=None,
+                    help="integration sub-box t0,t1,t2 or, with overlapping z windows, t0,t1,t2,zwin")
     ap.add_argument("--xc", default="lda_x", choices=["lda_x", "pbe_x"],
                     help="exchange functional (LDA Slater or PBE exchange, a GGA)")
     ap.add_argument("--configs", action="store_true",
@@ -416,7 +417,8 @@ def main():
     t0 = time.perf_counter()
     tile = tuple(int(x) for x in a.tile.split(",")) if a.tile else None
     tile_i = tuple(int(x) for x in a.tile_integ.split(",")) if a.tile_integ else None
-    shape = dict(tile=tile, tile_integ=tile_i)
+    shape = dict(tile=tile, tile_integ=tile_i[:3] if tile_i else None,
+                 integ_zwin=tile_i[3] if tile_i and len(tile_i) > 3 else None)
     if a.autotune:
         from paper_2603_24881_gb300.autotune import tune
         shape = tune(s).plan_kwargs()
@@ -547,6 +549,7 @@ def main():
                            "pair_points": st["pair_points"], "tasks": st["nentries"],
                            "l2": "no flush: plan tables, tasks and grids (>2 GB) exceed L2",
                            "tile": list(st["tile"]), "tile_integ": list(st["tile_integ"]),
+                           "integ_zwin": st["integ_zwin"],
                            "colloc_warps": st["colloc_warps"], "integ_chunk": st["integ_chunk"],
                            "launch_shape": "autotuned" if a.autotune else "library defaults",
                            "xc": a.xc, **({"screening": "GPW_FAST_BLOCK_PRUNE"} if a.fast_prune else {}),

@@ -136,9 +136,13 @@ typedef struct {
                                  GPW_FAST_BLOCK_PRUNE | GPW_DEBUG_CHECKS */
   int tile[3];                /* sub-box owned by one collocation thread block (grid
                                  points along a1, a2, a3); {0,0,0} = default {4,8,16} */
-  int tile_integ[3];          /* sub-box of one integration thread block;
-                                 {0,0,0} = default {8,8,32}.  Supported shapes:
-                                 gpw_tile_supported. */
+  int tile_integ[3];          /* sub-boxes of the integration (grid points along a1, a2,
+                                 a3; along a3 the stride of the z windows, see
+                                 integ_zwin); {0,0,0} = the default: {8,8,16} with
+                                 48-point z windows where the staging of the plan's
+                                 largest degree leaves two thread blocks per SM, else
+                                 {8,8,32}; non-orthogonal cells {4,8,16}.  Supported
+                                 shapes: gpw_tile_supported, gpw_integ_zwin_supported. */
   int colloc_warps;           /* warps per collocation thread block: 4, 6 or 8; 0 = the
                                  choice with the most resident warps per SM */
   int integ_chunk;            /* most (pair, sub-box) tasks per integration work item
@@ -147,6 +151,17 @@ typedef struct {
   int host_threads;           /* most host threads the planner uses (>= 0); 0 = OpenMP's
                                  default (all cores).  A server planning several cells
                                  at once on its own threads caps each plan here. */
+  int integ_zwin;             /* z extent (grid points) of the window one integration
+                                 thread block stages: a multiple of tile_integ[2], whose
+                                 sub-boxes then overlap along a3.  A pair box is cut
+                                 along a3 where a window starting in its current
+                                 sub-box ends, not at every sub-box boundary, so a
+                                 task's first (z) contraction runs over up to zwin
+                                 points and its y contraction once per window instead
+                                 of once per sub-box (the V tensor of Sec. III A; the
+                                 sums are the same, in another order).  0 = the
+                                 default (tile_integ[2], or 48 with the default
+                                 sub-boxes); only with tile_integ given otherwise. */
 } gpw_desc;
 
 /* Sizes and work counts of a plan (gpw_plan_query). */
@@ -174,6 +189,8 @@ typedef struct {
   double volume;       /* cell volume Omega = |det(lattice)| (Bohr^3) */
   double weight[GPW_MAX_LEVELS];  /* grid weight Omega / N_k of level k: the quadrature
                                      weight of eval_mat, the gradient and the energies */
+  int integ_zwin;      /* z window of the integration sub-boxes (= tile_integ[2]: plain
+                          tiling) */
 } gpw_plan_info;
 
 /* Build a plan: normalise primitives, screen pairs (Eq. cut; pairs a <= b over images T
@@ -205,6 +222,11 @@ int gpw_plan_commit(gpw_plan_t plan, void* stream);
 #define GPW_TILE_COLLOC 1
 #define GPW_TILE_INTEG 2
 int gpw_tile_supported(int t0, int t1, int t2);
+
+/* 1 if an integration kernel exists for sub-boxes (t0, t1, t2) whose thread blocks stage
+ * z windows of zwin grid points (gpw_desc.integ_zwin; zwin = t2 for every shape that
+ * gpw_tile_supported marks GPW_TILE_INTEG), else 0. */
+int gpw_integ_zwin_supported(int t0, int t1, int t2, int zwin);
 
 /* Fill *info (host). */
 int gpw_plan_query(gpw_plan_t plan, gpw_plan_info* info);

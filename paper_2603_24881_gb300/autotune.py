@@ -1,8 +1,10 @@
 """Autotuner for the launch shape of the grid kernels.
 
 Four knobs decide how the (pair, sub-box) tasks are cut and spread over the GPU:
-the collocation sub-box and its warps per thread block, and the integration sub-box and
-its tasks per work item (how many pair tasks one thread block takes).  The fastest
+the collocation sub-box and its warps per thread block, and the integration sub-box (with
+its z window: (t0, t1, t2) stages the sub-box itself, (t0, t1, t2, zwin) overlapping
+windows of zwin points) and its tasks per work item (how many pair tasks one thread
+block takes).  The fastest
 setting depends on the workload (pair box sizes against the sub-box, the mix of angular
 momenta, tasks per sub-box, one large cell or a batch of small ones), so it is measured:
 every candidate is planned, committed and timed with the library's per-phase CUDA-event
@@ -27,7 +29,7 @@ from dataclasses import asdict, dataclass, field
 
 import numpy as np
 
-from .binding import TILES, TILES_INTEG, Batch, GpwError, Plan
+from .binding import TILES, TILES_INTEG, TILES_INTEG_ZWIN, Batch, GpwError, Plan
 
 WARPS = (0, 8, 6, 4)             # 0 = the library's occupancy choice
 CHUNKS = (0, 64, 256, 1024, 4096)  # 0 = the library's default
@@ -42,8 +44,14 @@ class Choice:
     timings: dict = field(default_factory=dict)  # candidate -> ms per build (phase)
 
     def plan_kwargs(self) -> dict:
-        return dict(tile=tuple(self.tile), tile_integ=tuple(self.tile_integ),
-                    colloc_warps=int(self.colloc_warps), integ_chunk=int(self.integ_chunk))
+        return dict(tile=tuple(self.tile), colloc_warps=int(self.colloc_warps),
+                    integ_chunk=int(self.integ_chunk), **integ_kwargs(self.tile_integ))
+
+
+def integ_kwargs(t) -> dict:
+    """Plan arguments of an integration candidate (t0, t1, t2) or (t0, t1, t2, zwin)."""
+    t = tuple(int(x) for x in t)
+    return dict(tile_integ=t[:3], integ_zwin=t[3] if len(t) > 3 else None)
 
 
 def signature(systems) -> str:
@@ -144,7 +152,7 @@ def tune(systems, *, tiles=None, tiles_integ=None, warps=None, chunks=None, step
     if not isinstance(systems, (list, tuple)):
         systems = [systems]
     tiles = list(tiles or TILES)
-    tiles_integ = list(tiles_integ or TILES_INTEG)
+    tiles_integ = list(tiles_integ or (TILES_INTEG + TILES_INTEG_ZWIN))
     warps = list(WARPS if warps is None else warps)
     chunks = list(CHUNKS if chunks is None else chunks)
     meas = measure or (lambda ss, kw: measure_builds(ss, kw, steps=steps))
@@ -172,10 +180,9 @@ def tune(systems, *, tiles=None, tiles_integ=None, warps=None, chunks=None, step
 
     tile = best("tile", [tuple(t) for t in tiles], "collocate", lambda t: dict(tile=t))
     nw = best("colloc_warps", warps, "collocate", lambda w: dict(tile=tile, colloc_warps=w))
-    ti = best("tile_integ", [tuple(t) for t in tiles_integ], "integrate",
-              lambda t: dict(tile_integ=t))
+    ti = best("tile_integ", [tuple(t) for t in tiles_integ], "integrate", integ_kwargs)
     ch = best("integ_chunk", chunks, "integrate",
-              lambda c: dict(tile_integ=ti, integ_chunk=c))
+              lambda c: dict(integ_kwargs(ti), integ_chunk=c))
     choice = Choice(tile, ti, int(nw), int(ch), timings)
     _store(path, key, choice)
     return choice

@@ -29,6 +29,7 @@ EXPORTS = ["gpw_plan", "gpw_plan_query", "gpw_plan_update_coords", "gpw_plan_pai
            "gpw_eval_mat_tau", "gpw_eval_mat_tau_levels", "gpw_eval_mat_tau_ip1",
            "gpw_eval_mat_tau_ip1_levels", "gpw_plan_destroy_async", "gpw_fock", "gpw_fock_async",
            "gpw_fock_grad", "gpw_fock_grad_async", "gpw_fock_grad_host", "gpw_tile_supported",
+           "gpw_integ_zwin_supported",
            "gpw_plan_prepare", "gpw_plan_commit", "gpw_batch_create", "gpw_batch_set",
            "gpw_batch_fock_grad_async", "gpw_batch_generation", "gpw_batch_destroy",
            "gpw_check_device", "gpw_profile", "gpw_profile_read", "gpw_plan_destroy",
@@ -54,7 +55,7 @@ class Desc(ctypes.Structure):
                 ("flags", ctypes.c_int), ("tile", ctypes.c_int * 3),
                 ("tile_integ", ctypes.c_int * 3), ("colloc_warps", ctypes.c_int),
                 ("integ_chunk", ctypes.c_int), ("xc", ctypes.c_int),
-                ("host_threads", ctypes.c_int)]
+                ("host_threads", ctypes.c_int), ("integ_zwin", ctypes.c_int)]
 
 GPW_TAU = 1  # gpw_desc.flags: kinetic-energy-density kernels
 GPW_HOST_TASKS = 2  # gpw_desc.flags: task records built on the host (default: device)
@@ -68,6 +69,9 @@ XC = {"lda_x": 0, "pbe_x": 1}
 TILES = [(8, 8, 16), (4, 8, 32), (8, 8, 32), (4, 8, 64), (4, 8, 16), (4, 4, 16), (2, 8, 16),
          (4, 4, 32)]
 TILES_INTEG = TILES + [(8, 8, 64), (8, 4, 64)]
+# integration sub-boxes with overlapping z windows (gpw_integ_zwin_supported):
+# (t0, t1, t2, zwin)
+TILES_INTEG_ZWIN = [(8, 8, 16, 48)]
 
 
 class Info(ctypes.Structure):
@@ -84,7 +88,8 @@ class Info(ctypes.Structure):
                 ("tile", ctypes.c_int * 3), ("tile_integ", ctypes.c_int * 3),
                 ("nentries_integ", ctypes.c_longlong), ("colloc_warps", ctypes.c_int),
                 ("integ_chunk", ctypes.c_int), ("xc", ctypes.c_int),
-                ("volume", ctypes.c_double), ("weight", ctypes.c_double * GPW_MAX_LEVELS)]
+                ("volume", ctypes.c_double), ("weight", ctypes.c_double * GPW_MAX_LEVELS),
+                ("integ_zwin", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -127,6 +132,7 @@ def load(build_if_missing: bool = True):
         L.gpw_fock_grad_async.argtypes = [vp, vp, vp, vp, vp, vp]
         L.gpw_fock_grad_host.argtypes = [vp, vp, vp, vp, vp, vp]
         L.gpw_tile_supported.argtypes = [ci, ci, ci]
+        L.gpw_integ_zwin_supported.argtypes = [ci, ci, ci, ci]
         L.gpw_plan_prepare.argtypes = [ctypes.POINTER(Desc), ctypes.POINTER(vp)]
         L.gpw_plan_commit.argtypes = [vp, vp]
         L.gpw_batch_create.argtypes = [ci, ctypes.POINTER(vp)]
@@ -199,7 +205,7 @@ class Plan:
 
     def __init__(self, system, stream=None, tile=None, tile_integ=None, commit=True,
                  colloc_warps=None, integ_chunk=None, xc="lda_x", tau=False, host_threads=0,
-                 host_tasks=False, fast_prune=False, debug_checks=False):
+                 host_tasks=False, fast_prune=False, debug_checks=False, integ_zwin=None):
         """Prepare the plan on the host (screening, levels, task lists) and, unless
         commit=False, commit it to the current device.  An uncommitted plan reports its
         exact device footprint in stats()["device_bytes"].  tile, tile_integ,
@@ -211,7 +217,9 @@ class Plan:
         the collocation lists the (pair, sub-box) tasks wholly beyond the pair's extent
         (GPW_FAST_BLOCK_PRUNE: tau-sized changes, outside the strict definition);
         debug_checks: validate the task lists at commit and every output for values that
-        are not finite (GPW_DEBUG_CHECKS, read with check_device())."""
+        are not finite (GPW_DEBUG_CHECKS, read with check_device()); integ_zwin: z window
+        of the integration sub-boxes tile_integ (a multiple of tile_integ[2]; None = the
+        library default)."""
         self._lib = load()
         s = system
         self.system = s
@@ -252,6 +260,7 @@ class Plan:
                 d.tile_integ[i] = int(tile_integ[i])
         d.colloc_warps = int(colloc_warps or 0)
         d.integ_chunk = int(integ_chunk or 0)
+        d.integ_zwin = int(integ_zwin or 0)
         if xc not in XC:
             raise ValueError(f"unknown exchange functional {xc!r} (one of {sorted(XC)})")
         d.xc = XC[xc]
@@ -315,6 +324,7 @@ class Plan:
                     flops_rho=i.flops_rho, flops_mat=i.flops_mat, flops_ip1=i.flops_ip1,
                     level_cutoff=[i.level_cutoff[k] for k in range(i.nlevels)],
                     tile=tuple(i.tile), tile_integ=tuple(i.tile_integ),
+                    integ_zwin=i.integ_zwin,
                     nentries_integ=i.nentries_integ, colloc_warps=i.colloc_warps,
                     integ_chunk=i.integ_chunk,
                     xc={v: k for k, v in XC.items()}.get(i.xc, i.xc),

@@ -767,6 +767,7 @@ int gpw_plan_query(gpw_plan_t plan, gpw_plan_info* info) {
   info->tile[1] = P.tile[1];
   info->tile[2] = P.tile[2];
   for (int d = 0; d < 3; ++d) info->tile_integ[d] = P.tile_i[d];
+  info->integ_zwin = P.zwin_i;
   info->nentries_integ = P.nent_i;
   info->colloc_warps = P.committed ? P.nw_colloc : 0;
   info->integ_chunk = P.chunk_i;
@@ -1108,7 +1109,7 @@ int gpw_batch_set(gpw_batch_t b, int nplans, const gpw_plan_t* plans, void* stre
     const gpw::Plan& P = plans[i]->p;
     const gpw::Plan& P0 = plans[0]->p;
     for (int d = 0; d < 3; ++d)
-      if (P.tile[d] != P0.tile[d] || P.tile_i[d] != P0.tile_i[d]) {
+      if (P.tile[d] != P0.tile[d] || P.tile_i[d] != P0.tile_i[d] || P.zwin_i != P0.zwin_i) {
         set_error("gpw_batch_set: plans of a batch must share their sub-box shapes");
         return GPW_EINVAL;
       }
@@ -1122,7 +1123,7 @@ int gpw_batch_set(gpw_batch_t b, int nplans, const gpw_plan_t* plans, void* stre
     }
     lmax = std::max(lmax, P.lmax);
   }
-  cudaError_t e = gpw::configure_batch(plans[0]->p.tile, plans[0]->p.tile_i, lmax,
+  cudaError_t e = gpw::configure_batch(plans[0]->p.tile, plans[0]->p.tile_i, plans[0]->p.zwin_i, lmax,
                                        plans[0]->p.nw_colloc_req, &b->colloc,
                                        &b->integ1, skew_kind);
   if (e != cudaSuccess) {

@@ -172,7 +172,8 @@ struct Plan {
   int nao = 0, natm = 0, nlev = 0, lmax = 0;
   int nprim = 0, nshell = 0;
   int tile[3] = {kT0, kT1, kT2};      // collocation sub-box
-  int tile_i[3] = {8, 8, 32};         // integration sub-box
+  int tile_i[3] = {8, 8, 32};         // integration sub-box (along z: window stride)
+  int zwin_i = 32;                    // z window of the integration sub-boxes
   int chunk_i = 0;                    // most tasks per integration work item
   double L[3] = {0, 0, 0};   // lattice lengths |R_d|
   double omega = 0;
@@ -236,6 +237,10 @@ struct Plan {
 
 // plan.cpp (host): screening and task lists; fills everything except device arrays.
 int build_host_plan(const gpw_desc* desc, Plan* plan, struct HostArrays* host);
+// kernels.cu: shared memory of one integration thread block (eval_mat_ip1, degree
+// lmax + 1) for the sub-boxes `tile` with z windows of zwin points; 0 if no kernel exists
+// for that shape.  Host arithmetic only (no device query).
+size_t integ_block_smem(const int* tile, int zwin, int lmax);
 PlanView make_view(const Plan& p);
 
 void set_error(const std::string& msg);

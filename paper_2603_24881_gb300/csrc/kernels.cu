@@ -360,7 +360,10 @@ struct SubBox {
   long long eb, ee;
 };
 
-template <int T0, int T1, int T2>
+// Sub-box `sub` of a level cut into T0 x T1 x T2 sub-boxes; along z its thread block's
+// window spans W2 points from the sub-box start (W2 > T2: windows of neighbouring
+// sub-boxes overlap, see the integration kernel).
+template <int T0, int T1, int T2, int W2 = T2>
 __device__ __forceinline__ SubBox sub_box(const LevelInfo& lv, int sub, const long long* sub_off) {
   SubBox b;
   const int j2 = sub % lv.nsb[2];
@@ -371,7 +374,7 @@ __device__ __forceinline__ SubBox sub_box(const LevelInfo& lv, int sub, const lo
   b.s[2] = j2 * T2;
   b.ext[0] = min(T0, lv.N[0] - b.s[0]);
   b.ext[1] = min(T1, lv.N[1] - b.s[1]);
-  b.ext[2] = min(T2, lv.N[2] - b.s[2]);
+  b.ext[2] = min(W2, lv.N[2] - b.s[2]);
   b.eb = sub_off[lv.sub_base + sub];
   b.ee = sub_off[lv.sub_base + sub + 1];
   return b;
@@ -745,6 +748,10 @@ __global__ void __launch_bounds__(NW * 32, 24 / NW)
 // pair's tasks that share an x-segment and contracts once per segment (fixed order).
 // Lx = L + lext.  Shared rows are padded to an odd number of doubles (P = T + 1) so
 // that lanes walking different rows hit different banks.
+// Along z a block may stage a window of T2 points while the sub-boxes start every S2 <
+// T2 points: the plan then cuts a pair box along z where a window opened in its current
+// sub-box ends, so that most pair boxes take one task per (x, y) window instead of one
+// per sub-box they cross, and the W contraction (and its store) runs once for them.
 template <int T0, int T1, int T2>
 struct IntegLayout {
   static constexpr int P0 = T0 + 1, P1 = T1 + 1, P2 = T2 + 1;
@@ -755,7 +762,7 @@ struct IntegLayout {
   __host__ __device__ static int stage(int lpx) { return 2 * buf(lpx) + lpx * kUS; }
 };
 
-template <int T0, int T1, int T2, int NW, int SK = 0>
+template <int T0, int T1, int T2, int NW, int SK = 0, int S2 = T2>
 __global__ void __launch_bounds__(NW * 32)
     integrate_kernel(const PlanView* __restrict__ views, const int4* __restrict__ work,
                      const CoefTables* __restrict__ tabs, int lext, int lpx, int stg) {
@@ -778,7 +785,7 @@ __global__ void __launch_bounds__(NW * 32)
   const double* __restrict__ grids = pv.grids;
   double* __restrict__ part = pv.part;
   int* __restrict__ err = pv.err;
-  SubBox sb = sub_box<T0, T1, T2>(lv, item.z, pv.sub_off_i);
+  SubBox sb = sub_box<T0, T1, S2, T2>(lv, item.z, pv.sub_off_i);
   sb.eb += (long long)(item.y >> 4) * pv.chunk_i;  // this item's chunk of the task list
   sb.ee = min(sb.ee, sb.eb + pv.chunk_i);
   {
@@ -1911,12 +1918,12 @@ __global__ void finite_check_kernel(const double* __restrict__ x, long long n, i
 // sub-box): the pair exists, its level is the sub-box's, the record's degree and pair-box
 // extents are the pair's, the intersection lies inside the sub-box and the pair box and
 // sits, wrapped, where the record says, and the pairs come in order.
-__global__ void validate_tasks_kernel(const KLevels K, int T0, int T1, int T2, long long nsub,
+__global__ void validate_tasks_kernel(const KLevels K, int T0, int T1, int T2, int W2, long long nsub,
                                       const long long* __restrict__ sub_off,
                                       const int4* __restrict__ task,
                                       const int4* __restrict__ hot_a,
                                       const int4* __restrict__ hot_b, long long np, int* err) {
-  const int T[3] = {T0, T1, T2};
+  const int T[3] = {T0, T1, T2}, Wd[3] = {T0, T1, W2};
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < nsub;
        g += (long long)gridDim.x * blockDim.x) {
     int k = 0;
@@ -1942,7 +1949,7 @@ __global__ void validate_tasks_kernel(const KLevels K, int T0, int T1, int T2, l
         const int m = (r0.y >> (8 * d)) & 255, u = (r0.z >> (8 * d)) & 255;
         const int t = rt[d] & 0xffff, nn = (rt[d] >> 16) & 0xffff;
         const long long s0 = j[d] * T[d];
-        const long long ext = min((long long)T[d], (long long)lv.N[d] - s0);
+        const long long ext = min((long long)Wd[d], (long long)lv.N[d] - s0);
         const long long i = (long long)lo[d] + t;
         const long long w = ((i % lv.N[d]) + lv.N[d]) % lv.N[d];
         ok = nn == n[d] && m >= 1 && u + m <= ext && t + m <= n[d] && w == s0 + u;
@@ -1960,6 +1967,8 @@ constexpr int kNW = 8;
 #define GPW_COLLOC_SHAPES(X) \
   X(8, 8, 16) X(4, 8, 32) X(8, 8, 32) X(4, 8, 64) X(4, 8, 16) X(4, 4, 16) X(2, 8, 16) X(4, 4, 32)
 #define GPW_INTEG_SHAPES(X) GPW_COLLOC_SHAPES(X) X(8, 8, 64) X(8, 4, 64)
+// Integration sub-boxes (a, b, c) with z windows of w > c points (overlapping windows).
+#define GPW_INTEG_WSHAPES(X) X(8, 8, 16, 48)
 
 // per-warp staging doubles of the non-orthogonal variants (cross factors and their rows)
 template <int T0, int T1, int T2>
@@ -2024,6 +2033,15 @@ extern "C" int gpw_tile_supported(int t0, int t1, int t2) {
   return r;
 }
 
+extern "C" int gpw_integ_zwin_supported(int t0, int t1, int t2, int zwin) {
+  if (zwin == t2) return (gpw_tile_supported(t0, t1, t2) & GPW_TILE_INTEG) ? 1 : 0;
+#define GPW_ZWIN_CHECK(a, b, c, w) \
+  if (t0 == a && t1 == b && t2 == c && zwin == w) return 1;
+  GPW_INTEG_WSHAPES(GPW_ZWIN_CHECK)
+#undef GPW_ZWIN_CHECK
+  return 0;
+}
+
 KLevels make_klevels(const Plan& p, bool integ) {
   KLevels k;
   for (int i = 0; i < GPW_MAX_LEVELS; ++i) k.lv[i] = integ ? p.lev_i[i] : p.lev[i];
@@ -2038,6 +2056,18 @@ KLevels make_klevels(const Plan& p, bool integ) {
   }
   for (int i = 0; i < 9; ++i) k.rec[i] = p.rec[i];
   return k;
+}
+
+size_t integ_block_smem(const int* tile, int zwin, int lmax) {
+#define GPW_SMEM_IW(a, b, c, w)                                                       \
+  if (tile[0] == a && tile[1] == b && tile[2] == c && zwin == w)                      \
+    return integ_smem<a, b, w>(even(IntegLayout<a, b, w>::stage(lmax + 2)));
+#define GPW_SMEM_I(a, b, c) GPW_SMEM_IW(a, b, c, c)
+  GPW_INTEG_SHAPES(GPW_SMEM_I)
+  GPW_INTEG_WSHAPES(GPW_SMEM_IW)
+#undef GPW_SMEM_I
+#undef GPW_SMEM_IW
+  return 0;
 }
 
 cudaError_t configure_kernels(Plan* p) {
@@ -2063,10 +2093,16 @@ cudaError_t configure_kernels(Plan* p) {
   e = cudaFuncSetAttribute(integrate_kernel<a, b, c, kNW>,                                        \
                            cudaFuncAttributeMaxDynamicSharedMemorySize, optin);                   \
   if (e != cudaSuccess) return e;
+#define GPW_TILE_ATTR_W(a, b, c, w)                                                               \
+  e = cudaFuncSetAttribute(integrate_kernel<a, b, w, kNW, 0, c>,                                  \
+                           cudaFuncAttributeMaxDynamicSharedMemorySize, optin);                   \
+  if (e != cudaSuccess) return e;
   GPW_COLLOC_SHAPES(GPW_TILE_ATTR)
   GPW_INTEG_SHAPES(GPW_TILE_ATTR_I)
+  GPW_INTEG_WSHAPES(GPW_TILE_ATTR_W)
 #undef GPW_TILE_ATTR
 #undef GPW_TILE_ATTR_I
+#undef GPW_TILE_ATTR_W
   // the non-orthogonal variants (4x8x16 sub-boxes)
   for (const void* f : {(const void*)collocate_kernel<kT0, kT1, kT2, 8, 1>,
                         (const void*)collocate_kernel<kT0, kT1, kT2, 6, 1>,
@@ -2117,18 +2153,21 @@ cudaError_t configure_kernels(Plan* p) {
                                    &p->smem_colloc) == 0)                                \
       return cudaErrorInvalidValue;                                                 \
   }
-#define GPW_TILE_CONF_I(a, b, c)                                                    \
-  if (p->tile_i[0] == a && p->tile_i[1] == b && p->tile_i[2] == c) {                \
+#define GPW_TILE_CONF_IW(a, b, c, w)                                                \
+  if (p->tile_i[0] == a && p->tile_i[1] == b && p->tile_i[2] == c && p->zwin_i == w) { \
     found |= 2;                                                                     \
-    p->stg_integ = even(IntegLayout<a, b, c>::stage(p->lmax + 1));                  \
-    p->stg_integ1 = even(IntegLayout<a, b, c>::stage(p->lmax + 2));                 \
-    p->smem_integ = integ_smem<a, b, c>(p->stg_integ);                              \
-    p->smem_integ1 = integ_smem<a, b, c>(p->stg_integ1);                            \
+    p->stg_integ = even(IntegLayout<a, b, w>::stage(p->lmax + 1));                  \
+    p->stg_integ1 = even(IntegLayout<a, b, w>::stage(p->lmax + 2));                 \
+    p->smem_integ = integ_smem<a, b, w>(p->stg_integ);                              \
+    p->smem_integ1 = integ_smem<a, b, w>(p->stg_integ1);                            \
   }
+#define GPW_TILE_CONF_I(a, b, c) GPW_TILE_CONF_IW(a, b, c, c)
   GPW_COLLOC_SHAPES(GPW_TILE_CONF)
   GPW_INTEG_SHAPES(GPW_TILE_CONF_I)
+  GPW_INTEG_WSHAPES(GPW_TILE_CONF_IW)
 #undef GPW_TILE_CONF
 #undef GPW_TILE_CONF_I
+#undef GPW_TILE_CONF_IW
   if (found != 3) return cudaErrorInvalidValue;
   p->nw_integ = kNW;
   if (p->xr) {
@@ -2139,15 +2178,18 @@ cudaError_t configure_kernels(Plan* p) {
                                    &p->smem_colloc_t) == 0)                                 \
       return cudaErrorInvalidValue;                                                          \
   }
-#define GPW_TILE_CONF_I3(a, b, c)                                                            \
-  if (p->tile_i[0] == a && p->tile_i[1] == b && p->tile_i[2] == c) {                         \
-    p->stg_integ3 = even(IntegLayout<a, b, c>::stage(p->lmax + 4));                          \
-    p->smem_integ3 = integ_smem<a, b, c>(p->stg_integ3);                                     \
+#define GPW_TILE_CONF_I3W(a, b, c, w)                                                        \
+  if (p->tile_i[0] == a && p->tile_i[1] == b && p->tile_i[2] == c && p->zwin_i == w) {      \
+    p->stg_integ3 = even(IntegLayout<a, b, w>::stage(p->lmax + 4));                          \
+    p->smem_integ3 = integ_smem<a, b, w>(p->stg_integ3);                                     \
   }
+#define GPW_TILE_CONF_I3(a, b, c) GPW_TILE_CONF_I3W(a, b, c, c)
     GPW_COLLOC_SHAPES(GPW_TILE_CONF_T)
     GPW_INTEG_SHAPES(GPW_TILE_CONF_I3)
+    GPW_INTEG_WSHAPES(GPW_TILE_CONF_I3W)
 #undef GPW_TILE_CONF_T
 #undef GPW_TILE_CONF_I3
+#undef GPW_TILE_CONF_I3W
     if ((size_t)optin < std::max(p->smem_colloc_t, p->smem_integ3)) return cudaErrorInvalidValue;
   }
   if ((size_t)optin < std::max(p->smem_colloc, std::max(p->smem_integ, p->smem_integ1)))
@@ -2170,7 +2212,8 @@ cudaError_t launch_validate_tasks(const Plan& p, bool integ, cudaStream_t s) {
   ++p.launches;
   const long long blocks = std::min<long long>((nsub + 127) / 128, 152LL * 16);
   validate_tasks_kernel<<<(int)blocks, 128, 0, s>>>(
-      make_klevels(p, integ), T[0], T[1], T[2], nsub, integ ? p.d.sub_off_i : p.d.sub_off_c,
+      make_klevels(p, integ), T[0], T[1], T[2], integ ? p.zwin_i : T[2], nsub,
+      integ ? p.d.sub_off_i : p.d.sub_off_c,
       integ ? p.d.task_i : p.d.task_c, p.d.hot_a, p.d.hot_b, p.npairs, p.d.err);
   return cudaGetLastError();
 }
@@ -2260,14 +2303,18 @@ cudaError_t launch_integrate_views(const GridLaunch& cfg, int lext, const PlanVi
           views, work, tabs, lext, cfg.lp, cfg.stg);
     return cudaGetLastError();
   }
-#define GPW_LAUNCH_INTEG(a, b, c)                                                            \
-  if (t0 == a && t1 == b && t2 == c) {                                                     \
-    integrate_kernel<a, b, c, kNW><<<(int)nwork, kNW * 32, cfg.smem, s>>>(                 \
+  const int zw = cfg.zwin ? cfg.zwin : t2;
+#define GPW_LAUNCH_INTEGW(a, b, c, w)                                                        \
+  if (t0 == a && t1 == b && t2 == c && zw == w) {                                          \
+    integrate_kernel<a, b, w, kNW, 0, c><<<(int)nwork, kNW * 32, cfg.smem, s>>>(           \
         views, work, tabs, lext, cfg.lp, cfg.stg);                                         \
     return cudaGetLastError();                                                             \
   }
+#define GPW_LAUNCH_INTEG(a, b, c) GPW_LAUNCH_INTEGW(a, b, c, c)
   GPW_INTEG_SHAPES(GPW_LAUNCH_INTEG)
+  GPW_INTEG_WSHAPES(GPW_LAUNCH_INTEGW)
 #undef GPW_LAUNCH_INTEG
+#undef GPW_LAUNCH_INTEGW
   return cudaErrorInvalidValue;
 }
 
@@ -2291,6 +2338,7 @@ cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s) {
   ++p.launches;
   GridLaunch cfg;
   for (int d = 0; d < 3; ++d) cfg.tile[d] = p.tile_i[d];
+  cfg.zwin = p.zwin_i;
   cfg.nw = kNW;
   if (lext > 1 + p.xr) return cudaErrorInvalidValue;
   cfg.lp = p.lmax + lext + 1;
@@ -2301,7 +2349,7 @@ cudaError_t launch_integrate(const Plan& p, int lext, cudaStream_t s) {
 }
 
 // Launch shapes for a batch of plans with the same sub-boxes and largest degree lmax.
-cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int nw_req,
+cudaError_t configure_batch(const int* tile_c, const int* tile_i, int zwin_i, int lmax, int nw_req,
                             GridLaunch* colloc,
                             GridLaunch* integ1, int skew) {
   int dev = 0, per_sm = 0;
@@ -2314,6 +2362,7 @@ cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int 
     colloc->tile[d] = tile_c[d];
     integ1->tile[d] = tile_i[d];
   }
+  integ1->zwin = zwin_i;
   colloc->lp = lmax + 1;
   integ1->lp = lmax + 2;
   integ1->nw = kNW;
@@ -2324,16 +2373,19 @@ cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int 
     if (pick_colloc_warps<a, b, c>(colloc->stg, nw_req, &colloc->nw, &colloc->smem) == 0) \
       return cudaErrorInvalidValue;                                                         \
   }
-#define GPW_TILE_BCONF_I(a, b, c)                                                           \
-  if (tile_i[0] == a && tile_i[1] == b && tile_i[2] == c) {                                 \
+#define GPW_TILE_BCONF_IW(a, b, c, w)                                                       \
+  if (tile_i[0] == a && tile_i[1] == b && tile_i[2] == c && zwin_i == w) {                  \
     found |= 2;                                                                             \
-    integ1->stg = even(IntegLayout<a, b, c>::stage(lmax + 2));                              \
-    integ1->smem = integ_smem<a, b, c>(integ1->stg);                                        \
+    integ1->stg = even(IntegLayout<a, b, w>::stage(lmax + 2));                              \
+    integ1->smem = integ_smem<a, b, w>(integ1->stg);                                        \
   }
+#define GPW_TILE_BCONF_I(a, b, c) GPW_TILE_BCONF_IW(a, b, c, c)
   GPW_COLLOC_SHAPES(GPW_TILE_BCONF)
   GPW_INTEG_SHAPES(GPW_TILE_BCONF_I)
+  GPW_INTEG_WSHAPES(GPW_TILE_BCONF_IW)
 #undef GPW_TILE_BCONF
 #undef GPW_TILE_BCONF_I
+#undef GPW_TILE_BCONF_IW
   if (found != 3) return cudaErrorInvalidValue;
   colloc->skew = integ1->skew = skew;
   if (skew) {

@@ -22,13 +22,14 @@ struct GridLaunch {
   size_t smem;
   int ldeg = 0;  // collocation: degree added to every pair's L (2 for the kinetic density)
   int skew = 0;  // non-orthogonal cells: the kernels with cross factors
+  int zwin = 0;  // integration: z window of the sub-boxes (tile[2]: plain tiling)
 };
 cudaError_t launch_collocate_views(const GridLaunch& cfg, const PlanView* views, const int4* work,
                                    long long nwork, const CoefTables* tabs, cudaStream_t s);
 cudaError_t launch_integrate_views(const GridLaunch& cfg, int lext, const PlanView* views,
                                    const int4* work, long long nwork, const CoefTables* tabs,
                                    cudaStream_t s);
-cudaError_t configure_batch(const int* tile_c, const int* tile_i, int lmax, int nw_req,
+cudaError_t configure_batch(const int* tile_c, const int* tile_i, int zwin_i, int lmax, int nw_req,
                             GridLaunch* colloc,
                             GridLaunch* integ1, int skew = 0);
 

@@ -236,26 +236,37 @@ struct Seg {
 // most sub-box segments of one pair box along one axis
 constexpr size_t kSegMax = 512;
 
-// Number of sub-box segments of [lo, hi] along an axis of N points cut into sub-boxes of
-// T (the last one of each period clipped): the cells of the unwrapped axis are numbered
+// Segments of [lo, hi] along an axis of N points cut into sub-boxes of T (the last one of
+// each period clipped), whose thread blocks see windows of W >= T points from their
+// sub-box start (W = T: plain tiling).  A segment starts at lo or where the previous one
+// ended; it belongs to the sub-box j it starts in and ends where that sub-box's window
+// (clipped at the period) ends.  With W = T the cells of the unwrapped axis are numbered
 // g = period * nsb + sub-box, and [lo, hi] meets every cell from g(lo) to g(hi).
-long long nseg(int lo, int hi, int N, int T) {
+long long nseg(int lo, int hi, int N, int T, int W) {
   const long long nsb = (N + T - 1) / T;
-  auto g = [&](long long i) {
-    const long long q = floordiv(i, N);
-    return q * nsb + (i - q * N) / T;
-  };
-  return g(hi) - g(lo) + 1;
+  if (W == T) {
+    auto g = [&](long long i) {
+      const long long q = floordiv(i, N);
+      return q * nsb + (i - q * N) / T;
+    };
+    return g(hi) - g(lo) + 1;
+  }
+  long long n = 0;
+  for (long long i = lo; i <= hi; ++n) {
+    const long long k = floordiv(i, N), j = (i - k * N) / T;
+    i = k * N + std::min<long long>(j * T + W, N);
+  }
+  return n;
 }
 
-void segments(int lo, int hi, int N, int T, std::vector<Seg>* out) {
+void segments(int lo, int hi, int N, int T, int W, std::vector<Seg>* out) {
   out->clear();
   long long i = lo;
   while (i <= hi) {
     long long k = floordiv(i, N);
     long long ip = i - k * N;
     long long j = ip / T;
-    long long end = k * N + std::min<long long>((j + 1) * T, N) - 1;
+    long long end = k * N + std::min<long long>(j * T + W, N) - 1;
     out->push_back({(int)k, (int)j});
     i = std::min<long long>(hi, end) + 1;
   }
@@ -315,7 +326,8 @@ std::vector<PairBox> pairs_view(const std::vector<PairTmp>& pairs) {
 }
 
 // Task lists for one sub-box shape T: per level, sub-boxes of T (the last ones clipped
-// at the mesh edge), and for every pair each (sub-box, periodic copy) its box meets.
+// at the mesh edge), and for every pair each (sub-box, periodic copy) its box meets;
+// along z the segments follow the windows of zwin points (zwin = T[2]: plain tiling).
 // Fills lev[k].sub_base, the CSR offsets, the 2-int4 task records (sorted by pair
 // inside every sub-box), the work list (heaviest sub-box first) and, if ranks is
 // non-NULL (the integration tasks), the number of tasks of every pair, the size of its
@@ -325,7 +337,7 @@ std::vector<PairBox> pairs_view(const std::vector<PairTmp>& pairs) {
 // segments and r12 the task's index among them, so the tasks of one x-segment are
 // contiguous and every x-segment block starts at nc2(L+1) t0 ns12.
 int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector<int4>& hot_a,
-                const int* T, LevelInfo* lev, std::vector<long long>* sub_off,
+                const int* T, int zwin, LevelInfo* lev, std::vector<long long>* sub_off,
                 std::vector<int4>* task, std::vector<int4>* work, long long* nent_out,
                 long long* nwork_out, long long* nsub_out, std::vector<int>* ranks,
                 std::vector<long long>* psize, long long* chunk_io, bool prune = false) {
@@ -337,9 +349,11 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
     return block_beyond(t.q, ai, bi, lv.N, plan->prune_blen, !plan->skew, plan->prune_lam);
   };
   // unwrapped grid range [a, b] of segment s of [lo, hi] along an axis of N points
-  auto seg_range = [](int lo, int hi, int N, int Td, const Seg& s, long long* a, long long* b) {
+  const int Wd[3] = {T[0], T[1], zwin};
+  auto seg_range = [](int lo, int hi, int N, int Td, int Wn, const Seg& s, long long* a,
+                      long long* b) {
     const long long s0 = (long long)s.j * Td;
-    const long long ext = std::min<long long>(Td, N - s0);
+    const long long ext = std::min<long long>(Wn, N - s0);
     const long long o = (long long)s.k * N + s0;
     *a = std::max<long long>(lo, o);
     *b = std::min<long long>(hi, o + ext - 1);
@@ -367,14 +381,14 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
     for (long long p = p0; p < p1; ++p) {
       const PairBox& t = pairs[p];
       const LevelInfo& lv = lev[t.level];
-      for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
+      for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], Wd[d], &sg[d]);
       long long a[3], b[3];
       for (auto& s0 : sg[0]) {
-        seg_range(t.lo[0], t.hi[0], lv.N[0], T[0], s0, &a[0], &b[0]);
+        seg_range(t.lo[0], t.hi[0], lv.N[0], T[0], Wd[0], s0, &a[0], &b[0]);
         for (auto& s1 : sg[1]) {
-          seg_range(t.lo[1], t.hi[1], lv.N[1], T[1], s1, &a[1], &b[1]);
+          seg_range(t.lo[1], t.hi[1], lv.N[1], T[1], Wd[1], s1, &a[1], &b[1]);
           for (auto& s2 : sg[2]) {
-            seg_range(t.lo[2], t.hi[2], lv.N[2], T[2], s2, &a[2], &b[2]);
+            seg_range(t.lo[2], t.hi[2], lv.N[2], T[2], Wd[2], s2, &a[2], &b[2]);
             if (beyond(t, lv, a, b)) continue;
             c[lv.sub_base + ((long long)s0.j * lv.nsb[1] + s1.j) * lv.nsb[2] + s2.j]++;
           }
@@ -408,7 +422,7 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
     for (long long p = p0; p < p1; ++p) {
       const PairBox& t = pairs[p];
       const LevelInfo& lv = lev[t.level];
-      for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], &sg[d]);
+      for (int d = 0; d < 3; ++d) segments(t.lo[d], t.hi[d], lv.N[d], T[d], Wd[d], &sg[d]);
       const int L = hot_a[p].w;
       int n[3];
       bool bad = false;
@@ -438,7 +452,7 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
         for (size_t k = 0; k < sg[d].size(); ++k) {
           const Seg& sgm = sg[d][k];
           const long long s0 = (long long)sgm.j * T[d];
-          const long long ext = std::min<long long>(T[d], lv.N[d] - s0);
+          const long long ext = std::min<long long>(Wd[d], lv.N[d] - s0);
           const long long o = (long long)sgm.k * lv.N[d] + s0;
           const long long a = std::max<long long>(t.lo[d], o);
           const long long b = std::min<long long>(t.hi[d], o + ext - 1);
@@ -500,7 +514,7 @@ int build_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
 // of the pairs' task counts in pair order and *nent_out, and, for the integration shape,
 // each pair's task count (ranks) and W block size (psize).  Same limits as build_tasks.
 int count_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector<int4>& hot_a,
-                const int* T, LevelInfo* lev, long long* nsub_out, std::vector<long long>* toff,
+                const int* T, int zwin, LevelInfo* lev, long long* nsub_out, std::vector<long long>* toff,
                 long long* nent_out, std::vector<int>* ranks, std::vector<long long>* psize) {
   const int K = plan->nlev;
   const long long np = (long long)pairs.size();
@@ -523,7 +537,7 @@ int count_tasks(Plan* plan, const std::vector<PairBox>& pairs, const std::vector
     int n[3];
     for (int d = 0; d < 3; ++d) {
       n[d] = t.hi[d] - t.lo[d] + 1;
-      ns[d] = nseg(t.lo[d], t.hi[d], lv.N[d], T[d]);
+      ns[d] = nseg(t.lo[d], t.hi[d], lv.N[d], T[d], d == 2 ? zwin : T[d]);
       bad = bad || n[d] > 65535 || ns[d] > (long long)kSegMax;
     }
     const long long c = ns[0] * ns[1] * ns[2];
@@ -729,13 +743,18 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     }
     for (int d = 0; d < 3; ++d) plan->tile[d] = desc->tile[d];
   }
-  if (desc->tile_integ[0] || desc->tile_integ[1] || desc->tile_integ[2]) {
-    if (!(gpw_tile_supported(desc->tile_integ[0], desc->tile_integ[1], desc->tile_integ[2]) &
-          GPW_TILE_INTEG)) {
-      set_error("gpw_plan: unsupported integration tile shape");
+  const bool integ_default = !(desc->tile_integ[0] || desc->tile_integ[1] || desc->tile_integ[2]);
+  if (!integ_default) {
+    const int zw = desc->integ_zwin ? desc->integ_zwin : desc->tile_integ[2];
+    if (!gpw_integ_zwin_supported(desc->tile_integ[0], desc->tile_integ[1], desc->tile_integ[2], zw)) {
+      set_error("gpw_plan: unsupported integration tile shape or z window");
       return GPW_EINVAL;
     }
     for (int d = 0; d < 3; ++d) plan->tile_i[d] = desc->tile_integ[d];
+    plan->zwin_i = zw;
+  } else if (desc->integ_zwin) {
+    set_error("gpw_plan: integ_zwin needs an explicit tile_integ");
+    return GPW_EINVAL;
   }
   if (desc->colloc_warps != 0 && desc->colloc_warps != 4 && desc->colloc_warps != 6 &&
       desc->colloc_warps != 8) {
@@ -775,6 +794,7 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     plan->tile_i[0] = kT0;
     plan->tile_i[1] = kT1;
     plan->tile_i[2] = kT2;
+    plan->zwin_i = kT2;
   }
   plan->nw_colloc_req = desc->colloc_warps;
   plan->natm = desc->natm;
@@ -1201,6 +1221,18 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     plan->flops_ip1 += 2.0 * (L + 2) * (double)pts;
   }
   plan->lmax = lmax;
+  if (integ_default && !plan->skew) {
+    // default integration sub-boxes: 8x8x16 with 48-point z windows (a pair box crosses
+    // fewer window ends than sub-box ends: fewer tasks, one y contraction per window)
+    // when the staging of this plan's degrees leaves two thread blocks per SM (228 KB of
+    // shared memory, 1 KB of it reserved per block), else plain 8x8x32 sub-boxes
+    const int tw[3] = {8, 8, 16};
+    const size_t two_blocks = (228 * 1024 - 2 * 1024) / 2;
+    const size_t need = integ_block_smem(tw, 48, lmax);
+    const bool win = need > 0 && need <= two_blocks;
+    for (int d = 0; d < 3; ++d) plan->tile_i[d] = win ? tw[d] : (d == 2 ? 32 : 8);
+    plan->zwin_i = win ? 48 : 32;
+  }
   plan->tab_total = tab_total;
   plan->coef_total = coef_total;
   plan->xt_total = xt_total;
@@ -1221,10 +1253,12 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
     for (size_t p = 0; p < pv.size(); ++p) H->prune[p] = pv[p].q;
   }
   int rc = host_tasks
-               ? build_tasks(plan, pv, H->hot_a, plan->tile, plan->lev, &H->sub_off_c, &H->task_c,
+               ? build_tasks(plan, pv, H->hot_a, plan->tile, plan->tile[2], plan->lev,
+                             &H->sub_off_c, &H->task_c,
                              &H->work_c, &plan->nent, &plan->nwork, &plan->nsub_total, nullptr,
                              nullptr, nullptr, plan->prune)
-               : count_tasks(plan, pv, H->hot_a, plan->tile, plan->lev, &plan->nsub_total,
+               : count_tasks(plan, pv, H->hot_a, plan->tile, plan->tile[2], plan->lev,
+                             &plan->nsub_total,
                              &H->toff_c, &plan->nent, nullptr, nullptr);
   if (rc) return rc;
   for (int k = 0; k < K; ++k) plan->lev_i[k] = plan->lev[k];
@@ -1236,10 +1270,12 @@ int build_host_plan(const gpw_desc* desc, Plan* plan, HostArrays* H) {
   // so that no sub-box with many tasks is left running alone at the end
   long long chunk = desc->integ_chunk > 0 ? desc->integ_chunk : -1;
   if (host_tasks) {
-    rc = build_tasks(plan, pv, H->hot_a, plan->tile_i, plan->lev_i, &H->sub_off_i, &H->task_i,
+    rc = build_tasks(plan, pv, H->hot_a, plan->tile_i, plan->zwin_i, plan->lev_i,
+                     &H->sub_off_i, &H->task_i,
                      &H->work_i, &plan->nent_i, &plan->nwork_i, &nsub_i, &ranks, &psize, &chunk);
   } else {
-    rc = count_tasks(plan, pv, H->hot_a, plan->tile_i, plan->lev_i, &nsub_i, &H->toff_i,
+    rc = count_tasks(plan, pv, H->hot_a, plan->tile_i, plan->zwin_i, plan->lev_i, &nsub_i,
+                     &H->toff_i,
                      &plan->nent_i, &ranks, &psize);
     if (chunk < 0) chunk = default_chunk(plan->nent_i);
   }

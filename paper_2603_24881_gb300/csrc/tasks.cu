@@ -23,6 +23,7 @@ namespace {
 
 struct TaskGeom {
   int T[3];
+  int C[3];  // z windows of C[d] T[d] points (C = 1: plain tiling)
   int N[GPW_MAX_LEVELS][3];
   int nsb[GPW_MAX_LEVELS][3];
   long long sub_base[GPW_MAX_LEVELS];
@@ -67,10 +68,31 @@ __host__ __device__ __forceinline__ long long floordiv_d(long long a, long long 
   return q;
 }
 
-// unwrapped cell index of grid index i: period * nsb + sub-box
-__host__ __device__ __forceinline__ long long cell_of(long long i, int N, int T, int nsb) {
+// Segments of a pair box along an axis of N points cut into nsb sub-boxes of T, whose
+// blocks see windows of C T points from their sub-box start (C = 1: plain tiling): a
+// segment starts at the box start or where the previous one ended, belongs to the
+// sub-box it starts in and ends with that sub-box's window (clipped at the period).  In
+// the box's first period (q0) segments start in sub-boxes j0, j0 + C, ...; in later ones
+// in 0, C, 2C, ...
+struct AxisSeg {
+  long long q0, j0, nfirst, per;
+};
+
+__host__ __device__ __forceinline__ AxisSeg axis_seg(int lo, int N, int T, int nsb, int C) {
+  AxisSeg a;
+  a.q0 = floordiv_d(lo, N);
+  a.j0 = ((long long)lo - a.q0 * N) / T;
+  a.nfirst = (nsb - a.j0 + C - 1) / C;
+  a.per = (nsb + C - 1) / C;
+  return a;
+}
+
+// index of the segment holding grid index i >= lo
+__host__ __device__ __forceinline__ long long seg_of(long long i, const AxisSeg& a, int N, int T, int C) {
   const long long q = floordiv_d(i, N);
-  return q * nsb + (i - q * N) / T;
+  const long long j = (i - q * N) / T;
+  if (q == a.q0) return (j - a.j0) / C;
+  return a.nfirst + (q - a.q0 - 1) * a.per + j / C;
 }
 
 struct SegD {
@@ -81,13 +103,21 @@ struct SegD {
 // segment k of the pair box [lo, lo + n - 1] along axis d: the packed record fields of
 // build_tasks (length m, start u inside the sub-box, start t inside the pair box | n << 16)
 // and the sub-box coordinate j
-__host__ __device__ __forceinline__ SegD segment(int lo, int n, int N, int T, int nsb, long long k, int d) {
+__host__ __device__ __forceinline__ SegD segment(int lo, int n, int N, int T, int nsb, int C,
+                                                 long long k, int d) {
   const long long hi = (long long)lo + n - 1;
-  const long long g = cell_of(lo, N, T, nsb) + k;
-  const long long q = floordiv_d(g, nsb);
-  const long long j = g - q * nsb;
+  const AxisSeg as = axis_seg(lo, N, T, nsb, C);
+  long long q, j;
+  if (k < as.nfirst) {
+    q = as.q0;
+    j = as.j0 + k * C;
+  } else {
+    const long long r = k - as.nfirst;
+    q = as.q0 + 1 + r / as.per;
+    j = (r % as.per) * C;
+  }
   const long long s0 = j * T;
-  const long long ext = std::min<long long>(T, (long long)N - s0);
+  const long long ext = std::min<long long>((long long)C * T, (long long)N - s0);
   const long long o = q * N + s0;
   const long long a = std::max<long long>(lo, o);
   const long long b = std::min<long long>(hi, o + ext - 1);
@@ -99,8 +129,9 @@ __host__ __device__ __forceinline__ SegD segment(int lo, int n, int N, int T, in
   return r;
 }
 
-__host__ __device__ __forceinline__ long long nseg_d(int lo, int n, int N, int T, int nsb) {
-  return cell_of((long long)lo + n - 1, N, T, nsb) - cell_of(lo, N, T, nsb) + 1;
+__host__ __device__ __forceinline__ long long nseg_d(int lo, int n, int N, int T, int nsb, int C) {
+  const AxisSeg as = axis_seg(lo, N, T, nsb, C);
+  return seg_of((long long)lo + n - 1, as, N, T, C) + 1;
 }
 
 // pair of task t: the last p with toff[p] <= t
@@ -131,8 +162,8 @@ __host__ __device__ __forceinline__ TaskPos locate(const TaskGeom& G, const int4
   q.a = hot_a[q.p];
   q.b = hot_b[q.p];
   const int lev = q.b.w;
-  q.ns1 = nseg_d(q.a.y, q.b.y, G.N[lev][1], G.T[1], G.nsb[lev][1]);
-  q.ns2 = nseg_d(q.a.z, q.b.z, G.N[lev][2], G.T[2], G.nsb[lev][2]);
+  q.ns1 = nseg_d(q.a.y, q.b.y, G.N[lev][1], G.T[1], G.nsb[lev][1], G.C[1]);
+  q.ns2 = nseg_d(q.a.z, q.b.z, G.N[lev][2], G.T[2], G.nsb[lev][2], G.C[2]);
   q.k2 = q.r % q.ns2;
   q.k1 = (q.r / q.ns2) % q.ns1;
   q.k0 = q.r / (q.ns1 * q.ns2);
@@ -150,9 +181,9 @@ __global__ void task_keys_kernel(TaskGeom G, const int4* __restrict__ hot_a,
        t += (long long)gridDim.x * blockDim.x) {
     const TaskPos q = locate(G, hot_a, hot_b, toff, t);
     const int lev = q.b.w;
-    const SegD s0 = segment(q.a.x, q.b.x, G.N[lev][0], G.T[0], G.nsb[lev][0], q.k0, 0);
-    const SegD s1 = segment(q.a.y, q.b.y, G.N[lev][1], G.T[1], G.nsb[lev][1], q.k1, 1);
-    const SegD s2 = segment(q.a.z, q.b.z, G.N[lev][2], G.T[2], G.nsb[lev][2], q.k2, 2);
+    const SegD s0 = segment(q.a.x, q.b.x, G.N[lev][0], G.T[0], G.nsb[lev][0], G.C[0], q.k0, 0);
+    const SegD s1 = segment(q.a.y, q.b.y, G.N[lev][1], G.T[1], G.nsb[lev][1], G.C[1], q.k1, 1);
+    const SegD s2 = segment(q.a.z, q.b.z, G.N[lev][2], G.T[2], G.nsb[lev][2], G.C[2], q.k2, 2);
     unsigned key = (unsigned)(G.sub_base[lev] + (s0.j * G.nsb[lev][1] + s1.j) * G.nsb[lev][2] + s2.j);
     if (G.prune) {
       // the task box: from its start in the pair box (t) and its length (m)
@@ -176,9 +207,9 @@ __global__ void task_fill_kernel(TaskGeom G, const int4* __restrict__ hot_a,
        s += (long long)gridDim.x * blockDim.x) {
     const TaskPos q = locate(G, hot_a, hot_b, toff, (long long)perm[s]);
     const int lev = q.b.w, L = q.a.w;
-    const SegD s0 = segment(q.a.x, q.b.x, G.N[lev][0], G.T[0], G.nsb[lev][0], q.k0, 0);
-    const SegD s1 = segment(q.a.y, q.b.y, G.N[lev][1], G.T[1], G.nsb[lev][1], q.k1, 1);
-    const SegD s2 = segment(q.a.z, q.b.z, G.N[lev][2], G.T[2], G.nsb[lev][2], q.k2, 2);
+    const SegD s0 = segment(q.a.x, q.b.x, G.N[lev][0], G.T[0], G.nsb[lev][0], G.C[0], q.k0, 0);
+    const SegD s1 = segment(q.a.y, q.b.y, G.N[lev][1], G.T[1], G.nsb[lev][1], G.C[1], q.k1, 1);
+    const SegD s2 = segment(q.a.z, q.b.z, G.N[lev][2], G.T[2], G.nsb[lev][2], G.C[2], q.k2, 2);
     int w = 0;
     if (G.integ) {
       const long long S = nc2(L + 1 + G.xr);
@@ -232,7 +263,11 @@ TaskGeom geom(const Plan& P, bool integ) {
   TaskGeom G{};
   const LevelInfo* lev = integ ? P.lev_i : P.lev;
   const int* T = integ ? P.tile_i : P.tile;
-  for (int d = 0; d < 3; ++d) G.T[d] = T[d];
+  for (int d = 0; d < 3; ++d) {
+    G.T[d] = T[d];
+    G.C[d] = 1;
+  }
+  if (integ) G.C[2] = P.zwin_i / P.tile_i[2];
   for (int k = 0; k < P.nlev; ++k) {
     for (int d = 0; d < 3; ++d) {
       G.N[k][d] = lev[k].N[d];

@@ -51,6 +51,13 @@ def test_tile_support_mask_without_gpu():
         assert lib.gpw_tile_supported(*t) == 2, t
     assert lib.gpw_tile_supported(3, 8, 16) == 0
     assert lib.gpw_tile_supported(0, 0, 0) == 0
+    # z windows: every integration shape with its own height, and the overlapping ones
+    for t in binding.TILES_INTEG:
+        assert lib.gpw_integ_zwin_supported(*t, t[2]) == 1, t
+    for t in binding.TILES_INTEG_ZWIN:
+        assert lib.gpw_integ_zwin_supported(*t) == 1, t
+    assert lib.gpw_integ_zwin_supported(8, 8, 16, 32) == 0
+    assert lib.gpw_integ_zwin_supported(3, 8, 16, 16) == 0
 
 
 def test_missing_library_fails_loudly(monkeypatch, tmp_path):

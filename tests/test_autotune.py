@@ -32,7 +32,7 @@ def test_tune_picks_minima_and_caches(tmp_path):
     assert ch.tile_integ == (8, 4, 64) and ch.integ_chunk == 256
     n = len(calls)
     assert n == len(autotune.TILES) - 1 + len(autotune.WARPS) + len(autotune.TILES_INTEG) + \
-        len(autotune.CHUNKS) + 1  # the failing candidate is attempted once
+        len(autotune.TILES_INTEG_ZWIN) + len(autotune.CHUNKS) + 1  # the failing one once
     data = json.load(open(cache))
     assert len(data) == 1 and "tile=(2, 8, 16)" not in next(iter(data.values()))["timings"]
     # cache hit: no new measurements, same choice
@@ -72,3 +72,27 @@ def test_signature_tells_cell_shapes_apart():
     rc = systems.rotated(s, systems.rotation(12))
     assert not np.all(rc.lattice == np.diag(np.diag(rc.lattice)))
     assert autotune.signature([s]) != autotune.signature([rc])
+
+
+def test_tune_windowed_integration_candidate(tmp_path):
+    # an integration candidate with overlapping z windows is passed to the plan as
+    # tile_integ + integ_zwin, and a choice of it round-trips through the cache
+    seen = []
+
+    def m(systems, kw):
+        seen.append(dict(kw))
+        zw = kw.get("integ_zwin")
+        i = 5.0 if (kw.get("tile_integ"), zw) == ((8, 8, 16), 48) else 9.0
+        return {"collocate": 1.0, "integrate": i}
+
+    cache = str(tmp_path / "tune.json")
+    s = workloads.small_water(4, seed=11)
+    ch = autotune.tune(s, cache_path=cache, measure=m, tiles=[(4, 8, 16)], warps=[0],
+                       chunks=[0], tiles_integ=[(8, 8, 32), (8, 8, 16, 48)])
+    assert ch.tile_integ == (8, 8, 16, 48)
+    kw = ch.plan_kwargs()
+    assert kw["tile_integ"] == (8, 8, 16) and kw["integ_zwin"] == 48
+    assert any(k.get("integ_zwin") is None and k.get("tile_integ") == (8, 8, 32) for k in seen)
+    ch2 = autotune.tune(s, cache_path=cache, measure=m, tiles=[(4, 8, 16)], warps=[0],
+                        chunks=[0], tiles_integ=[(8, 8, 32), (8, 8, 16, 48)])
+    assert ch2.plan_kwargs() == kw

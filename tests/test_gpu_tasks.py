@@ -30,6 +30,7 @@ CASES = {
     "water4_tau": (lambda: workloads.config("water4"), dict(tau=True)),
     "f_shells": (lambda: systems.resolved(seed=8, shells=((0, 1), (1, 1), (2, 1), (3, 1)), natm=3), {}),
     "water32": (lambda: workloads.config("water32"), dict(integ_chunk=256)),
+    "water4_plain_z": (lambda: workloads.config("water4"), dict(tile_integ=(8, 8, 32))),
 }
 
 
