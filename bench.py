@@ -65,9 +65,9 @@ def _workload_desc(name: str, system, stats) -> str:
 # scaled by the work it processes), valid while the kernels and the plan (task lists,
 # work order) are unchanged: sha256 of csrc/kernels.cu + csrc/plan.cpp at capture time.
 TRAFFIC = {
-    # integration at degree L+1 (8x8x32 sub-box): read + write of one 32-water launch
-    # (1.804 GB) scaled by pair-points to the 256-water launch
-    "integrate_ip1": {"bytes_per_launch": 1.3113e+10, "src_sha": "3c2de7f0d0be42da",
+    # integration at degree L+1 (8x8x16 sub-boxes, 48-point z windows): read + write of
+    # one 32-water launch (1.394 GB) scaled by pair-points to the 256-water launch
+    "integrate_ip1": {"bytes_per_launch": 1.0131e+10, "src_sha": "76196fa12399129e",
                       "capture": "profiles/integrate_traffic_water32.md"},
 }
 
