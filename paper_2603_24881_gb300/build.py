@@ -15,7 +15,7 @@ LIB = os.path.join(BUILD, "libgpw.so")
 INCLUDE = os.path.join(ROOT, "include")
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cpp", "kernels.cu", "capi.cu", "noalloc.cu", "tasks.cu"]
+SOURCES = ["plan.cpp", "kernels.cu", "capi.cu", "noalloc.cu", "tasks.cu", "rfft.cu"]
 HEADERS = ["gpw_internal.h", "plan_host.h", "kernels.h"]
 
 

@@ -146,7 +146,7 @@ void free_plan(Plan* P, cudaStream_t stream = nullptr, bool sync = true) {
                   d.atom_list, d.tab, d.coef, d.part, d.pgrad, d.grids, d.spec, d.fspec,
                   d.fspec2, d.fine_a, d.fine_b, d.red, d.energies, d.err, d.tabs, d.view, d.g2tab,
                   d.g1tab, d.grad3, d.fspec3, d.mono_t, d.xfer_D, d.xfer_V, d.xfer_g,
-                  P->fft_work};
+                  d.fft_pack, d.fft_tw, P->fft_work};
   bool any = false;
   for (void* q : ptrs) any = any || q != nullptr;
   if (any && sync) cudaDeviceSynchronize();
@@ -155,7 +155,7 @@ void free_plan(Plan* P, cudaStream_t stream = nullptr, bool sync = true) {
     if (q) cudaFreeAsync(q, fs);
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
   P->ev_pool.clear();
-  for (int k = 0; k < GPW_MAX_LEVELS; ++k) P->fft_d2z[k] = P->fft_z2d[k] = nullptr;
+  for (int k = 0; k < GPW_MAX_LEVELS; ++k) P->fft_d2z[k] = P->fft_z2d[k] = P->fft_z2z[k] = nullptr;
   P->fft_work = nullptr;
   d = DeviceArrays();
   recycle_host_arrays(P->host);
@@ -197,9 +197,22 @@ long long estimate_bytes(const Plan& P, const HostArrays& H) {
     b += sz(3 * P.fine_n, sizeof(double)) + sz(P.fine_spec_n, sizeof(cufftDoubleComplex));
   if (P.skew) b += sz((long long)H.mono_t.size(), sizeof(double));
   size_t ws = 0;  // one work area: the largest transform of the plan
-  for (int k = 0; k < P.nlev; ++k)
+  bool packed = false;
+  for (int k = 0; k < P.nlev; ++k) {
     ws = std::max(ws, std::max(fft_estimate(P.lev[k].N, CUFFT_D2Z), fft_estimate(P.lev[k].N, CUFFT_Z2D)));
+    if (P.lev[k].N[2] % 2 == 0) {
+      const int h[3] = {P.lev[k].N[0], P.lev[k].N[1], P.lev[k].N[2] / 2};
+      ws = std::max(ws, fft_estimate(h, CUFFT_Z2Z));
+      packed = true;
+    }
+  }
   b += (long long)ws;
+  if (packed) {
+    b += sz(P.fine_n / 2, sizeof(cufftDoubleComplex));  // the half-length grid
+    long long ntw = 0;
+    for (int k = 0; k < P.nlev; ++k) ntw += P.lev[k].N[2] / 2 + 1;
+    b += sz(ntw, sizeof(cufftDoubleComplex));           // its twiddles
+  }
   return b;
 }
 
@@ -303,12 +316,22 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
 #define GPW_TRY2(x) \
   if ((rc = (x)) != GPW_OK) return rc
   size_t fws = 0;
+  std::vector<cufftDoubleComplex> tw;
   for (int k = 0; k < P->nlev; ++k) {
     const LevelInfo& lv = P->lev[k];
     GPW_TRY2(fft_entry(lv.N, CUFFT_D2Z, &P->fft_d2z[k]));
     GPW_TRY2(fft_entry(lv.N, CUFFT_Z2D, &P->fft_z2d[k]));
     fws = std::max(fws, std::max(P->fft_d2z[k]->ws, P->fft_z2d[k]->ws));
+    if (lv.N[2] % 2 == 0) {
+      const int h[3] = {lv.N[0], lv.N[1], lv.N[2] / 2};
+      GPW_TRY2(fft_entry(h, CUFFT_Z2Z, &P->fft_z2z[k]));
+      fws = std::max(fws, P->fft_z2z[k]->ws);
+      if (!d.fft_pack) GPW_TRY2(dalloc(&d.fft_pack, P->fine_n / 2, &b));
+      P->tw_off[k] = (long long)tw.size();
+      rfft_twiddles(lv.N[2], &tw);
+    }
   }
+  if (!tw.empty()) GPW_TRY2(upload(&d.fft_tw, tw, &b));
   GPW_TRY2(dalloc(&P->fft_work, (long long)((fws + sizeof(double) - 1) / sizeof(double)), &b));
   {
     std::vector<PlanView> v(1, PlanView());
@@ -330,7 +353,27 @@ int create_device(Plan* P, HostArrays& H, cudaStream_t s) {
 }
 #undef GPW_TRY2
 
+// Real transforms of level k (unnormalised, cuFFT's conventions).  With an even N2 and a
+// 16-byte aligned real grid they run as the complex transform of N0 x N1 x N2/2 plus one
+// pass that untangles (forward) or packs (inverse) the half spectrum (rfft.cu); the real
+// input of the forward transform and the half spectrum of the inverse stay unchanged.
+bool packed(const Plan& P, int k, const void* real) {
+  return P.fft_z2z[k] && P.d.fft_pack && P.d.fft_tw && (reinterpret_cast<uintptr_t>(real) & 15) == 0;
+}
+
 int fft_d2z(Plan& P, int k, const double* in, cufftDoubleComplex* out, cudaStream_t s) {
+  if (packed(P, k, in)) {
+    {
+      FftEntry* e = P.fft_z2z[k];
+      std::lock_guard<std::mutex> lk(e->mu);
+      GPW_CF(cufftSetStream(e->h, s));
+      GPW_CF(cufftSetWorkArea(e->h, P.fft_work));
+      GPW_CF(cufftExecZ2Z(e->h, reinterpret_cast<cufftDoubleComplex*>(const_cast<double*>(in)),
+                          P.d.fft_pack, CUFFT_FORWARD));
+    }
+    GPW_CK(launch_rfft_untangle(P.d.fft_pack, out, P.d.fft_tw + P.tw_off[k], P.lev[k].N, s));
+    return GPW_OK;
+  }
   FftEntry* e = P.fft_d2z[k];
   std::lock_guard<std::mutex> lk(e->mu);
   GPW_CF(cufftSetStream(e->h, s));
@@ -340,6 +383,16 @@ int fft_d2z(Plan& P, int k, const double* in, cufftDoubleComplex* out, cudaStrea
 }
 
 int fft_z2d(Plan& P, int k, cufftDoubleComplex* in, double* out, cudaStream_t s) {
+  if (packed(P, k, out)) {
+    GPW_CK(launch_rfft_pack(in, P.d.fft_pack, P.d.fft_tw + P.tw_off[k], P.lev[k].N, s));
+    FftEntry* e = P.fft_z2z[k];
+    std::lock_guard<std::mutex> lk(e->mu);
+    GPW_CF(cufftSetStream(e->h, s));
+    GPW_CF(cufftSetWorkArea(e->h, P.fft_work));
+    GPW_CF(cufftExecZ2Z(e->h, P.d.fft_pack, reinterpret_cast<cufftDoubleComplex*>(out),
+                        CUFFT_INVERSE));
+    return GPW_OK;
+  }
   FftEntry* e = P.fft_z2d[k];
   std::lock_guard<std::mutex> lk(e->mu);
   GPW_CF(cufftSetStream(e->h, s));

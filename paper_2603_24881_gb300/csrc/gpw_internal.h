@@ -163,6 +163,8 @@ struct DeviceArrays {
   double* xfer_D = nullptr;
   double* xfer_V = nullptr;
   double* xfer_g = nullptr;
+  cufftDoubleComplex* fft_pack = nullptr;  // half-length complex grid of the real transforms
+  cufftDoubleComplex* fft_tw = nullptr;    // their twiddles, per level (Plan::tw_off)
   CoefTables* tabs = nullptr;
   PlanView* view = nullptr;   // this plan's view (device)
 };
@@ -212,6 +214,9 @@ struct Plan {
   std::vector<int4> work_c_host, work_i_host;   // copies kept for batch merging
   struct FftEntry* fft_d2z[GPW_MAX_LEVELS] = {nullptr};  // shared cuFFT handles (cache)
   struct FftEntry* fft_z2d[GPW_MAX_LEVELS] = {nullptr};
+  // complex transforms of N0 x N1 x N2/2 for the real ones (N2 even; else nullptr)
+  struct FftEntry* fft_z2z[GPW_MAX_LEVELS] = {nullptr};
+  long long tw_off[GPW_MAX_LEVELS] = {0};  // level twiddles in d.fft_tw
   double* fft_work = nullptr;          // this plan's cuFFT work area
   cudaStream_t alloc_stream = nullptr; // stream of the plan's stream-ordered allocations
   int red_blocks = 0;

@@ -64,6 +64,15 @@ cudaError_t launch_energy_final(const Plan& p, int slot, int nparts, cudaStream_
 cudaError_t launch_finite_check(const Plan& p, const double* x, long long n, cudaStream_t s);
 cudaError_t launch_validate_tasks(const Plan& p, bool integ, cudaStream_t s);
 cudaError_t configure_kernels(Plan* p);
+// rfft.cu: real 3-D transforms of an N[0] x N[1] x N[2] grid (N[2] even) through the
+// complex transform of N[0] x N[1] x N[2]/2: the half spectrum X from that transform Z
+// (untangle), and the Z whose inverse transform is the real inverse of X (pack).
+// tw: the twiddles w^k2 = exp(-2 pi i k2 / N[2]), k2 = 0..N[2]/2 (rfft_twiddles).
+cudaError_t launch_rfft_untangle(const cufftDoubleComplex* Z, cufftDoubleComplex* X,
+                                 const cufftDoubleComplex* tw, const int* N, cudaStream_t s);
+cudaError_t launch_rfft_pack(const cufftDoubleComplex* X, cufftDoubleComplex* Z,
+                             const cufftDoubleComplex* tw, const int* N, cudaStream_t s);
+void rfft_twiddles(int N2, std::vector<cufftDoubleComplex>* out);
 
 constexpr int kRedBlocks = 304;
 constexpr int kRedThreads = 256;

@@ -269,6 +269,36 @@ def test_integration_z_windows(gpw, cases):
         gpw.Plan(s, tile_integ=(8, 8, 32), integ_zwin=48)
 
 
+def test_real_transforms_odd_and_even_meshes(gpw):
+    # the real FFTs of the combine and the restriction run as half-length complex
+    # transforms where the z extent is even and the grid 16-byte aligned, and as cuFFT's
+    # real transforms otherwise: here level 0 and 1 have odd z extents (so level 2's grid
+    # starts at an odd offset too) and the result is the oracle's all the same
+    import dataclasses
+    s = dataclasses.replace(workloads.tiny(),
+                            meshes=np.array([[40, 40, 41], [20, 20, 21], [10, 10, 10]], np.int32))
+    op = oracle.Plan(s)
+    gp = gpw.Plan(s)
+    out = gp.fock(s.D, want_rho=True, want_v=True)
+    ref = op.fock(s.D)
+    assert abs(out["EH"] - ref["EH"]) <= 1e-8 and abs(out["Ex"] - ref["Ex"]) <= 1e-8
+    assert _rel(out["rho"].cpu().numpy(), ref["rho_fine"]) <= RTOL
+    assert _rel(out["v"].cpu().numpy(), ref["v_fine"]) <= RTOL
+    assert _rel(out["V"].cpu().numpy(), ref["V"]) <= RTOL
+
+
+def test_real_transforms_keep_their_inputs(gpw, cases):
+    # the forward transform of a caller's potential (eval_mat) leaves it unchanged
+    s, op = cases["water4"]
+    gp = gpw.Plan(s)
+    vf = torch.as_tensor(s.potential.sample(op.meshes[0]), device="cuda")
+    v0 = vf.clone()
+    V = gp.eval_mat(vf)
+    torch.cuda.synchronize()
+    assert torch.equal(vf, v0)
+    assert _rel(V.cpu().numpy(), op.mat_levels(op.restrict(v0.cpu().numpy()))) <= RTOL
+
+
 def test_unsupported_tile(gpw):
     with pytest.raises(gpw.GpwError):
         gpw.Plan(workloads.tiny(), tile=(3, 8, 16))
