@@ -486,14 +486,23 @@ def main():
                    E=torch.empty(2, dtype=torch.float64, pin_memory=True))
         for _ in range(2):
             plan.fock_grad_host(Dh, out=out)
+        eclk = Clocks(_gpu_id(torch)) if rank == 0 else None
         replicas.barrier(dist)
+        # per step: the host lap and, from events on the call's stream around it, the
+        # device span of its copies and kernels
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(a.steps)]
         t1 = time.perf_counter()
         laps = []
-        for _ in range(a.steps):
+        for i in range(a.steps):
             tl = time.perf_counter()
+            evs[i][0].record()
             plan.fock_grad_host(Dh, out=out)
+            evs[i][1].record()
             laps.append(1e3 * (time.perf_counter() - tl))
         e2e_s = replicas.max_over_ranks(dist, time.perf_counter() - t1, device="cuda")
+        eclocks = eclk.stop() if eclk else None
+        dev = [b.elapsed_time(c) for b, c in evs]
         e2e = {"value": replicas.whole_job_rate(flops_step * a.steps, world, e2e_s) / 1e12,
                "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(Dh.numel() * 8),
@@ -501,7 +510,8 @@ def main():
                "api": "gpw_fock_grad_host through the C ABI (pinned host D in; V, gradient, "
                       "energies out; copies inside the timed region)",
                "ms_per_step": 1e3 * e2e_s / a.steps,
-               "ms_min_max": [min(laps), max(laps)]}
+               "ms_min_max": [min(laps), max(laps)],
+               "device_ms_min_max": [min(dev), max(dev)], "clocks": eclocks}
 
     tau = None
     if a.tau:
