@@ -131,3 +131,48 @@ def test_pair_order_is_shell_pair_primitives_image(lib, name):
     assert np.array_equal(order, np.arange(len(t)))
     ref = oracle.Plan(s).pair_table()
     assert np.array_equal(t[np.lexsort(t[:, ::-1].T)], ref)
+
+
+def _pieces(lo, hi, N, T, W):
+    """Segments of the unwrapped grid range [lo, hi] along an axis of N points with
+    sub-boxes of T whose windows span W points from their start (W = T: plain tiling):
+    each segment runs from where the previous one ended to the end of the window of the
+    sub-box it starts in (clipped at the period)."""
+    n, i = 0, lo
+    while i <= hi:
+        k = i // N
+        j = (i - k * N) // T
+        i = k * N + min(j * T + W, N)
+        n += 1
+    return n
+
+
+@pytest.mark.parametrize("name,kw,win", [
+    ("water4", {}, (8, 8, 16, 48)),                                   # the default
+    ("water4", dict(tile_integ=(8, 8, 16), integ_zwin=48), (8, 8, 16, 48)),
+    ("water4", dict(tile_integ=(8, 8, 32)), (8, 8, 32, 32)),
+    ("tiny", {}, (8, 8, 16, 48)),                                     # windows clipped at N
+    ("water4_triclinic", {}, (4, 8, 16, 16)),                         # plain 4x8x16
+])
+def test_integration_task_count_follows_the_windows(lib, name, kw, win):
+    # the planner's integration task count is the product over the three axes of the
+    # segments each pair box is cut into, counted here from the pair table alone
+    s = workloads.config(name) if name != "tiny" else workloads.tiny()
+    p = binding.Plan(s, commit=False, **kw)
+    st = p.stats()
+    assert tuple(st["tile_integ"]) + (st["integ_zwin"],) == win
+    t = p.pair_table(sort=False)
+    T0, T1, T2, W2 = win
+    want = 0
+    for r in t:
+        N = st["meshes"][r[5]]
+        want += (_pieces(r[6], r[9], N[0], T0, T0) * _pieces(r[7], r[10], N[1], T1, T1) *
+                 _pieces(r[8], r[11], N[2], T2, W2))
+    assert st["nentries_integ"] == want
+    # and the collocation lists are plain 4x8x16 sub-boxes
+    T = st["tile"]
+    want_c = sum(_pieces(r[6], r[9], st["meshes"][r[5]][0], T[0], T[0]) *
+                 _pieces(r[7], r[10], st["meshes"][r[5]][1], T[1], T[1]) *
+                 _pieces(r[8], r[11], st["meshes"][r[5]][2], T[2], T[2]) for r in t)
+    assert st["nentries"] == want_c
+    p.close()
