@@ -875,36 +875,58 @@ __global__ void __launch_bounds__(NW * 32)
         vbase = sVE;
         u0 = u1 = u2 = 0;
       }
-      // U[l2](i1, i0): lanes walk consecutive i1 (rows P2 apart: conflict free)
+      // U[l2](i1, i0): lanes walk consecutive i1 (rows P2 apart: conflict free).  Items
+      // go 32 at a time; a last round of at most 16 items gives each item two lanes, the
+      // lower and the upper half of its z sum, added with one shuffle (lanes k and
+      // k + 16): ceil(m2 / 2) + 1 FP64 instructions instead of m2 with half the lanes idle
       {
         const float inv01 = __frcp_rn((float)m01), inv1 = __frcp_rn((float)m1);
         const int items = (Lx + 1) * m01;
-        for (int it = lane; it < items; it += 32) {
+        const int full = items & ~31, rem = items - full;
+        auto u_item = [&](int it, int z0, int z1, bool store, bool pair) {
           const int l2 = fdiv(it, inv01), q = it - l2 * m01;
           const int i0 = fdiv(q, inv1), i1 = q - i0 * m1;
           const double* vr = vbase + ((u0 + i0) * T1 + (u1 + i1)) * P2 + u2;
           const double* gr = sg2 + l2 * P2;
           double a = 0.0;
-          for (int i2 = 0; i2 < m2; ++i2) a = fma(vr[i2], gr[i2], a);
+          for (int i2 = z0; i2 < z1; ++i2) a = fma(vr[i2], gr[i2], a);
+          if (pair) a += __shfl_down_sync(0xffffffffu, a, 16);
           if constexpr (SK != 0) a *= sR[i0 * T1 + i1];  // R01(i0, i1)
-          sU[l2 * kUS + i1 * P0 + i0] = a;
+          if (store) sU[l2 * kUS + i1 * P0 + i0] = a;
+        };
+        for (int it = lane; it < full; it += 32) u_item(it, 0, m2, true, false);
+        if (rem > 16) {
+          if (lane < rem) u_item(full + lane, 0, m2, true, false);
+        } else if (rem > 0) {
+          const int k = lane & 15, up = lane >> 4, h = (m2 + 1) >> 1;
+          u_item(full + (k < rem ? k : 0), up ? h : 0, up ? m2 : h, up == 0 && k < rem, true);
         }
       }
       __syncwarp();
-      // W[c21](i0) -> the task's slot (compact: item it = c21 m0 + i0, coalesced)
+      // W[c21](i0) -> the task's slot (compact: item it = c21 m0 + i0, coalesced); the
+      // last round split in two halves of the y sum as above
       {
         const float inv0 = __frcp_rn((float)m0);
         const int items = nc2(Lx) * m0;
+        const int full = items & ~31, rem = items - full;
         double* dst = part + apoff + a1.w;
-        for (int it = lane; it < items; it += 32) {
+        auto w_item = [&](int it, int y0, int y1, bool store, bool pair) {
           const int c21 = fdiv(it, inv0), i0 = it - c21 * m0;
           const int dc = s_dec21[Lx][c21];
           const int l2 = dc & 255, l1 = (dc >> 8) & 255;
           const double* ur = sU + l2 * kUS + i0;
           const double* gr = sg1 + l1 * P1;
           double a = 0.0;
-          for (int i1 = 0; i1 < m1; ++i1) a = fma(ur[i1 * P0], gr[i1], a);
-          dst[it] = a;
+          for (int i1 = y0; i1 < y1; ++i1) a = fma(ur[i1 * P0], gr[i1], a);
+          if (pair) a += __shfl_down_sync(0xffffffffu, a, 16);
+          if (store) dst[it] = a;
+        };
+        for (int it = lane; it < full; it += 32) w_item(it, 0, m1, true, false);
+        if (rem > 16) {
+          if (lane < rem) w_item(full + lane, 0, m1, true, false);
+        } else if (rem > 0) {
+          const int k = lane & 15, up = lane >> 4, h = (m1 + 1) >> 1;
+          w_item(full + (k < rem ? k : 0), up ? h : 0, up ? m1 : h, up == 0 && k < rem, true);
         }
       }
     }
