@@ -83,7 +83,7 @@ class _Req:
     plan: Plan | None = None
     bytes: int = 0
     cost: float = 0.0  # estimated GPU work: pair-points of the plan
-    kind: bool = False  # non-orthogonal cell
+    kind: object = False  # what a batch must share: cell kind and integration sub-boxes
     error: BaseException | None = None
     t_prepared: float = 0.0
     t_launch: float = 0.0
@@ -161,7 +161,9 @@ class Server:
     if None); tune_with: a list of sample cells to run the autotuner on (as one batch)
     instead, its choice (cached per GPU and workload class) then serves every request.
     Non-orthogonal cells plan with 4x8x16 sub-boxes for both passes, so a request of that
-    kind fails alone under another explicit shape; batches hold one kind of cell.
+    kind fails alone under another explicit shape; batches hold one kind of cell, and
+    only plans with the same integration sub-boxes (by default they follow a plan's
+    largest degree: cells with f shells take plain 8x8x32 sub-boxes).
     batch_cost: most pair-points (estimated GPU work) per batch, beyond its first
     request; small_cost: the most a request may cost to ride the priority lane;
     lane_cost: the cap on a priority-lane batch's work (default batch_cost);
@@ -282,7 +284,9 @@ class Server:
             st = req.plan.stats()
             req.bytes = int(st["device_bytes"]) + 8 * (2 * nao * nao + 3 * natm + 2)
             req.cost = float(st["pair_points"])
-            req.kind = _skewed(req.system)
+            # plans batch only with plans of the same kernels: orthorhombic or not, and the
+            # same integration sub-boxes (the library default depends on a plan's degrees)
+            req.kind = (_skewed(req.system), tuple(st["tile_integ"]), st["integ_zwin"])
             if req.bytes > self.budget:
                 raise MemoryError(f"request needs {req.bytes} device bytes, budget is {self.budget}")
         except BaseException as ex:  # the request fails alone; the server keeps serving

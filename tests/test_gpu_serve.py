@@ -233,3 +233,30 @@ def test_stream_wait_is_bounded(gpw):
     assert float(b[0, 0]) == 6144.0
     with pytest.raises(gpw.GpwError):
         stream_wait(s, -1.0)
+
+
+def test_server_mixes_integration_shapes(gpw):
+    # cells whose plans take different default integration sub-boxes (f shells: plain
+    # 8x8x32; waters: 8x8x16 with 48-point z windows) are served together: each batch
+    # holds plans of one shape, and every result is the request's alone-run result
+    import systems
+    from paper_2603_24881_gb300.serve import Server
+    cells = [systems.resolved(seed=8, shells=((0, 1), (1, 1), (2, 1), (3, 1)), natm=3),
+             workloads.small_water(4, seed=101),
+             systems.resolved(seed=9, shells=((0, 1), (1, 1), (2, 1), (3, 1)), natm=3),
+             workloads.small_water(4, seed=103)]
+    shapes = set()
+    ref = []
+    for c in cells:
+        p = gpw.Plan(c)
+        st = p.stats()
+        shapes.add((tuple(st["tile_integ"]), st["integ_zwin"]))
+        r = p.fock_grad(c.D)
+        ref.append(dict(V=r["V"].cpu().numpy(), grad=r["grad"].cpu().numpy(), EH=r["EH"], Ex=r["Ex"]))
+        p.close()
+    assert shapes == {((8, 8, 32), 32), ((8, 8, 16), 48)}
+    with Server(max_batch=4, streams=2) as srv:
+        futs = [srv.submit(c, want_grad=True) for c in cells]
+        res = [f.result(timeout=300) for f in futs]
+    for r, want in zip(res, ref):
+        _same(dict(V=r.V, grad=r.grad, EH=r.EH, Ex=r.Ex), want)
