@@ -269,8 +269,11 @@ __device__ __forceinline__ void ycontract_pair(int n0, int n1, const double* __r
                                                const double* __restrict__ r01,
                                                double* __restrict__ out, int lane) {
   const long long n01 = (long long)n0 * n1;
+  // (i0, i1) of item it = i0 n1 + i1, advanced by 32 items with a carry (no division
+  // per item)
+  const int dq = 32 / n1, di = 32 - dq * n1;
+  int i0 = lane / n1, i1 = lane - (lane / n1) * n1;
   for (long long it = lane; it < n01; it += 32) {
-    const int i0 = (int)(it / n1), i1 = (int)(it - (long long)i0 * n1);
     double g[L + 1];
 #pragma unroll
     for (int l1 = 0; l1 <= L; ++l1) g[l1] = g1[l1 * n1 + i1];
@@ -286,6 +289,12 @@ __device__ __forceinline__ void ycontract_pair(int n0, int n1, const double* __r
       for (int l1 = 0; l1 <= L - l2; ++l1) a = fma(x[(long long)(row + l1) * n0], g[l1], a);
       if constexpr (SKEW) a *= f;
       out[l2 * n01 + it] = a;
+    }
+    i0 += dq;
+    i1 += di;
+    if (i1 >= n1) {
+      i1 -= n1;
+      ++i0;
     }
   }
 }
@@ -1387,18 +1396,18 @@ __device__ __forceinline__ double gsq_k(int f0, int f1, int f2, const double* __
 
 // Fine spectrum S(G) = sum_k [|G| < G_k] rho^_k(G) / N_k (unnormalised level DFTs):
 // Fourier interpolation of every level onto the finest grid; one C2R then gives rho.
+// One block row per plane m0 (blockIdx.y), the plane's N1 x (N2/2 + 1) elements along x.
 __global__ void combine_kernel(const KLevels K, const double* __restrict__ g2t,
                                const cufftDoubleComplex* __restrict__ spec,
                                cufftDoubleComplex* __restrict__ fspec) {
   const LevelInfo& f = K.lv[0];
   const int h2 = f.N[2] / 2 + 1;
-  const long long total = (long long)f.N[0] * f.N[1] * h2;
-  for (long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
-       idx += (long long)gridDim.x * blockDim.x) {
-    const int m2 = (int)(idx % h2);
-    const long long r = idx / h2;
-    const int m1 = (int)(r % f.N[1]);
-    const int m0 = (int)(r / f.N[1]);
+  const int plane = f.N[1] * h2;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < plane) {
+    const int m0 = blockIdx.y;
+    const int m1 = j / h2, m2 = j - m1 * h2;
+    const long long idx = (long long)m0 * plane + j;
     const int s0 = signed_freq(m0, f.N[0]), s1 = signed_freq(m1, f.N[1]), s2 = m2;
     const double G2 = gsq_k(m0, m1, m2, g2t, f.N, K);
     double re = 0.0, im = 0.0;
@@ -1408,7 +1417,7 @@ __global__ void combine_kernel(const KLevels K, const double* __restrict__ g2t,
       if (2 * abs(s0) > lv.N[0] - 1 || 2 * abs(s1) > lv.N[1] - 1 || 2 * s2 > lv.N[2] - 1) continue;
       const int i0 = s0 < 0 ? s0 + lv.N[0] : s0;
       const int i1 = s1 < 0 ? s1 + lv.N[1] : s1;
-      const double inv = 1.0 / ((double)lv.N[0] * lv.N[1] * lv.N[2]);
+      const double inv = K.invn[k];
       const cufftDoubleComplex z =
           spec[lv.spec_off + ((long long)i0 * lv.N[1] + i1) * (lv.N[2] / 2 + 1) + s2];
       re += z.x * inv;
@@ -2077,6 +2086,10 @@ KLevels make_klevels(const Plan& p, bool integ) {
     k.gq[i] = p.skew ? tp2 * (bd[0] * be[0] + bd[1] * be[1] + bd[2] * be[2]) : 0.0;
   }
   for (int i = 0; i < 9; ++i) k.rec[i] = p.rec[i];
+  for (int i = 0; i < GPW_MAX_LEVELS; ++i) {
+    const LevelInfo& l = integ ? p.lev_i[i] : p.lev[i];
+    k.invn[i] = i < p.nlev ? 1.0 / ((double)l.N[0] * l.N[1] * l.N[2]) : 0.0;
+  }
   return k;
 }
 
@@ -2505,7 +2518,9 @@ cudaError_t launch_grad(const Plan& p, const double* D, double* grad, cudaStream
 
 cudaError_t launch_combine(const Plan& p, cudaStream_t s) {
   ++p.launches;
-  combine_kernel<<<152 * 8, 256, 0, s>>>(make_klevels(p, false), p.d.g2tab, p.d.spec, p.d.fspec);
+  const LevelInfo& f = p.lev[0];
+  const dim3 grid((unsigned)((f.N[1] * (f.N[2] / 2 + 1) + 255) / 256), (unsigned)f.N[0]);
+  combine_kernel<<<grid, 256, 0, s>>>(make_klevels(p, false), p.d.g2tab, p.d.spec, p.d.fspec);
   return cudaGetLastError();
 }
 

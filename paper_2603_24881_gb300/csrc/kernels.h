@@ -11,6 +11,7 @@ struct KLevels {
   int skew;       // non-orthogonal cell: |G|^2 has cross terms
   double gq[3];   // their coefficients 2 (2 pi)^2 (b0.b1, b0.b2, b1.b2)
   double rec[9];  // reciprocal rows b_d (Cartesian G = 2 pi sum_d s_d b_d)
+  double invn[GPW_MAX_LEVELS];  // 1 / (N0 N1 N2) of every level
 };
 
 KLevels make_klevels(const Plan& p, bool integ);

@@ -36,15 +36,15 @@ __device__ __forceinline__ double2 cconj(double2 a) { return make_double2(a.x, -
 
 // Z: N0 x N1 x M complex (the half-length transform); X: N0 x N1 x (M + 1), the half
 // spectrum; tw[k2] = w^k2 (k2 = 0..M, from the plan: a sine or cosine per element would
-// cost more FP64 work than the transform saves).  One thread per output element.
+// cost more FP64 work than the transform saves).  One thread per output element, one
+// row of blocks per plane k0 (blockIdx.y).
 __global__ void rfft_untangle_kernel(const double2* __restrict__ Z, double2* __restrict__ X,
                                      const double2* __restrict__ tw, int N0, int N1, int M) {
-  const long long total = (long long)N0 * N1 * (M + 1);
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int k2 = (int)(i % (M + 1));
-    const long long r = i / (M + 1);
-    const int k1 = (int)(r % N1), k0 = (int)(r / N1);
+  const int plane = N1 * (M + 1);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < plane) {
+    const int k0 = blockIdx.y, k1 = j / (M + 1), k2 = j - k1 * (M + 1);
+    const long long i = (long long)k0 * plane + j;
     const int q2 = k2 == M ? 0 : k2;
     const int m0 = k0 == 0 ? 0 : N0 - k0, m1 = k1 == 0 ? 0 : N1 - k1, mq = q2 == 0 ? 0 : M - q2;
     const double2 zk = Z[((long long)k0 * N1 + k1) * M + q2];
@@ -57,15 +57,14 @@ __global__ void rfft_untangle_kernel(const double2* __restrict__ Z, double2* __r
 }
 
 // X: N0 x N1 x (M + 1) half spectrum; Z: N0 x N1 x M; tw as above (its conjugate is
-// 1 / w^k2).  One thread per element of Z.
+// 1 / w^k2).  One thread per element of Z, one row of blocks per plane k0.
 __global__ void rfft_pack_kernel(const double2* __restrict__ X, double2* __restrict__ Z,
                                  const double2* __restrict__ tw, int N0, int N1, int M) {
-  const long long total = (long long)N0 * N1 * M;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-       i += (long long)gridDim.x * blockDim.x) {
-    const int k2 = (int)(i % M);
-    const long long r = i / M;
-    const int k1 = (int)(r % N1), k0 = (int)(r / N1);
+  const int plane = N1 * M;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j < plane) {
+    const int k0 = blockIdx.y, k1 = j / M, k2 = j - k1 * M;
+    const long long i = (long long)k0 * plane + j;
     const long long row = ((long long)k0 * N1 + k1) * (M + 1);
     const double2 x = X[row + k2];
     double2 xp;  // X(k0, k1, k2 + M): stored for k2 = 0, else the Hermitian mirror
@@ -80,17 +79,13 @@ __global__ void rfft_pack_kernel(const double2* __restrict__ X, double2* __restr
   }
 }
 
-int grid_for(long long n) {
-  const long long b = (n + 255) / 256;
-  return (int)(b < 152LL * 32 ? (b > 0 ? b : 1) : 152LL * 32);
-}
+dim3 grid_for(int plane, int N0) { return dim3((unsigned)((plane + 255) / 256), (unsigned)N0); }
 
 }  // namespace
 
 cudaError_t launch_rfft_untangle(const cufftDoubleComplex* Z, cufftDoubleComplex* X,
                                  const cufftDoubleComplex* tw, const int* N, cudaStream_t s) {
-  const long long n = (long long)N[0] * N[1] * (N[2] / 2 + 1);
-  rfft_untangle_kernel<<<grid_for(n), 256, 0, s>>>(
+  rfft_untangle_kernel<<<grid_for(N[1] * (N[2] / 2 + 1), N[0]), 256, 0, s>>>(
       reinterpret_cast<const double2*>(Z), reinterpret_cast<double2*>(X),
       reinterpret_cast<const double2*>(tw), N[0], N[1], N[2] / 2);
   return cudaGetLastError();
@@ -98,8 +93,7 @@ cudaError_t launch_rfft_untangle(const cufftDoubleComplex* Z, cufftDoubleComplex
 
 cudaError_t launch_rfft_pack(const cufftDoubleComplex* X, cufftDoubleComplex* Z,
                              const cufftDoubleComplex* tw, const int* N, cudaStream_t s) {
-  const long long n = (long long)N[0] * N[1] * (N[2] / 2);
-  rfft_pack_kernel<<<grid_for(n), 256, 0, s>>>(
+  rfft_pack_kernel<<<grid_for(N[1] * (N[2] / 2), N[0]), 256, 0, s>>>(
       reinterpret_cast<const double2*>(X), reinterpret_cast<double2*>(Z),
       reinterpret_cast<const double2*>(tw), N[0], N[1], N[2] / 2);
   return cudaGetLastError();
