@@ -322,11 +322,13 @@ int gpw_fock_grad(gpw_plan_t plan, const double* D, double* V, double* grad, dou
 
 /* gpw_fock_grad from and to HOST memory: D (host nao x nao) is copied to the device, the
  * Fock build and gradient run on `stream`, and V (host nao x nao), grad (host natm x 3)
- * and energies (host, 2 doubles) are copied back; returns after synchronising `stream`.
+ * and energies (host, 2 doubles) are copied back; returns after synchronising `stream`
+ * and the plan's own copy stream, which takes V back while the gradient kernels run.
  * Pinned (page-locked) host buffers give full-rate copies; pageable ones work too.  The
  * first call on a plan allocates the plan's device copies of D, V and the gradient
- * (2 nao^2 + 3 natm doubles, kept until the plan is destroyed); later calls allocate
- * nothing.  Not a paper operation: the end-to-end form of the same build. */
+ * (2 nao^2 + 3 natm doubles) and creates that stream and one event, all kept until the
+ * plan is destroyed; later calls allocate nothing.  Not a paper operation: the
+ * end-to-end form of the same build. */
 int gpw_fock_grad_host(gpw_plan_t plan, const double* D, double* V, double* grad,
                        double* energies, void* stream);
 

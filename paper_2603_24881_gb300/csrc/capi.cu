@@ -155,6 +155,10 @@ void free_plan(Plan* P, cudaStream_t stream = nullptr, bool sync = true) {
     if (q) cudaFreeAsync(q, fs);
   for (cudaEvent_t e : P->ev_pool) cudaEventDestroy(e);
   P->ev_pool.clear();
+  if (P->xfer_ev) cudaEventDestroy(P->xfer_ev);
+  if (P->xfer_stream) cudaStreamDestroy(P->xfer_stream);
+  P->xfer_ev = nullptr;
+  P->xfer_stream = nullptr;
   for (int k = 0; k < GPW_MAX_LEVELS; ++k) P->fft_d2z[k] = P->fft_z2d[k] = P->fft_z2z[k] = nullptr;
   P->fft_work = nullptr;
   d = DeviceArrays();
@@ -511,23 +515,29 @@ int mat_from_grids(Plan& P, double* V, cudaStream_t s) {
 
 // One integration pass at degree L + 1 serves both V (its monomials of degree <= L) and
 // the gradient contraction: Algorithms 2 and 3 share the task sweep.
-int finish_mat_ip1(Plan& P, const double* D, double* V, double* grad, cudaStream_t s);
 
-int mat_ip1_from_grids(Plan& P, const double* D, double* V, double* grad, cudaStream_t s) {
+int finish_mat_ip1(Plan& P, const double* D, double* V, double* grad, cudaStream_t s,
+                   cudaEvent_t v_ready);
+
+int mat_ip1_from_grids(Plan& P, const double* D, double* V, double* grad, cudaStream_t s,
+                       cudaEvent_t v_ready = nullptr) {
   {
     Phase ph(P, GPW_PHASE_INTEGRATE_IP1, s);
     GPW_CK(launch_integrate(P, 1, s));
   }
-  return finish_mat_ip1(P, D, V, grad, s);
+  return finish_mat_ip1(P, D, V, grad, s, v_ready);
 }
 
-// Per-pair V tensors (degree L+1) -> V and, if grad is non-NULL, the gradient.
-int finish_mat_ip1(Plan& P, const double* D, double* V, double* grad, cudaStream_t s) {
+// Per-pair V tensors (degree L+1) -> V and, if grad is non-NULL, the gradient; v_ready,
+// if given, is recorded on s once V is complete (before the gradient kernels).
+int finish_mat_ip1(Plan& P, const double* D, double* V, double* grad, cudaStream_t s,
+                   cudaEvent_t v_ready = nullptr) {
   {
     Phase ph(P, GPW_PHASE_ASSEMBLE, s);
     GPW_CK(launch_reduce_parts(P, 1, s));
     GPW_CK(launch_assemble_V(P, 1, V, s));
   }
+  if (v_ready) GPW_CK(cudaEventRecord(v_ready, s));
   if (!grad) return GPW_OK;
   Phase ph(P, GPW_PHASE_GRAD, s);
   GPW_CK(launch_grad(P, D, grad, s));
@@ -691,10 +701,10 @@ int fock_async(Plan& P, const double* D, double* V, double* energies_dev, double
 }
 
 int fock_grad_async(Plan& P, const double* D, double* V, double* grad, double* energies_dev,
-                    cudaStream_t s) {
+                    cudaStream_t s, cudaEvent_t v_ready = nullptr) {
   int rc = fock_potential(P, D, energies_dev, nullptr, nullptr, s);
   if (rc) return rc;
-  if ((rc = mat_ip1_from_grids(P, D, V, grad, s))) return rc;
+  if ((rc = mat_ip1_from_grids(P, D, V, grad, s, v_ready))) return rc;
   return check_outputs(P, s, V, (long long)P.nao * P.nao, grad, 3LL * P.natm, P.d.energies, 2);
 }
 
@@ -1108,18 +1118,31 @@ int gpw_fock_grad_host(gpw_plan_t plan, const double* D, double* V, double* grad
     }
     P.device_bytes += (long long)(2 * nn + ng);
   }
+  if (!P.xfer_stream) {
+    e = cudaStreamCreateWithFlags(&P.xfer_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&P.xfer_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      set_error(std::string("gpw_fock_grad_host: ") + cudaGetErrorString(e));
+      return GPW_ECUDA;
+    }
+  }
   e = cudaMemcpyAsync(P.d.xfer_D, D, nn, cudaMemcpyHostToDevice, s);
   if (e != cudaSuccess) {
     set_error(std::string("gpw_fock_grad_host: ") + cudaGetErrorString(e));
     return GPW_ECUDA;
   }
-  int rc = gpw::fock_grad_async(P, P.d.xfer_D, P.d.xfer_V, P.d.xfer_g, P.d.energies, s);
+  // V goes back on the copy stream as soon as it is assembled, while the gradient
+  // kernels run on s
+  int rc = gpw::fock_grad_async(P, P.d.xfer_D, P.d.xfer_V, P.d.xfer_g, P.d.energies, s,
+                                P.xfer_ev);
   if (rc) return rc;
-  e = cudaMemcpyAsync(V, P.d.xfer_V, nn, cudaMemcpyDeviceToHost, s);
+  e = cudaStreamWaitEvent(P.xfer_stream, P.xfer_ev, 0);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(V, P.d.xfer_V, nn, cudaMemcpyDeviceToHost, P.xfer_stream);
   if (e == cudaSuccess) e = cudaMemcpyAsync(grad, P.d.xfer_g, ng, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(energies, P.d.energies, 2 * sizeof(double), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P.xfer_stream);
   if (e != cudaSuccess) {
     set_error(std::string("gpw_fock_grad_host: ") + cudaGetErrorString(e));
     return GPW_ECUDA;

@@ -233,6 +233,10 @@ struct Plan {
   // profiler: event pairs per phase, recorded on the calling stream when enabled
   bool prof = false;
   std::vector<cudaEvent_t> ev_pool;
+  // gpw_fock_grad_host: a stream that copies V back while the gradient kernels run, and
+  // the event that marks V complete (made by its first call)
+  cudaStream_t xfer_stream = nullptr;
+  cudaEvent_t xfer_ev = nullptr;
   std::vector<int> ev_phase;   // phase of each recorded pair (pool index / 2)
   size_t ev_used = 0;
   double prof_ms[GPW_NPHASES] = {0};
