@@ -161,8 +161,10 @@ typedef struct {
                                  points and its y contraction once per window instead
                                  of once per sub-box (the V tensor of Sec. III A; the
                                  sums are the same, in another order).  0 = the
-                                 default (tile_integ[2], or 48 with the default
-                                 sub-boxes); only with tile_integ given otherwise. */
+                                 default: tile_integ[2] when tile_integ is given, else
+                                 what the default sub-boxes take; a non-zero value
+                                 needs an explicit tile_integ (GPW_EINVAL otherwise,
+                                 and for shapes gpw_integ_zwin_supported rejects). */
 } gpw_desc;
 
 /* Sizes and work counts of a plan (gpw_plan_query). */
