@@ -145,7 +145,7 @@ typedef struct {
                                  shapes: gpw_tile_supported, gpw_integ_zwin_supported. */
   int colloc_warps;           /* warps per collocation thread block: 4, 6 or 8; 0 = the
                                  choice with the most resident warps per SM (the
-                                 smaller block on a tie) */
+                                 larger block on a tie) */
   int integ_chunk;            /* most (pair, sub-box) tasks per integration work item
                                  (> 0); 0 = default max(64, tasks / 1216) */
   int xc;                     /* GPW_XC_LDA_X (0, default) or GPW_XC_PBE_X */

@@ -2027,17 +2027,17 @@ size_t integ_smem(int stg) {
 
 // Warps per collocation block: the candidate with the most resident warps per SM, as the
 // occupancy calculator reports it for this shared-memory size (registers included), the
-// smaller block on a tie.
+// larger block on a tie.
 template <int T0, int T1, int T2, int SK = 0>
 int pick_colloc_warps(int stg, int want, int* nw_out, size_t* smem_out) {
   int best = 0;
-  // candidates from the smallest block: a tie in resident warps goes to the smaller
-  // blocks (finer-grained scheduling; 1% faster collocation at 256 waters, where 4, 6
-  // and 8 warps all give 24 resident warps)
-  const void* fns[3] = {(const void*)collocate_kernel<T0, T1, T2, 4, SK>,
+  // a tie in resident warps goes to the larger block: smaller blocks make each sub-box
+  // take longer, which the launch's tail pays on small cells (4-warp blocks ran the
+  // 32-water collocation 30% slower, for 1% on the 256-water one)
+  const void* fns[3] = {(const void*)collocate_kernel<T0, T1, T2, 8, SK>,
                         (const void*)collocate_kernel<T0, T1, T2, 6, SK>,
-                        (const void*)collocate_kernel<T0, T1, T2, 8, SK>};
-  const int nws[3] = {4, 6, 8};
+                        (const void*)collocate_kernel<T0, T1, T2, 4, SK>};
+  const int nws[3] = {8, 6, 4};
   for (int i = 0; i < 3; ++i) {
     if (want != 0 && nws[i] != want) continue;  // a requested count (still must fit)
     const size_t need = colloc_smem<T0, T1, T2>(stg, nws[i]);
