@@ -66,8 +66,8 @@ def _workload_desc(name: str, system, stats) -> str:
 # work order) are unchanged: sha256 of csrc/kernels.cu + csrc/plan.cpp at capture time.
 TRAFFIC = {
     # integration at degree L+1 (8x8x16 sub-boxes, 48-point z windows): read + write of
-    # one 32-water launch (1.398 GB) scaled by pair-points to the 256-water launch
-    "integrate_ip1": {"bytes_per_launch": 1.0160e+10, "src_sha": "1571dbd8f83ae5f2",
+    # one 32-water launch (1.393 GB) scaled by pair-points to the 256-water launch
+    "integrate_ip1": {"bytes_per_launch": 1.0124e+10, "src_sha": "f56b93e800c9ee4f",
                       "capture": "profiles/integrate_traffic_water32.md"},
 }
 
