@@ -86,3 +86,20 @@ def test_lane_batches_have_their_own_cap():
     batch, keep, _ = p.form(staged, now=0.0)            # the regular cap
     assert names(batch) == ["s1", "s2", "s3", "s4"] and keep == []
     assert BatchPolicy(batch_cost=7.0).lane_cost == 7.0   # default: the regular cap
+
+
+def test_kinds_with_integration_shapes_batch_apart():
+    # the server's kind of a request: (non-orthogonal cell, integration sub-boxes, z
+    # window); plans of different kernels never share a batch, while those of one kind do
+    water = (False, (8, 8, 16), 48)
+    f_shells = (False, (8, 8, 32), 32)
+    skew = (True, (4, 8, 16), 16)
+    p = BatchPolicy(max_batch=8, batch_cost=100.0)
+    staged = [R("w1", 1, kind=water), R("f1", 1, kind=f_shells), R("w2", 1, kind=water),
+              R("s1", 1, kind=skew), R("f2", 1, kind=f_shells), R("w3", 1, kind=water)]
+    out = []
+    while staged:
+        batch, staged, _ = p.form(staged, now=0.0)
+        assert len({r.kind for r in batch}) == 1
+        out.append(names(batch))
+    assert out == [["w1", "w2", "w3"], ["f1", "f2"], ["s1"]]
