@@ -376,6 +376,7 @@ int fft_d2z(Plan& P, int k, const double* in, cufftDoubleComplex* out, cudaStrea
                           P.d.fft_pack, CUFFT_FORWARD));
     }
     GPW_CK(launch_rfft_untangle(P.d.fft_pack, out, P.d.fft_tw + P.tw_off[k], P.lev[k].N, s));
+    ++P.launches;
     return GPW_OK;
   }
   FftEntry* e = P.fft_d2z[k];
@@ -389,6 +390,7 @@ int fft_d2z(Plan& P, int k, const double* in, cufftDoubleComplex* out, cudaStrea
 int fft_z2d(Plan& P, int k, cufftDoubleComplex* in, double* out, cudaStream_t s) {
   if (packed(P, k, out)) {
     GPW_CK(launch_rfft_pack(in, P.d.fft_pack, P.d.fft_tw + P.tw_off[k], P.lev[k].N, s));
+    ++P.launches;
     FftEntry* e = P.fft_z2z[k];
     std::lock_guard<std::mutex> lk(e->mu);
     GPW_CF(cufftSetStream(e->h, s));
