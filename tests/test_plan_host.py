@@ -88,6 +88,14 @@ def test_validation(lib):
     binding.Plan(sk, commit=False, xc="pbe_x").close()
     binding.Plan(systems.skewed(shells=((0, 1), (2, 1))), commit=False, tau=True).close()
     _expect_error(sk, tile=(8, 8, 32))                # and the 4x8x16 sub-boxes
+    # integration z windows: only for shapes compiled with them, and only with an
+    # explicit tile_integ; non-orthogonal cells keep plain windows
+    _expect_error(s, tile_integ=(8, 8, 16), integ_zwin=32)
+    _expect_error(s, tile_integ=(8, 8, 32), integ_zwin=48)
+    _expect_error(s, integ_zwin=48)
+    _expect_error(sk, tile_integ=(8, 8, 16), integ_zwin=48)
+    binding.Plan(s, commit=False, tile_integ=(8, 8, 16), integ_zwin=48).close()
+    binding.Plan(s, commit=False, tile_integ=(8, 8, 16), integ_zwin=16).close()
     flat = sk.with_tau(sk.tau)
     flat.lattice = np.array([[6.0, 0.0, 0.0], [6.0, 0.0, 0.0], [0.0, 0.0, 6.0]])
     _expect_error(flat)                               # dependent rows
